@@ -1,0 +1,274 @@
+"""CPU oracle for the Contact-Field grasp path -- TEST INFRASTRUCTURE ONLY.
+
+Plain, slow, obviously-correct reference implementation (C in ``cf_oracle.c``,
+FP64 kinematics and LP, OpenMP over independent poses / tuples) that the GPU
+library is checked against.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+the CPU-baseline leg of ``bench.py`` may import this package.  It shares no code
+with the GPU library and never imports it.
+
+Functions (paper passages they follow are cited in ``cf_oracle.c``):
+  philox4x32_10       counter-based generator (Salmon et al., SC'11)
+  fk_links            FP64 forward kinematics of one finger (Sec. 2.1)
+  contact_vectors     FK((p,n); i, q) of all surface points of one finger sample
+  Field               the sampled hand contact field as a set of codes
+                      (Sec. 3.3, Alg. 1; Def. Contact Field (Hand))
+  Field.query         contact domains as bitmasks (Sec. 3.2, Sec. 3.3 query)
+  query_masks_brute   literal existential check, tiny inputs only
+  sample_tuples       random k-tuples from k distinct finger domains (Sec. 4.3)
+  closure_lp          linearised GSWO margin of one tuple (Eq. GSWO)
+  score_tuples        margins / accept flags of many tuples
+
+Parity status: every function is pinned by tests under ``tests/`` against
+closed forms, an independent library routine (scipy's HiGHS LP solver, triton's
+Philox in CPU-interpreter mode) or a brute-force definition, except the items
+listed as "parity unpinned" in the design notes (the value of the acceptance
+threshold eps and the synthetic hand surface-point set, which the paper does not
+fix).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from ctypes import POINTER, c_double, c_float, c_int, c_int32, c_int64, c_uint8, c_uint32, c_uint64, c_void_p
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cf_oracle.c")
+_LIB = os.path.join(_HERE, "liborc.so")
+
+__all__ = ["build", "lib", "philox4x32_10", "fk_links", "contact_vectors", "Field",
+           "query_masks_brute", "sample_tuples", "closure_lp", "score_tuples", "num_threads"]
+
+
+def build(force: bool = False) -> str:
+    """Compile cf_oracle.c into liborc.so (plain gcc, no CUDA)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        fp = POINTER(c_float)
+        dp = POINTER(c_double)
+        u32p = POINTER(c_uint32)
+        i32p = POINTER(c_int32)
+        u8p = POINTER(c_uint8)
+        L.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
+        L.orc_fk_links.argtypes = [c_int, fp, fp, fp, dp, dp, dp]
+        L.orc_contact_vectors.argtypes = [c_int, c_int, fp, fp, fp, fp, fp, i32p, dp, fp, fp, dp, dp]
+        L.orc_field_create.restype = c_void_p
+        L.orc_field_create.argtypes = [c_int, c_int, c_int, fp, fp, fp, fp, fp, i32p, fp, c_int, c_float,
+                                       c_int, fp, c_int, c_double, c_double]
+        L.orc_field_free.argtypes = [c_void_p]
+        L.orc_field_sizes.argtypes = [c_void_p, POINTER(c_int64)]
+        L.orc_field_codes.restype = c_int64
+        L.orc_field_codes.argtypes = [c_void_p, c_int, POINTER(c_uint64), c_int64]
+        L.orc_query_masks.argtypes = [c_void_p, c_int, fp, c_int, fp, u32p, u32p, u8p, u32p]
+        L.orc_query_masks_brute.argtypes = [c_int, c_int, c_int, fp, fp, fp, fp, fp, i32p, fp, c_int, c_float,
+                                            c_int, fp, c_int, fp, c_int, fp, u32p]
+        L.orc_sample_tuples.argtypes = [c_int, c_int, c_int, u32p, u32p, c_int, c_int, c_uint64, i32p, u8p]
+        L.orc_closure_lp.restype = c_double
+        L.orc_closure_lp.argtypes = [c_int, dp, dp, c_double, c_int, dp, c_double, dp, POINTER(c_int)]
+        L.orc_score_tuples.argtypes = [c_int, fp, c_int, c_int, i32p, c_float, c_int, fp, c_float, c_float,
+                                       dp, u8p, i32p]
+        L.orc_num_threads.restype = c_int
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray, ct):
+    return a.ctypes.data_as(POINTER(ct))
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(np.asarray(a, dtype=dtype))
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    c = _c(ctr, np.uint32)
+    k = _c(key, np.uint32)
+    out = np.zeros(4, np.uint32)
+    lib().orc_philox4x32_10(_p(c, c_uint32), _p(k, c_uint32), _p(out, c_uint32))
+    return out
+
+
+def fk_links(J: int, base12, axis, offset, q):
+    """Link frames of one finger: (R [J,3,3], t [J,3]) in FP64."""
+    b, a, o = _c(base12, np.float32), _c(axis, np.float32), _c(offset, np.float32)
+    qq = _c(q, np.float64)
+    R = np.zeros((J, 9))
+    t = np.zeros((J, 3))
+    lib().orc_fk_links(J, _p(b, c_float), _p(a, c_float), _p(o, c_float), _p(qq, c_double),
+                       _p(R, c_double), _p(t, c_double))
+    return R.reshape(J, 3, 3), t
+
+
+def contact_vectors(hand, f: int, q):
+    """Contact vectors of all M surface points of finger f at configuration q:
+    (p32, n32, p64, n64) with shapes [M,3]."""
+    J, M = hand.J, hand.M
+    qq = _c(q, np.float64)
+    p32 = np.zeros((M, 3), np.float32)
+    n32 = np.zeros((M, 3), np.float32)
+    p64 = np.zeros((M, 3))
+    n64 = np.zeros((M, 3))
+    b = _c(hand.base[f], np.float32)
+    a = _c(hand.axis[f], np.float32)
+    o = _c(hand.offset[f], np.float32)
+    sp = _c(hand.surf_p[f], np.float32)
+    sn = _c(hand.surf_n[f], np.float32)
+    sl = _c(hand.surf_link[f], np.int32)
+    lib().orc_contact_vectors(J, M, _p(b, c_float), _p(a, c_float), _p(o, c_float), _p(sp, c_float),
+                              _p(sn, c_float), _p(sl, c_int32), _p(qq, c_double), _p(p32, c_float),
+                              _p(n32, c_float), _p(p64, c_double), _p(n64, c_double))
+    return p32, n32, p64, n64
+
+
+def _hand_args(hand):
+    arrs = [_c(hand.base, np.float32), _c(hand.axis, np.float32), _c(hand.offset, np.float32),
+            _c(hand.surf_p, np.float32), _c(hand.surf_n, np.float32), _c(hand.surf_link, np.int32)]
+    ptrs = [_p(arrs[0], c_float), _p(arrs[1], c_float), _p(arrs[2], c_float), _p(arrs[3], c_float),
+            _p(arrs[4], c_float), _p(arrs[5], c_int32)]
+    return arrs, ptrs
+
+
+class Field:
+    """The sampled contact field of a hand as per-finger sets of
+    (cell, bin) codes.  ``band=True`` also keeps the FP64 / tolerance-band code
+    sets used to flag ambiguous entries (tau metres, bin_tol in cosine)."""
+
+    def __init__(self, hand, q: np.ndarray, inv_h, bins: np.ndarray, band: bool = False,
+                 tau: float = 1e-5, bin_tol: float = 1e-6):
+        self.F, self.J, self.M = hand.F, hand.J, hand.M
+        self.B = int(bins.shape[0])
+        self.inv_h = np.float32(inv_h)
+        keep, ptrs = _hand_args(hand)
+        qq = _c(q, np.float32)
+        self._bins = _c(bins, np.float32)
+        S = int(qq.shape[2])
+        self.band = bool(band)
+        self._h = lib().orc_field_create(self.F, self.J, self.M, *ptrs, _p(qq, c_float), S, c_float(self.inv_h),
+                                         self.B, _p(self._bins, c_float), int(band), tau, bin_tol)
+        del keep
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().orc_field_free(h)
+            self._h = None
+
+    def n_codes(self) -> np.ndarray:
+        out = np.zeros(self.F, np.int64)
+        lib().orc_field_sizes(self._h, out.ctypes.data_as(POINTER(c_int64)))
+        return out
+
+    def codes(self, f: int) -> np.ndarray:
+        """Sorted distinct (kx, ky, kz, bin) codes of finger f, int64 [n,4]."""
+        n = int(self.n_codes()[f])
+        raw = np.zeros(n, np.uint64)
+        lib().orc_field_codes(self._h, f, raw.ctypes.data_as(POINTER(c_uint64)), n)
+        off = 32768
+        kx = ((raw >> np.uint64(40)) & np.uint64(0xFFFF)).astype(np.int64) - off
+        ky = ((raw >> np.uint64(24)) & np.uint64(0xFFFF)).astype(np.int64) - off
+        kz = ((raw >> np.uint64(8)) & np.uint64(0xFFFF)).astype(np.int64) - off
+        b = (raw & np.uint64(0xFF)).astype(np.int64)
+        return np.stack([kx, ky, kz, b], axis=1)
+
+    def query(self, soa: np.ndarray, poses: np.ndarray, amb: bool = False, mask64: bool = False):
+        """Domain masks [P,F,W] uint32 and counts [P,F] uint32 (plus optional
+        ambiguity flags [P,F,N] uint8 and FP64-decision masks [P,F,W])."""
+        soa = _c(soa, np.float32)
+        poses = _c(poses, np.float32).reshape(-1, 12)
+        N = int(soa.shape[1])
+        P = int(poses.shape[0])
+        W = (N + 31) // 32
+        masks = np.zeros((P, self.F, W), np.uint32)
+        counts = np.zeros((P, self.F), np.uint32)
+        a = np.zeros((P, self.F, N), np.uint8) if amb else None
+        m64 = np.zeros((P, self.F, W), np.uint32) if mask64 else None
+        if (amb or mask64) and not self.band:
+            raise ValueError("ambiguity / FP64 outputs need Field(..., band=True)")
+        lib().orc_query_masks(self._h, N, _p(soa, c_float), P, _p(poses, c_float), _p(masks, c_uint32),
+                              _p(counts, c_uint32), _p(a, c_uint8) if a is not None else None,
+                              _p(m64, c_uint32) if m64 is not None else None)
+        out = [masks, counts]
+        if amb:
+            out.append(a)
+        if mask64:
+            out.append(m64)
+        return tuple(out)
+
+
+def query_masks_brute(hand, q, inv_h, bins, soa, poses) -> np.ndarray:
+    keep, ptrs = _hand_args(hand)
+    qq = _c(q, np.float32)
+    bb = _c(bins, np.float32)
+    soa = _c(soa, np.float32)
+    poses = _c(poses, np.float32).reshape(-1, 12)
+    N, P = int(soa.shape[1]), int(poses.shape[0])
+    W = (N + 31) // 32
+    masks = np.zeros((P, hand.F, W), np.uint32)
+    lib().orc_query_masks_brute(hand.F, hand.J, hand.M, *ptrs, _p(qq, c_float), int(qq.shape[2]),
+                                c_float(np.float32(inv_h)), int(bb.shape[0]), _p(bb, c_float), N,
+                                _p(soa, c_float), P, _p(poses, c_float), _p(masks, c_uint32))
+    del keep
+    return masks
+
+
+def sample_tuples(masks: np.ndarray, counts: np.ndarray, N: int, T: int, k: int, seed: int):
+    masks = _c(masks, np.uint32)
+    counts = _c(counts, np.uint32)
+    P, F = int(counts.shape[0]), int(counts.shape[1])
+    tuples = np.zeros((P, T, k), np.int32)
+    fingers = np.zeros((P, T, k), np.uint8)
+    lib().orc_sample_tuples(P, F, N, _p(masks, c_uint32), _p(counts, c_uint32), T, k, c_uint64(seed),
+                            _p(tuples, c_int32), _p(fingers, c_uint8))
+    return tuples, fingers
+
+
+def closure_lp(p, n, mu: float, K: int, c, rho: float):
+    """Margin t* of one tuple; returns (t*, t_per_j [k], pivots [k])."""
+    p = _c(p, np.float64).reshape(-1, 3)
+    n = _c(n, np.float64).reshape(-1, 3)
+    k = int(p.shape[0])
+    cc = _c(c, np.float64)
+    tj = np.zeros(k)
+    pv = np.zeros(k, np.int32)
+    t = lib().orc_closure_lp(k, _p(p, c_double), _p(n, c_double), float(mu), int(K), _p(cc, c_double),
+                             float(rho), _p(tj, c_double), pv.ctypes.data_as(POINTER(c_int)))
+    return float(t), tj, pv
+
+
+def score_tuples(soa: np.ndarray, tuples: np.ndarray, mu: float, K: int, c, rho: float, eps: float):
+    """margins (float64, +inf for invalid), accept (uint8), pivots (int32) per tuple."""
+    soa = _c(soa, np.float32)
+    N = int(soa.shape[1])
+    tuples = _c(tuples, np.int32)
+    k = int(tuples.shape[-1])
+    PT = int(tuples.size // k)
+    cc = _c(c, np.float32)
+    margin = np.zeros(PT)
+    accept = np.zeros(PT, np.uint8)
+    piv = np.zeros(PT, np.int32)
+    lib().orc_score_tuples(N, _p(soa, c_float), PT, k, _p(tuples, c_int32), c_float(np.float32(mu)), int(K),
+                           _p(cc, c_float), c_float(np.float32(rho)), c_float(np.float32(eps)),
+                           _p(margin, c_double), _p(accept, c_uint8), _p(piv, c_int32))
+    shp = tuples.shape[:-1]
+    return margin.reshape(shp), accept.reshape(shp), piv.reshape(shp)

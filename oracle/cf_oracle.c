@@ -1,0 +1,806 @@
+/*
+ * CPU oracle for the Contact-Field grasp path (Lightning Grasp, arXiv 2511.07418).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Plain, slow, obviously-correct reference code that
+ * the GPU library is checked against.  Only the test-suite, the smoke check and
+ * the CPU-baseline leg of the benchmark may load this file; the GPU library
+ * shares no source, header, table or constant with it.
+ *
+ * What it computes (each function cites the passage it follows):
+ *   - Philox4x32-10 counter-based generator (Salmon et al., SC'11), used to key
+ *     the random choices of tuple sampling;
+ *   - forward kinematics of a capsule-chain finger in FP64 (Sec. 2.1 notation,
+ *     Def. "Contact Field (Point)": FK((p,n); i, q));
+ *   - the sampled hand contact field as a SET of (finger, voxel cell, normal bin)
+ *     codes (Sec. 3.3 "Implementation", Alg. 1, Def. "Contact Field (Hand)"),
+ *     and the contact domain of an object pose as set membership of the
+ *     object's contact-surface codes (p, -n) (Def. "Contact Surface
+ *     Representation", Sec. 3.2 "Contact Interaction", Sec. 3.3 "Object Contact
+ *     Query");
+ *   - a literal brute-force existential check ("is there a field sample with the
+ *     same code?") for tiny inputs;
+ *   - random k-tuples of contacts from k distinct non-empty finger domains
+ *     (Sec. 4.3 "Contact Domain Generation": randomly select k domains;
+ *     Alg. 2 step "Random(D_i)");
+ *   - the closure margin: the GSWO subproblems (Eq. GSWO, Sec. 2.2) with the
+ *     friction cone replaced by an inscribed K-edge pyramid and the squared norm
+ *     replaced by a torque-weighted max-norm, so that each of the k convex
+ *     subproblems is a linear program, solved by a textbook two-phase dense
+ *     simplex with Bland's rule in FP64.
+ *
+ * Precision: kinematics, geometry and the LP are FP64.  The integer codes that
+ * the GPU decides in FP32 (voxel cell, normal bin) are decided here in the same
+ * precision, from FP32-rounded link transforms with single-rounding fused
+ * multiply-adds in the natural component order; an FP64 evaluation of the same
+ * codes is kept beside them to count the entries that sit within a tolerance
+ * band of a cell or bin boundary (the "ambiguous" entries).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as    */
+/* easy as 1, 2, 3", SC 2011): 4x32-bit counter, 2x32-bit key, 10 rounds of    */
+/* multiply-hi/lo S-boxes with a Weyl key schedule.                            */
+/* ------------------------------------------------------------------------ */
+#define ORC_PHILOX_M0 0xD2511F53u
+#define ORC_PHILOX_M1 0xCD9E8D57u
+#define ORC_PHILOX_W0 0x9E3779B9u
+#define ORC_PHILOX_W1 0xBB67AE85u
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t prod0 = (uint64_t)ORC_PHILOX_M0 * (uint64_t)x0;
+        uint64_t prod1 = (uint64_t)ORC_PHILOX_M1 * (uint64_t)x2;
+        uint32_t y0 = (uint32_t)(prod1 >> 32) ^ x1 ^ k0;
+        uint32_t y1 = (uint32_t)prod1;
+        uint32_t y2 = (uint32_t)(prod0 >> 32) ^ x3 ^ k1;
+        uint32_t y3 = (uint32_t)prod0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+        k0 += ORC_PHILOX_W0;
+        k1 += ORC_PHILOX_W1;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Forward kinematics (FP64).  Chain convention: frame_{-1} = base;           */
+/* frame_j = frame_{j-1} * Trans(offset_{j-1}) * Rot(axis_j, q_j).            */
+/* ------------------------------------------------------------------------ */
+static void rot_axis_angle(const double a[3], double q, double R[9]) {
+    /* Rodrigues: R = cos q I + sin q [a]x + (1 - cos q) a a^T */
+    double c = cos(q), s = sin(q), v = 1.0 - c;
+    R[0] = c + a[0] * a[0] * v;        R[1] = a[0] * a[1] * v - a[2] * s; R[2] = a[0] * a[2] * v + a[1] * s;
+    R[3] = a[1] * a[0] * v + a[2] * s; R[4] = c + a[1] * a[1] * v;        R[5] = a[1] * a[2] * v - a[0] * s;
+    R[6] = a[2] * a[0] * v - a[1] * s; R[7] = a[2] * a[1] * v + a[0] * s; R[8] = c + a[2] * a[2] * v;
+}
+
+static void matmul3(const double A[9], const double B[9], double C[9]) {
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c)
+            C[3 * r + c] = A[3 * r + 0] * B[0 + c] + A[3 * r + 1] * B[3 + c] + A[3 * r + 2] * B[6 + c];
+}
+
+/* Link frames of one finger for one configuration q[J]:
+ * Rout[J][9] (row-major), tout[J][3], both in the palm frame. */
+void orc_fk_links(int J, const float *base12, const float *axis, const float *offset,
+                  const double *q, double *Rout, double *tout) {
+    double R[9] = {base12[0], base12[1], base12[2], base12[4], base12[5], base12[6],
+                   base12[8], base12[9], base12[10]};
+    double t[3] = {base12[3], base12[7], base12[11]};
+    for (int j = 0; j < J; ++j) {
+        if (j > 0) {
+            const float *o = offset + 3 * (j - 1);
+            double o0 = o[0], o1 = o[1], o2 = o[2];
+            double t0 = t[0] + R[0] * o0 + R[1] * o1 + R[2] * o2;
+            double t1 = t[1] + R[3] * o0 + R[4] * o1 + R[5] * o2;
+            double t2 = t[2] + R[6] * o0 + R[7] * o1 + R[8] * o2;
+            t[0] = t0; t[1] = t1; t[2] = t2;
+        }
+        double a[3] = {axis[3 * j + 0], axis[3 * j + 1], axis[3 * j + 2]};
+        double Rj[9], Rn[9];
+        rot_axis_angle(a, q[j], Rj);
+        matmul3(R, Rj, Rn);
+        memcpy(R, Rn, sizeof R);
+        memcpy(Rout + 9 * j, R, sizeof R);
+        memcpy(tout + 3 * j, t, sizeof t);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* FP32 decision arithmetic: single-rounding fmaf in component order x, y, z. */
+/* ------------------------------------------------------------------------ */
+static inline void xform_point32(const float R[9], const float t[3], const float p[3], float o[3]) {
+    o[0] = fmaf(R[2], p[2], fmaf(R[1], p[1], fmaf(R[0], p[0], t[0])));
+    o[1] = fmaf(R[5], p[2], fmaf(R[4], p[1], fmaf(R[3], p[0], t[1])));
+    o[2] = fmaf(R[8], p[2], fmaf(R[7], p[1], fmaf(R[6], p[0], t[2])));
+}
+
+static inline void rotate32(const float R[9], const float n[3], float o[3]) {
+    float m0 = R[0] * n[0], m1 = R[3] * n[0], m2 = R[6] * n[0];
+    o[0] = fmaf(R[2], n[2], fmaf(R[1], n[1], m0));
+    o[1] = fmaf(R[5], n[2], fmaf(R[4], n[1], m1));
+    o[2] = fmaf(R[8], n[2], fmaf(R[7], n[1], m2));
+}
+
+/* cell index along one axis: floor of the exact real product x * inv_h */
+static inline int64_t cell_axis(float x, float inv_h) {
+    return (int64_t)floor((double)x * (double)inv_h);
+}
+
+/* normal bin: argmax_b d_b . m, first maximum wins (lowest index on ties) */
+static inline int bin32(const float m[3], int B, const float *dirs) {
+    int best_b = 0;
+    float best = -INFINITY;
+    for (int b = 0; b < B; ++b) {
+        const float *d = dirs + 3 * b;
+        float s = fmaf(d[2], m[2], fmaf(d[1], m[1], d[0] * m[0]));
+        if (s > best) { best = s; best_b = b; }
+    }
+    return best_b;
+}
+
+/* Contact vectors of one (finger, sample): p32/n32 are the FP32 decision values
+ * (FP32-rounded link transforms, fmaf transform), p64/n64 the FP64 values.
+ * Any output pointer may be NULL. */
+void orc_contact_vectors(int J, int M, const float *base12, const float *axis, const float *offset,
+                         const float *surf_p, const float *surf_n, const int32_t *surf_link,
+                         const double *q, float *p32, float *n32, double *p64, double *n64) {
+    double R[8 * 9], t[8 * 3];
+    orc_fk_links(J, base12, axis, offset, q, R, t);
+    float Rf[8 * 9], tf[8 * 3];
+    for (int i = 0; i < J * 9; ++i) Rf[i] = (float)R[i];
+    for (int i = 0; i < J * 3; ++i) tf[i] = (float)t[i];
+    for (int m = 0; m < M; ++m) {
+        int l = surf_link[m];
+        const float *ps = surf_p + 3 * m, *ns = surf_n + 3 * m;
+        if (p32) xform_point32(Rf + 9 * l, tf + 3 * l, ps, p32 + 3 * m);
+        if (n32) rotate32(Rf + 9 * l, ns, n32 + 3 * m);
+        const double *Rl = R + 9 * l, *tl = t + 3 * l;
+        for (int r = 0; r < 3; ++r) {
+            if (p64) p64[3 * m + r] = tl[r] + Rl[3 * r] * ps[0] + Rl[3 * r + 1] * ps[1] + Rl[3 * r + 2] * ps[2];
+            if (n64) n64[3 * m + r] = Rl[3 * r] * ns[0] + Rl[3 * r + 1] * ns[1] + Rl[3 * r + 2] * ns[2];
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Field as a set of codes                                                    */
+/* ------------------------------------------------------------------------ */
+#define ORC_KOFF 32768
+static inline int in_key_range(int64_t k) { return k > -ORC_KOFF && k < ORC_KOFF - 1; }
+
+static inline uint64_t pack_key(int f, int64_t kx, int64_t ky, int64_t kz, int b) {
+    return ((uint64_t)f << 56) | ((uint64_t)(kx + ORC_KOFF) << 40) | ((uint64_t)(ky + ORC_KOFF) << 24) |
+           ((uint64_t)(kz + ORC_KOFF) << 8) | (uint64_t)b;
+}
+
+typedef struct {
+    uint64_t *v;
+    int64_t n, cap;
+} keyvec;
+
+static void kv_push(keyvec *kv, uint64_t key) {
+    if (kv->n == kv->cap) {
+        kv->cap = kv->cap ? 2 * kv->cap : 1024;
+        kv->v = (uint64_t *)realloc(kv->v, (size_t)kv->cap * sizeof(uint64_t));
+    }
+    kv->v[kv->n++] = key;
+}
+
+static int cmp_u64(const void *a, const void *b) {
+    uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    return (x > y) - (x < y);
+}
+
+static void kv_sort_unique(keyvec *kv) {
+    if (kv->n == 0) return;
+    qsort(kv->v, (size_t)kv->n, sizeof(uint64_t), cmp_u64);
+    int64_t w = 1;
+    for (int64_t i = 1; i < kv->n; ++i)
+        if (kv->v[i] != kv->v[w - 1]) kv->v[w++] = kv->v[i];
+    kv->n = w;
+}
+
+static int kv_has(const keyvec *kv, uint64_t key) {
+    int64_t lo = 0, hi = kv->n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) / 2;
+        if (kv->v[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    return lo < kv->n && kv->v[lo] == key;
+}
+
+typedef struct {
+    int F, B;
+    float inv_h;
+    float *dirs;
+    double tau, bin_tol;
+    int with_band;
+    keyvec *k32;   /* [F] FP32-decision codes of all samples */
+    keyvec *k64;   /* [F] FP64-decision codes */
+    keyvec *kpos;  /* [F] codes a sample could take within the band */
+    keyvec *ksure; /* [F] codes of samples whose code is the same everywhere in the band */
+    int64_t n_samples_out_of_range;
+} orc_field;
+
+/* candidate codes of a vector within the tolerance band (FP64) */
+static int band_cells(double x, double tau, double inv_h, int64_t c[2]) {
+    c[0] = (int64_t)floor((x - tau) * inv_h);
+    c[1] = (int64_t)floor((x + tau) * inv_h);
+    return c[0] == c[1] ? 1 : 2;
+}
+
+static int band_bins(const double m[3], int B, const float *dirs, double tol, int out[64]) {
+    double best = -INFINITY;
+    double s[256];
+    for (int b = 0; b < B; ++b) {
+        s[b] = dirs[3 * b] * m[0] + dirs[3 * b + 1] * m[1] + dirs[3 * b + 2] * m[2];
+        if (s[b] > best) best = s[b];
+    }
+    int n = 0;
+    for (int b = 0; b < B && n < 64; ++b)
+        if (s[b] >= best - tol) out[n++] = b;
+    return n;
+}
+
+static int bin64(const double m[3], int B, const float *dirs) {
+    int best_b = 0;
+    double best = -INFINITY;
+    for (int b = 0; b < B; ++b) {
+        double s = dirs[3 * b] * m[0] + dirs[3 * b + 1] * m[1] + dirs[3 * b + 2] * m[2];
+        if (s > best) { best = s; best_b = b; }
+    }
+    return best_b;
+}
+
+/* Build the sampled contact field of a hand (Sec. 3.3, Alg. 1 input: all
+ * contact vectors FK((p,n); i, q_s) over sampled q_s), as code sets per finger.
+ * q is [F][J][S] float32 (widened to FP64).  with_band != 0 also builds the
+ * FP64 and tolerance-band sets used to count ambiguous entries. */
+void *orc_field_create(int F, int J, int M, const float *base, const float *axis, const float *offset,
+                       const float *surf_p, const float *surf_n, const int32_t *surf_link,
+                       const float *q, int S, float inv_h, int B, const float *dirs,
+                       int with_band, double tau, double bin_tol) {
+    orc_field *fd = (orc_field *)calloc(1, sizeof(orc_field));
+    fd->F = F; fd->B = B; fd->inv_h = inv_h;
+    fd->tau = tau; fd->bin_tol = bin_tol; fd->with_band = with_band;
+    fd->dirs = (float *)malloc(sizeof(float) * 3 * B);
+    memcpy(fd->dirs, dirs, sizeof(float) * 3 * B);
+    fd->k32 = (keyvec *)calloc(F, sizeof(keyvec));
+    fd->k64 = (keyvec *)calloc(F, sizeof(keyvec));
+    fd->kpos = (keyvec *)calloc(F, sizeof(keyvec));
+    fd->ksure = (keyvec *)calloc(F, sizeof(keyvec));
+    int64_t oor = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : oor)
+    for (int f = 0; f < F; ++f) {
+        const float *bf = base + 12 * f, *af = axis + 3 * J * f, *of = offset + 3 * J * f;
+        const float *spf = surf_p + 3 * M * f, *snf = surf_n + 3 * M * f;
+        const int32_t *slf = surf_link + M * f;
+        float *p32 = (float *)malloc(sizeof(float) * 3 * M), *n32 = (float *)malloc(sizeof(float) * 3 * M);
+        double *p64 = (double *)malloc(sizeof(double) * 3 * M), *n64 = (double *)malloc(sizeof(double) * 3 * M);
+        double qs[8];
+        for (int s = 0; s < S; ++s) {
+            for (int j = 0; j < J; ++j) qs[j] = (double)q[((size_t)f * J + j) * S + s];
+            orc_contact_vectors(J, M, bf, af, of, spf, snf, slf, qs, p32, n32,
+                                with_band ? p64 : NULL, with_band ? n64 : NULL);
+            for (int m = 0; m < M; ++m) {
+                int64_t kx = cell_axis(p32[3 * m], inv_h), ky = cell_axis(p32[3 * m + 1], inv_h),
+                        kz = cell_axis(p32[3 * m + 2], inv_h);
+                if (!in_key_range(kx) || !in_key_range(ky) || !in_key_range(kz)) { ++oor; continue; }
+                int b = bin32(n32 + 3 * m, B, dirs);
+                kv_push(&fd->k32[f], pack_key(f, kx, ky, kz, b));
+                if (!with_band) continue;
+                const double *pp = p64 + 3 * m, *nn = n64 + 3 * m;
+                int64_t cx[2], cy[2], cz[2];
+                int nx = band_cells(pp[0], tau, inv_h, cx), ny = band_cells(pp[1], tau, inv_h, cy),
+                    nz = band_cells(pp[2], tau, inv_h, cz);
+                int bins[64];
+                int nb = band_bins(nn, B, dirs, bin_tol, bins);
+                kv_push(&fd->k64[f], pack_key(f, (int64_t)floor(pp[0] * (double)inv_h),
+                                              (int64_t)floor(pp[1] * (double)inv_h),
+                                              (int64_t)floor(pp[2] * (double)inv_h), bin64(nn, B, dirs)));
+                for (int a = 0; a < nx; ++a)
+                    for (int c = 0; c < ny; ++c)
+                        for (int d = 0; d < nz; ++d)
+                            for (int e = 0; e < nb; ++e)
+                                kv_push(&fd->kpos[f], pack_key(f, cx[a], cy[c], cz[d], bins[e]));
+                if (nx == 1 && ny == 1 && nz == 1 && nb == 1)
+                    kv_push(&fd->ksure[f], pack_key(f, cx[0], cy[0], cz[0], bins[0]));
+            }
+        }
+        kv_sort_unique(&fd->k32[f]);
+        kv_sort_unique(&fd->k64[f]);
+        kv_sort_unique(&fd->kpos[f]);
+        kv_sort_unique(&fd->ksure[f]);
+        free(p32); free(n32); free(p64); free(n64);
+    }
+    fd->n_samples_out_of_range = oor;
+    return fd;
+}
+
+void orc_field_free(void *h) {
+    orc_field *fd = (orc_field *)h;
+    if (!fd) return;
+    for (int f = 0; f < fd->F; ++f) {
+        free(fd->k32[f].v); free(fd->k64[f].v); free(fd->kpos[f].v); free(fd->ksure[f].v);
+    }
+    free(fd->k32); free(fd->k64); free(fd->kpos); free(fd->ksure); free(fd->dirs);
+    free(fd);
+}
+
+/* number of distinct (cell, bin) codes per finger, FP32 decisions */
+void orc_field_sizes(const void *h, int64_t *n_codes) {
+    const orc_field *fd = (const orc_field *)h;
+    for (int f = 0; f < fd->F; ++f) n_codes[f] = fd->k32[f].n;
+}
+
+/* copy finger f's sorted FP32 code set (packed keys) into out (capacity cap) */
+int64_t orc_field_codes(const void *h, int f, uint64_t *out, int64_t cap) {
+    const orc_field *fd = (const orc_field *)h;
+    int64_t n = fd->k32[f].n < cap ? fd->k32[f].n : cap;
+    memcpy(out, fd->k32[f].v, (size_t)n * sizeof(uint64_t));
+    return fd->k32[f].n;
+}
+
+/* Contact domains (Sec. 3.2: CF(H) intersected with S(O); Sec. 3.3 object
+ * contact query).  For pose i = (R_i, t_i) (object -> palm) and object point x
+ * with outward normal n_x, the contact-surface vector is (R p_x + t, -(R n_x))
+ * (Def. "Contact Surface Representation" flips the normal).  Bit x of
+ * masks[i][f] is set iff finger f's field contains its (cell, bin) code.
+ * soa is [6][N] (px,py,pz,nx,ny,nz); poses [P][12] row-major (R | t).
+ * masks [P][F][W] with W = ceil(N/32), bit (x & 31) of word x >> 5.
+ * Optional outputs (NULL to skip; need with_band):
+ *   amb    [P][F][N] uint8: 1 if the decision is not the same everywhere within
+ *          the tolerance band (tau metres, bin_tol in cosine);
+ *   mask64 [P][F][W]: decisions with FP64 codes on both sides. */
+void orc_query_masks(const void *h, int N, const float *soa, int P, const float *poses,
+                     uint32_t *masks, uint32_t *counts, uint8_t *amb, uint32_t *mask64) {
+    const orc_field *fd = (const orc_field *)h;
+    const int F = fd->F, B = fd->B, W = (N + 31) / 32;
+    const float inv_h = fd->inv_h;
+    const double tau = fd->tau;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int i = 0; i < P; ++i) {
+        const float *T = poses + 12 * i;
+        const float R[9] = {T[0], T[1], T[2], T[4], T[5], T[6], T[8], T[9], T[10]};
+        const float t[3] = {T[3], T[7], T[11]};
+        uint32_t *mrow = masks + (size_t)i * F * W;
+        memset(mrow, 0, sizeof(uint32_t) * F * W);
+        if (mask64) memset(mask64 + (size_t)i * F * W, 0, sizeof(uint32_t) * F * W);
+        for (int x = 0; x < N; ++x) {
+            const float p[3] = {soa[x], soa[N + x], soa[2 * N + x]};
+            const float n[3] = {soa[3 * N + x], soa[4 * N + x], soa[5 * N + x]};
+            float pq[3], nq[3];
+            xform_point32(R, t, p, pq);
+            rotate32(R, n, nq);
+            const float mq[3] = {-nq[0], -nq[1], -nq[2]};
+            int64_t kx = cell_axis(pq[0], inv_h), ky = cell_axis(pq[1], inv_h), kz = cell_axis(pq[2], inv_h);
+            int ok = in_key_range(kx) && in_key_range(ky) && in_key_range(kz);
+            int b = bin32(mq, B, fd->dirs);
+            for (int f = 0; f < F; ++f)
+                if (ok && kv_has(&fd->k32[f], pack_key(f, kx, ky, kz, b)))
+                    mrow[(size_t)f * W + (x >> 5)] |= 1u << (x & 31);
+            if (!fd->with_band || (!amb && !mask64)) continue;
+            double p64[3], m64[3];
+            for (int r = 0; r < 3; ++r) {
+                p64[r] = (double)t[r] + (double)R[3 * r] * p[0] + (double)R[3 * r + 1] * p[1] + (double)R[3 * r + 2] * p[2];
+                m64[r] = -((double)R[3 * r] * n[0] + (double)R[3 * r + 1] * n[1] + (double)R[3 * r + 2] * n[2]);
+            }
+            int64_t cx[2], cy[2], cz[2];
+            int nx = band_cells(p64[0], tau, inv_h, cx), ny = band_cells(p64[1], tau, inv_h, cy),
+                nz = band_cells(p64[2], tau, inv_h, cz);
+            int bins[64];
+            int nb = band_bins(m64, B, fd->dirs, fd->bin_tol, bins);
+            int64_t ex = (int64_t)floor(p64[0] * (double)inv_h), ey = (int64_t)floor(p64[1] * (double)inv_h),
+                    ez = (int64_t)floor(p64[2] * (double)inv_h);
+            int b64 = bin64(m64, B, fd->dirs);
+            int ok64 = in_key_range(ex) && in_key_range(ey) && in_key_range(ez);
+            for (int f = 0; f < F; ++f) {
+                if (mask64 && ok64 && kv_has(&fd->k64[f], pack_key(f, ex, ey, ez, b64)))
+                    mask64[((size_t)i * F + f) * W + (x >> 5)] |= 1u << (x & 31);
+                if (!amb) continue;
+                int possible = 0, sure = 1;
+                for (int a = 0; a < nx; ++a)
+                    for (int c = 0; c < ny; ++c)
+                        for (int d = 0; d < nz; ++d)
+                            for (int e = 0; e < nb; ++e) {
+                                int rng_ok = in_key_range(cx[a]) && in_key_range(cy[c]) && in_key_range(cz[d]);
+                                uint64_t key = rng_ok ? pack_key(f, cx[a], cy[c], cz[d], bins[e]) : 0;
+                                if (rng_ok && kv_has(&fd->kpos[f], key)) possible = 1;
+                                if (!rng_ok || !kv_has(&fd->ksure[f], key)) sure = 0;
+                            }
+                amb[((size_t)i * F + f) * N + x] = (uint8_t)(possible != sure);
+            }
+        }
+        for (int f = 0; f < F; ++f) {
+            uint32_t c = 0;
+            for (int w = 0; w < W; ++w) c += (uint32_t)__builtin_popcount(mrow[(size_t)f * W + w]);
+            counts[(size_t)i * F + f] = c;
+        }
+    }
+}
+
+/* Literal existential check for tiny inputs: bit x of mask[i][f] is set iff
+ * SOME field sample (s, m) of finger f has the same cell and the same bin as the
+ * contact-surface vector of point x under pose i.  No index, no sorting. */
+void orc_query_masks_brute(int F, int J, int M, const float *base, const float *axis, const float *offset,
+                           const float *surf_p, const float *surf_n, const int32_t *surf_link,
+                           const float *q, int S, float inv_h, int B, const float *dirs,
+                           int N, const float *soa, int P, const float *poses, uint32_t *masks) {
+    const int W = (N + 31) / 32;
+    memset(masks, 0, sizeof(uint32_t) * (size_t)P * F * W);
+    if (M > 128 || J > 8) return;
+    /* per (f, s, m) codes of the samples, recomputed from FK */
+    int64_t *scode = (int64_t *)malloc(sizeof(int64_t) * 4 * (size_t)F * S * M);
+    for (int f = 0; f < F; ++f) {
+        float p32[3 * 128], n32[3 * 128];
+        double qs[8];
+        for (int s = 0; s < S; ++s) {
+            for (int j = 0; j < J; ++j) qs[j] = (double)q[((size_t)f * J + j) * S + s];
+            orc_contact_vectors(J, M, base + 12 * f, axis + 3 * J * f, offset + 3 * J * f, surf_p + 3 * M * f,
+                                surf_n + 3 * M * f, surf_link + M * f, qs, p32, n32, NULL, NULL);
+            for (int m = 0; m < M; ++m) {
+                int64_t *c = scode + 4 * (((size_t)f * S + s) * M + m);
+                c[0] = cell_axis(p32[3 * m], inv_h);
+                c[1] = cell_axis(p32[3 * m + 1], inv_h);
+                c[2] = cell_axis(p32[3 * m + 2], inv_h);
+                c[3] = bin32(n32 + 3 * m, B, dirs);
+            }
+        }
+    }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int i = 0; i < P; ++i) {
+        const float *T = poses + 12 * i;
+        const float R[9] = {T[0], T[1], T[2], T[4], T[5], T[6], T[8], T[9], T[10]};
+        const float t[3] = {T[3], T[7], T[11]};
+        for (int x = 0; x < N; ++x) {
+            const float p[3] = {soa[x], soa[N + x], soa[2 * N + x]};
+            const float n[3] = {soa[3 * N + x], soa[4 * N + x], soa[5 * N + x]};
+            float pq[3], nq[3];
+            xform_point32(R, t, p, pq);
+            rotate32(R, n, nq);
+            const float mq[3] = {-nq[0], -nq[1], -nq[2]};
+            int64_t qc[4] = {cell_axis(pq[0], inv_h), cell_axis(pq[1], inv_h), cell_axis(pq[2], inv_h),
+                             bin32(mq, B, dirs)};
+            for (int f = 0; f < F; ++f) {
+                const int64_t *c = scode + 4 * (size_t)f * S * M;
+                for (int64_t e = 0; e < (int64_t)S * M; ++e, c += 4) {
+                    if (c[0] == qc[0] && c[1] == qc[1] && c[2] == qc[2] && c[3] == qc[3]) {
+                        masks[((size_t)i * F + f) * W + (x >> 5)] |= 1u << (x & 31);
+                        break;
+                    }
+                }
+            }
+        }
+    }
+    free(scode);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Tuple sampling (Sec. 4.3: randomly select k contact domains of distinct    */
+/* fingers; Alg. 2: (p_i, n_i) <- Random(D_i)).                               */
+/* Draw d of tuple (i, tau) is word (d mod 4) of Philox4x32-10 with counter   */
+/* (i, tau, d div 4, 0) and key (seed lo, seed hi).  A uniform integer in     */
+/* [0, m) is floor(u * m / 2^32).  Fingers: partial Fisher-Yates over the     */
+/* non-empty fingers in ascending order with draws 0..k-1; point of chosen    */
+/* finger d: the r-th set bit (ascending) of its mask row, r from draw k + d. */
+/* Fewer than k non-empty fingers: tuple ids -1, finger ids 255.             */
+/* ------------------------------------------------------------------------ */
+static void tuple_draws(uint64_t seed, uint32_t i, uint32_t tau, int ndraw, uint32_t *u) {
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (int blk = 0; 4 * blk < ndraw; ++blk) {
+        uint32_t ctr[4] = {i, tau, (uint32_t)blk, 0u}, out[4];
+        orc_philox4x32_10(ctr, key, out);
+        for (int w = 0; w < 4 && 4 * blk + w < ndraw; ++w) u[4 * blk + w] = out[w];
+    }
+}
+
+static int32_t select_set_bit(const uint32_t *row, int W, uint32_t r) {
+    for (int w = 0; w < W; ++w) {
+        uint32_t v = row[w];
+        uint32_t c = (uint32_t)__builtin_popcount(v);
+        if (r < c) {
+            for (int b = 0; b < 32; ++b)
+                if (v >> b & 1u) {
+                    if (r == 0) return 32 * w + b;
+                    --r;
+                }
+        }
+        r -= c;
+    }
+    return -1;
+}
+
+void orc_sample_tuples(int P, int F, int N, const uint32_t *masks, const uint32_t *counts, int T, int k,
+                       uint64_t seed, int32_t *tuples, uint8_t *fingers) {
+    const int W = (N + 31) / 32;
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < P; ++i) {
+        int nonempty[32], m = 0;
+        for (int f = 0; f < F; ++f)
+            if (counts[(size_t)i * F + f] > 0) nonempty[m++] = f;
+        for (int tau = 0; tau < T; ++tau) {
+            int32_t *tp = tuples + ((size_t)i * T + tau) * k;
+            uint8_t *fp = fingers + ((size_t)i * T + tau) * k;
+            if (m < k) {
+                for (int d = 0; d < k; ++d) { tp[d] = -1; fp[d] = 255; }
+                continue;
+            }
+            uint32_t u[64];
+            tuple_draws(seed, (uint32_t)i, (uint32_t)tau, 2 * k, u);
+            int idx[32];
+            memcpy(idx, nonempty, sizeof(int) * m);
+            for (int d = 0; d < k; ++d) {
+                int j = d + (int)(((uint64_t)u[d] * (uint64_t)(m - d)) >> 32);
+                int tmp = idx[d]; idx[d] = idx[j]; idx[j] = tmp;
+            }
+            for (int d = 0; d < k; ++d) {
+                int f = idx[d];
+                uint32_t cnt = counts[(size_t)i * F + f];
+                uint32_t r = (uint32_t)(((uint64_t)u[k + d] * (uint64_t)cnt) >> 32);
+                tp[d] = select_set_bit(masks + ((size_t)i * F + f) * W, W, r);
+                fp[d] = (uint8_t)f;
+            }
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Closure margin (Eq. GSWO, Sec. 2.2, linearised).                           */
+/* Contact i: point p_i, outward normal n_i (object frame).  Force direction  */
+/* nu_i = -n_i (into the object); tangent basis (x_i, y_i) of nu_i by Duff et */
+/* al., "Building an Orthonormal Basis, Revisited" (JCGT 2017).  Cone edges  */
+/* e_im = nu_i + mu (cos th_m x_i + sin th_m y_i), th_m = 2 pi m / K.          */
+/* Wrench w_im = [e_im ; (p_i - c) x e_im / rho].                              */
+/* LP_j: minimise t s.t. -t <= (sum c_im w_im)_r <= t (r = 1..6),             */
+/*       sum_m c_jm = 1, c >= 0.      margin t* = min_j LP_j.                   */
+/* ------------------------------------------------------------------------ */
+static void onb_duff(const double n[3], double b1[3], double b2[3]) {
+    double sign = copysign(1.0, n[2]);
+    double a = -1.0 / (sign + n[2]);
+    double b = n[0] * n[1] * a;
+    b1[0] = 1.0 + sign * n[0] * n[0] * a; b1[1] = sign * b; b1[2] = -sign * n[0];
+    b2[0] = b; b2[1] = sign + n[1] * n[1] * a; b2[2] = -n[1];
+}
+
+#define ORC_LP_MAXV 160
+#define ORC_LP_ROWS 13
+#define ORC_LP_DTOL 1e-11  /* reduced-cost tolerance */
+#define ORC_LP_PTOL 1e-9   /* smallest admissible pivot entry */
+
+/* Solve M z = rhs (n x n) by Gaussian elimination with partial pivoting; M and
+ * rhs are overwritten (rhs becomes z).  Returns 0 if M is numerically singular. */
+static int dense_solve(int n, double M[ORC_LP_ROWS][ORC_LP_ROWS], double rhs[ORC_LP_ROWS]) {
+    for (int c = 0; c < n; ++c) {
+        int pr = c;
+        for (int r = c + 1; r < n; ++r)
+            if (fabs(M[r][c]) > fabs(M[pr][c])) pr = r;
+        if (fabs(M[pr][c]) < 1e-300) return 0;
+        if (pr != c) {
+            for (int k = 0; k < n; ++k) { double tmp = M[c][k]; M[c][k] = M[pr][k]; M[pr][k] = tmp; }
+            double tmp = rhs[c]; rhs[c] = rhs[pr]; rhs[pr] = tmp;
+        }
+        for (int r = c + 1; r < n; ++r) {
+            double f = M[r][c] / M[c][c];
+            if (f == 0.0) continue;
+            for (int k = c; k < n; ++k) M[r][k] -= f * M[c][k];
+            rhs[r] -= f * rhs[c];
+        }
+    }
+    for (int r = n - 1; r >= 0; --r) {
+        double s = rhs[r];
+        for (int k = r + 1; k < n; ++k) s -= M[r][k] * rhs[k];
+        rhs[r] = s / M[r][r];
+    }
+    return 1;
+}
+
+typedef struct {
+    int nv;
+    double A[ORC_LP_ROWS][ORC_LP_MAXV];
+    double b[ORC_LP_ROWS];
+} orc_lp;
+
+/* x_B = B^-1 b, y = B^-T c_B, u = B^-1 A_e, each from a fresh elimination on
+ * the original columns (no update formulae, so no drift). */
+static int basic_solution(const orc_lp *lp, const int basis[ORC_LP_ROWS], double x[ORC_LP_ROWS]) {
+    double M[ORC_LP_ROWS][ORC_LP_ROWS];
+    for (int r = 0; r < ORC_LP_ROWS; ++r) {
+        for (int c = 0; c < ORC_LP_ROWS; ++c) M[r][c] = lp->A[r][basis[c]];
+        x[r] = lp->b[r];
+    }
+    return dense_solve(ORC_LP_ROWS, M, x);
+}
+
+static int basis_duals(const orc_lp *lp, const int basis[ORC_LP_ROWS], const double *cost, double y[ORC_LP_ROWS]) {
+    double M[ORC_LP_ROWS][ORC_LP_ROWS];
+    for (int r = 0; r < ORC_LP_ROWS; ++r) {
+        for (int c = 0; c < ORC_LP_ROWS; ++c) M[r][c] = lp->A[c][basis[r]];
+        y[r] = cost[basis[r]];
+    }
+    return dense_solve(ORC_LP_ROWS, M, y);
+}
+
+static int basis_direction(const orc_lp *lp, const int basis[ORC_LP_ROWS], int e, double u[ORC_LP_ROWS]) {
+    double M[ORC_LP_ROWS][ORC_LP_ROWS];
+    for (int r = 0; r < ORC_LP_ROWS; ++r) {
+        for (int c = 0; c < ORC_LP_ROWS; ++c) M[r][c] = lp->A[r][basis[c]];
+        u[r] = lp->A[r][e];
+    }
+    return dense_solve(ORC_LP_ROWS, M, u);
+}
+
+/* Revised primal simplex with Bland's rule (lowest-index entering variable with
+ * negative reduced cost; among tied minimum ratios, lowest-index leaving
+ * variable).  Returns the number of basis changes, or -1 (unbounded /
+ * singular / no termination). */
+static int simplex_bland(const orc_lp *lp, int basis[ORC_LP_ROWS], const double *cost, const int *allowed,
+                         double *obj) {
+    const int nv = lp->nv;
+    int piv = 0;
+    double x[ORC_LP_ROWS], y[ORC_LP_ROWS], u[ORC_LP_ROWS];
+    for (;;) {
+        if (!basic_solution(lp, basis, x) || !basis_duals(lp, basis, cost, y)) return -1;
+        int isbasic[ORC_LP_MAXV] = {0};
+        for (int r = 0; r < ORC_LP_ROWS; ++r) isbasic[basis[r]] = 1;
+        int e = -1;
+        for (int v = 0; v < nv && e < 0; ++v) {
+            if (!allowed[v] || isbasic[v]) continue;
+            double d = cost[v];
+            for (int r = 0; r < ORC_LP_ROWS; ++r) d -= y[r] * lp->A[r][v];
+            if (d < -ORC_LP_DTOL) e = v;
+        }
+        if (e < 0) {
+            double z = 0.0;
+            for (int r = 0; r < ORC_LP_ROWS; ++r) z += cost[basis[r]] * x[r];
+            *obj = z;
+            return piv;
+        }
+        if (!basis_direction(lp, basis, e, u)) return -1;
+        int l = -1;
+        double best = INFINITY;
+        for (int r = 0; r < ORC_LP_ROWS; ++r) {
+            if (u[r] <= ORC_LP_PTOL) continue;
+            double ratio = (x[r] > 0.0 ? x[r] : 0.0) / u[r];
+            if (l < 0 || ratio < best - 1e-13 || (ratio <= best + 1e-13 && basis[r] < basis[l])) {
+                if (l < 0 || ratio < best) best = ratio;
+                l = r;
+            }
+        }
+        if (l < 0) return -1;
+        basis[l] = e;
+        if (++piv > 10000) return -1;
+    }
+}
+
+/* one tuple: k contacts with p[k][3], n[k][3]; returns t* and fills
+ * t_per_j[k] and pivots[k] (phase 1 + phase 2 basis changes of LP_j). */
+double orc_closure_lp(int k, const double *p, const double *n, double mu, int K, const double *c, double rho,
+                      double *t_per_j, int *pivots) {
+    const int nc = k * K;          /* c_im, i-major */
+    const int it = nc;             /* t */
+    const int is = nc + 1;         /* slacks s_0..s_11 */
+    const int ia = nc + 13;        /* artificial of the equality row */
+    const int nv = nc + 14;
+    double w[ORC_LP_MAXV][6];
+    for (int i = 0; i < k; ++i) {
+        double nu[3] = {-n[3 * i], -n[3 * i + 1], -n[3 * i + 2]};
+        double x[3], y[3];
+        onb_duff(nu, x, y);
+        double r[3] = {p[3 * i] - c[0], p[3 * i + 1] - c[1], p[3 * i + 2] - c[2]};
+        for (int m = 0; m < K; ++m) {
+            double th = 2.0 * M_PI * (double)m / (double)K;
+            double cs = cos(th), sn = sin(th);
+            double e[3];
+            for (int a = 0; a < 3; ++a) e[a] = nu[a] + mu * (cs * x[a] + sn * y[a]);
+            double *wv = w[i * K + m];
+            wv[0] = e[0]; wv[1] = e[1]; wv[2] = e[2];
+            wv[3] = (r[1] * e[2] - r[2] * e[1]) / rho;
+            wv[4] = (r[2] * e[0] - r[0] * e[2]) / rho;
+            wv[5] = (r[0] * e[1] - r[1] * e[0]) / rho;
+        }
+    }
+    double best = INFINITY;
+    for (int j = 0; j < k; ++j) {
+        orc_lp lp;
+        memset(&lp, 0, sizeof lp);
+        lp.nv = nv;
+        int basis[ORC_LP_ROWS];
+        /* rows 0..5:  sum c w_r - t + s_r = 0;  rows 6..11: -sum c w_r - t + s_{6+r} = 0;
+         * row 12: sum_m c_jm + a = 1 */
+        for (int r = 0; r < 6; ++r) {
+            for (int v = 0; v < nc; ++v) { lp.A[r][v] = w[v][r]; lp.A[6 + r][v] = -w[v][r]; }
+            lp.A[r][it] = -1.0; lp.A[6 + r][it] = -1.0;
+            lp.A[r][is + r] = 1.0; lp.A[6 + r][is + 6 + r] = 1.0;
+            basis[r] = is + r; basis[6 + r] = is + 6 + r;
+        }
+        for (int m = 0; m < K; ++m) lp.A[12][j * K + m] = 1.0;
+        lp.A[12][ia] = 1.0;
+        lp.b[12] = 1.0;
+        basis[12] = ia;
+        double cost1[ORC_LP_MAXV] = {0}, cost2[ORC_LP_MAXV] = {0};
+        int allowed[ORC_LP_MAXV];
+        for (int v = 0; v < nv; ++v) allowed[v] = 1;
+        cost1[ia] = 1.0;
+        double z1 = 0.0, z2 = 0.0;
+        /* phase 1: minimise the artificial */
+        int p1 = simplex_bland(&lp, basis, cost1, allowed, &z1);
+        /* a degenerate artificial left in the basis is exchanged for any column
+         * with a non-zero entry in its row of B^-1 A */
+        for (int r = 0; r < ORC_LP_ROWS && p1 >= 0; ++r) {
+            if (basis[r] != ia) continue;
+            int isbasic[ORC_LP_MAXV] = {0};
+            for (int q = 0; q < ORC_LP_ROWS; ++q) isbasic[basis[q]] = 1;
+            for (int v = 0; v < nv; ++v) {
+                double u[ORC_LP_ROWS];
+                if (v == ia || isbasic[v] || !basis_direction(&lp, basis, v, u)) continue;
+                if (fabs(u[r]) > ORC_LP_PTOL) { basis[r] = v; ++p1; break; }
+            }
+        }
+        allowed[ia] = 0;
+        cost2[it] = 1.0;
+        /* phase 2: minimise t */
+        int p2 = (p1 < 0 || z1 > 1e-9) ? -1 : simplex_bland(&lp, basis, cost2, allowed, &z2);
+        double tj = (p1 < 0 || p2 < 0) ? NAN : z2;
+        if (t_per_j) t_per_j[j] = tj;
+        if (pivots) pivots[j] = (p1 < 0 || p2 < 0) ? -1 : p1 + p2;
+        if (tj < best) best = tj;
+    }
+    return best;
+}
+
+/* Score sampled tuples: margin[P*T] (t*, +inf for invalid tuples),
+ * accept[P*T] = (t* <= eps), pivots[P*T] = total simplex pivots (or NULL).
+ * Points/normals come from soa [6][N] in the object frame; c, rho, mu, K as
+ * above. */
+void orc_score_tuples(int N, const float *soa, int PT, int k, const int32_t *tuples, float mu, int K,
+                      const float *c, float rho, float eps, double *margin, uint8_t *accept, int32_t *pivots) {
+    double cc[3] = {c[0], c[1], c[2]};
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int u = 0; u < PT; ++u) {
+        const int32_t *tp = tuples + (size_t)u * k;
+        int valid = 1;
+        for (int d = 0; d < k; ++d)
+            if (tp[d] < 0 || tp[d] >= N) valid = 0;
+        if (!valid) {
+            margin[u] = INFINITY;
+            accept[u] = 0;
+            if (pivots) pivots[u] = 0;
+            continue;
+        }
+        double p[3 * 16], n[3 * 16];
+        for (int d = 0; d < k; ++d) {
+            int x = tp[d];
+            for (int a = 0; a < 3; ++a) {
+                p[3 * d + a] = soa[(size_t)a * N + x];
+                n[3 * d + a] = soa[(size_t)(3 + a) * N + x];
+            }
+        }
+        double tj[16];
+        int pv[16];
+        double t = orc_closure_lp(k, p, n, (double)mu, K, cc, (double)rho, tj, pv);
+        margin[u] = t;
+        accept[u] = (uint8_t)(t <= (double)eps);
+        if (pivots) {
+            int s = 0;
+            for (int d = 0; d < k; ++d) s += pv[d];
+            pivots[u] = s;
+        }
+    }
+}
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
