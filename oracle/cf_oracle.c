@@ -574,7 +574,8 @@ static void onb_duff(const double n[3], double b1[3], double b2[3]) {
 #define ORC_LP_MAXV 160
 #define ORC_LP_ROWS 13
 #define ORC_LP_DTOL 1e-11  /* reduced-cost tolerance */
-#define ORC_LP_PTOL 1e-9   /* smallest admissible pivot entry */
+#define ORC_LP_PTOL 1e-7   /* smallest admissible pivot entry (entries of A are O(1); smaller
+                              * values of B^-1 A_e are rounding noise of a structural zero) */
 
 /* Solve M z = rhs (n x n) by Gaussian elimination with partial pivoting; M and
  * rhs are overwritten (rhs becomes z).  Returns 0 if M is numerically singular. */
@@ -583,7 +584,7 @@ static int dense_solve(int n, double M[ORC_LP_ROWS][ORC_LP_ROWS], double rhs[ORC
         int pr = c;
         for (int r = c + 1; r < n; ++r)
             if (fabs(M[r][c]) > fabs(M[pr][c])) pr = r;
-        if (fabs(M[pr][c]) < 1e-300) return 0;
+        if (!(fabs(M[pr][c]) > 1e-13)) return 0; /* singular to working precision */
         if (pr != c) {
             for (int k = 0; k < n; ++k) { double tmp = M[c][k]; M[c][k] = M[pr][k]; M[pr][k] = tmp; }
             double tmp = rhs[c]; rhs[c] = rhs[pr]; rhs[pr] = tmp;
@@ -752,7 +753,9 @@ double orc_closure_lp(int k, const double *p, const double *n, double mu, int K,
         double tj = (p1 < 0 || p2 < 0) ? NAN : z2;
         if (t_per_j) t_per_j[j] = tj;
         if (pivots) pivots[j] = (p1 < 0 || p2 < 0) ? -1 : p1 + p2;
-        if (tj < best) best = tj;
+        /* a failed subproblem poisons the margin: never silently dropped */
+        if (isnan(tj) || isnan(best)) best = NAN;
+        else if (tj < best) best = tj;
     }
     return best;
 }

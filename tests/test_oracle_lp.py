@@ -153,3 +153,34 @@ def test_score_tuples_marks_invalid_and_thresholds():
     assert np.isinf(m[1, 2]) and a[1, 2] == 0 and piv[1, 2] == 0
     fin = np.isfinite(m)
     assert np.array_equal(a[fin].astype(bool), m[fin] <= np.float32(0.01))
+
+
+def test_lp_matches_highs_on_tool_faces_with_axis_aligned_normals():
+    """Box faces of the tool object give normals with exact zero components;
+    their wrench columns are partly collinear, a degenerate case for the
+    simplex (rounding noise on structural zeros must never become a pivot)."""
+    import synth
+    obj = synth.tool_composite(4096, 1000)
+    rng = np.random.default_rng(21)
+    axis = np.sum(obj.n == 0.0, axis=1) >= 1
+    pool = np.nonzero(axis)[0]
+    c = obj.centroid.astype(np.float64)
+    for _ in range(120):
+        ids = rng.choice(pool, 3, replace=False)
+        p, n = obj.p[ids].astype(np.float64), obj.n[ids].astype(np.float64)
+        t, tj, piv = oracle.closure_lp(p, n, float(np.float32(0.4)), 8, c, float(obj.rho))
+        ref = _highs_margin(p, n, float(np.float32(0.4)), 8, c, float(obj.rho))
+        assert np.all(np.isfinite(tj))
+        assert np.allclose(tj, ref, atol=1e-9, rtol=1e-8)
+
+
+def test_oracle_workload_margins_are_never_nan():
+    import synth
+    w = synth.workload("hand20_tool", P=6, S=2048)
+    fd = oracle.Field(w.hand, w.q, w.inv_h, w.bins)
+    soa = w.obj.soa()
+    m, cnt = fd.query(soa, w.poses)
+    tup, _ = oracle.sample_tuples(m, cnt, w.obj.N, w.T, w.k, w.seed)
+    mar, _, piv = oracle.score_tuples(soa, tup, w.mu, w.K, w.obj.centroid, w.obj.rho, w.eps)
+    assert not np.isnan(mar).any()
+    assert (piv >= 0).all()
