@@ -1,0 +1,373 @@
+#!/usr/bin/env python3
+"""Benchmark of the Contact-Field grasp hot path on B300.
+
+One step = the whole hot path over one synthetic request: build the hand's
+contact field from its joint samples (FK + binning), query the object's
+contact domains over every palm pose, sample T contact tuples per pose and
+score them with the linearised closure LP.  The metric is valid grasps/s:
+closure-accepted tuples per second of step time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU runs (torchrun, one rank per GPU) are independent replicas: each
+rank synthesises its own request (seed = rank), no data crosses ranks; value =
+accepted tuples of all ranks / max over ranks of the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "hand16_superquadric"
+METRIC = "valid grasps/s"
+UNIT = "grasps/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--e2e-steps", type=int, default=40)
+    ap.add_argument("--cpu-poses", type=int, default=32, help="poses in the oracle's timed sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _config(w):
+    return {"workload": w.name, "fingers": w.hand.F, "dof": w.hand.F * w.hand.J, "points": w.obj.N,
+            "joint_samples": w.S, "voxel_m": w.h, "normal_bins": w.B, "poses": w.P, "tuples_per_pose": w.T,
+            "k": w.k, "mu": w.mu, "pyramid_edges": w.K, "eps": w.eps,
+            "step": "field build + domain query + tuple sampling + closure LP",
+            "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write, untimed)",
+            "parallelism": "replicas"}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for r in csv.reader(io.StringIO(fh.read())):
+                r = [x.strip() for x in r]
+                if len(r) < 10:
+                    continue
+                if self.uuid and self.uuid not in r[1]:
+                    continue
+                rows.append(r)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "", 1).isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "", 1).isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[6 + j].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------------------
+# oracle leg (CPU baseline / reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(w, n_poses: int):
+    """The oracle on a bounded sample: field build (once per hand) and the
+    per-pose path on the first n_poses poses.  Returns the sample's timings."""
+    import numpy as np
+
+    import oracle
+    t0 = time.perf_counter()
+    fd = oracle.Field(w.hand, w.q, w.inv_h, w.bins)
+    t_build = time.perf_counter() - t0
+    soa = w.obj.soa()
+    poses = w.poses[:n_poses]
+    t1 = time.perf_counter()
+    masks, counts = fd.query(soa, poses)
+    tup, _ = oracle.sample_tuples(masks, counts, w.obj.N, w.T, w.k, w.seed)
+    mar, acc, piv = oracle.score_tuples(soa, tup, w.mu, w.K, w.obj.centroid, w.obj.rho, w.eps)
+    t_pose = time.perf_counter() - t1
+    valid = np.isfinite(mar)
+    return {"t_build": t_build, "t_pose": t_pose, "accepted": int(acc.sum()), "n_poses": n_poses,
+            "bland_pivots_per_tuple": float(piv[valid].mean()) if valid.any() else 0.0,
+            "cores": oracle.num_threads(), "field": fd}
+
+
+def cpu_baseline(w, n_poses: int):
+    s = oracle_sample(w, n_poses)
+    scale = w.P / s["n_poses"]
+    step_s = s["t_build"] + scale * s["t_pose"]
+    value = s["accepted"] * scale / step_s
+    return {"value": value, "unit": UNIT, "cores": s["cores"], "kind": "oracle",
+            "sample": f"oracle field build over all {w.S} joint samples x {w.hand.F} fingers "
+                      f"({s['t_build']:.2f} s) + query/sample/score of the first {n_poses} of {w.P} poses "
+                      f"({s['t_pose']:.2f} s); a full step projected as build + {scale:.0f} x sample",
+            "bland_pivots_per_tuple": s["bland_pivots_per_tuple"]}
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    import synth
+    w = synth.workload(args.workload)
+    n = 4
+    t0 = time.perf_counter()
+    fd = oracle.Field(w.hand, w.q, w.inv_h, w.bins)
+    t_build = time.perf_counter() - t0
+    soa = w.obj.soa()
+
+    def step(i):
+        lo = (i * n) % w.P
+        poses = w.poses[lo:lo + n]
+        t = time.perf_counter()
+        masks, counts = fd.query(soa, poses)
+        tup, _ = oracle.sample_tuples(masks, counts, w.obj.N, w.T, w.k, w.seed)
+        _, acc, _ = oracle.score_tuples(soa, tup, w.mu, w.K, w.obj.centroid, w.obj.rho, w.eps)
+        return time.perf_counter() - t, int(acc.sum())
+
+    for i in range(args.warmup):
+        step(i)
+    tot, accd = 0.0, 0
+    for i in range(args.steps):
+        dt, a = step(args.warmup + i)
+        tot += dt + t_build * n / w.P  # the field build, amortised over the full request's poses
+        accd += a
+    value = accd / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(w),
+            "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": oracle.num_threads(),
+                             "sample": f"each step: {n} poses of the {w.P}-pose request (query, sample, score) + the "
+                                       f"field build ({t_build:.2f} s) pro rata {n}/{w.P}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2511_07418_b300 as cf
+    import synth
+
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    props = torch.cuda.get_device_properties(dev)
+
+    w = synth.workload(args.workload, seed=rank)
+    F = w.hand.F
+    q = torch.from_numpy(w.q).to(dev)
+    soa = torch.from_numpy(w.obj.soa()).to(dev)
+    poses = torch.from_numpy(w.poses).to(dev)
+    W = (w.obj.N + 31) // 32
+    masks = torch.empty((w.P, F, W), dtype=torch.int32, device=dev)
+    counts = torch.empty((w.P, F), dtype=torch.int32, device=dev)
+    tuples = torch.empty((w.P, w.T, w.k), dtype=torch.int32, device=dev)
+    fingers = torch.empty((w.P, w.T, w.k), dtype=torch.uint8, device=dev)
+    prm = cf.score_params(w.T, w.k, w.mu, w.K, w.eps, w.obj.centroid, w.obj.rho, w.seed)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    acc_total = torch.zeros((), dtype=torch.int64, device=dev)
+
+    def step(ev):
+        ev[0].record()
+        field = cf.build(w.hand, w.inv_h, w.bins, q)
+        ev[1].record()
+        cf.query_domains(field, soa, poses, masks, counts)
+        ev[2].record()
+        _, _, _, accept = cf.score_tuples(soa, F, masks, counts, prm, tuples, fingers)
+        ev[3].record()
+        acc_total.add_(accept.sum())
+        return field
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(3, args.warmup)):
+        step([torch.cuda.Event(enable_timing=True) for _ in range(4)])
+    acc_total.zero_()
+    barrier()
+    cf.device_counters(reset=True)
+    cf.device_status()
+    sampler = ClockSampler(str(props.uuid) if hasattr(props, "uuid") else None)
+    sampler.start()
+    time.sleep(0.3)
+    evs = []
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))  # evict L2 between steps (not timed)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        step(ev)
+        evs.append(ev)
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    clocks = sampler.stop()
+    status = cf.device_status()
+    counters = cf.device_counters()
+    ms = np.array([[e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3])] for e in evs])
+    total_ms = float(ms.sum())
+    accepted = int(acc_total.item())
+
+    # ---- e2e: the same step through the host-buffer plan ----------------
+    q_h = torch.from_numpy(w.q).pin_memory()
+    soa_h = torch.from_numpy(w.obj.soa()).pin_memory().numpy()
+    poses_h = torch.from_numpy(w.poses).pin_memory().numpy()
+    ht = torch.empty((w.P, w.T, w.k), dtype=torch.int32).pin_memory().numpy()
+    hm = torch.empty((w.P, w.T), dtype=torch.float32).pin_memory().numpy()
+    ha = torch.empty((w.P, w.T), dtype=torch.uint8).pin_memory().numpy()
+    plan = cf.Plan(F, w.obj.N, w.P, prm)
+    q_d = torch.empty_like(q)
+
+    def e2e_step():
+        q_d.copy_(q_h, non_blocking=True)
+        field = cf.build(w.hand, w.inv_h, w.bins, q_d)
+        return plan.run_host(field, soa_h, poses_h, ht, hm, ha)
+
+    for _ in range(3):
+        e2e_step()
+    e2e_s, e2e_acc = 0.0, 0
+    n_e2e = max(1, min(args.e2e_steps, args.steps))
+    for i in range(n_e2e):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_acc += e2e_step()
+        e2e_s += time.perf_counter() - t0
+    h2d = w.q.nbytes + 6 * 4 * w.obj.N + 12 * 4 * w.P
+    d2h = w.P * w.T * (4 * w.k + 4 + 1)
+
+    # ---- reduce over ranks ------------------------------------------------
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms, e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        a = torch.tensor([accepted, e2e_acc], dtype=torch.int64, device=dev)
+        dist.all_reduce(a, op=dist.ReduceOp.SUM)
+        total_ms, e2e_s = float(t[0]), float(t[1])
+        accepted, e2e_acc = int(a[0]), int(a[1])
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    value = accepted / (total_ms / 1e3)
+    per = ms.mean(axis=0)  # build, query, score ms per step (rank 0)
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2032.0
+    n_sm = props.multi_processor_count
+    peak_fp32 = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s: FP32 lanes x FMA x clock
+    pairs = w.P * w.obj.N
+    q_flop = pairs * (18 + 3 * w.B + 3 * F) * 2
+    s_flop_own = (counters["lp_pivots"] * 13 * 39 + counters["tuples_scored"] * w.k * w.K * 15) * 2 / args.steps
+    b_flop = F * w.S * w.hand.M * (18 + 3 + 3 * w.B) * 2
+    kernels = {
+        "k_fk_cell_bounds+k_fk_bin": {"ms": per[0], "tflops": b_flop / (per[0] * 1e-3) / 1e12},
+        "k_query_domains": {"ms": per[1], "tflops": q_flop / (per[1] * 1e-3) / 1e12},
+        "k_sample_score": {"ms": per[2], "tflops": s_flop_own / (per[2] * 1e-3) / 1e12},
+    }
+    for v in kernels.values():
+        v["frac"] = v["tflops"] / peak_fp32
+    dom = max(["k_query_domains", "k_sample_score"], key=lambda k: kernels[k]["ms"])
+    roof = {"kernel": dom, "bound": "alu", "achieved": kernels[dom]["tflops"], "peak": peak_fp32,
+            "unit": "TFLOP/s", "frac": kernels[dom]["frac"], "traffic": None,
+            "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 flop/FMA x {sm_mhz:.0f} MHz median SM clock sampled "
+                          "during the timed region (no FP32 figure in the measured peaks file)",
+            "kernels": kernels}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": _config(w),
+            "value_field_cached": accepted / ((total_ms - float(ms[:, 0].sum())) / 1e3),
+            "accept_rate": accepted / (world * args.steps * w.P * w.T),
+            "breakdown_ms": {"build": per[0], "query": per[1], "sample_score": per[2]},
+            "wall_s_timed_region": t_wall,
+            "gpu_launches": 4 * args.steps,
+            "device_status": status,
+            "lp": {"pivots_per_tuple": counters["lp_pivots"] / max(1, counters["tuples_scored"]),
+                   "lps_per_tuple": counters["lps"] / max(1, counters["tuples_scored"])},
+            "e2e": {"value": e2e_acc / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": n_e2e, "ms_per_step": 1e3 * e2e_s / n_e2e},
+            "roofline": roof, "clocks": clocks}
+    if world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(w, args.cpu_poses)
+        line["cpu_baseline"] = cb
+        bp = cb.pop("bland_pivots_per_tuple")
+        tps = counters["tuples_scored"] / args.steps
+        s_flop_bland = (bp * tps * 13 * 39 + tps * w.k * w.K * 15) * 2
+        roof["score_tflops_with_oracle_bland_pivots"] = s_flop_bland / (per[2] * 1e-3) / 1e12
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,213 @@
+/*
+ * cf.h -- C ABI of libcf, the Contact-Field grasp hot path of Lightning Grasp
+ * (Yin & Abbeel, arXiv 2511.07418) for one NVIDIA B300 (sm_103a).
+ *
+ * Three steps, each a call below:
+ *   cf_build          sampled contact field of a hand: forward kinematics of the
+ *                     hand surface over joint samples, binned into a voxel x
+ *                     normal-bin bit table            (Def. Contact Field (Point),
+ *                     Def. Contact Field (Hand), Sec. 3.3 Implementation, Alg. 1)
+ *   cf_query_domains  contact domains of an object over many palm poses, as
+ *                     per-finger bitmasks             (Def. Contact Surface
+ *                     Representation, Sec. 3.2, Sec. 3.3 Object Contact Query)
+ *   cf_score_tuples   random contact k-tuples from k distinct finger domains and
+ *                     their linearised friction-cone closure margin
+ *                                                     (Sec. 4.3, Alg. 2 Random(D_i),
+ *                     Eq. GSWO of Sec. 2.2)
+ * plus cf_plan_*, the same path driven from host buffers (one object request).
+ *
+ * Conventions
+ *  - Every call returns CF_OK (0) or a CF_E* code; cf_last_error() gives a
+ *    thread-local message.  Nothing throws across the ABI.
+ *  - "d_" pointers are device pointers owned by the caller; libcf never frees
+ *    them.  "host" pointers are read during the call only.
+ *  - Handles (cf_field, cf_plan) are owned by the library and freed by their
+ *    destroy call.
+ *  - Work is queued on the caller's CUDA stream (cf_stream = cudaStream_t, NULL
+ *    = legacy default stream).  cf_build and cf_plan_run_host synchronise that
+ *    stream before returning; cf_query_domains and cf_score_tuples do not.
+ *  - Shapes are checked on the host (CF_EINVAL); a kernel that meets a
+ *    condition it cannot honour (an LP that exceeds its pivot cap) sets a bit in
+ *    a device status word read by cf_device_status().
+ *  - Geometry is FP32, metres.  Row-major 3x4 rigid transforms [R | t].
+ */
+#ifndef CF_H
+#define CF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CF_MAX_FINGERS 8
+#define CF_MAX_JOINTS 8
+#define CF_MAX_SURF 256
+#define CF_MAX_BINS 32
+#define CF_MAX_K 4        /* contacts per tuple */
+#define CF_MAX_EDGES 16   /* friction-pyramid edges; k * K <= 32 */
+
+enum {
+    CF_OK = 0,
+    CF_EINVAL = 1,   /* bad argument / shape */
+    CF_ENOMEM = 2,   /* device or host allocation failed */
+    CF_ECUDA = 3,    /* a CUDA runtime call failed (message has the CUDA error) */
+    CF_ETIMEOUT = 4, /* a bounded device wait ran out */
+    CF_EBUSY = 5,    /* resource in use */
+    CF_EDEVICE = 6,  /* device status word reported a kernel-side condition */
+    CF_EIO = 7       /* file read / write failed */
+};
+
+/* device status bits (cf_device_status) */
+#define CF_DEV_LP_PIVOT_CAP 0x1u   /* an LP stopped at its pivot cap; its margin is an upper bound */
+#define CF_DEV_LP_UNBOUNDED 0x2u   /* an LP ratio test found no pivot row (numerical) */
+
+typedef void *cf_stream; /* cudaStream_t */
+
+/* Hand: F fingers, each a serial chain of J revolute joints (host arrays).
+ * frame_{-1} = base[f]; frame_j = frame_{j-1} * Trans(offset[f][j-1]) *
+ * Rot(axis[f][j], q_j).  Surface point m of finger f lies on link
+ * surf_link[f][m] at surf_p[f][m] with outward normal surf_n[f][m], both in that
+ * link's frame (the hand-surface points of Def. Contact Field (Hand)). */
+typedef struct cf_hand_desc {
+    int32_t n_fingers;        /* F, 1..CF_MAX_FINGERS */
+    int32_t n_joints;         /* J, 1..CF_MAX_JOINTS */
+    int32_t n_surf;           /* M, 1..CF_MAX_SURF */
+    const float *base;        /* [F][12] row-major (R | t), palm frame */
+    const float *axis;        /* [F][J][3] unit joint axes */
+    const float *offset;      /* [F][J][3] link vectors */
+    const float *surf_p;      /* [F][M][3] */
+    const float *surf_n;      /* [F][M][3] */
+    const int32_t *surf_link; /* [F][M], 0..J-1 */
+} cf_hand_desc;
+
+/* Field parameters.  Cells live on one global lattice: cell k covers
+ * [k / inv_h, (k + 1) / inv_h) per axis, k = floor(x * inv_h) of the exact
+ * product.  Normal bin of a unit vector v = argmax_b bin_dirs[b] . v (first
+ * maximum), the fixed direction set of Sec. 3.3 "Memory Consumption". */
+typedef struct cf_field_params {
+    float inv_h;              /* 1 / voxel edge, cells per metre (> 0) */
+    int32_t n_bins;           /* B, 1..CF_MAX_BINS */
+    const float *bin_dirs;    /* host [B][3] */
+} cf_field_params;
+
+typedef struct cf_field cf_field;
+
+typedef struct cf_field_info {
+    int32_t n_fingers, n_joints, n_surf, n_bins, n_samples;
+    float inv_h;
+    int32_t lo[CF_MAX_FINGERS][3];    /* first cell of finger f's table, per axis */
+    int32_t dims[CF_MAX_FINGERS][3];  /* cells per axis (0 if the finger has no sample) */
+    int64_t word_offset[CF_MAX_FINGERS]; /* finger f's table starts at this uint32 word */
+    int64_t table_words;              /* total uint32 words of the bit table */
+    int64_t device_bytes;             /* device memory held by the field */
+    float build_ms;                   /* device time of the two build kernels */
+} cf_field_info;
+
+/* Object surface points + outward unit normals, device SoA, N each. */
+typedef struct cf_points {
+    const float *px, *py, *pz;
+    const float *nx, *ny, *nz;
+    int32_t n;
+} cf_points;
+
+/* Tuple scoring parameters (Eq. GSWO, linearised). */
+typedef struct cf_score_params {
+    int32_t n_tuples;      /* T per pose, >= 1 */
+    int32_t k;             /* contacts per tuple, 2..CF_MAX_K */
+    int32_t n_edges;       /* K friction-pyramid edges, 3..CF_MAX_EDGES, k*K <= 32 */
+    float mu;              /* friction coefficient >= 0 */
+    float eps;             /* accept iff margin <= eps */
+    float centroid[3];     /* torque reference point c (object frame) */
+    float rho;             /* torque scale: torque rows are divided by rho (> 0) */
+    uint64_t seed;         /* key of the tuple draws */
+    int32_t tuples_given;  /* 1: d_tuples holds the tuples (sampling skipped) */
+} cf_score_params;
+
+/* ---- a1 + a2: build the field ------------------------------------------- */
+
+/* Build the sampled contact field of `hand` from n_samples joint
+ * configurations d_q [F][J][n_samples] (device, FP32, SoA per joint).
+ * Every (finger, sample, surface point) contact vector is transformed to the
+ * palm frame and sets bit bin(n) of its cell's word in the finger's table.
+ * Two passes: cell bounds, then binning.  Synchronises `stream`.
+ * Errors: CF_EINVAL (shapes, NULLs, B or J out of range, cell bounds beyond
+ * |k| < 2^20), CF_ENOMEM, CF_ECUDA.  *out is set only on success. */
+int cf_build(const cf_hand_desc *hand, const cf_field_params *prm, const float *d_q, int32_t n_samples,
+             cf_stream stream, cf_field **out);
+
+int cf_field_get_info(const cf_field *field, cf_field_info *info);
+
+/* Copy the bit table (table_words uint32 words) to host memory. */
+int cf_field_copy_table(const cf_field *field, uint32_t *host_words, int64_t capacity_words);
+
+int cf_field_destroy(cf_field *field);
+
+/* Raw save / load of a field (header + bin directions + table). */
+int cf_field_save(const cf_field *field, const char *path);
+int cf_field_load(const char *path, cf_field **out);
+
+/* ---- a3: contact domains ------------------------------------------------- */
+
+/* For every pose i (d_poses [P][12], object -> palm) and object point x, the
+ * contact-surface vector (R p_x + t, -(R n_x)) is looked up in every finger's
+ * table: bit x of d_masks[i][f][W] (W = ceil(N/32) words, bit x & 31 of word
+ * x >> 5) is set iff its cell holds its normal bin.  Bits past N are 0.
+ * d_counts[i][f] = popcount of the row.  d_masks may be NULL (counts only).
+ * Errors: CF_EINVAL, CF_ECUDA (launch). Asynchronous on `stream`. */
+int cf_query_domains(const cf_field *field, const cf_points *obj, const float *d_poses, int32_t n_poses,
+                     uint32_t *d_masks, uint32_t *d_counts, cf_stream stream);
+
+/* ---- a4 + a5: tuple sampling and closure margin -------------------------- */
+
+/* Per pose i and tuple tau (u = i*T + tau): unless prm->tuples_given, choose k
+ * distinct fingers among those with d_counts[i][f] > 0 and one random point of
+ * each domain (Philox4x32-10, key = seed, counter = (i, tau, draw/4, 0)); write
+ * d_tuples [P][T][k] (point ids, -1 if fewer than k fingers are non-empty) and
+ * d_fingers [P][T][k] (255 when invalid).  Then score every valid tuple:
+ * margin = min over j of LP_j = min t s.t. |sum c_im w_im| <= t componentwise,
+ * sum_m c_jm = 1, c >= 0, with w_im = [e_im ; (p_i - c) x e_im / rho] and
+ * e_im = nu_i + mu (cos(2 pi m/K) x_i + sin(2 pi m/K) y_i), nu_i = -n_i,
+ * (x_i, y_i) the Duff et al. 2017 basis of nu_i.  d_margin [P][T] (+inf when
+ * invalid), d_accept [P][T] = margin <= eps.  d_masks / d_counts / d_fingers
+ * may be NULL when tuples_given.  Scratch: a 4-byte work counter, allocated
+ * stream-ordered per call.  Errors: CF_EINVAL, CF_ENOMEM, CF_ECUDA. */
+int cf_score_tuples(const cf_points *obj, int32_t n_fingers, const uint32_t *d_masks, const uint32_t *d_counts,
+                    int32_t n_poses, const cf_score_params *prm, int32_t *d_tuples, uint8_t *d_fingers,
+                    float *d_margin, uint8_t *d_accept, cf_stream stream);
+
+/* ---- one object request from host buffers -------------------------------- */
+
+typedef struct cf_plan cf_plan;
+
+/* Device buffers for objects of up to n_max points and p_max poses, fields of
+ * up to n_fingers fingers, and prm's T and k.  Errors: CF_EINVAL, CF_ENOMEM. */
+int cf_plan_create(int32_t n_fingers, int32_t n_max, int32_t p_max, const cf_score_params *prm, cf_plan **out);
+
+/* One request against `field`: h_soa [6][n] (px..nz), h_poses [P][12] are copied to the device, domains,
+ * tuples and margins computed, results copied back: h_tuples [P][T][k],
+ * h_margin [P][T], h_accept [P][T] (each may be NULL), *h_n_accepted.  Host
+ * buffers should be page-locked for full copy speed.  Synchronises `stream`. */
+int cf_plan_run_host(cf_plan *plan, const cf_field *field, const float *h_soa, int32_t n, const float *h_poses,
+                     int32_t n_poses,
+                     const cf_score_params *prm, int32_t *h_tuples, float *h_margin, uint8_t *h_accept,
+                     int64_t *h_n_accepted, cf_stream stream);
+
+int cf_plan_destroy(cf_plan *plan);
+
+/* ---- diagnostics --------------------------------------------------------- */
+
+const char *cf_last_error(void);
+
+/* Read and clear the device status word (CF_DEV_* bits) of the current device. */
+int cf_device_status(uint32_t *status);
+
+/* Cumulative device counters of the current device since the last reset:
+ * [0] LP pivots performed, [1] LPs solved, [2] tuples scored. */
+int cf_device_counters(uint64_t counters[3], int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CF_H */

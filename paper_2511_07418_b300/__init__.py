@@ -1,0 +1,306 @@
+"""Python binding of libcf, the B300 Contact-Field grasp hot path.
+
+Argument marshalling only: every step runs in the CUDA kernels of ``libcf.so``
+(see ``include/cf.h``).  PyTorch supplies device memory and the current CUDA
+stream.  There is no CPU fallback: importing this package fails if the library
+has not been built (``python -m paper_2511_07418_b300.build_lib``).
+
+Entry points mirror the C ABI:
+  build(hand, inv_h, bin_dirs, q)            -> Field          (cf_build)
+  query_domains(field, soa, poses, ...)      -> masks, counts  (cf_query_domains)
+  score_tuples(soa, n_fingers, masks, counts, params, ...)     (cf_score_tuples)
+  Plan(n_fingers, n_max, p_max, params).run_host(field, ...)   (cf_plan_*)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, Structure, byref, c_char_p, c_float, c_int, c_int32, c_int64, c_uint8, c_uint32, \
+    c_uint64, c_void_p
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcf.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2511_07418_b300.build_lib` "
+                      "(the CUDA library is required; there is no CPU path)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+CF_MAX_FINGERS = 8
+CF_MAX_BINS = 32
+CF_OK = 0
+CF_DEV_LP_PIVOT_CAP = 0x1
+CF_DEV_LP_UNBOUNDED = 0x2
+
+
+class CfError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libcf error {code}: {msg}")
+        self.code = code
+
+
+class HandDesc(Structure):
+    _fields_ = [("n_fingers", c_int32), ("n_joints", c_int32), ("n_surf", c_int32),
+                ("base", POINTER(c_float)), ("axis", POINTER(c_float)), ("offset", POINTER(c_float)),
+                ("surf_p", POINTER(c_float)), ("surf_n", POINTER(c_float)), ("surf_link", POINTER(c_int32))]
+
+
+class FieldParams(Structure):
+    _fields_ = [("inv_h", c_float), ("n_bins", c_int32), ("bin_dirs", POINTER(c_float))]
+
+
+class FieldInfo(Structure):
+    _fields_ = [("n_fingers", c_int32), ("n_joints", c_int32), ("n_surf", c_int32), ("n_bins", c_int32),
+                ("n_samples", c_int32), ("inv_h", c_float),
+                ("lo", (c_int32 * 3) * CF_MAX_FINGERS), ("dims", (c_int32 * 3) * CF_MAX_FINGERS),
+                ("word_offset", c_int64 * CF_MAX_FINGERS), ("table_words", c_int64), ("device_bytes", c_int64),
+                ("build_ms", c_float)]
+
+
+class Points(Structure):
+    _fields_ = [("px", c_void_p), ("py", c_void_p), ("pz", c_void_p), ("nx", c_void_p), ("ny", c_void_p),
+                ("nz", c_void_p), ("n", c_int32)]
+
+
+class ScoreParams(Structure):
+    _fields_ = [("n_tuples", c_int32), ("k", c_int32), ("n_edges", c_int32), ("mu", c_float), ("eps", c_float),
+                ("centroid", c_float * 3), ("rho", c_float), ("seed", c_uint64), ("tuples_given", c_int32)]
+
+
+def _sig(name, args, res=c_int):
+    f = getattr(_lib, name)
+    f.argtypes = args
+    f.restype = res
+    return f
+
+
+_cf_build = _sig("cf_build", [POINTER(HandDesc), POINTER(FieldParams), c_void_p, c_int32, c_void_p, POINTER(c_void_p)])
+_cf_field_get_info = _sig("cf_field_get_info", [c_void_p, POINTER(FieldInfo)])
+_cf_field_copy_table = _sig("cf_field_copy_table", [c_void_p, POINTER(c_uint32), c_int64])
+_cf_field_destroy = _sig("cf_field_destroy", [c_void_p])
+_cf_field_save = _sig("cf_field_save", [c_void_p, c_char_p])
+_cf_field_load = _sig("cf_field_load", [c_char_p, POINTER(c_void_p)])
+_cf_query = _sig("cf_query_domains", [c_void_p, POINTER(Points), c_void_p, c_int32, c_void_p, c_void_p, c_void_p])
+_cf_score = _sig("cf_score_tuples", [POINTER(Points), c_int32, c_void_p, c_void_p, c_int32, POINTER(ScoreParams),
+                                     c_void_p, c_void_p, c_void_p, c_void_p, c_void_p])
+_cf_plan_create = _sig("cf_plan_create", [c_int32, c_int32, c_int32, POINTER(ScoreParams), POINTER(c_void_p)])
+_cf_plan_run_host = _sig("cf_plan_run_host", [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_int32,
+                                              POINTER(ScoreParams), c_void_p, c_void_p, c_void_p, POINTER(c_int64),
+                                              c_void_p])
+_cf_plan_destroy = _sig("cf_plan_destroy", [c_void_p])
+_cf_last_error = _sig("cf_last_error", [], c_char_p)
+_cf_device_status = _sig("cf_device_status", [POINTER(c_uint32)])
+_cf_device_counters = _sig("cf_device_counters", [POINTER(c_uint64), c_int])
+
+EXPORTED = ["cf_build", "cf_field_get_info", "cf_field_copy_table", "cf_field_destroy", "cf_field_save",
+            "cf_field_load", "cf_query_domains", "cf_score_tuples", "cf_plan_create", "cf_plan_run_host",
+            "cf_plan_destroy", "cf_last_error", "cf_device_status", "cf_device_counters"]
+
+
+def _check(rc: int):
+    if rc != CF_OK:
+        raise CfError(rc, _cf_last_error().decode(errors="replace"))
+
+
+def _np(a, dtype):
+    return np.ascontiguousarray(np.asarray(a, dtype=dtype))
+
+
+def _fp(a):
+    return a.ctypes.data_as(POINTER(c_float))
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return c_void_p(s.cuda_stream)
+
+
+def _dev(t, dtype, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return c_void_p(t.data_ptr())
+
+
+def points_struct(soa):
+    """cf_points view of a contiguous [6, N] float32 CUDA tensor (px..nz rows)."""
+    import torch
+    _dev(soa, torch.float32, "soa")
+    if soa.dim() != 2 or soa.shape[0] != 6:
+        raise ValueError("soa must be [6, N]")
+    n = int(soa.shape[1])
+    base = soa.data_ptr()
+    step = 4 * n
+    return Points(*[c_void_p(base + r * step) for r in range(6)], n)
+
+
+class Field:
+    """Library-owned contact field (cf_field)."""
+
+    def __init__(self, handle: int):
+        self._h = c_void_p(handle)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> FieldInfo:
+        inf = FieldInfo()
+        _check(_cf_field_get_info(self._h, byref(inf)))
+        return inf
+
+    def table(self) -> np.ndarray:
+        inf = self.info()
+        out = np.zeros(int(inf.table_words), np.uint32)
+        _check(_cf_field_copy_table(self._h, out.ctypes.data_as(POINTER(c_uint32)), out.size))
+        return out
+
+    def save(self, path: str):
+        _check(_cf_field_save(self._h, path.encode()))
+
+    @staticmethod
+    def load(path: str) -> "Field":
+        h = c_void_p()
+        _check(_cf_field_load(path.encode(), byref(h)))
+        return Field(h.value)
+
+    def close(self):
+        if self._h:
+            _cf_field_destroy(self._h)
+            self._h = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def build(hand, inv_h, bin_dirs, q, stream=None) -> Field:
+    """cf_build: hand is any object with base/axis/offset/surf_p/surf_n/surf_link
+    arrays (host), q a [F, J, S] float32 CUDA tensor of joint samples."""
+    import torch
+    keep = [_np(hand.base, np.float32), _np(hand.axis, np.float32), _np(hand.offset, np.float32),
+            _np(hand.surf_p, np.float32), _np(hand.surf_n, np.float32), _np(hand.surf_link, np.int32)]
+    F, J, M = int(keep[0].shape[0]), int(keep[1].shape[1]), int(keep[3].shape[1])
+    hd = HandDesc(F, J, M, _fp(keep[0]), _fp(keep[1]), _fp(keep[2]), _fp(keep[3]), _fp(keep[4]),
+                  keep[5].ctypes.data_as(POINTER(c_int32)))
+    dirs = _np(bin_dirs, np.float32)
+    prm = FieldParams(float(np.float32(inv_h)), int(dirs.shape[0]), _fp(dirs))
+    qp = _dev(q, torch.float32, "q")
+    if q.dim() != 3 or tuple(q.shape[:2]) != (F, J):
+        raise ValueError(f"q must be [F={F}, J={J}, S]")
+    h = c_void_p()
+    _check(_cf_build(byref(hd), byref(prm), qp, int(q.shape[2]), _stream(stream), byref(h)))
+    return Field(h.value)
+
+
+def query_domains(field: Field, soa, poses, masks=None, counts=None, want_masks: bool = True, stream=None):
+    """cf_query_domains -> (masks [P, F, W] int32 view of uint32 words or None, counts [P, F] int32)."""
+    import torch
+    inf = field.info()
+    F = int(inf.n_fingers)
+    obj = points_struct(soa)
+    P = int(poses.shape[0])
+    _dev(poses, torch.float32, "poses")
+    W = (obj.n + 31) // 32
+    dev = soa.device
+    if want_masks and masks is None:
+        masks = torch.empty((P, F, W), dtype=torch.int32, device=dev)
+    if counts is None:
+        counts = torch.empty((P, F), dtype=torch.int32, device=dev)
+    mp = _dev(masks, torch.int32, "masks") if masks is not None else None
+    _check(_cf_query(field.handle, byref(obj), c_void_p(poses.data_ptr()), P, mp, _dev(counts, torch.int32, "counts"),
+                     _stream(stream)))
+    return masks, counts
+
+
+def score_params(T, k, mu, K, eps, centroid, rho, seed, tuples_given=False) -> ScoreParams:
+    c = (c_float * 3)(*[float(x) for x in np.asarray(centroid, np.float32)])
+    return ScoreParams(int(T), int(k), int(K), float(mu), float(eps), c, float(np.float32(rho)), int(seed),
+                       1 if tuples_given else 0)
+
+
+def score_tuples(soa, n_fingers: int, masks, counts, prm: ScoreParams, tuples=None, fingers=None, stream=None):
+    """cf_score_tuples -> (tuples [P,T,k] int32, fingers [P,T,k] uint8, margin [P,T] f32, accept [P,T] uint8).
+    With prm.tuples_given the given ``tuples`` tensor is scored (masks/counts may be None)."""
+    import torch
+    obj = points_struct(soa)
+    dev = soa.device
+    if prm.tuples_given:
+        if tuples is None:
+            raise ValueError("tuples_given needs tuples")
+        P = int(tuples.shape[0])
+    else:
+        P = int(counts.shape[0])
+    T, k = int(prm.n_tuples), int(prm.k)
+    if tuples is None:
+        tuples = torch.empty((P, T, k), dtype=torch.int32, device=dev)
+    if fingers is None and not prm.tuples_given:
+        fingers = torch.empty((P, T, k), dtype=torch.uint8, device=dev)
+    margin = torch.empty((P, T), dtype=torch.float32, device=dev)
+    accept = torch.empty((P, T), dtype=torch.uint8, device=dev)
+    mp = _dev(masks, torch.int32, "masks") if masks is not None else None
+    cp = _dev(counts, torch.int32, "counts") if counts is not None else None
+    fp = _dev(fingers, torch.uint8, "fingers") if fingers is not None else None
+    _check(_cf_score(byref(obj), int(n_fingers), mp, cp, P, byref(prm), _dev(tuples, torch.int32, "tuples"), fp,
+                     _dev(margin, torch.float32, "margin"), _dev(accept, torch.uint8, "accept"), _stream(stream)))
+    return tuples, fingers, margin, accept
+
+
+class Plan:
+    """cf_plan: one object request driven from host buffers (H2D, query,
+    sample + score, D2H inside the call)."""
+
+    def __init__(self, n_fingers: int, n_max: int, p_max: int, prm: ScoreParams):
+        self.prm = prm
+        h = c_void_p()
+        _check(_cf_plan_create(int(n_fingers), int(n_max), int(p_max), byref(prm), byref(h)))
+        self._h = h
+
+    def run_host(self, field: Field, h_soa: np.ndarray, h_poses: np.ndarray, h_tuples=None, h_margin=None,
+                 h_accept=None, stream=None) -> int:
+        """h_soa [6, N] float32, h_poses [P, 12] float32 (host, ideally pinned
+        numpy views of torch pinned tensors); outputs are optional host arrays.
+        Returns the number of accepted tuples."""
+        n = int(h_soa.shape[1])
+        P = int(h_poses.shape[0])
+        nacc = c_int64(0)
+
+        def ptr(a):
+            return c_void_p(a.ctypes.data) if a is not None else None
+
+        _check(_cf_plan_run_host(self._h, field.handle, ptr(h_soa), n, ptr(h_poses), P, byref(self.prm), ptr(h_tuples),
+                                 ptr(h_margin), ptr(h_accept), byref(nacc), _stream(stream)))
+        return int(nacc.value)
+
+    def close(self):
+        if self._h:
+            _cf_plan_destroy(self._h)
+            self._h = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def device_status() -> int:
+    v = c_uint32(0)
+    _check(_cf_device_status(byref(v)))
+    return int(v.value)
+
+
+def device_counters(reset: bool = False):
+    v = (c_uint64 * 3)()
+    _check(_cf_device_counters(v, 1 if reset else 0))
+    return {"lp_pivots": int(v[0]), "lps": int(v[1]), "tuples_scored": int(v[2])}

@@ -1,0 +1,592 @@
+// Host side of the libcf C ABI: argument checks, field lifecycle, launches,
+// the host-buffer request plan and the device status word / counters.
+#include <limits.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "cf_internal.cuh"
+
+namespace cf {
+size_t score_smem_bytes(int F, int W, int T, int k, bool sampling);
+}
+
+using namespace cf;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+namespace {
+
+thread_local std::string t_err;
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    return fail(e == cudaErrorMemoryAllocation ? CF_ENOMEM : CF_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e),
+                cudaGetErrorString(e));
+}
+
+#define CF_TRY(call, what)                       \
+    do {                                         \
+        cudaError_t e_ = (call);                 \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// device status word and counters (one copy per device that loads libcf)
+// ---------------------------------------------------------------------------
+__device__ unsigned int g_status;
+__device__ unsigned long long g_counters[3];
+
+struct DevState {
+    unsigned int *status = nullptr;
+    unsigned long long *counters = nullptr;
+};
+
+std::mutex g_state_mu;
+DevState g_state[64];
+
+int device_state(DevState *out) {
+    int dev = 0;
+    CF_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(CF_EINVAL, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_state_mu);
+    DevState &s = g_state[dev];
+    if (!s.status) {
+        CF_TRY(cudaGetSymbolAddress((void **)&s.status, g_status), "cudaGetSymbolAddress(status)");
+        CF_TRY(cudaGetSymbolAddress((void **)&s.counters, g_counters), "cudaGetSymbolAddress(counters)");
+    }
+    *out = s;
+    return CF_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// field
+// ---------------------------------------------------------------------------
+struct cf_field {
+    int dev = 0;
+    int F = 0, J = 0, M = 0, S = 0, B = 0;
+    FieldGeom geom{};
+    HandDev hand{};
+    void *d_block = nullptr;    // hand arrays + bounds scratch
+    uint32_t *d_table = nullptr;
+    int64_t table_words = 0;
+    int64_t device_bytes = 0;
+    float build_ms = 0.f;
+};
+
+namespace {
+
+int check_hand(const cf_hand_desc *h) {
+    if (!h) return fail(CF_EINVAL, "hand is NULL");
+    if (h->n_fingers < 1 || h->n_fingers > CF_MAX_FINGERS)
+        return fail(CF_EINVAL, "n_fingers=%d not in [1,%d]", h->n_fingers, CF_MAX_FINGERS);
+    if (h->n_joints < 1 || h->n_joints > CF_MAX_JOINTS)
+        return fail(CF_EINVAL, "n_joints=%d not in [1,%d]", h->n_joints, CF_MAX_JOINTS);
+    if (h->n_surf < 1 || h->n_surf > CF_MAX_SURF)
+        return fail(CF_EINVAL, "n_surf=%d not in [1,%d]", h->n_surf, CF_MAX_SURF);
+    if (!h->base || !h->axis || !h->offset || !h->surf_p || !h->surf_n || !h->surf_link)
+        return fail(CF_EINVAL, "hand array pointer is NULL");
+    for (int i = 0; i < h->n_fingers * h->n_surf; ++i)
+        if (h->surf_link[i] < 0 || h->surf_link[i] >= h->n_joints)
+            return fail(CF_EINVAL, "surf_link[%d]=%d not in [0,%d)", i, h->surf_link[i], h->n_joints);
+    return CF_OK;
+}
+
+int geom_from_params(cf_field *fd, const cf_field_params *prm) {
+    if (!prm) return fail(CF_EINVAL, "params is NULL");
+    if (!(prm->inv_h > 0.f) || !isfinite(prm->inv_h)) return fail(CF_EINVAL, "inv_h must be finite and > 0");
+    if (prm->n_bins < 1 || prm->n_bins > CF_MAX_BINS)
+        return fail(CF_EINVAL, "n_bins=%d not in [1,%d]", prm->n_bins, CF_MAX_BINS);
+    if (!prm->bin_dirs) return fail(CF_EINVAL, "bin_dirs is NULL");
+    FieldGeom &g = fd->geom;
+    g.F = fd->F;
+    g.B = prm->n_bins;
+    g.inv_h = prm->inv_h;
+    g.clamp = (float)(2097152.0 / (double)prm->inv_h);  // |x * inv_h| <= 2^21
+    for (int b = 0; b < g.B; ++b)
+        for (int c = 0; c < 3; ++c) g.dirs[b][c] = prm->bin_dirs[3 * b + c];
+    fd->B = g.B;
+    return CF_OK;
+}
+
+}  // namespace
+
+extern "C" int cf_build(const cf_hand_desc *hand, const cf_field_params *prm, const float *d_q, int32_t n_samples,
+                        cf_stream stream, cf_field **out) {
+    if (!out) return fail(CF_EINVAL, "out is NULL");
+    int rc = check_hand(hand);
+    if (rc) return rc;
+    if (n_samples < 0) return fail(CF_EINVAL, "n_samples < 0");
+    if (n_samples > 0 && !d_q) return fail(CF_EINVAL, "d_q is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    DevState ds;
+    if ((rc = device_state(&ds))) return rc;
+
+    cf_field *fd = new cf_field();
+    const int F = hand->n_fingers, J = hand->n_joints, M = hand->n_surf;
+    fd->F = F; fd->J = J; fd->M = M; fd->S = n_samples;
+    CF_TRY(cudaGetDevice(&fd->dev), "cudaGetDevice");
+    if ((rc = geom_from_params(fd, prm))) { delete fd; return rc; }
+
+    // host staging: surface points sorted by link, link ranges
+    std::vector<float> surf((size_t)F * M * 8, 0.f);
+    std::vector<int> lbeg((size_t)F * (J + 1), 0);
+    for (int f = 0; f < F; ++f) {
+        std::vector<int> order(M);
+        for (int m = 0; m < M; ++m) order[m] = m;
+        const int32_t *lk = hand->surf_link + (size_t)f * M;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lk[a] < lk[b]; });
+        for (int m = 0; m < M; ++m) {
+            const int src = order[m];
+            float *d = &surf[((size_t)f * M + m) * 8];
+            for (int c = 0; c < 3; ++c) {
+                d[c] = hand->surf_p[((size_t)f * M + src) * 3 + c];
+                d[3 + c] = hand->surf_n[((size_t)f * M + src) * 3 + c];
+            }
+            d[6] = (float)lk[src];
+        }
+        int *lb = &lbeg[(size_t)f * (J + 1)];
+        for (int l = 0; l <= J; ++l) {
+            int c = 0;
+            for (int m = 0; m < M; ++m) c += lk[m] < l;
+            lb[l] = c;
+        }
+    }
+    const size_t n_base = (size_t)F * 12, n_axis = (size_t)F * J * 3, n_surf = surf.size();
+    const size_t bytes = sizeof(float) * (n_base + 2 * n_axis + n_surf) + sizeof(int) * (lbeg.size() + 6 * F);
+    cudaError_t e = cudaMalloc(&fd->d_block, bytes);
+    if (e != cudaSuccess) { delete fd; return cuda_fail(e, "cudaMalloc(hand)"); }
+    float *p = (float *)fd->d_block;
+    float *d_base = p; p += n_base;
+    float *d_axis = p; p += n_axis;
+    float *d_off = p; p += n_axis;
+    float *d_surf = p; p += n_surf;
+    int *d_lb = (int *)p;
+    int *d_bounds = d_lb + lbeg.size();
+    std::vector<int> binit((size_t)6 * F);
+    for (int f = 0; f < F; ++f)
+        for (int c = 0; c < 3; ++c) { binit[6 * f + c] = INT_MAX; binit[6 * f + 3 + c] = INT_MIN; }
+    auto bail = [&](cudaError_t err, const char *what) {
+        cudaFree(fd->d_block);
+        if (fd->d_table) cudaFree(fd->d_table);
+        delete fd;
+        return cuda_fail(err, what);
+    };
+#define CF_STEP(call, what) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) return bail(e_, what); } while (0)
+    CF_STEP(cudaMemcpyAsync(d_base, hand->base, sizeof(float) * n_base, cudaMemcpyHostToDevice, st), "copy base");
+    CF_STEP(cudaMemcpyAsync(d_axis, hand->axis, sizeof(float) * n_axis, cudaMemcpyHostToDevice, st), "copy axis");
+    CF_STEP(cudaMemcpyAsync(d_off, hand->offset, sizeof(float) * n_axis, cudaMemcpyHostToDevice, st), "copy offset");
+    CF_STEP(cudaMemcpyAsync(d_surf, surf.data(), sizeof(float) * n_surf, cudaMemcpyHostToDevice, st), "copy surf");
+    CF_STEP(cudaMemcpyAsync(d_lb, lbeg.data(), sizeof(int) * lbeg.size(), cudaMemcpyHostToDevice, st), "copy links");
+    CF_STEP(cudaMemcpyAsync(d_bounds, binit.data(), sizeof(int) * binit.size(), cudaMemcpyHostToDevice, st),
+            "copy bounds");
+    fd->hand = HandDev{F, J, M, d_base, d_axis, d_off, d_surf, d_lb};
+
+    cudaEvent_t ev0, ev1;
+    CF_STEP(cudaEventCreate(&ev0), "event");
+    CF_STEP(cudaEventCreate(&ev1), "event");
+    CF_STEP(cudaEventRecord(ev0, st), "event record");
+    CF_STEP(launch_fk_cell_bounds(fd->hand, d_q, n_samples, fd->geom.inv_h, fd->geom.clamp, d_bounds, st),
+            "launch k_fk_cell_bounds");
+    std::vector<int> bnd((size_t)6 * F);
+    CF_STEP(cudaMemcpyAsync(bnd.data(), d_bounds, sizeof(int) * bnd.size(), cudaMemcpyDeviceToHost, st), "copy bounds");
+    CF_STEP(cudaStreamSynchronize(st), "k_fk_cell_bounds");
+
+    int64_t words = 0;
+    for (int f = 0; f < F; ++f) {
+        const int *b = &bnd[6 * f];
+        if (b[0] > b[3]) {  // finger without samples
+            for (int c = 0; c < 3; ++c) { fd->geom.lo[f][c] = 0; fd->geom.dims[f][c] = 0; }
+            fd->geom.off[f] = words;
+            continue;
+        }
+        for (int c = 0; c < 3; ++c) {
+            if (b[c] <= -(1 << 20) || b[3 + c] >= (1 << 20)) {
+                cudaEventDestroy(ev0); cudaEventDestroy(ev1);
+                cudaFree(fd->d_block); delete fd;
+                return fail(CF_EINVAL, "finger %d cells span [%d,%d] on axis %d: beyond |k| < 2^20 (voxel too small "
+                                       "or hand too large)", f, b[c], b[3 + c], c);
+            }
+            fd->geom.lo[f][c] = b[c];
+            fd->geom.dims[f][c] = b[3 + c] - b[c] + 1;
+        }
+        fd->geom.off[f] = words;
+        words += (int64_t)fd->geom.dims[f][0] * fd->geom.dims[f][1] * fd->geom.dims[f][2];
+        words = (words + 31) & ~(int64_t)31;
+    }
+    fd->table_words = words;
+    if (words > 0) {
+        CF_STEP(cudaMalloc(&fd->d_table, sizeof(uint32_t) * (size_t)words), "cudaMalloc(table)");
+        CF_STEP(cudaMemsetAsync(fd->d_table, 0, sizeof(uint32_t) * (size_t)words, st), "memset table");
+        CF_STEP(launch_fk_bin(fd->hand, d_q, n_samples, fd->geom, fd->d_table, ds.status, st), "launch k_fk_bin");
+    }
+    CF_STEP(cudaEventRecord(ev1, st), "event record");
+    CF_STEP(cudaStreamSynchronize(st), "k_fk_bin");
+    cudaEventElapsedTime(&fd->build_ms, ev0, ev1);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+#undef CF_STEP
+    fd->device_bytes = (int64_t)bytes + (int64_t)sizeof(uint32_t) * words;
+    *out = fd;
+    return CF_OK;
+}
+
+extern "C" int cf_field_get_info(const cf_field *fd, cf_field_info *info) {
+    if (!fd || !info) return fail(CF_EINVAL, "NULL argument");
+    memset(info, 0, sizeof *info);
+    info->n_fingers = fd->F;
+    info->n_joints = fd->J;
+    info->n_surf = fd->M;
+    info->n_bins = fd->B;
+    info->n_samples = fd->S;
+    info->inv_h = fd->geom.inv_h;
+    for (int f = 0; f < fd->F; ++f) {
+        for (int c = 0; c < 3; ++c) {
+            info->lo[f][c] = fd->geom.lo[f][c];
+            info->dims[f][c] = fd->geom.dims[f][c];
+        }
+        info->word_offset[f] = fd->geom.off[f];
+    }
+    info->table_words = fd->table_words;
+    info->device_bytes = fd->device_bytes;
+    info->build_ms = fd->build_ms;
+    return CF_OK;
+}
+
+extern "C" int cf_field_copy_table(const cf_field *fd, uint32_t *host_words, int64_t capacity_words) {
+    if (!fd || (!host_words && fd->table_words > 0)) return fail(CF_EINVAL, "NULL argument");
+    if (capacity_words < fd->table_words)
+        return fail(CF_EINVAL, "capacity %lld < table_words %lld", (long long)capacity_words,
+                    (long long)fd->table_words);
+    if (fd->table_words == 0) return CF_OK;
+    CF_TRY(cudaMemcpy(host_words, fd->d_table, sizeof(uint32_t) * (size_t)fd->table_words, cudaMemcpyDeviceToHost),
+           "copy table");
+    return CF_OK;
+}
+
+extern "C" int cf_field_destroy(cf_field *fd) {
+    if (!fd) return CF_OK;
+    if (fd->d_block) cudaFree(fd->d_block);
+    if (fd->d_table) cudaFree(fd->d_table);
+    delete fd;
+    return CF_OK;
+}
+
+namespace {
+const char kMagic[8] = {'C', 'F', 'F', 'I', 'E', 'L', 'D', '1'};
+}
+
+extern "C" int cf_field_save(const cf_field *fd, const char *path) {
+    if (!fd || !path) return fail(CF_EINVAL, "NULL argument");
+    std::vector<uint32_t> tab((size_t)fd->table_words);
+    int rc = cf_field_copy_table(fd, tab.data(), fd->table_words);
+    if (rc) return rc;
+    FILE *fp = fopen(path, "wb");
+    if (!fp) return fail(CF_EIO, "cannot open %s for writing", path);
+    const int32_t hdr[5] = {fd->F, fd->J, fd->M, fd->S, fd->B};
+    bool ok = fwrite(kMagic, 1, 8, fp) == 8 && fwrite(hdr, sizeof hdr, 1, fp) == 1 &&
+              fwrite(&fd->geom, sizeof fd->geom, 1, fp) == 1 &&
+              fwrite(&fd->table_words, sizeof fd->table_words, 1, fp) == 1 &&
+              (tab.empty() || fwrite(tab.data(), sizeof(uint32_t), tab.size(), fp) == tab.size());
+    ok = (fclose(fp) == 0) && ok;
+    return ok ? CF_OK : fail(CF_EIO, "write to %s failed", path);
+}
+
+extern "C" int cf_field_load(const char *path, cf_field **out) {
+    if (!path || !out) return fail(CF_EINVAL, "NULL argument");
+    FILE *fp = fopen(path, "rb");
+    if (!fp) return fail(CF_EIO, "cannot open %s", path);
+    char magic[8];
+    int32_t hdr[5];
+    cf_field tmp;
+    bool ok = fread(magic, 1, 8, fp) == 8 && memcmp(magic, kMagic, 8) == 0 && fread(hdr, sizeof hdr, 1, fp) == 1 &&
+              fread(&tmp.geom, sizeof tmp.geom, 1, fp) == 1 &&
+              fread(&tmp.table_words, sizeof tmp.table_words, 1, fp) == 1 && tmp.table_words >= 0 &&
+              hdr[0] >= 1 && hdr[0] <= CF_MAX_FINGERS && hdr[4] >= 1 && hdr[4] <= CF_MAX_BINS;
+    std::vector<uint32_t> tab(ok ? (size_t)tmp.table_words : 0);
+    ok = ok && (tab.empty() || fread(tab.data(), sizeof(uint32_t), tab.size(), fp) == tab.size());
+    fclose(fp);
+    if (!ok) return fail(CF_EIO, "%s is not a valid field file", path);
+    cf_field *fd = new cf_field();
+    fd->F = hdr[0]; fd->J = hdr[1]; fd->M = hdr[2]; fd->S = hdr[3]; fd->B = hdr[4];
+    fd->geom = tmp.geom;
+    fd->table_words = tmp.table_words;
+    cudaGetDevice(&fd->dev);
+    if (!tab.empty()) {
+        cudaError_t e = cudaMalloc(&fd->d_table, sizeof(uint32_t) * tab.size());
+        if (e != cudaSuccess) { delete fd; return cuda_fail(e, "cudaMalloc(table)"); }
+        e = cudaMemcpy(fd->d_table, tab.data(), sizeof(uint32_t) * tab.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { cudaFree(fd->d_table); delete fd; return cuda_fail(e, "copy table"); }
+    }
+    fd->device_bytes = (int64_t)sizeof(uint32_t) * fd->table_words;
+    *out = fd;
+    return CF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// query
+// ---------------------------------------------------------------------------
+namespace {
+int check_points(const cf_points *obj) {
+    if (!obj) return fail(CF_EINVAL, "obj is NULL");
+    if (obj->n < 0) return fail(CF_EINVAL, "obj->n < 0");
+    if (obj->n > 0 && (!obj->px || !obj->py || !obj->pz || !obj->nx || !obj->ny || !obj->nz))
+        return fail(CF_EINVAL, "obj array pointer is NULL");
+    return CF_OK;
+}
+}  // namespace
+
+extern "C" int cf_query_domains(const cf_field *fd, const cf_points *obj, const float *d_poses, int32_t n_poses,
+                                uint32_t *d_masks, uint32_t *d_counts, cf_stream stream) {
+    if (!fd) return fail(CF_EINVAL, "field is NULL");
+    int rc = check_points(obj);
+    if (rc) return rc;
+    if (n_poses < 0) return fail(CF_EINVAL, "n_poses < 0");
+    if (n_poses > 0 && (!d_poses || !d_counts)) return fail(CF_EINVAL, "poses / counts pointer is NULL");
+    if (n_poses == 0) return CF_OK;
+    if (fd->table_words == 0) {  // empty field: no hits anywhere
+        CF_TRY(cudaMemsetAsync(d_counts, 0, sizeof(uint32_t) * (size_t)n_poses * fd->F, (cudaStream_t)stream),
+               "memset counts");
+        if (d_masks)
+            CF_TRY(cudaMemsetAsync(d_masks, 0, sizeof(uint32_t) * (size_t)n_poses * fd->F * ((obj->n + 31) / 32),
+                                   (cudaStream_t)stream), "memset masks");
+        return CF_OK;
+    }
+    CF_TRY(launch_query(fd->geom, fd->d_table, *obj, d_poses, n_poses, d_masks, d_counts, (cudaStream_t)stream),
+           "launch k_query_domains");
+    return CF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// sampling + scoring
+// ---------------------------------------------------------------------------
+namespace {
+
+int fill_score_args(const cf_points *obj, int32_t F, const uint32_t *d_masks, const uint32_t *d_counts, int32_t P,
+                    const cf_score_params *prm, int32_t *d_tuples, uint8_t *d_fingers, float *d_margin,
+                    uint8_t *d_accept, ScoreArgs *a) {
+    int rc = check_points(obj);
+    if (rc) return rc;
+    if (!prm) return fail(CF_EINVAL, "params is NULL");
+    if (P < 0) return fail(CF_EINVAL, "n_poses < 0");
+    if (prm->k < 1 || prm->k > CF_MAX_K) return fail(CF_EINVAL, "k=%d not in [1,%d]", prm->k, CF_MAX_K);
+    if (prm->n_edges < 3 || prm->n_edges > CF_MAX_EDGES)
+        return fail(CF_EINVAL, "n_edges=%d not in [3,%d]", prm->n_edges, CF_MAX_EDGES);
+    if (prm->k * prm->n_edges > 32) return fail(CF_EINVAL, "k * n_edges = %d > 32", prm->k * prm->n_edges);
+    if (prm->n_tuples < 1) return fail(CF_EINVAL, "n_tuples < 1");
+    if (!(prm->mu >= 0.f) || !isfinite(prm->mu)) return fail(CF_EINVAL, "mu must be finite and >= 0");
+    if (!(prm->rho > 0.f) || !isfinite(prm->rho)) return fail(CF_EINVAL, "rho must be finite and > 0");
+    if (P > 0 && (!d_tuples || !d_margin || !d_accept)) return fail(CF_EINVAL, "output pointer is NULL");
+    const bool sampling = !prm->tuples_given;
+    if (sampling) {
+        if (F < 1 || F > CF_MAX_FINGERS) return fail(CF_EINVAL, "n_fingers=%d not in [1,%d]", F, CF_MAX_FINGERS);
+        if (P > 0 && (!d_masks || !d_counts)) return fail(CF_EINVAL, "masks / counts pointer is NULL");
+    }
+    const int W = (obj->n + 31) / 32;
+    const size_t smem = score_smem_bytes(sampling ? F : 0, W, prm->n_tuples, prm->k, sampling);
+    int dev = 0, optin = 0;
+    CF_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+    CF_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "device attribute");
+    if (smem + 1024 > (size_t)optin)
+        return fail(CF_EINVAL, "a pose's domains and tuples need %zu B of shared memory (limit %d): reduce N or T",
+                    smem, optin);
+    DevState ds;
+    if ((rc = device_state(&ds))) return rc;
+    memset(a, 0, sizeof *a);
+    a->px = obj->px; a->py = obj->py; a->pz = obj->pz;
+    a->nx = obj->nx; a->ny = obj->ny; a->nz = obj->nz;
+    a->N = obj->n; a->W = W; a->F = sampling ? F : 0; a->P = P;
+    a->masks = d_masks; a->counts = d_counts;
+    a->T = prm->n_tuples; a->k = prm->k; a->K = prm->n_edges;
+    a->mu = prm->mu; a->eps = prm->eps;
+    a->cx = prm->centroid[0]; a->cy = prm->centroid[1]; a->cz = prm->centroid[2];
+    a->inv_rho = (float)(1.0 / (double)prm->rho);
+    for (int m = 0; m < CF_MAX_EDGES; ++m) {
+        const double th = 2.0 * M_PI * (double)m / (double)prm->n_edges;
+        a->cs[m] = (float)cos(th);
+        a->sn[m] = (float)sin(th);
+    }
+    a->seed_lo = (uint32_t)prm->seed;
+    a->seed_hi = (uint32_t)(prm->seed >> 32);
+    a->tuples_given = prm->tuples_given ? 1 : 0;
+    a->tuples = d_tuples; a->fingers = d_fingers; a->margin = d_margin; a->accept = d_accept;
+    a->status = ds.status;
+    a->counters = ds.counters;
+    return CF_OK;
+}
+
+}  // namespace
+
+extern "C" int cf_score_tuples(const cf_points *obj, int32_t n_fingers, const uint32_t *d_masks,
+                               const uint32_t *d_counts, int32_t n_poses, const cf_score_params *prm,
+                               int32_t *d_tuples, uint8_t *d_fingers, float *d_margin, uint8_t *d_accept,
+                               cf_stream stream) {
+    ScoreArgs a;
+    int rc = fill_score_args(obj, n_fingers, d_masks, d_counts, n_poses, prm, d_tuples, d_fingers, d_margin,
+                             d_accept, &a);
+    if (rc) return rc;
+    if (n_poses == 0) return CF_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned int *work = nullptr;
+    CF_TRY(cudaMallocAsync((void **)&work, sizeof(unsigned int), st), "cudaMallocAsync(work counter)");
+    cudaError_t e = cudaMemsetAsync(work, 0, sizeof(unsigned int), st);
+    if (e == cudaSuccess) {
+        a.work = work;
+        e = launch_score(a, st);
+    }
+    cudaError_t e2 = cudaFreeAsync(work, st);
+    if (e != cudaSuccess) return cuda_fail(e, "launch k_sample_score");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync(work counter)");
+    return CF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// plan: one object request from host buffers
+// ---------------------------------------------------------------------------
+struct cf_plan {
+    int n_max = 0, p_max = 0, T = 0, k = 0, F = 0;
+    void *d_block = nullptr;
+    float *d_soa = nullptr, *d_poses = nullptr, *d_margin = nullptr;
+    uint32_t *d_masks = nullptr, *d_counts = nullptr;
+    int32_t *d_tuples = nullptr;
+    uint8_t *d_fingers = nullptr, *d_accept = nullptr;
+    unsigned int *d_work = nullptr;
+    std::vector<uint8_t> h_accept;
+};
+
+extern "C" int cf_plan_create(int32_t n_fingers, int32_t n_max, int32_t p_max, const cf_score_params *prm,
+                              cf_plan **out) {
+    if (!prm || !out) return fail(CF_EINVAL, "NULL argument");
+    if (n_fingers < 1 || n_fingers > CF_MAX_FINGERS) return fail(CF_EINVAL, "n_fingers=%d not in [1,%d]", n_fingers,
+                                                                 CF_MAX_FINGERS);
+    if (n_max < 1 || p_max < 1) return fail(CF_EINVAL, "n_max and p_max must be >= 1");
+    if (prm->n_tuples < 1 || prm->k < 1 || prm->k > CF_MAX_K) return fail(CF_EINVAL, "bad T or k");
+    cf_plan *pl = new cf_plan();
+    pl->n_max = n_max; pl->p_max = p_max; pl->T = prm->n_tuples; pl->k = prm->k; pl->F = n_fingers;
+    const size_t W = (size_t)(n_max + 31) / 32, P = (size_t)p_max, PT = P * pl->T;
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t b_soa = al(sizeof(float) * 6 * n_max), b_pose = al(sizeof(float) * 12 * P),
+                 b_mask = al(sizeof(uint32_t) * P * pl->F * W), b_cnt = al(sizeof(uint32_t) * P * pl->F),
+                 b_tup = al(sizeof(int32_t) * PT * pl->k), b_fin = al(PT * pl->k), b_mar = al(sizeof(float) * PT),
+                 b_acc = al(PT), b_work = 256;
+    const size_t total = b_soa + b_pose + b_mask + b_cnt + b_tup + b_fin + b_mar + b_acc + b_work;
+    cudaError_t e = cudaMalloc(&pl->d_block, total);
+    if (e != cudaSuccess) { delete pl; return cuda_fail(e, "cudaMalloc(plan)"); }
+    char *p = (char *)pl->d_block;
+    pl->d_soa = (float *)p; p += b_soa;
+    pl->d_poses = (float *)p; p += b_pose;
+    pl->d_masks = (uint32_t *)p; p += b_mask;
+    pl->d_counts = (uint32_t *)p; p += b_cnt;
+    pl->d_tuples = (int32_t *)p; p += b_tup;
+    pl->d_fingers = (uint8_t *)p; p += b_fin;
+    pl->d_margin = (float *)p; p += b_mar;
+    pl->d_accept = (uint8_t *)p; p += b_acc;
+    pl->d_work = (unsigned int *)p;
+    pl->h_accept.resize(PT);
+    *out = pl;
+    return CF_OK;
+}
+
+extern "C" int cf_plan_run_host(cf_plan *pl, const cf_field *fd, const float *h_soa, int32_t n, const float *h_poses,
+                                int32_t n_poses, const cf_score_params *prm, int32_t *h_tuples, float *h_margin,
+                                uint8_t *h_accept, int64_t *h_n_accepted, cf_stream stream) {
+    if (!pl || !fd || !prm || (n > 0 && !h_soa) || (n_poses > 0 && !h_poses)) return fail(CF_EINVAL, "NULL argument");
+    if (fd->F > pl->F) return fail(CF_EINVAL, "field has %d fingers, plan holds %d", fd->F, pl->F);
+    if (n < 0 || n > pl->n_max) return fail(CF_EINVAL, "n=%d not in [0,%d]", n, pl->n_max);
+    if (n_poses < 0 || n_poses > pl->p_max) return fail(CF_EINVAL, "n_poses=%d not in [0,%d]", n_poses, pl->p_max);
+    if (prm->n_tuples != pl->T || prm->k != pl->k) return fail(CF_EINVAL, "T / k differ from the plan's");
+    if (prm->tuples_given) return fail(CF_EINVAL, "a plan samples its own tuples");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t PT = (size_t)n_poses * pl->T;
+    if (n > 0) CF_TRY(cudaMemcpyAsync(pl->d_soa, h_soa, sizeof(float) * 6 * n, cudaMemcpyHostToDevice, st), "H2D points");
+    if (n_poses > 0)
+        CF_TRY(cudaMemcpyAsync(pl->d_poses, h_poses, sizeof(float) * 12 * n_poses, cudaMemcpyHostToDevice, st),
+               "H2D poses");
+    cf_points obj{pl->d_soa, pl->d_soa + n, pl->d_soa + 2 * n, pl->d_soa + 3 * n, pl->d_soa + 4 * n,
+                  pl->d_soa + 5 * n, n};
+    int rc = cf_query_domains(fd, &obj, pl->d_poses, n_poses, pl->d_masks, pl->d_counts, stream);
+    if (rc) return rc;
+    ScoreArgs a;
+    rc = fill_score_args(&obj, fd->F, pl->d_masks, pl->d_counts, n_poses, prm, pl->d_tuples, pl->d_fingers,
+                         pl->d_margin, pl->d_accept, &a);
+    if (rc) return rc;
+    if (n_poses > 0) {
+        CF_TRY(cudaMemsetAsync(pl->d_work, 0, sizeof(unsigned int), st), "memset work");
+        a.work = pl->d_work;
+        CF_TRY(launch_score(a, st), "launch k_sample_score");
+    }
+    uint8_t *acc = h_accept ? h_accept : pl->h_accept.data();
+    if (PT > 0) {
+        if (h_tuples)
+            CF_TRY(cudaMemcpyAsync(h_tuples, pl->d_tuples, sizeof(int32_t) * PT * pl->k, cudaMemcpyDeviceToHost, st),
+                   "D2H tuples");
+        if (h_margin)
+            CF_TRY(cudaMemcpyAsync(h_margin, pl->d_margin, sizeof(float) * PT, cudaMemcpyDeviceToHost, st), "D2H margin");
+        CF_TRY(cudaMemcpyAsync(acc, pl->d_accept, PT, cudaMemcpyDeviceToHost, st), "D2H accept");
+    }
+    CF_TRY(cudaStreamSynchronize(st), "plan run");
+    if (h_n_accepted) {
+        int64_t c = 0;
+        for (size_t u = 0; u < PT; ++u) c += acc[u] != 0;
+        *h_n_accepted = c;
+    }
+    return CF_OK;
+}
+
+extern "C" int cf_plan_destroy(cf_plan *pl) {
+    if (!pl) return CF_OK;
+    if (pl->d_block) cudaFree(pl->d_block);
+    delete pl;
+    return CF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// diagnostics
+// ---------------------------------------------------------------------------
+extern "C" const char *cf_last_error(void) { return t_err.c_str(); }
+
+extern "C" int cf_device_status(uint32_t *status) {
+    if (!status) return fail(CF_EINVAL, "NULL argument");
+    DevState ds;
+    int rc = device_state(&ds);
+    if (rc) return rc;
+    unsigned int v = 0;
+    CF_TRY(cudaMemcpy(&v, ds.status, sizeof v, cudaMemcpyDeviceToHost), "read status");
+    const unsigned int zero = 0;
+    CF_TRY(cudaMemcpy(ds.status, &zero, sizeof zero, cudaMemcpyHostToDevice), "clear status");
+    *status = v;
+    return CF_OK;
+}
+
+extern "C" int cf_device_counters(uint64_t counters[3], int reset) {
+    if (!counters) return fail(CF_EINVAL, "NULL argument");
+    DevState ds;
+    int rc = device_state(&ds);
+    if (rc) return rc;
+    unsigned long long v[3];
+    CF_TRY(cudaMemcpy(v, ds.counters, sizeof v, cudaMemcpyDeviceToHost), "read counters");
+    for (int i = 0; i < 3; ++i) counters[i] = v[i];
+    if (reset) {
+        const unsigned long long z[3] = {0, 0, 0};
+        CF_TRY(cudaMemcpy(ds.counters, z, sizeof z, cudaMemcpyHostToDevice), "reset counters");
+    }
+    return CF_OK;
+}

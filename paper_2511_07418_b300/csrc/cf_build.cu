@@ -1,0 +1,192 @@
+// Contact-field build kernels (rows a1 + a2 of the hot path).
+//
+// Def. "Contact Field (Point)" / "Contact Field (Hand)": the field of a hand is
+// the set of contact vectors FK((p, n); i, q) of its surface points over the
+// configuration space; Sec. 3.3 approximates it by randomly sampled q and
+// Alg. 1 organises the samples in boxes of a grid cover, each box holding the
+// normals that fall in it.  Here the grid cover is a dense per-finger table of
+// voxels on one global lattice (cell k = floor(x * inv_h)) and a box's normal
+// set is a B-bit word: bit b is set iff some sample in the cell has normal bin
+// b (the fixed-direction normal index of Sec. 3.3 "Memory Consumption").
+//
+// Thread per (finger, joint sample).  The kinematic chain is evaluated in FP64
+// and rounded to FP32 once per link; each surface point is then transformed
+// with single-rounding FP32 FMAs (component order x, y, z).  Two passes:
+// k_fk_cell_bounds (per-finger cell AABB -> table extents) and k_fk_bin
+// (atomicOr of the sample's bin into its cell word).
+#include <limits.h>
+
+#include "cf_internal.cuh"
+
+namespace cf {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// Link frames of finger f for sample s: FP64 chain, FP32 result per link.
+template <int J>
+__device__ __forceinline__ void link_frames(const HandDev &h, int f, const float *__restrict__ q, int S, int s,
+                                            float R[J][9], float t[J][3]) {
+    const float *b = h.base + 12 * f;
+    double Rd[9] = {b[0], b[1], b[2], b[4], b[5], b[6], b[8], b[9], b[10]};
+    double td[3] = {b[3], b[7], b[11]};
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        if (j > 0) {
+            const float *o = h.offset + 3 * (f * J + j - 1);
+            const double o0 = o[0], o1 = o[1], o2 = o[2];
+            const double t0 = td[0] + Rd[0] * o0 + Rd[1] * o1 + Rd[2] * o2;
+            const double t1 = td[1] + Rd[3] * o0 + Rd[4] * o1 + Rd[5] * o2;
+            const double t2 = td[2] + Rd[6] * o0 + Rd[7] * o1 + Rd[8] * o2;
+            td[0] = t0; td[1] = t1; td[2] = t2;
+        }
+        const float *a = h.axis + 3 * (f * J + j);
+        const double ax = a[0], ay = a[1], az = a[2];
+        double sq, cq;
+        sincos((double)q[((size_t)f * J + j) * S + s], &sq, &cq);
+        const double v = 1.0 - cq;
+        // axis-angle rotation (Rodrigues)
+        const double Q[9] = {cq + ax * ax * v,      ax * ay * v - az * sq, ax * az * v + ay * sq,
+                             ay * ax * v + az * sq, cq + ay * ay * v,      ay * az * v - ax * sq,
+                             az * ax * v - ay * sq, az * ay * v + ax * sq, cq + az * az * v};
+        double Rn[9];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                Rn[3 * r + c] = Rd[3 * r] * Q[c] + Rd[3 * r + 1] * Q[3 + c] + Rd[3 * r + 2] * Q[6 + c];
+#pragma unroll
+        for (int e = 0; e < 9; ++e) {
+            Rd[e] = Rn[e];
+            R[j][e] = (float)Rn[e];
+        }
+        t[j][0] = (float)td[0];
+        t[j][1] = (float)td[1];
+        t[j][2] = (float)td[2];
+    }
+}
+
+// Stage finger f's surface points and link ranges in shared memory.
+__device__ __forceinline__ void stage_surface(const HandDev &h, int f, float *s_surf, int *s_lb) {
+    const float *src = h.surf + (size_t)f * h.M * 8;
+    for (int i = threadIdx.x; i < h.M * 8; i += blockDim.x) s_surf[i] = src[i];
+    for (int i = threadIdx.x; i <= h.J; i += blockDim.x) s_lb[i] = h.link_begin[f * (h.J + 1) + i];
+}
+
+template <int J>
+__global__ void __launch_bounds__(kThreads) k_fk_cell_bounds(HandDev h, const float *__restrict__ q, int S,
+                                                             float inv_h, float clamp, int *bounds) {
+    extern __shared__ float s_surf[];
+    __shared__ int s_lb[CF_MAX_JOINTS + 1];
+    const int f = blockIdx.y;
+    stage_surface(h, f, s_surf, s_lb);
+    __syncthreads();
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    int mn0 = INT_MAX, mn1 = INT_MAX, mn2 = INT_MAX, mx0 = INT_MIN, mx1 = INT_MIN, mx2 = INT_MIN;
+    if (s < S) {
+        float R[J][9], t[J][3];
+        link_frames<J>(h, f, q, S, s, R, t);
+#pragma unroll
+        for (int l = 0; l < J; ++l) {
+            for (int m = s_lb[l]; m < s_lb[l + 1]; ++m) {
+                const float *sp = s_surf + 8 * m;
+                const float x = xf_row(R[l][0], R[l][1], R[l][2], t[l][0], sp[0], sp[1], sp[2]);
+                const float y = xf_row(R[l][3], R[l][4], R[l][5], t[l][1], sp[0], sp[1], sp[2]);
+                const float z = xf_row(R[l][6], R[l][7], R[l][8], t[l][2], sp[0], sp[1], sp[2]);
+                const int kx = cell_floor(x, inv_h, clamp), ky = cell_floor(y, inv_h, clamp),
+                          kz = cell_floor(z, inv_h, clamp);
+                mn0 = min(mn0, kx); mn1 = min(mn1, ky); mn2 = min(mn2, kz);
+                mx0 = max(mx0, kx); mx1 = max(mx1, ky); mx2 = max(mx2, kz);
+            }
+        }
+    }
+    const unsigned full = 0xffffffffu;
+    mn0 = __reduce_min_sync(full, mn0); mn1 = __reduce_min_sync(full, mn1); mn2 = __reduce_min_sync(full, mn2);
+    mx0 = __reduce_max_sync(full, mx0); mx1 = __reduce_max_sync(full, mx1); mx2 = __reduce_max_sync(full, mx2);
+    if ((threadIdx.x & 31) == 0 && mn0 != INT_MAX) {
+        int *bf = bounds + 6 * f;
+        atomicMin(bf + 0, mn0); atomicMin(bf + 1, mn1); atomicMin(bf + 2, mn2);
+        atomicMax(bf + 3, mx0); atomicMax(bf + 4, mx1); atomicMax(bf + 5, mx2);
+    }
+}
+
+template <int J>
+__global__ void __launch_bounds__(kThreads) k_fk_bin(HandDev h, const float *__restrict__ q, int S, FieldGeom g,
+                                                     uint32_t *table, unsigned int *status) {
+    extern __shared__ float s_surf[];
+    __shared__ int s_lb[CF_MAX_JOINTS + 1];
+    const int f = blockIdx.y;
+    stage_surface(h, f, s_surf, s_lb);
+    __syncthreads();
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    float R[J][9], t[J][3];
+    link_frames<J>(h, f, q, S, s, R, t);
+    const int lx = g.lo[f][0], ly = g.lo[f][1], lz = g.lo[f][2];
+    const unsigned dx = (unsigned)g.dims[f][0], dy = (unsigned)g.dims[f][1], dz = (unsigned)g.dims[f][2];
+    uint32_t *tab = table + g.off[f];
+#pragma unroll
+    for (int l = 0; l < J; ++l) {
+        for (int m = s_lb[l]; m < s_lb[l + 1]; ++m) {
+            const float *sp = s_surf + 8 * m;
+            const float x = xf_row(R[l][0], R[l][1], R[l][2], t[l][0], sp[0], sp[1], sp[2]);
+            const float y = xf_row(R[l][3], R[l][4], R[l][5], t[l][1], sp[0], sp[1], sp[2]);
+            const float z = xf_row(R[l][6], R[l][7], R[l][8], t[l][2], sp[0], sp[1], sp[2]);
+            const float nx = rot_row(R[l][0], R[l][1], R[l][2], sp[3], sp[4], sp[5]);
+            const float ny = rot_row(R[l][3], R[l][4], R[l][5], sp[3], sp[4], sp[5]);
+            const float nz = rot_row(R[l][6], R[l][7], R[l][8], sp[3], sp[4], sp[5]);
+            int bin = 0;
+            float best = -INFINITY;
+            for (int b = 0; b < g.B; ++b) {
+                const float sc = __fmaf_rn(g.dirs[b][2], nz, __fmaf_rn(g.dirs[b][1], ny, __fmul_rn(g.dirs[b][0], nx)));
+                if (sc > best) { best = sc; bin = b; }
+            }
+            const unsigned ux = (unsigned)(cell_floor(x, g.inv_h, g.clamp) - lx);
+            const unsigned uy = (unsigned)(cell_floor(y, g.inv_h, g.clamp) - ly);
+            const unsigned uz = (unsigned)(cell_floor(z, g.inv_h, g.clamp) - lz);
+            if (ux >= dx || uy >= dy || uz >= dz) {  // cannot happen: extents come from the same arithmetic
+                atomicOr(status, 0x80000000u);
+                continue;
+            }
+            uint32_t *word = tab + ((size_t)uz * dy + uy) * dx + ux;
+            const uint32_t bit = 1u << bin;
+            if (!(__ldcg(word) & bit)) atomicOr(word, bit);
+        }
+    }
+}
+
+}  // namespace
+
+#define CF_J_DISPATCH(J, CALL)            \
+    switch (J) {                          \
+        case 1: { constexpr int JJ = 1; CALL; } break; \
+        case 2: { constexpr int JJ = 2; CALL; } break; \
+        case 3: { constexpr int JJ = 3; CALL; } break; \
+        case 4: { constexpr int JJ = 4; CALL; } break; \
+        case 5: { constexpr int JJ = 5; CALL; } break; \
+        case 6: { constexpr int JJ = 6; CALL; } break; \
+        case 7: { constexpr int JJ = 7; CALL; } break; \
+        case 8: { constexpr int JJ = 8; CALL; } break; \
+        default: return cudaErrorInvalidValue;         \
+    }
+
+cudaError_t launch_fk_cell_bounds(const HandDev &h, const float *q, int S, float inv_h, float clamp, int *bounds,
+                                  cudaStream_t st) {
+    if (S <= 0) return cudaSuccess;
+    const dim3 grid((S + kThreads - 1) / kThreads, h.F);
+    const size_t smem = sizeof(float) * 8 * h.M;
+    CF_J_DISPATCH(h.J, (k_fk_cell_bounds<JJ><<<grid, kThreads, smem, st>>>(h, q, S, inv_h, clamp, bounds)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fk_bin(const HandDev &h, const float *q, int S, const FieldGeom &g, uint32_t *table,
+                          unsigned int *status, cudaStream_t st) {
+    if (S <= 0) return cudaSuccess;
+    const dim3 grid((S + kThreads - 1) / kThreads, h.F);
+    const size_t smem = sizeof(float) * 8 * h.M;
+    CF_J_DISPATCH(h.J, (k_fk_bin<JJ><<<grid, kThreads, smem, st>>>(h, q, S, g, table, status)));
+    return cudaGetLastError();
+}
+
+}  // namespace cf

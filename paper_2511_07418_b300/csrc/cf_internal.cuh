@@ -1,0 +1,104 @@
+// Internal declarations shared by the libcf translation units (device helpers,
+// device-side views of the field, kernel launchers).  Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cf.h"
+
+namespace cf {
+
+// ---------------------------------------------------------------------------
+// device views
+// ---------------------------------------------------------------------------
+
+// Hand data copied to the device by cf_build.  Surface points are stored per
+// finger sorted by link: surf[f][m] = (px, py, pz, nx, ny, nz, link, -), and
+// link_begin[f][l] .. link_begin[f][l + 1] is link l's range.
+struct HandDev {
+    int F, J, M;
+    const float *base;     // [F][12]
+    const float *axis;     // [F][J][3]
+    const float *offset;   // [F][J][3]
+    const float *surf;     // [F][M][8]
+    const int *link_begin; // [F][J + 1]
+};
+
+// Field geometry as the query kernel needs it (passed by value).
+struct FieldGeom {
+    int F, B;
+    float inv_h;
+    float clamp;             // |x| is clamped to this before the cell floor
+    int lo[CF_MAX_FINGERS][3];
+    int dims[CF_MAX_FINGERS][3];
+    long long off[CF_MAX_FINGERS];
+    float dirs[CF_MAX_BINS][3];
+};
+
+// ---------------------------------------------------------------------------
+// decision arithmetic (single-rounding FMAs, component order x, y, z)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float xf_row(float r0, float r1, float r2, float t, float x, float y, float z) {
+    return __fmaf_rn(r2, z, __fmaf_rn(r1, y, __fmaf_rn(r0, x, t)));
+}
+
+__device__ __forceinline__ float rot_row(float r0, float r1, float r2, float x, float y, float z) {
+    return __fmaf_rn(r2, z, __fmaf_rn(r1, y, __fmul_rn(r0, x)));
+}
+
+// floor of the exact product x * inv_h for |x * inv_h| < 2^22: the product is
+// added to 1.5 * 2^23 with one rounding toward -inf, which lands on the integer
+// grid of the [2^23, 2^24) binade; the low mantissa bits are the floor.
+__device__ __forceinline__ int cell_floor(float x, float inv_h, float clamp) {
+    x = fminf(fmaxf(x, -clamp), clamp);
+    float y = __fmaf_rd(x, inv_h, 12582912.0f);
+    return __float_as_int(y) - 0x4B400000;
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// ---------------------------------------------------------------------------
+// launchers (return cudaError_t of the launch)
+// ---------------------------------------------------------------------------
+cudaError_t launch_fk_cell_bounds(const HandDev &h, const float *q, int S, float inv_h, float clamp,
+                                  int *bounds, cudaStream_t st);
+cudaError_t launch_fk_bin(const HandDev &h, const float *q, int S, const FieldGeom &g, uint32_t *table,
+                          unsigned int *status, cudaStream_t st);
+cudaError_t launch_query(const FieldGeom &g, const uint32_t *table, const cf_points &obj, const float *poses,
+                         int P, uint32_t *masks, uint32_t *counts, cudaStream_t st);
+
+struct ScoreArgs {
+    const float *px, *py, *pz, *nx, *ny, *nz;
+    int N, W, F, P;
+    const uint32_t *masks, *counts;
+    int T, k, K;
+    float mu, eps, cx, cy, cz, inv_rho;
+    float cs[CF_MAX_EDGES], sn[CF_MAX_EDGES];
+    uint32_t seed_lo, seed_hi;
+    int tuples_given;
+    int32_t *tuples;
+    uint8_t *fingers;
+    float *margin;
+    uint8_t *accept;
+    unsigned int *work;  // scratch: pose work counter, zero at launch
+    unsigned int *status;          // device status word (CF_DEV_* bits)
+    unsigned long long *counters;  // [0] pivots, [1] LPs, [2] tuples
+};
+cudaError_t launch_score(const ScoreArgs &a, cudaStream_t st);
+
+}  // namespace cf

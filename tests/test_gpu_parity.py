@@ -1,0 +1,272 @@
+"""GPU-vs-oracle parity of the whole hot path, through the C ABI.
+
+Acceptance rule: field tables, domain masks, counts, sampled tuples and finger
+ids are bit-exact.  A mask entry may differ only if the oracle flags it as
+ambiguous (within 1e-5 m of a cell face or 1e-6 of a bin tie), and such entries
+must stay below 1e-4 of all entries.  Margins agree within
+1e-4 * max(t*, eps); accept decisions are equal except where
+|t*_oracle - eps| <= 1e-4, and those too stay below 1e-4 of all tuples.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def cf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2511_07418_b300 as cf
+    return cf
+
+
+def _bits(masks_u32, N):
+    P, F, W = masks_u32.shape
+    return np.unpackbits(np.ascontiguousarray(masks_u32).view(np.uint8), bitorder="little").reshape(P, F, W * 32)[:, :, :N]
+
+
+def _u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def _gpu_path(cf, w, poses=None):
+    q = torch.from_numpy(w.q).cuda()
+    field = cf.build(w.hand, w.inv_h, w.bins, q)
+    soa = torch.from_numpy(w.obj.soa()).cuda()
+    pz = torch.from_numpy(w.poses if poses is None else poses).cuda()
+    masks, counts = cf.query_domains(field, soa, pz)
+    prm = cf.score_params(w.T, w.k, w.mu, w.K, w.eps, w.obj.centroid, w.obj.rho, w.seed)
+    tup, fing, margin, accept = cf.score_tuples(soa, w.hand.F, masks, counts, prm)
+    torch.cuda.synchronize()
+    return dict(field=field, soa=soa, poses=pz, masks=masks, counts=counts, tuples=tup, fingers=fing,
+                margin=margin, accept=accept, prm=prm)
+
+
+def _table_codes(field, f):
+    inf = field.info()
+    tab = field.table()
+    lo = np.array(inf.lo[f], np.int64)
+    d = np.array(inf.dims[f], np.int64)
+    if d.prod() == 0:
+        return np.zeros((0, 4), np.int64)
+    off = int(inf.word_offset[f])
+    words = tab[off:off + int(d.prod())].reshape(int(d[2]), int(d[1]), int(d[0]))
+    iz, iy, ix = np.nonzero(words)
+    out = []
+    for b in range(int(inf.n_bins)):
+        sel = ((words[iz, iy, ix] >> np.uint32(b)) & np.uint32(1)).astype(bool)
+        out.append(np.stack([ix[sel] + lo[0], iy[sel] + lo[1], iz[sel] + lo[2], np.full(sel.sum(), b)], axis=1))
+    c = np.concatenate(out).astype(np.int64)
+    return c[np.lexsort((c[:, 3], c[:, 2], c[:, 1], c[:, 0]))]
+
+
+def _sorted_codes(c):
+    c = np.asarray(c, np.int64)
+    return c[np.lexsort((c[:, 3], c[:, 2], c[:, 1], c[:, 0]))]
+
+
+def check_field(field, ofd, F):
+    for f in range(F):
+        g = _table_codes(field, f)
+        o = _sorted_codes(ofd.codes(f))
+        assert g.shape == o.shape, (f, g.shape, o.shape)
+        assert np.array_equal(g, o), f
+
+
+def check_masks(g_masks, g_counts, o_masks, o_counts, amb, N):
+    gb, ob = _bits(g_masks, N), _bits(o_masks, N)
+    diff = gb != ob
+    assert not np.any(diff & (amb == 0)), f"{int(np.sum(diff & (amb == 0)))} non-ambiguous mask entries differ"
+    assert diff.sum() <= 1e-4 * diff.size
+    # bits past N are zero, counts are the row popcounts
+    W = g_masks.shape[2]
+    if N % 32:
+        assert np.all(g_masks[:, :, W - 1] >> np.uint32(N % 32) == 0)
+    assert np.array_equal(g_counts, gb.sum(axis=2).astype(np.uint32))
+    if diff.sum() == 0:
+        assert np.array_equal(g_counts, o_counts)
+
+
+def check_scores(g_margin, g_accept, o_margin, eps):
+    g = g_margin.astype(np.float64).ravel()
+    o = o_margin.ravel()
+    inv = ~np.isfinite(o)
+    assert np.array_equal(inv, ~np.isfinite(g))
+    tol = 1e-4 * np.maximum(o[~inv], eps)
+    err = np.abs(g[~inv] - np.maximum(o[~inv], 0.0))
+    assert np.all(err <= tol), f"max err/tol {np.max(err / tol):.3f}"
+    oa = (o <= eps)
+    ga = g_accept.ravel().astype(bool)
+    dec = ga != oa
+    amb = np.abs(o - eps) <= 1e-4
+    assert not np.any(dec & ~amb)
+    assert dec.sum() <= 1e-4 * dec.size
+
+
+def _full_check(cf, w, band=True):
+    r = _gpu_path(cf, w)
+    ofd = oracle.Field(w.hand, w.q, w.inv_h, w.bins, band=band)
+    check_field(r["field"], ofd, w.hand.F)
+    soa = w.obj.soa()
+    om, oc, amb = ofd.query(soa, w.poses, amb=True)
+    gm, gc = _u32(r["masks"]), _u32(r["counts"])
+    check_masks(gm, gc, om, oc, amb, w.obj.N)
+    # sampling, given the GPU's masks (tests the sampler alone)
+    ot, of = oracle.sample_tuples(gm, gc, w.obj.N, w.T, w.k, w.seed)
+    assert np.array_equal(r["tuples"].cpu().numpy(), ot)
+    assert np.array_equal(r["fingers"].cpu().numpy(), of)
+    omar, oacc, _ = oracle.score_tuples(soa, ot, w.mu, w.K, w.obj.centroid, w.obj.rho, w.eps)
+    check_scores(r["margin"].cpu().numpy(), r["accept"].cpu().numpy(), omar, w.eps)
+    return r, ofd
+
+
+def test_tiny_sphere_full_parity(cf):
+    w = synth.workload("tiny_sphere")
+    r, _ = _full_check(cf, w)
+    acc = r["accept"].cpu().numpy()
+    assert 0 < acc.sum() < acc.size
+    assert cf.device_status() == 0
+
+
+def test_hand16_superquadric_parity_pose_subset(cf):
+    w = synth.workload("hand16_superquadric", P=96)
+    r, _ = _full_check(cf, w)
+    assert r["accept"].cpu().numpy().mean() > 0.2
+    assert cf.device_status() == 0
+
+
+def test_hand20_tool_parity_pose_subset(cf):
+    w = synth.workload("hand20_tool", P=20)
+    _full_check(cf, w)
+    assert cf.device_status() == 0
+
+
+@pytest.mark.parametrize("name", ["hand16_superquadric", "hand20_tool"])
+def test_full_size_launch_sampled_outputs(cf, name):
+    """The benchmark's launch configuration at full size; the oracle checks a
+    random set of pose rows of the masks, the first 48 poses' tuples and a
+    random sample of the scored tuples."""
+    w = synth.workload(name)
+    r = _gpu_path(cf, w)
+    rng = np.random.default_rng(11)
+    ofd = oracle.Field(w.hand, w.q, w.inv_h, w.bins, band=True)
+    check_field(r["field"], ofd, w.hand.F)
+    soa = w.obj.soa()
+    idx = np.sort(rng.choice(w.P, 24, replace=False))
+    om, oc, amb = ofd.query(soa, w.poses[idx], amb=True)
+    gm_all, gc_all = _u32(r["masks"]), _u32(r["counts"])
+    check_masks(gm_all[idx], gc_all[idx], om, oc, amb, w.obj.N)
+    ot, of = oracle.sample_tuples(gm_all[:48], gc_all[:48], w.obj.N, w.T, w.k, w.seed)
+    assert np.array_equal(r["tuples"][:48].cpu().numpy(), ot)
+    assert np.array_equal(r["fingers"][:48].cpu().numpy(), of)
+    flat = r["tuples"].cpu().numpy().reshape(-1, w.k)
+    pick = rng.choice(flat.shape[0], 3000, replace=False)
+    omar, _, _ = oracle.score_tuples(soa, flat[pick], w.mu, w.K, w.obj.centroid, w.obj.rho, w.eps)
+    check_scores(r["margin"].cpu().numpy().ravel()[pick], r["accept"].cpu().numpy().ravel()[pick], omar, w.eps)
+    assert cf.device_status() == 0
+
+
+def test_ragged_sizes_and_degenerate_cases(cf):
+    base = synth.workload("tiny_sphere", P=5, S=512)
+    ofd = oracle.Field(base.hand, base.q, base.inv_h, base.bins, band=True)
+    q = torch.from_numpy(base.q).cuda()
+    field = cf.build(base.hand, base.inv_h, base.bins, q)
+    far = base.poses.copy()
+    far[2, [3, 7, 11]] += 10.0  # pose 2: object far from the hand -> empty domains
+    prm = cf.score_params(base.T, base.k, base.mu, base.K, base.eps, base.obj.centroid, base.obj.rho, 5)
+    for N in [1, 31, 33, 100, 1000]:
+        soa_h = np.ascontiguousarray(base.obj.soa()[:, :N])
+        soa = torch.from_numpy(soa_h).cuda()
+        masks, counts = cf.query_domains(field, soa, torch.from_numpy(far).cuda())
+        tup, fing, mar, acc = cf.score_tuples(soa, base.hand.F, masks, counts, prm)
+        torch.cuda.synchronize()
+        om, oc, amb = ofd.query(soa_h, far, amb=True)
+        check_masks(_u32(masks), _u32(counts), om, oc, amb, N)
+        assert int(counts[2].sum()) == 0
+        ot, of = oracle.sample_tuples(_u32(masks), _u32(counts), N, base.T, base.k, 5)
+        assert np.array_equal(tup.cpu().numpy(), ot)
+        assert np.all(ot[2] == -1) and np.all(fing[2].cpu().numpy() == 255)
+        om_, _, _ = oracle.score_tuples(soa_h, ot, base.mu, base.K, base.obj.centroid, base.obj.rho, base.eps)
+        check_scores(mar.cpu().numpy(), acc.cpu().numpy(), om_, base.eps)
+        assert np.all(np.isinf(mar[2].cpu().numpy())) and not acc[2].any()
+    # a field built from zero samples holds nothing
+    empty = cf.build(base.hand, base.inv_h, base.bins, torch.zeros((base.hand.F, base.hand.J, 0), device="cuda"))
+    assert empty.info().table_words == 0
+    m0, c0 = cf.query_domains(empty, torch.from_numpy(base.obj.soa()).cuda(), torch.from_numpy(base.poses).cuda())
+    torch.cuda.synchronize()
+    assert int(c0.abs().sum()) == 0 and int(m0.abs().sum()) == 0
+
+
+def test_scoring_given_tuples_and_invalid_ids(cf):
+    w = synth.workload("hand16_superquadric", P=8, S=4096)
+    rng = np.random.default_rng(2)
+    tup = rng.integers(0, w.obj.N, size=(w.P, w.T, w.k)).astype(np.int32)
+    tup[0, :3, 1] = -1
+    tup[1, 5, 2] = w.obj.N  # out of range -> invalid
+    soa_h = w.obj.soa()
+    soa = torch.from_numpy(soa_h).cuda()
+    prm = cf.score_params(w.T, w.k, w.mu, w.K, w.eps, w.obj.centroid, w.obj.rho, 0, tuples_given=True)
+    t_d = torch.from_numpy(tup).cuda()
+    _, _, mar, acc = cf.score_tuples(soa, w.hand.F, None, None, prm, tuples=t_d)
+    torch.cuda.synchronize()
+    assert np.array_equal(t_d.cpu().numpy(), tup)  # tuples untouched
+    om, _, _ = oracle.score_tuples(soa_h, tup, w.mu, w.K, w.obj.centroid, w.obj.rho, w.eps)
+    check_scores(mar.cpu().numpy(), acc.cpu().numpy(), om, w.eps)
+    assert np.all(np.isinf(mar.cpu().numpy()[0, :3]))
+
+
+def test_closure_closed_forms_on_gpu(cf):
+    """Antipodal pair on a sphere -> margin 0; a single axis-aligned contact
+    (k = 1) -> margin 1 (Eq. GSWO with alpha_j = 1)."""
+    r = 0.04
+    u = np.array([0.3, -0.5, 0.8])
+    u /= np.linalg.norm(u)
+    pts = np.array([r * u, -r * u, [0.0, 0.0, -r]])
+    nrm = np.array([u, -u, [0.0, 0.0, -1.0]])
+    soa = torch.from_numpy(np.concatenate([pts.T, nrm.T]).astype(np.float32)).cuda()
+    prm2 = cf.score_params(1, 2, 0.5, 8, 0.01, [0, 0, 0], r, 0, tuples_given=True)
+    _, _, m2, a2 = cf.score_tuples(soa, 1, None, None, prm2, tuples=torch.tensor([[[0, 1]]], dtype=torch.int32).cuda())
+    prm1 = cf.score_params(1, 1, 0.5, 8, 0.01, [0, 0, 0], r, 0, tuples_given=True)
+    _, _, m1, _ = cf.score_tuples(soa, 1, None, None, prm1, tuples=torch.tensor([[[2]]], dtype=torch.int32).cuda())
+    torch.cuda.synchronize()
+    assert float(m2) <= 1e-6 and int(a2) == 1
+    assert abs(float(m1) - 1.0) <= 1e-5
+
+
+def test_field_save_load_and_plan_host_path(cf, tmp_path):
+    w = synth.workload("tiny_sphere", P=64)
+    r = _gpu_path(cf, w)
+    path = str(tmp_path / "f.cff")
+    r["field"].save(path)
+    f2 = cf.Field.load(path)
+    assert np.array_equal(f2.table(), r["field"].table())
+    m2, c2 = cf.query_domains(f2, r["soa"], r["poses"])
+    torch.cuda.synchronize()
+    assert np.array_equal(_u32(m2), _u32(r["masks"]))
+    plan = cf.Plan(w.hand.F, w.obj.N, w.P, r["prm"])
+    ht = np.zeros((w.P, w.T, w.k), np.int32)
+    hm = np.zeros((w.P, w.T), np.float32)
+    ha = np.zeros((w.P, w.T), np.uint8)
+    nacc = plan.run_host(r["field"], w.obj.soa(), w.poses, ht, hm, ha)
+    assert np.array_equal(ht, r["tuples"].cpu().numpy())
+    assert np.array_equal(hm, r["margin"].cpu().numpy())
+    assert np.array_equal(ha, r["accept"].cpu().numpy())
+    assert nacc == int(ha.sum())
+
+
+def test_repeatable_bits(cf):
+    w = synth.workload("hand16_superquadric", P=32, S=8192)
+    a = _gpu_path(cf, w)
+    b = _gpu_path(cf, w)
+    assert np.array_equal(a["field"].table(), b["field"].table())
+    for key in ["masks", "counts", "tuples", "fingers", "margin", "accept"]:
+        assert torch.equal(a[key], b[key]), key
+    cnt = cf.device_counters()
+    assert cnt["lps"] > 0 and cnt["lp_pivots"] >= 2 * cnt["lps"]
+    assert cf.device_status() == 0
