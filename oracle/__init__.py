@@ -1,8 +1,10 @@
 """CPU oracle for the Contact-Field grasp path -- TEST INFRASTRUCTURE ONLY.
 
-Plain, slow, obviously-correct reference implementation (C in ``cf_oracle.c``,
-FP64 kinematics and LP, OpenMP over independent poses / tuples) that the GPU
-library is checked against.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+Plain, slow, obviously-correct reference implementation that the GPU library is
+checked against: C in ``cf_oracle.c`` for kinematics, field codes, masks and
+sampling (FP64 geometry, OpenMP over independent poses), numpy for the wrench
+construction, and a library LP solver (scipy's HiGHS) for the closure LPs, which
+are written out exactly as defined.  Only ``tests/``, ``__graft_entry__.smoke()`` and
 the CPU-baseline leg of ``bench.py`` may import this package.  It shares no code
 with the GPU library and never imports it.
 
@@ -15,12 +17,13 @@ Functions (paper passages they follow are cited in ``cf_oracle.c``):
   Field.query         contact domains as bitmasks (Sec. 3.2, Sec. 3.3 query)
   query_masks_brute   literal existential check, tiny inputs only
   sample_tuples       random k-tuples from k distinct finger domains (Sec. 4.3)
-  closure_lp          linearised GSWO margin of one tuple (Eq. GSWO)
-  score_tuples        margins / accept flags of many tuples
+  closure_lp          linearised GSWO margin of one tuple (Eq. GSWO): k LPs
+  score_tuples        margins / accept flags of many tuples (process pool)
 
 Parity status: every function is pinned by tests under ``tests/`` against
-closed forms, an independent library routine (scipy's HiGHS LP solver, triton's
-Philox in CPU-interpreter mode) or a brute-force definition, except the items
+closed forms, an independent library routine (triton's Philox in
+CPU-interpreter mode), brute force (vertex enumeration of small LPs, literal
+existential mask check) or invariants, except the items
 listed as "parity unpinned" in the design notes (the value of the acceptance
 threshold eps and the synthetic hand surface-point set, which the paper does not
 fix).
@@ -28,6 +31,7 @@ fix).
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 from ctypes import POINTER, c_double, c_float, c_int, c_int32, c_int64, c_uint8, c_uint32, c_uint64, c_void_p
@@ -80,10 +84,6 @@ def lib():
         L.orc_query_masks_brute.argtypes = [c_int, c_int, c_int, fp, fp, fp, fp, fp, i32p, fp, c_int, c_float,
                                             c_int, fp, c_int, fp, c_int, fp, u32p]
         L.orc_sample_tuples.argtypes = [c_int, c_int, c_int, u32p, u32p, c_int, c_int, c_uint64, i32p, u8p]
-        L.orc_closure_lp.restype = c_double
-        L.orc_closure_lp.argtypes = [c_int, dp, dp, c_double, c_int, dp, c_double, dp, POINTER(c_int)]
-        L.orc_score_tuples.argtypes = [c_int, fp, c_int, c_int, i32p, c_float, c_int, fp, c_float, c_float,
-                                       dp, u8p, i32p]
         L.orc_num_threads.restype = c_int
         _lib = L
     return _lib
@@ -243,32 +243,126 @@ def sample_tuples(masks: np.ndarray, counts: np.ndarray, N: int, T: int, k: int,
     return tuples, fingers
 
 
+# ---------------------------------------------------------------------------
+# closure margin (Eq. GSWO, Sec. 2.2, linearised)
+# ---------------------------------------------------------------------------
+
+def _onb_duff(nu):
+    """Tangent basis (x, y) of unit vector nu: Duff et al., "Building an
+    Orthonormal Basis, Revisited" (JCGT 2017)."""
+    s = math.copysign(1.0, nu[2])
+    a = -1.0 / (s + nu[2])
+    b = nu[0] * nu[1] * a
+    x = np.array([1.0 + s * nu[0] * nu[0] * a, s * b, -s * nu[0]])
+    y = np.array([b, s + nu[1] * nu[1] * a, -nu[1]])
+    return x, y
+
+
+def wrench_matrix(p, n, mu: float, K: int, c, rho: float) -> np.ndarray:
+    """6 x kK matrix of pyramid-edge wrenches, column i*K + m:
+    w_im = [e_im ; (p_i - c) x e_im / rho], e_im = nu_i + mu (cos th_m x_i +
+    sin th_m y_i), th_m = 2 pi m / K, nu_i = -n_i (force into the object)."""
+    p = np.asarray(p, np.float64).reshape(-1, 3)
+    n = np.asarray(n, np.float64).reshape(-1, 3)
+    c = np.asarray(c, np.float64)
+    cols = []
+    for i in range(p.shape[0]):
+        nu = -n[i]
+        x, y = _onb_duff(nu)
+        r = p[i] - c
+        for m in range(K):
+            th = 2.0 * math.pi * m / K
+            e = nu + mu * (math.cos(th) * x + math.sin(th) * y)
+            cols.append(np.concatenate([e, np.cross(r, e) / rho]))
+    return np.array(cols).T
+
+
+def lp_subproblem(W: np.ndarray, K: int, j: int):
+    """LP_j: minimise t over (c >= 0, t) subject to -t <= (W c)_r <= t for the
+    six wrench rows and sum_m c_jm = 1.  Returns (t*, solver iterations)."""
+    from scipy.optimize import linprog
+    nc = W.shape[1]
+    cost = np.zeros(nc + 1)
+    cost[-1] = 1.0
+    A = np.zeros((12, nc + 1))
+    A[:6, :nc] = W
+    A[6:, :nc] = -W
+    A[:, nc] = -1.0
+    Aeq = np.zeros((1, nc + 1))
+    Aeq[0, j * K:(j + 1) * K] = 1.0
+    res = linprog(cost, A_ub=A, b_ub=np.zeros(12), A_eq=Aeq, b_eq=[1.0], bounds=[(0, None)] * (nc + 1),
+                  method="highs")
+    if res.status != 0:
+        return float("nan"), -1
+    return float(res.fun), int(res.nit)
+
+
 def closure_lp(p, n, mu: float, K: int, c, rho: float):
-    """Margin t* of one tuple; returns (t*, t_per_j [k], pivots [k])."""
-    p = _c(p, np.float64).reshape(-1, 3)
-    n = _c(n, np.float64).reshape(-1, 3)
-    k = int(p.shape[0])
-    cc = _c(c, np.float64)
+    """Margin t* = min_j LP_j of one tuple; returns (t*, t_per_j [k], iterations [k]).
+    A failed subproblem makes t* NaN."""
+    W = wrench_matrix(p, n, mu, K, c, rho)
+    k = W.shape[1] // K
     tj = np.zeros(k)
-    pv = np.zeros(k, np.int32)
-    t = lib().orc_closure_lp(k, _p(p, c_double), _p(n, c_double), float(mu), int(K), _p(cc, c_double),
-                             float(rho), _p(tj, c_double), pv.ctypes.data_as(POINTER(c_int)))
-    return float(t), tj, pv
+    it = np.zeros(k, np.int32)
+    for j in range(k):
+        tj[j], it[j] = lp_subproblem(W, K, j)
+    t = float("nan") if np.isnan(tj).any() else float(tj.min())
+    return t, tj, it
 
 
-def score_tuples(soa: np.ndarray, tuples: np.ndarray, mu: float, K: int, c, rho: float, eps: float):
-    """margins (float64, +inf for invalid), accept (uint8), pivots (int32) per tuple."""
+def _score_chunk(args):
+    soa, tuples, mu, K, c, rho, eps = args
+    N = soa.shape[1]
+    out_m = np.empty(len(tuples))
+    out_it = np.zeros(len(tuples), np.int32)
+    for u, ids in enumerate(tuples):
+        if np.any(ids < 0) or np.any(ids >= N):
+            out_m[u] = np.inf
+            continue
+        p = soa[0:3, ids].T.astype(np.float64)
+        nn = soa[3:6, ids].T.astype(np.float64)
+        t, _, it = closure_lp(p, nn, mu, K, c, rho)
+        out_m[u] = t
+        out_it[u] = int(it.sum())
+    return out_m, out_it
+
+
+_pool = None
+
+
+def _get_pool():
+    """Process pool started with 'spawn' (safe after CUDA initialisation)."""
+    global _pool
+    if _pool is None:
+        import concurrent.futures
+        import multiprocessing as mp
+        _pool = concurrent.futures.ProcessPoolExecutor(max_workers=max(1, os.cpu_count() or 1),
+                                                       mp_context=mp.get_context("spawn"))
+    return _pool
+
+
+def score_tuples(soa: np.ndarray, tuples: np.ndarray, mu: float, K: int, c, rho: float, eps: float,
+                 workers: bool = True):
+    """margins (float64, +inf for invalid tuples), accept (uint8: margin <= eps),
+    solver iterations (int32) per tuple.  mu, c, rho, eps are taken at the FP32
+    values the GPU receives."""
     soa = _c(soa, np.float32)
-    N = int(soa.shape[1])
     tuples = _c(tuples, np.int32)
     k = int(tuples.shape[-1])
-    PT = int(tuples.size // k)
-    cc = _c(c, np.float32)
-    margin = np.zeros(PT)
-    accept = np.zeros(PT, np.uint8)
-    piv = np.zeros(PT, np.int32)
-    lib().orc_score_tuples(N, _p(soa, c_float), PT, k, _p(tuples, c_int32), c_float(np.float32(mu)), int(K),
-                           _p(cc, c_float), c_float(np.float32(rho)), c_float(np.float32(eps)),
-                           _p(margin, c_double), _p(accept, c_uint8), _p(piv, c_int32))
+    flat = tuples.reshape(-1, k)
+    mu64 = float(np.float32(mu))
+    c64 = np.asarray(c, np.float32).astype(np.float64)
+    rho64 = float(np.float32(rho))
+    eps32 = float(np.float32(eps))
+    n = flat.shape[0]
+    if workers and n > 64:
+        chunks = np.array_split(np.arange(n), max(1, min(n // 64, 4 * (os.cpu_count() or 1))))
+        futs = [_get_pool().submit(_score_chunk, (soa, flat[ch], mu64, K, c64, rho64, eps32)) for ch in chunks]
+        res = [f.result() for f in futs]
+        margin = np.concatenate([r[0] for r in res])
+        iters = np.concatenate([r[1] for r in res])
+    else:
+        margin, iters = _score_chunk((soa, flat, mu64, K, c64, rho64, eps32))
+    accept = (margin <= eps32).astype(np.uint8)
     shp = tuples.shape[:-1]
-    return margin.reshape(shp), accept.reshape(shp), piv.reshape(shp)
+    return margin.reshape(shp), accept.reshape(shp), iters.reshape(shp)

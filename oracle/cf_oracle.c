@@ -22,13 +22,10 @@
  *   - random k-tuples of contacts from k distinct non-empty finger domains
  *     (Sec. 4.3 "Contact Domain Generation": randomly select k domains;
  *     Alg. 2 step "Random(D_i)");
- *   - the closure margin: the GSWO subproblems (Eq. GSWO, Sec. 2.2) with the
- *     friction cone replaced by an inscribed K-edge pyramid and the squared norm
- *     replaced by a torque-weighted max-norm, so that each of the k convex
- *     subproblems is a linear program, solved by a textbook two-phase dense
- *     simplex with Bland's rule in FP64.
+ *   (the closure margin's linear programs are written out and solved in
+ *   oracle/__init__.py with a library LP solver).
  *
- * Precision: kinematics, geometry and the LP are FP64.  The integer codes that
+ * Precision: kinematics and geometry are FP64.  The integer codes that
  * the GPU decides in FP32 (voxel cell, normal bin) are decided here in the same
  * precision, from FP32-rounded link transforms with single-rounding fused
  * multiply-adds in the natural component order; an FP64 evaluation of the same
@@ -549,253 +546,6 @@ void orc_sample_tuples(int P, int F, int N, const uint32_t *masks, const uint32_
                 tp[d] = select_set_bit(masks + ((size_t)i * F + f) * W, W, r);
                 fp[d] = (uint8_t)f;
             }
-        }
-    }
-}
-
-/* ------------------------------------------------------------------------ */
-/* Closure margin (Eq. GSWO, Sec. 2.2, linearised).                           */
-/* Contact i: point p_i, outward normal n_i (object frame).  Force direction  */
-/* nu_i = -n_i (into the object); tangent basis (x_i, y_i) of nu_i by Duff et */
-/* al., "Building an Orthonormal Basis, Revisited" (JCGT 2017).  Cone edges  */
-/* e_im = nu_i + mu (cos th_m x_i + sin th_m y_i), th_m = 2 pi m / K.          */
-/* Wrench w_im = [e_im ; (p_i - c) x e_im / rho].                              */
-/* LP_j: minimise t s.t. -t <= (sum c_im w_im)_r <= t (r = 1..6),             */
-/*       sum_m c_jm = 1, c >= 0.      margin t* = min_j LP_j.                   */
-/* ------------------------------------------------------------------------ */
-static void onb_duff(const double n[3], double b1[3], double b2[3]) {
-    double sign = copysign(1.0, n[2]);
-    double a = -1.0 / (sign + n[2]);
-    double b = n[0] * n[1] * a;
-    b1[0] = 1.0 + sign * n[0] * n[0] * a; b1[1] = sign * b; b1[2] = -sign * n[0];
-    b2[0] = b; b2[1] = sign + n[1] * n[1] * a; b2[2] = -n[1];
-}
-
-#define ORC_LP_MAXV 160
-#define ORC_LP_ROWS 13
-#define ORC_LP_DTOL 1e-11  /* reduced-cost tolerance */
-#define ORC_LP_PTOL 1e-7   /* smallest admissible pivot entry (entries of A are O(1); smaller
-                              * values of B^-1 A_e are rounding noise of a structural zero) */
-
-/* Solve M z = rhs (n x n) by Gaussian elimination with partial pivoting; M and
- * rhs are overwritten (rhs becomes z).  Returns 0 if M is numerically singular. */
-static int dense_solve(int n, double M[ORC_LP_ROWS][ORC_LP_ROWS], double rhs[ORC_LP_ROWS]) {
-    for (int c = 0; c < n; ++c) {
-        int pr = c;
-        for (int r = c + 1; r < n; ++r)
-            if (fabs(M[r][c]) > fabs(M[pr][c])) pr = r;
-        if (!(fabs(M[pr][c]) > 1e-13)) return 0; /* singular to working precision */
-        if (pr != c) {
-            for (int k = 0; k < n; ++k) { double tmp = M[c][k]; M[c][k] = M[pr][k]; M[pr][k] = tmp; }
-            double tmp = rhs[c]; rhs[c] = rhs[pr]; rhs[pr] = tmp;
-        }
-        for (int r = c + 1; r < n; ++r) {
-            double f = M[r][c] / M[c][c];
-            if (f == 0.0) continue;
-            for (int k = c; k < n; ++k) M[r][k] -= f * M[c][k];
-            rhs[r] -= f * rhs[c];
-        }
-    }
-    for (int r = n - 1; r >= 0; --r) {
-        double s = rhs[r];
-        for (int k = r + 1; k < n; ++k) s -= M[r][k] * rhs[k];
-        rhs[r] = s / M[r][r];
-    }
-    return 1;
-}
-
-typedef struct {
-    int nv;
-    double A[ORC_LP_ROWS][ORC_LP_MAXV];
-    double b[ORC_LP_ROWS];
-} orc_lp;
-
-/* x_B = B^-1 b, y = B^-T c_B, u = B^-1 A_e, each from a fresh elimination on
- * the original columns (no update formulae, so no drift). */
-static int basic_solution(const orc_lp *lp, const int basis[ORC_LP_ROWS], double x[ORC_LP_ROWS]) {
-    double M[ORC_LP_ROWS][ORC_LP_ROWS];
-    for (int r = 0; r < ORC_LP_ROWS; ++r) {
-        for (int c = 0; c < ORC_LP_ROWS; ++c) M[r][c] = lp->A[r][basis[c]];
-        x[r] = lp->b[r];
-    }
-    return dense_solve(ORC_LP_ROWS, M, x);
-}
-
-static int basis_duals(const orc_lp *lp, const int basis[ORC_LP_ROWS], const double *cost, double y[ORC_LP_ROWS]) {
-    double M[ORC_LP_ROWS][ORC_LP_ROWS];
-    for (int r = 0; r < ORC_LP_ROWS; ++r) {
-        for (int c = 0; c < ORC_LP_ROWS; ++c) M[r][c] = lp->A[c][basis[r]];
-        y[r] = cost[basis[r]];
-    }
-    return dense_solve(ORC_LP_ROWS, M, y);
-}
-
-static int basis_direction(const orc_lp *lp, const int basis[ORC_LP_ROWS], int e, double u[ORC_LP_ROWS]) {
-    double M[ORC_LP_ROWS][ORC_LP_ROWS];
-    for (int r = 0; r < ORC_LP_ROWS; ++r) {
-        for (int c = 0; c < ORC_LP_ROWS; ++c) M[r][c] = lp->A[r][basis[c]];
-        u[r] = lp->A[r][e];
-    }
-    return dense_solve(ORC_LP_ROWS, M, u);
-}
-
-/* Revised primal simplex with Bland's rule (lowest-index entering variable with
- * negative reduced cost; among tied minimum ratios, lowest-index leaving
- * variable).  Returns the number of basis changes, or -1 (unbounded /
- * singular / no termination). */
-static int simplex_bland(const orc_lp *lp, int basis[ORC_LP_ROWS], const double *cost, const int *allowed,
-                         double *obj) {
-    const int nv = lp->nv;
-    int piv = 0;
-    double x[ORC_LP_ROWS], y[ORC_LP_ROWS], u[ORC_LP_ROWS];
-    for (;;) {
-        if (!basic_solution(lp, basis, x) || !basis_duals(lp, basis, cost, y)) return -1;
-        int isbasic[ORC_LP_MAXV] = {0};
-        for (int r = 0; r < ORC_LP_ROWS; ++r) isbasic[basis[r]] = 1;
-        int e = -1;
-        for (int v = 0; v < nv && e < 0; ++v) {
-            if (!allowed[v] || isbasic[v]) continue;
-            double d = cost[v];
-            for (int r = 0; r < ORC_LP_ROWS; ++r) d -= y[r] * lp->A[r][v];
-            if (d < -ORC_LP_DTOL) e = v;
-        }
-        if (e < 0) {
-            double z = 0.0;
-            for (int r = 0; r < ORC_LP_ROWS; ++r) z += cost[basis[r]] * x[r];
-            *obj = z;
-            return piv;
-        }
-        if (!basis_direction(lp, basis, e, u)) return -1;
-        int l = -1;
-        double best = INFINITY;
-        for (int r = 0; r < ORC_LP_ROWS; ++r) {
-            if (u[r] <= ORC_LP_PTOL) continue;
-            double ratio = (x[r] > 0.0 ? x[r] : 0.0) / u[r];
-            if (l < 0 || ratio < best - 1e-13 || (ratio <= best + 1e-13 && basis[r] < basis[l])) {
-                if (l < 0 || ratio < best) best = ratio;
-                l = r;
-            }
-        }
-        if (l < 0) return -1;
-        basis[l] = e;
-        if (++piv > 10000) return -1;
-    }
-}
-
-/* one tuple: k contacts with p[k][3], n[k][3]; returns t* and fills
- * t_per_j[k] and pivots[k] (phase 1 + phase 2 basis changes of LP_j). */
-double orc_closure_lp(int k, const double *p, const double *n, double mu, int K, const double *c, double rho,
-                      double *t_per_j, int *pivots) {
-    const int nc = k * K;          /* c_im, i-major */
-    const int it = nc;             /* t */
-    const int is = nc + 1;         /* slacks s_0..s_11 */
-    const int ia = nc + 13;        /* artificial of the equality row */
-    const int nv = nc + 14;
-    double w[ORC_LP_MAXV][6];
-    for (int i = 0; i < k; ++i) {
-        double nu[3] = {-n[3 * i], -n[3 * i + 1], -n[3 * i + 2]};
-        double x[3], y[3];
-        onb_duff(nu, x, y);
-        double r[3] = {p[3 * i] - c[0], p[3 * i + 1] - c[1], p[3 * i + 2] - c[2]};
-        for (int m = 0; m < K; ++m) {
-            double th = 2.0 * M_PI * (double)m / (double)K;
-            double cs = cos(th), sn = sin(th);
-            double e[3];
-            for (int a = 0; a < 3; ++a) e[a] = nu[a] + mu * (cs * x[a] + sn * y[a]);
-            double *wv = w[i * K + m];
-            wv[0] = e[0]; wv[1] = e[1]; wv[2] = e[2];
-            wv[3] = (r[1] * e[2] - r[2] * e[1]) / rho;
-            wv[4] = (r[2] * e[0] - r[0] * e[2]) / rho;
-            wv[5] = (r[0] * e[1] - r[1] * e[0]) / rho;
-        }
-    }
-    double best = INFINITY;
-    for (int j = 0; j < k; ++j) {
-        orc_lp lp;
-        memset(&lp, 0, sizeof lp);
-        lp.nv = nv;
-        int basis[ORC_LP_ROWS];
-        /* rows 0..5:  sum c w_r - t + s_r = 0;  rows 6..11: -sum c w_r - t + s_{6+r} = 0;
-         * row 12: sum_m c_jm + a = 1 */
-        for (int r = 0; r < 6; ++r) {
-            for (int v = 0; v < nc; ++v) { lp.A[r][v] = w[v][r]; lp.A[6 + r][v] = -w[v][r]; }
-            lp.A[r][it] = -1.0; lp.A[6 + r][it] = -1.0;
-            lp.A[r][is + r] = 1.0; lp.A[6 + r][is + 6 + r] = 1.0;
-            basis[r] = is + r; basis[6 + r] = is + 6 + r;
-        }
-        for (int m = 0; m < K; ++m) lp.A[12][j * K + m] = 1.0;
-        lp.A[12][ia] = 1.0;
-        lp.b[12] = 1.0;
-        basis[12] = ia;
-        double cost1[ORC_LP_MAXV] = {0}, cost2[ORC_LP_MAXV] = {0};
-        int allowed[ORC_LP_MAXV];
-        for (int v = 0; v < nv; ++v) allowed[v] = 1;
-        cost1[ia] = 1.0;
-        double z1 = 0.0, z2 = 0.0;
-        /* phase 1: minimise the artificial */
-        int p1 = simplex_bland(&lp, basis, cost1, allowed, &z1);
-        /* a degenerate artificial left in the basis is exchanged for any column
-         * with a non-zero entry in its row of B^-1 A */
-        for (int r = 0; r < ORC_LP_ROWS && p1 >= 0; ++r) {
-            if (basis[r] != ia) continue;
-            int isbasic[ORC_LP_MAXV] = {0};
-            for (int q = 0; q < ORC_LP_ROWS; ++q) isbasic[basis[q]] = 1;
-            for (int v = 0; v < nv; ++v) {
-                double u[ORC_LP_ROWS];
-                if (v == ia || isbasic[v] || !basis_direction(&lp, basis, v, u)) continue;
-                if (fabs(u[r]) > ORC_LP_PTOL) { basis[r] = v; ++p1; break; }
-            }
-        }
-        allowed[ia] = 0;
-        cost2[it] = 1.0;
-        /* phase 2: minimise t */
-        int p2 = (p1 < 0 || z1 > 1e-9) ? -1 : simplex_bland(&lp, basis, cost2, allowed, &z2);
-        double tj = (p1 < 0 || p2 < 0) ? NAN : z2;
-        if (t_per_j) t_per_j[j] = tj;
-        if (pivots) pivots[j] = (p1 < 0 || p2 < 0) ? -1 : p1 + p2;
-        /* a failed subproblem poisons the margin: never silently dropped */
-        if (isnan(tj) || isnan(best)) best = NAN;
-        else if (tj < best) best = tj;
-    }
-    return best;
-}
-
-/* Score sampled tuples: margin[P*T] (t*, +inf for invalid tuples),
- * accept[P*T] = (t* <= eps), pivots[P*T] = total simplex pivots (or NULL).
- * Points/normals come from soa [6][N] in the object frame; c, rho, mu, K as
- * above. */
-void orc_score_tuples(int N, const float *soa, int PT, int k, const int32_t *tuples, float mu, int K,
-                      const float *c, float rho, float eps, double *margin, uint8_t *accept, int32_t *pivots) {
-    double cc[3] = {c[0], c[1], c[2]};
-#pragma omp parallel for schedule(dynamic, 16)
-    for (int u = 0; u < PT; ++u) {
-        const int32_t *tp = tuples + (size_t)u * k;
-        int valid = 1;
-        for (int d = 0; d < k; ++d)
-            if (tp[d] < 0 || tp[d] >= N) valid = 0;
-        if (!valid) {
-            margin[u] = INFINITY;
-            accept[u] = 0;
-            if (pivots) pivots[u] = 0;
-            continue;
-        }
-        double p[3 * 16], n[3 * 16];
-        for (int d = 0; d < k; ++d) {
-            int x = tp[d];
-            for (int a = 0; a < 3; ++a) {
-                p[3 * d + a] = soa[(size_t)a * N + x];
-                n[3 * d + a] = soa[(size_t)(3 + a) * N + x];
-            }
-        }
-        double tj[16];
-        int pv[16];
-        double t = orc_closure_lp(k, p, n, (double)mu, K, cc, (double)rho, tj, pv);
-        margin[u] = t;
-        accept[u] = (uint8_t)(t <= (double)eps);
-        if (pivots) {
-            int s = 0;
-            for (int d = 0; d < k; ++d) s += pv[d];
-            pivots[u] = s;
         }
     }
 }

@@ -229,7 +229,7 @@ def test_closure_closed_forms_on_gpu(cf):
     u /= np.linalg.norm(u)
     pts = np.array([r * u, -r * u, [0.0, 0.0, -r]])
     nrm = np.array([u, -u, [0.0, 0.0, -1.0]])
-    soa = torch.from_numpy(np.concatenate([pts.T, nrm.T]).astype(np.float32)).cuda()
+    soa = torch.from_numpy(np.ascontiguousarray(np.concatenate([pts.T, nrm.T]), dtype=np.float32)).cuda()
     prm2 = cf.score_params(1, 2, 0.5, 8, 0.01, [0, 0, 0], r, 0, tuples_given=True)
     _, _, m2, a2 = cf.score_tuples(soa, 1, None, None, prm2, tuples=torch.tensor([[[0, 1]]], dtype=torch.int32).cuda())
     prm1 = cf.score_params(1, 1, 0.5, 8, 0.01, [0, 0, 0], r, 0, tuples_given=True)

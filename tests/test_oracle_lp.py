@@ -1,17 +1,18 @@
 """Pins for the oracle's closure margin (Eq. GSWO, Sec. 2.2, linearised:
 K-edge inscribed friction pyramid, torque-weighted max-norm, one LP per
-j with alpha_j = 1, margin = min over j)."""
+j with alpha_j = 1, margin = min over j).  The LP solver is a library routine;
+these tests pin the LP it is given: brute-force vertex enumeration, the
+wrench columns against their definition, closed forms and invariances."""
 import math
 
 import numpy as np
 import pytest
-from scipy.optimize import linprog
 
 import oracle
 
 
 def _onb(n):
-    # Duff et al. 2017 branchless basis, restated for the check's wrench build
+    # Duff et al. 2017 branchless basis (used by the two-contact construction below)
     s = math.copysign(1.0, n[2])
     a = -1.0 / (s + n[2])
     b = n[0] * n[1] * a
@@ -19,56 +20,81 @@ def _onb(n):
             np.array([b, s + n[1] * n[1] * a, -n[1]]))
 
 
-def _highs_margin(p, n, mu, K, c, rho):
-    """Same LPs solved by scipy's HiGHS (an independent LP library)."""
-    k = len(p)
-    W = []
-    for i in range(k):
-        nu = -np.asarray(n[i], float)
-        x, y = _onb(nu)
-        r = np.asarray(p[i], float) - c
-        for m in range(K):
-            th = 2 * math.pi * m / K
-            e = nu + mu * (math.cos(th) * x + math.sin(th) * y)
-            W.append(np.concatenate([e, np.cross(r, e) / rho]))
-    W = np.array(W).T  # 6 x kK
-    out = []
-    nv = k * K + 1
-    for j in range(k):
-        cost = np.zeros(nv)
-        cost[-1] = 1.0
-        A = np.zeros((12, nv))
-        A[:6, :-1] = W
-        A[6:, :-1] = -W
-        A[:, -1] = -1.0
-        Aeq = np.zeros((1, nv))
-        Aeq[0, j * K:(j + 1) * K] = 1.0
-        res = linprog(cost, A_ub=A, b_ub=np.zeros(12), A_eq=Aeq, b_eq=[1.0],
-                      bounds=[(0, None)] * nv, method="highs")
-        assert res.status == 0
-        out.append(res.fun)
-    return np.array(out)
+def _vertex_enumeration(W, K, j):
+    """LP_j by brute force: every vertex of {(c, t): -t <= W c <= t, c >= 0,
+    t >= 0, sum_m c_jm = 1} is the solution of the equality plus nv - 1 active
+    inequalities; the optimum of min t is the smallest t over feasible vertices."""
+    import itertools
+    nc = W.shape[1]
+    nv = nc + 1
+    G = np.zeros((12 + nv, nv))          # G z <= 0
+    G[:6, :nc] = W
+    G[6:12, :nc] = -W
+    G[:12, nc] = -1.0
+    G[12:, :] = -np.eye(nv)
+    a = np.zeros(nv)
+    a[j * K:(j + 1) * K] = 1.0
+    combos = np.array(list(itertools.combinations(range(G.shape[0]), nv - 1)))
+    M = np.concatenate([np.broadcast_to(a, (len(combos), 1, nv)), G[combos]], axis=1)
+    rhs = np.zeros((len(combos), nv))
+    rhs[:, 0] = 1.0
+    ok = np.abs(np.linalg.det(M)) > 1e-12
+    z = np.linalg.solve(M[ok], rhs[ok][..., None])[..., 0]
+    feas = np.all(z @ G.T <= 1e-9, axis=1)
+    return float(z[feas, nc].min())
 
 
-def _rand_contacts(rng, k):
+def _rand_contacts(rng, k, axis_aligned=False):
     p = rng.normal(size=(k, 3)) * 0.05
-    n = rng.normal(size=(k, 3))
-    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    if axis_aligned:
+        n = np.zeros((k, 3))
+        for i in range(k):
+            n[i, rng.integers(3)] = rng.choice([-1.0, 1.0])
+            if rng.random() < 0.5:  # a face normal with one exact zero component
+                n[i] = n[i] + np.roll(n[i], 1) * rng.uniform(0.2, 1.0)
+        n /= np.linalg.norm(n, axis=1, keepdims=True)
+    else:
+        n = rng.normal(size=(k, 3))
+        n /= np.linalg.norm(n, axis=1, keepdims=True)
     return p, n
 
 
-@pytest.mark.parametrize("k,K,mu", [(2, 4, 0.5), (3, 8, 0.5), (3, 8, 0.4), (4, 6, 0.8), (3, 8, 0.0)])
-def test_lp_matches_highs(k, K, mu):
-    rng = np.random.default_rng(100 + k * 10 + K)
-    for _ in range(40):
-        p, n = _rand_contacts(rng, k)
+@pytest.mark.parametrize("k,K,mu,aligned,reps", [(2, 3, 0.5, False, 8), (2, 4, 0.5, False, 2),
+                                                 (2, 4, 0.3, True, 2), (1, 4, 0.5, False, 6), (3, 3, 0.4, True, 1),
+                                                 (2, 3, 0.0, False, 4), (2, 3, 0.8, True, 6)])
+def test_lp_matches_vertex_enumeration(k, K, mu, aligned, reps):
+    rng = np.random.default_rng(100 + 10 * k + K + int(aligned))
+    for _ in range(reps):
+        p, n = _rand_contacts(rng, k, aligned)
         c = p.mean(axis=0) + rng.normal(size=3) * 0.01
         rho = float(np.max(np.linalg.norm(p - c, axis=1)))
-        t, tj, piv = oracle.closure_lp(p, n, mu, K, c, rho)
-        ref = _highs_margin(p, n, mu, K, c, rho)
-        assert np.allclose(tj, ref, atol=1e-9, rtol=1e-8)
-        assert abs(t - ref.min()) <= 1e-9
-        assert (piv > 0).all()
+        t, tj, it = oracle.closure_lp(p, n, mu, K, c, rho)
+        W = oracle.wrench_matrix(p, n, mu, K, c, rho)
+        ref = np.array([_vertex_enumeration(W, K, j) for j in range(k)])
+        assert np.allclose(tj, ref, atol=1e-8, rtol=1e-7), (tj, ref)
+        assert abs(t - ref.min()) <= 1e-8
+
+
+def test_wrench_columns_match_their_definition():
+    """Edge m of contact i: normal component 1 along nu = -n, tangential part
+    of length mu at angle 2 pi m / K in the (x, y) basis; torque = r x e / rho."""
+    rng = np.random.default_rng(3)
+    p, n = _rand_contacts(rng, 2)
+    c = np.array([0.01, -0.02, 0.0])
+    W = oracle.wrench_matrix(p, n, 0.5, 8, c, 0.1)
+    for i in range(2):
+        nu = -n[i]
+        x, y = _onb(nu)
+        assert abs(x @ nu) < 1e-12 and abs(y @ nu) < 1e-12 and abs(x @ y) < 1e-12
+        assert np.allclose(np.cross(x, y), nu, atol=1e-12)  # right-handed
+        for m in range(8):
+            e = W[:3, 8 * i + m]
+            assert abs(e @ nu - 1.0) < 1e-12
+            tang = e - nu
+            assert abs(np.linalg.norm(tang) - 0.5) < 1e-12
+            ang = math.atan2(tang @ y, tang @ x) % (2 * math.pi)
+            assert abs(ang - 2 * math.pi * m / 8) < 1e-9 or abs(ang - 2 * math.pi * m / 8 - 2 * math.pi) < 1e-9
+            assert np.allclose(W[3:, 8 * i + m], np.cross(p[i] - c, e) / 0.1, atol=1e-12)
 
 
 def test_antipodal_pair_on_a_sphere_balances_exactly():
@@ -153,25 +179,6 @@ def test_score_tuples_marks_invalid_and_thresholds():
     assert np.isinf(m[1, 2]) and a[1, 2] == 0 and piv[1, 2] == 0
     fin = np.isfinite(m)
     assert np.array_equal(a[fin].astype(bool), m[fin] <= np.float32(0.01))
-
-
-def test_lp_matches_highs_on_tool_faces_with_axis_aligned_normals():
-    """Box faces of the tool object give normals with exact zero components;
-    their wrench columns are partly collinear, a degenerate case for the
-    simplex (rounding noise on structural zeros must never become a pivot)."""
-    import synth
-    obj = synth.tool_composite(4096, 1000)
-    rng = np.random.default_rng(21)
-    axis = np.sum(obj.n == 0.0, axis=1) >= 1
-    pool = np.nonzero(axis)[0]
-    c = obj.centroid.astype(np.float64)
-    for _ in range(120):
-        ids = rng.choice(pool, 3, replace=False)
-        p, n = obj.p[ids].astype(np.float64), obj.n[ids].astype(np.float64)
-        t, tj, piv = oracle.closure_lp(p, n, float(np.float32(0.4)), 8, c, float(obj.rho))
-        ref = _highs_margin(p, n, float(np.float32(0.4)), 8, c, float(obj.rho))
-        assert np.all(np.isfinite(tj))
-        assert np.allclose(tj, ref, atol=1e-9, rtol=1e-8)
 
 
 def test_oracle_workload_margins_are_never_nan():
