@@ -3,7 +3,7 @@
 Argument marshalling only: every step runs in the CUDA kernels of ``libcf.so``
 (see ``include/cf.h``).  PyTorch supplies device memory and the current CUDA
 stream.  There is no CPU fallback: importing this package fails if the library
-has not been built (``python -m paper_2511_07418_b300.build_lib``).
+has not been built (``python paper_2511_07418_b300/build_lib.py``).
 
 Entry points mirror the C ABI:
   build(hand, inv_h, bin_dirs, q)            -> Field          (cf_build)
@@ -24,7 +24,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libcf.so")
 
 if not os.path.exists(LIB_PATH):
-    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2511_07418_b300.build_lib` "
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python paper_2511_07418_b300/build_lib.py` "
                       "(the CUDA library is required; there is no CPU path)")
 
 _lib = ctypes.CDLL(LIB_PATH)

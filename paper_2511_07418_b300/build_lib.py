@@ -1,6 +1,6 @@
 """Compile libcf.so (the CUDA kernels + C ABI) in-tree for sm_103a with nvcc.
 
-Usage: python -m paper_2511_07418_b300.build_lib [--force] [--verbose]
+Usage: python paper_2511_07418_b300/build_lib.py [--force] [--verbose]
 """
 from __future__ import annotations
 
