@@ -177,6 +177,27 @@ int cf_score_tuples(const cf_points *obj, int32_t n_fingers, const uint32_t *d_m
                     int32_t n_poses, const cf_score_params *prm, int32_t *d_tuples, uint8_t *d_fingers,
                     float *d_margin, uint8_t *d_accept, cf_stream stream);
 
+/* Same computation and outputs as cf_score_tuples, but this call allocates no
+ * device memory.  It is for callers that cannot allocate while scoring.  Some
+ * have given a fixed budget of device memory to other work on the same GPU
+ * (a robot controller or renderer sharing the device).  Some must not risk a
+ * failed or blocking allocation in the middle of a control loop.  Some run
+ * where the allocator belongs to another framework.  The only scratch the
+ * kernel needs is its 4-byte pose work counter.  Here it lives in a
+ * library-wide device array of CF_NOALLOC_SCRATCH_BYTES bytes; every GPU that
+ * loads libcf holds that array until the process exits.  A call whose scratch
+ * need exceeds that size is rejected with CF_EINVAL.  The first call on each
+ * device looks up the array's device address.  Make that first call before
+ * any stream capture.  Every call shares the array and clears the counter
+ * before its kernel runs.  Calls whose work overlaps on the GPU (different
+ * streams, or different host threads on one device) race on the counter and
+ * must be serialised by the caller.  The paper has no counterpart to this
+ * entry point.  Errors: as cf_score_tuples, except CF_ENOMEM. */
+#define CF_NOALLOC_SCRATCH_BYTES 256
+int cf_score_tuples_noalloc(const cf_points *obj, int32_t n_fingers, const uint32_t *d_masks,
+                            const uint32_t *d_counts, int32_t n_poses, const cf_score_params *prm, int32_t *d_tuples,
+                            uint8_t *d_fingers, float *d_margin, uint8_t *d_accept, cf_stream stream);
+
 /* ---- one object request from host buffers -------------------------------- */
 
 typedef struct cf_plan cf_plan;

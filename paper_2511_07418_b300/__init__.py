@@ -86,6 +86,9 @@ _cf_field_load = _sig("cf_field_load", [c_char_p, POINTER(c_void_p)])
 _cf_query = _sig("cf_query_domains", [c_void_p, POINTER(Points), c_void_p, c_int32, c_void_p, c_void_p, c_void_p])
 _cf_score = _sig("cf_score_tuples", [POINTER(Points), c_int32, c_void_p, c_void_p, c_int32, POINTER(ScoreParams),
                                      c_void_p, c_void_p, c_void_p, c_void_p, c_void_p])
+_cf_score_noalloc = _sig("cf_score_tuples_noalloc", [POINTER(Points), c_int32, c_void_p, c_void_p, c_int32,
+                                                     POINTER(ScoreParams), c_void_p, c_void_p, c_void_p, c_void_p,
+                                                     c_void_p])
 _cf_plan_create = _sig("cf_plan_create", [c_int32, c_int32, c_int32, POINTER(ScoreParams), POINTER(c_void_p)])
 _cf_plan_run_host = _sig("cf_plan_run_host", [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_int32,
                                               POINTER(ScoreParams), c_void_p, c_void_p, c_void_p, POINTER(c_int64),
@@ -97,7 +100,7 @@ _cf_device_counters = _sig("cf_device_counters", [POINTER(c_uint64), c_int])
 
 EXPORTED = ["cf_build", "cf_field_get_info", "cf_field_copy_table", "cf_field_destroy", "cf_field_save",
             "cf_field_load", "cf_query_domains", "cf_score_tuples", "cf_plan_create", "cf_plan_run_host",
-            "cf_plan_destroy", "cf_last_error", "cf_device_status", "cf_device_counters"]
+            "cf_plan_destroy", "cf_last_error", "cf_device_status", "cf_device_counters", "cf_score_tuples_noalloc"]
 
 
 def _check(rc: int):
@@ -253,6 +256,24 @@ def score_tuples(soa, n_fingers: int, masks, counts, prm: ScoreParams, tuples=No
     fp = _dev(fingers, torch.uint8, "fingers") if fingers is not None else None
     _check(_cf_score(byref(obj), int(n_fingers), mp, cp, P, byref(prm), _dev(tuples, torch.int32, "tuples"), fp,
                      _dev(margin, torch.float32, "margin"), _dev(accept, torch.uint8, "accept"), _stream(stream)))
+    return tuples, fingers, margin, accept
+
+
+def score_tuples_noalloc(soa, n_fingers: int, masks, counts, prm: ScoreParams, tuples, fingers, margin, accept,
+                         stream=None):
+    """cf_score_tuples_noalloc: like score_tuples, but every output tensor is
+    supplied by the caller and libcf allocates no device memory during the call
+    (its work counter lives in a library-wide device array; calls that overlap
+    on the GPU must be serialised by the caller)."""
+    import torch
+    obj = points_struct(soa)
+    P = int(tuples.shape[0])
+    mp = _dev(masks, torch.int32, "masks") if masks is not None else None
+    cp = _dev(counts, torch.int32, "counts") if counts is not None else None
+    fp = _dev(fingers, torch.uint8, "fingers") if fingers is not None else None
+    _check(_cf_score_noalloc(byref(obj), int(n_fingers), mp, cp, P, byref(prm), _dev(tuples, torch.int32, "tuples"),
+                             fp, _dev(margin, torch.float32, "margin"), _dev(accept, torch.uint8, "accept"),
+                             _stream(stream)))
     return tuples, fingers, margin, accept
 
 

@@ -459,6 +459,56 @@ extern "C" int cf_score_tuples(const cf_points *obj, int32_t n_fingers, const ui
 }
 
 // ---------------------------------------------------------------------------
+// scoring without allocation: the work counter lives in a static device array
+// ---------------------------------------------------------------------------
+namespace {
+
+static __device__ __align__(256) unsigned int g_noalloc_scratch[CF_NOALLOC_SCRATCH_BYTES / sizeof(unsigned int)];
+
+std::mutex g_noalloc_mu;
+unsigned int *g_noalloc_addr[64] = {};  // device address of g_noalloc_scratch, per device
+
+// Device address of the scratch array on the current device (looked up once
+// per device; the host-side symbol is not a device address).
+int noalloc_scratch(unsigned int **out) {
+    int dev = 0;
+    CF_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(CF_EINVAL, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        unsigned int *p = nullptr;
+        CF_TRY(cudaGetSymbolAddress((void **)&p, g_noalloc_scratch), "cudaGetSymbolAddress(noalloc scratch)");
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return CF_OK;
+}
+
+}  // namespace
+
+extern "C" int cf_score_tuples_noalloc(const cf_points *obj, int32_t n_fingers, const uint32_t *d_masks,
+                                       const uint32_t *d_counts, int32_t n_poses, const cf_score_params *prm,
+                                       int32_t *d_tuples, uint8_t *d_fingers, float *d_margin, uint8_t *d_accept,
+                                       cf_stream stream) {
+    ScoreArgs a;
+    int rc = fill_score_args(obj, n_fingers, d_masks, d_counts, n_poses, prm, d_tuples, d_fingers, d_margin,
+                             d_accept, &a);
+    if (rc) return rc;
+    const size_t need = sizeof(unsigned int);  // the pose work counter
+    if (need > (size_t)CF_NOALLOC_SCRATCH_BYTES)
+        return fail(CF_EINVAL, "scratch need %zu B exceeds the %d B no-allocation scratch", need,
+                    CF_NOALLOC_SCRATCH_BYTES);
+    unsigned int *scratch = nullptr;
+    if ((rc = noalloc_scratch(&scratch))) return rc;
+    if (n_poses == 0) return CF_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    CF_TRY(cudaMemsetAsync(scratch, 0, need, st), "clear no-allocation scratch");
+    a.work = scratch;
+    CF_TRY(launch_score(a, st), "launch k_sample_score");
+    return CF_OK;
+}
+
+// ---------------------------------------------------------------------------
 // plan: one object request from host buffers
 // ---------------------------------------------------------------------------
 struct cf_plan {
