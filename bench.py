@@ -220,8 +220,11 @@ def run_ours(args):
     tuples = torch.empty((w.P, w.T, w.k), dtype=torch.int32, device=dev)
     fingers = torch.empty((w.P, w.T, w.k), dtype=torch.uint8, device=dev)
     prm = cf.score_params(w.T, w.k, w.mu, w.K, w.eps, w.obj.centroid, w.obj.rho, w.seed)
+    prm_given = cf.score_params(w.T, w.k, w.mu, w.K, w.eps, w.obj.centroid, w.obj.rho, w.seed, tuples_given=True)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     acc_total = torch.zeros((), dtype=torch.int64, device=dev)
+
+    n_ev = 5
 
     def step(ev):
         ev[0].record()
@@ -229,8 +232,10 @@ def run_ours(args):
         ev[1].record()
         cf.query_domains(field, soa, poses, masks, counts)
         ev[2].record()
-        _, _, _, accept = cf.score_tuples(soa, F, masks, counts, prm, tuples, fingers)
+        cf.sample_tuples(soa, F, masks, counts, prm, tuples, fingers)
         ev[3].record()
+        _, _, _, accept = cf.score_tuples(soa, F, None, None, prm_given, tuples)
+        ev[4].record()
         acc_total.add_(accept.sum())
         return field
 
@@ -241,7 +246,7 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     for _ in range(max(3, args.warmup)):
-        step([torch.cuda.Event(enable_timing=True) for _ in range(4)])
+        step([torch.cuda.Event(enable_timing=True) for _ in range(n_ev)])
     acc_total.zero_()
     barrier()
     cf.device_counters(reset=True)
@@ -253,7 +258,7 @@ def run_ours(args):
     t_wall = time.perf_counter()
     for i in range(args.steps):
         flush.fill_(float(i))  # evict L2 between steps (not timed)
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(n_ev)]
         step(ev)
         evs.append(ev)
     barrier()
@@ -261,7 +266,7 @@ def run_ours(args):
     clocks = sampler.stop()
     status = cf.device_status()
     counters = cf.device_counters()
-    ms = np.array([[e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3])] for e in evs])
+    ms = np.array([[e[j].elapsed_time(e[j + 1]) for j in range(n_ev - 1)] for e in evs])
     total_ms = float(ms.sum())
     accepted = int(acc_total.item())
 
@@ -308,7 +313,7 @@ def run_ours(args):
         return
 
     value = accepted / (total_ms / 1e3)
-    per = ms.mean(axis=0)  # build, query, score ms per step (rank 0)
+    per = ms.mean(axis=0)  # build, query, sample, score ms per step (rank 0)
     sm_mhz = (clocks or {}).get("sm_mhz") or 2032.0
     n_sm = props.multi_processor_count
     peak_fp32 = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s: FP32 lanes x FMA x clock
@@ -319,11 +324,13 @@ def run_ours(args):
     kernels = {
         "k_fk_cell_bounds+k_fk_bin": {"ms": per[0], "tflops": b_flop / (per[0] * 1e-3) / 1e12},
         "k_query_domains": {"ms": per[1], "tflops": q_flop / (per[1] * 1e-3) / 1e12},
-        "k_sample_score": {"ms": per[2], "tflops": s_flop_own / (per[2] * 1e-3) / 1e12},
+        "k_sample_tuples": {"ms": per[2]},
+        "k_score_tuples": {"ms": per[3], "tflops": s_flop_own / (per[3] * 1e-3) / 1e12},
     }
     for v in kernels.values():
-        v["frac"] = v["tflops"] / peak_fp32
-    dom = max(["k_query_domains", "k_sample_score"], key=lambda k: kernels[k]["ms"])
+        if "tflops" in v:
+            v["frac"] = v["tflops"] / peak_fp32
+    dom = max(["k_query_domains", "k_score_tuples"], key=lambda k: kernels[k]["ms"])
     roof = {"kernel": dom, "bound": "alu", "achieved": kernels[dom]["tflops"], "peak": peak_fp32,
             "unit": "TFLOP/s", "frac": kernels[dom]["frac"], "traffic": None,
             "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 flop/FMA x {sm_mhz:.0f} MHz median SM clock sampled "
@@ -335,9 +342,9 @@ def run_ours(args):
             "config": _config(w),
             "value_field_cached": accepted / ((total_ms - float(ms[:, 0].sum())) / 1e3),
             "accept_rate": accepted / (world * args.steps * w.P * w.T),
-            "breakdown_ms": {"build": per[0], "query": per[1], "sample_score": per[2]},
+            "breakdown_ms": {"build": per[0], "query": per[1], "sample": per[2], "score": per[3]},
             "wall_s_timed_region": t_wall,
-            "gpu_launches": 4 * args.steps,
+            "gpu_launches": 5 * args.steps,
             "device_status": status,
             "lp": {"pivots_per_tuple": counters["lp_pivots"] / max(1, counters["tuples_scored"]),
                    "lps_per_tuple": counters["lps"] / max(1, counters["tuples_scored"])},

@@ -171,8 +171,8 @@ int cf_query_domains(const cf_field *field, const cf_points *obj, const float *d
  * e_im = nu_i + mu (cos(2 pi m/K) x_i + sin(2 pi m/K) y_i), nu_i = -n_i,
  * (x_i, y_i) the Duff et al. 2017 basis of nu_i.  d_margin [P][T] (+inf when
  * invalid), d_accept [P][T] = margin <= eps.  d_masks / d_counts / d_fingers
- * may be NULL when tuples_given.  Scratch: a 4-byte work counter, allocated
- * stream-ordered per call.  Errors: CF_EINVAL, CF_ENOMEM, CF_ECUDA. */
+ * may be NULL when tuples_given.  Scratch: a 4-byte tuple work counter,
+ * allocated stream-ordered per call.  Errors: CF_EINVAL, CF_ENOMEM, CF_ECUDA. */
 int cf_score_tuples(const cf_points *obj, int32_t n_fingers, const uint32_t *d_masks, const uint32_t *d_counts,
                     int32_t n_poses, const cf_score_params *prm, int32_t *d_tuples, uint8_t *d_fingers,
                     float *d_margin, uint8_t *d_accept, cf_stream stream);
@@ -183,7 +183,7 @@ int cf_score_tuples(const cf_points *obj, int32_t n_fingers, const uint32_t *d_m
  * (a robot controller or renderer sharing the device).  Some must not risk a
  * failed or blocking allocation in the middle of a control loop.  Some run
  * where the allocator belongs to another framework.  The only scratch the
- * kernel needs is its 4-byte pose work counter.  Here it lives in a
+ * kernel needs is its 4-byte tuple work counter.  Here it lives in a
  * library-wide device array of CF_NOALLOC_SCRATCH_BYTES bytes; every GPU that
  * loads libcf holds that array until the process exits.  A call whose scratch
  * need exceeds that size is rejected with CF_EINVAL.  The first call on each
@@ -197,6 +197,14 @@ int cf_score_tuples(const cf_points *obj, int32_t n_fingers, const uint32_t *d_m
 int cf_score_tuples_noalloc(const cf_points *obj, int32_t n_fingers, const uint32_t *d_masks,
                             const uint32_t *d_counts, int32_t n_poses, const cf_score_params *prm, int32_t *d_tuples,
                             uint8_t *d_fingers, float *d_margin, uint8_t *d_accept, cf_stream stream);
+
+/* Sampling step of cf_score_tuples on its own (Sec. 4.3, Alg. 2 Random(D_i)):
+ * writes d_tuples / d_fingers exactly as cf_score_tuples would, scores
+ * nothing.  prm->tuples_given must be 0; d_margin-style outputs are not used.
+ * Errors: CF_EINVAL, CF_ECUDA.  Asynchronous on `stream`. */
+int cf_sample_tuples(const cf_points *obj, int32_t n_fingers, const uint32_t *d_masks, const uint32_t *d_counts,
+                     int32_t n_poses, const cf_score_params *prm, int32_t *d_tuples, uint8_t *d_fingers,
+                     cf_stream stream);
 
 /* ---- one object request from host buffers -------------------------------- */
 

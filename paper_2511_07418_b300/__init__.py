@@ -86,6 +86,8 @@ _cf_field_load = _sig("cf_field_load", [c_char_p, POINTER(c_void_p)])
 _cf_query = _sig("cf_query_domains", [c_void_p, POINTER(Points), c_void_p, c_int32, c_void_p, c_void_p, c_void_p])
 _cf_score = _sig("cf_score_tuples", [POINTER(Points), c_int32, c_void_p, c_void_p, c_int32, POINTER(ScoreParams),
                                      c_void_p, c_void_p, c_void_p, c_void_p, c_void_p])
+_cf_sample = _sig("cf_sample_tuples", [POINTER(Points), c_int32, c_void_p, c_void_p, c_int32, POINTER(ScoreParams),
+                                       c_void_p, c_void_p, c_void_p])
 _cf_score_noalloc = _sig("cf_score_tuples_noalloc", [POINTER(Points), c_int32, c_void_p, c_void_p, c_int32,
                                                      POINTER(ScoreParams), c_void_p, c_void_p, c_void_p, c_void_p,
                                                      c_void_p])
@@ -100,7 +102,8 @@ _cf_device_counters = _sig("cf_device_counters", [POINTER(c_uint64), c_int])
 
 EXPORTED = ["cf_build", "cf_field_get_info", "cf_field_copy_table", "cf_field_destroy", "cf_field_save",
             "cf_field_load", "cf_query_domains", "cf_score_tuples", "cf_plan_create", "cf_plan_run_host",
-            "cf_plan_destroy", "cf_last_error", "cf_device_status", "cf_device_counters", "cf_score_tuples_noalloc"]
+            "cf_plan_destroy", "cf_last_error", "cf_device_status", "cf_device_counters", "cf_score_tuples_noalloc",
+            "cf_sample_tuples"]
 
 
 def _check(rc: int):
@@ -257,6 +260,22 @@ def score_tuples(soa, n_fingers: int, masks, counts, prm: ScoreParams, tuples=No
     _check(_cf_score(byref(obj), int(n_fingers), mp, cp, P, byref(prm), _dev(tuples, torch.int32, "tuples"), fp,
                      _dev(margin, torch.float32, "margin"), _dev(accept, torch.uint8, "accept"), _stream(stream)))
     return tuples, fingers, margin, accept
+
+
+def sample_tuples(soa, n_fingers: int, masks, counts, prm: ScoreParams, tuples=None, fingers=None, stream=None):
+    """cf_sample_tuples -> (tuples [P,T,k] int32, fingers [P,T,k] uint8)."""
+    import torch
+    obj = points_struct(soa)
+    P = int(counts.shape[0])
+    T, k = int(prm.n_tuples), int(prm.k)
+    if tuples is None:
+        tuples = torch.empty((P, T, k), dtype=torch.int32, device=soa.device)
+    if fingers is None:
+        fingers = torch.empty((P, T, k), dtype=torch.uint8, device=soa.device)
+    _check(_cf_sample(byref(obj), int(n_fingers), _dev(masks, torch.int32, "masks"), _dev(counts, torch.int32, "counts"),
+                      P, byref(prm), _dev(tuples, torch.int32, "tuples"), _dev(fingers, torch.uint8, "fingers"),
+                      _stream(stream)))
+    return tuples, fingers
 
 
 def score_tuples_noalloc(soa, n_fingers: int, masks, counts, prm: ScoreParams, tuples, fingers, margin, accept,

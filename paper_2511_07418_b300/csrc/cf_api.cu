@@ -453,8 +453,21 @@ extern "C" int cf_score_tuples(const cf_points *obj, int32_t n_fingers, const ui
         e = launch_score(a, st);
     }
     cudaError_t e2 = cudaFreeAsync(work, st);
-    if (e != cudaSuccess) return cuda_fail(e, "launch k_sample_score");
+    if (e != cudaSuccess) return cuda_fail(e, "launch k_sample_tuples / k_score_tuples");
     if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync(work counter)");
+    return CF_OK;
+}
+
+extern "C" int cf_sample_tuples(const cf_points *obj, int32_t n_fingers, const uint32_t *d_masks,
+                                const uint32_t *d_counts, int32_t n_poses, const cf_score_params *prm,
+                                int32_t *d_tuples, uint8_t *d_fingers, cf_stream stream) {
+    if (prm && prm->tuples_given) return fail(CF_EINVAL, "cf_sample_tuples needs tuples_given = 0");
+    ScoreArgs a;
+    int rc = fill_score_args(obj, n_fingers, d_masks, d_counts, n_poses, prm, d_tuples, d_fingers,
+                             (float *)d_tuples, (uint8_t *)d_tuples, &a);
+    if (rc) return rc;
+    if (n_poses == 0) return CF_OK;
+    CF_TRY(launch_sample(a, (cudaStream_t)stream), "launch k_sample_tuples");
     return CF_OK;
 }
 
@@ -494,7 +507,7 @@ extern "C" int cf_score_tuples_noalloc(const cf_points *obj, int32_t n_fingers, 
     int rc = fill_score_args(obj, n_fingers, d_masks, d_counts, n_poses, prm, d_tuples, d_fingers, d_margin,
                              d_accept, &a);
     if (rc) return rc;
-    const size_t need = sizeof(unsigned int);  // the pose work counter
+    const size_t need = sizeof(unsigned int);  // the tuple work counter
     if (need > (size_t)CF_NOALLOC_SCRATCH_BYTES)
         return fail(CF_EINVAL, "scratch need %zu B exceeds the %d B no-allocation scratch", need,
                     CF_NOALLOC_SCRATCH_BYTES);
@@ -504,7 +517,7 @@ extern "C" int cf_score_tuples_noalloc(const cf_points *obj, int32_t n_fingers, 
     cudaStream_t st = (cudaStream_t)stream;
     CF_TRY(cudaMemsetAsync(scratch, 0, need, st), "clear no-allocation scratch");
     a.work = scratch;
-    CF_TRY(launch_score(a, st), "launch k_sample_score");
+    CF_TRY(launch_score(a, st), "launch k_sample_tuples / k_score_tuples");
     return CF_OK;
 }
 
@@ -581,7 +594,7 @@ extern "C" int cf_plan_run_host(cf_plan *pl, const cf_field *fd, const float *h_
     if (n_poses > 0) {
         CF_TRY(cudaMemsetAsync(pl->d_work, 0, sizeof(unsigned int), st), "memset work");
         a.work = pl->d_work;
-        CF_TRY(launch_score(a, st), "launch k_sample_score");
+        CF_TRY(launch_score(a, st), "launch k_sample_tuples / k_score_tuples");
     }
     uint8_t *acc = h_accept ? h_accept : pl->h_accept.data();
     if (PT > 0) {

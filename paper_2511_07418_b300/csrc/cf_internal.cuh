@@ -95,10 +95,13 @@ struct ScoreArgs {
     uint8_t *fingers;
     float *margin;
     uint8_t *accept;
-    unsigned int *work;  // scratch: pose work counter, zero at launch
+    unsigned int *work;  // scratch: tuple work counter, zero at launch
     unsigned int *status;          // device status word (CF_DEV_* bits)
     unsigned long long *counters;  // [0] pivots, [1] LPs, [2] tuples
 };
+// k_sample_tuples (unless tuples_given) then k_score_tuples
 cudaError_t launch_score(const ScoreArgs &a, cudaStream_t st);
+// k_sample_tuples only
+cudaError_t launch_sample(const ScoreArgs &a, cudaStream_t st);
 
 }  // namespace cf

@@ -270,3 +270,14 @@ def test_repeatable_bits(cf):
     cnt = cf.device_counters()
     assert cnt["lps"] > 0 and cnt["lp_pivots"] >= 2 * cnt["lps"]
     assert cf.device_status() == 0
+
+
+def test_split_sampling_and_scoring_equal_the_fused_call(cf):
+    w = synth.workload("hand16_superquadric", P=40, S=8192)
+    r = _gpu_path(cf, w)
+    t2, f2 = cf.sample_tuples(r["soa"], w.hand.F, r["masks"], r["counts"], r["prm"])
+    pg = cf.score_params(w.T, w.k, w.mu, w.K, w.eps, w.obj.centroid, w.obj.rho, w.seed, tuples_given=True)
+    _, _, m2, a2 = cf.score_tuples(r["soa"], w.hand.F, None, None, pg, tuples=t2)
+    torch.cuda.synchronize()
+    assert torch.equal(t2, r["tuples"]) and torch.equal(f2, r["fingers"])
+    assert torch.equal(m2, r["margin"]) and torch.equal(a2, r["accept"])
