@@ -24,8 +24,11 @@
  *  - Handles (cf_field, cf_plan) are owned by the library and freed by their
  *    destroy call.
  *  - Work is queued on the caller's CUDA stream (cf_stream = cudaStream_t, NULL
- *    = legacy default stream).  cf_build and cf_plan_run_host synchronise that
- *    stream before returning; cf_query_domains and cf_score_tuples do not.
+ *    = legacy default stream).  cf_build waits once on that stream (for the
+ *    table's extents) and returns with its last kernel queued;
+ *    cf_plan_run_host synchronises the stream; the other calls do not.
+ *  - Device memory the library owns comes from a per-device stream-ordered
+ *    pool that keeps freed blocks for reuse.
  *  - Shapes are checked on the host (CF_EINVAL); a kernel that meets a
  *    condition it cannot honour (an LP that exceeds its pivot cap) sets a bit in
  *    a device status word read by cf_device_status().
@@ -94,15 +97,23 @@ typedef struct cf_field_params {
 
 typedef struct cf_field cf_field;
 
+/* Table layout: one box of cells covering every finger's samples.  Cell
+ * (x, y, z) of the box (x fastest) owns a record of record_words uint32 words;
+ * finger f's normal-bin set is bits [(f % fingers_per_word) * bits_per_finger,
+ * + n_bins) of word f / fingers_per_word of the record. */
 typedef struct cf_field_info {
     int32_t n_fingers, n_joints, n_surf, n_bins, n_samples;
     float inv_h;
-    int32_t lo[CF_MAX_FINGERS][3];    /* first cell of finger f's table, per axis */
-    int32_t dims[CF_MAX_FINGERS][3];  /* cells per axis (0 if the finger has no sample) */
-    int64_t word_offset[CF_MAX_FINGERS]; /* finger f's table starts at this uint32 word */
-    int64_t table_words;              /* total uint32 words of the bit table */
-    int64_t device_bytes;             /* device memory held by the field */
-    float build_ms;                   /* device time of the two build kernels */
+    int32_t box_lo[3];                 /* first cell of the box, per axis */
+    int32_t box_dims[3];               /* cells per axis (0 when the field is empty) */
+    int32_t bits_per_finger;           /* 8, 16 or 32 */
+    int32_t fingers_per_word;          /* 32 / bits_per_finger */
+    int32_t record_words;              /* ceil(n_fingers / fingers_per_word) */
+    int32_t finger_lo[CF_MAX_FINGERS][3];   /* tight cell bounds of finger f's samples */
+    int32_t finger_dims[CF_MAX_FINGERS][3]; /* (0 if the finger has no sample) */
+    int64_t table_words;               /* total uint32 words of the bit table */
+    int64_t device_bytes;              /* device memory held by the field */
+    float build_ms;                    /* device time of the two build kernels */
 } cf_field_info;
 
 /* Object surface points + outward unit normals, device SoA, N each. */
@@ -131,7 +142,8 @@ typedef struct cf_score_params {
  * configurations d_q [F][J][n_samples] (device, FP32, SoA per joint).
  * Every (finger, sample, surface point) contact vector is transformed to the
  * palm frame and sets bit bin(n) of its cell's word in the finger's table.
- * Two passes: cell bounds, then binning.  Synchronises `stream`.
+ * Two passes: cell bounds (the host reads them back: one wait on `stream`),
+ * then binning, left queued on `stream`.
  * Errors: CF_EINVAL (shapes, NULLs, B or J out of range, cell bounds beyond
  * |k| < 2^20), CF_ENOMEM, CF_ECUDA.  *out is set only on success. */
 int cf_build(const cf_hand_desc *hand, const cf_field_params *prm, const float *d_q, int32_t n_samples,
@@ -142,6 +154,10 @@ int cf_field_get_info(const cf_field *field, cf_field_info *info);
 /* Copy the bit table (table_words uint32 words) to host memory. */
 int cf_field_copy_table(const cf_field *field, uint32_t *host_words, int64_t capacity_words);
 
+/* Frees the field.  Its device memory is released in order on the stream it was
+ * built on (that stream must still exist); work that uses the field on other
+ * streams must be finished, or ordered before that stream's current work,
+ * when this is called. */
 int cf_field_destroy(cf_field *field);
 
 /* Raw save / load of a field (header + bin directions + table). */

@@ -55,9 +55,10 @@ class FieldParams(Structure):
 class FieldInfo(Structure):
     _fields_ = [("n_fingers", c_int32), ("n_joints", c_int32), ("n_surf", c_int32), ("n_bins", c_int32),
                 ("n_samples", c_int32), ("inv_h", c_float),
-                ("lo", (c_int32 * 3) * CF_MAX_FINGERS), ("dims", (c_int32 * 3) * CF_MAX_FINGERS),
-                ("word_offset", c_int64 * CF_MAX_FINGERS), ("table_words", c_int64), ("device_bytes", c_int64),
-                ("build_ms", c_float)]
+                ("box_lo", c_int32 * 3), ("box_dims", c_int32 * 3), ("bits_per_finger", c_int32),
+                ("fingers_per_word", c_int32), ("record_words", c_int32),
+                ("finger_lo", (c_int32 * 3) * CF_MAX_FINGERS), ("finger_dims", (c_int32 * 3) * CF_MAX_FINGERS),
+                ("table_words", c_int64), ("device_bytes", c_int64), ("build_ms", c_float)]
 
 
 class Points(Structure):

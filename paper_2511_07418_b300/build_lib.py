@@ -14,7 +14,7 @@ SRC_DIR = os.path.join(HERE, "csrc")
 INC_DIR = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcf.so")
-SOURCES = ["cf_api.cu", "cf_build.cu", "cf_query.cu", "cf_score.cu"]
+SOURCES = ["cf_api.cu", "cf_build.cu", "cf_query.cu", "cf_score.cu", "cf_bincand.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 
@@ -33,7 +33,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if verbose:
         common += ["-Xptxas", "-v"]
     for src in SOURCES:
-        obj = os.path.join(BUILD_DIR, src.replace(".cu", ".o"))
+        obj = os.path.join(BUILD_DIR, os.path.splitext(src)[0] + ".o")
         cmd = [NVCC, *common, "-c", os.path.join(SRC_DIR, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:

@@ -78,21 +78,94 @@ int device_state(DevState *out) {
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// device memory: one stream-ordered pool per device, owned by the library
+// (allocations and frees are ordered on the caller's stream; the pool keeps
+// freed memory for reuse instead of returning it to the driver)
+// ---------------------------------------------------------------------------
+namespace {
+
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[64] = {};
+
+int device_pool(cudaMemPool_t *out) {
+    int dev = 0;
+    CF_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(CF_EINVAL, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof props);
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        CF_TRY(cudaMemPoolCreate(&g_pool[dev], &props), "cudaMemPoolCreate");
+        uint64_t keep = UINT64_MAX;
+        CF_TRY(cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &keep), "pool attribute");
+    }
+    *out = g_pool[dev];
+    return CF_OK;
+}
+
+int pool_alloc(void **p, size_t bytes, cudaStream_t st, const char *what) {
+    cudaMemPool_t pool;
+    int rc = device_pool(&pool);
+    if (rc) return rc;
+    CF_TRY(cudaMallocFromPoolAsync(p, bytes ? bytes : 1, pool, st), what);
+    return CF_OK;
+}
+
+// Normal-bin candidate tables, computed once per distinct direction set.
+struct CandEntry {
+    std::vector<float> dirs;
+    std::vector<uint32_t> table;
+    int worst;
+};
+std::mutex g_cand_mu;
+std::vector<CandEntry *> g_cand_cache;
+
+const CandEntry *cached_candidates(const float *dirs, int B) {
+    std::lock_guard<std::mutex> lk(g_cand_mu);
+    for (const CandEntry *c : g_cand_cache)
+        if ((int)c->dirs.size() == 3 * B && memcmp(c->dirs.data(), dirs, sizeof(float) * 3 * B) == 0) return c;
+    CandEntry *c = new CandEntry();
+    c->dirs.assign(dirs, dirs + 3 * B);
+    c->table.resize(kCandCells);
+    c->worst = build_bin_candidates(dirs, B, c->table.data());
+    g_cand_cache.push_back(c);
+    return c;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
 // field
 // ---------------------------------------------------------------------------
 struct cf_field {
     int dev = 0;
+    cudaStream_t st = nullptr;  // device memory is freed on this stream
     int F = 0, J = 0, M = 0, S = 0, B = 0;
     FieldGeom geom{};
     HandDev hand{};
-    void *d_block = nullptr;    // hand arrays + bounds scratch
+    void *d_block = nullptr;     // hand arrays + bounds scratch
     uint32_t *d_table = nullptr;
+    uint32_t *d_cand = nullptr;  // normal-bin candidate table
     int64_t table_words = 0;
     int64_t device_bytes = 0;
-    float build_ms = 0.f;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    float build_ms = -1.f;
 };
 
 namespace {
+
+void field_release(cf_field *fd) {
+    if (!fd) return;
+    if (fd->d_block) cudaFreeAsync(fd->d_block, fd->st);
+    if (fd->d_table) cudaFreeAsync(fd->d_table, fd->st);
+    if (fd->d_cand) cudaFreeAsync(fd->d_cand, fd->st);
+    if (fd->ev0) cudaEventDestroy(fd->ev0);
+    if (fd->ev1) cudaEventDestroy(fd->ev1);
+    delete fd;
+}
 
 int check_hand(const cf_hand_desc *h) {
     if (!h) return fail(CF_EINVAL, "hand is NULL");
@@ -107,6 +180,18 @@ int check_hand(const cf_hand_desc *h) {
     for (int i = 0; i < h->n_fingers * h->n_surf; ++i)
         if (h->surf_link[i] < 0 || h->surf_link[i] >= h->n_joints)
             return fail(CF_EINVAL, "surf_link[%d]=%d not in [0,%d)", i, h->surf_link[i], h->n_joints);
+    return CF_OK;
+}
+
+// Upload the normal-bin candidate table of fd's directions (stream-ordered).
+int setup_candidates(cf_field *fd) {
+    const CandEntry *c = cached_candidates(&fd->geom.dirs[0][0], fd->geom.B);
+    fd->geom.use_cand = c->worst <= 4 ? 1 : 0;
+    int rc = pool_alloc((void **)&fd->d_cand, sizeof(uint32_t) * kCandCells, fd->st, "alloc candidates");
+    if (rc) return rc;
+    CF_TRY(cudaMemcpyAsync(fd->d_cand, c->table.data(), sizeof(uint32_t) * kCandCells, cudaMemcpyHostToDevice, fd->st),
+           "copy candidates");
+    fd->geom.cand = fd->d_cand;
     return CF_OK;
 }
 
@@ -143,12 +228,20 @@ extern "C" int cf_build(const cf_hand_desc *hand, const cf_field_params *prm, co
     cf_field *fd = new cf_field();
     const int F = hand->n_fingers, J = hand->n_joints, M = hand->n_surf;
     fd->F = F; fd->J = J; fd->M = M; fd->S = n_samples;
+    fd->st = st;
     CF_TRY(cudaGetDevice(&fd->dev), "cudaGetDevice");
-    if ((rc = geom_from_params(fd, prm))) { delete fd; return rc; }
+    if ((rc = geom_from_params(fd, prm)) || (rc = setup_candidates(fd))) { field_release(fd); return rc; }
 
-    // host staging: surface points sorted by link, link ranges
-    std::vector<float> surf((size_t)F * M * 8, 0.f);
-    std::vector<int> lbeg((size_t)F * (J + 1), 0);
+    // host staging of the hand block: base | axis | offset | surf (sorted by link) | link ranges | bounds init
+    const size_t n_base = (size_t)F * 12, n_axis = (size_t)F * J * 3, n_surf = (size_t)F * M * 8;
+    const size_t n_lb = (size_t)F * (J + 1), n_bnd = (size_t)6 * F;
+    const size_t bytes = sizeof(float) * (n_base + 2 * n_axis + n_surf) + sizeof(int) * (n_lb + n_bnd);
+    std::vector<char> stage(bytes, 0);
+    float *h_base = (float *)stage.data(), *h_axis = h_base + n_base, *h_off = h_axis + n_axis, *h_surf = h_off + n_axis;
+    int *h_lb = (int *)(h_surf + n_surf), *h_bnd = h_lb + n_lb;
+    memcpy(h_base, hand->base, sizeof(float) * n_base);
+    memcpy(h_axis, hand->axis, sizeof(float) * n_axis);
+    memcpy(h_off, hand->offset, sizeof(float) * n_axis);
     for (int f = 0; f < F; ++f) {
         std::vector<int> order(M);
         for (int m = 0; m < M; ++m) order[m] = m;
@@ -156,95 +249,93 @@ extern "C" int cf_build(const cf_hand_desc *hand, const cf_field_params *prm, co
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lk[a] < lk[b]; });
         for (int m = 0; m < M; ++m) {
             const int src = order[m];
-            float *d = &surf[((size_t)f * M + m) * 8];
+            float *d = h_surf + ((size_t)f * M + m) * 8;
             for (int c = 0; c < 3; ++c) {
                 d[c] = hand->surf_p[((size_t)f * M + src) * 3 + c];
                 d[3 + c] = hand->surf_n[((size_t)f * M + src) * 3 + c];
             }
             d[6] = (float)lk[src];
         }
-        int *lb = &lbeg[(size_t)f * (J + 1)];
         for (int l = 0; l <= J; ++l) {
             int c = 0;
             for (int m = 0; m < M; ++m) c += lk[m] < l;
-            lb[l] = c;
+            h_lb[(size_t)f * (J + 1) + l] = c;
         }
+        for (int c = 0; c < 3; ++c) { h_bnd[6 * f + c] = INT_MAX; h_bnd[6 * f + 3 + c] = INT_MIN; }
     }
-    const size_t n_base = (size_t)F * 12, n_axis = (size_t)F * J * 3, n_surf = surf.size();
-    const size_t bytes = sizeof(float) * (n_base + 2 * n_axis + n_surf) + sizeof(int) * (lbeg.size() + 6 * F);
-    cudaError_t e = cudaMalloc(&fd->d_block, bytes);
-    if (e != cudaSuccess) { delete fd; return cuda_fail(e, "cudaMalloc(hand)"); }
-    float *p = (float *)fd->d_block;
-    float *d_base = p; p += n_base;
-    float *d_axis = p; p += n_axis;
-    float *d_off = p; p += n_axis;
-    float *d_surf = p; p += n_surf;
-    int *d_lb = (int *)p;
-    int *d_bounds = d_lb + lbeg.size();
-    std::vector<int> binit((size_t)6 * F);
-    for (int f = 0; f < F; ++f)
-        for (int c = 0; c < 3; ++c) { binit[6 * f + c] = INT_MAX; binit[6 * f + 3 + c] = INT_MIN; }
+    if ((rc = pool_alloc(&fd->d_block, bytes, st, "alloc hand block"))) { field_release(fd); return rc; }
+    float *d_base = (float *)fd->d_block, *d_axis = d_base + n_base, *d_off = d_axis + n_axis, *d_surf = d_off + n_axis;
+    int *d_lb = (int *)(d_surf + n_surf), *d_bounds = d_lb + n_lb;
+    fd->hand = HandDev{F, J, M, d_base, d_axis, d_off, d_surf, d_lb};
+    float *d_links = nullptr;
     auto bail = [&](cudaError_t err, const char *what) {
-        cudaFree(fd->d_block);
-        if (fd->d_table) cudaFree(fd->d_table);
-        delete fd;
+        if (d_links) cudaFreeAsync(d_links, st);
+        field_release(fd);
         return cuda_fail(err, what);
     };
 #define CF_STEP(call, what) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) return bail(e_, what); } while (0)
-    CF_STEP(cudaMemcpyAsync(d_base, hand->base, sizeof(float) * n_base, cudaMemcpyHostToDevice, st), "copy base");
-    CF_STEP(cudaMemcpyAsync(d_axis, hand->axis, sizeof(float) * n_axis, cudaMemcpyHostToDevice, st), "copy axis");
-    CF_STEP(cudaMemcpyAsync(d_off, hand->offset, sizeof(float) * n_axis, cudaMemcpyHostToDevice, st), "copy offset");
-    CF_STEP(cudaMemcpyAsync(d_surf, surf.data(), sizeof(float) * n_surf, cudaMemcpyHostToDevice, st), "copy surf");
-    CF_STEP(cudaMemcpyAsync(d_lb, lbeg.data(), sizeof(int) * lbeg.size(), cudaMemcpyHostToDevice, st), "copy links");
-    CF_STEP(cudaMemcpyAsync(d_bounds, binit.data(), sizeof(int) * binit.size(), cudaMemcpyHostToDevice, st),
-            "copy bounds");
-    fd->hand = HandDev{F, J, M, d_base, d_axis, d_off, d_surf, d_lb};
+    CF_STEP(cudaMemcpyAsync(fd->d_block, stage.data(), bytes, cudaMemcpyHostToDevice, st), "copy hand");
+    CF_STEP(cudaEventCreate(&fd->ev0), "event");
+    CF_STEP(cudaEventCreate(&fd->ev1), "event");
+    CF_STEP(cudaEventRecord(fd->ev0, st), "event record");
+    if (n_samples > 0) {
+        if ((rc = pool_alloc((void **)&d_links, sizeof(float) * 12 * (size_t)F * J * n_samples, st, "alloc links"))) {
+            field_release(fd);
+            return rc;
+        }
+        CF_STEP(launch_fk_cell_bounds(fd->hand, d_q, n_samples, fd->geom.inv_h, fd->geom.clamp, d_bounds, d_links, st),
+                "launch k_fk_cell_bounds");
+    }
+    std::vector<int> bnd(n_bnd);
+    CF_STEP(cudaMemcpyAsync(bnd.data(), d_bounds, sizeof(int) * n_bnd, cudaMemcpyDeviceToHost, st), "copy bounds");
+    CF_STEP(cudaStreamSynchronize(st), "k_fk_cell_bounds");  // the table's size depends on these bounds
 
-    cudaEvent_t ev0, ev1;
-    CF_STEP(cudaEventCreate(&ev0), "event");
-    CF_STEP(cudaEventCreate(&ev1), "event");
-    CF_STEP(cudaEventRecord(ev0, st), "event record");
-    CF_STEP(launch_fk_cell_bounds(fd->hand, d_q, n_samples, fd->geom.inv_h, fd->geom.clamp, d_bounds, st),
-            "launch k_fk_cell_bounds");
-    std::vector<int> bnd((size_t)6 * F);
-    CF_STEP(cudaMemcpyAsync(bnd.data(), d_bounds, sizeof(int) * bnd.size(), cudaMemcpyDeviceToHost, st), "copy bounds");
-    CF_STEP(cudaStreamSynchronize(st), "k_fk_cell_bounds");
-
-    int64_t words = 0;
+    // one box over all fingers' samples; per-finger tight bounds are kept for reporting
+    FieldGeom &g = fd->geom;
+    int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
     for (int f = 0; f < F; ++f) {
         const int *b = &bnd[6 * f];
         if (b[0] > b[3]) {  // finger without samples
-            for (int c = 0; c < 3; ++c) { fd->geom.lo[f][c] = 0; fd->geom.dims[f][c] = 0; }
-            fd->geom.off[f] = words;
+            for (int c = 0; c < 3; ++c) { g.flo[f][c] = 0; g.fdims[f][c] = 0; }
             continue;
         }
         for (int c = 0; c < 3; ++c) {
             if (b[c] <= -(1 << 20) || b[3 + c] >= (1 << 20)) {
-                cudaEventDestroy(ev0); cudaEventDestroy(ev1);
-                cudaFree(fd->d_block); delete fd;
+                if (d_links) cudaFreeAsync(d_links, st);
+                field_release(fd);
                 return fail(CF_EINVAL, "finger %d cells span [%d,%d] on axis %d: beyond |k| < 2^20 (voxel too small "
                                        "or hand too large)", f, b[c], b[3 + c], c);
             }
-            fd->geom.lo[f][c] = b[c];
-            fd->geom.dims[f][c] = b[3 + c] - b[c] + 1;
+            g.flo[f][c] = b[c];
+            g.fdims[f][c] = b[3 + c] - b[c] + 1;
+            lo[c] = std::min(lo[c], b[c]);
+            hi[c] = std::max(hi[c], b[3 + c]);
         }
-        fd->geom.off[f] = words;
-        words += (int64_t)fd->geom.dims[f][0] * fd->geom.dims[f][1] * fd->geom.dims[f][2];
-        words = (words + 31) & ~(int64_t)31;
+    }
+    g.bits = slot_bits_for(g.B);
+    g.fpw = 32 / g.bits;
+    g.rw = (F + g.fpw - 1) / g.fpw;
+    int64_t words = 0;
+    if (lo[0] <= hi[0]) {
+        for (int c = 0; c < 3; ++c) { g.lo[c] = lo[c]; g.dims[c] = hi[c] - lo[c] + 1; }
+        words = (int64_t)g.dims[0] * g.dims[1] * g.dims[2] * g.rw;
+    } else {
+        for (int c = 0; c < 3; ++c) { g.lo[c] = 0; g.dims[c] = 0; }
     }
     fd->table_words = words;
     if (words > 0) {
-        CF_STEP(cudaMalloc(&fd->d_table, sizeof(uint32_t) * (size_t)words), "cudaMalloc(table)");
+        if ((rc = pool_alloc((void **)&fd->d_table, sizeof(uint32_t) * (size_t)words, st, "alloc table"))) {
+            if (d_links) cudaFreeAsync(d_links, st);
+            field_release(fd);
+            return rc;
+        }
         CF_STEP(cudaMemsetAsync(fd->d_table, 0, sizeof(uint32_t) * (size_t)words, st), "memset table");
-        CF_STEP(launch_fk_bin(fd->hand, d_q, n_samples, fd->geom, fd->d_table, ds.status, st), "launch k_fk_bin");
+        CF_STEP(launch_fk_bin(fd->hand, d_links, n_samples, fd->geom, fd->d_table, ds.status, st), "launch k_fk_bin");
     }
-    CF_STEP(cudaEventRecord(ev1, st), "event record");
-    CF_STEP(cudaStreamSynchronize(st), "k_fk_bin");
-    cudaEventElapsedTime(&fd->build_ms, ev0, ev1);
-    cudaEventDestroy(ev0);
-    cudaEventDestroy(ev1);
+    if (d_links) CF_STEP(cudaFreeAsync(d_links, st), "free links");
+    CF_STEP(cudaEventRecord(fd->ev1, st), "event record");
 #undef CF_STEP
-    fd->device_bytes = (int64_t)bytes + (int64_t)sizeof(uint32_t) * words;
+    fd->device_bytes = (int64_t)bytes + (int64_t)sizeof(uint32_t) * (words + kCandCells);
     *out = fd;
     return CF_OK;
 }
@@ -258,16 +349,26 @@ extern "C" int cf_field_get_info(const cf_field *fd, cf_field_info *info) {
     info->n_bins = fd->B;
     info->n_samples = fd->S;
     info->inv_h = fd->geom.inv_h;
-    for (int f = 0; f < fd->F; ++f) {
-        for (int c = 0; c < 3; ++c) {
-            info->lo[f][c] = fd->geom.lo[f][c];
-            info->dims[f][c] = fd->geom.dims[f][c];
-        }
-        info->word_offset[f] = fd->geom.off[f];
+    for (int c = 0; c < 3; ++c) {
+        info->box_lo[c] = fd->geom.lo[c];
+        info->box_dims[c] = fd->geom.dims[c];
     }
+    info->bits_per_finger = fd->geom.bits;
+    info->fingers_per_word = fd->geom.fpw;
+    info->record_words = fd->geom.rw;
+    for (int f = 0; f < fd->F; ++f)
+        for (int c = 0; c < 3; ++c) {
+            info->finger_lo[f][c] = fd->geom.flo[f][c];
+            info->finger_dims[f][c] = fd->geom.fdims[f][c];
+        }
     info->table_words = fd->table_words;
     info->device_bytes = fd->device_bytes;
-    info->build_ms = fd->build_ms;
+    cf_field *mfd = const_cast<cf_field *>(fd);
+    if (mfd->build_ms < 0.f && mfd->ev1) {
+        CF_TRY(cudaEventSynchronize(mfd->ev1), "build event");
+        cudaEventElapsedTime(&mfd->build_ms, mfd->ev0, mfd->ev1);
+    }
+    info->build_ms = fd->build_ms < 0.f ? 0.f : fd->build_ms;
     return CF_OK;
 }
 
@@ -277,21 +378,19 @@ extern "C" int cf_field_copy_table(const cf_field *fd, uint32_t *host_words, int
         return fail(CF_EINVAL, "capacity %lld < table_words %lld", (long long)capacity_words,
                     (long long)fd->table_words);
     if (fd->table_words == 0) return CF_OK;
+    CF_TRY(cudaStreamSynchronize(fd->st), "field stream");
     CF_TRY(cudaMemcpy(host_words, fd->d_table, sizeof(uint32_t) * (size_t)fd->table_words, cudaMemcpyDeviceToHost),
            "copy table");
     return CF_OK;
 }
 
 extern "C" int cf_field_destroy(cf_field *fd) {
-    if (!fd) return CF_OK;
-    if (fd->d_block) cudaFree(fd->d_block);
-    if (fd->d_table) cudaFree(fd->d_table);
-    delete fd;
+    field_release(fd);
     return CF_OK;
 }
 
 namespace {
-const char kMagic[8] = {'C', 'F', 'F', 'I', 'E', 'L', 'D', '1'};
+const char kMagic[8] = {'C', 'F', 'F', 'I', 'E', 'L', 'D', '2'};
 }
 
 extern "C" int cf_field_save(const cf_field *fd, const char *path) {
@@ -328,15 +427,23 @@ extern "C" int cf_field_load(const char *path, cf_field **out) {
     cf_field *fd = new cf_field();
     fd->F = hdr[0]; fd->J = hdr[1]; fd->M = hdr[2]; fd->S = hdr[3]; fd->B = hdr[4];
     fd->geom = tmp.geom;
+    fd->geom.cand = nullptr;
     fd->table_words = tmp.table_words;
+    fd->st = nullptr;
+    fd->build_ms = 0.f;
     cudaGetDevice(&fd->dev);
+    if (int rc2 = setup_candidates(fd)) { field_release(fd); return rc2; }
     if (!tab.empty()) {
-        cudaError_t e = cudaMalloc(&fd->d_table, sizeof(uint32_t) * tab.size());
-        if (e != cudaSuccess) { delete fd; return cuda_fail(e, "cudaMalloc(table)"); }
-        e = cudaMemcpy(fd->d_table, tab.data(), sizeof(uint32_t) * tab.size(), cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) { cudaFree(fd->d_table); delete fd; return cuda_fail(e, "copy table"); }
+        if (int rc2 = pool_alloc((void **)&fd->d_table, sizeof(uint32_t) * tab.size(), nullptr, "alloc table")) {
+            field_release(fd);
+            return rc2;
+        }
+        cudaError_t e = cudaMemcpyAsync(fd->d_table, tab.data(), sizeof(uint32_t) * tab.size(), cudaMemcpyHostToDevice,
+                                        nullptr);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
+        if (e != cudaSuccess) { field_release(fd); return cuda_fail(e, "copy table"); }
     }
-    fd->device_bytes = (int64_t)sizeof(uint32_t) * fd->table_words;
+    fd->device_bytes = (int64_t)sizeof(uint32_t) * (fd->table_words + kCandCells);
     *out = fd;
     return CF_OK;
 }
@@ -446,7 +553,7 @@ extern "C" int cf_score_tuples(const cf_points *obj, int32_t n_fingers, const ui
     if (n_poses == 0) return CF_OK;
     cudaStream_t st = (cudaStream_t)stream;
     unsigned int *work = nullptr;
-    CF_TRY(cudaMallocAsync((void **)&work, sizeof(unsigned int), st), "cudaMallocAsync(work counter)");
+    if ((rc = pool_alloc((void **)&work, sizeof(unsigned int), st, "alloc work counter"))) return rc;
     cudaError_t e = cudaMemsetAsync(work, 0, sizeof(unsigned int), st);
     if (e == cudaSuccess) {
         a.work = work;

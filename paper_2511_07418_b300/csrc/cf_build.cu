@@ -9,11 +9,17 @@
 // set is a B-bit word: bit b is set iff some sample in the cell has normal bin
 // b (the fixed-direction normal index of Sec. 3.3 "Memory Consumption").
 //
+// The table is one box of cells over all fingers; a cell's record holds the
+// bin sets of all fingers (finger f: bits (f % fpw) * bits .. of word f / fpw).
+//
 // Thread per (finger, joint sample).  The kinematic chain is evaluated in FP64
 // and rounded to FP32 once per link; each surface point is then transformed
 // with single-rounding FP32 FMAs (component order x, y, z).  Two passes:
-// k_fk_cell_bounds (per-finger cell AABB -> table extents) and k_fk_bin
-// (atomicOr of the sample's bin into its cell word).
+// k_fk_cell_bounds evaluates the chain, stores the FP32 link frames
+// ([F][J][12][S], coalesced over samples) and reduces the per-finger cell AABB
+// (-> table extents); k_fk_bin reads the frames back and sets the sample's bin
+// in its cell word (atomicOr, skipped when the bit is already set).  Bins come
+// from the same cube-map candidate lists as the query when they are valid.
 #include <limits.h>
 
 #include "cf_internal.cuh"
@@ -76,7 +82,8 @@ __device__ __forceinline__ void stage_surface(const HandDev &h, int f, float *s_
 
 template <int J>
 __global__ void __launch_bounds__(kThreads) k_fk_cell_bounds(HandDev h, const float *__restrict__ q, int S,
-                                                             float inv_h, float clamp, int *bounds) {
+                                                             float inv_h, float clamp, int *bounds,
+                                                             float *__restrict__ links) {
     extern __shared__ float s_surf[];
     __shared__ int s_lb[CF_MAX_JOINTS + 1];
     const int f = blockIdx.y;
@@ -87,6 +94,14 @@ __global__ void __launch_bounds__(kThreads) k_fk_cell_bounds(HandDev h, const fl
     if (s < S) {
         float R[J][9], t[J][3];
         link_frames<J>(h, f, q, S, s, R, t);
+#pragma unroll
+        for (int l = 0; l < J; ++l) {
+            float *lk = links + ((size_t)(f * J + l) * 12) * S + s;
+#pragma unroll
+            for (int e = 0; e < 9; ++e) lk[(size_t)e * S] = R[l][e];
+#pragma unroll
+            for (int e = 0; e < 3; ++e) lk[(size_t)(9 + e) * S] = t[l][e];
+        }
 #pragma unroll
         for (int l = 0; l < J; ++l) {
             for (int m = s_lb[l]; m < s_lb[l + 1]; ++m) {
@@ -111,21 +126,36 @@ __global__ void __launch_bounds__(kThreads) k_fk_cell_bounds(HandDev h, const fl
     }
 }
 
-template <int J>
-__global__ void __launch_bounds__(kThreads) k_fk_bin(HandDev h, const float *__restrict__ q, int S, FieldGeom g,
+template <int J, bool CAND>
+__global__ void __launch_bounds__(kThreads) k_fk_bin(HandDev h, const float *__restrict__ links, int S, FieldGeom g,
                                                      uint32_t *table, unsigned int *status) {
     extern __shared__ float s_surf[];
     __shared__ int s_lb[CF_MAX_JOINTS + 1];
+    __shared__ float4 s_dir[CF_MAX_BINS];
+    __shared__ uint32_t s_cand[CAND ? kCandCells : 1];
     const int f = blockIdx.y;
     stage_surface(h, f, s_surf, s_lb);
+    if (CAND) {
+        for (int e = threadIdx.x; e < kCandCells; e += blockDim.x) s_cand[e] = __ldg(g.cand + e);
+        if (threadIdx.x < g.B)
+            s_dir[threadIdx.x] = make_float4(g.dirs[threadIdx.x][0], g.dirs[threadIdx.x][1], g.dirs[threadIdx.x][2], 0.f);
+    }
     __syncthreads();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
     float R[J][9], t[J][3];
-    link_frames<J>(h, f, q, S, s, R, t);
-    const int lx = g.lo[f][0], ly = g.lo[f][1], lz = g.lo[f][2];
-    const unsigned dx = (unsigned)g.dims[f][0], dy = (unsigned)g.dims[f][1], dz = (unsigned)g.dims[f][2];
-    uint32_t *tab = table + g.off[f];
+#pragma unroll
+    for (int l = 0; l < J; ++l) {
+        const float *lk = links + ((size_t)(f * J + l) * 12) * S + s;
+#pragma unroll
+        for (int e = 0; e < 9; ++e) R[l][e] = __ldg(lk + (size_t)e * S);
+#pragma unroll
+        for (int e = 0; e < 3; ++e) t[l][e] = __ldg(lk + (size_t)(9 + e) * S);
+    }
+    const int lx = g.lo[0], ly = g.lo[1], lz = g.lo[2];
+    const unsigned dx = (unsigned)g.dims[0], dy = (unsigned)g.dims[1], dz = (unsigned)g.dims[2];
+    uint32_t *tab = table + f / g.fpw;
+    const int shift = (f % g.fpw) * g.bits;
 #pragma unroll
     for (int l = 0; l < J; ++l) {
         for (int m = s_lb[l]; m < s_lb[l + 1]; ++m) {
@@ -137,10 +167,15 @@ __global__ void __launch_bounds__(kThreads) k_fk_bin(HandDev h, const float *__r
             const float ny = rot_row(R[l][3], R[l][4], R[l][5], sp[3], sp[4], sp[5]);
             const float nz = rot_row(R[l][6], R[l][7], R[l][8], sp[3], sp[4], sp[5]);
             int bin = 0;
-            float best = -INFINITY;
-            for (int b = 0; b < g.B; ++b) {
-                const float sc = __fmaf_rn(g.dirs[b][2], nz, __fmaf_rn(g.dirs[b][1], ny, __fmul_rn(g.dirs[b][0], nx)));
-                if (sc > best) { best = sc; bin = b; }
+            if (CAND) {
+                bin = bin_by_candidates(nx, ny, nz, s_cand, s_dir);
+            } else {
+                float best = -INFINITY;
+                for (int b = 0; b < g.B; ++b) {
+                    const float sc =
+                        __fmaf_rn(g.dirs[b][2], nz, __fmaf_rn(g.dirs[b][1], ny, __fmul_rn(g.dirs[b][0], nx)));
+                    if (sc > best) { best = sc; bin = b; }
+                }
             }
             const unsigned ux = (unsigned)(cell_floor(x, g.inv_h, g.clamp) - lx);
             const unsigned uy = (unsigned)(cell_floor(y, g.inv_h, g.clamp) - ly);
@@ -149,8 +184,8 @@ __global__ void __launch_bounds__(kThreads) k_fk_bin(HandDev h, const float *__r
                 atomicOr(status, 0x80000000u);
                 continue;
             }
-            uint32_t *word = tab + ((size_t)uz * dy + uy) * dx + ux;
-            const uint32_t bit = 1u << bin;
+            uint32_t *word = tab + (((size_t)uz * dy + uy) * dx + ux) * g.rw;
+            const uint32_t bit = 1u << (shift + bin);
             if (!(__ldcg(word) & bit)) atomicOr(word, bit);
         }
     }
@@ -172,20 +207,24 @@ __global__ void __launch_bounds__(kThreads) k_fk_bin(HandDev h, const float *__r
     }
 
 cudaError_t launch_fk_cell_bounds(const HandDev &h, const float *q, int S, float inv_h, float clamp, int *bounds,
-                                  cudaStream_t st) {
+                                  float *links, cudaStream_t st) {
     if (S <= 0) return cudaSuccess;
     const dim3 grid((S + kThreads - 1) / kThreads, h.F);
     const size_t smem = sizeof(float) * 8 * h.M;
-    CF_J_DISPATCH(h.J, (k_fk_cell_bounds<JJ><<<grid, kThreads, smem, st>>>(h, q, S, inv_h, clamp, bounds)));
+    CF_J_DISPATCH(h.J, (k_fk_cell_bounds<JJ><<<grid, kThreads, smem, st>>>(h, q, S, inv_h, clamp, bounds, links)));
     return cudaGetLastError();
 }
 
-cudaError_t launch_fk_bin(const HandDev &h, const float *q, int S, const FieldGeom &g, uint32_t *table,
+cudaError_t launch_fk_bin(const HandDev &h, const float *links, int S, const FieldGeom &g, uint32_t *table,
                           unsigned int *status, cudaStream_t st) {
     if (S <= 0) return cudaSuccess;
     const dim3 grid((S + kThreads - 1) / kThreads, h.F);
     const size_t smem = sizeof(float) * 8 * h.M;
-    CF_J_DISPATCH(h.J, (k_fk_bin<JJ><<<grid, kThreads, smem, st>>>(h, q, S, g, table, status)));
+    if (g.use_cand && g.B > 8) {
+        CF_J_DISPATCH(h.J, (k_fk_bin<JJ, true><<<grid, kThreads, smem, st>>>(h, links, S, g, table, status)));
+    } else {
+        CF_J_DISPATCH(h.J, (k_fk_bin<JJ, false><<<grid, kThreads, smem, st>>>(h, links, S, g, table, status)));
+    }
     return cudaGetLastError();
 }
 

@@ -25,16 +25,63 @@ struct HandDev {
     const int *link_begin; // [F][J + 1]
 };
 
-// Field geometry as the query kernel needs it (passed by value).
+// Normal-bin candidate table: a cube map of 6 faces x kCandG x kCandG cells
+// over the unit sphere.  Each cell lists, ascending, every bin that can be the
+// argmax for some direction in the cell (up to 4, 6 bits each, in bits 0..23;
+// the count in bits 24..26), so evaluating only the listed bins gives exactly
+// the full-scan result; a single listed bin needs no evaluation at all.
+constexpr int kCandG = 32;
+constexpr int kCandCells = 6 * kCandG * kCandG;
+
+// Field geometry as the kernels need it (passed by value).  The table is one
+// box of cells over all fingers; each cell owns a record of `rw` words and
+// finger f's bin set sits at bit (f % fpw) * bits of word f / fpw.
 struct FieldGeom {
     int F, B;
     float inv_h;
     float clamp;             // |x| is clamped to this before the cell floor
-    int lo[CF_MAX_FINGERS][3];
-    int dims[CF_MAX_FINGERS][3];
-    long long off[CF_MAX_FINGERS];
+    int lo[3];               // box: first cell
+    int dims[3];             // box: cells per axis
+    int bits, fpw, rw;       // bits per finger slot, slots per word, words per record
+    int flo[CF_MAX_FINGERS][3], fdims[CF_MAX_FINGERS][3];  // tight per-finger bounds (reported only)
     float dirs[CF_MAX_BINS][3];
+    int use_cand;            // 1: candidate table valid (every cell has <= 4 candidates)
+    const uint32_t *cand;    // device [kCandCells]
 };
+
+inline int slot_bits_for(int B) { return B <= 8 ? 8 : (B <= 16 ? 16 : 32); }
+
+// Host: fill the candidate table for the given directions; returns the largest
+// per-cell candidate count.
+int build_bin_candidates(const float *dirs, int B, uint32_t *table);
+
+// bin of m from the cube-map candidate list (exactly the full-scan argmax)
+__device__ __forceinline__ int bin_by_candidates(float mx, float my, float mz, const uint32_t *s_cand,
+                                                 const float4 *s_dir) {
+    const float ax = fabsf(mx), ay = fabsf(my), az = fabsf(mz);
+    const bool xmaj = ax >= ay && ax >= az;
+    const bool ymaj = !xmaj && ay >= az;
+    const int face = xmaj ? (mx < 0.f ? 1 : 0) : (ymaj ? (my < 0.f ? 3 : 2) : (mz < 0.f ? 5 : 4));
+    const float ma = xmaj ? my : mx;
+    const float mb = (xmaj || ymaj) ? mz : my;
+    const float inv = __frcp_rn(xmaj ? ax : (ymaj ? ay : az));
+    const int iu = min(max((int)__fmaf_rn(ma, inv * (0.5f * kCandG), 0.5f * kCandG), 0), kCandG - 1);
+    const int iv = min(max((int)__fmaf_rn(mb, inv * (0.5f * kCandG), 0.5f * kCandG), 0), kCandG - 1);
+    const uint32_t word = s_cand[(face * kCandG + iu) * kCandG + iv];
+    const int cnt = (int)(word >> 24);
+    int bin = (int)(word & 63u);
+    if (cnt > 1) {
+        float4 d = s_dir[bin];
+        float best = __fmaf_rn(d.z, mz, __fmaf_rn(d.y, my, __fmul_rn(d.x, mx)));
+        for (int c = 1; c < cnt; ++c) {
+            const int b = (int)((word >> (6 * c)) & 63u);
+            d = s_dir[b];
+            const float sc = __fmaf_rn(d.z, mz, __fmaf_rn(d.y, my, __fmul_rn(d.x, mx)));
+            if (sc > best) { best = sc; bin = b; }
+        }
+    }
+    return bin;
+}
 
 // ---------------------------------------------------------------------------
 // decision arithmetic (single-rounding FMAs, component order x, y, z)
@@ -76,8 +123,8 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 // launchers (return cudaError_t of the launch)
 // ---------------------------------------------------------------------------
 cudaError_t launch_fk_cell_bounds(const HandDev &h, const float *q, int S, float inv_h, float clamp,
-                                  int *bounds, cudaStream_t st);
-cudaError_t launch_fk_bin(const HandDev &h, const float *q, int S, const FieldGeom &g, uint32_t *table,
+                                  int *bounds, float *links, cudaStream_t st);
+cudaError_t launch_fk_bin(const HandDev &h, const float *links, int S, const FieldGeom &g, uint32_t *table,
                           unsigned int *status, cudaStream_t st);
 cudaError_t launch_query(const FieldGeom &g, const uint32_t *table, const cf_points &obj, const float *poses,
                          int P, uint32_t *masks, uint32_t *counts, cudaStream_t st);

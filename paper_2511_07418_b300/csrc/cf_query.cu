@@ -9,12 +9,17 @@
 // (R p_x + t, -(R n_x)); it hits finger f iff the finger's table has a word at
 // cell(R p_x + t) whose bit bin(-(R n_x)) is set.
 //
-// Launch: one block per QP consecutive poses; each warp walks the mask words
+// Launch: one block per 8 consecutive poses; each warp walks the mask words
 // of the object (32 points per word, one point per lane, held in registers),
-// and for each pose of the block transforms its point, bins the normal, looks
-// the cell up in every finger's table (L1/L2-resident, read-only path) and
-// ballots the hits into the F mask words of that (pose, word).  Counts are
-// accumulated per (pose, finger) in shared memory.
+// and for each pose of the block transforms its point, bins the normal, loads
+// the cell's record (the bin sets of all fingers, one vector load from the
+// L2-resident table) and ballots the hits into the F mask words of that
+// (pose, word).  Counts are accumulated per (pose, finger) in shared memory.
+//
+// Binning: with the candidate table (see cf_bincand.cu) the normal's cube-map
+// cell names at most 4 bins, evaluated in ascending order with the same FP32
+// dot products and first-maximum rule as a full scan over the B directions,
+// so the bin is identical to the full scan's.
 #include "cf_internal.cuh"
 
 namespace cf {
@@ -25,22 +30,51 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kPosesPerBlock = 8;
 
-template <int F, int BT>
+template <int RW>
+__device__ __forceinline__ void load_record(const uint32_t *__restrict__ r, uint32_t (&rec)[RW]) {
+    if (RW == 1) {
+        rec[0] = __ldg(r);
+    } else if (RW == 2) {
+        const uint2 v = __ldg(reinterpret_cast<const uint2 *>(r));
+        rec[0] = v.x;
+        rec[1 % RW] = v.y;
+    } else if (RW == 4) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(r));
+        rec[0] = v.x;
+        rec[1 % RW] = v.y;
+        rec[2 % RW] = v.z;
+        rec[3 % RW] = v.w;
+    } else {
+#pragma unroll
+        for (int i = 0; i < RW; ++i) rec[i] = __ldg(r + i);
+    }
+}
+
+template <int F, int BITS, bool CAND>
 __global__ void __launch_bounds__(kThreads) k_query_domains(FieldGeom g, const uint32_t *__restrict__ table,
                                                             cf_points obj, const float *__restrict__ poses, int P,
                                                             int W, uint32_t *__restrict__ masks,
                                                             uint32_t *__restrict__ counts) {
-    __shared__ float s_pose[kPosesPerBlock][12];
+    __shared__ __align__(16) float s_pose[kPosesPerBlock][12];
     __shared__ unsigned s_cnt[kPosesPerBlock][F];
+    __shared__ float4 s_dir[CF_MAX_BINS];
+    __shared__ uint32_t s_cand[CAND ? kCandCells : 1];
     const int i0 = blockIdx.x * kPosesPerBlock;
     const int np = min(kPosesPerBlock, P - i0);
     for (int e = threadIdx.x; e < np * 12; e += kThreads) s_pose[e / 12][e % 12] = poses[(size_t)i0 * 12 + e];
     for (int e = threadIdx.x; e < kPosesPerBlock * F; e += kThreads) s_cnt[e / F][e % F] = 0u;
+    if (CAND) {
+        for (int e = threadIdx.x; e < kCandCells; e += kThreads) s_cand[e] = __ldg(g.cand + e);
+        if (threadIdx.x < g.B) s_dir[threadIdx.x] = make_float4(g.dirs[threadIdx.x][0], g.dirs[threadIdx.x][1],
+                                                                g.dirs[threadIdx.x][2], 0.f);
+    }
     __syncthreads();
 
+    constexpr int FPW = 32 / BITS;
+    constexpr int RW = (F + FPW - 1) / FPW;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int N = obj.n;
-    const int B = BT > 0 ? BT : g.B;
+    const int B = g.B;
     for (int w = warp; w < W; w += kWarps) {
         const int x = 32 * w + lane;
         const bool valid = x < N;
@@ -49,38 +83,43 @@ __global__ void __launch_bounds__(kThreads) k_query_domains(FieldGeom g, const u
         const float nx = valid ? __ldg(obj.nx + x) : 0.f, ny = valid ? __ldg(obj.ny + x) : 0.f,
                     nz = valid ? __ldg(obj.nz + x) : 0.f;
         for (int pi = 0; pi < np; ++pi) {
-            const float *T = s_pose[pi];
-            const float qx = xf_row(T[0], T[1], T[2], T[3], px, py, pz);
-            const float qy = xf_row(T[4], T[5], T[6], T[7], px, py, pz);
-            const float qz = xf_row(T[8], T[9], T[10], T[11], px, py, pz);
+            const float4 T0 = reinterpret_cast<const float4 *>(s_pose[pi])[0];
+            const float4 T1 = reinterpret_cast<const float4 *>(s_pose[pi])[1];
+            const float4 T2 = reinterpret_cast<const float4 *>(s_pose[pi])[2];
+            const float qx = xf_row(T0.x, T0.y, T0.z, T0.w, px, py, pz);
+            const float qy = xf_row(T1.x, T1.y, T1.z, T1.w, px, py, pz);
+            const float qz = xf_row(T2.x, T2.y, T2.z, T2.w, px, py, pz);
             // contact-surface normal -(R n): exact negation of the rotated normal
-            const float mx = -rot_row(T[0], T[1], T[2], nx, ny, nz);
-            const float my = -rot_row(T[4], T[5], T[6], nx, ny, nz);
-            const float mz = -rot_row(T[8], T[9], T[10], nx, ny, nz);
+            const float mx = -rot_row(T0.x, T0.y, T0.z, nx, ny, nz);
+            const float my = -rot_row(T1.x, T1.y, T1.z, nx, ny, nz);
+            const float mz = -rot_row(T2.x, T2.y, T2.z, nx, ny, nz);
             int bin = 0;
-            float best = -INFINITY;
-#pragma unroll(BT > 0 ? BT : 4)
-            for (int b = 0; b < B; ++b) {
-                const float sc =
-                    __fmaf_rn(g.dirs[b][2], mz, __fmaf_rn(g.dirs[b][1], my, __fmul_rn(g.dirs[b][0], mx)));
-                if (sc > best) { best = sc; bin = b; }
+            if (CAND) {
+                bin = bin_by_candidates(mx, my, mz, s_cand, s_dir);
+            } else {
+                float best = -INFINITY;
+#pragma unroll 4
+                for (int b = 0; b < B; ++b) {
+                    const float sc =
+                        __fmaf_rn(g.dirs[b][2], mz, __fmaf_rn(g.dirs[b][1], my, __fmul_rn(g.dirs[b][0], mx)));
+                    if (sc > best) { best = sc; bin = b; }
+                }
             }
             const int kx = cell_floor(qx, g.inv_h, g.clamp);
             const int ky = cell_floor(qy, g.inv_h, g.clamp);
             const int kz = cell_floor(qz, g.inv_h, g.clamp);
+            const unsigned ux = (unsigned)(kx - g.lo[0]);
+            const unsigned uy = (unsigned)(ky - g.lo[1]);
+            const unsigned uz = (unsigned)(kz - g.lo[2]);
+            uint32_t rec[RW];
+#pragma unroll
+            for (int i = 0; i < RW; ++i) rec[i] = 0u;
+            if (valid && ux < (unsigned)g.dims[0] && uy < (unsigned)g.dims[1] && uz < (unsigned)g.dims[2])
+                load_record<RW>(table + (((size_t)uz * g.dims[1] + uy) * g.dims[0] + ux) * RW, rec);
             uint32_t mine = 0u;
 #pragma unroll
             for (int f = 0; f < F; ++f) {
-                const unsigned ux = (unsigned)(kx - g.lo[f][0]);
-                const unsigned uy = (unsigned)(ky - g.lo[f][1]);
-                const unsigned uz = (unsigned)(kz - g.lo[f][2]);
-                bool hit = false;
-                if (valid && ux < (unsigned)g.dims[f][0] && uy < (unsigned)g.dims[f][1] &&
-                    uz < (unsigned)g.dims[f][2]) {
-                    const uint32_t word =
-                        __ldg(table + g.off[f] + ((size_t)uz * g.dims[f][1] + uy) * g.dims[f][0] + ux);
-                    hit = (word >> bin) & 1u;
-                }
+                const bool hit = (rec[f / FPW] >> ((f % FPW) * BITS + bin)) & 1u;
                 const uint32_t bal = __ballot_sync(0xffffffffu, hit);
                 if (lane == f) mine = bal;
             }
@@ -94,18 +133,28 @@ __global__ void __launch_bounds__(kThreads) k_query_domains(FieldGeom g, const u
     for (int e = threadIdx.x; e < np * F; e += kThreads) counts[(size_t)(i0 + e / F) * F + e % F] = s_cnt[e / F][e % F];
 }
 
+template <int F, int BITS>
+cudaError_t launch_fb(const FieldGeom &g, const uint32_t *table, const cf_points &obj, const float *poses, int P,
+                      uint32_t *masks, uint32_t *counts, cudaStream_t st) {
+    const int W = (obj.n + 31) / 32;
+    const int grid = (P + kPosesPerBlock - 1) / kPosesPerBlock;
+    // a full scan of <= 8 bins costs no more than the candidate lookup
+    if (BITS > 8 && g.use_cand && g.B > 8)
+        k_query_domains<F, BITS, (BITS > 8)><<<grid, kThreads, 0, st>>>(g, table, obj, poses, P, W, masks, counts);
+    else
+        k_query_domains<F, BITS, false><<<grid, kThreads, 0, st>>>(g, table, obj, poses, P, W, masks, counts);
+    return cudaGetLastError();
+}
+
 template <int F>
 cudaError_t launch_f(const FieldGeom &g, const uint32_t *table, const cf_points &obj, const float *poses, int P,
                      uint32_t *masks, uint32_t *counts, cudaStream_t st) {
-    const int W = (obj.n + 31) / 32;
-    const int grid = (P + kPosesPerBlock - 1) / kPosesPerBlock;
-    switch (g.B) {
-        case 8: k_query_domains<F, 8><<<grid, kThreads, 0, st>>>(g, table, obj, poses, P, W, masks, counts); break;
-        case 16: k_query_domains<F, 16><<<grid, kThreads, 0, st>>>(g, table, obj, poses, P, W, masks, counts); break;
-        case 32: k_query_domains<F, 32><<<grid, kThreads, 0, st>>>(g, table, obj, poses, P, W, masks, counts); break;
-        default: k_query_domains<F, 0><<<grid, kThreads, 0, st>>>(g, table, obj, poses, P, W, masks, counts); break;
+    switch (g.bits) {
+        case 8: return launch_fb<F, 8>(g, table, obj, poses, P, masks, counts, st);
+        case 16: return launch_fb<F, 16>(g, table, obj, poses, P, masks, counts, st);
+        case 32: return launch_fb<F, 32>(g, table, obj, poses, P, masks, counts, st);
+        default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 }  // namespace

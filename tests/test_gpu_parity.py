@@ -49,18 +49,20 @@ def _gpu_path(cf, w, poses=None):
 
 
 def _table_codes(field, f):
+    """Finger f's (kx, ky, kz, bin) codes decoded from the record layout."""
     inf = field.info()
     tab = field.table()
-    lo = np.array(inf.lo[f], np.int64)
-    d = np.array(inf.dims[f], np.int64)
+    lo = np.array(inf.box_lo, np.int64)
+    d = np.array(inf.box_dims, np.int64)
     if d.prod() == 0:
         return np.zeros((0, 4), np.int64)
-    off = int(inf.word_offset[f])
-    words = tab[off:off + int(d.prod())].reshape(int(d[2]), int(d[1]), int(d[0]))
-    iz, iy, ix = np.nonzero(words)
+    rw, fpw, bits = int(inf.record_words), int(inf.fingers_per_word), int(inf.bits_per_finger)
+    words = tab.reshape(int(d[2]), int(d[1]), int(d[0]), rw)[..., f // fpw]
+    sh = np.uint32((f % fpw) * bits)
+    iz, iy, ix = np.nonzero((words >> sh) & np.uint32((1 << bits) - 1 if bits < 32 else 0xFFFFFFFF))
     out = []
     for b in range(int(inf.n_bins)):
-        sel = ((words[iz, iy, ix] >> np.uint32(b)) & np.uint32(1)).astype(bool)
+        sel = ((words[iz, iy, ix] >> (sh + np.uint32(b))) & np.uint32(1)).astype(bool)
         out.append(np.stack([ix[sel] + lo[0], iy[sel] + lo[1], iz[sel] + lo[2], np.full(sel.sum(), b)], axis=1))
     c = np.concatenate(out).astype(np.int64)
     return c[np.lexsort((c[:, 3], c[:, 2], c[:, 1], c[:, 0]))]
