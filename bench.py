@@ -114,6 +114,20 @@ def _dist():
     return world, rank, local
 
 
+def reduce_over_ranks(times_ms, accepted, device=None):
+    """Replica results -> job totals: the slowest rank's times (max) and the
+    accepted tuples of all ranks (sum).  No data crosses ranks during a step;
+    this runs once, after the timed region."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x) for x in times_ms], dtype=torch.float64, device=device)
+    a = torch.tensor([int(x) for x in accepted], dtype=torch.int64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(a, op=dist.ReduceOp.SUM)
+    return [float(x) for x in t.tolist()], [int(x) for x in a.tolist()]
+
+
 # ---------------------------------------------------------------------------
 # oracle leg (CPU baseline / reference arm)
 # ---------------------------------------------------------------------------
@@ -299,14 +313,7 @@ def run_ours(args):
     d2h = w.P * w.T * (4 * w.k + 4 + 1)
 
     # ---- reduce over ranks ------------------------------------------------
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms, e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        a = torch.tensor([accepted, e2e_acc], dtype=torch.int64, device=dev)
-        dist.all_reduce(a, op=dist.ReduceOp.SUM)
-        total_ms, e2e_s = float(t[0]), float(t[1])
-        accepted, e2e_acc = int(a[0]), int(a[1])
+    (total_ms, e2e_s), (accepted, e2e_acc) = reduce_over_ranks([total_ms, e2e_s], [accepted, e2e_acc], dev)
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()

@@ -188,14 +188,16 @@ struct LpWarp {
 // row's entry (mycol) back.
 __device__ __forceinline__ float publish_column(const LpWarp &s, int e, int lane, float *buf) {
     const bool slotB = e >= 32;
-    if (lane == (e & 31)) {
-        if (slotB) {
+    const bool owner = lane == (e & 31);
+    float v[14];
 #pragma unroll
-            for (int r = 0; r < 14; ++r) buf[r] = s.B[r];
-        } else {
-#pragma unroll
-            for (int r = 0; r < 14; ++r) buf[r] = s.A[r];
-        }
+    for (int r = 0; r < 14; ++r) v[r] = slotB ? s.B[r] : s.A[r];
+    if (owner) {  // predicated vector stores (no divergent path)
+        float4 *b4 = reinterpret_cast<float4 *>(buf);
+        b4[0] = make_float4(v[0], v[1], v[2], v[3]);
+        b4[1] = make_float4(v[4], v[5], v[6], v[7]);
+        b4[2] = make_float4(v[8], v[9], v[10], v[11]);
+        reinterpret_cast<float2 *>(buf)[6] = make_float2(v[12], v[13]);
     }
     __syncwarp();
     return lane < 14 ? buf[lane] : 0.f;
@@ -204,7 +206,7 @@ __device__ __forceinline__ float publish_column(const LpWarp &s, int e, int lane
 // Pivot on (row l, column e) once the column is published in buf.
 __device__ __forceinline__ void pivot(LpWarp &s, float mycol, int l, int e, int lane, const float *buf) {
     const float pe = __shfl_sync(kFull, mycol, l);
-    const float inv = __frcp_rn(pe);
+    const float inv = __fdividef(1.f, pe);  // fast reciprocal: pivot entries are >= kPTol in size
     float pa = 0.f, pb = 0.f;
     switch (l) {
 #define CF_GET(r) \
