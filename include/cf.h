@@ -222,6 +222,43 @@ int cf_sample_tuples(const cf_points *obj, int32_t n_fingers, const uint32_t *d_
                      int32_t n_poses, const cf_score_params *prm, int32_t *d_tuples, uint8_t *d_fingers,
                      cf_stream stream);
 
+/* ---- many objects in one graph launch ------------------------------------ */
+
+/* One object request of a batch: the same inputs and caller-owned outputs as
+ * cf_query_domains + cf_score_tuples (prm.tuples_given must be 0). */
+typedef struct cf_batch_item {
+    const cf_field *field;
+    cf_points obj;
+    const float *d_poses;
+    int32_t n_poses;
+    cf_score_params prm;
+    uint32_t *d_masks, *d_counts;
+    int32_t *d_tuples;
+    uint8_t *d_fingers;
+    float *d_margin;
+    uint8_t *d_accept;
+} cf_batch_item;
+
+typedef struct cf_batch cf_batch;
+
+/* Plan a batch of objects (fields may differ): items are grouped by kernel
+ * variant, and each group runs as ONE launch per step (domain query, tuple
+ * sampling, LP scoring), its blocks and tuples spread over the group's
+ * objects.  Results equal the per-object calls bit for bit.  The items'
+ * buffers are used in place by every run.  Errors: CF_EINVAL, CF_ENOMEM,
+ * CF_ECUDA. */
+int cf_batch_create(const cf_batch_item *items, int32_t n_items, cf_batch **out);
+
+/* Run the batch after the work already queued on `stream`.  The first run
+ * captures the launches into a CUDA graph; later runs replay it (one graph
+ * launch).  Asynchronous. */
+int cf_batch_run(cf_batch *batch, cf_stream stream);
+
+/* Number of kernel launches one run performs and the number of launch groups. */
+int cf_batch_launches(const cf_batch *batch, int32_t *n_launches, int32_t *n_groups);
+
+int cf_batch_destroy(cf_batch *batch);
+
 /* ---- one object request from host buffers -------------------------------- */
 
 typedef struct cf_plan cf_plan;

@@ -71,6 +71,12 @@ class ScoreParams(Structure):
                 ("centroid", c_float * 3), ("rho", c_float), ("seed", c_uint64), ("tuples_given", c_int32)]
 
 
+class BatchItem(Structure):
+    _fields_ = [("field", c_void_p), ("obj", Points), ("d_poses", c_void_p), ("n_poses", c_int32),
+                ("prm", ScoreParams), ("d_masks", c_void_p), ("d_counts", c_void_p), ("d_tuples", c_void_p),
+                ("d_fingers", c_void_p), ("d_margin", c_void_p), ("d_accept", c_void_p)]
+
+
 def _sig(name, args, res=c_int):
     f = getattr(_lib, name)
     f.argtypes = args
@@ -92,6 +98,10 @@ _cf_sample = _sig("cf_sample_tuples", [POINTER(Points), c_int32, c_void_p, c_voi
 _cf_score_noalloc = _sig("cf_score_tuples_noalloc", [POINTER(Points), c_int32, c_void_p, c_void_p, c_int32,
                                                      POINTER(ScoreParams), c_void_p, c_void_p, c_void_p, c_void_p,
                                                      c_void_p])
+_cf_batch_create = _sig("cf_batch_create", [POINTER(BatchItem), c_int32, POINTER(c_void_p)])
+_cf_batch_run = _sig("cf_batch_run", [c_void_p, c_void_p])
+_cf_batch_launches = _sig("cf_batch_launches", [c_void_p, POINTER(c_int32), POINTER(c_int32)])
+_cf_batch_destroy = _sig("cf_batch_destroy", [c_void_p])
 _cf_plan_create = _sig("cf_plan_create", [c_int32, c_int32, c_int32, POINTER(ScoreParams), POINTER(c_void_p)])
 _cf_plan_run_host = _sig("cf_plan_run_host", [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_int32,
                                               POINTER(ScoreParams), c_void_p, c_void_p, c_void_p, POINTER(c_int64),
@@ -104,7 +114,7 @@ _cf_device_counters = _sig("cf_device_counters", [POINTER(c_uint64), c_int])
 EXPORTED = ["cf_build", "cf_field_get_info", "cf_field_copy_table", "cf_field_destroy", "cf_field_save",
             "cf_field_load", "cf_query_domains", "cf_score_tuples", "cf_plan_create", "cf_plan_run_host",
             "cf_plan_destroy", "cf_last_error", "cf_device_status", "cf_device_counters", "cf_score_tuples_noalloc",
-            "cf_sample_tuples"]
+            "cf_sample_tuples", "cf_batch_create", "cf_batch_run", "cf_batch_launches", "cf_batch_destroy"]
 
 
 def _check(rc: int):
@@ -295,6 +305,65 @@ def score_tuples_noalloc(soa, n_fingers: int, masks, counts, prm: ScoreParams, t
                              fp, _dev(margin, torch.float32, "margin"), _dev(accept, torch.uint8, "accept"),
                              _stream(stream)))
     return tuples, fingers, margin, accept
+
+
+class Batch:
+    """cf_batch: many object requests run as one launch per kernel variant,
+    replayed as a CUDA graph.  ``items`` are dicts with keys field, soa, poses,
+    prm, masks, counts, tuples, fingers, margin, accept (CUDA tensors as in
+    query_domains / score_tuples)."""
+
+    def __init__(self, items):
+        import torch
+        arr = (BatchItem * len(items))()
+        self._keep = []
+        for j, it in enumerate(items):
+            obj = points_struct(it["soa"])
+            P = int(it["poses"].shape[0])
+            arr[j] = BatchItem(it["field"].handle, obj, _dev(it["poses"], torch.float32, "poses"), P, it["prm"],
+                               _dev(it["masks"], torch.int32, "masks"), _dev(it["counts"], torch.int32, "counts"),
+                               _dev(it["tuples"], torch.int32, "tuples"), _dev(it["fingers"], torch.uint8, "fingers"),
+                               _dev(it["margin"], torch.float32, "margin"), _dev(it["accept"], torch.uint8, "accept"))
+            self._keep.append(it)
+        h = c_void_p()
+        _check(_cf_batch_create(arr, len(items), byref(h)))
+        self._h = h
+
+    def run(self, stream=None):
+        _check(_cf_batch_run(self._h, _stream(stream)))
+
+    def launches(self):
+        n, g = c_int32(0), c_int32(0)
+        _check(_cf_batch_launches(self._h, byref(n), byref(g)))
+        return int(n.value), int(g.value)
+
+    def close(self):
+        if self._h:
+            _cf_batch_destroy(self._h)
+            self._h = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_item(field: Field, soa, poses, prm: ScoreParams):
+    """Allocate the outputs of one batch item (torch, on soa's device)."""
+    import torch
+    F = int(field.info().n_fingers)
+    P = int(poses.shape[0])
+    W = (int(soa.shape[1]) + 31) // 32
+    T, k = int(prm.n_tuples), int(prm.k)
+    dev = soa.device
+    return dict(field=field, soa=soa, poses=poses, prm=prm,
+                masks=torch.empty((P, F, W), dtype=torch.int32, device=dev),
+                counts=torch.empty((P, F), dtype=torch.int32, device=dev),
+                tuples=torch.empty((P, T, k), dtype=torch.int32, device=dev),
+                fingers=torch.empty((P, T, k), dtype=torch.uint8, device=dev),
+                margin=torch.empty((P, T), dtype=torch.float32, device=dev),
+                accept=torch.empty((P, T), dtype=torch.uint8, device=dev))
 
 
 class Plan:

@@ -629,6 +629,231 @@ extern "C" int cf_score_tuples_noalloc(const cf_points *obj, int32_t n_fingers, 
 }
 
 // ---------------------------------------------------------------------------
+// batch: many objects, one launch per kernel variant, replayed as a CUDA graph
+// ---------------------------------------------------------------------------
+struct cf_batch {
+    int dev = 0;
+    cudaStream_t st = nullptr;          // internal stream the graph runs on
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    void *d_block = nullptr;            // descriptors, prefix sums, work counters
+    struct QGroup { FieldGeom g0; QueryDesc *d_descs; int n; int blocks; };
+    struct SGroup { ScoreArgs launch; ScoreArgs *d_descs; long long *d_tuple0; int n; long long tuples; };
+    std::vector<QGroup> qgroups;
+    std::vector<SGroup> sgroups;
+    ScoreArgs *d_sdescs = nullptr;      // all items, for sampling
+    long long *d_pose0 = nullptr;
+    int n_items = 0;
+    long long total_poses = 0;
+    size_t sample_smem = 0;
+    std::vector<FieldGeom> geoms;
+    FieldGeom *d_geoms = nullptr;
+    int launches = 0;
+};
+
+extern "C" int cf_batch_create(const cf_batch_item *items, int32_t n_items, cf_batch **out) {
+    if (!items || !out || n_items < 1) return fail(CF_EINVAL, "items / out NULL or n_items < 1");
+    std::vector<ScoreArgs> sargs(n_items);
+    std::vector<int> geom_of(n_items);
+    cf_batch *b = new cf_batch();
+    CF_TRY(cudaGetDevice(&b->dev), "cudaGetDevice");
+    std::vector<const cf_field *> fields;
+    for (int i = 0; i < n_items; ++i) {
+        const cf_batch_item &it = items[i];
+        if (!it.field) { delete b; return fail(CF_EINVAL, "item %d: field is NULL", i); }
+        if (it.prm.tuples_given) { delete b; return fail(CF_EINVAL, "item %d: batches sample their own tuples", i); }
+        if (it.field->table_words == 0) { delete b; return fail(CF_EINVAL, "item %d: empty field", i); }
+        int rc = check_points(&it.obj);
+        if (!rc) rc = fill_score_args(&it.obj, it.field->F, it.d_masks, it.d_counts, it.n_poses, &it.prm, it.d_tuples,
+                                      it.d_fingers, it.d_margin, it.d_accept, &sargs[i]);
+        if (rc) { delete b; return fail(rc, "item %d: %s", i, t_err.c_str()); }
+        if (it.n_poses > 0 && (!it.d_poses || !it.d_counts || !it.d_masks)) {
+            delete b;
+            return fail(CF_EINVAL, "item %d: poses / masks / counts NULL", i);
+        }
+        int gi = -1;
+        for (size_t f = 0; f < fields.size(); ++f)
+            if (fields[f] == it.field) gi = (int)f;
+        if (gi < 0) {
+            gi = (int)fields.size();
+            fields.push_back(it.field);
+            b->geoms.push_back(it.field->geom);
+        }
+        geom_of[i] = gi;
+    }
+    // query groups: same F, bits and binning method
+    auto qkey = [&](int i) {
+        const FieldGeom &g = b->geoms[geom_of[i]];
+        const int cand = (g.bits > 8 && g.use_cand && g.B > 8) ? 1 : 0;
+        return g.F * 1000 + g.bits * 10 + cand;
+    };
+    std::vector<int> qkeys;
+    for (int i = 0; i < n_items; ++i)
+        if (std::find(qkeys.begin(), qkeys.end(), qkey(i)) == qkeys.end()) qkeys.push_back(qkey(i));
+    // score groups: same k and K (the LP lane layout)
+    std::vector<int> skeys;
+    for (int i = 0; i < n_items; ++i) {
+        const int key = sargs[i].k * 100 + sargs[i].K;
+        if (std::find(skeys.begin(), skeys.end(), key) == skeys.end()) skeys.push_back(key);
+    }
+    // host images of everything uploaded
+    std::vector<QueryDesc> qdesc_all;
+    std::vector<ScoreArgs> sdesc_all;
+    std::vector<long long> tuple0_all, pose0(n_items + 1, 0);
+    std::vector<size_t> q_off, s_off, t_off;
+    for (int key : qkeys) {
+        cf_batch::QGroup qg{};
+        q_off.push_back(qdesc_all.size());
+        int blocks = 0;
+        for (int i = 0; i < n_items; ++i) {
+            if (qkey(i) != key || items[i].n_poses == 0) continue;
+            QueryDesc d;
+            memset(&d, 0, sizeof d);
+            d.obj = items[i].obj;
+            d.poses = items[i].d_poses;
+            d.P = items[i].n_poses;
+            d.W = (items[i].obj.n + 31) / 32;
+            d.masks = items[i].d_masks;
+            d.counts = items[i].d_counts;
+            d.table = items[i].field->d_table;
+            d.geom = geom_of[i];
+            d.block0 = blocks;
+            blocks += query_blocks(d.P);
+            qdesc_all.push_back(d);
+            qg.g0 = b->geoms[geom_of[i]];
+        }
+        qg.n = (int)(qdesc_all.size() - q_off.back());
+        qg.blocks = blocks;
+        b->qgroups.push_back(qg);
+    }
+    size_t smem = 0;
+    for (int i = 0; i < n_items; ++i) {
+        pose0[i + 1] = pose0[i] + items[i].n_poses;
+        smem = std::max(smem, score_smem_bytes(sargs[i].F, sargs[i].W, sargs[i].T, sargs[i].k, true));
+    }
+    b->total_poses = pose0[n_items];
+    b->sample_smem = smem;
+    for (int key : skeys) {
+        cf_batch::SGroup sg{};
+        s_off.push_back(sdesc_all.size());
+        t_off.push_back(tuple0_all.size());
+        long long tuples = 0;
+        for (int i = 0; i < n_items; ++i) {
+            if (sargs[i].k * 100 + sargs[i].K != key) continue;
+            tuple0_all.push_back(tuples);
+            tuples += (long long)sargs[i].P * sargs[i].T;
+            sdesc_all.push_back(sargs[i]);
+            sg.launch = sargs[i];
+        }
+        tuple0_all.push_back(tuples);
+        sg.n = (int)(sdesc_all.size() - s_off.back());
+        sg.tuples = tuples;
+        if (tuples >= (1LL << 32)) { delete b; return fail(CF_EINVAL, "a score group holds >= 2^32 tuples"); }
+        b->sgroups.push_back(sg);
+    }
+    // one device block: geoms | query descs | score descs (grouped) | sample descs (all) | pose0 | tuple0 | counters
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t o_geom = 0, o_q = al(o_geom + sizeof(FieldGeom) * b->geoms.size());
+    const size_t o_s = al(o_q + sizeof(QueryDesc) * std::max<size_t>(1, qdesc_all.size()));
+    const size_t o_sa = al(o_s + sizeof(ScoreArgs) * sdesc_all.size());
+    const size_t o_p0 = al(o_sa + sizeof(ScoreArgs) * n_items);
+    const size_t o_t0 = al(o_p0 + sizeof(long long) * pose0.size());
+    const size_t o_w = al(o_t0 + sizeof(long long) * tuple0_all.size());
+    const size_t total = al(o_w + sizeof(unsigned int) * b->sgroups.size());
+    CF_TRY(cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking), "stream");
+    CF_TRY(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming), "event");
+    CF_TRY(cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming), "event");
+    int rc = pool_alloc(&b->d_block, total, b->st, "alloc batch");
+    if (rc) { cf_batch_destroy(b); return rc; }
+    char *base = (char *)b->d_block;
+    b->d_geoms = (FieldGeom *)(base + o_geom);
+    b->d_sdescs = (ScoreArgs *)(base + o_sa);
+    b->d_pose0 = (long long *)(base + o_p0);
+    unsigned int *d_work = (unsigned int *)(base + o_w);
+    for (size_t g = 0; g < b->qgroups.size(); ++g) b->qgroups[g].d_descs = (QueryDesc *)(base + o_q) + q_off[g];
+    for (size_t g = 0; g < b->sgroups.size(); ++g) {
+        b->sgroups[g].d_descs = (ScoreArgs *)(base + o_s) + s_off[g];
+        b->sgroups[g].d_tuple0 = (long long *)(base + o_t0) + t_off[g];
+        b->sgroups[g].launch.work = d_work + g;
+    }
+    std::vector<char> img(total, 0);
+    memcpy(img.data() + o_geom, b->geoms.data(), sizeof(FieldGeom) * b->geoms.size());
+    if (!qdesc_all.empty()) memcpy(img.data() + o_q, qdesc_all.data(), sizeof(QueryDesc) * qdesc_all.size());
+    memcpy(img.data() + o_s, sdesc_all.data(), sizeof(ScoreArgs) * sdesc_all.size());
+    memcpy(img.data() + o_sa, sargs.data(), sizeof(ScoreArgs) * n_items);
+    memcpy(img.data() + o_p0, pose0.data(), sizeof(long long) * pose0.size());
+    memcpy(img.data() + o_t0, tuple0_all.data(), sizeof(long long) * tuple0_all.size());
+    cudaError_t e = cudaMemcpyAsync(b->d_block, img.data(), total, cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+    if (e != cudaSuccess) { cf_batch_destroy(b); return cuda_fail(e, "upload batch"); }
+    b->n_items = n_items;
+    b->launches = (int)b->qgroups.size() + (b->total_poses > 0 ? 1 : 0) + (int)b->sgroups.size();
+    *out = b;
+    return CF_OK;
+}
+
+namespace {
+int batch_enqueue(cf_batch *b, cudaStream_t st) {
+    for (const auto &qg : b->qgroups)
+        CF_TRY(launch_query_batch(qg.g0, qg.d_descs, b->d_geoms, qg.n, qg.blocks, st), "batch query");
+    CF_TRY(launch_sample_batch(b->d_sdescs, b->d_pose0, b->n_items, b->total_poses, b->sample_smem, st),
+           "batch sample");
+    for (const auto &sg : b->sgroups) {
+        CF_TRY(cudaMemsetAsync(sg.launch.work, 0, sizeof(unsigned int), st), "batch work counter");
+        CF_TRY(launch_score_batch(sg.launch, sg.d_descs, sg.d_tuple0, sg.n, sg.tuples, st), "batch score");
+    }
+    return CF_OK;
+}
+}  // namespace
+
+extern "C" int cf_batch_run(cf_batch *b, cf_stream stream) {
+    if (!b) return fail(CF_EINVAL, "batch is NULL");
+    cudaStream_t caller = (cudaStream_t)stream;
+    CF_TRY(cudaEventRecord(b->ev_in, caller), "event record");
+    CF_TRY(cudaStreamWaitEvent(b->st, b->ev_in, 0), "stream wait");
+    if (!b->exec) {
+        cudaGraph_t graph = nullptr;
+        CF_TRY(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal), "begin capture");
+        const int rc = batch_enqueue(b, b->st);
+        const cudaError_t e = cudaStreamEndCapture(b->st, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "end capture");
+        const cudaError_t ei = cudaGraphInstantiate(&b->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) { b->exec = nullptr; return cuda_fail(ei, "graph instantiate"); }
+    }
+    CF_TRY(cudaGraphLaunch(b->exec, b->st), "graph launch");
+    CF_TRY(cudaEventRecord(b->ev_out, b->st), "event record");
+    CF_TRY(cudaStreamWaitEvent(caller, b->ev_out, 0), "stream wait");
+    return CF_OK;
+}
+
+extern "C" int cf_batch_launches(const cf_batch *b, int32_t *n_launches, int32_t *n_groups) {
+    if (!b) return fail(CF_EINVAL, "batch is NULL");
+    if (n_launches) *n_launches = b->launches;
+    if (n_groups) *n_groups = (int)(b->qgroups.size() + b->sgroups.size());
+    return CF_OK;
+}
+
+extern "C" int cf_batch_destroy(cf_batch *b) {
+    if (!b) return CF_OK;
+    if (b->st) cudaStreamSynchronize(b->st);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->d_block) cudaFreeAsync(b->d_block, b->st);
+    if (b->st) {
+        cudaStreamSynchronize(b->st);
+        cudaStreamDestroy(b->st);
+    }
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    delete b;
+    return CF_OK;
+}
+
+// ---------------------------------------------------------------------------
 // plan: one object request from host buffers
 // ---------------------------------------------------------------------------
 struct cf_plan {

@@ -129,6 +129,23 @@ cudaError_t launch_fk_bin(const HandDev &h, const float *links, int S, const Fie
 cudaError_t launch_query(const FieldGeom &g, const uint32_t *table, const cf_points &obj, const float *poses,
                          int P, uint32_t *masks, uint32_t *counts, cudaStream_t st);
 
+// One object's domain query (the plain call uses one by value; a batch keeps an
+// array of them in device memory, block0 = first grid block of the object).
+struct QueryDesc {
+    cf_points obj;
+    const float *poses;
+    int P, W;
+    uint32_t *masks, *counts;
+    const uint32_t *table;
+    int geom;     // index into the batch's FieldGeom array
+    int block0;   // first block of this object in the batch grid
+};
+
+// All objects of a batch group share F, bits and the binning method.
+cudaError_t launch_query_batch(const FieldGeom &g0, const QueryDesc *d_descs, const FieldGeom *d_geoms, int n_desc,
+                               int total_blocks, cudaStream_t st);
+int query_blocks(int P);  // grid blocks one object of P poses needs
+
 struct ScoreArgs {
     const float *px, *py, *pz, *nx, *ny, *nz;
     int N, W, F, P;
@@ -150,5 +167,12 @@ struct ScoreArgs {
 cudaError_t launch_score(const ScoreArgs &a, cudaStream_t st);
 // k_sample_tuples only
 cudaError_t launch_sample(const ScoreArgs &a, cudaStream_t st);
+// batches: pose0 / tuple0 = [n_desc + 1] prefix sums (device); the score launch's
+// work counter, status and counters come from `launch`, which also fixes k and K
+cudaError_t launch_sample_batch(const ScoreArgs *d_descs, const long long *d_pose0, int n_desc, long long total_poses,
+                                size_t smem, cudaStream_t st);
+cudaError_t launch_score_batch(const ScoreArgs &launch, const ScoreArgs *d_descs, const long long *d_tuple0, int n_desc,
+                               long long total_tuples, cudaStream_t st);
+size_t score_smem_bytes(int F, int W, int T, int k, bool sampling);
 
 }  // namespace cf

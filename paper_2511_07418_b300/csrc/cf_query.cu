@@ -20,6 +20,8 @@
 // cell names at most 4 bins, evaluated in ascending order with the same FP32
 // dot products and first-maximum rule as a full scan over the B directions,
 // so the bin is identical to the full scan's.
+#include <string.h>
+
 #include "cf_internal.cuh"
 
 namespace cf {
@@ -50,16 +52,49 @@ __device__ __forceinline__ void load_record(const uint32_t *__restrict__ r, uint
     }
 }
 
-template <int F, int BITS, bool CAND>
-__global__ void __launch_bounds__(kThreads) k_query_domains(FieldGeom g, const uint32_t *__restrict__ table,
-                                                            cf_points obj, const float *__restrict__ poses, int P,
-                                                            int W, uint32_t *__restrict__ masks,
-                                                            uint32_t *__restrict__ counts) {
+struct QueryArgs {
+    FieldGeom g;               // single object: geometry
+    QueryDesc one;             // single object: request
+    const QueryDesc *descs;    // batch: requests (device)
+    const FieldGeom *geoms;    // batch: geometries (device)
+    int n_desc;
+};
+
+// MULTI: the block's object is found from the descriptors (blocks of object d
+// are [descs[d].block0, descs[d + 1].block0)); its request and field geometry
+// are copied to shared memory.
+template <int F, int BITS, bool CAND, bool MULTI>
+__global__ void __launch_bounds__(kThreads) k_query_domains(const QueryArgs a) {
     __shared__ __align__(16) float s_pose[kPosesPerBlock][12];
     __shared__ unsigned s_cnt[kPosesPerBlock][F];
     __shared__ float4 s_dir[CF_MAX_BINS];
     __shared__ uint32_t s_cand[CAND ? kCandCells : 1];
-    const int i0 = blockIdx.x * kPosesPerBlock;
+    __shared__ FieldGeom s_geom;
+    __shared__ QueryDesc s_desc;
+    if (MULTI) {
+        if (threadIdx.x == 0) {
+            int lo = 0, hi = a.n_desc - 1;  // last descriptor with block0 <= blockIdx.x
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (a.descs[mid].block0 <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+            }
+            s_desc = a.descs[lo];
+        }
+        __syncthreads();
+        const int *src = reinterpret_cast<const int *>(a.geoms + s_desc.geom);
+        int *dst = reinterpret_cast<int *>(&s_geom);
+        for (int e = threadIdx.x; e < (int)(sizeof(FieldGeom) / sizeof(int)); e += kThreads) dst[e] = src[e];
+        __syncthreads();
+    }
+    const FieldGeom &g = MULTI ? s_geom : a.g;
+    const QueryDesc &D = MULTI ? s_desc : a.one;
+    const cf_points &obj = D.obj;
+    const float *__restrict__ poses = D.poses;
+    const int P = D.P, W = D.W;
+    uint32_t *__restrict__ masks = D.masks;
+    uint32_t *__restrict__ counts = D.counts;
+    const uint32_t *__restrict__ table = D.table;
+    const int i0 = ((int)blockIdx.x - (MULTI ? D.block0 : 0)) * kPosesPerBlock;
     const int np = min(kPosesPerBlock, P - i0);
     for (int e = threadIdx.x; e < np * 12; e += kThreads) s_pose[e / 12][e % 12] = poses[(size_t)i0 * 12 + e];
     for (int e = threadIdx.x; e < kPosesPerBlock * F; e += kThreads) s_cnt[e / F][e % F] = 0u;
@@ -133,46 +168,62 @@ __global__ void __launch_bounds__(kThreads) k_query_domains(FieldGeom g, const u
     for (int e = threadIdx.x; e < np * F; e += kThreads) counts[(size_t)(i0 + e / F) * F + e % F] = s_cnt[e / F][e % F];
 }
 
-template <int F, int BITS>
-cudaError_t launch_fb(const FieldGeom &g, const uint32_t *table, const cf_points &obj, const float *poses, int P,
-                      uint32_t *masks, uint32_t *counts, cudaStream_t st) {
-    const int W = (obj.n + 31) / 32;
-    const int grid = (P + kPosesPerBlock - 1) / kPosesPerBlock;
+template <int F, int BITS, bool MULTI>
+cudaError_t launch_fb(const QueryArgs &a, const FieldGeom &g, int grid, cudaStream_t st) {
     // a full scan of <= 8 bins costs no more than the candidate lookup
     if (BITS > 8 && g.use_cand && g.B > 8)
-        k_query_domains<F, BITS, (BITS > 8)><<<grid, kThreads, 0, st>>>(g, table, obj, poses, P, W, masks, counts);
+        k_query_domains<F, BITS, (BITS > 8), MULTI><<<grid, kThreads, 0, st>>>(a);
     else
-        k_query_domains<F, BITS, false><<<grid, kThreads, 0, st>>>(g, table, obj, poses, P, W, masks, counts);
+        k_query_domains<F, BITS, false, MULTI><<<grid, kThreads, 0, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int F>
-cudaError_t launch_f(const FieldGeom &g, const uint32_t *table, const cf_points &obj, const float *poses, int P,
-                     uint32_t *masks, uint32_t *counts, cudaStream_t st) {
-    switch (g.bits) {
-        case 8: return launch_fb<F, 8>(g, table, obj, poses, P, masks, counts, st);
-        case 16: return launch_fb<F, 16>(g, table, obj, poses, P, masks, counts, st);
-        case 32: return launch_fb<F, 32>(g, table, obj, poses, P, masks, counts, st);
+template <bool MULTI>
+cudaError_t launch_any(const QueryArgs &a, const FieldGeom &g, int grid, cudaStream_t st) {
+#define CF_QF(FF)                                                          \
+    case FF:                                                               \
+        switch (g.bits) {                                                  \
+            case 8: return launch_fb<FF, 8, MULTI>(a, g, grid, st);       \
+            case 16: return launch_fb<FF, 16, MULTI>(a, g, grid, st);     \
+            case 32: return launch_fb<FF, 32, MULTI>(a, g, grid, st);     \
+            default: return cudaErrorInvalidValue;                         \
+        }
+    switch (g.F) {
+        CF_QF(1) CF_QF(2) CF_QF(3) CF_QF(4) CF_QF(5) CF_QF(6) CF_QF(7) CF_QF(8)
         default: return cudaErrorInvalidValue;
     }
+#undef CF_QF
 }
 
 }  // namespace
 
+int query_blocks(int P) { return (P + kPosesPerBlock - 1) / kPosesPerBlock; }
+
 cudaError_t launch_query(const FieldGeom &g, const uint32_t *table, const cf_points &obj, const float *poses, int P,
                          uint32_t *masks, uint32_t *counts, cudaStream_t st) {
     if (P <= 0) return cudaSuccess;
-    switch (g.F) {
-        case 1: return launch_f<1>(g, table, obj, poses, P, masks, counts, st);
-        case 2: return launch_f<2>(g, table, obj, poses, P, masks, counts, st);
-        case 3: return launch_f<3>(g, table, obj, poses, P, masks, counts, st);
-        case 4: return launch_f<4>(g, table, obj, poses, P, masks, counts, st);
-        case 5: return launch_f<5>(g, table, obj, poses, P, masks, counts, st);
-        case 6: return launch_f<6>(g, table, obj, poses, P, masks, counts, st);
-        case 7: return launch_f<7>(g, table, obj, poses, P, masks, counts, st);
-        case 8: return launch_f<8>(g, table, obj, poses, P, masks, counts, st);
-        default: return cudaErrorInvalidValue;
-    }
+    QueryArgs a;
+    memset(&a, 0, sizeof a);
+    a.g = g;
+    a.one.obj = obj;
+    a.one.poses = poses;
+    a.one.P = P;
+    a.one.W = (obj.n + 31) / 32;
+    a.one.masks = masks;
+    a.one.counts = counts;
+    a.one.table = table;
+    return launch_any<false>(a, g, query_blocks(P), st);
+}
+
+cudaError_t launch_query_batch(const FieldGeom &g0, const QueryDesc *d_descs, const FieldGeom *d_geoms, int n_desc,
+                               int total_blocks, cudaStream_t st) {
+    if (total_blocks <= 0) return cudaSuccess;
+    QueryArgs a;
+    memset(&a, 0, sizeof a);
+    a.descs = d_descs;
+    a.geoms = d_geoms;
+    a.n_desc = n_desc;
+    return launch_any<true>(a, g0, total_blocks, st);
 }
 
 }  // namespace cf

@@ -29,6 +29,8 @@
 // degenerate pivots.  FP32 throughout.
 #include <limits.h>
 
+#include <string.h>
+
 #include <algorithm>
 
 #include "cf_internal.cuh"
@@ -91,14 +93,33 @@ __device__ __forceinline__ uint32_t draw_word(const uint4 &a, const uint4 &b, in
     }
 }
 
-__global__ void __launch_bounds__(kSampleThreads) k_sample_tuples(ScoreArgs a) {
+// MULTI: block b samples pose b - pose0[d] of object d, pose0 = first block of
+// each object (ascending); the object's arguments are copied to shared memory.
+template <bool MULTI>
+__global__ void __launch_bounds__(kSampleThreads) k_sample_tuples(const ScoreArgs a1, const ScoreArgs *descs,
+                                                                  const long long *pose0, int n_desc) {
     extern __shared__ uint32_t s_dyn[];
     __shared__ uint32_t s_cnt[CF_MAX_FINGERS];
+    __shared__ ScoreArgs s_args;
+    __shared__ int s_i;
+    if (MULTI) {
+        if (threadIdx.x == 0) {
+            int lo = 0, hi = n_desc - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (pose0[mid] <= (long long)blockIdx.x) lo = mid; else hi = mid - 1;
+            }
+            s_args = descs[lo];
+            s_i = (int)((long long)blockIdx.x - pose0[lo]);
+        }
+        __syncthreads();
+    }
+    const ScoreArgs &a = MULTI ? s_args : a1;
     const int F = a.F, W = a.W, T = a.T, k = a.k;
     const int G = (W + 31) / 32;
     uint32_t *s_mask = s_dyn;           // [F][W]
     uint32_t *s_gpre = s_mask + F * W;  // [F][G + 1]
-    const int i = blockIdx.x;
+    const int i = MULTI ? s_i : (int)blockIdx.x;
     if (threadIdx.x < F) s_cnt[threadIdx.x] = a.counts[(size_t)i * F + threadIdx.x];
     const uint32_t *src = a.masks + (size_t)i * F * W;
     for (int e = threadIdx.x; e < F * W; e += blockDim.x) s_mask[e] = src[e];
@@ -330,31 +351,55 @@ __device__ float solve_lp(const float (&w)[6], bool colA, int ci, int j, int lan
     return fmaxf(z, 0.f);
 }
 
-__global__ void __launch_bounds__(kScoreThreads, 3) k_score_tuples(ScoreArgs a) {
+// MULTI: global tuple u belongs to object d with tuple0[d] <= u < tuple0[d + 1]
+// (all objects of one launch share k and K); each warp keeps its current
+// object's arguments in shared memory.
+template <bool MULTI>
+__global__ void __launch_bounds__(kScoreThreads, 3) k_score_tuples(const ScoreArgs a1, const ScoreArgs *descs,
+                                                                    const long long *tuple0, int n_desc,
+                                                                    unsigned total) {
     __shared__ __align__(16) float s_buf[kScoreWarps][16];
-    __shared__ float s_cs[CF_MAX_EDGES], s_sn[CF_MAX_EDGES];
-    if (threadIdx.x < CF_MAX_EDGES) {
-        s_cs[threadIdx.x] = a.cs[threadIdx.x] * a.mu;
-        s_sn[threadIdx.x] = a.sn[threadIdx.x] * a.mu;
-    }
-    __syncthreads();
+    __shared__ ScoreArgs s_obj[MULTI ? kScoreWarps : 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int k = a.k, K = a.K, kK = k * K;
+    const int k = a1.k, K = a1.K, kK = k * K;
     const bool colA = lane < kK;
     const int ci = colA ? lane / K : 0, cm = colA ? lane % K : 0;
-    const float ec = s_cs[cm], es = s_sn[cm];
+    float ec = a1.cs[cm] * a1.mu, es = a1.sn[cm] * a1.mu;
     float *buf = s_buf[warp];
-    const unsigned total = (unsigned)a.P * (unsigned)a.T;
+    int cur = -1;
+    long long cur0 = 0, cur1 = 0;
     unsigned long long n_piv = 0, n_lp = 0, n_tup = 0;
     unsigned flags = 0;
 
     for (;;) {
         unsigned u0 = 0;
-        if (lane == 0) u0 = atomicAdd(a.work, (unsigned)kTupleBatch);
+        if (lane == 0) u0 = atomicAdd(a1.work, (unsigned)kTupleBatch);
         u0 = __shfl_sync(kFull, u0, 0);
         if (u0 >= total) break;
         const unsigned uend = min(u0 + (unsigned)kTupleBatch, total);
-        for (unsigned u = u0; u < uend; ++u) {
+        for (unsigned ug = u0; ug < uend; ++ug) {
+            unsigned u = ug;
+            if (MULTI) {
+                if ((long long)ug < cur0 || (long long)ug >= cur1) {  // switch object
+                    int lo = 0, hi = n_desc - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (__ldg(tuple0 + mid) <= (long long)ug) lo = mid; else hi = mid - 1;
+                    }
+                    cur = lo;
+                    cur0 = __ldg(tuple0 + lo);
+                    cur1 = __ldg(tuple0 + lo + 1);
+                    __syncwarp();
+                    const int *src = reinterpret_cast<const int *>(descs + cur);
+                    int *dst = reinterpret_cast<int *>(&s_obj[warp]);
+                    for (int e = lane; e < (int)(sizeof(ScoreArgs) / sizeof(int)); e += 32) dst[e] = src[e];
+                    __syncwarp();
+                    ec = s_obj[warp].cs[cm] * s_obj[warp].mu;
+                    es = s_obj[warp].sn[cm] * s_obj[warp].mu;
+                }
+                u = (unsigned)((long long)ug - cur0);
+            }
+            const ScoreArgs &a = MULTI ? s_obj[warp] : a1;
             const int32_t *st = a.tuples + (size_t)u * k;
             bool valid = true;
             for (int d = 0; d < k; ++d) {
@@ -398,10 +443,10 @@ __global__ void __launch_bounds__(kScoreThreads, 3) k_score_tuples(ScoreArgs a) 
         }
     }
     if (lane == 0) {
-        atomicAdd(a.counters + 0, n_piv);
-        atomicAdd(a.counters + 1, n_lp);
-        atomicAdd(a.counters + 2, n_tup);
-        if (flags) atomicOr(a.status, flags);
+        atomicAdd(a1.counters + 0, n_piv);
+        atomicAdd(a1.counters + 1, n_lp);
+        atomicAdd(a1.counters + 2, n_tup);
+        if (flags) atomicOr(a1.status, flags);
     }
 }
 
@@ -418,28 +463,58 @@ cudaError_t launch_sample(const ScoreArgs &a, cudaStream_t st) {
     if (a.P <= 0) return cudaSuccess;
     const size_t smem = score_smem_bytes(a.F, a.W, a.T, a.k, true);
     if (smem > 48 * 1024) {
-        cudaError_t err = cudaFuncSetAttribute(k_sample_tuples, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t err =
+            cudaFuncSetAttribute(k_sample_tuples<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
     }
-    k_sample_tuples<<<a.P, kSampleThreads, smem, st>>>(a);
+    k_sample_tuples<false><<<a.P, kSampleThreads, smem, st>>>(a, nullptr, nullptr, 0);
     return cudaGetLastError();
 }
+
+namespace {
+template <bool MULTI>
+cudaError_t launch_score_grid(const ScoreArgs &a1, const ScoreArgs *descs, const long long *tuple0, int n_desc,
+                              long long total, cudaStream_t st) {
+    cudaError_t err;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
+    if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
+    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_score_tuples<MULTI>, kScoreThreads, 0)) !=
+        cudaSuccess)
+        return err;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const long long warps_needed = (total + kTupleBatch - 1) / kTupleBatch;
+    const int grid = (int)std::min<long long>((long long)sms * per_sm, (warps_needed + kScoreWarps - 1) / kScoreWarps);
+    k_score_tuples<MULTI><<<grid, kScoreThreads, 0, st>>>(a1, descs, tuple0, n_desc, (unsigned)total);
+    return cudaGetLastError();
+}
+}  // namespace
 
 cudaError_t launch_score(const ScoreArgs &a, cudaStream_t st) {
     if (a.P <= 0) return cudaSuccess;
     cudaError_t err;
     if (!a.tuples_given && (err = launch_sample(a, st)) != cudaSuccess) return err;
-    int dev = 0, sms = 0, per_sm = 0;
-    if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
-    if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
-    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_score_tuples, kScoreThreads, 0)) != cudaSuccess)
-        return err;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const long long tuples = (long long)a.P * a.T;
-    const long long warps_needed = (tuples + kTupleBatch - 1) / kTupleBatch;
-    const int grid = (int)std::min<long long>((long long)sms * per_sm, (warps_needed + kScoreWarps - 1) / kScoreWarps);
-    k_score_tuples<<<grid, kScoreThreads, 0, st>>>(a);
+    return launch_score_grid<false>(a, nullptr, nullptr, 0, (long long)a.P * a.T, st);
+}
+
+cudaError_t launch_sample_batch(const ScoreArgs *d_descs, const long long *d_pose0, int n_desc, long long total_poses,
+                                size_t smem, cudaStream_t st) {
+    if (total_poses <= 0) return cudaSuccess;
+    if (smem > 48 * 1024) {
+        cudaError_t err =
+            cudaFuncSetAttribute(k_sample_tuples<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+    }
+    ScoreArgs dummy;
+    memset(&dummy, 0, sizeof dummy);
+    k_sample_tuples<true><<<(unsigned)total_poses, kSampleThreads, smem, st>>>(dummy, d_descs, d_pose0, n_desc);
     return cudaGetLastError();
+}
+
+cudaError_t launch_score_batch(const ScoreArgs &launch, const ScoreArgs *d_descs, const long long *d_tuple0, int n_desc,
+                               long long total_tuples, cudaStream_t st) {
+    if (total_tuples <= 0) return cudaSuccess;
+    return launch_score_grid<true>(launch, d_descs, d_tuple0, n_desc, total_tuples, st);
 }
 
 }  // namespace cf

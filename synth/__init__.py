@@ -28,7 +28,7 @@ __all__ = [
     "Hand", "Obj", "Workload",
     "fibonacci_dirs", "hand_three_finger", "hand_anthropomorphic",
     "joint_samples", "sphere", "superquadric", "tool_composite",
-    "palm_poses", "workload", "WORKLOADS",
+    "palm_poses", "workload", "WORKLOADS", "batch_objects", "batch_object_inputs",
 ]
 
 # ---------------------------------------------------------------------------
@@ -533,6 +533,31 @@ def _make_obj(kind: str, N: int, seed: int) -> Obj:
     if kind == "tool":
         return tool_composite(N, seed)
     raise ValueError(kind)
+
+
+def batch_objects(n: int, seed: int = 0, n_range=(2048, 131072), p_range=(4096, 32768),
+                  scale: float = 1.0):
+    """The many-object batch: n objects, half superquadrics and half tool
+    composites, point counts and pose counts log-uniform in the given ranges
+    (times ``scale``), each with a hand drawn uniformly from the three hands.
+    Returns a list of dicts (kind, hand key, N, P, obj seed, pose seed)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for o in range(n):
+        lo, hi = np.log(n_range[0] * scale), np.log(n_range[1] * scale)
+        N = int(max(32, round(np.exp(rng.uniform(lo, hi)))))
+        P = int(max(8, round(np.exp(rng.uniform(np.log(p_range[0] * scale), np.log(p_range[1] * scale))))))
+        hand = ["tiny_sphere", "hand16_superquadric", "hand20_tool"][int(rng.integers(3))]
+        out.append(dict(kind="superquadric" if o % 2 == 0 else "tool", hand=hand, N=N, P=P,
+                        obj_seed=1000 + o, pose_seed=seed * 7919 + o))
+    return out
+
+
+def batch_object_inputs(spec: dict, hand: Hand):
+    """(Obj, poses) of one batch object."""
+    obj = superquadric(spec["N"], spec["obj_seed"]) if spec["kind"] == "superquadric" else \
+        tool_composite(spec["N"], spec["obj_seed"])
+    return obj, palm_poses(spec["P"], spec["pose_seed"], hand.grasp_centre, obj.centroid)
 
 
 def workload(name: str, *, P: int | None = None, N: int | None = None, S: int | None = None,
