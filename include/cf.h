@@ -259,6 +259,80 @@ int cf_batch_launches(const cf_batch *batch, int32_t *n_launches, int32_t *n_gro
 
 int cf_batch_destroy(cf_batch *batch);
 
+/* ---- served form: continuous batching over arriving requests -------------- */
+
+typedef struct cf_engine cf_engine;
+
+typedef struct cf_engine_params {
+    const cf_field *const *fields;  /* resident hand fields (not owned; must outlive the engine) */
+    int32_t n_fields;
+    int64_t hbm_budget_bytes;       /* device memory the active requests may hold together */
+    int32_t max_active;             /* requests processed concurrently (slots) */
+    int32_t pose_chunk;             /* poses of each active request per round */
+    int32_t pose_cap;               /* poses a request may use before it ends with a partial result */
+} cf_engine_params;
+
+typedef struct cf_request {
+    int32_t field;                  /* index into cf_engine_params.fields */
+    const float *h_soa;             /* host [6][n] object points + outward normals (copied by submit) */
+    int32_t n;
+    const float *h_poses;           /* host [n_poses][12] candidate palm poses, used in order (copied) */
+    int32_t n_poses;
+    cf_score_params prm;            /* T, k, K, mu, eps, centroid, rho, seed (tuples_given = 0) */
+    int32_t n_grasps;               /* the request ends once this many tuples are accepted */
+    uint64_t tag;                   /* caller's label, returned with the result */
+} cf_request;
+
+typedef struct cf_result {
+    uint64_t id, tag;
+    int32_t status;                 /* CF_OK or the error that ended the request */
+    int32_t partial;                /* 1: the pose cap (or the pose list) ran out first */
+    int32_t k;
+    int32_t n_accepted;             /* accepted tuples (all of the last round's chunk, may exceed n_grasps) */
+    int32_t n_poses_used;
+    double t_submit, t_admit, t_done;  /* seconds on the engine's clock */
+    int32_t *pose;                  /* [n_accepted] pose index of each accepted tuple */
+    int32_t *tuples;                /* [n_accepted][k] object point ids */
+    float *margin;                  /* [n_accepted] closure margins */
+} cf_result;
+
+typedef struct cf_engine_stats {
+    int64_t submitted, completed, rounds, launches;
+    int32_t queued, active;
+    int64_t bytes_in_use, peak_bytes_in_use;
+    int32_t peak_active;
+} cf_engine_stats;
+
+/* Start an engine: a worker thread on the current device admits queued
+ * requests in arrival order while a slot is free and their device state fits
+ * in the HBM budget, then runs rounds: every active request contributes its
+ * next pose_chunk poses, and all of them go through the grouped query,
+ * sampling and scoring launches together.  Requests that arrive while others
+ * are on the GPU join at the next round.  Tuple draws are keyed by the
+ * request's seed and global pose index, so a request's result does not depend
+ * on what it shares rounds with.  Errors: CF_EINVAL, CF_ENOMEM, CF_ECUDA. */
+int cf_engine_create(const cf_engine_params *prm, cf_engine **out);
+
+/* Queue a request (copies its host arrays); never blocks on the GPU.  A
+ * request whose device state alone exceeds the budget completes at once with
+ * status CF_ENOMEM. */
+int cf_engine_submit(cf_engine *eng, const cf_request *req, uint64_t *id);
+
+/* Take up to max finished requests (non-blocking); free each with
+ * cf_engine_result_free. */
+int cf_engine_poll(cf_engine *eng, cf_result *out, int32_t max, int32_t *n_done);
+
+int cf_engine_result_free(cf_result *res);
+
+int cf_engine_get_stats(const cf_engine *eng, cf_engine_stats *out);
+
+/* Wait (up to timeout_ms; < 0: no limit) until nothing is queued or active.
+ * Returns CF_ETIMEOUT if work remains. */
+int cf_engine_drain(cf_engine *eng, int32_t timeout_ms);
+
+/* Stops the worker after the current round; unfinished requests are dropped. */
+int cf_engine_destroy(cf_engine *eng);
+
 /* ---- one object request from host buffers -------------------------------- */
 
 typedef struct cf_plan cf_plan;

@@ -15,8 +15,8 @@ from __future__ import annotations
 
 import ctypes
 import os
-from ctypes import POINTER, Structure, byref, c_char_p, c_float, c_int, c_int32, c_int64, c_uint8, c_uint32, \
-    c_uint64, c_void_p
+from ctypes import POINTER, Structure, byref, c_char_p, c_double, c_float, c_int, c_int32, c_int64, c_uint8, \
+    c_uint32, c_uint64, c_void_p
 
 import numpy as np
 
@@ -77,6 +77,29 @@ class BatchItem(Structure):
                 ("d_fingers", c_void_p), ("d_margin", c_void_p), ("d_accept", c_void_p)]
 
 
+class EngineParams(Structure):
+    _fields_ = [("fields", POINTER(c_void_p)), ("n_fields", c_int32), ("hbm_budget_bytes", c_int64),
+                ("max_active", c_int32), ("pose_chunk", c_int32), ("pose_cap", c_int32)]
+
+
+class Request(Structure):
+    _fields_ = [("field", c_int32), ("h_soa", c_void_p), ("n", c_int32), ("h_poses", c_void_p), ("n_poses", c_int32),
+                ("prm", ScoreParams), ("n_grasps", c_int32), ("tag", c_uint64)]
+
+
+class Result(Structure):
+    _fields_ = [("id", c_uint64), ("tag", c_uint64), ("status", c_int32), ("partial", c_int32), ("k", c_int32),
+                ("n_accepted", c_int32), ("n_poses_used", c_int32), ("t_submit", c_double), ("t_admit", c_double),
+                ("t_done", c_double), ("pose", POINTER(c_int32)), ("tuples", POINTER(c_int32)),
+                ("margin", POINTER(c_float))]
+
+
+class EngineStats(Structure):
+    _fields_ = [("submitted", c_int64), ("completed", c_int64), ("rounds", c_int64), ("launches", c_int64),
+                ("queued", c_int32), ("active", c_int32), ("bytes_in_use", c_int64), ("peak_bytes_in_use", c_int64),
+                ("peak_active", c_int32)]
+
+
 def _sig(name, args, res=c_int):
     f = getattr(_lib, name)
     f.argtypes = args
@@ -102,6 +125,13 @@ _cf_batch_create = _sig("cf_batch_create", [POINTER(BatchItem), c_int32, POINTER
 _cf_batch_run = _sig("cf_batch_run", [c_void_p, c_void_p])
 _cf_batch_launches = _sig("cf_batch_launches", [c_void_p, POINTER(c_int32), POINTER(c_int32)])
 _cf_batch_destroy = _sig("cf_batch_destroy", [c_void_p])
+_cf_engine_create = _sig("cf_engine_create", [POINTER(EngineParams), POINTER(c_void_p)])
+_cf_engine_submit = _sig("cf_engine_submit", [c_void_p, POINTER(Request), POINTER(c_uint64)])
+_cf_engine_poll = _sig("cf_engine_poll", [c_void_p, POINTER(Result), c_int32, POINTER(c_int32)])
+_cf_engine_result_free = _sig("cf_engine_result_free", [POINTER(Result)])
+_cf_engine_get_stats = _sig("cf_engine_get_stats", [c_void_p, POINTER(EngineStats)])
+_cf_engine_drain = _sig("cf_engine_drain", [c_void_p, c_int32])
+_cf_engine_destroy = _sig("cf_engine_destroy", [c_void_p])
 _cf_plan_create = _sig("cf_plan_create", [c_int32, c_int32, c_int32, POINTER(ScoreParams), POINTER(c_void_p)])
 _cf_plan_run_host = _sig("cf_plan_run_host", [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_int32,
                                               POINTER(ScoreParams), c_void_p, c_void_p, c_void_p, POINTER(c_int64),
@@ -114,7 +144,9 @@ _cf_device_counters = _sig("cf_device_counters", [POINTER(c_uint64), c_int])
 EXPORTED = ["cf_build", "cf_field_get_info", "cf_field_copy_table", "cf_field_destroy", "cf_field_save",
             "cf_field_load", "cf_query_domains", "cf_score_tuples", "cf_plan_create", "cf_plan_run_host",
             "cf_plan_destroy", "cf_last_error", "cf_device_status", "cf_device_counters", "cf_score_tuples_noalloc",
-            "cf_sample_tuples", "cf_batch_create", "cf_batch_run", "cf_batch_launches", "cf_batch_destroy"]
+            "cf_sample_tuples", "cf_batch_create", "cf_batch_run", "cf_batch_launches", "cf_batch_destroy",
+            "cf_engine_create", "cf_engine_submit", "cf_engine_poll", "cf_engine_result_free", "cf_engine_get_stats",
+            "cf_engine_drain", "cf_engine_destroy"]
 
 
 def _check(rc: int):
@@ -364,6 +396,69 @@ def batch_item(field: Field, soa, poses, prm: ScoreParams):
                 fingers=torch.empty((P, T, k), dtype=torch.uint8, device=dev),
                 margin=torch.empty((P, T), dtype=torch.float32, device=dev),
                 accept=torch.empty((P, T), dtype=torch.uint8, device=dev))
+
+
+class Engine:
+    """cf_engine: the served form (continuous batching over arriving requests).
+    Results come back as dicts with the accepted tuples copied to numpy."""
+
+    def __init__(self, fields, hbm_budget_bytes=64 << 30, max_active=64, pose_chunk=256, pose_cap=65536):
+        self.fields = list(fields)
+        arr = (c_void_p * len(self.fields))(*[f.handle.value for f in self.fields])
+        self._arr = arr
+        p = EngineParams(arr, len(self.fields), int(hbm_budget_bytes), int(max_active), int(pose_chunk),
+                         int(pose_cap))
+        h = c_void_p()
+        _check(_cf_engine_create(byref(p), byref(h)))
+        self._h = h
+
+    def submit(self, field: int, h_soa: np.ndarray, h_poses: np.ndarray, prm: ScoreParams, n_grasps: int,
+               tag: int = 0) -> int:
+        soa = _np(h_soa, np.float32)
+        poses = _np(h_poses, np.float32).reshape(-1, 12)
+        q = Request(int(field), c_void_p(soa.ctypes.data), int(soa.shape[1]), c_void_p(poses.ctypes.data),
+                    int(poses.shape[0]), prm, int(n_grasps), int(tag))
+        rid = c_uint64(0)
+        _check(_cf_engine_submit(self._h, byref(q), byref(rid)))
+        return int(rid.value)
+
+    def poll(self, max_results: int = 256):
+        buf = (Result * max_results)()
+        n = c_int32(0)
+        _check(_cf_engine_poll(self._h, buf, max_results, byref(n)))
+        out = []
+        for i in range(n.value):
+            r = buf[i]
+            na, k = int(r.n_accepted), int(r.k)
+            d = dict(id=int(r.id), tag=int(r.tag), status=int(r.status), partial=bool(r.partial),
+                     n_accepted=na, n_poses_used=int(r.n_poses_used), t_submit=r.t_submit, t_admit=r.t_admit,
+                     t_done=r.t_done,
+                     pose=np.ctypeslib.as_array(r.pose, (na,)).copy() if na else np.zeros(0, np.int32),
+                     tuples=np.ctypeslib.as_array(r.tuples, (na * k,)).reshape(na, k).copy() if na
+                     else np.zeros((0, k), np.int32),
+                     margin=np.ctypeslib.as_array(r.margin, (na,)).copy() if na else np.zeros(0, np.float32))
+            _cf_engine_result_free(byref(buf[i]))
+            out.append(d)
+        return out
+
+    def stats(self) -> dict:
+        s = EngineStats()
+        _check(_cf_engine_get_stats(self._h, byref(s)))
+        return {f: getattr(s, f) for f, _ in EngineStats._fields_}
+
+    def drain(self, timeout_ms: int = -1):
+        _check(_cf_engine_drain(self._h, int(timeout_ms)))
+
+    def close(self):
+        if self._h:
+            _cf_engine_destroy(self._h)
+            self._h = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Plan:

@@ -13,16 +13,12 @@
 
 #include "cf_internal.cuh"
 
-namespace cf {
-size_t score_smem_bytes(int F, int W, int T, int k, bool sampling);
-}
-
 using namespace cf;
 
 // ---------------------------------------------------------------------------
 // errors
 // ---------------------------------------------------------------------------
-namespace {
+namespace cf {
 
 thread_local std::string t_err;
 
@@ -41,11 +37,6 @@ int cuda_fail(cudaError_t e, const char *what) {
                 cudaGetErrorString(e));
 }
 
-#define CF_TRY(call, what)                       \
-    do {                                         \
-        cudaError_t e_ = (call);                 \
-        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
-    } while (0)
 
 // ---------------------------------------------------------------------------
 // device status word and counters (one copy per device that loads libcf)
@@ -75,14 +66,14 @@ int device_state(DevState *out) {
     return CF_OK;
 }
 
-}  // namespace
+}  // namespace cf
 
 // ---------------------------------------------------------------------------
 // device memory: one stream-ordered pool per device, owned by the library
 // (allocations and frees are ordered on the caller's stream; the pool keeps
 // freed memory for reuse instead of returning it to the driver)
 // ---------------------------------------------------------------------------
-namespace {
+namespace cf {
 
 std::mutex g_pool_mu;
 cudaMemPool_t g_pool[64] = {};
@@ -135,25 +126,11 @@ const CandEntry *cached_candidates(const float *dirs, int B) {
     return c;
 }
 
-}  // namespace
+}  // namespace cf
 
 // ---------------------------------------------------------------------------
 // field
 // ---------------------------------------------------------------------------
-struct cf_field {
-    int dev = 0;
-    cudaStream_t st = nullptr;  // device memory is freed on this stream
-    int F = 0, J = 0, M = 0, S = 0, B = 0;
-    FieldGeom geom{};
-    HandDev hand{};
-    void *d_block = nullptr;     // hand arrays + bounds scratch
-    uint32_t *d_table = nullptr;
-    uint32_t *d_cand = nullptr;  // normal-bin candidate table
-    int64_t table_words = 0;
-    int64_t device_bytes = 0;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    float build_ms = -1.f;
-};
 
 namespace {
 
@@ -451,7 +428,7 @@ extern "C" int cf_field_load(const char *path, cf_field **out) {
 // ---------------------------------------------------------------------------
 // query
 // ---------------------------------------------------------------------------
-namespace {
+namespace cf {
 int check_points(const cf_points *obj) {
     if (!obj) return fail(CF_EINVAL, "obj is NULL");
     if (obj->n < 0) return fail(CF_EINVAL, "obj->n < 0");
@@ -459,7 +436,7 @@ int check_points(const cf_points *obj) {
         return fail(CF_EINVAL, "obj array pointer is NULL");
     return CF_OK;
 }
-}  // namespace
+}  // namespace cf
 
 extern "C" int cf_query_domains(const cf_field *fd, const cf_points *obj, const float *d_poses, int32_t n_poses,
                                 uint32_t *d_masks, uint32_t *d_counts, cf_stream stream) {
@@ -485,7 +462,7 @@ extern "C" int cf_query_domains(const cf_field *fd, const cf_points *obj, const 
 // ---------------------------------------------------------------------------
 // sampling + scoring
 // ---------------------------------------------------------------------------
-namespace {
+namespace cf {
 
 int fill_score_args(const cf_points *obj, int32_t F, const uint32_t *d_masks, const uint32_t *d_counts, int32_t P,
                     const cf_score_params *prm, int32_t *d_tuples, uint8_t *d_fingers, float *d_margin,
@@ -540,7 +517,7 @@ int fill_score_args(const cf_points *obj, int32_t F, const uint32_t *d_masks, co
     return CF_OK;
 }
 
-}  // namespace
+}  // namespace cf
 
 extern "C" int cf_score_tuples(const cf_points *obj, int32_t n_fingers, const uint32_t *d_masks,
                                const uint32_t *d_counts, int32_t n_poses, const cf_score_params *prm,

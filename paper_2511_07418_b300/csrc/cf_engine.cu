@@ -1,0 +1,493 @@
+// Served form: a request engine with continuous batching.
+//
+// A worker thread owns a stream on the engine's device.  Requests are queued
+// by cf_engine_submit (their host arrays copied).  Each loop iteration:
+//   1. admission: queued requests are admitted in arrival order while a slot
+//      is free and their device state (points, poses, one chunk of domains,
+//      tuples and margins) fits in the HBM budget;
+//   2. a round: every active request takes its next pose chunk; all chunks go
+//      through one launch per query group (same finger count, slot bits and
+//      binning method), one sampling launch and one launch per score group
+//      (same k, K), exactly as a cf_batch does;
+//   3. results: the chunk's tuples, margins and accept flags come back; the
+//      accepted ones are appended to the request; a request that reached its
+//      grasp count or ran out of poses completes, frees its device state and
+//      its slot, and the next round admits whoever is waiting.
+// Tuple draws use the request's seed and the GLOBAL pose index (pose_base), so
+// a request's result is independent of the rounds it shares.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "cf_internal.cuh"
+
+using namespace cf;
+
+namespace {
+
+struct EngReq {
+    uint64_t id = 0;
+    cf_request req{};
+    const cf_field *fd = nullptr;
+    std::vector<float> soa, poses;
+    int limit = 0;  // poses this request may use
+    // device state
+    void *d_block = nullptr;
+    size_t bytes = 0;
+    float *d_soa = nullptr, *d_poses = nullptr, *d_margin = nullptr;
+    uint32_t *d_masks = nullptr, *d_counts = nullptr;
+    int32_t *d_tuples = nullptr;
+    uint8_t *d_fingers = nullptr, *d_accept = nullptr;
+    // progress
+    int pose_next = 0, chunk = 0;
+    std::vector<int32_t> h_tuples;
+    std::vector<float> h_margin;
+    std::vector<uint8_t> h_accept;
+    std::vector<int32_t> res_pose, res_tuples;
+    std::vector<float> res_margin;
+    double t_submit = 0, t_admit = 0;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+size_t state_bytes(const cf_request &r, int F, int chunk) {
+    const size_t W = (size_t)(r.n + 31) / 32, T = r.prm.n_tuples, k = r.prm.k;
+    return align256(sizeof(float) * 6 * r.n) + align256(sizeof(float) * 12 * (size_t)r.n_poses) +
+           align256(sizeof(uint32_t) * chunk * F * W) + align256(sizeof(uint32_t) * chunk * F) +
+           align256(sizeof(int32_t) * chunk * T * k) + align256(chunk * T * k) + align256(sizeof(float) * chunk * T) +
+           align256(chunk * T);
+}
+
+}  // namespace
+
+struct cf_engine {
+    cf_engine_params prm{};
+    std::vector<const cf_field *> fields;
+    std::vector<FieldGeom> geoms;
+    int dev = 0;
+    cudaStream_t st = nullptr;
+    std::thread worker;
+    std::mutex mu;
+    std::condition_variable cv, cv_idle;
+    bool stop = false;
+    std::deque<EngReq *> queue;
+    std::vector<EngReq *> active;
+    std::deque<cf_result> done;
+    uint64_t next_id = 1;
+    cf_engine_stats stats{};
+    std::chrono::steady_clock::time_point t0;
+    // round scratch (device): geoms | query descs | score descs | all descs | prefixes | counters
+    void *d_round = nullptr;
+    size_t round_bytes = 0;
+    std::string worker_error;
+
+    double now() const {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+};
+
+namespace {
+
+void finish(cf_engine *e, EngReq *r, int status, bool partial) {
+    cf_result res;
+    memset(&res, 0, sizeof res);
+    res.id = r->id;
+    res.tag = r->req.tag;
+    res.status = status;
+    res.partial = partial ? 1 : 0;
+    res.k = r->req.prm.k;
+    res.n_accepted = (int32_t)r->res_margin.size();
+    res.n_poses_used = r->pose_next;
+    res.t_submit = r->t_submit;
+    res.t_admit = r->t_admit;
+    res.t_done = e->now();
+    if (res.n_accepted > 0) {
+        res.pose = (int32_t *)malloc(sizeof(int32_t) * res.n_accepted);
+        res.tuples = (int32_t *)malloc(sizeof(int32_t) * res.n_accepted * res.k);
+        res.margin = (float *)malloc(sizeof(float) * res.n_accepted);
+        memcpy(res.pose, r->res_pose.data(), sizeof(int32_t) * res.n_accepted);
+        memcpy(res.tuples, r->res_tuples.data(), sizeof(int32_t) * res.n_accepted * res.k);
+        memcpy(res.margin, r->res_margin.data(), sizeof(float) * res.n_accepted);
+    }
+    if (r->d_block) cudaFreeAsync(r->d_block, e->st);
+    std::lock_guard<std::mutex> lk(e->mu);
+    if (r->d_block) e->stats.bytes_in_use -= (int64_t)r->bytes;
+    e->done.push_back(res);
+    e->stats.completed++;
+    delete r;
+}
+
+// Allocate a request's device state and upload its points and poses.
+int admit_one(cf_engine *e, EngReq *r) {
+    const int F = r->fd->F;
+    const cf_request &q = r->req;
+    int rc = pool_alloc(&r->d_block, r->bytes, e->st, "alloc request");
+    if (rc) return rc;
+    char *p = (char *)r->d_block;
+    const size_t W = (size_t)(q.n + 31) / 32, T = q.prm.n_tuples, k = q.prm.k, c = (size_t)e->prm.pose_chunk;
+    r->d_soa = (float *)p; p += align256(sizeof(float) * 6 * q.n);
+    r->d_poses = (float *)p; p += align256(sizeof(float) * 12 * (size_t)q.n_poses);
+    r->d_masks = (uint32_t *)p; p += align256(sizeof(uint32_t) * c * F * W);
+    r->d_counts = (uint32_t *)p; p += align256(sizeof(uint32_t) * c * F);
+    r->d_tuples = (int32_t *)p; p += align256(sizeof(int32_t) * c * T * k);
+    r->d_fingers = (uint8_t *)p; p += align256(c * T * k);
+    r->d_margin = (float *)p; p += align256(sizeof(float) * c * T);
+    r->d_accept = (uint8_t *)p;
+    if (q.n > 0) CF_TRY(cudaMemcpyAsync(r->d_soa, r->soa.data(), sizeof(float) * 6 * q.n, cudaMemcpyHostToDevice, e->st),
+                        "upload points");
+    if (q.n_poses > 0)
+        CF_TRY(cudaMemcpyAsync(r->d_poses, r->poses.data(), sizeof(float) * 12 * (size_t)q.n_poses,
+                               cudaMemcpyHostToDevice, e->st), "upload poses");
+    r->h_tuples.resize(c * T * k);
+    r->h_margin.resize(c * T);
+    r->h_accept.resize(c * T);
+    return CF_OK;
+}
+
+// One round over the active requests.  Returns CF_OK or an error code.
+int run_round(cf_engine *e, std::vector<EngReq *> &act) {
+    const int n = (int)act.size();
+    std::vector<ScoreArgs> sargs(n);
+    std::vector<cf_points> objs(n);
+    for (int i = 0; i < n; ++i) {
+        EngReq *r = act[i];
+        const cf_request &q = r->req;
+        r->chunk = std::min(e->prm.pose_chunk, r->limit - r->pose_next);
+        objs[i] = cf_points{r->d_soa, r->d_soa + q.n, r->d_soa + 2 * q.n, r->d_soa + 3 * q.n, r->d_soa + 4 * q.n,
+                            r->d_soa + 5 * q.n, q.n};
+        int rc = fill_score_args(&objs[i], r->fd->F, r->d_masks, r->d_counts, r->chunk, &q.prm, r->d_tuples,
+                                 r->d_fingers, r->d_margin, r->d_accept, &sargs[i]);
+        if (rc) return rc;
+        sargs[i].pose_base = (uint32_t)r->pose_next;
+    }
+    auto geom_of = [&](int i) {
+        for (size_t f = 0; f < e->fields.size(); ++f)
+            if (e->fields[f] == act[i]->fd) return (int)f;
+        return 0;
+    };
+    auto qkey = [&](int i) {
+        const FieldGeom &g = e->geoms[geom_of(i)];
+        return g.F * 1000 + g.bits * 10 + ((g.bits > 8 && g.use_cand && g.B > 8) ? 1 : 0);
+    };
+    std::vector<int> qkeys, skeys;
+    for (int i = 0; i < n; ++i) {
+        if (std::find(qkeys.begin(), qkeys.end(), qkey(i)) == qkeys.end()) qkeys.push_back(qkey(i));
+        const int sk = sargs[i].k * 100 + sargs[i].K;
+        if (std::find(skeys.begin(), skeys.end(), sk) == skeys.end()) skeys.push_back(sk);
+    }
+    std::vector<QueryDesc> qd;
+    std::vector<int> q_off, q_n, q_blocks, q_geom;
+    for (int key : qkeys) {
+        q_off.push_back((int)qd.size());
+        int blocks = 0, g0 = 0;
+        for (int i = 0; i < n; ++i) {
+            if (qkey(i) != key) continue;
+            QueryDesc d;
+            memset(&d, 0, sizeof d);
+            d.obj = objs[i];
+            d.poses = act[i]->d_poses + 12 * (size_t)act[i]->pose_next;
+            d.P = act[i]->chunk;
+            d.W = (objs[i].n + 31) / 32;
+            d.masks = act[i]->d_masks;
+            d.counts = act[i]->d_counts;
+            d.table = act[i]->fd->d_table;
+            d.geom = geom_of(i);
+            d.block0 = blocks;
+            blocks += query_blocks(d.P);
+            g0 = d.geom;
+            qd.push_back(d);
+        }
+        q_n.push_back((int)qd.size() - q_off.back());
+        q_blocks.push_back(blocks);
+        q_geom.push_back(g0);
+    }
+    std::vector<ScoreArgs> sd;
+    std::vector<long long> t0, pose0(n + 1, 0);
+    std::vector<int> s_off, t_off, s_n;
+    std::vector<long long> s_tuples;
+    size_t smem = 0;
+    for (int i = 0; i < n; ++i) {
+        pose0[i + 1] = pose0[i] + act[i]->chunk;
+        smem = std::max(smem, score_smem_bytes(sargs[i].F, sargs[i].W, sargs[i].T, sargs[i].k, true));
+    }
+    for (int key : skeys) {
+        s_off.push_back((int)sd.size());
+        t_off.push_back((int)t0.size());
+        long long tuples = 0;
+        for (int i = 0; i < n; ++i) {
+            if (sargs[i].k * 100 + sargs[i].K != key) continue;
+            t0.push_back(tuples);
+            tuples += (long long)sargs[i].P * sargs[i].T;
+            sd.push_back(sargs[i]);
+        }
+        t0.push_back(tuples);
+        s_n.push_back((int)sd.size() - s_off.back());
+        s_tuples.push_back(tuples);
+    }
+    // upload descriptors
+    const size_t o_g = 0, o_q = align256(sizeof(FieldGeom) * e->geoms.size());
+    const size_t o_s = align256(o_q + sizeof(QueryDesc) * qd.size());
+    const size_t o_a = align256(o_s + sizeof(ScoreArgs) * sd.size());
+    const size_t o_p = align256(o_a + sizeof(ScoreArgs) * n);
+    const size_t o_t = align256(o_p + sizeof(long long) * pose0.size());
+    const size_t o_w = align256(o_t + sizeof(long long) * t0.size());
+    const size_t total = align256(o_w + sizeof(unsigned int) * skeys.size());
+    if (total > e->round_bytes) {
+        if (e->d_round) cudaFreeAsync(e->d_round, e->st);
+        e->d_round = nullptr;
+        int rc = pool_alloc(&e->d_round, 2 * total, e->st, "alloc round");
+        if (rc) return rc;
+        e->round_bytes = 2 * total;
+    }
+    std::vector<char> img(total, 0);
+    memcpy(img.data() + o_g, e->geoms.data(), sizeof(FieldGeom) * e->geoms.size());
+    memcpy(img.data() + o_q, qd.data(), sizeof(QueryDesc) * qd.size());
+    memcpy(img.data() + o_s, sd.data(), sizeof(ScoreArgs) * sd.size());
+    memcpy(img.data() + o_a, sargs.data(), sizeof(ScoreArgs) * n);
+    memcpy(img.data() + o_p, pose0.data(), sizeof(long long) * pose0.size());
+    memcpy(img.data() + o_t, t0.data(), sizeof(long long) * t0.size());
+    char *base = (char *)e->d_round;
+    CF_TRY(cudaMemcpyAsync(base, img.data(), total, cudaMemcpyHostToDevice, e->st), "upload round");
+    const FieldGeom *d_geoms = (const FieldGeom *)(base + o_g);
+    unsigned int *d_work = (unsigned int *)(base + o_w);
+    int launches = 0;
+    for (size_t g = 0; g < qkeys.size(); ++g) {
+        CF_TRY(launch_query_batch(e->geoms[q_geom[g]], (const QueryDesc *)(base + o_q) + q_off[g], d_geoms, q_n[g],
+                                  q_blocks[g], e->st), "round query");
+        ++launches;
+    }
+    CF_TRY(launch_sample_batch((const ScoreArgs *)(base + o_a), (const long long *)(base + o_p), n, pose0[n], smem,
+                               e->st), "round sample");
+    ++launches;
+    for (size_t g = 0; g < skeys.size(); ++g) {
+        ScoreArgs launch = sd[s_off[g]];
+        launch.work = d_work + g;
+        CF_TRY(cudaMemsetAsync(launch.work, 0, sizeof(unsigned int), e->st), "round work counter");
+        CF_TRY(launch_score_batch(launch, (const ScoreArgs *)(base + o_s) + s_off[g], (const long long *)(base + o_t) + t_off[g],
+                                  s_n[g], s_tuples[g], e->st), "round score");
+        ++launches;
+    }
+    for (int i = 0; i < n; ++i) {
+        EngReq *r = act[i];
+        const size_t nt = (size_t)r->chunk * r->req.prm.n_tuples;
+        if (nt == 0) continue;
+        CF_TRY(cudaMemcpyAsync(r->h_tuples.data(), r->d_tuples, sizeof(int32_t) * nt * r->req.prm.k,
+                               cudaMemcpyDeviceToHost, e->st), "download tuples");
+        CF_TRY(cudaMemcpyAsync(r->h_margin.data(), r->d_margin, sizeof(float) * nt, cudaMemcpyDeviceToHost, e->st),
+               "download margins");
+        CF_TRY(cudaMemcpyAsync(r->h_accept.data(), r->d_accept, nt, cudaMemcpyDeviceToHost, e->st), "download accept");
+    }
+    CF_TRY(cudaStreamSynchronize(e->st), "round");
+    std::lock_guard<std::mutex> lk(e->mu);
+    e->stats.rounds++;
+    e->stats.launches += launches;
+    return CF_OK;
+}
+
+void worker_main(cf_engine *e) {
+    cudaSetDevice(e->dev);
+    for (;;) {
+        std::vector<EngReq *> act;
+        std::vector<EngReq *> rejected;
+        {
+            std::unique_lock<std::mutex> lk(e->mu);
+            for (;;) {
+                if (e->stop) return;
+                // admission, in arrival order
+                while (!e->queue.empty() && (int)e->active.size() < e->prm.max_active) {
+                    EngReq *r = e->queue.front();
+                    if ((int64_t)r->bytes > e->prm.hbm_budget_bytes) {  // can never fit
+                        e->queue.pop_front();
+                        rejected.push_back(r);
+                        continue;
+                    }
+                    if (e->stats.bytes_in_use + (int64_t)r->bytes > e->prm.hbm_budget_bytes) break;
+                    e->queue.pop_front();
+                    e->stats.bytes_in_use += (int64_t)r->bytes;
+                    e->stats.peak_bytes_in_use = std::max(e->stats.peak_bytes_in_use, e->stats.bytes_in_use);
+                    r->t_admit = e->now();
+                    e->active.push_back(r);
+                    act.push_back(r);  // newly admitted: uploaded below
+                }
+                e->stats.peak_active = std::max(e->stats.peak_active, (int32_t)e->active.size());
+                if (!e->active.empty() || !rejected.empty()) break;
+                e->cv_idle.notify_all();
+                e->cv.wait_for(lk, std::chrono::milliseconds(5));
+            }
+        }
+        for (EngReq *r : rejected) finish(e, r, CF_ENOMEM, false);
+        rejected.clear();
+        for (EngReq *r : act) {
+            const int arc = admit_one(e, r);
+            if (arc != CF_OK) {  // the request ends with the error; its budget share is returned by finish
+                {
+                    std::lock_guard<std::mutex> lk(e->mu);
+                    e->active.erase(std::find(e->active.begin(), e->active.end(), r));
+                    if (!r->d_block) e->stats.bytes_in_use -= (int64_t)r->bytes;
+                }
+                finish(e, r, arc, false);
+            }
+        }
+        std::vector<EngReq *> round;
+        {
+            std::lock_guard<std::mutex> lk(e->mu);
+            round = e->active;
+        }
+        if (round.empty()) continue;
+        const int rc = run_round(e, round);
+        std::vector<EngReq *> finished;
+        for (EngReq *r : round) {
+            bool done = rc != CF_OK;
+            if (rc == CF_OK) {
+                const int T = r->req.prm.n_tuples, k = r->req.prm.k;
+                for (int i = 0; i < r->chunk; ++i)
+                    for (int t = 0; t < T; ++t) {
+                        const size_t u = (size_t)i * T + t;
+                        if (!r->h_accept[u]) continue;
+                        r->res_pose.push_back(r->pose_next + i);
+                        r->res_margin.push_back(r->h_margin[u]);
+                        for (int d = 0; d < k; ++d) r->res_tuples.push_back(r->h_tuples[u * k + d]);
+                    }
+                r->pose_next += r->chunk;
+                done = (int)r->res_margin.size() >= r->req.n_grasps || r->pose_next >= r->limit;
+            }
+            if (done) finished.push_back(r);
+        }
+        {
+            std::lock_guard<std::mutex> lk(e->mu);
+            for (EngReq *r : finished) e->active.erase(std::find(e->active.begin(), e->active.end(), r));
+        }
+        for (EngReq *r : finished)
+            finish(e, r, rc, rc == CF_OK && (int)r->res_margin.size() < r->req.n_grasps);
+    }
+}
+
+}  // namespace
+
+extern "C" int cf_engine_create(const cf_engine_params *prm, cf_engine **out) {
+    if (!prm || !out) return fail(CF_EINVAL, "NULL argument");
+    if (prm->n_fields < 1 || !prm->fields) return fail(CF_EINVAL, "no fields");
+    if (prm->max_active < 1 || prm->pose_chunk < 1 || prm->pose_cap < 1 || prm->hbm_budget_bytes <= 0)
+        return fail(CF_EINVAL, "max_active, pose_chunk, pose_cap and the budget must be positive");
+    cf_engine *e = new cf_engine();
+    e->prm = *prm;
+    for (int i = 0; i < prm->n_fields; ++i) {
+        if (!prm->fields[i] || prm->fields[i]->table_words == 0) {
+            delete e;
+            return fail(CF_EINVAL, "field %d is NULL or empty", i);
+        }
+        e->fields.push_back(prm->fields[i]);
+        e->geoms.push_back(prm->fields[i]->geom);
+    }
+    e->prm.fields = nullptr;
+    CF_TRY(cudaGetDevice(&e->dev), "cudaGetDevice");
+    cudaError_t err = cudaStreamCreateWithFlags(&e->st, cudaStreamNonBlocking);
+    if (err != cudaSuccess) { delete e; return cuda_fail(err, "stream"); }
+    e->t0 = std::chrono::steady_clock::now();
+    e->worker = std::thread(worker_main, e);
+    *out = e;
+    return CF_OK;
+}
+
+extern "C" int cf_engine_submit(cf_engine *e, const cf_request *q, uint64_t *id) {
+    if (!e || !q) return fail(CF_EINVAL, "NULL argument");
+    if (q->field < 0 || q->field >= (int)e->fields.size()) return fail(CF_EINVAL, "field %d out of range", q->field);
+    if (q->n < 1 || !q->h_soa || q->n_poses < 1 || !q->h_poses) return fail(CF_EINVAL, "empty object or pose list");
+    if (q->prm.tuples_given) return fail(CF_EINVAL, "requests sample their own tuples");
+    if (q->prm.k < 1 || q->prm.k > CF_MAX_K || q->prm.n_edges < 3 || q->prm.n_edges > CF_MAX_EDGES ||
+        q->prm.k * q->prm.n_edges > 32 || q->prm.n_tuples < 1 || q->n_grasps < 1)
+        return fail(CF_EINVAL, "bad k / K / T / n_grasps");
+    EngReq *r = new EngReq();
+    r->req = *q;
+    r->fd = e->fields[q->field];
+    r->soa.assign(q->h_soa, q->h_soa + 6 * (size_t)q->n);
+    r->poses.assign(q->h_poses, q->h_poses + 12 * (size_t)q->n_poses);
+    r->req.h_soa = nullptr;
+    r->req.h_poses = nullptr;
+    r->limit = std::min(q->n_poses, e->prm.pose_cap);
+    r->bytes = state_bytes(*q, r->fd->F, e->prm.pose_chunk);
+    {
+        std::lock_guard<std::mutex> lk(e->mu);
+        r->id = e->next_id++;
+        r->t_submit = e->now();
+        e->queue.push_back(r);
+        e->stats.submitted++;
+    }
+    e->cv.notify_all();
+    if (id) *id = r->id;
+    return CF_OK;
+}
+
+extern "C" int cf_engine_poll(cf_engine *e, cf_result *out, int32_t max, int32_t *n_done) {
+    if (!e || !out || !n_done) return fail(CF_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(e->mu);
+    int n = 0;
+    while (n < max && !e->done.empty()) {
+        out[n++] = e->done.front();
+        e->done.pop_front();
+    }
+    *n_done = n;
+    return CF_OK;
+}
+
+extern "C" int cf_engine_result_free(cf_result *r) {
+    if (!r) return CF_OK;
+    free(r->pose);
+    free(r->tuples);
+    free(r->margin);
+    r->pose = r->tuples = nullptr;
+    r->margin = nullptr;
+    return CF_OK;
+}
+
+extern "C" int cf_engine_get_stats(const cf_engine *ce, cf_engine_stats *out) {
+    if (!ce || !out) return fail(CF_EINVAL, "NULL argument");
+    cf_engine *e = const_cast<cf_engine *>(ce);
+    std::lock_guard<std::mutex> lk(e->mu);
+    *out = e->stats;
+    out->queued = (int32_t)e->queue.size();
+    out->active = (int32_t)e->active.size();
+    return CF_OK;
+}
+
+extern "C" int cf_engine_drain(cf_engine *e, int32_t timeout_ms) {
+    if (!e) return fail(CF_EINVAL, "NULL argument");
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms);
+    std::unique_lock<std::mutex> lk(e->mu);
+    while (!e->queue.empty() || !e->active.empty()) {
+        if (timeout_ms >= 0 && std::chrono::steady_clock::now() >= deadline)
+            return fail(CF_ETIMEOUT, "engine still has %zu queued and %zu active requests", e->queue.size(),
+                        e->active.size());
+        e->cv_idle.wait_for(lk, std::chrono::milliseconds(2));
+    }
+    return CF_OK;
+}
+
+extern "C" int cf_engine_destroy(cf_engine *e) {
+    if (!e) return CF_OK;
+    {
+        std::lock_guard<std::mutex> lk(e->mu);
+        e->stop = true;
+    }
+    e->cv.notify_all();
+    if (e->worker.joinable()) e->worker.join();
+    for (EngReq *r : e->active) {
+        if (r->d_block) cudaFreeAsync(r->d_block, e->st);
+        delete r;
+    }
+    for (EngReq *r : e->queue) delete r;
+    for (cf_result &r : e->done) cf_engine_result_free(&r);
+    if (e->d_round) cudaFreeAsync(e->d_round, e->st);
+    cudaStreamSynchronize(e->st);
+    cudaStreamDestroy(e->st);
+    delete e;
+    return CF_OK;
+}

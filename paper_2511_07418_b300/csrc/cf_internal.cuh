@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "cf.h"
 
 namespace cf {
@@ -155,6 +157,7 @@ struct ScoreArgs {
     float cs[CF_MAX_EDGES], sn[CF_MAX_EDGES];
     uint32_t seed_lo, seed_hi;
     int tuples_given;
+    uint32_t pose_base;  // added to the pose index in the tuple draws' counter
     int32_t *tuples;
     uint8_t *fingers;
     float *margin;
@@ -175,4 +178,38 @@ cudaError_t launch_score_batch(const ScoreArgs &launch, const ScoreArgs *d_descs
                                long long total_tuples, cudaStream_t st);
 size_t score_smem_bytes(int F, int W, int T, int k, bool sampling);
 
+// ---------------------------------------------------------------------------
+// host helpers shared by the ABI translation units
+// ---------------------------------------------------------------------------
+extern thread_local std::string t_err;
+int fail(int code, const char *fmt, ...);                // sets the thread's error message, returns code
+int cuda_fail(cudaError_t e, const char *what);
+int pool_alloc(void **p, size_t bytes, cudaStream_t st, const char *what);  // library stream-ordered pool
+int check_points(const cf_points *obj);
+int fill_score_args(const cf_points *obj, int32_t F, const uint32_t *d_masks, const uint32_t *d_counts, int32_t P,
+                    const cf_score_params *prm, int32_t *d_tuples, uint8_t *d_fingers, float *d_margin,
+                    uint8_t *d_accept, ScoreArgs *a);
+
+#define CF_TRY(call, what)                                     \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return ::cf::cuda_fail(e_, what); \
+    } while (0)
+
 }  // namespace cf
+
+// the field handle of the ABI (opaque to callers)
+struct cf_field {
+    int dev = 0;
+    cudaStream_t st = nullptr;  // device memory is freed on this stream
+    int F = 0, J = 0, M = 0, S = 0, B = 0;
+    cf::FieldGeom geom{};
+    cf::HandDev hand{};
+    void *d_block = nullptr;     // hand arrays + bounds scratch
+    uint32_t *d_table = nullptr;
+    uint32_t *d_cand = nullptr;  // normal-bin candidate table
+    int64_t table_words = 0;
+    int64_t device_bytes = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    float build_ms = -1.f;
+};

@@ -154,8 +154,9 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_tuples(const ScoreArg
             }
             continue;
         }
-        const uint4 u0 = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)tau, 0u, 0u), key);
-        const uint4 u1 = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)tau, 1u, 0u), key);
+        const uint32_t pid = (uint32_t)i + a.pose_base;
+        const uint4 u0 = philox4x32_10(make_uint4(pid, (uint32_t)tau, 0u, 0u), key);
+        const uint4 u1 = philox4x32_10(make_uint4(pid, (uint32_t)tau, 1u, 0u), key);
         uint32_t pk = pk0;
         for (int d = 0; d < k; ++d) {  // partial Fisher-Yates over the non-empty fingers
             const int jj = d + (int)__umulhi(draw_word(u0, u1, d), (uint32_t)(m - d));
