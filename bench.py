@@ -46,6 +46,9 @@ def _args():
     ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--cpu-poses", type=int, default=32, help="poses in the oracle's timed sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-objects", type=int, default=64, help="objects of the batched-form leg (0: skip)")
+    ap.add_argument("--served-seconds", type=float, default=4.0, help="seconds per offered rate (0: skip)")
+    ap.add_argument("--served-rates", default="10,100,1000")
     return ap.parse_args()
 
 
@@ -358,11 +361,146 @@ def run_ours(args):
             "e2e": {"value": e2e_acc / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": n_e2e, "ms_per_step": 1e3 * e2e_s / n_e2e},
             "roofline": roof, "clocks": clocks}
+    if world == 1 and (args.batch_objects > 0 or args.served_seconds > 0):
+        ws, fields = _hand_fields(cf, torch, dev)
+        if args.batch_objects > 0:
+            line["batched"] = run_batched(cf, torch, dev, args.batch_objects, ws, fields)
+        if args.served_seconds > 0:
+            rates = [float(x) for x in args.served_rates.split(",") if x]
+            line["served"] = run_served(cf, torch, dev, ws, fields, rates, args.served_seconds)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_poses)
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# batched and served forms (same GPU, against the plain one-object-per-launch form)
+# ---------------------------------------------------------------------------
+
+def _hand_fields(cf, torch, dev):
+    import synth
+    ws, fields = [], []
+    for name in ["tiny_sphere", "hand16_superquadric", "hand20_tool"]:
+        w = synth.workload(name, P=1, N=64)
+        ws.append(w)
+        fields.append(cf.build(w.hand, w.inv_h, w.bins, torch.from_numpy(w.q).to(dev)))
+    torch.cuda.synchronize()
+    return ws, fields
+
+
+def run_batched(cf, torch, dev, n_objects, ws, fields):
+    """The many-object batch: every object's query + sampling + scoring, once as
+    plain per-object calls on one stream, once as the batch's graph replay."""
+    import numpy as np
+
+    import synth
+    names = ["tiny_sphere", "hand16_superquadric", "hand20_tool"]
+    t_gen = time.perf_counter()
+    specs = synth.batch_objects(n_objects, seed=0)
+    items = []
+    for j, sp in enumerate(specs):
+        hi = names.index(sp["hand"])
+        w = ws[hi]
+        obj, poses = synth.batch_object_inputs(sp, w.hand)
+        prm = cf.score_params(w.T, w.k, w.mu, w.K, w.eps, obj.centroid, obj.rho, 7000 + j)
+        it = cf.batch_item(fields[hi], torch.from_numpy(obj.soa()).to(dev), torch.from_numpy(poses).to(dev), prm)
+        it["F"] = w.hand.F
+        items.append(it)
+    t_gen = time.perf_counter() - t_gen
+    pairs = sum(int(it["soa"].shape[1]) * int(it["poses"].shape[0]) for it in items)
+    tuples = sum(int(it["tuples"].numel()) // int(it["prm"].k) for it in items)
+
+    def plain():
+        for it in items:
+            cf.query_domains(it["field"], it["soa"], it["poses"], it["masks"], it["counts"])
+            cf.score_tuples(it["soa"], it["F"], it["masks"], it["counts"], it["prm"], it["tuples"], it["fingers"])
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        best = None
+        for _ in range(reps):
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        return best
+
+    t_plain = timed(plain)
+    # the plain calls above allocate margin/accept per call; the batch writes into the items' own buffers
+    batch = cf.Batch(items)
+    t_batch = timed(batch.run)
+    accepted = sum(int(it["accept"].sum()) for it in items)
+    n_launch, n_groups = batch.launches()
+    batch.close()
+    return {"objects": n_objects, "pose_point_pairs": pairs, "tuples": tuples, "accepted": accepted,
+            "plain_ms": t_plain, "batched_ms": t_batch, "plain_grasps_per_s": accepted / (t_plain / 1e3),
+            "batched_grasps_per_s": accepted / (t_batch / 1e3), "batched_launches": n_launch,
+            "plain_launches": 3 * n_objects, "generate_s": t_gen,
+            "workload": "64 objects (superquadrics / tool composites), points log-uniform 2,048-131,072, poses "
+                        "log-uniform 4,096-32,768, hand per object from the 3/4/5-finger hands (fields cached)"}
+
+
+def run_served(cf, torch, dev, ws, fields, rates, seconds, pool=24):
+    """Poisson request streams against the engine (continuous batching) and
+    against the same engine with one slot (one request at a time, plain
+    per-request launches); p50 / p99 latency and valid grasps/s per rate."""
+    import numpy as np
+
+    import synth
+    rng = np.random.default_rng(11)
+    names = ["tiny_sphere", "hand16_superquadric", "hand20_tool"]
+    objs = []
+    for o in range(pool):
+        N = int(round(np.exp(rng.uniform(np.log(1024), np.log(65536)))))
+        obj = synth.superquadric(N, 3000 + o) if o % 2 == 0 else synth.tool_composite(N, 3000 + o)
+        hi = int(rng.integers(3))
+        poses = synth.palm_poses(8192, 4000 + o, ws[hi].hand.grasp_centre, obj.centroid)
+        objs.append((hi, obj.soa(), poses, obj))
+
+    def stream(max_active, rate):
+        eng = cf.Engine(fields, hbm_budget_bytes=64 << 30, max_active=max_active, pose_chunk=256, pose_cap=65536)
+        r = np.random.default_rng(int(rate) * 7 + max_active)
+        t = 0.0
+        arrivals = []
+        while t < seconds:
+            t += r.exponential(1.0 / rate)
+            arrivals.append(t)
+        done = []
+        t0 = time.perf_counter()
+        for j, ta in enumerate(arrivals):
+            while time.perf_counter() - t0 < ta:
+                done += eng.poll()
+                time.sleep(0.0002)
+            hi, soa, poses, obj = objs[int(r.integers(pool))]
+            w = ws[hi]
+            prm = cf.score_params(w.T, w.k, w.mu, w.K, w.eps, obj.centroid, obj.rho, 90000 + j)
+            eng.submit(hi, soa, poses, prm, int(r.integers(100, 5001)), j)
+        eng.drain(600000)
+        done += eng.poll(4096)
+        wall = time.perf_counter() - t0
+        st = eng.stats()
+        eng.close()
+        lat = np.array([d["t_done"] - d["t_submit"] for d in done]) * 1e3
+        acc = sum(d["n_accepted"] for d in done)
+        return {"rate": rate, "requests": len(arrivals), "completed": len(done),
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "grasps_per_s": acc / wall, "rounds": st["rounds"], "peak_active": st["peak_active"],
+                "peak_gb": st["peak_bytes_in_use"] / 1e9}
+
+    out = {"continuous_batching": [], "one_at_a_time": [],
+           "workload": f"Poisson arrivals, {seconds:g} s per rate; objects drawn from {pool} generated objects "
+                       "(superquadric / tool, 1,024-65,536 points) with a random hand; 100-5,000 grasps requested; "
+                       "8,192 candidate poses per request (pose cap 65,536), chunk 256 poses, HBM budget 64 GiB"}
+    for rate in rates:
+        out["continuous_batching"].append(stream(64, rate))
+        out["one_at_a_time"].append(stream(1, rate))
+    return out
 
 
 def main():
