@@ -49,6 +49,7 @@ def _args():
     ap.add_argument("--batch-objects", type=int, default=64, help="objects of the batched-form leg (0: skip)")
     ap.add_argument("--served-seconds", type=float, default=4.0, help="seconds per offered rate (0: skip)")
     ap.add_argument("--served-rates", default="10,100,1000")
+    ap.add_argument("--realized-steps", type=int, default=20, help="steps of the IK + realization leg (0: skip)")
     return ap.parse_args()
 
 
@@ -361,6 +362,9 @@ def run_ours(args):
             "e2e": {"value": e2e_acc / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": n_e2e, "ms_per_step": 1e3 * e2e_s / n_e2e},
             "roofline": roof, "clocks": clocks}
+    if world == 1 and args.realized_steps > 0:
+        line["realized"] = run_realized(cf, torch, dev, w, args.realized_steps, soa, poses, masks, counts, tuples,
+                                        fingers, prm, prm_given, flush)
     if world == 1 and (args.batch_objects > 0 or args.served_seconds > 0):
         ws, fields = _hand_fields(cf, torch, dev)
         if args.batch_objects > 0:
@@ -373,6 +377,85 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# end to end through the kinematics rows: IK, re-scoring, realization
+# ---------------------------------------------------------------------------
+
+SDF_H = 0.004        # object SDF grid spacing (m)
+SDF_MARGIN = 0.02    # grid margin around the object (> largest capsule radius + penetration margin)
+PEN_MARGIN = 2e-3    # tolerated capsule penetration (m)
+
+
+def run_realized(cf, torch, dev, w, steps, soa, poses, masks, counts, tuples, fingers, prm, prm_given, flush):
+    """Valid grasps/s after kinematics optimisation and post-processing.  One
+    step = domain query, tuple sampling, closure scoring, the object's SDF grid,
+    reverse lookup + DLS IK of every accepted tuple, closure re-scoring of the
+    realised contacts, and the realization filter (random free joints,
+    capsule-vs-SDF penetration, finger-finger capsule intersection).  The
+    hand's field (with its reverse-lookup table) is built once, outside."""
+    import numpy as np
+    F, k = w.hand.F, w.k
+    n = w.P * w.T
+    q = torch.from_numpy(w.q).to(dev)
+    field = cf.build(w.hand, w.inv_h, w.bins, q, want_rep=True)
+    lo, h, dims = cf.sdf_box(w.obj.soa(), SDF_H, SDF_MARGIN)
+    ikp = cf.ik_params()
+    rp = cf.realize_params(PEN_MARGIN, 0.5 / float(w.inv_h), w.seed)
+    prm_re = cf.score_params(1, k, w.mu, w.K, w.eps, w.obj.centroid, w.obj.rho, w.seed, tuples_given=True)
+    tot = torch.zeros(5, dtype=torch.int64, device=dev)  # accepted, ik ok, re-accepted, valid, scored
+    n_ev = 8
+
+    def step(ev):
+        ev[0].record()
+        cf.query_domains(field, soa, poses, masks, counts)
+        ev[1].record()
+        cf.sample_tuples(soa, F, masks, counts, prm, tuples, fingers)
+        ev[2].record()
+        _, _, _, accept = cf.score_tuples(soa, F, None, None, prm_given, tuples)
+        ev[3].record()
+        sdf = cf.Sdf(soa, lo, h, dims)
+        ev[4].record()
+        ik = cf.ik_dls(field, soa, poses, w.T, k, tuples, fingers, accept, ikp)
+        ev[5].record()
+        _, _, _, acc2 = cf.score_tuples(ik["contacts"], F, None, None, prm_re, tuples=ik["rtuples"].view(n, 1, k))
+        ev[6].record()
+        flags = cf.realize(field, sdf, poses, w.T, ik["q"], ik["used"], ik["ok"], acc2.view(n), rp)
+        ev[7].record()
+        tot[0].add_(accept.sum())
+        tot[1].add_(ik["ok"].sum())
+        tot[2].add_(acc2.sum())
+        tot[3].add_((flags == 0).sum())
+        return sdf
+
+    for _ in range(3):
+        step([torch.cuda.Event(enable_timing=True) for _ in range(n_ev)])
+    tot.zero_()
+    cf.device_status()
+    evs = []
+    for i in range(steps):
+        flush.fill_(float(i))
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(n_ev)]
+        step(ev)
+        evs.append(ev)
+    torch.cuda.synchronize()
+    ms = np.array([[e[j].elapsed_time(e[j + 1]) for j in range(n_ev - 1)] for e in evs])
+    t = tot.cpu().numpy()
+    total_ms = float(ms.sum())
+    per = ms.mean(axis=0)
+    names = ["query", "sample", "score", "sdf_build", "ik_dls", "rescore", "realize"]
+    return {"metric": "valid grasps/s after IK + realization", "value": float(t[3]) / (total_ms / 1e3),
+            "unit": UNIT, "steps": steps, "ms_per_step": total_ms / steps,
+            "breakdown_ms": {nm: float(v) for nm, v in zip(names, per)},
+            "per_step": {"accepted": t[0] / steps, "ik_ok": t[1] / steps, "re_accepted": t[2] / steps,
+                         "valid": t[3] / steps},
+            "gpu_launches_per_step": 9,
+            "params": {"sdf_h": SDF_H, "sdf_dims": [int(x) for x in dims], "pen_margin": PEN_MARGIN,
+                       "axis_step": 0.5 / float(w.inv_h), "ik": {"beta": 0.01, "lambda": 1e-4, "phase1": 16,
+                                                                  "rounds": 4, "phase2": 4, "tol_pos": 2e-3,
+                                                                  "tol_deg": 20.0}},
+            "device_status": cf.device_status()}
 
 
 # ---------------------------------------------------------------------------

@@ -65,6 +65,9 @@ enum {
 /* device status bits (cf_device_status) */
 #define CF_DEV_LP_PIVOT_CAP 0x1u   /* an LP stopped at its pivot cap; its margin is an upper bound */
 #define CF_DEV_LP_UNBOUNDED 0x2u   /* an LP ratio test found no pivot row (numerical) */
+#define CF_DEV_REP_FULL 0x4u       /* the representative table had no free slot (cannot happen at load <= 1/2) */
+#define CF_DEV_REP_MISS 0x8u       /* an IK contact's code has no representative (tuple not from this field) */
+#define CF_DEV_BIN_RANGE 0x80000000u /* a build sample fell outside the table box (cannot happen) */
 
 typedef void *cf_stream; /* cudaStream_t */
 
@@ -83,6 +86,8 @@ typedef struct cf_hand_desc {
     const float *surf_p;      /* [F][M][3] */
     const float *surf_n;      /* [F][M][3] */
     const int32_t *surf_link; /* [F][M], 0..J-1 */
+    const float *lo, *hi;     /* [F][J] joint limits (rad); NULL: the field cannot drive IK / realization */
+    const float *radius;      /* [F][J] capsule radius of link j (0 for a zero-length link) */
 } cf_hand_desc;
 
 /* Field parameters.  Cells live on one global lattice: cell k covers
@@ -93,6 +98,8 @@ typedef struct cf_field_params {
     float inv_h;              /* 1 / voxel edge, cells per metre (> 0) */
     int32_t n_bins;           /* B, 1..CF_MAX_BINS */
     const float *bin_dirs;    /* host [B][3] */
+    int32_t want_rep;         /* 1: also keep, per (cell, finger, bin) code, the smallest s * M + m of the
+                                 samples that produced it (reverse lookup, Sec. 4.5) */
 } cf_field_params;
 
 typedef struct cf_field cf_field;
@@ -153,6 +160,13 @@ int cf_field_get_info(const cf_field *field, cf_field_info *info);
 
 /* Copy the bit table (table_words uint32 words) to host memory. */
 int cf_field_copy_table(const cf_field *field, uint32_t *host_words, int64_t capacity_words);
+
+/* Representative table (want_rep): open-addressing hash of rep_slots slots;
+ * key = record word index * 32 + bit (the code's position in the table,
+ * ~0 for an empty slot), value = smallest sample * M + surface point (original
+ * order) that set that bit.  *slots = 0 when the field has none. */
+int cf_field_rep_slots(const cf_field *field, int64_t *slots);
+int cf_field_copy_rep(const cf_field *field, uint64_t *host_keys, uint32_t *host_vals, int64_t capacity);
 
 /* Frees the field.  Its device memory is released in order on the stream it was
  * built on (that stream must still exist); work that uses the field on other
@@ -221,6 +235,83 @@ int cf_score_tuples_noalloc(const cf_points *obj, int32_t n_fingers, const uint3
 int cf_sample_tuples(const cf_points *obj, int32_t n_fingers, const uint32_t *d_masks, const uint32_t *d_counts,
                      int32_t n_poses, const cf_score_params *prm, int32_t *d_tuples, uint8_t *d_fingers,
                      cf_stream stream);
+
+/* ---- a6: reverse lookup + damped-least-squares IK (Sec. 4.5) ------------- */
+
+typedef struct cf_ik_params {
+    float beta;         /* lever of the normal target (m): p~ + beta n~ -> p + beta n */
+    float lambda;       /* DLS damping (> 0) */
+    int32_t n_phase1;   /* DLS steps from the representative sample */
+    int32_t n_rounds;   /* Phase II rounds: project p onto the contact link's capsule, then n_phase2 steps */
+    int32_t n_phase2;
+    float tol_pos;      /* success: |p~ - p| <= tol_pos (m) ... */
+    float tol_cos;      /* ... and n~ . n >= tol_cos, after a last projection */
+} cf_ik_params;
+
+/* Kinematics optimisation of tuple slots u = 0..n_slots-1 (pose u / n_tuples),
+ * typically cf_score_tuples' outputs.  Slot u is attempted when d_accept[u]
+ * (NULL: every slot) and its k contacts (point d_tuples[u][c] of finger
+ * d_fingers[u][c]) are valid and of distinct fingers.  Contact c targets the
+ * query's contact-surface vector p = R p_x + t, n = -(R n_x) of pose u / T.  The
+ * reverse lookup reads the representative (sample s, surface point m) of the
+ * contact's (cell, bin) code in finger f's table, and the IK starts from joint
+ * sample s with p~, n~ = surface point m; then n_phase1 DLS steps
+ * dq = (J^T J + lambda I)^-1 J^T e (e stacks p - p~ and p + beta n - (p~ + beta
+ * n~); J their position Jacobians), q clamped to [lo, hi]; then the Phase II
+ * rounds; then one last projection.  Fingers share no joint, so each contact is
+ * solved on its own.  Outputs (device, caller-owned):
+ *   d_q [n_slots][F][J]       joint values (rows of fingers without a contact: 0)
+ *   d_used [n_slots][F][J]    1 for joints 0..(contact link) of contact fingers
+ *   d_contacts [6][n_slots*k] realised contacts in the object frame (px py pz
+ *                             nx ny nz; n = -R^T n~, the object's outward normal)
+ *   d_rtuples [n_slots][k]    u*k + c when every contact of the slot succeeded, else -1
+ *                             (pass with d_contacts to cf_score_tuples, tuples_given,
+ *                             n_poses = n_slots, T = 1, to re-score the realised contacts)
+ *   d_resid [n_slots][k][2]   |p~ - p| and n~ . n (inf / -2 when not attempted)
+ *   d_ok [n_slots]            1 when every contact succeeded
+ * The field must have been built with joint limits and want_rep.  A contact
+ * whose code has no representative sets CF_DEV_REP_MISS and fails.
+ * Errors: CF_EINVAL, CF_ECUDA.  Asynchronous on `stream`. */
+int cf_ik_dls(const cf_field *field, const cf_points *obj, const float *d_poses, int32_t n_slots, int32_t n_tuples,
+              int32_t k, const int32_t *d_tuples, const uint8_t *d_fingers, const uint8_t *d_accept,
+              const cf_ik_params *prm, float *d_q, uint8_t *d_used, float *d_contacts, int32_t *d_rtuples,
+              float *d_resid, uint8_t *d_ok, cf_stream stream);
+
+/* ---- a7: object SDF grid and the realization filter (Sec. 4.6) ----------- */
+
+typedef struct cf_sdf cf_sdf;
+
+/* Signed distance of the object's oriented point set on the grid
+ * lo + (i, j, k) h, i < dims[0] ... (x fastest): distance to the nearest point
+ * (first on ties), negative when (x - p) . n of that point is < 0.  Brute force
+ * over all points.  The grid should extend past the object by more than the
+ * largest capsule radius: lookups outside it count as far away.
+ * Errors: CF_EINVAL, CF_ENOMEM, CF_ECUDA. */
+int cf_sdf_build(const cf_points *obj, const float lo[3], float h, const int32_t dims[3], cf_stream stream,
+                 cf_sdf **out);
+int cf_sdf_copy(const cf_sdf *sdf, float *host, int64_t capacity);
+int cf_sdf_destroy(cf_sdf *sdf);
+
+typedef struct cf_realize_params {
+    float pen_margin;   /* tolerated penetration depth (m) */
+    float axis_step;    /* spacing of the samples along each capsule axis (m) */
+    uint64_t seed;      /* key of the random joint values */
+} cf_realize_params;
+
+/* Post-processing of tuple slots u (pose u / n_tuples): when d_gate_a[u] and
+ * d_gate_b[u] (NULL: 1), every joint with d_used == 0 gets a uniform value in
+ * its limits, lo + (u24 * 2^-24) * (hi - lo) in FP32 with u24 the top 24 bits of
+ * word j % 4 of Philox4x32-10(counter (u, f, j / 4, 0x7EA1), key seed), written
+ * back to d_q.  Capsule links (radius > 0, length > 0) are then checked:
+ * penetration when the trilinear SDF at a sample x_s = a + (s / ns)(b - a),
+ * s = 0..ns, ns = ceil(length / axis_step), taken to the object frame, is below
+ * radius - pen_margin; self-collision when capsules of two fingers are closer
+ * than the sum of their radii.  d_flags[u] = 0 for a realised grasp, else bits
+ * 1 (gated out), 2 (penetration), 4 (self-collision).
+ * Errors: CF_EINVAL, CF_ECUDA.  Asynchronous on `stream`. */
+int cf_realize(const cf_field *field, const cf_sdf *sdf, const float *d_poses, int32_t n_slots, int32_t n_tuples,
+               const cf_realize_params *prm, const uint8_t *d_gate_a, const uint8_t *d_gate_b, float *d_q,
+               const uint8_t *d_used, uint8_t *d_flags, cf_stream stream);
 
 /* ---- many objects in one graph launch ------------------------------------ */
 

@@ -19,6 +19,10 @@ Functions (paper passages they follow are cited in ``cf_oracle.c``):
   sample_tuples       random k-tuples from k distinct finger domains (Sec. 4.3)
   closure_lp          linearised GSWO margin of one tuple (Eq. GSWO): k LPs
   score_tuples        margins / accept flags of many tuples (process pool)
+  rep_codes           reverse-lookup representatives of a finger's codes (Sec. 4.5)
+  point_codes         FP32 code of an object point under a pose (the query's decision)
+  kinematics.*        FP64 numpy FK / Jacobian / DLS IK / SDF grid / realization
+                      checks (Sec. 4.5, Sec. 4.6)
 
 Parity status: every function is pinned by tests under ``tests/`` against
 closed forms, an independent library routine (triton's Philox in
@@ -43,7 +47,8 @@ _SRC = os.path.join(_HERE, "cf_oracle.c")
 _LIB = os.path.join(_HERE, "liborc.so")
 
 __all__ = ["build", "lib", "philox4x32_10", "fk_links", "contact_vectors", "Field",
-           "query_masks_brute", "sample_tuples", "closure_lp", "score_tuples", "num_threads"]
+           "query_masks_brute", "sample_tuples", "closure_lp", "score_tuples", "num_threads", "pack_code",
+           "rep_codes", "point_codes"]
 
 
 def build(force: bool = False) -> str:
@@ -85,6 +90,10 @@ def lib():
                                             c_int, fp, c_int, fp, c_int, fp, u32p]
         L.orc_sample_tuples.argtypes = [c_int, c_int, c_int, u32p, u32p, c_int, c_int, c_uint64, i32p, u8p]
         L.orc_num_threads.restype = c_int
+        L.orc_rep_codes.restype = c_int64
+        L.orc_rep_codes.argtypes = [c_int, c_int, c_int, fp, fp, fp, fp, fp, i32p, fp, c_int, c_float, c_int, fp,
+                                    c_int, POINTER(c_uint64), u32p, c_int64]
+        L.orc_point_codes.argtypes = [c_int, fp, fp, c_int, i32p, i32p, c_float, c_int, fp, POINTER(c_int64)]
         _lib = L
     return _lib
 
@@ -230,6 +239,47 @@ def query_masks_brute(hand, q, inv_h, bins, soa, poses) -> np.ndarray:
                                 _p(soa, c_float), P, _p(poses, c_float), _p(masks, c_uint32))
     del keep
     return masks
+
+
+KEY_OFFSET = 32768
+
+
+def pack_code(f, kx, ky, kz, b) -> int:
+    """Packed (finger, cell, bin) key of the oracle's code sets."""
+    o = KEY_OFFSET
+    return (int(f) << 56) | ((int(kx) + o) << 40) | ((int(ky) + o) << 24) | ((int(kz) + o) << 8) | int(b)
+
+
+def rep_codes(hand, q, inv_h, bins, f: int) -> dict:
+    """Reverse lookup table of finger f (Sec. 4.5): packed code -> smallest
+    s * M + m over the field samples producing it (m in the hand's order)."""
+    keep, ptrs = _hand_args(hand)
+    qq = _c(q, np.float32)
+    bb = _c(bins, np.float32)
+    S = int(qq.shape[2])
+    cap = S * hand.M
+    keys = np.zeros(max(cap, 1), np.uint64)
+    vals = np.zeros(max(cap, 1), np.uint32)
+    n = lib().orc_rep_codes(hand.F, hand.J, hand.M, *ptrs, _p(qq, c_float), S, c_float(np.float32(inv_h)),
+                            int(bb.shape[0]), _p(bb, c_float), int(f), keys.ctypes.data_as(POINTER(c_uint64)),
+                            _p(vals, c_uint32), cap)
+    del keep
+    return dict(zip(keys[:n].tolist(), vals[:n].tolist()))
+
+
+def point_codes(soa, poses, pose_idx, pt_idx, inv_h, bins) -> np.ndarray:
+    """FP32 (kx, ky, kz, bin) of the contact-surface vector of points pt_idx
+    under poses pose_idx, as the domain query decides it: int64 [n, 4]."""
+    soa = _c(soa, np.float32)
+    poses = _c(poses, np.float32).reshape(-1, 12)
+    pi = _c(pose_idx, np.int32).ravel()
+    xi = _c(pt_idx, np.int32).ravel()
+    bb = _c(bins, np.float32)
+    out = np.zeros((pi.size, 4), np.int64)
+    lib().orc_point_codes(int(soa.shape[1]), _p(soa, c_float), _p(poses, c_float), int(pi.size), _p(pi, c_int32),
+                          _p(xi, c_int32), c_float(np.float32(inv_h)), int(bb.shape[0]), _p(bb, c_float),
+                          out.ctypes.data_as(POINTER(c_int64)))
+    return out
 
 
 def sample_tuples(masks: np.ndarray, counts: np.ndarray, N: int, T: int, k: int, seed: int):

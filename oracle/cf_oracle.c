@@ -557,3 +557,75 @@ int orc_num_threads(void) {
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* Reverse lookup (Sec. 4.5 "Kinematics Optimization")                       */
+/* ------------------------------------------------------------------------ */
+typedef struct { uint64_t key; uint32_t val; } keyval;
+
+static int cmp_keyval(const void *a, const void *b) {
+    const keyval *x = (const keyval *)a, *y = (const keyval *)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    return x->val < y->val ? -1 : (x->val > y->val);
+}
+
+/* For every FP32 (cell, bin) code of finger f: the smallest s * M + m over the
+ * field samples (joint sample s, surface point m in the caller's order) whose
+ * contact vector has that code -- the sample the reverse lookup retrieves.
+ * Writes up to cap (packed key, value) pairs sorted by key; returns the number
+ * of distinct codes. */
+int64_t orc_rep_codes(int F, int J, int M, const float *base, const float *axis, const float *offset,
+                      const float *surf_p, const float *surf_n, const int32_t *surf_link, const float *q, int S,
+                      float inv_h, int B, const float *dirs, int f, uint64_t *keys, uint32_t *vals, int64_t cap) {
+    (void)F;
+    const float *bf = base + 12 * f, *af = axis + 3 * J * f, *of = offset + 3 * J * f;
+    const float *spf = surf_p + 3 * M * f, *snf = surf_n + 3 * M * f;
+    const int32_t *slf = surf_link + M * f;
+    keyval *kv = (keyval *)malloc(sizeof(keyval) * (size_t)S * M + 1);
+    float *p32 = (float *)malloc(sizeof(float) * 3 * M), *n32 = (float *)malloc(sizeof(float) * 3 * M);
+    int64_t n = 0;
+    double qs[8];
+    for (int s = 0; s < S; ++s) {
+        for (int j = 0; j < J; ++j) qs[j] = (double)q[((size_t)f * J + j) * S + s];
+        orc_contact_vectors(J, M, bf, af, of, spf, snf, slf, qs, p32, n32, NULL, NULL);
+        for (int m = 0; m < M; ++m) {
+            int64_t kx = cell_axis(p32[3 * m], inv_h), ky = cell_axis(p32[3 * m + 1], inv_h),
+                    kz = cell_axis(p32[3 * m + 2], inv_h);
+            if (!in_key_range(kx) || !in_key_range(ky) || !in_key_range(kz)) continue;
+            kv[n].key = pack_key(f, kx, ky, kz, bin32(n32 + 3 * m, B, dirs));
+            kv[n].val = (uint32_t)s * (uint32_t)M + (uint32_t)m;
+            ++n;
+        }
+    }
+    qsort(kv, (size_t)n, sizeof(keyval), cmp_keyval);
+    int64_t u = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (i > 0 && kv[i].key == kv[i - 1].key) continue;  /* first of each key = smallest value */
+        if (u < cap) { keys[u] = kv[i].key; vals[u] = kv[i].val; }
+        ++u;
+    }
+    free(kv); free(p32); free(n32);
+    return u;
+}
+
+/* FP32 (cell, bin) code of the contact-surface vector of point pt[i] under pose
+ * pose[i], exactly as the domain query decides it: out[i] = (kx, ky, kz, bin). */
+void orc_point_codes(int N, const float *soa, const float *poses, int n, const int32_t *pose_idx,
+                     const int32_t *pt_idx, float inv_h, int B, const float *dirs, int64_t *out) {
+    for (int i = 0; i < n; ++i) {
+        const float *T = poses + 12 * (size_t)pose_idx[i];
+        const float R[9] = {T[0], T[1], T[2], T[4], T[5], T[6], T[8], T[9], T[10]};
+        const float t[3] = {T[3], T[7], T[11]};
+        const int x = pt_idx[i];
+        const float p[3] = {soa[x], soa[N + x], soa[2 * N + x]};
+        const float nv[3] = {soa[3 * N + x], soa[4 * N + x], soa[5 * N + x]};
+        float pq[3], nq[3];
+        xform_point32(R, t, p, pq);
+        rotate32(R, nv, nq);
+        const float mq[3] = {-nq[0], -nq[1], -nq[2]};
+        out[4 * i] = cell_axis(pq[0], inv_h);
+        out[4 * i + 1] = cell_axis(pq[1], inv_h);
+        out[4 * i + 2] = cell_axis(pq[2], inv_h);
+        out[4 * i + 3] = bin32(mq, B, dirs);
+    }
+}

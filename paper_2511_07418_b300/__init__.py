@@ -10,6 +10,8 @@ Entry points mirror the C ABI:
   query_domains(field, soa, poses, ...)      -> masks, counts  (cf_query_domains)
   score_tuples(soa, n_fingers, masks, counts, params, ...)     (cf_score_tuples)
   Plan(n_fingers, n_max, p_max, params).run_host(field, ...)   (cf_plan_*)
+  ik_dls(field, soa, poses, T, k, tuples, fingers, accept, params)  (cf_ik_dls)
+  Sdf(soa, lo, h, dims); realize(field, sdf, poses, T, q, used, ...)  (cf_sdf_build, cf_realize)
 """
 from __future__ import annotations
 
@@ -34,6 +36,8 @@ CF_MAX_BINS = 32
 CF_OK = 0
 CF_DEV_LP_PIVOT_CAP = 0x1
 CF_DEV_LP_UNBOUNDED = 0x2
+CF_DEV_REP_FULL = 0x4
+CF_DEV_REP_MISS = 0x8
 
 
 class CfError(RuntimeError):
@@ -45,11 +49,21 @@ class CfError(RuntimeError):
 class HandDesc(Structure):
     _fields_ = [("n_fingers", c_int32), ("n_joints", c_int32), ("n_surf", c_int32),
                 ("base", POINTER(c_float)), ("axis", POINTER(c_float)), ("offset", POINTER(c_float)),
-                ("surf_p", POINTER(c_float)), ("surf_n", POINTER(c_float)), ("surf_link", POINTER(c_int32))]
+                ("surf_p", POINTER(c_float)), ("surf_n", POINTER(c_float)), ("surf_link", POINTER(c_int32)),
+                ("lo", POINTER(c_float)), ("hi", POINTER(c_float)), ("radius", POINTER(c_float))]
 
 
 class FieldParams(Structure):
-    _fields_ = [("inv_h", c_float), ("n_bins", c_int32), ("bin_dirs", POINTER(c_float))]
+    _fields_ = [("inv_h", c_float), ("n_bins", c_int32), ("bin_dirs", POINTER(c_float)), ("want_rep", c_int32)]
+
+
+class IkParams(Structure):
+    _fields_ = [("beta", c_float), ("lambda_", c_float), ("n_phase1", c_int32), ("n_rounds", c_int32),
+                ("n_phase2", c_int32), ("tol_pos", c_float), ("tol_cos", c_float)]
+
+
+class RealizeParams(Structure):
+    _fields_ = [("pen_margin", c_float), ("axis_step", c_float), ("seed", c_uint64)]
 
 
 class FieldInfo(Structure):
@@ -137,6 +151,17 @@ _cf_plan_run_host = _sig("cf_plan_run_host", [c_void_p, c_void_p, c_void_p, c_in
                                               POINTER(ScoreParams), c_void_p, c_void_p, c_void_p, POINTER(c_int64),
                                               c_void_p])
 _cf_plan_destroy = _sig("cf_plan_destroy", [c_void_p])
+_cf_field_rep_slots = _sig("cf_field_rep_slots", [c_void_p, POINTER(c_int64)])
+_cf_field_copy_rep = _sig("cf_field_copy_rep", [c_void_p, POINTER(c_uint64), POINTER(c_uint32), c_int64])
+_cf_ik_dls = _sig("cf_ik_dls", [c_void_p, POINTER(Points), c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p,
+                                c_void_p, POINTER(IkParams), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                c_void_p, c_void_p])
+_cf_sdf_build = _sig("cf_sdf_build", [POINTER(Points), POINTER(c_float), c_float, POINTER(c_int32), c_void_p,
+                                      POINTER(c_void_p)])
+_cf_sdf_copy = _sig("cf_sdf_copy", [c_void_p, POINTER(c_float), c_int64])
+_cf_sdf_destroy = _sig("cf_sdf_destroy", [c_void_p])
+_cf_realize = _sig("cf_realize", [c_void_p, c_void_p, c_void_p, c_int32, c_int32, POINTER(RealizeParams), c_void_p,
+                                  c_void_p, c_void_p, c_void_p, c_void_p, c_void_p])
 _cf_last_error = _sig("cf_last_error", [], c_char_p)
 _cf_device_status = _sig("cf_device_status", [POINTER(c_uint32)])
 _cf_device_counters = _sig("cf_device_counters", [POINTER(c_uint64), c_int])
@@ -146,7 +171,8 @@ EXPORTED = ["cf_build", "cf_field_get_info", "cf_field_copy_table", "cf_field_de
             "cf_plan_destroy", "cf_last_error", "cf_device_status", "cf_device_counters", "cf_score_tuples_noalloc",
             "cf_sample_tuples", "cf_batch_create", "cf_batch_run", "cf_batch_launches", "cf_batch_destroy",
             "cf_engine_create", "cf_engine_submit", "cf_engine_poll", "cf_engine_result_free", "cf_engine_get_stats",
-            "cf_engine_drain", "cf_engine_destroy"]
+            "cf_engine_drain", "cf_engine_destroy", "cf_field_rep_slots", "cf_field_copy_rep", "cf_ik_dls",
+            "cf_sdf_build", "cf_sdf_copy", "cf_sdf_destroy", "cf_realize"]
 
 
 def _check(rc: int):
@@ -212,6 +238,17 @@ class Field:
         _check(_cf_field_copy_table(self._h, out.ctypes.data_as(POINTER(c_uint32)), out.size))
         return out
 
+    def rep(self):
+        """Representative table (want_rep): (keys uint64 [slots], vals uint32 [slots]); empty slots have key ~0."""
+        n = c_int64()
+        _check(_cf_field_rep_slots(self._h, byref(n)))
+        keys = np.zeros(int(n.value), np.uint64)
+        vals = np.zeros(int(n.value), np.uint32)
+        if n.value:
+            _check(_cf_field_copy_rep(self._h, keys.ctypes.data_as(POINTER(c_uint64)),
+                                      vals.ctypes.data_as(POINTER(c_uint32)), keys.size))
+        return keys, vals
+
     def save(self, path: str):
         _check(_cf_field_save(self._h, path.encode()))
 
@@ -233,17 +270,25 @@ class Field:
             pass
 
 
-def build(hand, inv_h, bin_dirs, q, stream=None) -> Field:
+def build(hand, inv_h, bin_dirs, q, stream=None, want_rep: bool = False) -> Field:
     """cf_build: hand is any object with base/axis/offset/surf_p/surf_n/surf_link
-    arrays (host), q a [F, J, S] float32 CUDA tensor of joint samples."""
+    arrays (host) and optionally lo/hi/radius, q a [F, J, S] float32 CUDA tensor
+    of joint samples.  want_rep keeps the reverse-lookup table (needs limits)."""
     import torch
     keep = [_np(hand.base, np.float32), _np(hand.axis, np.float32), _np(hand.offset, np.float32),
             _np(hand.surf_p, np.float32), _np(hand.surf_n, np.float32), _np(hand.surf_link, np.int32)]
     F, J, M = int(keep[0].shape[0]), int(keep[1].shape[1]), int(keep[3].shape[1])
+    lim = None
+    if getattr(hand, "lo", None) is not None:
+        lim = [_np(hand.lo, np.float32), _np(hand.hi, np.float32), _np(hand.radius, np.float32)]
+        for a in lim:
+            if a.shape != (F, J):
+                raise ValueError(f"lo / hi / radius must be [F={F}, J={J}]")
     hd = HandDesc(F, J, M, _fp(keep[0]), _fp(keep[1]), _fp(keep[2]), _fp(keep[3]), _fp(keep[4]),
-                  keep[5].ctypes.data_as(POINTER(c_int32)))
+                  keep[5].ctypes.data_as(POINTER(c_int32)),
+                  *([_fp(a) for a in lim] if lim else [None, None, None]))
     dirs = _np(bin_dirs, np.float32)
-    prm = FieldParams(float(np.float32(inv_h)), int(dirs.shape[0]), _fp(dirs))
+    prm = FieldParams(float(np.float32(inv_h)), int(dirs.shape[0]), _fp(dirs), 1 if want_rep else 0)
     qp = _dev(q, torch.float32, "q")
     if q.dim() != 3 or tuple(q.shape[:2]) != (F, J):
         raise ValueError(f"q must be [F={F}, J={J}, S]")
@@ -497,6 +542,100 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def ik_params(beta=0.01, lam=1e-4, n_phase1=16, n_rounds=4, n_phase2=4, tol_pos=2e-3, tol_deg=20.0) -> IkParams:
+    return IkParams(float(beta), float(lam), int(n_phase1), int(n_rounds), int(n_phase2), float(tol_pos),
+                    float(np.float32(np.cos(np.radians(tol_deg)))))
+
+
+def ik_dls(field: Field, soa, poses, T: int, k: int, tuples, fingers, accept, prm: IkParams, stream=None):
+    """cf_ik_dls over n = tuples.numel() // k slots -> dict of q [n,F,J] f32, used [n,F,J] u8,
+    contacts [6, n*k] f32 (object frame), rtuples [n,k] i32, resid [n,k,2] f32, ok [n] u8."""
+    import torch
+    inf = field.info()
+    F, J = int(inf.n_fingers), int(inf.n_joints)
+    obj = points_struct(soa)
+    n = int(tuples.numel()) // int(k)
+    dev = soa.device
+    out = dict(q=torch.empty((n, F, J), dtype=torch.float32, device=dev),
+               used=torch.empty((n, F, J), dtype=torch.uint8, device=dev),
+               contacts=torch.empty((6, n * k), dtype=torch.float32, device=dev),
+               rtuples=torch.empty((n, k), dtype=torch.int32, device=dev),
+               resid=torch.empty((n, k, 2), dtype=torch.float32, device=dev),
+               ok=torch.empty((n,), dtype=torch.uint8, device=dev))
+    ap = _dev(accept, torch.uint8, "accept") if accept is not None else None
+    _check(_cf_ik_dls(field.handle, byref(obj), _dev(poses, torch.float32, "poses"), n, int(T), int(k),
+                      _dev(tuples, torch.int32, "tuples"), _dev(fingers, torch.uint8, "fingers"), ap, byref(prm),
+                      _dev(out["q"], torch.float32, "q"), _dev(out["used"], torch.uint8, "used"),
+                      _dev(out["contacts"], torch.float32, "contacts"), _dev(out["rtuples"], torch.int32, "rtuples"),
+                      _dev(out["resid"], torch.float32, "resid"), _dev(out["ok"], torch.uint8, "ok"),
+                      _stream(stream)))
+    return out
+
+
+def sdf_box(soa_host, h: float, margin: float):
+    """Grid box of cf_sdf_build for host points [6, N]: lo = min - margin, dims to cover max + margin."""
+    p = np.asarray(soa_host, np.float64)[:3]
+    lo = (p.min(axis=1) - margin).astype(np.float32)
+    hi = p.max(axis=1) + margin
+    dims = (np.ceil((hi - lo.astype(np.float64)) / float(np.float32(h))).astype(np.int64) + 1).astype(np.int32)
+    return lo, float(np.float32(h)), dims
+
+
+class Sdf:
+    """Library-owned object SDF grid (cf_sdf)."""
+
+    def __init__(self, soa, lo, h: float, dims, stream=None):
+        obj = points_struct(soa)
+        lo_ = _np(lo, np.float32)
+        dims_ = _np(dims, np.int32)
+        if lo_.shape != (3,) or dims_.shape != (3,):
+            raise ValueError("lo and dims must have 3 entries")
+        self.lo, self.h, self.dims = lo_, float(np.float32(h)), dims_
+        hh = c_void_p()
+        _check(_cf_sdf_build(byref(obj), _fp(lo_), float(h), dims_.ctypes.data_as(POINTER(c_int32)),
+                             _stream(stream), byref(hh)))
+        self._h = hh
+
+    @property
+    def handle(self):
+        return self._h
+
+    def grid(self) -> np.ndarray:
+        """[dims[2], dims[1], dims[0]] float32 (x fastest)."""
+        n = int(np.prod(self.dims.astype(np.int64)))
+        out = np.zeros(n, np.float32)
+        _check(_cf_sdf_copy(self._h, _fp(out), n))
+        return out.reshape(int(self.dims[2]), int(self.dims[1]), int(self.dims[0]))
+
+    def close(self):
+        if self._h:
+            _cf_sdf_destroy(self._h)
+            self._h = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def realize_params(pen_margin=2e-3, axis_step=1.25e-3, seed=0) -> RealizeParams:
+    return RealizeParams(float(pen_margin), float(axis_step), int(seed))
+
+
+def realize(field: Field, sdf: Sdf, poses, T: int, q, used, gate_a, gate_b, prm: RealizeParams, stream=None):
+    """cf_realize: fills the free joints of q in place; returns flags [n] uint8 (0 = realised grasp)."""
+    import torch
+    n = int(q.shape[0])
+    flags = torch.empty((n,), dtype=torch.uint8, device=q.device)
+    ga = _dev(gate_a, torch.uint8, "gate_a") if gate_a is not None else None
+    gb = _dev(gate_b, torch.uint8, "gate_b") if gate_b is not None else None
+    _check(_cf_realize(field.handle, sdf.handle, _dev(poses, torch.float32, "poses"), n, int(T), byref(prm), ga, gb,
+                       _dev(q, torch.float32, "q"), _dev(used, torch.uint8, "used"),
+                       _dev(flags, torch.uint8, "flags"), _stream(stream)))
+    return flags
 
 
 def device_status() -> int:

@@ -139,6 +139,8 @@ void field_release(cf_field *fd) {
     if (fd->d_block) cudaFreeAsync(fd->d_block, fd->st);
     if (fd->d_table) cudaFreeAsync(fd->d_table, fd->st);
     if (fd->d_cand) cudaFreeAsync(fd->d_cand, fd->st);
+    if (fd->d_rep) cudaFreeAsync(fd->d_rep, fd->st);
+    if (fd->d_qs) cudaFreeAsync(fd->d_qs, fd->st);
     if (fd->ev0) cudaEventDestroy(fd->ev0);
     if (fd->ev1) cudaEventDestroy(fd->ev1);
     delete fd;
@@ -157,6 +159,15 @@ int check_hand(const cf_hand_desc *h) {
     for (int i = 0; i < h->n_fingers * h->n_surf; ++i)
         if (h->surf_link[i] < 0 || h->surf_link[i] >= h->n_joints)
             return fail(CF_EINVAL, "surf_link[%d]=%d not in [0,%d)", i, h->surf_link[i], h->n_joints);
+    if ((h->lo != nullptr) != (h->hi != nullptr) || (h->lo != nullptr) != (h->radius != nullptr))
+        return fail(CF_EINVAL, "lo, hi and radius must be given together");
+    if (h->lo)
+        for (int i = 0; i < h->n_fingers * h->n_joints; ++i) {
+            if (!(h->lo[i] <= h->hi[i]) || !isfinite(h->lo[i]) || !isfinite(h->hi[i]))
+                return fail(CF_EINVAL, "joint %d: limits [%g, %g] are not a finite interval", i, h->lo[i], h->hi[i]);
+            if (!(h->radius[i] >= 0.f) || !isfinite(h->radius[i]))
+                return fail(CF_EINVAL, "joint %d: radius %g must be finite and >= 0", i, h->radius[i]);
+        }
     return CF_OK;
 }
 
@@ -209,16 +220,32 @@ extern "C" int cf_build(const cf_hand_desc *hand, const cf_field_params *prm, co
     CF_TRY(cudaGetDevice(&fd->dev), "cudaGetDevice");
     if ((rc = geom_from_params(fd, prm)) || (rc = setup_candidates(fd))) { field_release(fd); return rc; }
 
-    // host staging of the hand block: base | axis | offset | surf (sorted by link) | link ranges | bounds init
+    const bool want_rep = prm->want_rep != 0;
+    if (want_rep && !hand->lo) { field_release(fd); return fail(CF_EINVAL, "want_rep needs the joint limits"); }
+    if (want_rep && (uint64_t)n_samples * (uint64_t)M >= 0xffffffffull) {
+        field_release(fd);
+        return fail(CF_EINVAL, "want_rep: n_samples * n_surf = %lld does not fit 32 bits",
+                    (long long)n_samples * M);
+    }
+    fd->has_limits = hand->lo != nullptr;
+
+    // host staging of the hand block: base | axis | offset | surf (sorted by link) | lo | hi | radius |
+    // link ranges | sorted position of each surface point | bounds init
     const size_t n_base = (size_t)F * 12, n_axis = (size_t)F * J * 3, n_surf = (size_t)F * M * 8;
-    const size_t n_lb = (size_t)F * (J + 1), n_bnd = (size_t)6 * F;
-    const size_t bytes = sizeof(float) * (n_base + 2 * n_axis + n_surf) + sizeof(int) * (n_lb + n_bnd);
+    const size_t n_fj = (size_t)F * J, n_lb = (size_t)F * (J + 1), n_so = (size_t)F * M, n_bnd = (size_t)6 * F;
+    const size_t bytes = sizeof(float) * (n_base + 2 * n_axis + n_surf + 3 * n_fj) + sizeof(int) * (n_lb + n_so + n_bnd);
     std::vector<char> stage(bytes, 0);
     float *h_base = (float *)stage.data(), *h_axis = h_base + n_base, *h_off = h_axis + n_axis, *h_surf = h_off + n_axis;
-    int *h_lb = (int *)(h_surf + n_surf), *h_bnd = h_lb + n_lb;
+    float *h_lo = h_surf + n_surf, *h_hi = h_lo + n_fj, *h_rad = h_hi + n_fj;
+    int *h_lb = (int *)(h_rad + n_fj), *h_so = h_lb + n_lb, *h_bnd = h_so + n_so;
     memcpy(h_base, hand->base, sizeof(float) * n_base);
     memcpy(h_axis, hand->axis, sizeof(float) * n_axis);
     memcpy(h_off, hand->offset, sizeof(float) * n_axis);
+    if (hand->lo) {
+        memcpy(h_lo, hand->lo, sizeof(float) * n_fj);
+        memcpy(h_hi, hand->hi, sizeof(float) * n_fj);
+        memcpy(h_rad, hand->radius, sizeof(float) * n_fj);
+    }
     for (int f = 0; f < F; ++f) {
         std::vector<int> order(M);
         for (int m = 0; m < M; ++m) order[m] = m;
@@ -232,6 +259,8 @@ extern "C" int cf_build(const cf_hand_desc *hand, const cf_field_params *prm, co
                 d[3 + c] = hand->surf_n[((size_t)f * M + src) * 3 + c];
             }
             d[6] = (float)lk[src];
+            d[7] = (float)src;  // original index (exact: M <= CF_MAX_SURF)
+            h_so[(size_t)f * M + src] = m;
         }
         for (int l = 0; l <= J; ++l) {
             int c = 0;
@@ -242,8 +271,16 @@ extern "C" int cf_build(const cf_hand_desc *hand, const cf_field_params *prm, co
     }
     if ((rc = pool_alloc(&fd->d_block, bytes, st, "alloc hand block"))) { field_release(fd); return rc; }
     float *d_base = (float *)fd->d_block, *d_axis = d_base + n_base, *d_off = d_axis + n_axis, *d_surf = d_off + n_axis;
-    int *d_lb = (int *)(d_surf + n_surf), *d_bounds = d_lb + n_lb;
-    fd->hand = HandDev{F, J, M, d_base, d_axis, d_off, d_surf, d_lb};
+    float *d_lo = d_surf + n_surf, *d_hi = d_lo + n_fj, *d_rad = d_hi + n_fj;
+    int *d_lb = (int *)(d_rad + n_fj), *d_so = d_lb + n_lb, *d_bounds = d_so + n_so;
+    fd->hand = HandDev{F, J, M, d_base, d_axis, d_off, d_surf, d_lb, hand->lo ? d_lo : nullptr,
+                       hand->lo ? d_hi : nullptr, d_rad, d_so};
+    if (hand->lo) {
+        fd->h_lo.assign(hand->lo, hand->lo + n_fj);
+        fd->h_hi.assign(hand->hi, hand->hi + n_fj);
+        fd->h_radius.assign(hand->radius, hand->radius + n_fj);
+    }
+    fd->h_offset.assign(hand->offset, hand->offset + n_axis);
     float *d_links = nullptr;
     auto bail = [&](cudaError_t err, const char *what) {
         if (d_links) cudaFreeAsync(d_links, st);
@@ -309,10 +346,54 @@ extern "C" int cf_build(const cf_hand_desc *hand, const cf_field_params *prm, co
         CF_STEP(cudaMemsetAsync(fd->d_table, 0, sizeof(uint32_t) * (size_t)words, st), "memset table");
         CF_STEP(launch_fk_bin(fd->hand, d_links, n_samples, fd->geom, fd->d_table, ds.status, st), "launch k_fk_bin");
     }
+    int64_t rep_bytes = 0;
+    if (want_rep) {
+        // keep the joint samples (reverse lookup starts IK from them) and build the representative table:
+        // count the codes (one more wait), size the hash at load <= 1/2, then pass 3
+        const size_t qbytes = sizeof(float) * (size_t)F * J * n_samples;
+        if (qbytes) {
+            if ((rc = pool_alloc((void **)&fd->d_qs, qbytes, st, "alloc samples"))) {
+                if (d_links) cudaFreeAsync(d_links, st);
+                field_release(fd);
+                return rc;
+            }
+            CF_STEP(cudaMemcpyAsync(fd->d_qs, d_q, qbytes, cudaMemcpyDeviceToDevice, st), "copy samples");
+        }
+        unsigned long long *d_cnt = nullptr;
+        if ((rc = pool_alloc((void **)&d_cnt, sizeof(unsigned long long), st, "alloc count"))) {
+            if (d_links) cudaFreeAsync(d_links, st);
+            field_release(fd);
+            return rc;
+        }
+        CF_STEP(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), st), "memset count");
+        CF_STEP(launch_popcount(fd->d_table, words, d_cnt, st), "launch k_popcount");
+        unsigned long long n_codes = 0;
+        CF_STEP(cudaMemcpyAsync(&n_codes, d_cnt, sizeof n_codes, cudaMemcpyDeviceToHost, st), "copy count");
+        CF_STEP(cudaFreeAsync(d_cnt, st), "free count");
+        CF_STEP(cudaStreamSynchronize(st), "k_popcount");
+        int lg = 4;
+        while ((1ull << lg) < 2 * n_codes) ++lg;
+        if (lg > 31) {
+            if (d_links) cudaFreeAsync(d_links, st);
+            field_release(fd);
+            return fail(CF_EINVAL, "%llu field codes: too many for the representative table", n_codes);
+        }
+        const size_t slots = (size_t)1 << lg;
+        rep_bytes = (int64_t)(slots * (sizeof(unsigned long long) + sizeof(uint32_t)));
+        if ((rc = pool_alloc(&fd->d_rep, (size_t)rep_bytes, st, "alloc representative table"))) {
+            if (d_links) cudaFreeAsync(d_links, st);
+            field_release(fd);
+            return rc;
+        }
+        fd->rep = RepTable{(unsigned long long *)fd->d_rep, (uint32_t *)((char *)fd->d_rep + slots * 8), lg};
+        CF_STEP(cudaMemsetAsync(fd->d_rep, 0xff, (size_t)rep_bytes, st), "memset representative table");
+        CF_STEP(launch_fk_rep(fd->hand, d_links, n_samples, fd->geom, fd->rep, ds.status, st), "launch k_fk_rep");
+        rep_bytes += (int64_t)qbytes;
+    }
     if (d_links) CF_STEP(cudaFreeAsync(d_links, st), "free links");
     CF_STEP(cudaEventRecord(fd->ev1, st), "event record");
 #undef CF_STEP
-    fd->device_bytes = (int64_t)bytes + (int64_t)sizeof(uint32_t) * (words + kCandCells);
+    fd->device_bytes = (int64_t)bytes + (int64_t)sizeof(uint32_t) * (words + kCandCells) + rep_bytes;
     *out = fd;
     return CF_OK;
 }
@@ -358,6 +439,24 @@ extern "C" int cf_field_copy_table(const cf_field *fd, uint32_t *host_words, int
     CF_TRY(cudaStreamSynchronize(fd->st), "field stream");
     CF_TRY(cudaMemcpy(host_words, fd->d_table, sizeof(uint32_t) * (size_t)fd->table_words, cudaMemcpyDeviceToHost),
            "copy table");
+    return CF_OK;
+}
+
+extern "C" int cf_field_rep_slots(const cf_field *fd, int64_t *slots) {
+    if (!fd || !slots) return fail(CF_EINVAL, "NULL argument");
+    *slots = fd->d_rep ? ((int64_t)1 << fd->rep.log2_slots) : 0;
+    return CF_OK;
+}
+
+extern "C" int cf_field_copy_rep(const cf_field *fd, uint64_t *host_keys, uint32_t *host_vals, int64_t capacity) {
+    if (!fd) return fail(CF_EINVAL, "field is NULL");
+    if (!fd->d_rep) return fail(CF_EINVAL, "the field was built without want_rep");
+    const int64_t slots = (int64_t)1 << fd->rep.log2_slots;
+    if (!host_keys || !host_vals) return fail(CF_EINVAL, "NULL argument");
+    if (capacity < slots) return fail(CF_EINVAL, "capacity %lld < rep slots %lld", (long long)capacity, (long long)slots);
+    CF_TRY(cudaStreamSynchronize(fd->st), "field stream");
+    CF_TRY(cudaMemcpy(host_keys, fd->rep.keys, sizeof(uint64_t) * (size_t)slots, cudaMemcpyDeviceToHost), "copy rep keys");
+    CF_TRY(cudaMemcpy(host_vals, fd->rep.vals, sizeof(uint32_t) * (size_t)slots, cudaMemcpyDeviceToHost), "copy rep vals");
     return CF_OK;
 }
 
@@ -927,6 +1026,172 @@ extern "C" int cf_plan_destroy(cf_plan *pl) {
     if (!pl) return CF_OK;
     if (pl->d_block) cudaFree(pl->d_block);
     delete pl;
+    return CF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// a6: reverse lookup + DLS IK;  a7: object SDF grid and realization filter
+// ---------------------------------------------------------------------------
+struct cf_sdf {
+    int dev = 0;
+    cudaStream_t st = nullptr;
+    cf::SdfGrid g{};
+    float *d_grid = nullptr;
+    int64_t nodes = 0;
+};
+
+extern "C" int cf_ik_dls(const cf_field *fd, const cf_points *obj, const float *d_poses, int32_t n_slots,
+                         int32_t n_tuples, int32_t k, const int32_t *d_tuples, const uint8_t *d_fingers,
+                         const uint8_t *d_accept, const cf_ik_params *prm, float *d_q, uint8_t *d_used,
+                         float *d_contacts, int32_t *d_rtuples, float *d_resid, uint8_t *d_ok, cf_stream stream) {
+    if (!fd || !prm) return fail(CF_EINVAL, "NULL argument");
+    if (!fd->d_rep || !fd->d_qs || !fd->has_limits)
+        return fail(CF_EINVAL, "the field needs joint limits and a representative table (want_rep)");
+    int rc = check_points(obj);
+    if (rc) return rc;
+    if (n_slots < 0 || n_tuples < 1) return fail(CF_EINVAL, "n_slots < 0 or n_tuples < 1");
+    if (k < 1 || k > CF_MAX_K || k > fd->F) return fail(CF_EINVAL, "k=%d not in [1,min(%d,F)]", k, CF_MAX_K);
+    if (!(prm->lambda > 0.f) || !isfinite(prm->lambda)) return fail(CF_EINVAL, "lambda must be finite and > 0");
+    if (!isfinite(prm->beta) || !isfinite(prm->tol_pos) || !isfinite(prm->tol_cos))
+        return fail(CF_EINVAL, "beta / tolerances must be finite");
+    if (prm->n_phase1 < 0 || prm->n_rounds < 0 || prm->n_phase2 < 0 || prm->n_phase1 > 4096 ||
+        prm->n_rounds > 256 || prm->n_phase2 > 4096)
+        return fail(CF_EINVAL, "iteration counts out of range");
+    if (n_slots == 0) return CF_OK;
+    if (!d_poses || !d_tuples || !d_fingers || !d_q || !d_used || !d_contacts || !d_rtuples || !d_resid || !d_ok)
+        return fail(CF_EINVAL, "array pointer is NULL");
+    DevState ds;
+    if ((rc = device_state(&ds))) return rc;
+    IkArgs a;
+    memset(&a, 0, sizeof a);
+    a.h = fd->hand;
+    a.g = fd->geom;
+    a.rep = fd->rep;
+    a.qs = fd->d_qs;
+    a.S = fd->S;
+    a.obj = *obj;
+    a.poses = d_poses;
+    a.n = n_slots;
+    a.T = n_tuples;
+    a.k = k;
+    a.tuples = d_tuples;
+    a.fingers = d_fingers;
+    a.accept = d_accept;
+    a.beta = prm->beta;
+    a.lambda = prm->lambda;
+    a.tol_pos = prm->tol_pos;
+    a.tol_cos = prm->tol_cos;
+    a.n1 = prm->n_phase1;
+    a.nr = prm->n_rounds;
+    a.n2 = prm->n_phase2;
+    a.q = d_q;
+    a.used = d_used;
+    const size_t nk = (size_t)n_slots * k;
+    for (int i = 0; i < 6; ++i) a.cp[i] = d_contacts + i * nk;
+    a.rtuples = d_rtuples;
+    a.resid = d_resid;
+    a.ok = d_ok;
+    a.status = ds.status;
+    CF_TRY(launch_ik(a, (cudaStream_t)stream), "launch k_ik_dls");
+    return CF_OK;
+}
+
+extern "C" int cf_sdf_build(const cf_points *obj, const float lo[3], float h, const int32_t dims[3],
+                            cf_stream stream, cf_sdf **out) {
+    if (!out || !lo || !dims) return fail(CF_EINVAL, "NULL argument");
+    int rc = check_points(obj);
+    if (rc) return rc;
+    if (!(h > 0.f) || !isfinite(h)) return fail(CF_EINVAL, "h must be finite and > 0");
+    for (int c = 0; c < 3; ++c) {
+        if (!isfinite(lo[c])) return fail(CF_EINVAL, "lo must be finite");
+        if (dims[c] < 2 || dims[c] > 4096) return fail(CF_EINVAL, "dims[%d]=%d not in [2,4096]", c, dims[c]);
+    }
+    const int64_t nodes = (int64_t)dims[0] * dims[1] * dims[2];
+    if (nodes > ((int64_t)1 << 31)) return fail(CF_EINVAL, "%lld grid nodes: too many", (long long)nodes);
+    cf_sdf *s = new cf_sdf();
+    s->st = (cudaStream_t)stream;
+    cudaGetDevice(&s->dev);
+    for (int c = 0; c < 3; ++c) { s->g.lo[c] = lo[c]; s->g.dims[c] = dims[c]; }
+    s->g.h = h;
+    s->g.inv_h = 1.f / h;
+    s->nodes = nodes;
+    if ((rc = pool_alloc((void **)&s->d_grid, sizeof(float) * (size_t)nodes, s->st, "alloc sdf grid"))) {
+        delete s;
+        return rc;
+    }
+    s->g.v = s->d_grid;
+    cudaError_t e = launch_sdf(*obj, s->g, s->d_grid, s->st);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(s->d_grid, s->st);
+        delete s;
+        return cuda_fail(e, "launch k_sdf_build");
+    }
+    *out = s;
+    return CF_OK;
+}
+
+extern "C" int cf_sdf_copy(const cf_sdf *s, float *host, int64_t capacity) {
+    if (!s || !host) return fail(CF_EINVAL, "NULL argument");
+    if (capacity < s->nodes) return fail(CF_EINVAL, "capacity %lld < nodes %lld", (long long)capacity, (long long)s->nodes);
+    CF_TRY(cudaStreamSynchronize(s->st), "sdf stream");
+    CF_TRY(cudaMemcpy(host, s->d_grid, sizeof(float) * (size_t)s->nodes, cudaMemcpyDeviceToHost), "copy sdf");
+    return CF_OK;
+}
+
+extern "C" int cf_sdf_destroy(cf_sdf *s) {
+    if (!s) return CF_OK;
+    if (s->d_grid) cudaFreeAsync(s->d_grid, s->st);
+    delete s;
+    return CF_OK;
+}
+
+extern "C" int cf_realize(const cf_field *fd, const cf_sdf *sdf, const float *d_poses, int32_t n_slots,
+                          int32_t n_tuples, const cf_realize_params *prm, const uint8_t *d_gate_a,
+                          const uint8_t *d_gate_b, float *d_q, const uint8_t *d_used, uint8_t *d_flags,
+                          cf_stream stream) {
+    if (!fd || !sdf || !prm) return fail(CF_EINVAL, "NULL argument");
+    if (!fd->has_limits) return fail(CF_EINVAL, "the field's hand has no joint limits / radii");
+    if (n_slots < 0 || n_tuples < 1) return fail(CF_EINVAL, "n_slots < 0 or n_tuples < 1");
+    if (!(prm->axis_step > 0.f) || !isfinite(prm->axis_step)) return fail(CF_EINVAL, "axis_step must be > 0");
+    if (!isfinite(prm->pen_margin)) return fail(CF_EINVAL, "pen_margin must be finite");
+    if (n_slots == 0) return CF_OK;
+    if (!d_poses || !d_q || !d_used || !d_flags) return fail(CF_EINVAL, "array pointer is NULL");
+    RealizeArgs a;
+    memset(&a, 0, sizeof a);
+    a.h = fd->hand;
+    a.sdf = sdf->g;
+    a.poses = d_poses;
+    a.n = n_slots;
+    a.T = n_tuples;
+    a.gate_a = d_gate_a;
+    a.gate_b = d_gate_b;
+    a.q = d_q;
+    a.used = d_used;
+    a.flags = d_flags;
+    a.pen_margin = prm->pen_margin;
+    a.seed_lo = (uint32_t)prm->seed;
+    a.seed_hi = (uint32_t)(prm->seed >> 32);
+    // capsules: links of positive radius and length, in (finger, link) order; axis samples at s / ns
+    const int F = fd->F, J = fd->J;
+    for (int f = 0; f < F; ++f)
+        for (int j = 0; j < J; ++j) {
+            const float *o = &fd->h_offset[3 * ((size_t)f * J + j)];
+            const double len = sqrt((double)o[0] * o[0] + (double)o[1] * o[1] + (double)o[2] * o[2]);
+            const float r = fd->h_radius[(size_t)f * J + j];
+            if (!(r > 0.f) || !(len > 0.0)) {
+                a.cap_of[f * J + j] = -1;
+                continue;
+            }
+            const double ns = std::max(1.0, ceil(len / (double)prm->axis_step));
+            if (ns > 32767.0) return fail(CF_EINVAL, "axis_step too small: %g samples on one link", ns);
+            const int cid = a.n_caps++;
+            a.cap_of[f * J + j] = (int8_t)cid;
+            a.cap_f[cid] = (uint8_t)f;
+            a.cap_ns[cid] = (int16_t)ns;
+            a.cap_r[cid] = r;
+        }
+    for (int i = F * J; i < kMaxCapsules; ++i) a.cap_of[i] = -1;
+    CF_TRY(launch_realize(a, (cudaStream_t)stream), "launch k_realize");
     return CF_OK;
 }
 

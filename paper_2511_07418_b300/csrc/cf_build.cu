@@ -22,6 +22,8 @@
 // from the same cube-map candidate lists as the query when they are valid.
 #include <limits.h>
 
+#include <algorithm>
+
 #include "cf_internal.cuh"
 
 namespace cf {
@@ -181,7 +183,7 @@ __global__ void __launch_bounds__(kThreads) k_fk_bin(HandDev h, const float *__r
             const unsigned uy = (unsigned)(cell_floor(y, g.inv_h, g.clamp) - ly);
             const unsigned uz = (unsigned)(cell_floor(z, g.inv_h, g.clamp) - lz);
             if (ux >= dx || uy >= dy || uz >= dz) {  // cannot happen: extents come from the same arithmetic
-                atomicOr(status, 0x80000000u);
+                atomicOr(status, CF_DEV_BIN_RANGE);
                 continue;
             }
             uint32_t *word = tab + (((size_t)uz * dy + uy) * dx + ux) * g.rw;
@@ -206,6 +208,75 @@ __global__ void __launch_bounds__(kThreads) k_fk_bin(HandDev h, const float *__r
         default: return cudaErrorInvalidValue;         \
     }
 
+__global__ void k_popcount(const uint32_t *__restrict__ table, long long words, unsigned long long *count) {
+    unsigned long long c = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < words; i += (long long)gridDim.x * blockDim.x)
+        c += __popc(__ldg(table + i));
+    c = __reduce_add_sync(0xffffffffu, (unsigned)c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+// Pass 3 (reverse lookup): every contact vector offers s * M + m (original m)
+// for its code; the table keeps the smallest.  Open addressing, linear probing.
+template <int J>
+__global__ void __launch_bounds__(kThreads) k_fk_rep(HandDev h, const float *__restrict__ links, int S, FieldGeom g,
+                                                     RepTable t, unsigned int *status) {
+    extern __shared__ float s_surf[];
+    __shared__ int s_lb[CF_MAX_JOINTS + 1];
+    const int f = blockIdx.y;
+    stage_surface(h, f, s_surf, s_lb);
+    __syncthreads();
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    float R[J][9], tt[J][3];
+#pragma unroll
+    for (int l = 0; l < J; ++l) {
+        const float *lk = links + ((size_t)(f * J + l) * 12) * S + s;
+#pragma unroll
+        for (int e = 0; e < 9; ++e) R[l][e] = __ldg(lk + (size_t)e * S);
+#pragma unroll
+        for (int e = 0; e < 3; ++e) tt[l][e] = __ldg(lk + (size_t)(9 + e) * S);
+    }
+    const unsigned mask = (1u << t.log2_slots) - 1u;
+#pragma unroll
+    for (int l = 0; l < J; ++l) {
+        for (int m = s_lb[l]; m < s_lb[l + 1]; ++m) {
+            const float *sp = s_surf + 8 * m;
+            const float x = xf_row(R[l][0], R[l][1], R[l][2], tt[l][0], sp[0], sp[1], sp[2]);
+            const float y = xf_row(R[l][3], R[l][4], R[l][5], tt[l][1], sp[0], sp[1], sp[2]);
+            const float z = xf_row(R[l][6], R[l][7], R[l][8], tt[l][2], sp[0], sp[1], sp[2]);
+            const float nx = rot_row(R[l][0], R[l][1], R[l][2], sp[3], sp[4], sp[5]);
+            const float ny = rot_row(R[l][3], R[l][4], R[l][5], sp[3], sp[4], sp[5]);
+            const float nz = rot_row(R[l][6], R[l][7], R[l][8], sp[3], sp[4], sp[5]);
+            int bin = 0;
+            float best = -INFINITY;
+            for (int b = 0; b < g.B; ++b) {
+                const float sc = __fmaf_rn(g.dirs[b][2], nz, __fmaf_rn(g.dirs[b][1], ny, __fmul_rn(g.dirs[b][0], nx)));
+                if (sc > best) { best = sc; bin = b; }
+            }
+            const unsigned ux = (unsigned)(cell_floor(x, g.inv_h, g.clamp) - g.lo[0]);
+            const unsigned uy = (unsigned)(cell_floor(y, g.inv_h, g.clamp) - g.lo[1]);
+            const unsigned uz = (unsigned)(cell_floor(z, g.inv_h, g.clamp) - g.lo[2]);
+            if (ux >= (unsigned)g.dims[0] || uy >= (unsigned)g.dims[1] || uz >= (unsigned)g.dims[2]) continue;
+            const unsigned long long word = (((unsigned long long)uz * g.dims[1] + uy) * g.dims[0] + ux) * g.rw + f / g.fpw;
+            const unsigned long long key = word * 32ull + (unsigned)((f % g.fpw) * g.bits + bin);
+            const uint32_t val = (uint32_t)s * (uint32_t)h.M + (uint32_t)sp[7];
+            unsigned hh = rep_hash(key, t.log2_slots);
+            bool placed = false;
+            for (int probe = 0; probe <= (int)mask; ++probe, hh = (hh + 1) & mask) {
+                unsigned long long prev = __ldcg(t.keys + hh);
+                if (prev == kRepEmpty) prev = atomicCAS(t.keys + hh, kRepEmpty, key);
+                if (prev == kRepEmpty || prev == key) {
+                    if (val < __ldcg(t.vals + hh)) atomicMin(t.vals + hh, val);  // most samples repeat a code
+                    placed = true;
+                    break;
+                }
+            }
+            if (!placed) atomicOr(status, CF_DEV_REP_FULL);
+        }
+    }
+}
+
 cudaError_t launch_fk_cell_bounds(const HandDev &h, const float *q, int S, float inv_h, float clamp, int *bounds,
                                   float *links, cudaStream_t st) {
     if (S <= 0) return cudaSuccess;
@@ -225,6 +296,22 @@ cudaError_t launch_fk_bin(const HandDev &h, const float *links, int S, const Fie
     } else {
         CF_J_DISPATCH(h.J, (k_fk_bin<JJ, false><<<grid, kThreads, smem, st>>>(h, links, S, g, table, status)));
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_popcount(const uint32_t *table, long long words, unsigned long long *count, cudaStream_t st) {
+    if (words <= 0) return cudaSuccess;
+    const long long blocks = std::min<long long>((words + kThreads - 1) / kThreads, 4096);
+    k_popcount<<<(unsigned)blocks, kThreads, 0, st>>>(table, words, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fk_rep(const HandDev &h, const float *links, int S, const FieldGeom &g, RepTable t,
+                          unsigned int *status, cudaStream_t st) {
+    if (S <= 0) return cudaSuccess;
+    const dim3 grid((S + kThreads - 1) / kThreads, h.F);
+    const size_t smem = sizeof(float) * 8 * h.M;
+    CF_J_DISPATCH(h.J, (k_fk_rep<JJ><<<grid, kThreads, smem, st>>>(h, links, S, g, t, status)));
     return cudaGetLastError();
 }
 

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "cf.h"
 
@@ -23,9 +24,36 @@ struct HandDev {
     const float *base;     // [F][12]
     const float *axis;     // [F][J][3]
     const float *offset;   // [F][J][3]
-    const float *surf;     // [F][M][8]
+    const float *surf;     // [F][M][8]: p, n, link, original index (sorted by link)
     const int *link_begin; // [F][J + 1]
+    const float *lo, *hi;  // [F][J] joint limits (NULL when not given)
+    const float *radius;   // [F][J]
+    const int *sorted_of;  // [F][M]: sorted position of original surface point m
 };
+
+// Representative hash: key = record word index * 32 + bit, value = min s*M + m.
+constexpr unsigned long long kRepEmpty = ~0ull;
+struct RepTable {
+    unsigned long long *keys;
+    uint32_t *vals;
+    int log2_slots;
+};
+
+__device__ __forceinline__ unsigned rep_hash(unsigned long long key, int log2_slots) {
+    return (unsigned)((key * 0x9E3779B97F4A7C15ull) >> (64 - log2_slots));
+}
+
+// value for key, or 0xffffffff when absent
+__device__ __forceinline__ uint32_t rep_lookup(const RepTable &t, unsigned long long key) {
+    const unsigned mask = (1u << t.log2_slots) - 1u;
+    unsigned h = rep_hash(key, t.log2_slots);
+    for (int probe = 0; probe <= (int)mask; ++probe, h = (h + 1) & mask) {
+        const unsigned long long k = __ldg(t.keys + h);
+        if (k == key) return __ldg(t.vals + h);
+        if (k == kRepEmpty) return 0xffffffffu;
+    }
+    return 0xffffffffu;
+}
 
 // Normal-bin candidate table: a cube map of 6 faces x kCandG x kCandG cells
 // over the unit sphere.  Each cell lists, ascending, every bin that can be the
@@ -128,6 +156,63 @@ cudaError_t launch_fk_cell_bounds(const HandDev &h, const float *q, int S, float
                                   int *bounds, float *links, cudaStream_t st);
 cudaError_t launch_fk_bin(const HandDev &h, const float *links, int S, const FieldGeom &g, uint32_t *table,
                           unsigned int *status, cudaStream_t st);
+// ---- a6 / a7: reverse lookup + DLS IK, object SDF grid, realization ----------
+struct IkArgs {
+    HandDev h;
+    FieldGeom g;
+    RepTable rep;
+    const float *qs;  // field joint samples [F][J][S]
+    int S;
+    cf_points obj;
+    const float *poses;
+    int n, T, k;
+    const int32_t *tuples;
+    const uint8_t *fingers;
+    const uint8_t *accept;
+    float beta, lambda, tol_pos, tol_cos;
+    int n1, nr, n2;
+    float *q;
+    uint8_t *used;
+    float *cp[6];     // realised contacts, object frame: px py pz nx ny nz [n * k]
+    int32_t *rtuples;
+    float *resid;     // [n][k][2]: distance, cosine
+    uint8_t *ok;
+    unsigned int *status;
+};
+
+struct SdfGrid {
+    const float *v;
+    float lo[3];
+    float h, inv_h;
+    int dims[3];
+};
+
+constexpr int kMaxCapsules = CF_MAX_FINGERS * CF_MAX_JOINTS;
+struct RealizeArgs {
+    HandDev h;
+    SdfGrid sdf;
+    const float *poses;
+    int n, T;
+    const uint8_t *gate_a, *gate_b;
+    float *q;
+    const uint8_t *used;
+    uint8_t *flags;
+    float pen_margin;
+    uint32_t seed_lo, seed_hi;
+    int n_caps;
+    int8_t cap_of[kMaxCapsules];   // capsule id of (f, j), -1 when link j of finger f has none
+    uint8_t cap_f[kMaxCapsules];
+    int16_t cap_ns[kMaxCapsules];  // axis intervals: samples at s / ns, s = 0..ns
+    float cap_r[kMaxCapsules];
+};
+
+cudaError_t launch_ik(const IkArgs &a, cudaStream_t st);
+cudaError_t launch_sdf(const cf_points &obj, const SdfGrid &g, float *grid, cudaStream_t st);
+cudaError_t launch_realize(const RealizeArgs &a, cudaStream_t st);
+
+cudaError_t launch_popcount(const uint32_t *table, long long words, unsigned long long *count, cudaStream_t st);
+cudaError_t launch_fk_rep(const HandDev &h, const float *links, int S, const FieldGeom &g, RepTable t,
+                          unsigned int *status, cudaStream_t st);
 cudaError_t launch_query(const FieldGeom &g, const uint32_t *table, const cf_points &obj, const float *poses,
                          int P, uint32_t *masks, uint32_t *counts, cudaStream_t st);
 
@@ -212,4 +297,9 @@ struct cf_field {
     int64_t device_bytes = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     float build_ms = -1.f;
+    cf::RepTable rep{nullptr, nullptr, 0};  // reverse-lookup table (want_rep)
+    void *d_rep = nullptr;
+    float *d_qs = nullptr;                  // joint samples [F][J][S] (kept with the representative table)
+    bool has_limits = false;
+    std::vector<float> h_lo, h_hi, h_radius, h_offset;  // host copies for realization planning
 };

@@ -1,0 +1,264 @@
+"""GPU-vs-oracle parity of the kinematics rows (Sec. 4.5 reverse lookup + DLS
+IK, Sec. 4.6 post-processing), through the C ABI.
+
+Inputs are the oracle's own: its field, masks and sampled tuples feed both the
+library and the FP64 oracle.
+
+Acceptance rule.
+ - Representative table: bit-exact (same codes, same smallest s * M + m).
+ - IK: the kernel runs in FP32, the oracle in FP64.  A contact is *sensitive*
+   when an oracle re-run with the targets moved by 1e-6 m and the start joints
+   by 1e-6 rad changes its final joints by more than 1e-4 rad, or when its
+   residual lies within 5e-5 m / 2e-4 (cosine) of the success thresholds.
+   Sensitive slots must stay below 5%; every other contact agrees within
+   1e-3 rad (joints), 5e-5 m (residual, realised point), 2e-4 (cosine,
+   realised normal), and every other slot has the same success flag.
+ - SDF grid: within 1e-6 m at nodes whose sign decision the oracle does not
+   flag as ambiguous (a near tie between points that disagree on the side).
+ - Realization: free joints filled bit for bit (the same FP32 operations);
+   flags equal wherever the oracle's decision is clear of its 1e-5 m band.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import kinematics as K
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+TOL_Q, TOL_POS, TOL_COS = 1e-3, 5e-5, 2e-4
+SENS_Q, SENS_POS, SENS_COS = 1e-4, 5e-5, 2e-4
+
+
+@pytest.fixture(scope="module")
+def cf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2511_07418_b300 as cf
+    return cf
+
+
+def _oracle_tuples(w):
+    fd = oracle.Field(w.hand, w.q, w.inv_h, w.bins)
+    soa = w.obj.soa()
+    m, c = fd.query(soa, w.poses)
+    tup, fing = oracle.sample_tuples(m, c, w.obj.N, w.T, w.k, w.seed)
+    valid = (tup.reshape(-1, w.k)[:, 0] >= 0).astype(np.uint8)
+    return soa, tup, fing, valid
+
+
+def _decode_rep(field):
+    keys, vals = field.rep()
+    inf = field.info()
+    sel = keys != np.uint64(0xFFFFFFFFFFFFFFFF)
+    keys, vals = keys[sel].astype(np.int64), vals[sel].astype(np.int64)
+    rw, fpw, bits = int(inf.record_words), int(inf.fingers_per_word), int(inf.bits_per_finger)
+    dx, dy = int(inf.box_dims[0]), int(inf.box_dims[1])
+    lo = [int(v) for v in inf.box_lo]
+    word, bit = keys >> 5, keys & 31
+    f = (word % rw) * fpw + bit // bits
+    b = bit % bits
+    cell = word // rw
+    kx, ky, kz = cell % dx + lo[0], (cell // dx) % dy + lo[1], cell // (dx * dy) + lo[2]
+    return {oracle.pack_code(*v[:5]): int(v[5]) for v in np.stack([f, kx, ky, kz, b, vals], 1).tolist()}
+
+
+@pytest.mark.parametrize("name,S", [("tiny_sphere", 2048), ("hand16_superquadric", 4096)])
+def test_rep_table_bit_exact(cf, name, S):
+    w = synth.workload(name, P=2, S=S)
+    field = cf.build(w.hand, w.inv_h, w.bins, torch.from_numpy(w.q).cuda(), want_rep=True)
+    g = _decode_rep(field)
+    o = {}
+    for f in range(w.hand.F):
+        o.update(oracle.rep_codes(w.hand, w.q, w.inv_h, w.bins, f))
+    assert len(g) == len(o)
+    assert g == o
+    assert cf.device_status() == 0
+
+
+def _ik_both(cf, w, field, soa, tup, fing, valid, prm_kw=None):
+    prm_kw = prm_kw or {}
+    g = cf.ik_dls(field, torch.from_numpy(soa).cuda(), torch.from_numpy(w.poses).cuda(), w.T, w.k,
+                  torch.from_numpy(tup).cuda(), torch.from_numpy(fing).cuda(), torch.from_numpy(valid).cuda(),
+                  cf.ik_params(**prm_kw))
+    torch.cuda.synchronize()
+    g = {k: v.cpu().numpy() for k, v in g.items()}
+    rep = {f: oracle.rep_codes(w.hand, w.q, w.inv_h, w.bins, f) for f in range(w.hand.F)}
+    okw = dict(beta=prm_kw.get("beta", 0.01), lam=prm_kw.get("lam", 1e-4), n_phase1=prm_kw.get("n_phase1", 16),
+               n_rounds=prm_kw.get("n_rounds", 4), n_phase2=prm_kw.get("n_phase2", 4),
+               tol_pos=prm_kw.get("tol_pos", 2e-3), tol_deg=prm_kw.get("tol_deg", 20.0), rep=rep)
+    o = K.ik_dls(w.hand, w.q, w.inv_h, w.bins, soa, w.poses, w.T, w.k, tup, fing, valid, **okw)
+    pr = K.ik_dls(w.hand, w.q, w.inv_h, w.bins, soa, w.poses, w.T, w.k, tup, fing, valid, perturb=1e-6, **okw)
+    return g, o, pr
+
+
+def _sensitive(w, o, pr, tup, fing, valid):
+    n, k = valid.size, w.k
+    tol_pos = 2e-3
+    tol_cos = float(np.float32(math.cos(math.radians(20.0))))
+    f = fing.reshape(n, k).astype(np.int64)
+    sens = np.zeros((n, k), bool)
+    for c in range(k):
+        fc = np.minimum(f[:, c], w.hand.F - 1)
+        dq = np.abs(o["q"][np.arange(n), fc] - pr["q"][np.arange(n), fc]).max(axis=1)
+        sens[:, c] = (dq > SENS_Q) | (np.abs(o["resid"][:, c, 0] - tol_pos) <= SENS_POS) | \
+                     (np.abs(o["resid"][:, c, 1] - tol_cos) <= SENS_COS) | o["miss"][:, c] | pr["miss"][:, c]
+    return sens & valid.astype(bool)[:, None]
+
+
+@pytest.mark.parametrize("name,P,S", [("hand16_superquadric", 6, 8192), ("hand20_tool", 3, 8192),
+                                      ("tiny_sphere", 24, 4096)])
+def test_ik_parity(cf, name, P, S):
+    w = synth.workload(name, P=P, S=S)
+    field = cf.build(w.hand, w.inv_h, w.bins, torch.from_numpy(w.q).cuda(), want_rep=True)
+    soa, tup, fing, valid = _oracle_tuples(w)
+    g, o, pr = _ik_both(cf, w, field, soa, tup, fing, valid)
+    n, k, F = valid.size, w.k, w.hand.F
+    assert cf.device_status() == 0
+    sens_c = _sensitive(w, o, pr, tup, fing, valid)
+    sens = sens_c.any(axis=1)
+    att = valid.astype(bool)
+    assert sens[att].mean() < 0.05, sens[att].mean()
+    clear = att & ~sens
+    # structure: bit-exact
+    assert np.array_equal(g["used"], o["used"])
+    assert np.array_equal(g["ok"][clear], o["ok"][clear])
+    assert np.array_equal(g["ok"][~att], o["ok"][~att]) and not g["ok"][~att].any()
+    e = np.arange(n * k).reshape(n, k)
+    assert np.array_equal(g["rtuples"], np.where(g["ok"][:, None].astype(bool), e, -1))
+    # values of clear contacts
+    fc = fing.reshape(n, k).astype(np.int64)
+    for c in range(k):
+        rows = np.nonzero(clear)[0]
+        gq = g["q"][rows, fc[rows, c]]
+        oq = o["q"][rows, fc[rows, c]]
+        assert np.abs(gq - oq).max(initial=0) <= TOL_Q
+        assert np.abs(g["resid"][rows, c, 0] - o["resid"][rows, c, 0]).max(initial=0) <= TOL_POS
+        assert np.abs(g["resid"][rows, c, 1] - o["resid"][rows, c, 1]).max(initial=0) <= TOL_COS
+        ee = rows * k + c
+        assert np.abs(g["contacts"][:3, ee] - o["contacts"][:3, ee]).max(initial=0) <= TOL_POS
+        assert np.abs(g["contacts"][3:, ee] - o["contacts"][3:, ee]).max(initial=0) <= TOL_COS
+    # rows of fingers without a contact are zero on both sides
+    for u in np.nonzero(att)[0]:
+        free = np.setdiff1d(np.arange(F), fc[u])
+        assert np.all(g["q"][u, free] == 0) and np.all(g["used"][u, free] == 0)
+    # slots not attempted: untouched outputs are defined
+    assert np.all(np.isinf(g["resid"][~att, :, 0])) and np.all(g["resid"][~att, :, 1] == -2)
+    if name != "tiny_sphere":
+        assert o["ok"][att].sum() > 0 and g["ok"][att].sum() > 0
+
+
+def test_ik_edge_cases(cf):
+    w = synth.workload("tiny_sphere", P=2, S=1024)
+    q = torch.from_numpy(w.q).cuda()
+    field = cf.build(w.hand, w.inv_h, w.bins, q, want_rep=True)
+    soa = torch.from_numpy(w.obj.soa()).cuda()
+    poses = torch.from_numpy(w.poses).cuda()
+    k, n = w.k, 5
+    tup = torch.tensor([[0, 1, 2], [-1, 4, 5], [6, 7, 8], [9, 10, 11], [w.obj.N, 1, 2]], dtype=torch.int32).cuda()
+    fing = torch.tensor([[0, 1, 2], [0, 1, 2], [0, 0, 2], [0, 1, 2], [0, 1, 2]], dtype=torch.uint8).cuda()
+    acc = torch.tensor([1, 1, 1, 0, 1], dtype=torch.uint8).cuda()
+    out = cf.ik_dls(field, soa, poses, 8, k, tup, fing, acc, cf.ik_params())
+    torch.cuda.synchronize()
+    ok = out["ok"].cpu().numpy()
+    resid = out["resid"].cpu().numpy()
+    # slot 1: an invalid point id; slot 2: a repeated finger; slot 3: not accepted; slot 4: id out of range
+    for u in (1, 2, 3, 4):
+        assert ok[u] == 0 and np.all(np.isinf(resid[u, :, 0]))
+        assert np.all(out["q"][u].cpu().numpy() == 0) and np.all(out["used"][u].cpu().numpy() == 0)
+        assert np.all(out["rtuples"][u].cpu().numpy() == -1)
+    # slot 0 is attempted; its arbitrary points need not lie in the domains, so a
+    # contact may find no representative (flagged in the device status)
+    assert ok[0] in (0, 1)
+    st = cf.device_status()
+    assert st & ~cf.CF_DEV_REP_MISS == 0
+    # empty call
+    e = torch.empty((0, k), dtype=torch.int32).cuda()
+    out0 = cf.ik_dls(field, soa, poses, 8, k, e, e.to(torch.uint8), None, cf.ik_params())
+    assert out0["ok"].numel() == 0
+    # a field without the representative table cannot drive IK
+    plain = cf.build(w.hand, w.inv_h, w.bins, q)
+    with pytest.raises(cf.CfError):
+        cf.ik_dls(plain, soa, poses, 8, k, tup, fing, acc, cf.ik_params())
+    with pytest.raises(cf.CfError):
+        cf.ik_dls(field, soa, poses, 8, k, tup, fing, acc, cf.ik_params(lam=0.0))
+    assert cf.device_status() == 0
+
+
+@pytest.mark.parametrize("name", ["tiny_sphere", "hand16_superquadric"])
+def test_sdf_parity(cf, name):
+    w = synth.workload(name, P=1, N=2048, S=256)
+    soa = w.obj.soa()
+    lo, h, dims = cf.sdf_box(soa, 0.004, 0.02)
+    sdf = cf.Sdf(torch.from_numpy(soa).cuda(), lo, h, dims)
+    g = sdf.grid()
+    o, amb = K.sdf_grid(soa, lo, h, dims)
+    assert g.shape == o.shape
+    assert amb.mean() < 1e-3
+    assert np.abs(g[~amb] - o[~amb]).max() <= 1e-6
+
+
+def _realize_inputs(w):
+    soa, tup, fing, valid = _oracle_tuples(w)
+    rep = {f: oracle.rep_codes(w.hand, w.q, w.inv_h, w.bins, f) for f in range(w.hand.F)}
+    o = K.ik_dls(w.hand, w.q, w.inv_h, w.bins, soa, w.poses, w.T, w.k, tup, fing, valid, rep=rep)
+    return soa, tup, fing, valid, o
+
+
+@pytest.mark.parametrize("name,P", [("hand16_superquadric", 4), ("hand20_tool", 2)])
+def test_realize_parity(cf, name, P):
+    w = synth.workload(name, P=P, N=2048, S=4096)
+    field = cf.build(w.hand, w.inv_h, w.bins, torch.from_numpy(w.q).cuda(), want_rep=True)
+    soa, tup, fing, valid, o = _realize_inputs(w)
+    lo, h, dims = cf.sdf_box(soa, 0.003, 0.03)
+    sdf = cf.Sdf(torch.from_numpy(soa).cuda(), lo, h, dims)
+    grid, amb = K.sdf_grid(soa, lo, h, dims)
+    q32 = o["q"].astype(np.float32)
+    used = o["used"].astype(np.uint8)
+    step = 0.5 / float(w.inv_h)
+    seed = 77
+    qg = torch.from_numpy(q32.copy()).cuda()
+    flags = cf.realize(field, sdf, torch.from_numpy(w.poses).cuda(), w.T, qg, torch.from_numpy(used).cuda(),
+                       torch.from_numpy(valid).cuda(), None, cf.realize_params(2e-3, step, seed))
+    torch.cuda.synchronize()
+    gq, gf = qg.cpu().numpy(), flags.cpu().numpy()
+    oq, of, oamb = K.realize(w.hand, grid, amb, lo, h, w.poses, w.T, q32, used, valid, None, pen_margin=2e-3,
+                             axis_step=step, seed=seed)
+    assert np.array_equal(gq, oq)  # bit for bit
+    att = valid.astype(bool)
+    assert np.all(gf[~att] == 1)
+    assert oamb[att].mean() < 0.02
+    clear = att & ~oamb
+    assert np.array_equal(gf[clear], of[clear])
+    # the filter does reject and does pass some candidates on this workload
+    assert (of[clear] == 0).any() and (of[clear] != 0).any()
+
+
+def test_realized_rescore_parity(cf):
+    """IK contacts re-scored by the closure LP (tuples_given over the realised
+    contacts): accept flags agree with the oracle's LP on its own contacts."""
+    w = synth.workload("hand20_tool", P=3, S=8192)
+    field = cf.build(w.hand, w.inv_h, w.bins, torch.from_numpy(w.q).cuda(), want_rep=True)
+    soa, tup, fing, valid = _oracle_tuples(w)
+    g, o, pr = _ik_both(cf, w, field, soa, tup, fing, valid)
+    n, k = valid.size, w.k
+    sens = _sensitive(w, o, pr, tup, fing, valid).any(axis=1)
+    prm = cf.score_params(1, k, w.mu, w.K, w.eps, w.obj.centroid, w.obj.rho, w.seed, tuples_given=True)
+    ct = torch.from_numpy(g["contacts"]).cuda()
+    rt = torch.from_numpy(g["rtuples"].astype(np.int32)).cuda().reshape(n, 1, k)
+    _, _, margin, accept = cf.score_tuples(ct, w.hand.F, None, None, prm, tuples=rt)
+    torch.cuda.synchronize()
+    gm, ga = margin.cpu().numpy().reshape(-1), accept.cpu().numpy().reshape(-1)
+    okrows = np.nonzero(o["ok"].astype(bool) & ~sens)[0]
+    assert okrows.size > 0
+    om, oa, _ = oracle.score_tuples(o["contacts"].astype(np.float32), o["rtuples"][okrows].reshape(-1, 1, k),
+                                    w.mu, w.K, w.obj.centroid, w.obj.rho, w.eps)
+    om, oa = om.reshape(-1), oa.reshape(-1)
+    clear = np.abs(om - w.eps) > 2e-3  # contacts differ by <= 5e-5 m: margins by well under this
+    assert np.array_equal(ga[okrows][clear], oa[clear])
+    assert np.all(np.isinf(gm[~g["ok"].astype(bool)]))
