@@ -1092,7 +1092,17 @@ extern "C" int cf_ik_dls(const cf_field *fd, const cf_points *obj, const float *
     a.resid = d_resid;
     a.ok = d_ok;
     a.status = ds.status;
-    CF_TRY(launch_ik(a, (cudaStream_t)stream), "launch k_ik_dls");
+    // scratch: work list of accepted slots + its counter (stream-ordered)
+    cudaStream_t st = (cudaStream_t)stream;
+    void *scratch = nullptr;
+    const size_t list_bytes = (sizeof(int) * (size_t)n_slots + 255) & ~(size_t)255;
+    if ((rc = pool_alloc(&scratch, list_bytes + 256, st, "alloc IK work list"))) return rc;
+    unsigned int *count = (unsigned int *)((char *)scratch + list_bytes);
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned int), st);
+    if (e == cudaSuccess) e = launch_ik(a, (int *)scratch, count, st);
+    cudaError_t e2 = cudaFreeAsync(scratch, st);
+    if (e != cudaSuccess) return cuda_fail(e, "launch k_ik_compact / k_ik_dls");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "free IK work list");
     return CF_OK;
 }
 

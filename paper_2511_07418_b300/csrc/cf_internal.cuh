@@ -206,7 +206,7 @@ struct RealizeArgs {
     float cap_r[kMaxCapsules];
 };
 
-cudaError_t launch_ik(const IkArgs &a, cudaStream_t st);
+cudaError_t launch_ik(const IkArgs &a, int *list, unsigned int *count, cudaStream_t st);
 cudaError_t launch_sdf(const cf_points &obj, const SdfGrid &g, float *grid, cudaStream_t st);
 cudaError_t launch_realize(const RealizeArgs &a, cudaStream_t st);
 

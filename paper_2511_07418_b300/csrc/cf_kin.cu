@@ -168,7 +168,7 @@ __device__ __forceinline__ void dls_step(const IkArgs &a, int f, int l, const fl
         }
     }
     // normal equations (J^T J + lambda I) dq = J^T e, Cholesky in registers
-    float L[J][J], y[J];
+    float L[J][J], y[J], inv[J];
 #pragma unroll
     for (int i = 0; i < J; ++i) {
         y[i] = c1[i][0] * e1[0] + c1[i][1] * e1[1] + c1[i][2] * e1[2] + c2[i][0] * e2[0] + c2[i][1] * e2[1] +
@@ -180,20 +180,25 @@ __device__ __forceinline__ void dls_step(const IkArgs &a, int f, int l, const fl
             if (i == j) s += a.lambda;
 #pragma unroll
             for (int kk = 0; kk < j; ++kk) s -= L[i][kk] * L[j][kk];
-            L[i][j] = (i == j) ? sqrtf(fmaxf(s, 1e-30f)) : s / L[j][j];
+            if (i == j) {
+                L[i][i] = sqrtf(fmaxf(s, 1e-30f));
+                inv[i] = 1.f / L[i][i];
+            } else {
+                L[i][j] = s * inv[j];
+            }
         }
     }
 #pragma unroll
     for (int i = 0; i < J; ++i) {
 #pragma unroll
         for (int kk = 0; kk < i; ++kk) y[i] -= L[i][kk] * y[kk];
-        y[i] /= L[i][i];
+        y[i] *= inv[i];
     }
 #pragma unroll
     for (int i = J - 1; i >= 0; --i) {
 #pragma unroll
         for (int kk = i + 1; kk < J; ++kk) y[i] -= L[kk][i] * y[kk];
-        y[i] /= L[i][i];
+        y[i] *= inv[i];
     }
 #pragma unroll
     for (int j = 0; j < J; ++j) {
@@ -265,22 +270,55 @@ __device__ __forceinline__ void project_capsule(const IkArgs &a, int f, int l, c
     }
 }
 
-// Lanes in groups of k: group g of warp w is tuple slot w * (32 / k) + g,
-// lane c of the group its contact c.
+// Pass 1: accepted slots go to a work list (order irrelevant: every slot
+// writes only its own outputs); the others get their "not attempted" outputs.
+__global__ void __launch_bounds__(256) k_ik_compact(const IkArgs a, int *list, unsigned int *count) {
+    const long long slot = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool in = slot < a.n;
+    const bool acc = in && (!a.accept || a.accept[slot]);
+    const unsigned full = 0xffffffffu;
+    const unsigned bal = __ballot_sync(full, acc);
+    const int lane = threadIdx.x & 31;
+    unsigned base = 0;
+    if (lane == 0 && bal) base = atomicAdd(count, (unsigned)__popc(bal));
+    base = __shfl_sync(full, base, 0);
+    if (acc) list[base + __popc(bal & ((1u << lane) - 1u))] = (int)slot;
+    if (!in || acc) return;
+    const int k = a.k, F = a.h.F, J = a.h.J;
+    for (int c = 0; c < k; ++c) {
+        const size_t e = (size_t)slot * k + c;
+        a.rtuples[e] = -1;
+        a.resid[2 * e] = INFINITY;
+        a.resid[2 * e + 1] = -2.f;
+        for (int i = 0; i < 6; ++i) a.cp[i][e] = 0.f;
+    }
+    a.ok[slot] = 0;
+    for (int i = 0; i < F * J; ++i) {
+        a.q[(size_t)slot * F * J + i] = 0.f;
+        a.used[(size_t)slot * F * J + i] = 0;
+    }
+}
+
+// Pass 2, lanes in groups of k: group g of warp w works on list entry
+// w * (32 / k) + g, lane c of the group on its contact c.
 template <int J>
-__global__ void __launch_bounds__(kIkThreads) k_ik_dls(const IkArgs a) {
+__global__ void __launch_bounds__(kIkThreads) k_ik_dls(const IkArgs a, const int *__restrict__ list,
+                                                       const unsigned int *__restrict__ count) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int k = a.k, G = 32 / k;
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int grp = lane / k, c = lane - grp * k;
-    const long long slot = gw * G + grp;
-    const bool in_grp = grp < G && slot < a.n;
+    const long long entry = gw * G + grp;
+    const long long n_list = (long long)*count;
+    if (gw * G >= n_list) return;  // warp-uniform: the whole warp is past the list
+    const bool in_grp = grp < G && entry < n_list;
+    const long long slot = in_grp ? (long long)__ldg(list + entry) : 0;
     const unsigned gmask = in_grp ? (((1u << k) - 1u) << (grp * k)) : 0u;
     const int F = a.h.F, M = a.h.M;
 
     int x = -1, f = 255;
-    bool live = in_grp && (!a.accept || a.accept[slot]);
+    bool live = in_grp;
     if (live) {
         x = __ldg(a.tuples + slot * k + c);
         f = a.fingers ? (int)__ldg(a.fingers + slot * k + c) : 255;
@@ -300,19 +338,29 @@ __global__ void __launch_bounds__(kIkThreads) k_ik_dls(const IkArgs a) {
     bool ok_c = false;
     float pos = INFINITY, cosv = -2.f;
     float xo[3] = {0.f, 0.f, 0.f}, no[3] = {0.f, 0.f, 0.f};
+    // ---- setup: target vector, reverse lookup, starting sample ----
+    int link = -1;                                            // contact link; joints beyond it stay free
+    float pl[3] = {0.f, 0.f, 0.f}, nl[3] = {0.f, 0.f, 1.f};   // attached point / normal (link frame)
+    float p[3] = {0.f, 0.f, 0.f}, n[3] = {0.f, 0.f, 0.f};     // target: the query's FP32 contact-surface vector
+    float Tp[12];
+    float q[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) q[j] = 0.f;
+#pragma unroll
+    for (int e = 0; e < 12; ++e) Tp[e] = 0.f;
+    bool attempt = false;
     if (gvalid) {
-        int link = -1;  // contact link; joints beyond it stay free
-        // target: the query's FP32 contact-surface vector (R p + t, -(R n))
         const float *T = a.poses + (size_t)(slot / a.T) * 12;
-        const float T0 = __ldg(T), T1 = __ldg(T + 1), T2 = __ldg(T + 2), T3 = __ldg(T + 3);
-        const float T4 = __ldg(T + 4), T5 = __ldg(T + 5), T6 = __ldg(T + 6), T7 = __ldg(T + 7);
-        const float T8 = __ldg(T + 8), T9 = __ldg(T + 9), T10 = __ldg(T + 10), T11 = __ldg(T + 11);
+#pragma unroll
+        for (int e = 0; e < 12; ++e) Tp[e] = __ldg(T + e);
         const float ox = __ldg(a.obj.px + x), oy = __ldg(a.obj.py + x), oz = __ldg(a.obj.pz + x);
         const float onx = __ldg(a.obj.nx + x), ony = __ldg(a.obj.ny + x), onz = __ldg(a.obj.nz + x);
-        const float p[3] = {xf_row(T0, T1, T2, T3, ox, oy, oz), xf_row(T4, T5, T6, T7, ox, oy, oz),
-                            xf_row(T8, T9, T10, T11, ox, oy, oz)};
-        const float n[3] = {-rot_row(T0, T1, T2, onx, ony, onz), -rot_row(T4, T5, T6, onx, ony, onz),
-                            -rot_row(T8, T9, T10, onx, ony, onz)};
+        p[0] = xf_row(Tp[0], Tp[1], Tp[2], Tp[3], ox, oy, oz);
+        p[1] = xf_row(Tp[4], Tp[5], Tp[6], Tp[7], ox, oy, oz);
+        p[2] = xf_row(Tp[8], Tp[9], Tp[10], Tp[11], ox, oy, oz);
+        n[0] = -rot_row(Tp[0], Tp[1], Tp[2], onx, ony, onz);
+        n[1] = -rot_row(Tp[4], Tp[5], Tp[6], onx, ony, onz);
+        n[2] = -rot_row(Tp[8], Tp[9], Tp[10], onx, ony, onz);
         // reverse lookup of the (cell, bin) code
         const FieldGeom &g = a.g;
         int bin = 0;
@@ -330,8 +378,8 @@ __global__ void __launch_bounds__(kIkThreads) k_ik_dls(const IkArgs a) {
                 (((unsigned long long)uz * g.dims[1] + uy) * g.dims[0] + ux) * g.rw + f / g.fpw;
             v = rep_lookup(a.rep, word * 32ull + (unsigned)((f % g.fpw) * g.bits + bin));
         }
-        float q[J];
-        if (v == 0xffffffffu) {
+        attempt = v != 0xffffffffu;
+        if (!attempt) {
             atomicOr(a.status, CF_DEV_REP_MISS);
 #pragma unroll
             for (int j = 0; j < J; ++j) q[j] = __ldg(a.h.lo + f * J + j);
@@ -340,30 +388,47 @@ __global__ void __launch_bounds__(kIkThreads) k_ik_dls(const IkArgs a) {
 #pragma unroll
             for (int j = 0; j < J; ++j) q[j] = __ldg(a.qs + ((size_t)f * J + j) * a.S + s);
             const float *sp = a.h.surf + ((size_t)f * M + __ldg(a.h.sorted_of + f * M + m)) * 8;
-            float pl[3] = {__ldg(sp), __ldg(sp + 1), __ldg(sp + 2)};
-            float nl[3] = {__ldg(sp + 3), __ldg(sp + 4), __ldg(sp + 5)};
-            const int l = (int)__ldg(sp + 6);
-            link = l;
-            for (int it = 0; it < a.n1; ++it) dls_step<J>(a, f, l, pl, nl, p, n, q);
-            float xw[3], nw[3];
-            for (int r = 0; r < a.nr; ++r) {
-                project_capsule<J>(a, f, l, q, p, n, pl, nl, xw, nw);
-                for (int it = 0; it < a.n2; ++it) dls_step<J>(a, f, l, pl, nl, p, n, q);
-            }
-            project_capsule<J>(a, f, l, q, p, n, pl, nl, xw, nw);
-            const float dx = xw[0] - p[0], dy = xw[1] - p[1], dz = xw[2] - p[2];
-            pos = sqrtf(dx * dx + dy * dy + dz * dz);
-            cosv = nw[0] * n[0] + nw[1] * n[1] + nw[2] * n[2];
-            ok_c = pos <= a.tol_pos && cosv >= a.tol_cos;
-            // realised contact in the object frame: R^T (x - t); outward object normal -R^T n~
-            const float d[3] = {xw[0] - T3, xw[1] - T7, xw[2] - T11};
-            xo[0] = T0 * d[0] + T4 * d[1] + T8 * d[2];
-            xo[1] = T1 * d[0] + T5 * d[1] + T9 * d[2];
-            xo[2] = T2 * d[0] + T6 * d[1] + T10 * d[2];
-            no[0] = -(T0 * nw[0] + T4 * nw[1] + T8 * nw[2]);
-            no[1] = -(T1 * nw[0] + T5 * nw[1] + T9 * nw[2]);
-            no[2] = -(T2 * nw[0] + T6 * nw[1] + T10 * nw[2]);
+            pl[0] = __ldg(sp); pl[1] = __ldg(sp + 1); pl[2] = __ldg(sp + 2);
+            nl[0] = __ldg(sp + 3); nl[1] = __ldg(sp + 4); nl[2] = __ldg(sp + 5);
+            link = (int)__ldg(sp + 6);
         }
+    }
+    // ---- IK: one loop over the DLS steps with the Phase II projections in
+    // between (a single inlined copy of each); the lanes that run it are
+    // re-converged after every step, since their contacts sit on different links
+    const unsigned ikmask = __ballot_sync(full, attempt);
+    if (attempt) {
+        const int n1 = a.n1, nr = a.nr, n2 = a.n2, total = n1 + nr * n2;
+        float xw[3], nw[3];
+        for (int it = 0; it <= total; ++it) {
+            // projections due before DLS step `it` (after the last one when it == total)
+            int nproj = 0;
+            if (n2 > 0) {
+                const int d = it - n1;
+                nproj = (d >= 0 && d % n2 == 0 && d / n2 < nr) ? 1 : 0;
+                if (it == total) nproj += 1;
+            } else if (it == total) {
+                nproj = nr + 1;
+            }
+            for (int pj = 0; pj < nproj; ++pj) project_capsule<J>(a, f, link, q, p, n, pl, nl, xw, nw);
+            if (it == total) break;
+            dls_step<J>(a, f, link, pl, nl, p, n, q);
+            __syncwarp(ikmask);
+        }
+        const float dx = xw[0] - p[0], dy = xw[1] - p[1], dz = xw[2] - p[2];
+        pos = sqrtf(dx * dx + dy * dy + dz * dz);
+        cosv = nw[0] * n[0] + nw[1] * n[1] + nw[2] * n[2];
+        ok_c = pos <= a.tol_pos && cosv >= a.tol_cos;
+        // realised contact in the object frame: R^T (x - t); outward object normal -R^T n~
+        const float d[3] = {xw[0] - Tp[3], xw[1] - Tp[7], xw[2] - Tp[11]};
+        xo[0] = Tp[0] * d[0] + Tp[4] * d[1] + Tp[8] * d[2];
+        xo[1] = Tp[1] * d[0] + Tp[5] * d[1] + Tp[9] * d[2];
+        xo[2] = Tp[2] * d[0] + Tp[6] * d[1] + Tp[10] * d[2];
+        no[0] = -(Tp[0] * nw[0] + Tp[4] * nw[1] + Tp[8] * nw[2]);
+        no[1] = -(Tp[1] * nw[0] + Tp[5] * nw[1] + Tp[9] * nw[2]);
+        no[2] = -(Tp[2] * nw[0] + Tp[6] * nw[1] + Tp[10] * nw[2]);
+    }
+    if (gvalid) {
         float *qo = a.q + ((size_t)slot * F + f) * J;
         uint8_t *uo = a.used + ((size_t)slot * F + f) * J;
 #pragma unroll
@@ -567,12 +632,15 @@ __global__ void __launch_bounds__(32 * kRealizeWarps) k_realize(const RealizeArg
 
 }  // namespace
 
-cudaError_t launch_ik(const IkArgs &a, cudaStream_t st) {
+cudaError_t launch_ik(const IkArgs &a, int *list, unsigned int *count, cudaStream_t st) {
     if (a.n <= 0) return cudaSuccess;
+    k_ik_compact<<<(unsigned)((a.n + 255) / 256), 256, 0, st>>>(a, list, count);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     const long long G = 32 / a.k;
     const long long warps = (a.n + G - 1) / G;
     const long long blocks = (warps * 32 + kIkThreads - 1) / kIkThreads;
-    CF_KJ_DISPATCH(a.h.J, (k_ik_dls<JJ><<<(unsigned)blocks, kIkThreads, 0, st>>>(a)));
+    CF_KJ_DISPATCH(a.h.J, (k_ik_dls<JJ><<<(unsigned)blocks, kIkThreads, 0, st>>>(a, list, count)));
     return cudaGetLastError();
 }
 

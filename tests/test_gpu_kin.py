@@ -7,12 +7,14 @@ library and the FP64 oracle.
 Acceptance rule.
  - Representative table: bit-exact (same codes, same smallest s * M + m).
  - IK: the kernel runs in FP32, the oracle in FP64.  A contact is *sensitive*
-   when an oracle re-run with the targets moved by 1e-6 m and the start joints
-   by 1e-6 rad changes its final joints by more than 1e-4 rad, or when its
-   residual lies within 5e-5 m / 2e-4 (cosine) of the success thresholds.
+   when an oracle re-run with the targets moved by 1e-7 m and the start joints
+   by 1e-7 rad (a few FP32 roundings of a 0.1 m / 1 rad quantity) changes its
+   final joints by more than 1e-4 rad (an amplification above 1000), or when
+   its residual lies within 1e-5 m / 5e-5 (cosine) of the success thresholds.
    Sensitive slots must stay below 5%; every other contact agrees within
-   1e-3 rad (joints), 5e-5 m (residual, realised point), 2e-4 (cosine,
-   realised normal), and every other slot has the same success flag.
+   1e-3 rad (joints), 1e-5 m (residual, realised point) and 1e-3 (cosine,
+   realised normal: a normal turns with its link, by at most the sum of its
+   joints' differences), and every other slot has the same success flag.
  - SDF grid: within 1e-6 m at nodes whose sign decision the oracle does not
    flag as ambiguous (a near tie between points that disagree on the side).
  - Realization: free joints filled bit for bit (the same FP32 operations);
@@ -31,8 +33,9 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-TOL_Q, TOL_POS, TOL_COS = 1e-3, 5e-5, 2e-4
-SENS_Q, SENS_POS, SENS_COS = 1e-4, 5e-5, 2e-4
+TOL_Q, TOL_POS, TOL_COS = 1e-3, 1e-5, 1e-3
+SENS_Q, SENS_POS, SENS_COS, SENS_PERTURB = 1e-4, 1e-5, 5e-5, 1e-7
+MAX_SENSITIVE = 0.05
 
 
 @pytest.fixture(scope="module")
@@ -93,7 +96,8 @@ def _ik_both(cf, w, field, soa, tup, fing, valid, prm_kw=None):
                n_rounds=prm_kw.get("n_rounds", 4), n_phase2=prm_kw.get("n_phase2", 4),
                tol_pos=prm_kw.get("tol_pos", 2e-3), tol_deg=prm_kw.get("tol_deg", 20.0), rep=rep)
     o = K.ik_dls(w.hand, w.q, w.inv_h, w.bins, soa, w.poses, w.T, w.k, tup, fing, valid, **okw)
-    pr = K.ik_dls(w.hand, w.q, w.inv_h, w.bins, soa, w.poses, w.T, w.k, tup, fing, valid, perturb=1e-6, **okw)
+    pr = K.ik_dls(w.hand, w.q, w.inv_h, w.bins, soa, w.poses, w.T, w.k, tup, fing, valid, perturb=SENS_PERTURB,
+                  **okw)
     return g, o, pr
 
 
@@ -120,34 +124,39 @@ def test_ik_parity(cf, name, P, S):
     g, o, pr = _ik_both(cf, w, field, soa, tup, fing, valid)
     n, k, F = valid.size, w.k, w.hand.F
     assert cf.device_status() == 0
-    sens_c = _sensitive(w, o, pr, tup, fing, valid)
-    sens = sens_c.any(axis=1)
+    sens = _sensitive(w, o, pr, tup, fing, valid).any(axis=1)
     att = valid.astype(bool)
-    assert sens[att].mean() < 0.05, sens[att].mean()
     clear = att & ~sens
-    # structure: bit-exact
-    assert np.array_equal(g["used"], o["used"])
-    assert np.array_equal(g["ok"][clear], o["ok"][clear])
-    assert np.array_equal(g["ok"][~att], o["ok"][~att]) and not g["ok"][~att].any()
-    e = np.arange(n * k).reshape(n, k)
-    assert np.array_equal(g["rtuples"], np.where(g["ok"][:, None].astype(bool), e, -1))
-    # values of clear contacts
+    rows = np.nonzero(clear)[0]
     fc = fing.reshape(n, k).astype(np.int64)
+    d = dict(q=0.0, pos=0.0, cos=0.0, cp=0.0, cn=0.0)
     for c in range(k):
-        rows = np.nonzero(clear)[0]
-        gq = g["q"][rows, fc[rows, c]]
-        oq = o["q"][rows, fc[rows, c]]
-        assert np.abs(gq - oq).max(initial=0) <= TOL_Q
-        assert np.abs(g["resid"][rows, c, 0] - o["resid"][rows, c, 0]).max(initial=0) <= TOL_POS
-        assert np.abs(g["resid"][rows, c, 1] - o["resid"][rows, c, 1]).max(initial=0) <= TOL_COS
+        d["q"] = max(d["q"], np.abs(g["q"][rows, fc[rows, c]] - o["q"][rows, fc[rows, c]]).max(initial=0))
+        d["pos"] = max(d["pos"], np.abs(g["resid"][rows, c, 0] - o["resid"][rows, c, 0]).max(initial=0))
+        d["cos"] = max(d["cos"], np.abs(g["resid"][rows, c, 1] - o["resid"][rows, c, 1]).max(initial=0))
         ee = rows * k + c
-        assert np.abs(g["contacts"][:3, ee] - o["contacts"][:3, ee]).max(initial=0) <= TOL_POS
-        assert np.abs(g["contacts"][3:, ee] - o["contacts"][3:, ee]).max(initial=0) <= TOL_COS
-    # rows of fingers without a contact are zero on both sides
+        d["cp"] = max(d["cp"], np.abs(g["contacts"][:3, ee] - o["contacts"][:3, ee]).max(initial=0))
+        d["cn"] = max(d["cn"], np.abs(g["contacts"][3:, ee] - o["contacts"][3:, ee]).max(initial=0))
+    ok_diff = int((g["ok"][clear] != o["ok"][clear]).sum())
+    info = (f"{name}: sensitive {sens[att].mean():.4f} of {att.sum()} slots, clear ok differ {ok_diff}, "
+            f"max diffs q {d['q']:.3g} pos {d['pos']:.3g} cos {d['cos']:.3g} point {d['cp']:.3g} "
+            f"normal {d['cn']:.3g}, ok gpu {int(g['ok'].sum())} oracle {int(o['ok'].sum())}")
+    print(info)
+    # structure: bit-exact
+    assert np.array_equal(g["used"], o["used"]), info
+    assert not g["ok"][~att].any(), info
+    e = np.arange(n * k).reshape(n, k)
+    assert np.array_equal(g["rtuples"], np.where(g["ok"][:, None].astype(bool), e, -1)), info
+    # values of clear contacts
+    assert d["q"] <= TOL_Q and d["pos"] <= TOL_POS and d["cos"] <= TOL_COS, info
+    assert d["cp"] <= TOL_POS and d["cn"] <= TOL_COS, info
+    assert ok_diff == 0, info
+    assert sens[att].mean() < MAX_SENSITIVE, info
+    # rows of fingers without a contact are zero
     for u in np.nonzero(att)[0]:
         free = np.setdiff1d(np.arange(F), fc[u])
         assert np.all(g["q"][u, free] == 0) and np.all(g["used"][u, free] == 0)
-    # slots not attempted: untouched outputs are defined
+    # slots not attempted: outputs are defined
     assert np.all(np.isinf(g["resid"][~att, :, 0])) and np.all(g["resid"][~att, :, 1] == -2)
     if name != "tiny_sphere":
         assert o["ok"][att].sum() > 0 and g["ok"][att].sum() > 0
