@@ -34,6 +34,10 @@ WORKLOAD = "hand16_superquadric"
 METRIC = "valid grasps/s"
 UNIT = "grasps/s"
 L2_FLUSH_BYTES = 256 << 20
+# DRAM bytes (read + write) per launch from the committed ncu captures of the
+# current kernels on this workload (profiles/k_score_tuples_hand16_superquadric.md,
+# profiles/k_query_domains_hand16_superquadric.md); None for other workloads.
+NCU_TRAFFIC = {"hand16_superquadric": {"k_score_tuples": 6_705_408, "k_query_domains": 2_571_008 + 12_937_216}}
 
 
 def _args():
@@ -332,18 +336,22 @@ def run_ours(args):
     q_flop = pairs * (18 + 3 * w.B + 3 * F) * 2
     s_flop_own = (counters["lp_pivots"] * 13 * 39 + counters["tuples_scored"] * w.k * w.K * 15) * 2 / args.steps
     b_flop = F * w.S * w.hand.M * (18 + 3 + 3 * w.B) * 2
+    traffic = NCU_TRAFFIC.get(w.name, {})
     kernels = {
         "k_fk_cell_bounds+k_fk_bin": {"ms": per[0], "tflops": b_flop / (per[0] * 1e-3) / 1e12},
-        "k_query_domains": {"ms": per[1], "tflops": q_flop / (per[1] * 1e-3) / 1e12},
+        "k_query_domains": {"ms": per[1], "tflops": q_flop / (per[1] * 1e-3) / 1e12,
+                            "traffic": traffic.get("k_query_domains")},
         "k_sample_tuples": {"ms": per[2]},
-        "k_score_tuples": {"ms": per[3], "tflops": s_flop_own / (per[3] * 1e-3) / 1e12},
+        "k_score_tuples": {"ms": per[3], "tflops": s_flop_own / (per[3] * 1e-3) / 1e12,
+                           "traffic": traffic.get("k_score_tuples")},
     }
     for v in kernels.values():
         if "tflops" in v:
             v["frac"] = v["tflops"] / peak_fp32
     dom = max(["k_query_domains", "k_score_tuples"], key=lambda k: kernels[k]["ms"])
     roof = {"kernel": dom, "bound": "alu", "achieved": kernels[dom]["tflops"], "peak": peak_fp32,
-            "unit": "TFLOP/s", "frac": kernels[dom]["frac"], "traffic": None,
+            "unit": "TFLOP/s", "frac": kernels[dom]["frac"], "traffic": kernels[dom].get("traffic"),
+            "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
             "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 flop/FMA x {sm_mhz:.0f} MHz median SM clock sampled "
                           "during the timed region (no FP32 figure in the measured peaks file)",
             "kernels": kernels}
@@ -365,6 +373,9 @@ def run_ours(args):
     if world == 1 and args.realized_steps > 0:
         line["realized"] = run_realized(cf, torch, dev, w, args.realized_steps, soa, poses, masks, counts, tuples,
                                         fingers, prm, prm_given, flush)
+        ikr = line["realized"]["ik_roofline"]
+        ikr["peak"] = peak_fp32
+        ikr["frac"] = ikr["achieved"] / peak_fp32
     if world == 1 and (args.batch_objects > 0 or args.served_seconds > 0):
         ws, fields = _hand_fields(cf, torch, dev)
         if args.batch_objects > 0:
@@ -445,12 +456,21 @@ def run_realized(cf, torch, dev, w, steps, soa, poses, masks, counts, tuples, fi
     total_ms = float(ms.sum())
     per = ms.mean(axis=0)
     names = ["query", "sample", "score", "sdf_build", "ik_dls", "rescore", "realize"]
+    # algorithmic FP32 work of the IK per contact (FMA-equivalents; J joints):
+    # a DLS step = chain 72J + Jacobian 24J + normal equations 3J(J+1) + 6J + Cholesky J^3/6 + solves J^2
+    # + targets 51; a projection = chain 72J + 40
+    J = w.hand.J
+    n_steps, n_proj = 16 + 4 * 4, 4 + 1
+    fma_contact = n_steps * (72 * J + 24 * J + 3 * J * (J + 1) + 6 * J + J ** 3 / 6 + J * J + 51) + n_proj * (72 * J + 40)
+    ik_tflops = t[0] / steps * k * 2 * fma_contact / (per[4] * 1e-3) / 1e12
     return {"metric": "valid grasps/s after IK + realization", "value": float(t[3]) / (total_ms / 1e3),
             "unit": UNIT, "steps": steps, "ms_per_step": total_ms / steps,
             "breakdown_ms": {nm: float(v) for nm, v in zip(names, per)},
             "per_step": {"accepted": t[0] / steps, "ik_ok": t[1] / steps, "re_accepted": t[2] / steps,
                          "valid": t[3] / steps},
-            "gpu_launches_per_step": 9,
+            "ik_roofline": {"bound": "alu", "achieved": ik_tflops, "unit": "TFLOP/s",
+                            "flop_per_contact": 2 * fma_contact, "contacts_per_step": t[0] / steps * k},
+            "gpu_launches_per_step": 10,
             "params": {"sdf_h": SDF_H, "sdf_dims": [int(x) for x in dims], "pen_margin": PEN_MARGIN,
                        "axis_step": 0.5 / float(w.inv_h), "ik": {"beta": 0.01, "lambda": 1e-4, "phase1": 16,
                                                                   "rounds": 4, "phase2": 4, "tol_pos": 2e-3,
