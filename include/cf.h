@@ -445,6 +445,11 @@ int cf_plan_destroy(cf_plan *plan);
 
 /* ---- diagnostics --------------------------------------------------------- */
 
+/* FP32 FMA throughput of the current device in TFLOP/s (2 flop per FMA),
+ * measured by a kernel of independent FMA chains timed with CUDA events: the
+ * denominator of the FP32-issue-bound rooflines.  Synchronous. */
+int cf_fp32_peak(double *tflops);
+
 const char *cf_last_error(void);
 
 /* Read and clear the device status word (CF_DEV_* bits) of the current device. */

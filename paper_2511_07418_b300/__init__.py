@@ -162,6 +162,7 @@ _cf_sdf_copy = _sig("cf_sdf_copy", [c_void_p, POINTER(c_float), c_int64])
 _cf_sdf_destroy = _sig("cf_sdf_destroy", [c_void_p])
 _cf_realize = _sig("cf_realize", [c_void_p, c_void_p, c_void_p, c_int32, c_int32, POINTER(RealizeParams), c_void_p,
                                   c_void_p, c_void_p, c_void_p, c_void_p, c_void_p])
+_cf_fp32_peak = _sig("cf_fp32_peak", [POINTER(c_double)])
 _cf_last_error = _sig("cf_last_error", [], c_char_p)
 _cf_device_status = _sig("cf_device_status", [POINTER(c_uint32)])
 _cf_device_counters = _sig("cf_device_counters", [POINTER(c_uint64), c_int])
@@ -172,7 +173,7 @@ EXPORTED = ["cf_build", "cf_field_get_info", "cf_field_copy_table", "cf_field_de
             "cf_sample_tuples", "cf_batch_create", "cf_batch_run", "cf_batch_launches", "cf_batch_destroy",
             "cf_engine_create", "cf_engine_submit", "cf_engine_poll", "cf_engine_result_free", "cf_engine_get_stats",
             "cf_engine_drain", "cf_engine_destroy", "cf_field_rep_slots", "cf_field_copy_rep", "cf_ik_dls",
-            "cf_sdf_build", "cf_sdf_copy", "cf_sdf_destroy", "cf_realize"]
+            "cf_sdf_build", "cf_sdf_copy", "cf_sdf_destroy", "cf_realize", "cf_fp32_peak"]
 
 
 def _check(rc: int):
@@ -636,6 +637,13 @@ def realize(field: Field, sdf: Sdf, poses, T: int, q, used, gate_a, gate_b, prm:
                        _dev(q, torch.float32, "q"), _dev(used, torch.uint8, "used"),
                        _dev(flags, torch.uint8, "flags"), _stream(stream)))
     return flags
+
+
+def fp32_peak() -> float:
+    """Measured FP32 FMA throughput of the current device, TFLOP/s (cf_fp32_peak)."""
+    v = c_double()
+    _check(_cf_fp32_peak(byref(v)))
+    return float(v.value)
 
 
 def device_status() -> int:
