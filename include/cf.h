@@ -6,14 +6,14 @@
  *   cf_build          sampled contact field of a hand: forward kinematics of the
  *                     hand surface over joint samples, binned into a voxel x
  *                     normal-bin bit table            (Def. Contact Field (Point),
- *                     Def. Contact Field (Hand), Sec. 3.3 Implementation, Alg. 1)
+ *                     Def. Contact Field (Hand), Sec. 4.3 Implementation, Alg. 1)
  *   cf_query_domains  contact domains of an object over many palm poses, as
  *                     per-finger bitmasks             (Def. Contact Surface
- *                     Representation, Sec. 3.2, Sec. 3.3 Object Contact Query)
+ *                     Representation, Sec. 4.2, Sec. 4.3 Object Contact Query)
  *   cf_score_tuples   random contact k-tuples from k distinct finger domains and
  *                     their linearised friction-cone closure margin
- *                                                     (Sec. 4.3, Alg. 2 Random(D_i),
- *                     Eq. GSWO of Sec. 2.2)
+ *                                                     (Sec. 5.3, Alg. 2 Random(D_i),
+ *                     Eq. GSWO of Sec. 3.2)
  * plus cf_plan_*, the same path driven from host buffers (one object request).
  *
  * Conventions
@@ -93,13 +93,13 @@ typedef struct cf_hand_desc {
 /* Field parameters.  Cells live on one global lattice: cell k covers
  * [k / inv_h, (k + 1) / inv_h) per axis, k = floor(x * inv_h) of the exact
  * product.  Normal bin of a unit vector v = argmax_b bin_dirs[b] . v (first
- * maximum), the fixed direction set of Sec. 3.3 "Memory Consumption". */
+ * maximum), the fixed direction set of Sec. 4.3 "Memory Consumption". */
 typedef struct cf_field_params {
     float inv_h;              /* 1 / voxel edge, cells per metre (> 0) */
     int32_t n_bins;           /* B, 1..CF_MAX_BINS */
     const float *bin_dirs;    /* host [B][3] */
     int32_t want_rep;         /* 1: also keep, per (cell, finger, bin) code, the smallest s * M + m of the
-                                 samples that produced it (reverse lookup, Sec. 4.5) */
+                                 samples that produced it (reverse lookup, Sec. 5.5) */
 } cf_field_params;
 
 typedef struct cf_field cf_field;
@@ -228,7 +228,7 @@ int cf_score_tuples_noalloc(const cf_points *obj, int32_t n_fingers, const uint3
                             const uint32_t *d_counts, int32_t n_poses, const cf_score_params *prm, int32_t *d_tuples,
                             uint8_t *d_fingers, float *d_margin, uint8_t *d_accept, cf_stream stream);
 
-/* Sampling step of cf_score_tuples on its own (Sec. 4.3, Alg. 2 Random(D_i)):
+/* Sampling step of cf_score_tuples on its own (Sec. 5.3, Alg. 2 Random(D_i)):
  * writes d_tuples / d_fingers exactly as cf_score_tuples would, scores
  * nothing.  prm->tuples_given must be 0; d_margin-style outputs are not used.
  * Errors: CF_EINVAL, CF_ECUDA.  Asynchronous on `stream`. */
@@ -236,7 +236,7 @@ int cf_sample_tuples(const cf_points *obj, int32_t n_fingers, const uint32_t *d_
                      int32_t n_poses, const cf_score_params *prm, int32_t *d_tuples, uint8_t *d_fingers,
                      cf_stream stream);
 
-/* ---- a6: reverse lookup + damped-least-squares IK (Sec. 4.5) ------------- */
+/* ---- a6: reverse lookup + damped-least-squares IK (Sec. 5.5) ------------- */
 
 typedef struct cf_ik_params {
     float beta;         /* lever of the normal target (m): p~ + beta n~ -> p + beta n */
@@ -277,7 +277,7 @@ int cf_ik_dls(const cf_field *field, const cf_points *obj, const float *d_poses,
               const cf_ik_params *prm, float *d_q, uint8_t *d_used, float *d_contacts, int32_t *d_rtuples,
               float *d_resid, uint8_t *d_ok, cf_stream stream);
 
-/* ---- a7: object SDF grid and the realization filter (Sec. 4.6) ----------- */
+/* ---- a7: object SDF grid and the realization filter (Sec. 5.6) ----------- */
 
 typedef struct cf_sdf cf_sdf;
 
@@ -312,6 +312,33 @@ typedef struct cf_realize_params {
 int cf_realize(const cf_field *field, const cf_sdf *sdf, const float *d_poses, int32_t n_slots, int32_t n_tuples,
                const cf_realize_params *prm, const uint8_t *d_gate_a, const uint8_t *d_gate_b, float *d_q,
                const uint8_t *d_used, uint8_t *d_flags, cf_stream stream);
+
+/* ---- Alg. 2: blockwise zeroth-order contact optimisation (Sec. 5.4) ------ */
+
+typedef struct cf_opt_params {
+    int32_t n_outer;    /* outer iterations n_o (0..64) */
+    int32_t n_inner;    /* mutations per contact and iteration n_in: 4, 8 or 16 */
+    float sigma;        /* standard deviation of each tangent-plane mutation component (m) */
+    float zero_tol;     /* margins <= zero_tol count as 0 (a closed grasp): optimisation stops there */
+} cf_opt_params;
+
+/* Improves every valid tuple of d_tuples [P][T][k] in place (prm->tuples_given
+ * must be 1; d_fingers [P][T][k] gives each contact's finger).  For it = 0 ..
+ * n_outer-1 and each contact i: with (x, y) the Duff et al. 2017 basis of
+ * nu = -n_i, candidate c = 0 .. n_inner-1 mutates p_i by sigma (g1 x + g2 y), with
+ * (g1, g2) the Box-Muller pair of Philox4x32-10 words (2 (c mod 2), 2 (c mod 2)
+ * + 1) at counter (pose, tau, (it k + i) ceil(n_inner / 2) + c / 2, 0xA162), key
+ * seed: u1 = (w >> 8 + 1) 2^-24, u2 = (w' >> 8) 2^-24, g = sqrt(-2 ln u1)
+ * (cos, sin)(2 pi u2).  Each mutation is projected onto finger f_i's domain at
+ * the pose (the object point with its mask bit set nearest to it, lowest index
+ * on ties), and contact i moves to the candidate of least closure margin if it
+ * is lower than the current one (margins <= zero_tol count as 0; ties keep the
+ * current point, then the lower candidate).  d_margin / d_accept receive the
+ * final tuple's margin and margin <= eps.  Invalid tuples (an id < 0) are left
+ * unchanged with margin +inf.  Errors: CF_EINVAL, CF_ENOMEM, CF_ECUDA. */
+int cf_optimize_tuples(const cf_points *obj, int32_t n_fingers, const uint32_t *d_masks, int32_t n_poses,
+                       const cf_score_params *prm, const cf_opt_params *opt, int32_t *d_tuples,
+                       const uint8_t *d_fingers, float *d_margin, uint8_t *d_accept, cf_stream stream);
 
 /* ---- many objects in one graph launch ------------------------------------ */
 

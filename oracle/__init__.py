@@ -10,19 +10,19 @@ with the GPU library and never imports it.
 
 Functions (paper passages they follow are cited in ``cf_oracle.c``):
   philox4x32_10       counter-based generator (Salmon et al., SC'11)
-  fk_links            FP64 forward kinematics of one finger (Sec. 2.1)
+  fk_links            FP64 forward kinematics of one finger (Sec. 3.1)
   contact_vectors     FK((p,n); i, q) of all surface points of one finger sample
   Field               the sampled hand contact field as a set of codes
-                      (Sec. 3.3, Alg. 1; Def. Contact Field (Hand))
-  Field.query         contact domains as bitmasks (Sec. 3.2, Sec. 3.3 query)
+                      (Sec. 4.3, Alg. 1; Def. Contact Field (Hand))
+  Field.query         contact domains as bitmasks (Sec. 4.2, Sec. 4.3 query)
   query_masks_brute   literal existential check, tiny inputs only
-  sample_tuples       random k-tuples from k distinct finger domains (Sec. 4.3)
+  sample_tuples       random k-tuples from k distinct finger domains (Sec. 5.3)
   closure_lp          linearised GSWO margin of one tuple (Eq. GSWO): k LPs
   score_tuples        margins / accept flags of many tuples (process pool)
-  rep_codes           reverse-lookup representatives of a finger's codes (Sec. 4.5)
+  rep_codes           reverse-lookup representatives of a finger's codes (Sec. 5.5)
   point_codes         FP32 code of an object point under a pose (the query's decision)
   kinematics.*        FP64 numpy FK / Jacobian / DLS IK / SDF grid / realization
-                      checks (Sec. 4.5, Sec. 4.6)
+                      checks (Sec. 5.5, Sec. 5.6)
 
 Parity status: every function is pinned by tests under ``tests/`` against
 closed forms, an independent library routine (triton's Philox in
@@ -251,7 +251,7 @@ def pack_code(f, kx, ky, kz, b) -> int:
 
 
 def rep_codes(hand, q, inv_h, bins, f: int) -> dict:
-    """Reverse lookup table of finger f (Sec. 4.5): packed code -> smallest
+    """Reverse lookup table of finger f (Sec. 5.5): packed code -> smallest
     s * M + m over the field samples producing it (m in the hand's order)."""
     keep, ptrs = _hand_args(hand)
     qq = _c(q, np.float32)
@@ -294,7 +294,7 @@ def sample_tuples(masks: np.ndarray, counts: np.ndarray, N: int, T: int, k: int,
 
 
 # ---------------------------------------------------------------------------
-# closure margin (Eq. GSWO, Sec. 2.2, linearised)
+# closure margin (Eq. GSWO, Sec. 3.2, linearised)
 # ---------------------------------------------------------------------------
 
 def _onb_duff(nu):

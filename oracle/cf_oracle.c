@@ -9,18 +9,18 @@
  * What it computes (each function cites the passage it follows):
  *   - Philox4x32-10 counter-based generator (Salmon et al., SC'11), used to key
  *     the random choices of tuple sampling;
- *   - forward kinematics of a capsule-chain finger in FP64 (Sec. 2.1 notation,
+ *   - forward kinematics of a capsule-chain finger in FP64 (Sec. 3.1 notation,
  *     Def. "Contact Field (Point)": FK((p,n); i, q));
  *   - the sampled hand contact field as a SET of (finger, voxel cell, normal bin)
- *     codes (Sec. 3.3 "Implementation", Alg. 1, Def. "Contact Field (Hand)"),
+ *     codes (Sec. 4.3 "Implementation", Alg. 1, Def. "Contact Field (Hand)"),
  *     and the contact domain of an object pose as set membership of the
  *     object's contact-surface codes (p, -n) (Def. "Contact Surface
- *     Representation", Sec. 3.2 "Contact Interaction", Sec. 3.3 "Object Contact
+ *     Representation", Sec. 4.2 "Contact Interaction", Sec. 4.3 "Object Contact
  *     Query");
  *   - a literal brute-force existential check ("is there a field sample with the
  *     same code?") for tiny inputs;
  *   - random k-tuples of contacts from k distinct non-empty finger domains
- *     (Sec. 4.3 "Contact Domain Generation": randomly select k domains;
+ *     (Sec. 5.3 "Contact Domain Generation": randomly select k domains;
  *     Alg. 2 step "Random(D_i)");
  *   (the closure margin's linear programs are written out and solved in
  *   oracle/__init__.py with a library LP solver).
@@ -258,7 +258,7 @@ static int bin64(const double m[3], int B, const float *dirs) {
     return best_b;
 }
 
-/* Build the sampled contact field of a hand (Sec. 3.3, Alg. 1 input: all
+/* Build the sampled contact field of a hand (Sec. 4.3, Alg. 1 input: all
  * contact vectors FK((p,n); i, q_s) over sampled q_s), as code sets per finger.
  * q is [F][J][S] float32 (widened to FP64).  with_band != 0 also builds the
  * FP64 and tolerance-band sets used to count ambiguous entries. */
@@ -347,7 +347,7 @@ int64_t orc_field_codes(const void *h, int f, uint64_t *out, int64_t cap) {
     return fd->k32[f].n;
 }
 
-/* Contact domains (Sec. 3.2: CF(H) intersected with S(O); Sec. 3.3 object
+/* Contact domains (Sec. 4.2: CF(H) intersected with S(O); Sec. 4.3 object
  * contact query).  For pose i = (R_i, t_i) (object -> palm) and object point x
  * with outward normal n_x, the contact-surface vector is (R p_x + t, -(R n_x))
  * (Def. "Contact Surface Representation" flips the normal).  Bit x of
@@ -482,7 +482,7 @@ void orc_query_masks_brute(int F, int J, int M, const float *base, const float *
 }
 
 /* ------------------------------------------------------------------------ */
-/* Tuple sampling (Sec. 4.3: randomly select k contact domains of distinct    */
+/* Tuple sampling (Sec. 5.3: randomly select k contact domains of distinct    */
 /* fingers; Alg. 2: (p_i, n_i) <- Random(D_i)).                               */
 /* Draw d of tuple (i, tau) is word (d mod 4) of Philox4x32-10 with counter   */
 /* (i, tau, d div 4, 0) and key (seed lo, seed hi).  A uniform integer in     */
@@ -559,7 +559,7 @@ int orc_num_threads(void) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* Reverse lookup (Sec. 4.5 "Kinematics Optimization")                       */
+/* Reverse lookup (Sec. 5.5 "Kinematics Optimization")                       */
 /* ------------------------------------------------------------------------ */
 typedef struct { uint64_t key; uint32_t val; } keyval;
 

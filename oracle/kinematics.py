@@ -6,13 +6,13 @@ Plain numpy, vectorised over contacts, following the paper's steps in order:
 
   chain / jacobian   forward kinematics of a finger chain and the position
                      Jacobian of a point attached to link l: column j is
-                     a_j x (x - o_j) for j <= l, else 0 (Sec. 4.5, the point
+                     a_j x (x - o_j) for j <= l, else 0 (Sec. 5.5, the point
                      form of J_p - [p~]x J_r)
   dls_step           one damped-least-squares update: the solution of
                      (J^T J + lambda I) dq = J^T e for the two position targets
-                     p~ -> p and p~ + beta n~ -> p + beta n (Eq. DLS, Sec. 4.5),
+                     p~ -> p and p~ + beta n~ -> p + beta n (Eq. DLS, Sec. 5.5),
                      then clamped to the joint limits
-  project_capsule    Phase II ("Finetuning" of Sec. 4.5): the contact vector
+  project_capsule    Phase II ("Finetuning" of Sec. 5.5): the contact vector
                      (p, n) projected onto the contact link's capsule -- the
                      axis point nearest p, and there the capsule normal that
                      minimises the DLS objective
@@ -24,7 +24,7 @@ Plain numpy, vectorised over contacts, following the paper's steps in order:
                      the unit square over its stationary point and four edges
   realize            random values for free joints, capsule-vs-SDF
                      penetration and finger-finger capsule intersection
-                     (Sec. 4.6 "Postprocessing")
+                     (Sec. 5.6 "Postprocessing")
 
 Decisions that sit within a tolerance band of their threshold are reported as
 ambiguous rather than forced, so that tests compare only what FP32 and FP64
@@ -175,7 +175,7 @@ def _pose_targets(soa, poses, pose_idx, x):
 def ik_dls(hand, qs, inv_h, bins, soa, poses, T: int, k: int, tuples, fingers, accept, beta=0.01, lam=1e-4,
            n_phase1=16, n_rounds=4, n_phase2=4, tol_pos=2e-3, tol_cos=None, tol_deg=20.0, rep=None,
            perturb: float = 0.0):
-    """Kinematics optimisation of tuple slots (Sec. 4.5), same outputs as the
+    """Kinematics optimisation of tuple slots (Sec. 5.5), same outputs as the
     library call: dict(q [n,F,J], used, contacts [6,n*k], rtuples [n,k],
     resid [n,k,2], ok [n], miss [n,k] (contact code without representative)).
     ``rep`` maps finger -> {packed code: s*M + m}; computed when None.
@@ -379,7 +379,7 @@ def random_joint(lo, hi, word):
 
 def realize(hand, sdf, sdf_amb, sdf_lo, sdf_h, poses, T: int, q, used, gate_a, gate_b, pen_margin=2e-3,
             axis_step=1.25e-3, seed=0, band=1e-5):
-    """Post-processing of tuple slots (Sec. 4.6).  Returns (q [n,F,J] float32
+    """Post-processing of tuple slots (Sec. 5.6).  Returns (q [n,F,J] float32
     with free joints filled, flags [n] uint8 (1 gated out, 2 penetration,
     4 self-collision), ambiguous [n] bool)."""
     q = np.array(q, np.float32, copy=True)

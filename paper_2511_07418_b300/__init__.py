@@ -62,6 +62,10 @@ class IkParams(Structure):
                 ("n_phase2", c_int32), ("tol_pos", c_float), ("tol_cos", c_float)]
 
 
+class OptParams(Structure):
+    _fields_ = [("n_outer", c_int32), ("n_inner", c_int32), ("sigma", c_float), ("zero_tol", c_float)]
+
+
 class RealizeParams(Structure):
     _fields_ = [("pen_margin", c_float), ("axis_step", c_float), ("seed", c_uint64)]
 
@@ -163,6 +167,8 @@ _cf_sdf_destroy = _sig("cf_sdf_destroy", [c_void_p])
 _cf_realize = _sig("cf_realize", [c_void_p, c_void_p, c_void_p, c_int32, c_int32, POINTER(RealizeParams), c_void_p,
                                   c_void_p, c_void_p, c_void_p, c_void_p, c_void_p])
 _cf_fp32_peak = _sig("cf_fp32_peak", [POINTER(c_double)])
+_cf_optimize = _sig("cf_optimize_tuples", [POINTER(Points), c_int32, c_void_p, c_int32, POINTER(ScoreParams),
+                                           POINTER(OptParams), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p])
 _cf_last_error = _sig("cf_last_error", [], c_char_p)
 _cf_device_status = _sig("cf_device_status", [POINTER(c_uint32)])
 _cf_device_counters = _sig("cf_device_counters", [POINTER(c_uint64), c_int])
@@ -173,7 +179,7 @@ EXPORTED = ["cf_build", "cf_field_get_info", "cf_field_copy_table", "cf_field_de
             "cf_sample_tuples", "cf_batch_create", "cf_batch_run", "cf_batch_launches", "cf_batch_destroy",
             "cf_engine_create", "cf_engine_submit", "cf_engine_poll", "cf_engine_result_free", "cf_engine_get_stats",
             "cf_engine_drain", "cf_engine_destroy", "cf_field_rep_slots", "cf_field_copy_rep", "cf_ik_dls",
-            "cf_sdf_build", "cf_sdf_copy", "cf_sdf_destroy", "cf_realize", "cf_fp32_peak"]
+            "cf_sdf_build", "cf_sdf_copy", "cf_sdf_destroy", "cf_realize", "cf_fp32_peak", "cf_optimize_tuples"]
 
 
 def _check(rc: int):
@@ -543,6 +549,24 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def opt_params(n_outer=2, n_inner=8, sigma=0.005, zero_tol=1e-6) -> OptParams:
+    return OptParams(int(n_outer), int(n_inner), float(sigma), float(zero_tol))
+
+
+def optimize_tuples(soa, n_fingers: int, masks, prm: ScoreParams, opt: OptParams, tuples, fingers, stream=None):
+    """cf_optimize_tuples: improves ``tuples`` [P,T,k] in place; returns (margin [P,T] f32, accept [P,T] u8).
+    ``prm`` must have tuples_given set."""
+    import torch
+    obj = points_struct(soa)
+    P, T = int(tuples.shape[0]), int(prm.n_tuples)
+    margin = torch.empty((P, T), dtype=torch.float32, device=soa.device)
+    accept = torch.empty((P, T), dtype=torch.uint8, device=soa.device)
+    _check(_cf_optimize(byref(obj), int(n_fingers), _dev(masks, torch.int32, "masks"), P, byref(prm), byref(opt),
+                        _dev(tuples, torch.int32, "tuples"), _dev(fingers, torch.uint8, "fingers"),
+                        _dev(margin, torch.float32, "margin"), _dev(accept, torch.uint8, "accept"), _stream(stream)))
+    return margin, accept
 
 
 def ik_params(beta=0.01, lam=1e-4, n_phase1=16, n_rounds=4, n_phase2=4, tol_pos=2e-3, tol_deg=20.0) -> IkParams:

@@ -641,6 +641,40 @@ extern "C" int cf_score_tuples(const cf_points *obj, int32_t n_fingers, const ui
     return CF_OK;
 }
 
+extern "C" int cf_optimize_tuples(const cf_points *obj, int32_t n_fingers, const uint32_t *d_masks, int32_t n_poses,
+                                  const cf_score_params *prm, const cf_opt_params *opt, int32_t *d_tuples,
+                                  const uint8_t *d_fingers, float *d_margin, uint8_t *d_accept, cf_stream stream) {
+    if (!prm || !opt) return fail(CF_EINVAL, "NULL argument");
+    if (!prm->tuples_given) return fail(CF_EINVAL, "cf_optimize_tuples needs tuples_given = 1 (tuples are in/out)");
+    if (n_fingers < 1 || n_fingers > CF_MAX_FINGERS)
+        return fail(CF_EINVAL, "n_fingers=%d not in [1,%d]", n_fingers, CF_MAX_FINGERS);
+    if (opt->n_outer < 0 || opt->n_outer > 64) return fail(CF_EINVAL, "n_outer=%d not in [0,64]", opt->n_outer);
+    if (opt->n_inner != 4 && opt->n_inner != 8 && opt->n_inner != 16)
+        return fail(CF_EINVAL, "n_inner=%d not in {4, 8, 16}", opt->n_inner);
+    if (!(opt->sigma >= 0.f) || !isfinite(opt->sigma)) return fail(CF_EINVAL, "sigma must be finite and >= 0");
+    if (!(opt->zero_tol >= 0.f) || !isfinite(opt->zero_tol)) return fail(CF_EINVAL, "zero_tol must be >= 0");
+    ScoreArgs a;
+    int rc = fill_score_args(obj, n_fingers, d_masks, nullptr, n_poses, prm, d_tuples, const_cast<uint8_t *>(d_fingers),
+                             d_margin, d_accept, &a);
+    if (rc) return rc;
+    if (n_poses == 0) return CF_OK;
+    if (!d_masks || !d_fingers) return fail(CF_EINVAL, "masks / fingers pointer is NULL");
+    a.F = n_fingers;
+    a.masks = d_masks;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned int *work = nullptr;
+    if ((rc = pool_alloc((void **)&work, sizeof(unsigned int), st, "alloc work counter"))) return rc;
+    cudaError_t e = cudaMemsetAsync(work, 0, sizeof(unsigned int), st);
+    if (e == cudaSuccess) {
+        a.work = work;
+        e = launch_optimize(a, opt->n_outer, opt->n_inner, opt->sigma, opt->zero_tol, st);
+    }
+    cudaError_t e2 = cudaFreeAsync(work, st);
+    if (e != cudaSuccess) return cuda_fail(e, "launch k_optimize_tuples");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync(work counter)");
+    return CF_OK;
+}
+
 extern "C" int cf_sample_tuples(const cf_points *obj, int32_t n_fingers, const uint32_t *d_masks,
                                 const uint32_t *d_counts, int32_t n_poses, const cf_score_params *prm,
                                 int32_t *d_tuples, uint8_t *d_fingers, cf_stream stream) {

@@ -1,12 +1,12 @@
 // Kinematics optimisation and post-processing (rows a6, a7 of the path).
 //
-// k_ik_dls (Sec. 4.5 "Kinematics Optimization"): for every contact of an
+// k_ik_dls (Sec. 5.5 "Kinematics Optimization"): for every contact of an
 // accepted tuple, the reverse lookup finds the hand-surface sample that put
 // the contact's (cell, normal bin) code into the field -- the smallest
 // s * M + m over the samples that did, kept by the build's representative
 // table -- and starts from that sample's joint vector q_s.  Damped least
 // squares then moves the attached hand point p~ onto the object point p and
-// p~ + beta n~ onto p + beta n (Eq. DLS of Sec. 4.5; n the inward contact
+// p~ + beta n~ onto p + beta n (Eq. DLS of Sec. 5.5; n the inward contact
 // normal, n~ the hand's outward normal):
 //     dq = (J^T J + lambda I)^-1 J^T e,   q <- clamp(q + dq, lo, hi),
 // J the 6 x J position Jacobian of the two points, column j = a_j x (x - o_j)
@@ -25,7 +25,7 @@
 // regular grid, by brute force over all points (nearest point, sign of
 // (x - p) . n of that point).
 //
-// k_realize (Sec. 4.6 "Postprocessing"): joints the IK left free get uniform
+// k_realize (Sec. 5.6 "Postprocessing"): joints the IK left free get uniform
 // random values in their limits (Philox4x32-10); the grasp is rejected when a
 // link capsule's axis comes closer to the object surface than its radius less
 // the penetration margin (trilinear SDF along the axis), or when capsules of two

@@ -1,8 +1,8 @@
 // Contact-domain query kernel (row a3 of the hot path).
 //
 // Def. "Contact Surface Representation": an object contributes the vectors
-// (p, -n) of its surface points; Sec. 3.2 defines the contact domain as the
-// intersection of the hand's contact field with them, and Sec. 3.3 ("Object
+// (p, -n) of its surface points; Sec. 4.2 defines the contact domain as the
+// intersection of the hand's contact field with them, and Sec. 4.3 ("Object
 // Contact Query") queries the field with the object's points: position part to
 // find the box, normal part to test the box's normal set.  For a palm pose
 // (R, t) (object -> palm) the query vector of object point x is

@@ -1,8 +1,8 @@
 // Tuple sampling + closure margin kernels (rows a4 + a5 of the hot path).
 //
-// Sec. 4.3: a k-contact grasp takes k contact domains of different fingers
+// Sec. 5.3: a k-contact grasp takes k contact domains of different fingers
 // (independent dependency groups) chosen at random; Alg. 2 starts from
-// (p_i, n_i) <- Random(D_i).  Eq. GSWO (Sec. 2.2) scores the contacts: with
+// (p_i, n_i) <- Random(D_i).  Eq. GSWO (Sec. 3.2) scores the contacts: with
 // alpha_j = 1 for some j and friction forces inside the cones, minimise the
 // resultant force and (weighted) torque; the problem splits into one convex
 // subproblem per j.  Linearised here: each cone becomes its inscribed K-edge
@@ -451,6 +451,192 @@ __global__ void __launch_bounds__(kScoreThreads, 3) k_score_tuples(const ScoreAr
     }
 }
 
+// ---------------------------------------------------------------------------
+// Alg. 2: blockwise zeroth-order contact optimisation
+// ---------------------------------------------------------------------------
+constexpr int kOptThreads = 128;
+constexpr int kOptWarps = kOptThreads / 32;
+
+// Wrench column of this lane (contact ci = lane / K, edge cm) for point x.
+__device__ __forceinline__ void wrench_column(const ScoreArgs &a, int x, float ec, float es, float (&wv)[6]) {
+    const float px = __ldg(a.px + x), py = __ldg(a.py + x), pz = __ldg(a.pz + x);
+    const float vx = -__ldg(a.nx + x), vy = -__ldg(a.ny + x), vz = -__ldg(a.nz + x);
+    const float sgn = copysignf(1.f, vz);
+    const float aa = -1.f / (sgn + vz);
+    const float bb = vx * vy * aa;
+    const float xx = 1.f + sgn * vx * vx * aa, xy = sgn * bb, xz = -sgn * vx;
+    const float yx = bb, yy = sgn + vy * vy * aa, yz = -vy;
+    const float ex = vx + ec * xx + es * yx, ey = vy + ec * xy + es * yy, ez = vz + ec * xz + es * yz;
+    const float rx = px - a.cx, ry = py - a.cy, rz = pz - a.cz;
+    wv[0] = ex; wv[1] = ey; wv[2] = ez;
+    wv[3] = (ry * ez - rz * ey) * a.inv_rho;
+    wv[4] = (rz * ex - rx * ez) * a.inv_rho;
+    wv[5] = (rx * ey - ry * ex) * a.inv_rho;
+}
+
+// Closure margin of the tuple whose contact d is point id_d (min over j of LP_j,
+// stopping at a zero), computed by the whole warp.
+__device__ __forceinline__ float tuple_margin(const ScoreArgs &a, int id0, int id1, int id2, int id3, int k, bool colA,
+                                              int ci, float ec, float es, int lane, float *buf,
+                                              unsigned long long &n_piv, unsigned long long &n_lp, unsigned &flags) {
+    float wv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (colA) wrench_column(a, ci == 0 ? id0 : ci == 1 ? id1 : ci == 2 ? id2 : id3, ec, es, wv);
+    float margin = INFINITY;
+    for (int j = 0; j < k; ++j) {
+        int np = 0;
+        const float tj = solve_lp(wv, colA, ci, j, lane, buf, np, flags);
+        n_piv += np;
+        ++n_lp;
+        margin = fminf(margin, tj);
+        if (margin <= kZeroExit) break;
+    }
+    return margin;
+}
+
+struct OptArgs {
+    int n_outer, n_inner;
+    float sigma, zero_tol;
+};
+
+// One warp per tuple (persistent warps, work counter).  Per outer iteration and
+// contact i: NI Gaussian mutations of p_i in its tangent plane (Box-Muller on
+// Philox4x32-10 words), each projected onto finger f_i's domain (the nearest
+// object point whose mask bit is set; all lanes scan the mask words, then one
+// warp reduction per candidate), then the argmin of the closure margin over
+// {current, candidates}: margins <= zero_tol count as 0, ties keep the lower
+// index (the current point first), so the margin never increases.
+template <int NI>
+__global__ void __launch_bounds__(kOptThreads) k_optimize_tuples(const ScoreArgs a, const OptArgs o, unsigned total) {
+    __shared__ __align__(16) float s_buf[kOptWarps][16];
+    __shared__ float s_cand[kOptWarps][NI][3];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int k = a.k, K = a.K, kK = k * K, F = a.F, W = a.W;
+    const bool colA = lane < kK;
+    const int ci = colA ? lane / K : 0, cm = colA ? lane % K : 0;
+    const float ec = a.cs[cm] * a.mu, es = a.sn[cm] * a.mu;
+    float *buf = s_buf[warp];
+    unsigned long long n_piv = 0, n_lp = 0, n_tup = 0;
+    unsigned flags = 0;
+    const uint2 key = make_uint2(a.seed_lo, a.seed_hi);
+    const int blocks_per_draw = (NI + 1) / 2;
+    for (;;) {
+        unsigned u = 0;
+        if (lane == 0) u = atomicAdd(a.work, 1u);
+        u = __shfl_sync(kFull, u, 0);
+        if (u >= total) break;
+        const int pose = (int)(u / (unsigned)a.T), tau = (int)(u % (unsigned)a.T);
+        int id[CF_MAX_K] = {0, 0, 0, 0}, fg[CF_MAX_K] = {0, 0, 0, 0};
+        bool valid = true;
+        for (int d = 0; d < k; ++d) {
+            id[d] = __ldg(a.tuples + (size_t)u * k + d);
+            fg[d] = (int)__ldg(a.fingers + (size_t)u * k + d);
+            valid = valid && id[d] >= 0 && id[d] < a.N && fg[d] < F;
+        }
+        float J = INFINITY;
+        if (valid) {
+            J = tuple_margin(a, id[0], id[1], id[2], id[3], k, colA, ci, ec, es, lane, buf, n_piv, n_lp, flags);
+            float Jc = J <= o.zero_tol ? 0.f : J;
+            const uint32_t pid = (uint32_t)pose + a.pose_base;
+            for (int it = 0; it < o.n_outer && Jc > 0.f; ++it) {
+                for (int i = 0; i < k && Jc > 0.f; ++i) {
+                    const int x0 = i == 0 ? id[0] : i == 1 ? id[1] : i == 2 ? id[2] : id[3];
+                    const int fi = i == 0 ? fg[0] : i == 1 ? fg[1] : i == 2 ? fg[2] : fg[3];
+                    // tangent basis of nu = -n at the current point (Duff et al. 2017)
+                    const float px = __ldg(a.px + x0), py = __ldg(a.py + x0), pz = __ldg(a.pz + x0);
+                    const float vx = -__ldg(a.nx + x0), vy = -__ldg(a.ny + x0), vz = -__ldg(a.nz + x0);
+                    const float sgn = copysignf(1.f, vz);
+                    const float aa = -1.f / (sgn + vz);
+                    const float bb = vx * vy * aa;
+                    const float xx = 1.f + sgn * vx * vx * aa, xy = sgn * bb, xz = -sgn * vx;
+                    const float yx = bb, yy = sgn + vy * vy * aa, yz = -vy;
+                    if (lane < NI) {  // candidate `lane`: one Box-Muller pair
+                        const int c = lane;
+                        const uint4 w4 = philox4x32_10(
+                            make_uint4(pid, (uint32_t)tau, (uint32_t)((it * k + i) * blocks_per_draw + c / 2), 0xA162u),
+                            key);
+                        const uint32_t w0 = (c & 1) ? w4.z : w4.x, w1 = (c & 1) ? w4.w : w4.y;
+                        const float u1 = (float)((w0 >> 8) + 1u) * 5.9604644775390625e-8f;  // (0, 1]
+                        const float u2 = (float)(w1 >> 8) * 5.9604644775390625e-8f;         // [0, 1)
+                        const float r = sqrtf(-2.f * logf(u1));
+                        float sn, cs;
+                        sincospif(2.f * u2, &sn, &cs);
+                        const float g1 = r * cs * o.sigma, g2 = r * sn * o.sigma;
+                        s_cand[warp][c][0] = px + g1 * xx + g2 * yx;
+                        s_cand[warp][c][1] = py + g1 * xy + g2 * yy;
+                        s_cand[warp][c][2] = pz + g1 * xz + g2 * yz;
+                    }
+                    __syncwarp();
+                    // projection onto the domain: lanes scan mask words lane, lane + 32, ...
+                    float bd[NI];
+                    int bi[NI];
+#pragma unroll
+                    for (int c = 0; c < NI; ++c) { bd[c] = INFINITY; bi[c] = INT_MAX; }
+                    const uint32_t *row = a.masks + ((size_t)pose * F + fi) * W;
+                    for (int w = lane; w < W; w += 32) {
+                        uint32_t bits = __ldg(row + w);
+                        while (bits) {
+                            const int b = __ffs(bits) - 1;
+                            bits &= bits - 1;
+                            const int x = 32 * w + b;
+                            const float qx = __ldg(a.px + x), qy = __ldg(a.py + x), qz = __ldg(a.pz + x);
+#pragma unroll
+                            for (int c = 0; c < NI; ++c) {
+                                const float dx = qx - s_cand[warp][c][0], dy = qy - s_cand[warp][c][1],
+                                            dz = qz - s_cand[warp][c][2];
+                                const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+                                if (d2 < bd[c]) { bd[c] = d2; bi[c] = x; }
+                            }
+                        }
+                    }
+                    int cand_mine = -1;  // lane c < NI keeps candidate c's point
+#pragma unroll
+                    for (int c = 0; c < NI; ++c) {
+                        const unsigned kd = fkey(bd[c]);
+                        const unsigned kmin = __reduce_min_sync(kFull, kd);
+                        const unsigned imin = __reduce_min_sync(kFull, kd == kmin ? (unsigned)bi[c] : 0xffffffffu);
+                        if (lane == c) cand_mine = imin == 0xffffffffu ? -1 : (int)imin;
+                    }
+                    // candidates equal to the current point or to an earlier candidate cannot win
+                    const unsigned same = __match_any_sync(kFull, lane < NI ? cand_mine : -2 - lane);
+                    const bool skip = lane >= NI || cand_mine < 0 || cand_mine == x0 ||
+                                      (same & ((1u << lane) - 1u)) != 0u;
+                    const unsigned todo = __ballot_sync(kFull, !skip);
+                    float best = Jc, bestJ = J;
+                    int bestc = -1;
+                    for (unsigned m = todo; m; m &= m - 1) {
+                        const int c = __ffs(m) - 1;
+                        const int xc = __shfl_sync(kFull, cand_mine, c);
+                        const float Jt = tuple_margin(a, i == 0 ? xc : id[0], i == 1 ? xc : id[1],
+                                                      i == 2 ? xc : id[2], i == 3 ? xc : id[3], k, colA, ci, ec, es,
+                                                      lane, buf, n_piv, n_lp, flags);
+                        const float Jtc = Jt <= o.zero_tol ? 0.f : Jt;
+                        if (Jtc < best) { best = Jtc; bestJ = Jt; bestc = xc; }
+                    }
+                    if (bestc >= 0) {
+                        if (i == 0) id[0] = bestc; else if (i == 1) id[1] = bestc; else if (i == 2) id[2] = bestc; else id[3] = bestc;
+                        Jc = best;
+                        J = bestJ;
+                    }
+                }
+            }
+            ++n_tup;
+        }
+        if (lane == 0) {
+            if (valid)
+                for (int d = 0; d < k; ++d) a.tuples[(size_t)u * k + d] = id[d];
+            a.margin[u] = J;
+            a.accept[u] = (uint8_t)(J <= a.eps);
+        }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        atomicAdd(a.counters + 0, n_piv);
+        atomicAdd(a.counters + 1, n_lp);
+        atomicAdd(a.counters + 2, n_tup);
+        if (flags) atomicOr(a.status, flags);
+    }
+}
+
 }  // namespace
 
 size_t score_smem_bytes(int F, int W, int T, int k, bool sampling) {
@@ -496,6 +682,26 @@ cudaError_t launch_score(const ScoreArgs &a, cudaStream_t st) {
     cudaError_t err;
     if (!a.tuples_given && (err = launch_sample(a, st)) != cudaSuccess) return err;
     return launch_score_grid<false>(a, nullptr, nullptr, 0, (long long)a.P * a.T, st);
+}
+
+cudaError_t launch_optimize(const ScoreArgs &a, int n_outer, int n_inner, float sigma, float zero_tol,
+                            cudaStream_t st) {
+    if (a.P <= 0) return cudaSuccess;
+    const OptArgs o{n_outer, n_inner, sigma, zero_tol};
+    const long long total = (long long)a.P * a.T;
+    cudaError_t err;
+    int dev = 0, sms = 0;
+    if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
+    if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
+    const long long want = (total + kOptWarps - 1) / kOptWarps;
+    const int grid = (int)std::min<long long>((long long)sms * 16, want);
+    switch (n_inner) {
+        case 4: k_optimize_tuples<4><<<grid, kOptThreads, 0, st>>>(a, o, (unsigned)total); break;
+        case 8: k_optimize_tuples<8><<<grid, kOptThreads, 0, st>>>(a, o, (unsigned)total); break;
+        case 16: k_optimize_tuples<16><<<grid, kOptThreads, 0, st>>>(a, o, (unsigned)total); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_sample_batch(const ScoreArgs *d_descs, const long long *d_pose0, int n_desc, long long total_poses,

@@ -12,10 +12,10 @@ int32) so that both sides see bit-identical inputs.
 
 The paper's hands (Allegro, LEAP, Shadow, DClaw) and objects (YCB / Sketchfab
 meshes) are not available; the generators below stand in for them with the
-shapes, sizes and structure of the paper's workloads (Sec. 5, Table 1):
+shapes, sizes and structure of the paper's workloads (Sec. 6, Table 1):
 3/4/5-finger capsule hands, a sphere, a superquadric and an irregular
 tool-like composite, poses in a canonical placement box above the palm
-(Sec. 4.2, "Canonical Placement").
+(Sec. 5.2, "Canonical Placement").
 """
 from __future__ import annotations
 
@@ -33,7 +33,7 @@ __all__ = [
 
 # ---------------------------------------------------------------------------
 # normal-bin directions (the fixed direction set that quantises normals;
-# Sec. 3.3 "Memory Consumption": normals become an index on a fixed sphere set)
+# Sec. 4.3 "Memory Consumption": normals become an index on a fixed sphere set)
 # ---------------------------------------------------------------------------
 
 def fibonacci_dirs(B: int) -> np.ndarray:
@@ -227,7 +227,7 @@ def hand_anthropomorphic(n_fingers: int) -> Hand:
 
 def joint_samples(hand: Hand, S: int, seed: int) -> np.ndarray:
     """i.i.d. uniform joint configurations inside the limits, float32 [F,J,S]
-    (Sec. 3.3: the field is approximated by randomly sampled configurations)."""
+    (Sec. 4.3: the field is approximated by randomly sampled configurations)."""
     rng = np.random.default_rng(seed)
     u = rng.random((hand.F, hand.J, S))
     lo = hand.lo.astype(np.float64)[:, :, None]
@@ -440,7 +440,7 @@ def palm_poses(P: int, seed: int, grasp_centre: np.ndarray, obj_centroid: np.nda
                d_lo: float = 0.08, d_hi: float = 0.12) -> np.ndarray:
     """[P,12] float32 object->palm rigid transforms, row-major 3x4 (R | t).
 
-    Canonical placement (Sec. 4.2): the object centroid goes to
+    Canonical placement (Sec. 5.2): the object centroid goes to
     grasp_centre + d * z_palm, d ~ U[d_lo, d_hi], with a uniformly random
     rotation about the centroid."""
     rng = np.random.default_rng(seed)

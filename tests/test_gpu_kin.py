@@ -1,5 +1,5 @@
-"""GPU-vs-oracle parity of the kinematics rows (Sec. 4.5 reverse lookup + DLS
-IK, Sec. 4.6 post-processing), through the C ABI.
+"""GPU-vs-oracle parity of the kinematics rows (Sec. 5.5 reverse lookup + DLS
+IK, Sec. 5.6 post-processing), through the C ABI.
 
 Inputs are the oracle's own: its field, masks and sampled tuples feed both the
 library and the FP64 oracle.

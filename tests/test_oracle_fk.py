@@ -1,5 +1,5 @@
 """Pins for the oracle's forward kinematics and contact vectors
-(Sec. 2.1 notation; Def. "Contact Field (Point)": FK((p, n); i, q))."""
+(Sec. 3.1 notation; Def. "Contact Field (Point)": FK((p, n); i, q))."""
 import math
 
 import numpy as np

@@ -1,5 +1,5 @@
-"""Pins of the FP64 kinematics oracle (Sec. 4.5 kinematics optimisation,
-Sec. 4.6 post-processing) against closed forms, finite differences, an
+"""Pins of the FP64 kinematics oracle (Sec. 5.5 kinematics optimisation,
+Sec. 5.6 post-processing) against closed forms, finite differences, an
 independent least-squares route, brute force and analytic distance fields."""
 import math
 

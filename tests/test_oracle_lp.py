@@ -1,4 +1,4 @@
-"""Pins for the oracle's closure margin (Eq. GSWO, Sec. 2.2, linearised:
+"""Pins for the oracle's closure margin (Eq. GSWO, Sec. 3.2, linearised:
 K-edge inscribed friction pyramid, torque-weighted max-norm, one LP per
 j with alpha_j = 1, margin = min over j).  The LP solver is a library routine;
 these tests pin the LP it is given: brute-force vertex enumeration, the

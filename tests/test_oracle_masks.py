@@ -1,6 +1,6 @@
 """Pins for the oracle's contact field and contact-domain masks
-(Def. Contact Field (Hand); Def. Contact Surface Representation; Sec. 3.2
-contact domain CF(H) intersected with S(O); Sec. 3.3 Object Contact Query)."""
+(Def. Contact Field (Hand); Def. Contact Surface Representation; Sec. 4.2
+contact domain CF(H) intersected with S(O); Sec. 4.3 Object Contact Query)."""
 import math
 
 import numpy as np
@@ -144,7 +144,7 @@ def test_ambiguity_band_brackets_the_fp32_decision(tiny):
 
 
 def test_paper_normal_bin_cone_half_angle():
-    """Sec. 3.3: 256 directions give each a cone half-angle of about 7 degrees.
+    """Sec. 4.3: 256 directions give each a cone half-angle of about 7 degrees.
     The equal-area cap of 1/256 of the sphere has half-angle arccos(1 - 2/256);
     the oracle's binning of random directions onto a 256-point Fibonacci set
     stays within that scale."""

@@ -1,4 +1,4 @@
-"""Pins for the oracle's tuple sampling (Sec. 4.3: k domains of distinct
+"""Pins for the oracle's tuple sampling (Sec. 5.3: k domains of distinct
 fingers chosen at random; Alg. 2: (p_i, n_i) <- Random(D_i))."""
 import numpy as np
 
