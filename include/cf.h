@@ -320,6 +320,7 @@ typedef struct cf_opt_params {
     int32_t n_inner;    /* mutations per contact and iteration n_in: 4, 8 or 16 */
     float sigma;        /* standard deviation of each tangent-plane mutation component (m) */
     float zero_tol;     /* margins <= zero_tol count as 0 (a closed grasp): optimisation stops there */
+    float min_gain;     /* a candidate replaces the best so far only when its margin is < (1 - min_gain) x best */
 } cf_opt_params;
 
 /* Improves every valid tuple of d_tuples [P][T][k] in place (prm->tuples_given
@@ -331,9 +332,9 @@ typedef struct cf_opt_params {
  * seed: u1 = (w >> 8 + 1) 2^-24, u2 = (w' >> 8) 2^-24, g = sqrt(-2 ln u1)
  * (cos, sin)(2 pi u2).  Each mutation is projected onto finger f_i's domain at
  * the pose (the object point with its mask bit set nearest to it, lowest index
- * on ties), and contact i moves to the candidate of least closure margin if it
- * is lower than the current one (margins <= zero_tol count as 0; ties keep the
- * current point, then the lower candidate).  d_margin / d_accept receive the
+ * on ties).  Starting from the current point, the candidates in order replace
+ * the best so far when their closure margin is below (1 - min_gain) x best
+ * (margins <= zero_tol count as 0); contact i moves to the final best.  d_margin / d_accept receive the
  * final tuple's margin and margin <= eps.  Invalid tuples (an id < 0) are left
  * unchanged with margin +inf.  Errors: CF_EINVAL, CF_ENOMEM, CF_ECUDA. */
 int cf_optimize_tuples(const cf_points *obj, int32_t n_fingers, const uint32_t *d_masks, int32_t n_poses,

@@ -63,7 +63,8 @@ class IkParams(Structure):
 
 
 class OptParams(Structure):
-    _fields_ = [("n_outer", c_int32), ("n_inner", c_int32), ("sigma", c_float), ("zero_tol", c_float)]
+    _fields_ = [("n_outer", c_int32), ("n_inner", c_int32), ("sigma", c_float), ("zero_tol", c_float),
+                ("min_gain", c_float)]
 
 
 class RealizeParams(Structure):
@@ -551,8 +552,8 @@ class Plan:
             pass
 
 
-def opt_params(n_outer=2, n_inner=8, sigma=0.005, zero_tol=1e-6) -> OptParams:
-    return OptParams(int(n_outer), int(n_inner), float(sigma), float(zero_tol))
+def opt_params(n_outer=2, n_inner=8, sigma=0.005, zero_tol=1e-6, min_gain=1e-3) -> OptParams:
+    return OptParams(int(n_outer), int(n_inner), float(sigma), float(zero_tol), float(min_gain))
 
 
 def optimize_tuples(soa, n_fingers: int, masks, prm: ScoreParams, opt: OptParams, tuples, fingers, stream=None):

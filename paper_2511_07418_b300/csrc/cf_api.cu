@@ -653,6 +653,7 @@ extern "C" int cf_optimize_tuples(const cf_points *obj, int32_t n_fingers, const
         return fail(CF_EINVAL, "n_inner=%d not in {4, 8, 16}", opt->n_inner);
     if (!(opt->sigma >= 0.f) || !isfinite(opt->sigma)) return fail(CF_EINVAL, "sigma must be finite and >= 0");
     if (!(opt->zero_tol >= 0.f) || !isfinite(opt->zero_tol)) return fail(CF_EINVAL, "zero_tol must be >= 0");
+    if (!(opt->min_gain >= 0.f && opt->min_gain < 1.f)) return fail(CF_EINVAL, "min_gain must be in [0, 1)");
     ScoreArgs a;
     int rc = fill_score_args(obj, n_fingers, d_masks, nullptr, n_poses, prm, d_tuples, const_cast<uint8_t *>(d_fingers),
                              d_margin, d_accept, &a);
@@ -667,7 +668,7 @@ extern "C" int cf_optimize_tuples(const cf_points *obj, int32_t n_fingers, const
     cudaError_t e = cudaMemsetAsync(work, 0, sizeof(unsigned int), st);
     if (e == cudaSuccess) {
         a.work = work;
-        e = launch_optimize(a, opt->n_outer, opt->n_inner, opt->sigma, opt->zero_tol, st);
+        e = launch_optimize(a, opt->n_outer, opt->n_inner, opt->sigma, opt->zero_tol, opt->min_gain, st);
     }
     cudaError_t e2 = cudaFreeAsync(work, st);
     if (e != cudaSuccess) return cuda_fail(e, "launch k_optimize_tuples");

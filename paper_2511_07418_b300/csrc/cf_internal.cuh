@@ -265,7 +265,7 @@ size_t score_smem_bytes(int F, int W, int T, int k, bool sampling);
 // Alg. 2 contact optimisation of the tuples in place (a.tuples / a.fingers given;
 // a.masks, a.work zeroed, margin / accept out); n_inner in {4, 8, 16}
 cudaError_t launch_optimize(const ScoreArgs &a, int n_outer, int n_inner, float sigma, float zero_tol,
-                            cudaStream_t st);
+                            float min_gain, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // host helpers shared by the ABI translation units

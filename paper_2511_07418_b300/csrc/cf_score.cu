@@ -495,16 +495,16 @@ __device__ __forceinline__ float tuple_margin(const ScoreArgs &a, int id0, int i
 
 struct OptArgs {
     int n_outer, n_inner;
-    float sigma, zero_tol;
+    float sigma, zero_tol, min_gain;
 };
 
 // One warp per tuple (persistent warps, work counter).  Per outer iteration and
 // contact i: NI Gaussian mutations of p_i in its tangent plane (Box-Muller on
 // Philox4x32-10 words), each projected onto finger f_i's domain (the nearest
 // object point whose mask bit is set; all lanes scan the mask words, then one
-// warp reduction per candidate), then the argmin of the closure margin over
-// {current, candidates}: margins <= zero_tol count as 0, ties keep the lower
-// index (the current point first), so the margin never increases.
+// warp reduction per candidate), then the candidates in order replace the best
+// so far when their margin is lower by more than the relative min_gain (margins
+// <= zero_tol count as 0), so the margin never increases.
 template <int NI>
 __global__ void __launch_bounds__(kOptThreads) k_optimize_tuples(const ScoreArgs a, const OptArgs o, unsigned total) {
     __shared__ __align__(16) float s_buf[kOptWarps][16];
@@ -610,7 +610,7 @@ __global__ void __launch_bounds__(kOptThreads) k_optimize_tuples(const ScoreArgs
                                                       i == 2 ? xc : id[2], i == 3 ? xc : id[3], k, colA, ci, ec, es,
                                                       lane, buf, n_piv, n_lp, flags);
                         const float Jtc = Jt <= o.zero_tol ? 0.f : Jt;
-                        if (Jtc < best) { best = Jtc; bestJ = Jt; bestc = xc; }
+                        if (Jtc < (1.f - o.min_gain) * best) { best = Jtc; bestJ = Jt; bestc = xc; }
                     }
                     if (bestc >= 0) {
                         if (i == 0) id[0] = bestc; else if (i == 1) id[1] = bestc; else if (i == 2) id[2] = bestc; else id[3] = bestc;
@@ -685,9 +685,9 @@ cudaError_t launch_score(const ScoreArgs &a, cudaStream_t st) {
 }
 
 cudaError_t launch_optimize(const ScoreArgs &a, int n_outer, int n_inner, float sigma, float zero_tol,
-                            cudaStream_t st) {
+                            float min_gain, cudaStream_t st) {
     if (a.P <= 0) return cudaSuccess;
-    const OptArgs o{n_outer, n_inner, sigma, zero_tol};
+    const OptArgs o{n_outer, n_inner, sigma, zero_tol, min_gain};
     const long long total = (long long)a.P * a.T;
     cudaError_t err;
     int dev = 0, sms = 0;

@@ -1,0 +1,88 @@
+"""GPU-vs-oracle parity of the Alg. 2 contact optimisation (Sec. 5.4), through
+the C ABI.  The oracle's own masks and sampled tuples feed both sides.
+
+Acceptance rule: the oracle marks a tuple ambiguous when any decision on its
+path is within what FP32 may flip (two distinct domain points within a
+relative 1e-4 in squared distance, a replacement test within 2e-4 max(J, eps)
+of its threshold, a margin within a factor 2 of zero_tol); those stay below 5%
+of the tuples.  Every other tuple ends with the same contacts bit for bit, its
+margin agrees within 1e-4 max(t*, eps), and its accept flag is equal unless
+|t* - eps| <= 1e-4 max(t*, eps)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import contact_opt as CO
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def cf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2511_07418_b300 as cf
+    return cf
+
+
+def _inputs(name, P, S):
+    w = synth.workload(name, P=P, S=S)
+    fd = oracle.Field(w.hand, w.q, w.inv_h, w.bins)
+    soa = w.obj.soa()
+    m, c = fd.query(soa, w.poses)
+    tup, fing = oracle.sample_tuples(m, c, w.obj.N, w.T, w.k, w.seed)
+    return w, soa, m, tup, fing
+
+
+def _gpu(cf, w, soa, m, tup, fing, **kw):
+    prm = cf.score_params(w.T, w.k, w.mu, w.K, w.eps, w.obj.centroid, w.obj.rho, w.seed, tuples_given=True)
+    t = torch.from_numpy(tup.copy()).cuda()
+    margin, accept = cf.optimize_tuples(torch.from_numpy(soa).cuda(), w.hand.F,
+                                        torch.from_numpy(m.view(np.int32)).cuda(), prm, cf.opt_params(**kw), t,
+                                        torch.from_numpy(fing).cuda())
+    torch.cuda.synchronize()
+    return t.cpu().numpy(), margin.cpu().numpy(), accept.cpu().numpy()
+
+
+@pytest.mark.parametrize("name,P,S,n_inner", [("hand16_superquadric", 4, 8192, 8), ("tiny_sphere", 16, 4096, 8),
+                                              ("hand20_tool", 2, 8192, 8), ("hand16_superquadric", 2, 4096, 4),
+                                              ("tiny_sphere", 8, 2048, 16)])
+def test_optimize_parity(cf, name, P, S, n_inner):
+    w, soa, m, tup, fing = _inputs(name, P, S)
+    kw = dict(n_outer=2, n_inner=n_inner, sigma=0.005, zero_tol=1e-6, min_gain=1e-3)
+    gt, gm, ga = _gpu(cf, w, soa, m, tup, fing, **kw)
+    ot, om, oa, amb = CO.optimize_tuples(soa, m, tup, fing, w.T, w.mu, w.K, w.obj.centroid, w.obj.rho, w.eps, w.seed,
+                                         **kw)
+    assert cf.device_status() == 0
+    clear = ~amb
+    info = f"{name}: ambiguous {amb.mean():.4f}, changed {(ot != tup).any(-1).mean():.3f}"
+    print(info)
+    assert amb.mean() < 0.05, info
+    assert np.array_equal(gt[clear], ot[clear]), info
+    fin = clear & np.isfinite(om)
+    assert np.array_equal(np.isfinite(gm), np.isfinite(om)), info
+    err = np.abs(gm[fin] - np.maximum(om[fin], 0))
+    assert np.all(err <= 1e-4 * np.maximum(om[fin], w.eps)), (info, err.max())
+    firm = fin & (np.abs(om - w.eps) > 1e-4 * np.maximum(om, w.eps))
+    assert np.array_equal(ga[firm], oa[firm]), info
+
+
+def test_optimize_degenerate(cf):
+    w, soa, m, tup, fing = _inputs("tiny_sphere", 4, 1024)
+    prm = cf.score_params(w.T, w.k, w.mu, w.K, w.eps, w.obj.centroid, w.obj.rho, w.seed, tuples_given=True)
+    gt, gm, _ = _gpu(cf, w, soa, m, tup, fing, n_outer=0)
+    assert np.array_equal(gt, tup)
+    # no iteration: the margins are the closure margins of the given tuples
+    _, _, sm, sa = cf.score_tuples(torch.from_numpy(soa).cuda(), w.hand.F, None, None, prm,
+                                   tuples=torch.from_numpy(tup.copy()).cuda())
+    smn = sm.cpu().numpy()
+    assert np.array_equal(np.isfinite(gm), np.isfinite(smn))
+    f = np.isfinite(gm)
+    assert np.allclose(gm[f], smn[f], rtol=1e-5, atol=1e-7)
+    gt2, _, _ = _gpu(cf, w, soa, m, tup, fing, sigma=0.0)
+    assert np.array_equal(gt2, tup)
+    with pytest.raises(cf.CfError):
+        _gpu(cf, w, soa, m, tup, fing, n_inner=5)
