@@ -488,7 +488,7 @@ def run_realized(cf, torch, dev, w, steps, soa, poses, masks, counts, tuples, fi
 # contact optimisation (Alg. 2) on top of the sampled tuples
 # ---------------------------------------------------------------------------
 
-OPT = dict(n_outer=2, n_inner=8, sigma=0.005, zero_tol=1e-6, min_gain=1e-3)
+OPT = dict(n_outer=2, n_inner=8, sigma=0.005, zero_tol=1e-6, min_gain=1e-2)
 
 
 def run_optimized(cf, torch, dev, w, steps, soa, poses, masks, counts, tuples, fingers, prm, flush):

@@ -9,6 +9,11 @@ The steps of Alg. 2 in the paper's order, for one tuple (p_1, ..., p_k):
     [dx], [dy] = Normal(n_in, sigma^2) x, y     Box-Muller pairs of Philox words
     [p_i'] = p_i + [dx] + [dy]
     [p_i', n_i'] = Project([p_i'], D_i)          nearest point of the domain
+
+The projection decides an index, so it is taken in the kernel's precision: the
+normals in FP64 rounded to FP32, the tangent basis, mutated point and squared
+distances in FP32 with the same operations in the same order (no fused
+multiply-adds), which makes it bit-exact.
     (p_i, n_i) = argmin J over the candidates     J = closure margin (closure_lp)
 
 Readings (the paper leaves them open): the current point competes with the
@@ -22,10 +27,10 @@ counter (pose, tau, (it k + i) ceil(n_in / 2) + c / 2, 0xA162), key seed, words
 (2 (c mod 2), 2 (c mod 2) + 1) -> u1 = ((w >> 8) + 1) 2^-24,
 u2 = (w' >> 8) 2^-24, (g1, g2) = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2).
 
-Each decision that FP32 arithmetic could take the other way is recorded:
-a projection whose two nearest (distinct) domain points are within a relative
-1e-4 in squared distance, a replacement test within 2e-4 max(J, eps) of its
-threshold, or a margin within a factor 2 of zero_tol.  Tests compare
+Each decision the two sides could take differently is recorded: a normal whose
+FP64 value lies within a few FP64 ulps of an FP32 rounding boundary, a
+replacement test within 2e-4 max(J, eps) of its threshold (the closure-margin
+parity tolerance on each side), or a margin within a factor 2 of zero_tol.  Tests compare
 only tuples whose whole path is clear of those.
 """
 from __future__ import annotations
@@ -34,20 +39,33 @@ import math
 
 import numpy as np
 
-from . import _get_pool, _onb_duff, closure_lp, philox4x32_10
+from . import _get_pool, closure_lp, philox4x32_10
 
 OPT_TAG = 0xA162
 
 
+def _f32_checked(v: float):
+    """FP32 rounding of an FP64 value, and whether the value lies so close to a
+    rounding boundary (within a few FP64 ulps) that another correctly rounded
+    FP64 evaluation of the same expression could round the other way."""
+    f = np.float32(v)
+    lo = np.nextafter(f, np.float32(-np.inf))
+    hi = np.nextafter(f, np.float32(np.inf))
+    tol = 8.0 * float(np.spacing(abs(v))) if v != 0.0 else 0.0
+    amb = any(abs(v - (float(f) + float(b)) / 2.0) <= tol for b in (lo, hi))
+    return f, amb
+
+
 def box_muller(w0: int, w1: int):
+    """FP64 normal pair from two Philox words (u1 in (0, 1], u2 in [0, 1))."""
     u1 = ((int(w0) >> 8) + 1) * 2.0 ** -24
     u2 = (int(w1) >> 8) * 2.0 ** -24
     r = math.sqrt(-2.0 * math.log(u1))
-    return r * math.cos(2.0 * math.pi * u2), r * math.sin(2.0 * math.pi * u2)
+    return r * math.cos(math.pi * (2.0 * u2)), r * math.sin(math.pi * (2.0 * u2))
 
 
 def mutation_normals(pose: int, tau: int, it: int, i: int, k: int, n_in: int, seed: int):
-    """(g1, g2) of candidates 0 .. n_in-1 of block (it, i)."""
+    """(g1, g2) of candidates 0 .. n_in-1 of block (it, i), FP64."""
     per = (n_in + 1) // 2
     key = [int(seed) & 0xFFFFFFFF, (int(seed) >> 32) & 0xFFFFFFFF]
     out = []
@@ -58,17 +76,31 @@ def mutation_normals(pose: int, tau: int, it: int, i: int, k: int, n_in: int, se
     return out
 
 
-def project_to_domain(pts: np.ndarray, dom: np.ndarray, q: np.ndarray):
-    """Nearest domain point (lowest index on ties) to q; returns (index,
-    ambiguous).  Copies of the nearest point (same coordinates) tie exactly in
-    any precision and go to the lowest index; only a different point within a
-    relative 1e-4 in squared distance makes the choice ambiguous."""
-    d2 = np.sum((pts[dom] - q[None, :]) ** 2, axis=1)
-    o = np.argsort(d2, kind="stable")
-    best = int(dom[o[0]])
-    other = [j for j in o[1:] if not np.array_equal(pts[dom[j]], pts[best])][:1]
-    amb = bool(other) and (d2[other[0]] - d2[o[0]]) <= 1e-4 * d2[o[0]] + 1e-18
-    return best, bool(amb)
+def tangent_basis32(n):
+    """Duff et al. 2017 basis (x, y) of nu = -n, every operation rounded to FP32."""
+    f = np.float32
+    vx, vy, vz = -f(n[0]), -f(n[1]), -f(n[2])
+    sgn = f(math.copysign(1.0, float(vz)))
+    aa = f(-1.0) / (sgn + vz)
+    bb = (vx * vy) * aa
+    x = (f(1.0) + ((sgn * vx) * vx) * aa, sgn * bb, -(sgn * vx))
+    y = (bb, sgn + (vy * vy) * aa, -vy)
+    return x, y
+
+
+def mutate32(p, xv, yv, g1, g2, sigma):
+    """p + sigma (g1 x + g2 y) in FP32, operation by operation."""
+    f = np.float32
+    s = f(sigma)
+    return tuple(f(p[d]) + s * (g1 * xv[d] + g2 * yv[d]) for d in range(3))
+
+
+def project_to_domain(pts32: np.ndarray, dom: np.ndarray, q):
+    """Nearest domain point to q by FP32 squared distance ((dx dx + dy dy) + dz dz,
+    dx = x - q, each operation rounded), lowest index on ties."""
+    d = [pts32[dom, j] - np.float32(q[j]) for j in range(3)]
+    d2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]
+    return int(dom[int(np.argmin(d2))])
 
 
 def _margin(soa64, ids, mu, K, c, rho):
@@ -79,17 +111,18 @@ def _margin(soa64, ids, mu, K, c, rho):
 
 
 def optimize_tuple(soa, masks_pose, ids, fingers, pose, tau, mu, K, c, rho, eps, seed, n_outer, n_inner, sigma,
-                   zero_tol, min_gain=1e-3):
+                   zero_tol, min_gain=1e-2):
     """One tuple through Alg. 2.  masks_pose = [F][W] mask words of its pose.
     Returns (ids, margin, ambiguous)."""
     soa64 = np.asarray(soa, np.float64)
-    pts = soa64[0:3].T
     ids = [int(x) for x in ids]
     k = len(ids)
     N = soa64.shape[1]
     if any(x < 0 or x >= N for x in ids):
         return ids, math.inf, False
     amb = False
+    pts32 = np.ascontiguousarray(np.asarray(soa, np.float32)[0:3].T)
+    nrm32 = np.asarray(soa, np.float32)[3:6].T
     J = _margin(soa64, ids, mu, K, c, rho)
 
     def cls(v):
@@ -107,13 +140,14 @@ def optimize_tuple(soa, masks_pose, ids, fingers, pose, tau, mu, K, c, rho, eps,
                 break
             x0 = ids[i]
             dom = np.nonzero(bits[i][:N])[0]
-            xv, yv = _onb_duff(-soa64[3:6, x0])
+            xv, yv = tangent_basis32(nrm32[x0])
             cands = []
             for (g1, g2) in mutation_normals(pose, tau, it, i, k, n_inner, seed):
-                q = pts[x0] + sigma * (g1 * xv + g2 * yv)
-                xc, a = project_to_domain(pts, dom, q)
-                amb |= a
-                cands.append(xc)
+                g1f, a1 = _f32_checked(g1)
+                g2f, a2 = _f32_checked(g2)
+                amb |= a1 or a2
+                q = mutate32(pts32[x0], xv, yv, g1f, g2f, sigma)
+                cands.append(project_to_domain(pts32, dom, q))
             best_c, best_raw, best_x = Jc, J, x0
             seen = {x0}
             for xc in cands:
@@ -149,7 +183,7 @@ def _opt_chunk(args):
 
 
 def optimize_tuples(soa, masks, tuples, fingers, T, mu, K, c, rho, eps, seed, n_outer=2, n_inner=8, sigma=0.005,
-                    zero_tol=1e-6, min_gain=1e-3, workers: bool = True):
+                    zero_tol=1e-6, min_gain=1e-2, workers: bool = True):
     """All tuples [P,T,k] through Alg. 2: returns (tuples [P,T,k] int32,
     margin [P,T], accept [P,T] uint8, ambiguous [P,T] bool)."""
     P = masks.shape[0]

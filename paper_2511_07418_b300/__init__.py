@@ -552,7 +552,7 @@ class Plan:
             pass
 
 
-def opt_params(n_outer=2, n_inner=8, sigma=0.005, zero_tol=1e-6, min_gain=1e-3) -> OptParams:
+def opt_params(n_outer=2, n_inner=8, sigma=0.005, zero_tol=1e-6, min_gain=1e-2) -> OptParams:
     return OptParams(int(n_outer), int(n_inner), float(sigma), float(zero_tol), float(min_gain))
 
 

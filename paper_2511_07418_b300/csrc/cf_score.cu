@@ -541,29 +541,33 @@ __global__ void __launch_bounds__(kOptThreads) k_optimize_tuples(const ScoreArgs
                 for (int i = 0; i < k && Jc > 0.f; ++i) {
                     const int x0 = i == 0 ? id[0] : i == 1 ? id[1] : i == 2 ? id[2] : id[3];
                     const int fi = i == 0 ? fg[0] : i == 1 ? fg[1] : i == 2 ? fg[2] : fg[3];
-                    // tangent basis of nu = -n at the current point (Duff et al. 2017)
+                    // tangent basis of nu = -n at the current point (Duff et al. 2017); this
+                    // and the mutated points use explicitly rounded FP32 operations, so the
+                    // projection below (an index decision) is reproducible operation by operation
                     const float px = __ldg(a.px + x0), py = __ldg(a.py + x0), pz = __ldg(a.pz + x0);
                     const float vx = -__ldg(a.nx + x0), vy = -__ldg(a.ny + x0), vz = -__ldg(a.nz + x0);
                     const float sgn = copysignf(1.f, vz);
-                    const float aa = -1.f / (sgn + vz);
-                    const float bb = vx * vy * aa;
-                    const float xx = 1.f + sgn * vx * vx * aa, xy = sgn * bb, xz = -sgn * vx;
-                    const float yx = bb, yy = sgn + vy * vy * aa, yz = -vy;
-                    if (lane < NI) {  // candidate `lane`: one Box-Muller pair
+                    const float aa = __fdiv_rn(-1.f, __fadd_rn(sgn, vz));
+                    const float bb = __fmul_rn(__fmul_rn(vx, vy), aa);
+                    const float xx = __fadd_rn(1.f, __fmul_rn(__fmul_rn(__fmul_rn(sgn, vx), vx), aa));
+                    const float xy = __fmul_rn(sgn, bb), xz = -__fmul_rn(sgn, vx);
+                    const float yx = bb, yy = __fadd_rn(sgn, __fmul_rn(__fmul_rn(vy, vy), aa)), yz = -vy;
+                    if (lane < NI) {  // candidate `lane`: one Box-Muller pair, FP64 then rounded to FP32
                         const int c = lane;
                         const uint4 w4 = philox4x32_10(
                             make_uint4(pid, (uint32_t)tau, (uint32_t)((it * k + i) * blocks_per_draw + c / 2), 0xA162u),
                             key);
                         const uint32_t w0 = (c & 1) ? w4.z : w4.x, w1 = (c & 1) ? w4.w : w4.y;
-                        const float u1 = (float)((w0 >> 8) + 1u) * 5.9604644775390625e-8f;  // (0, 1]
-                        const float u2 = (float)(w1 >> 8) * 5.9604644775390625e-8f;         // [0, 1)
-                        const float r = sqrtf(-2.f * logf(u1));
-                        float sn, cs;
-                        sincospif(2.f * u2, &sn, &cs);
-                        const float g1 = r * cs * o.sigma, g2 = r * sn * o.sigma;
-                        s_cand[warp][c][0] = px + g1 * xx + g2 * yx;
-                        s_cand[warp][c][1] = py + g1 * xy + g2 * yy;
-                        s_cand[warp][c][2] = pz + g1 * xz + g2 * yz;
+                        const double u1 = (double)((w0 >> 8) + 1u) * 5.9604644775390625e-8;  // (0, 1]
+                        const double u2 = (double)(w1 >> 8) * 5.9604644775390625e-8;         // [0, 1)
+                        const double r = sqrt(-2.0 * log(u1));
+                        double sd, cd;
+                        sincospi(2.0 * u2, &sd, &cd);
+                        const float g1 = (float)(r * cd), g2 = (float)(r * sd);
+                        const float sg = o.sigma;
+                        s_cand[warp][c][0] = __fadd_rn(px, __fmul_rn(sg, __fadd_rn(__fmul_rn(g1, xx), __fmul_rn(g2, yx))));
+                        s_cand[warp][c][1] = __fadd_rn(py, __fmul_rn(sg, __fadd_rn(__fmul_rn(g1, xy), __fmul_rn(g2, yy))));
+                        s_cand[warp][c][2] = __fadd_rn(pz, __fmul_rn(sg, __fadd_rn(__fmul_rn(g1, xz), __fmul_rn(g2, yz))));
                     }
                     __syncwarp();
                     // projection onto the domain: lanes scan mask words lane, lane + 32, ...
@@ -581,9 +585,9 @@ __global__ void __launch_bounds__(kOptThreads) k_optimize_tuples(const ScoreArgs
                             const float qx = __ldg(a.px + x), qy = __ldg(a.py + x), qz = __ldg(a.pz + x);
 #pragma unroll
                             for (int c = 0; c < NI; ++c) {
-                                const float dx = qx - s_cand[warp][c][0], dy = qy - s_cand[warp][c][1],
-                                            dz = qz - s_cand[warp][c][2];
-                                const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+                                const float dx = __fsub_rn(qx, s_cand[warp][c][0]), dy = __fsub_rn(qy, s_cand[warp][c][1]),
+                                            dz = __fsub_rn(qz, s_cand[warp][c][2]);
+                                const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
                                 if (d2 < bd[c]) { bd[c] = d2; bi[c] = x; }
                             }
                         }

@@ -52,7 +52,7 @@ def _gpu(cf, w, soa, m, tup, fing, **kw):
                                               ("tiny_sphere", 8, 2048, 16)])
 def test_optimize_parity(cf, name, P, S, n_inner):
     w, soa, m, tup, fing = _inputs(name, P, S)
-    kw = dict(n_outer=2, n_inner=n_inner, sigma=0.005, zero_tol=1e-6, min_gain=1e-3)
+    kw = dict(n_outer=2, n_inner=n_inner, sigma=0.005, zero_tol=1e-6, min_gain=1e-2)
     gt, gm, ga = _gpu(cf, w, soa, m, tup, fing, **kw)
     ot, om, oa, amb = CO.optimize_tuples(soa, m, tup, fing, w.T, w.mu, w.K, w.obj.centroid, w.obj.rho, w.eps, w.seed,
                                          **kw)

@@ -35,19 +35,37 @@ def test_box_muller_extremes():
 
 def test_projection_is_nearest_domain_point():
     rng = np.random.default_rng(1)
-    pts = rng.normal(size=(500, 3))
+    pts = rng.normal(size=(500, 3)).astype(np.float32)
     dom = np.sort(rng.choice(500, 120, replace=False))
     for _ in range(50):
-        q = rng.normal(size=3)
-        x, _ = CO.project_to_domain(pts, dom, q)
+        q = rng.normal(size=3).astype(np.float32)
+        x = CO.project_to_domain(pts, dom, q)
         assert x in dom
-        d = np.linalg.norm(pts[dom] - q, axis=1)
-        assert np.linalg.norm(pts[x] - q) <= d.min() + 1e-15
-    # exact copies of the nearest point: lowest index, not ambiguous
-    pts2 = np.vstack([pts, pts[dom[5]]])
+        d = np.linalg.norm(pts[dom].astype(np.float64) - q, axis=1)
+        assert np.linalg.norm(pts[x].astype(np.float64) - q) <= d.min() * (1 + 1e-6)
+    # exact copies of the nearest point: the lowest index
+    pts2 = np.vstack([pts, pts[dom[5]][None]])
     dom2 = np.append(dom, 500)
-    x, amb = CO.project_to_domain(pts2, dom2, pts[dom[5]] + 1e-9)
-    assert x == dom[5] and not amb
+    assert CO.project_to_domain(pts2, dom2, pts[dom[5]]) == dom[5]
+
+
+def test_tangent_basis32_is_orthonormal():
+    rng = np.random.default_rng(2)
+    for _ in range(200):
+        n = rng.normal(size=3)
+        n /= np.linalg.norm(n)
+        x, y = CO.tangent_basis32(n.astype(np.float32))
+        x, y = np.array(x, np.float64), np.array(y, np.float64)
+        assert abs(x @ y) < 1e-6 and abs(x @ n) < 1e-6 and abs(y @ n) < 1e-6
+        assert abs(np.linalg.norm(x) - 1) < 1e-6 and abs(np.linalg.norm(y) - 1) < 1e-6
+
+
+def test_f32_rounding_check():
+    f, amb = CO._f32_checked(0.1)
+    assert f == np.float32(0.1) and not amb
+    one = np.float32(1.0)
+    mid = (1.0 + float(np.nextafter(one, np.float32(2.0)))) / 2.0  # a tie between two floats
+    assert CO._f32_checked(mid)[1]
 
 
 @pytest.fixture(scope="module")
