@@ -55,6 +55,7 @@ def _args():
     ap.add_argument("--served-rates", default="10,100,1000")
     ap.add_argument("--realized-steps", type=int, default=20, help="steps of the IK + realization leg (0: skip)")
     ap.add_argument("--optimized-steps", type=int, default=5, help="steps of the Alg. 2 optimisation leg (0: skip)")
+    ap.add_argument("--gswo-steps", type=int, default=10, help="steps of the Eq. GSWO scoring leg (0: skip)")
     return ap.parse_args()
 
 
@@ -382,6 +383,10 @@ def run_ours(args):
     if world == 1 and args.optimized_steps > 0:
         line["optimized"] = run_optimized(cf, torch, dev, w, args.optimized_steps, soa, poses, masks, counts, tuples,
                                           fingers, prm, flush)
+    if world == 1 and args.gswo_steps > 0:
+        line["gswo"] = run_gswo(cf, torch, dev, w, args.gswo_steps, soa, poses, masks, counts, tuples, fingers, prm,
+                                prm_given, flush)
+        line["gswo"]["frac_of_fp32"] = line["gswo"]["gswo_tflops"] / peak_fp32
     if world == 1 and (args.batch_objects > 0 or args.served_seconds > 0):
         ws, fields = _hand_fields(cf, torch, dev)
         if args.batch_objects > 0:
@@ -538,6 +543,66 @@ def run_optimized(cf, torch, dev, w, steps, soa, poses, masks, counts, tuples, f
             "lp_per_tuple": counters["lps"] / max(1, counters["tuples_scored"]),
             "pivots_per_lp": counters["lp_pivots"] / max(1, counters["lps"]),
             "gpu_launches_per_step": 4, "device_status": cf.device_status()}
+
+
+# ---------------------------------------------------------------------------
+# the paper's own metric: Eq. GSWO with true friction cones
+# ---------------------------------------------------------------------------
+
+GSWO_ITERS = 256
+GSWO_EPS = 1e-4   # on the squared objective (the LP's eps = 1e-2 on the max-norm, squared)
+
+
+def run_gswo(cf, torch, dev, w, steps, soa, poses, masks, counts, tuples, fingers, prm, prm_given, flush):
+    """Valid grasps/s when the sampled tuples are scored with Eq. GSWO (true
+    cones, squared L2, accelerated projected gradient) instead of the
+    linearised LP.  One step = domain query, tuple sampling, GSWO scoring; the
+    field is built once, outside.  Also reports how often the two metrics agree
+    on acceptance (LP scores computed outside the timed steps)."""
+    import numpy as np
+    F = w.hand.F
+    q = torch.from_numpy(w.q).to(dev)
+    field = cf.build(w.hand, w.inv_h, w.bins, q)
+    tot = torch.zeros(1, dtype=torch.int64, device=dev)
+    n_ev = 4
+
+    def step(ev):
+        ev[0].record()
+        cf.query_domains(field, soa, poses, masks, counts)
+        ev[1].record()
+        cf.sample_tuples(soa, F, masks, counts, prm, tuples, fingers)
+        ev[2].record()
+        _, accept = cf.score_gswo(soa, prm_given, tuples, GSWO_ITERS, GSWO_EPS)
+        ev[3].record()
+        tot.add_(accept.sum())
+        return accept
+
+    for _ in range(3):
+        step([torch.cuda.Event(enable_timing=True) for _ in range(n_ev)])
+    tot.zero_()
+    evs = []
+    for i in range(steps):
+        flush.fill_(float(i))
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(n_ev)]
+        acc_g = step(ev)
+        evs.append(ev)
+    torch.cuda.synchronize()
+    _, _, _, acc_lp = cf.score_tuples(soa, F, None, None, prm_given, tuples)
+    agree = float((acc_lp.view(-1) == acc_g.view(-1)).float().mean().item())
+    ms = np.array([[e[j].elapsed_time(e[j + 1]) for j in range(n_ev - 1)] for e in evs])
+    acc = int(tot.item())
+    total_ms = float(ms.sum())
+    per = ms.mean(axis=0)
+    k = w.k
+    # FMA per tuple: k subproblems x (Q y 9k^2 + step 3k + momentum 6k + projections 10k) per iteration
+    fma_tuple = k * GSWO_ITERS * (9 * k * k + 19 * k)
+    return {"metric": "valid grasps/s under Eq. GSWO (true cones)", "value": acc / (total_ms / 1e3),
+            "unit": UNIT, "steps": steps, "ms_per_step": total_ms / steps,
+            "breakdown_ms": {"query": float(per[0]), "sample": float(per[1]), "gswo": float(per[2])},
+            "accept_rate": acc / (steps * w.P * w.T), "agreement_with_lp_accept": agree,
+            "params": {"n_iter": GSWO_ITERS, "eps_g": GSWO_EPS},
+            "gswo_tflops": w.P * w.T * 2 * fma_tuple / (per[2] * 1e-3) / 1e12,
+            "gpu_launches_per_step": 3, "device_status": cf.device_status()}
 
 
 # ---------------------------------------------------------------------------

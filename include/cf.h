@@ -313,6 +313,20 @@ int cf_realize(const cf_field *field, const cf_sdf *sdf, const float *d_poses, i
                const cf_realize_params *prm, const uint8_t *d_gate_a, const uint8_t *d_gate_b, float *d_q,
                const uint8_t *d_used, uint8_t *d_flags, cf_stream stream);
 
+/* ---- Eq. GSWO with true friction cones (Sec. 3.2) ------------------------ */
+
+/* The paper's own metric for given tuples d_tuples [P][T][k] (prm: T, k, mu,
+ * centroid, rho; n_edges, eps and seed unused): contact i applies
+ * f_i = alpha_i nu_i + bx_i x_i + by_i y_i (nu_i = -n_i, (x_i, y_i) the Duff et
+ * al. 2017 basis of nu_i); J_j = min |sum f_i|^2 + |sum (p_i - c) x f_i|^2 / rho^2
+ * s.t. alpha_j = 1, |b_j| <= mu, |b_i| <= mu alpha_i (i != j); d_value = min_j J_j,
+ * d_accept = d_value <= eps_g.  Each J_j is the value after n_iter projected
+ * gradient steps with Nesterov momentum (FISTA), step 1 / (2 tr(A^T A)), from
+ * alpha = e_j, beta = 0 (an upper bound that tightens with n_iter).  Invalid
+ * tuples (an id < 0) get +inf.  Errors: CF_EINVAL, CF_ECUDA.  Asynchronous. */
+int cf_score_gswo(const cf_points *obj, int32_t n_poses, const cf_score_params *prm, int32_t n_iter, float eps_g,
+                  const int32_t *d_tuples, float *d_value, uint8_t *d_accept, cf_stream stream);
+
 /* ---- Alg. 2: blockwise zeroth-order contact optimisation (Sec. 5.4) ------ */
 
 typedef struct cf_opt_params {

@@ -168,6 +168,8 @@ _cf_sdf_destroy = _sig("cf_sdf_destroy", [c_void_p])
 _cf_realize = _sig("cf_realize", [c_void_p, c_void_p, c_void_p, c_int32, c_int32, POINTER(RealizeParams), c_void_p,
                                   c_void_p, c_void_p, c_void_p, c_void_p, c_void_p])
 _cf_fp32_peak = _sig("cf_fp32_peak", [POINTER(c_double)])
+_cf_gswo = _sig("cf_score_gswo", [POINTER(Points), c_int32, POINTER(ScoreParams), c_int32, c_float, c_void_p, c_void_p,
+                                  c_void_p, c_void_p])
 _cf_optimize = _sig("cf_optimize_tuples", [POINTER(Points), c_int32, c_void_p, c_int32, POINTER(ScoreParams),
                                            POINTER(OptParams), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p])
 _cf_last_error = _sig("cf_last_error", [], c_char_p)
@@ -180,7 +182,7 @@ EXPORTED = ["cf_build", "cf_field_get_info", "cf_field_copy_table", "cf_field_de
             "cf_sample_tuples", "cf_batch_create", "cf_batch_run", "cf_batch_launches", "cf_batch_destroy",
             "cf_engine_create", "cf_engine_submit", "cf_engine_poll", "cf_engine_result_free", "cf_engine_get_stats",
             "cf_engine_drain", "cf_engine_destroy", "cf_field_rep_slots", "cf_field_copy_rep", "cf_ik_dls",
-            "cf_sdf_build", "cf_sdf_copy", "cf_sdf_destroy", "cf_realize", "cf_fp32_peak", "cf_optimize_tuples"]
+            "cf_sdf_build", "cf_sdf_copy", "cf_sdf_destroy", "cf_realize", "cf_fp32_peak", "cf_optimize_tuples", "cf_score_gswo"]
 
 
 def _check(rc: int):
@@ -550,6 +552,18 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def score_gswo(soa, prm: ScoreParams, tuples, n_iter: int = 256, eps_g: float = 1e-4, stream=None):
+    """cf_score_gswo over tuples [P,T,k] -> (value [P,T] f32, accept [P,T] u8)."""
+    import torch
+    obj = points_struct(soa)
+    P, T = int(tuples.shape[0]), int(prm.n_tuples)
+    value = torch.empty((P, T), dtype=torch.float32, device=soa.device)
+    accept = torch.empty((P, T), dtype=torch.uint8, device=soa.device)
+    _check(_cf_gswo(byref(obj), P, byref(prm), int(n_iter), float(eps_g), _dev(tuples, torch.int32, "tuples"),
+                    _dev(value, torch.float32, "value"), _dev(accept, torch.uint8, "accept"), _stream(stream)))
+    return value, accept
 
 
 def opt_params(n_outer=2, n_inner=8, sigma=0.005, zero_tol=1e-6, min_gain=1e-2) -> OptParams:

@@ -641,6 +641,28 @@ extern "C" int cf_score_tuples(const cf_points *obj, int32_t n_fingers, const ui
     return CF_OK;
 }
 
+extern "C" int cf_score_gswo(const cf_points *obj, int32_t n_poses, const cf_score_params *prm, int32_t n_iter,
+                             float eps_g, const int32_t *d_tuples, float *d_value, uint8_t *d_accept,
+                             cf_stream stream) {
+    int rc = check_points(obj);
+    if (rc) return rc;
+    if (!prm) return fail(CF_EINVAL, "params is NULL");
+    if (n_poses < 0 || prm->n_tuples < 1) return fail(CF_EINVAL, "n_poses < 0 or n_tuples < 1");
+    if (prm->k < 2 || prm->k > CF_MAX_K) return fail(CF_EINVAL, "k=%d not in [2,%d]", prm->k, CF_MAX_K);
+    if (!(prm->mu >= 0.f) || !isfinite(prm->mu)) return fail(CF_EINVAL, "mu must be finite and >= 0");
+    if (!(prm->rho > 0.f) || !isfinite(prm->rho)) return fail(CF_EINVAL, "rho must be finite and > 0");
+    if (n_iter < 0 || n_iter > 1000000) return fail(CF_EINVAL, "n_iter=%d out of range", n_iter);
+    if (!isfinite(eps_g)) return fail(CF_EINVAL, "eps_g must be finite");
+    const long long n = (long long)n_poses * prm->n_tuples;
+    if (n == 0) return CF_OK;
+    if (!d_tuples || !d_value || !d_accept) return fail(CF_EINVAL, "array pointer is NULL");
+    const float *pts[6] = {obj->px, obj->py, obj->pz, obj->nx, obj->ny, obj->nz};
+    CF_TRY(launch_gswo(pts, obj->n, n, prm->k, prm->mu, prm->centroid, prm->rho, eps_g, n_iter, d_tuples, d_value,
+                       d_accept, (cudaStream_t)stream),
+           "launch k_gswo");
+    return CF_OK;
+}
+
 extern "C" int cf_optimize_tuples(const cf_points *obj, int32_t n_fingers, const uint32_t *d_masks, int32_t n_poses,
                                   const cf_score_params *prm, const cf_opt_params *opt, int32_t *d_tuples,
                                   const uint8_t *d_fingers, float *d_margin, uint8_t *d_accept, cf_stream stream) {

@@ -210,6 +210,8 @@ cudaError_t launch_ik(const IkArgs &a, int *list, unsigned int *count, cudaStrea
 cudaError_t launch_sdf(const cf_points &obj, const SdfGrid &g, float *grid, cudaStream_t st);
 cudaError_t launch_realize(const RealizeArgs &a, cudaStream_t st);
 
+cudaError_t launch_gswo(const float *const pts[6], int N, long long n, int k, float mu, const float c[3], float rho,
+                        float eps, int n_iter, const int32_t *tuples, float *value, uint8_t *accept, cudaStream_t st);
 cudaError_t launch_popcount(const uint32_t *table, long long words, unsigned long long *count, cudaStream_t st);
 cudaError_t launch_fk_rep(const HandDev &h, const float *links, int S, const FieldGeom &g, RepTable t,
                           unsigned int *status, cudaStream_t st);

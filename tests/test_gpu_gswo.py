@@ -1,0 +1,69 @@
+"""GPU-vs-oracle parity of the paper's own metric, Eq. GSWO with true friction
+cones (Sec. 3.2), through the C ABI.  Both sides run the same accelerated
+projected-gradient iteration (the kernel in FP32, the oracle in FP64) on the
+oracle's sampled tuples.
+
+Acceptance rule: values agree within 1e-3 max(J, eps_g) (the iteration is a
+non-expansive map composed with momentum; FP32 rounding of ~1e-7 per step
+stays below that after 256 steps), and accept flags are equal unless the oracle
+value lies within that band of eps_g."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import gswo as G
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+EPS_G = 1e-4
+REL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def cf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2511_07418_b300 as cf
+    return cf
+
+
+@pytest.mark.parametrize("name,P,S,n_iter", [("hand16_superquadric", 2, 4096, 256), ("tiny_sphere", 8, 2048, 256),
+                                             ("hand20_tool", 1, 4096, 256), ("tiny_sphere", 2, 1024, 32)])
+def test_gswo_parity(cf, name, P, S, n_iter):
+    w = synth.workload(name, P=P, S=S)
+    fd = oracle.Field(w.hand, w.q, w.inv_h, w.bins)
+    soa = w.obj.soa()
+    m, c = fd.query(soa, w.poses)
+    tup, _ = oracle.sample_tuples(m, c, w.obj.N, w.T, w.k, w.seed)
+    prm = cf.score_params(w.T, w.k, w.mu, w.K, w.eps, w.obj.centroid, w.obj.rho, w.seed, tuples_given=True)
+    gv, ga = cf.score_gswo(torch.from_numpy(soa).cuda(), prm, torch.from_numpy(tup).cuda(), n_iter, EPS_G)
+    torch.cuda.synchronize()
+    gv, ga = gv.cpu().numpy().astype(np.float64), ga.cpu().numpy()
+    ov = G.score_gswo(soa, tup, w.mu, w.obj.centroid, w.obj.rho, n_iter)
+    fin = np.isfinite(ov)
+    assert np.array_equal(np.isfinite(gv), fin)
+    err = np.abs(gv[fin] - ov[fin]) / np.maximum(ov[fin], EPS_G)
+    print(f"{name}: {fin.sum()} tuples, max relative error {err.max():.3g}, accept {ga[fin].mean():.3f}")
+    assert err.max() <= REL
+    firm = fin & (np.abs(ov - EPS_G) > REL * np.maximum(ov, EPS_G))
+    assert np.array_equal(ga[firm], (ov[firm] <= EPS_G).astype(np.uint8))
+    assert np.all(ga[~fin] == 0)
+
+
+def test_gswo_edge_cases(cf):
+    w = synth.workload("tiny_sphere", P=1, S=64)
+    soa = torch.from_numpy(w.obj.soa()).cuda()
+    prm = cf.score_params(2, 2, w.mu, w.K, w.eps, w.obj.centroid, w.obj.rho, w.seed, tuples_given=True)
+    t = torch.tensor([[[0, 1], [-1, 3]]], dtype=torch.int32).cuda()
+    v, a = cf.score_gswo(soa, prm, t, 0, EPS_G)  # no step: J_j at alpha = e_j
+    v = v.cpu().numpy()
+    assert np.isinf(v[0, 1]) and np.isfinite(v[0, 0])
+    s = w.obj.soa().astype(np.float64)
+    A = G.gswo_matrix(s[0:3, [0, 1]].T, s[3:6, [0, 1]].T, w.obj.centroid, w.obj.rho)
+    ref = min(float(A[:, 0] @ A[:, 0]), float(A[:, 3] @ A[:, 3]))
+    assert abs(v[0, 0] - ref) <= 1e-5 * ref
+    with pytest.raises(cf.CfError):
+        cf.score_gswo(soa, cf.score_params(2, 1, w.mu, w.K, w.eps, w.obj.centroid, w.obj.rho, 0, True), t, 8)
