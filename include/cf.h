@@ -100,6 +100,9 @@ typedef struct cf_field_params {
     const float *bin_dirs;    /* host [B][3] */
     int32_t want_rep;         /* 1: also keep, per (cell, finger, bin) code, the smallest s * M + m of the
                                  samples that produced it (reverse lookup, Sec. 5.5) */
+    float dilate_cos;         /* theta-dilated bins (the leaf test -x^T n >= theta_hit of Sec. 4.3): a query
+                                 of bin b accepts every bin b' with d_b . d_b' >= dilate_cos (FP64 on the
+                                 host); > 1 (e.g. 2) = same bin only */
 } cf_field_params;
 
 typedef struct cf_field cf_field;
@@ -121,6 +124,8 @@ typedef struct cf_field_info {
     int64_t table_words;               /* total uint32 words of the bit table */
     int64_t device_bytes;              /* device memory held by the field */
     float build_ms;                    /* device time of the two build kernels */
+    float dilate_cos;                  /* bin dilation of queries (> 1: none) */
+    uint32_t dilation[CF_MAX_BINS];    /* bins accepted by a query of bin b */
 } cf_field_info;
 
 /* Object surface points + outward unit normals, device SoA, N each. */

@@ -48,7 +48,7 @@ _LIB = os.path.join(_HERE, "liborc.so")
 
 __all__ = ["build", "lib", "philox4x32_10", "fk_links", "contact_vectors", "Field",
            "query_masks_brute", "sample_tuples", "closure_lp", "score_tuples", "num_threads", "pack_code",
-           "rep_codes", "point_codes"]
+           "rep_codes", "point_codes", "dilation_masks"]
 
 
 def build(force: bool = False) -> str:
@@ -87,7 +87,8 @@ def lib():
         L.orc_field_codes.argtypes = [c_void_p, c_int, POINTER(c_uint64), c_int64]
         L.orc_query_masks.argtypes = [c_void_p, c_int, fp, c_int, fp, u32p, u32p, u8p, u32p]
         L.orc_query_masks_brute.argtypes = [c_int, c_int, c_int, fp, fp, fp, fp, fp, i32p, fp, c_int, c_float,
-                                            c_int, fp, c_int, fp, c_int, fp, u32p]
+                                            c_int, fp, c_int, fp, c_int, fp, u32p, u32p]
+        L.orc_field_set_dilation.argtypes = [c_void_p, u32p]
         L.orc_sample_tuples.argtypes = [c_int, c_int, c_int, u32p, u32p, c_int, c_int, c_uint64, i32p, u8p]
         L.orc_num_threads.restype = c_int
         L.orc_rep_codes.restype = c_int64
@@ -164,7 +165,7 @@ class Field:
     sets used to flag ambiguous entries (tau metres, bin_tol in cosine)."""
 
     def __init__(self, hand, q: np.ndarray, inv_h, bins: np.ndarray, band: bool = False,
-                 tau: float = 1e-5, bin_tol: float = 1e-6):
+                 tau: float = 1e-5, bin_tol: float = 1e-6, dilate_cos=None):
         self.F, self.J, self.M = hand.F, hand.J, hand.M
         self.B = int(bins.shape[0])
         self.inv_h = np.float32(inv_h)
@@ -176,6 +177,9 @@ class Field:
         self._h = lib().orc_field_create(self.F, self.J, self.M, *ptrs, _p(qq, c_float), S, c_float(self.inv_h),
                                          self.B, _p(self._bins, c_float), int(band), tau, bin_tol)
         del keep
+        self.dilation = dilation_masks(self._bins, dilate_cos) if dilate_cos is not None else None
+        if self.dilation is not None:
+            lib().orc_field_set_dilation(self._h, _p(self.dilation, c_uint32))
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -225,7 +229,24 @@ class Field:
         return tuple(out)
 
 
-def query_masks_brute(hand, q, inv_h, bins, soa, poses) -> np.ndarray:
+def dilation_masks(bins: np.ndarray, dilate_cos: float) -> np.ndarray:
+    """Theta-dilated bins (the leaf test -x^T n >= theta_hit of Sec. 4.3): bit b'
+    of entry b is set when d_b . d_b' >= dilate_cos (FP64 dot of the FP32
+    directions, x + y + z in that order); bit b always."""
+    d = np.asarray(bins, np.float32).astype(np.float64)
+    B = d.shape[0]
+    out = np.zeros(B, np.uint32)
+    for b in range(B):
+        m = 1 << b
+        for b2 in range(B):
+            dot = float(d[b, 0]) * float(d[b2, 0]) + float(d[b, 1]) * float(d[b2, 1]) + float(d[b, 2]) * float(d[b2, 2])
+            if dot >= float(np.float32(dilate_cos)):
+                m |= 1 << b2
+        out[b] = m
+    return out
+
+
+def query_masks_brute(hand, q, inv_h, bins, soa, poses, dilate_cos=None) -> np.ndarray:
     keep, ptrs = _hand_args(hand)
     qq = _c(q, np.float32)
     bb = _c(bins, np.float32)
@@ -234,9 +255,11 @@ def query_masks_brute(hand, q, inv_h, bins, soa, poses) -> np.ndarray:
     N, P = int(soa.shape[1]), int(poses.shape[0])
     W = (N + 31) // 32
     masks = np.zeros((P, hand.F, W), np.uint32)
+    dil = dilation_masks(bb, dilate_cos) if dilate_cos is not None else None
     lib().orc_query_masks_brute(hand.F, hand.J, hand.M, *ptrs, _p(qq, c_float), int(qq.shape[2]),
                                 c_float(np.float32(inv_h)), int(bb.shape[0]), _p(bb, c_float), N,
-                                _p(soa, c_float), P, _p(poses, c_float), _p(masks, c_uint32))
+                                _p(soa, c_float), P, _p(poses, c_float),
+                                _p(dil, c_uint32) if dil is not None else None, _p(masks, c_uint32))
     del keep
     return masks
 

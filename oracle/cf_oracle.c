@@ -226,7 +226,17 @@ typedef struct {
     keyvec *kpos;  /* [F] codes a sample could take within the band */
     keyvec *ksure; /* [F] codes of samples whose code is the same everywhere in the band */
     int64_t n_samples_out_of_range;
+    uint32_t dil[64]; /* bins a query of bin b accepts (theta-dilated bins, Sec. 4.3 leaf test); bit b alone by default */
 } orc_field;
+
+/* does finger f's code set hold cell (kx, ky, kz) with any bin of `bins`? */
+static int has_any_bin(const keyvec *kv, int f, int64_t kx, int64_t ky, int64_t kz, uint32_t bins) {
+    for (; bins; bins &= bins - 1) {
+        const int b = __builtin_ctz(bins);
+        if (kv_has(kv, pack_key(f, kx, ky, kz, b))) return 1;
+    }
+    return 0;
+}
 
 /* candidate codes of a vector within the tolerance band (FP64) */
 static int band_cells(double x, double tau, double inv_h, int64_t c[2]) {
@@ -268,6 +278,7 @@ void *orc_field_create(int F, int J, int M, const float *base, const float *axis
                        int with_band, double tau, double bin_tol) {
     orc_field *fd = (orc_field *)calloc(1, sizeof(orc_field));
     fd->F = F; fd->B = B; fd->inv_h = inv_h;
+    for (int b = 0; b < 64; ++b) fd->dil[b] = b < 32 ? 1u << b : 0u;
     fd->tau = tau; fd->bin_tol = bin_tol; fd->with_band = with_band;
     fd->dirs = (float *)malloc(sizeof(float) * 3 * B);
     memcpy(fd->dirs, dirs, sizeof(float) * 3 * B);
@@ -321,6 +332,12 @@ void *orc_field_create(int F, int J, int M, const float *base, const float *axis
     }
     fd->n_samples_out_of_range = oor;
     return fd;
+}
+
+/* theta-dilated bins: a query of bin b hits when the cell holds any bin of dil[b] */
+void orc_field_set_dilation(void *h, const uint32_t *dil) {
+    orc_field *fd = (orc_field *)h;
+    for (int b = 0; b < fd->B; ++b) fd->dil[b] = dil ? (dil[b] | (1u << b)) : (1u << b);
 }
 
 void orc_field_free(void *h) {
@@ -383,7 +400,7 @@ void orc_query_masks(const void *h, int N, const float *soa, int P, const float 
             int ok = in_key_range(kx) && in_key_range(ky) && in_key_range(kz);
             int b = bin32(mq, B, fd->dirs);
             for (int f = 0; f < F; ++f)
-                if (ok && kv_has(&fd->k32[f], pack_key(f, kx, ky, kz, b)))
+                if (ok && has_any_bin(&fd->k32[f], f, kx, ky, kz, fd->dil[b]))
                     mrow[(size_t)f * W + (x >> 5)] |= 1u << (x & 31);
             if (!fd->with_band || (!amb && !mask64)) continue;
             double p64[3], m64[3];
@@ -401,7 +418,7 @@ void orc_query_masks(const void *h, int N, const float *soa, int P, const float 
             int b64 = bin64(m64, B, fd->dirs);
             int ok64 = in_key_range(ex) && in_key_range(ey) && in_key_range(ez);
             for (int f = 0; f < F; ++f) {
-                if (mask64 && ok64 && kv_has(&fd->k64[f], pack_key(f, ex, ey, ez, b64)))
+                if (mask64 && ok64 && has_any_bin(&fd->k64[f], f, ex, ey, ez, fd->dil[b64]))
                     mask64[((size_t)i * F + f) * W + (x >> 5)] |= 1u << (x & 31);
                 if (!amb) continue;
                 int possible = 0, sure = 1;
@@ -410,9 +427,9 @@ void orc_query_masks(const void *h, int N, const float *soa, int P, const float 
                         for (int d = 0; d < nz; ++d)
                             for (int e = 0; e < nb; ++e) {
                                 int rng_ok = in_key_range(cx[a]) && in_key_range(cy[c]) && in_key_range(cz[d]);
-                                uint64_t key = rng_ok ? pack_key(f, cx[a], cy[c], cz[d], bins[e]) : 0;
-                                if (rng_ok && kv_has(&fd->kpos[f], key)) possible = 1;
-                                if (!rng_ok || !kv_has(&fd->ksure[f], key)) sure = 0;
+                                const uint32_t acc = fd->dil[bins[e]];
+                                if (rng_ok && has_any_bin(&fd->kpos[f], f, cx[a], cy[c], cz[d], acc)) possible = 1;
+                                if (!rng_ok || !has_any_bin(&fd->ksure[f], f, cx[a], cy[c], cz[d], acc)) sure = 0;
                             }
                 amb[((size_t)i * F + f) * N + x] = (uint8_t)(possible != sure);
             }
@@ -426,12 +443,15 @@ void orc_query_masks(const void *h, int N, const float *soa, int P, const float 
 }
 
 /* Literal existential check for tiny inputs: bit x of mask[i][f] is set iff
- * SOME field sample (s, m) of finger f has the same cell and the same bin as the
- * contact-surface vector of point x under pose i.  No index, no sorting. */
+ * SOME field sample (s, m) of finger f has the same cell as the contact-surface
+ * vector of point x under pose i and a bin that query accepts (the same bin, or
+ * one of dil[bin] with theta-dilated bins; dil may be NULL).  No index, no
+ * sorting. */
 void orc_query_masks_brute(int F, int J, int M, const float *base, const float *axis, const float *offset,
                            const float *surf_p, const float *surf_n, const int32_t *surf_link,
                            const float *q, int S, float inv_h, int B, const float *dirs,
-                           int N, const float *soa, int P, const float *poses, uint32_t *masks) {
+                           int N, const float *soa, int P, const float *poses, const uint32_t *dil,
+                           uint32_t *masks) {
     const int W = (N + 31) / 32;
     memset(masks, 0, sizeof(uint32_t) * (size_t)P * F * W);
     if (M > 128 || J > 8) return;
@@ -467,10 +487,11 @@ void orc_query_masks_brute(int F, int J, int M, const float *base, const float *
             const float mq[3] = {-nq[0], -nq[1], -nq[2]};
             int64_t qc[4] = {cell_axis(pq[0], inv_h), cell_axis(pq[1], inv_h), cell_axis(pq[2], inv_h),
                              bin32(mq, B, dirs)};
+            const uint32_t acc = dil ? (dil[qc[3]] | (1u << qc[3])) : (1u << qc[3]);
             for (int f = 0; f < F; ++f) {
                 const int64_t *c = scode + 4 * (size_t)f * S * M;
                 for (int64_t e = 0; e < (int64_t)S * M; ++e, c += 4) {
-                    if (c[0] == qc[0] && c[1] == qc[1] && c[2] == qc[2] && c[3] == qc[3]) {
+                    if (c[0] == qc[0] && c[1] == qc[1] && c[2] == qc[2] && ((acc >> c[3]) & 1u)) {
                         masks[((size_t)i * F + f) * W + (x >> 5)] |= 1u << (x & 31);
                         break;
                     }

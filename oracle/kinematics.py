@@ -174,7 +174,7 @@ def _pose_targets(soa, poses, pose_idx, x):
 
 def ik_dls(hand, qs, inv_h, bins, soa, poses, T: int, k: int, tuples, fingers, accept, beta=0.01, lam=1e-4,
            n_phase1=16, n_rounds=4, n_phase2=4, tol_pos=2e-3, tol_cos=None, tol_deg=20.0, rep=None,
-           perturb: float = 0.0):
+           perturb: float = 0.0, dilation=None):
     """Kinematics optimisation of tuple slots (Sec. 5.5), same outputs as the
     library call: dict(q [n,F,J], used, contacts [6,n*k], rtuples [n,k],
     resid [n,k,2], ok [n], miss [n,k] (contact code without representative)).
@@ -208,8 +208,19 @@ def ik_dls(hand, qs, inv_h, bins, soa, poses, T: int, k: int, tuples, fingers, a
     if rep is None:
         rep = {ff: rep_codes(hand, qs, inv_h, bins, ff) for ff in np.unique(f).tolist()}
     codes = point_codes(soa, poses, pose_idx, x, inv_h, bins)
-    v = np.array([rep[int(ff)].get(pack_code(ff, *cd), -1) for ff, cd in zip(f.tolist(), codes.tolist())],
-                 np.int64)
+    def lookup(ff, cd):
+        # the contact's own bin first; with dilated bins, then the lowest other accepted bin present
+        kx, ky, kz, b = cd
+        order = [b]
+        if dilation is not None:
+            order += [b2 for b2 in range(32) if (int(dilation[b]) >> b2) & 1 and b2 != b]
+        for b2 in order:
+            v = rep[int(ff)].get(pack_code(ff, kx, ky, kz, b2))
+            if v is not None:
+                return v
+        return -1
+
+    v = np.array([lookup(ff, cd) for ff, cd in zip(f.tolist(), codes.tolist())], np.int64)
     miss = v < 0
     vv = np.where(miss, 0, v)
     s_idx, m_idx = vv // M, vv % M

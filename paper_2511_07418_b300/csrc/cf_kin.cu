@@ -376,7 +376,11 @@ __global__ void __launch_bounds__(kIkThreads) k_ik_dls(const IkArgs a, const int
         if (ux < (unsigned)g.dims[0] && uy < (unsigned)g.dims[1] && uz < (unsigned)g.dims[2]) {
             const unsigned long long word =
                 (((unsigned long long)uz * g.dims[1] + uy) * g.dims[0] + ux) * g.rw + f / g.fpw;
-            v = rep_lookup(a.rep, word * 32ull + (unsigned)((f % g.fpw) * g.bits + bin));
+            const unsigned long long base = word * 32ull + (unsigned)((f % g.fpw) * g.bits);
+            v = rep_lookup(a.rep, base + (unsigned)bin);
+            // with dilated bins the hit may come from another accepted bin: the lowest one present
+            for (uint32_t rest = g.dil[bin] & ~(1u << bin); v == 0xffffffffu && rest; rest &= rest - 1)
+                v = rep_lookup(a.rep, base + (unsigned)(__ffs(rest) - 1));
         }
         attempt = v != 0xffffffffu;
         if (!attempt) {

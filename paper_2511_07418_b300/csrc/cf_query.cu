@@ -15,6 +15,8 @@
 // the cell's record (the bin sets of all fingers, one vector load from the
 // L2-resident table) and ballots the hits into the F mask words of that
 // (pose, word).  Counts are accumulated per (pose, finger) in shared memory.
+// With theta-dilated bins (Sec. 4.3 leaf test -x^T n >= theta_hit) the query of
+// bin b hits when the cell holds any bin b' with d_b . d_b' >= cos(theta).
 //
 // Binning: with the candidate table (see cf_bincand.cu) the normal's cube-map
 // cell names at most 4 bins, evaluated in ascending order with the same FP32
@@ -68,6 +70,7 @@ __global__ void __launch_bounds__(kThreads) k_query_domains(const QueryArgs a) {
     __shared__ __align__(16) float s_pose[kPosesPerBlock][12];
     __shared__ unsigned s_cnt[kPosesPerBlock][F];
     __shared__ float4 s_dir[CF_MAX_BINS];
+    __shared__ uint32_t s_dil[CF_MAX_BINS];
     __shared__ uint32_t s_cand[CAND ? kCandCells : 1];
     __shared__ FieldGeom s_geom;
     __shared__ QueryDesc s_desc;
@@ -98,6 +101,7 @@ __global__ void __launch_bounds__(kThreads) k_query_domains(const QueryArgs a) {
     const int np = min(kPosesPerBlock, P - i0);
     for (int e = threadIdx.x; e < np * 12; e += kThreads) s_pose[e / 12][e % 12] = poses[(size_t)i0 * 12 + e];
     for (int e = threadIdx.x; e < kPosesPerBlock * F; e += kThreads) s_cnt[e / F][e % F] = 0u;
+    if (threadIdx.x < CF_MAX_BINS) s_dil[threadIdx.x] = g.dil[threadIdx.x];
     if (CAND) {
         for (int e = threadIdx.x; e < kCandCells; e += kThreads) s_cand[e] = __ldg(g.cand + e);
         if (threadIdx.x < g.B) s_dir[threadIdx.x] = make_float4(g.dirs[threadIdx.x][0], g.dirs[threadIdx.x][1],
@@ -152,9 +156,10 @@ __global__ void __launch_bounds__(kThreads) k_query_domains(const QueryArgs a) {
             if (valid && ux < (unsigned)g.dims[0] && uy < (unsigned)g.dims[1] && uz < (unsigned)g.dims[2])
                 load_record<RW>(table + (((size_t)uz * g.dims[1] + uy) * g.dims[0] + ux) * RW, rec);
             uint32_t mine = 0u;
+            const uint32_t dm = s_dil[bin];  // the bins this query accepts (bit `bin` alone without dilation)
 #pragma unroll
             for (int f = 0; f < F; ++f) {
-                const bool hit = (rec[f / FPW] >> ((f % FPW) * BITS + bin)) & 1u;
+                const bool hit = ((rec[f / FPW] >> ((f % FPW) * BITS)) & dm) != 0u;
                 const uint32_t bal = __ballot_sync(0xffffffffu, hit);
                 if (lane == f) mine = bal;
             }

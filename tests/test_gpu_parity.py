@@ -111,6 +111,18 @@ def check_scores(g_margin, g_accept, o_margin, eps):
     assert dec.sum() <= 1e-4 * dec.size
 
 
+def check_sampling(g_tuples, g_fingers, g_masks, o_masks, o_counts, N, T, k, seed):
+    """The oracle samples from its OWN masks; the GPU's tuples must equal them on
+    every pose whose mask rows agree (all but ambiguous entries).  Returns the
+    oracle's tuples and the agreeing poses."""
+    ot, of = oracle.sample_tuples(o_masks, o_counts, N, T, k, seed)
+    same = np.all(g_masks.reshape(g_masks.shape[0], -1) == o_masks.reshape(o_masks.shape[0], -1), axis=1)
+    assert same.mean() >= 0.99, f"{int((~same).sum())} poses with differing (ambiguous) mask rows"
+    assert np.array_equal(g_tuples[same], ot[same])
+    assert np.array_equal(g_fingers[same], of[same])
+    return ot, of, same
+
+
 def _full_check(cf, w, band=True):
     r = _gpu_path(cf, w)
     ofd = oracle.Field(w.hand, w.q, w.inv_h, w.bins, band=band)
@@ -119,12 +131,11 @@ def _full_check(cf, w, band=True):
     om, oc, amb = ofd.query(soa, w.poses, amb=True)
     gm, gc = _u32(r["masks"]), _u32(r["counts"])
     check_masks(gm, gc, om, oc, amb, w.obj.N)
-    # sampling, given the GPU's masks (tests the sampler alone)
-    ot, of = oracle.sample_tuples(gm, gc, w.obj.N, w.T, w.k, w.seed)
-    assert np.array_equal(r["tuples"].cpu().numpy(), ot)
-    assert np.array_equal(r["fingers"].cpu().numpy(), of)
-    omar, oacc, _ = oracle.score_tuples(soa, ot, w.mu, w.K, w.obj.centroid, w.obj.rho, w.eps)
-    check_scores(r["margin"].cpu().numpy(), r["accept"].cpu().numpy(), omar, w.eps)
+    # sampling and scoring: the oracle works from its own masks and tuples
+    ot, of, same = check_sampling(r["tuples"].cpu().numpy(), r["fingers"].cpu().numpy(), gm, om, oc, w.obj.N, w.T,
+                                  w.k, w.seed)
+    omar, oacc, _ = oracle.score_tuples(soa, ot[same], w.mu, w.K, w.obj.centroid, w.obj.rho, w.eps)
+    check_scores(r["margin"].cpu().numpy()[same], r["accept"].cpu().numpy()[same], omar, w.eps)
     return r, ofd
 
 
@@ -164,13 +175,16 @@ def test_full_size_launch_sampled_outputs(cf, name):
     om, oc, amb = ofd.query(soa, w.poses[idx], amb=True)
     gm_all, gc_all = _u32(r["masks"]), _u32(r["counts"])
     check_masks(gm_all[idx], gc_all[idx], om, oc, amb, w.obj.N)
-    ot, of = oracle.sample_tuples(gm_all[:48], gc_all[:48], w.obj.N, w.T, w.k, w.seed)
-    assert np.array_equal(r["tuples"][:48].cpu().numpy(), ot)
-    assert np.array_equal(r["fingers"][:48].cpu().numpy(), of)
-    flat = r["tuples"].cpu().numpy().reshape(-1, w.k)
-    pick = rng.choice(flat.shape[0], 3000, replace=False)
+    # the first 48 poses: the oracle's own masks -> its tuples -> its scores of a random sample of them
+    om48, oc48 = ofd.query(soa, w.poses[:48])
+    ot, of, same = check_sampling(r["tuples"][:48].cpu().numpy(), r["fingers"][:48].cpu().numpy(), gm_all[:48], om48,
+                                  oc48, w.obj.N, w.T, w.k, w.seed)
+    flat = ot[same].reshape(-1, w.k)
+    pick = rng.choice(flat.shape[0], min(3000, flat.shape[0]), replace=False)
     omar, _, _ = oracle.score_tuples(soa, flat[pick], w.mu, w.K, w.obj.centroid, w.obj.rho, w.eps)
-    check_scores(r["margin"].cpu().numpy().ravel()[pick], r["accept"].cpu().numpy().ravel()[pick], omar, w.eps)
+    g_mar = r["margin"][:48].cpu().numpy()[same].ravel()[pick]
+    g_acc = r["accept"][:48].cpu().numpy()[same].ravel()[pick]
+    check_scores(g_mar, g_acc, omar, w.eps)
     assert cf.device_status() == 0
 
 
@@ -191,11 +205,10 @@ def test_ragged_sizes_and_degenerate_cases(cf):
         om, oc, amb = ofd.query(soa_h, far, amb=True)
         check_masks(_u32(masks), _u32(counts), om, oc, amb, N)
         assert int(counts[2].sum()) == 0
-        ot, of = oracle.sample_tuples(_u32(masks), _u32(counts), N, base.T, base.k, 5)
-        assert np.array_equal(tup.cpu().numpy(), ot)
+        ot, of, same = check_sampling(tup.cpu().numpy(), fing.cpu().numpy(), _u32(masks), om, oc, N, base.T, base.k, 5)
         assert np.all(ot[2] == -1) and np.all(fing[2].cpu().numpy() == 255)
-        om_, _, _ = oracle.score_tuples(soa_h, ot, base.mu, base.K, base.obj.centroid, base.obj.rho, base.eps)
-        check_scores(mar.cpu().numpy(), acc.cpu().numpy(), om_, base.eps)
+        om_, _, _ = oracle.score_tuples(soa_h, ot[same], base.mu, base.K, base.obj.centroid, base.obj.rho, base.eps)
+        check_scores(mar.cpu().numpy()[same], acc.cpu().numpy()[same], om_, base.eps)
         assert np.all(np.isinf(mar[2].cpu().numpy())) and not acc[2].any()
     # a field built from zero samples holds nothing
     empty = cf.build(base.hand, base.inv_h, base.bins, torch.zeros((base.hand.F, base.hand.J, 0), device="cuda"))
