@@ -39,8 +39,8 @@ def _bits(m, N):
     return np.unpackbits(np.ascontiguousarray(m).view(np.uint8), bitorder="little").reshape(P, F, W * 32)[:, :, :N]
 
 
-@pytest.mark.parametrize("name,P,S,deg", [("tiny_sphere", 32, 2048, 50), ("hand16_superquadric", 6, 8192, 35),
-                                          ("hand20_tool", 2, 8192, 25)])
+@pytest.mark.parametrize("name,P,S,deg", [("tiny_sphere", 32, 2048, 70), ("hand16_superquadric", 6, 8192, 50),
+                                          ("hand20_tool", 2, 8192, 36)])
 def test_dilated_masks(cf, name, P, S, deg):
     w = synth.workload(name, P=P, S=S)
     c = _cos_between_levels(w.bins, deg)
@@ -74,7 +74,7 @@ def test_dilated_reverse_lookup_ik(cf):
     """With dilated bins a domain point may hit through a neighbouring bin; the
     reverse lookup then takes the lowest accepted bin present, on both sides."""
     w = synth.workload("hand16_superquadric", P=3, S=8192)
-    c = _cos_between_levels(w.bins, 35)
+    c = _cos_between_levels(w.bins, 50)
     field = cf.build(w.hand, w.inv_h, w.bins, torch.from_numpy(w.q).cuda(), want_rep=True, dilate_cos=c)
     ofd = oracle.Field(w.hand, w.q, w.inv_h, w.bins, dilate_cos=c)
     soa = w.obj.soa()

@@ -63,13 +63,14 @@ def test_no_and_full_dilation(small):
 def test_dilation_monotone_and_brute_force(small):
     w, soa = small
     prev = None
-    for deg in (20, 45, 75):
+    for deg in (20, 70, 110):
         c = _cos_between_levels(w.bins, deg)
         m, _ = oracle.Field(w.hand, w.q, w.inv_h, w.bins, dilate_cos=c).query(soa, w.poses)
         if prev is not None:
             assert np.all((prev & ~m) == 0)  # a wider angle only adds hits
+            assert (m & ~prev).any()         # and past the bin spacing it does add some
         prev = m
-    c = _cos_between_levels(w.bins, 60)
+    c = _cos_between_levels(w.bins, 70)
     q = np.ascontiguousarray(w.q[:, :, :64])
     idx, _ = oracle.Field(w.hand, q, w.inv_h, w.bins, dilate_cos=c).query(soa, w.poses[:2])
     brute = oracle.query_masks_brute(w.hand, q, w.inv_h, w.bins, soa, w.poses[:2], dilate_cos=c)
