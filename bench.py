@@ -661,8 +661,17 @@ def run_batched(cf, torch, dev, n_objects, ws, fields):
             best = ms if best is None else min(best, ms)
         return best
 
+    default_tuning = cf.get_tuning()
     t_plain = timed(plain)
     # the plain calls above allocate margin/accept per call; the batch writes into the items' own buffers
+    batch = cf.Batch(items)
+    t_batch_default = timed(batch.run)
+    batch.close()
+    # the autotuner picks the launch shapes on these objects; the batch is re-created under them
+    t_tune = time.perf_counter()
+    tuning, tune_ms = cf.autotune(items, reps=2)
+    t_tune = time.perf_counter() - t_tune
+    t_plain_tuned = timed(plain)
     batch = cf.Batch(items)
     t_batch = timed(batch.run)
     accepted = sum(int(it["accept"].sum()) for it in items)
@@ -671,6 +680,9 @@ def run_batched(cf, torch, dev, n_objects, ws, fields):
     return {"objects": n_objects, "pose_point_pairs": pairs, "tuples": tuples, "accepted": accepted,
             "plain_ms": t_plain, "batched_ms": t_batch, "plain_grasps_per_s": accepted / (t_plain / 1e3),
             "batched_grasps_per_s": accepted / (t_batch / 1e3), "batched_launches": n_launch,
+            "default_tuning": default_tuning, "batched_ms_default_tuning": t_batch_default,
+            "autotuned": tuning, "plain_ms_autotuned": t_plain_tuned, "autotune_s": t_tune,
+            "autotune_query_score_ms": list(tune_ms),
             "plain_launches": 3 * n_objects, "generate_s": t_gen,
             "workload": "64 objects (superquadrics / tool composites), points log-uniform 2,048-131,072, poses "
                         "log-uniform 4,096-32,768, hand per object from the 3/4/5-finger hands (fields cached)"}

@@ -397,6 +397,29 @@ int cf_batch_launches(const cf_batch *batch, int32_t *n_launches, int32_t *n_gro
 
 int cf_batch_destroy(cf_batch *batch);
 
+/* ---- launch shapes and the autotuner ------------------------------------- */
+
+/* Launch shapes of the query and scoring kernels on the current device.  The
+ * results of every call are the same under any shape; only the time changes.
+ * Batches and engines take the shapes current at their creation. */
+typedef struct cf_tuning {
+    int32_t query_poses_per_block;  /* poses per domain-query block: 4, 8 or 16 (default 8) */
+    int32_t score_tuples_per_grab;  /* tuples a scoring warp takes per work-counter grab: 1, 2, 4 or 8 (default 4) */
+    int32_t score_blocks_per_sm;    /* scoring blocks per SM: 1, 2, 3, or 0 = as many as fit (default 0) */
+} cf_tuning;
+
+int cf_get_tuning(cf_tuning *out);
+int cf_set_tuning(const cf_tuning *tuning);
+
+/* Autotuner: runs the items' query launches under every poses-per-block
+ * candidate, then their sampling + scoring under every (tuples per grab,
+ * blocks per SM) candidate, `reps` times each (median of the summed CUDA-event
+ * times), keeps the fastest and makes it the device's tuning; *out (if not
+ * NULL) receives it and best_ms[0..1] the query and scoring times it measured.
+ * The items' output buffers are written by the trial runs.  Synchronous.
+ * Errors: CF_EINVAL, CF_ENOMEM, CF_ECUDA. */
+int cf_autotune(const cf_batch_item *items, int32_t n_items, int32_t reps, cf_tuning *out, double *best_ms);
+
 /* ---- served form: continuous batching over arriving requests -------------- */
 
 typedef struct cf_engine cf_engine;

@@ -68,6 +68,11 @@ class OptParams(Structure):
                 ("min_gain", c_float)]
 
 
+class Tuning(Structure):
+    _fields_ = [("query_poses_per_block", c_int32), ("score_tuples_per_grab", c_int32),
+                ("score_blocks_per_sm", c_int32)]
+
+
 class RealizeParams(Structure):
     _fields_ = [("pen_margin", c_float), ("axis_step", c_float), ("seed", c_uint64)]
 
@@ -170,6 +175,9 @@ _cf_sdf_destroy = _sig("cf_sdf_destroy", [c_void_p])
 _cf_realize = _sig("cf_realize", [c_void_p, c_void_p, c_void_p, c_int32, c_int32, POINTER(RealizeParams), c_void_p,
                                   c_void_p, c_void_p, c_void_p, c_void_p, c_void_p])
 _cf_fp32_peak = _sig("cf_fp32_peak", [POINTER(c_double)])
+_cf_get_tuning = _sig("cf_get_tuning", [POINTER(Tuning)])
+_cf_set_tuning = _sig("cf_set_tuning", [POINTER(Tuning)])
+_cf_autotune = _sig("cf_autotune", [POINTER(BatchItem), c_int32, c_int32, POINTER(Tuning), POINTER(c_double)])
 _cf_gswo = _sig("cf_score_gswo", [POINTER(Points), c_int32, POINTER(ScoreParams), c_int32, c_float, c_void_p, c_void_p,
                                   c_void_p, c_void_p])
 _cf_optimize = _sig("cf_optimize_tuples", [POINTER(Points), c_int32, c_void_p, c_int32, POINTER(ScoreParams),
@@ -184,7 +192,8 @@ EXPORTED = ["cf_build", "cf_field_get_info", "cf_field_copy_table", "cf_field_de
             "cf_sample_tuples", "cf_batch_create", "cf_batch_run", "cf_batch_launches", "cf_batch_destroy",
             "cf_engine_create", "cf_engine_submit", "cf_engine_poll", "cf_engine_result_free", "cf_engine_get_stats",
             "cf_engine_drain", "cf_engine_destroy", "cf_field_rep_slots", "cf_field_copy_rep", "cf_ik_dls",
-            "cf_sdf_build", "cf_sdf_copy", "cf_sdf_destroy", "cf_realize", "cf_fp32_peak", "cf_optimize_tuples", "cf_score_gswo"]
+            "cf_sdf_build", "cf_sdf_copy", "cf_sdf_destroy", "cf_realize", "cf_fp32_peak", "cf_optimize_tuples", "cf_score_gswo",
+            "cf_get_tuning", "cf_set_tuning", "cf_autotune"]
 
 
 def _check(rc: int):
@@ -397,6 +406,19 @@ def score_tuples_noalloc(soa, n_fingers: int, masks, counts, prm: ScoreParams, t
     return tuples, fingers, margin, accept
 
 
+def _batch_items(items):
+    import torch
+    arr = (BatchItem * len(items))()
+    for j, it in enumerate(items):
+        obj = points_struct(it["soa"])
+        P = int(it["poses"].shape[0])
+        arr[j] = BatchItem(it["field"].handle, obj, _dev(it["poses"], torch.float32, "poses"), P, it["prm"],
+                           _dev(it["masks"], torch.int32, "masks"), _dev(it["counts"], torch.int32, "counts"),
+                           _dev(it["tuples"], torch.int32, "tuples"), _dev(it["fingers"], torch.uint8, "fingers"),
+                           _dev(it["margin"], torch.float32, "margin"), _dev(it["accept"], torch.uint8, "accept"))
+    return arr
+
+
 class Batch:
     """cf_batch: many object requests run as one launch per kernel variant,
     replayed as a CUDA graph.  ``items`` are dicts with keys field, soa, poses,
@@ -404,17 +426,8 @@ class Batch:
     query_domains / score_tuples)."""
 
     def __init__(self, items):
-        import torch
-        arr = (BatchItem * len(items))()
-        self._keep = []
-        for j, it in enumerate(items):
-            obj = points_struct(it["soa"])
-            P = int(it["poses"].shape[0])
-            arr[j] = BatchItem(it["field"].handle, obj, _dev(it["poses"], torch.float32, "poses"), P, it["prm"],
-                               _dev(it["masks"], torch.int32, "masks"), _dev(it["counts"], torch.int32, "counts"),
-                               _dev(it["tuples"], torch.int32, "tuples"), _dev(it["fingers"], torch.uint8, "fingers"),
-                               _dev(it["margin"], torch.float32, "margin"), _dev(it["accept"], torch.uint8, "accept"))
-            self._keep.append(it)
+        arr = _batch_items(items)
+        self._keep = list(items)
         h = c_void_p()
         _check(_cf_batch_create(arr, len(items), byref(h)))
         self._h = h
@@ -679,6 +692,26 @@ def realize(field: Field, sdf: Sdf, poses, T: int, q, used, gate_a, gate_b, prm:
                        _dev(q, torch.float32, "q"), _dev(used, torch.uint8, "used"),
                        _dev(flags, torch.uint8, "flags"), _stream(stream)))
     return flags
+
+
+def get_tuning() -> dict:
+    t = Tuning()
+    _check(_cf_get_tuning(byref(t)))
+    return {f: getattr(t, f) for f, _ in Tuning._fields_}
+
+
+def set_tuning(query_poses_per_block=8, score_tuples_per_grab=4, score_blocks_per_sm=0):
+    _check(_cf_set_tuning(byref(Tuning(int(query_poses_per_block), int(score_tuples_per_grab),
+                                       int(score_blocks_per_sm)))))
+
+
+def autotune(items, reps: int = 3):
+    """cf_autotune over batch items (dicts from batch_item): returns (tuning dict, (query ms, score ms))."""
+    arr = _batch_items(items)
+    t = Tuning()
+    ms = (c_double * 2)()
+    _check(_cf_autotune(arr, len(items), int(reps), byref(t), ms))
+    return {f: getattr(t, f) for f, _ in Tuning._fields_}, (ms[0], ms[1])
 
 
 def fp32_peak() -> float:

@@ -52,6 +52,11 @@ struct DevState {
 std::mutex g_state_mu;
 DevState g_state[64];
 
+std::mutex g_tune_mu;
+Tuning g_tune[64];
+bool g_tune_set[64] = {};
+constexpr Tuning kDefaultTuning{8, 4, 0};
+
 int device_state(DevState *out) {
     int dev = 0;
     CF_TRY(cudaGetDevice(&dev), "cudaGetDevice");
@@ -212,6 +217,15 @@ int geom_from_params(cf_field *fd, const cf_field_params *prm) {
 }
 
 }  // namespace
+
+namespace cf {
+Tuning current_tuning() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return kDefaultTuning;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return g_tune_set[dev] ? g_tune[dev] : kDefaultTuning;
+}
+}  // namespace cf
 
 extern "C" int cf_build(const cf_hand_desc *hand, const cf_field_params *prm, const float *d_q, int32_t n_samples,
                         cf_stream stream, cf_field **out) {
@@ -566,7 +580,8 @@ extern "C" int cf_query_domains(const cf_field *fd, const cf_points *obj, const 
                                    (cudaStream_t)stream), "memset masks");
         return CF_OK;
     }
-    CF_TRY(launch_query(fd->geom, fd->d_table, *obj, d_poses, n_poses, d_masks, d_counts, (cudaStream_t)stream),
+    CF_TRY(launch_query(fd->geom, fd->d_table, *obj, d_poses, n_poses, d_masks, d_counts, current_tuning().query_ppb,
+                        (cudaStream_t)stream),
            "launch k_query_domains");
     return CF_OK;
 }
@@ -626,6 +641,9 @@ int fill_score_args(const cf_points *obj, int32_t F, const uint32_t *d_masks, co
     a->tuples = d_tuples; a->fingers = d_fingers; a->margin = d_margin; a->accept = d_accept;
     a->status = ds.status;
     a->counters = ds.counters;
+    const Tuning tu = current_tuning();
+    a->batch = tu.score_batch;
+    a->bpsm = tu.score_bpsm;
     return CF_OK;
 }
 
@@ -795,6 +813,7 @@ struct cf_batch {
     std::vector<FieldGeom> geoms;
     FieldGeom *d_geoms = nullptr;
     int launches = 0;
+    int ppb = 8;                        // query poses per block (the tuning at creation)
 };
 
 extern "C" int cf_batch_create(const cf_batch_item *items, int32_t n_items, cf_batch **out) {
@@ -803,6 +822,7 @@ extern "C" int cf_batch_create(const cf_batch_item *items, int32_t n_items, cf_b
     std::vector<int> geom_of(n_items);
     cf_batch *b = new cf_batch();
     CF_TRY(cudaGetDevice(&b->dev), "cudaGetDevice");
+    b->ppb = current_tuning().query_ppb;
     std::vector<const cf_field *> fields;
     for (int i = 0; i < n_items; ++i) {
         const cf_batch_item &it = items[i];
@@ -864,7 +884,7 @@ extern "C" int cf_batch_create(const cf_batch_item *items, int32_t n_items, cf_b
             d.table = items[i].field->d_table;
             d.geom = geom_of[i];
             d.block0 = blocks;
-            blocks += query_blocks(d.P);
+            blocks += query_blocks(d.P, b->ppb);
             qdesc_all.push_back(d);
             qg.g0 = b->geoms[geom_of[i]];
         }
@@ -941,7 +961,7 @@ extern "C" int cf_batch_create(const cf_batch_item *items, int32_t n_items, cf_b
 namespace {
 int batch_enqueue(cf_batch *b, cudaStream_t st) {
     for (const auto &qg : b->qgroups)
-        CF_TRY(launch_query_batch(qg.g0, qg.d_descs, b->d_geoms, qg.n, qg.blocks, st), "batch query");
+        CF_TRY(launch_query_batch(qg.g0, qg.d_descs, b->d_geoms, qg.n, qg.blocks, b->ppb, st), "batch query");
     CF_TRY(launch_sample_batch(b->d_sdescs, b->d_pose0, b->n_items, b->total_poses, b->sample_smem, st),
            "batch sample");
     for (const auto &sg : b->sgroups) {
@@ -996,6 +1016,110 @@ extern "C" int cf_batch_destroy(cf_batch *b) {
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev_out) cudaEventDestroy(b->ev_out);
     delete b;
+    return CF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// launch shapes and the autotuner
+// ---------------------------------------------------------------------------
+namespace {
+bool tuning_valid(const cf_tuning *t) {
+    const int p = t->query_poses_per_block, b = t->score_tuples_per_grab, s = t->score_blocks_per_sm;
+    return (p == 4 || p == 8 || p == 16) && (b == 1 || b == 2 || b == 4 || b == 8) && s >= 0 && s <= 3;
+}
+}  // namespace
+
+extern "C" int cf_get_tuning(cf_tuning *out) {
+    if (!out) return fail(CF_EINVAL, "NULL argument");
+    const Tuning t = current_tuning();
+    out->query_poses_per_block = t.query_ppb;
+    out->score_tuples_per_grab = t.score_batch;
+    out->score_blocks_per_sm = t.score_bpsm;
+    return CF_OK;
+}
+
+extern "C" int cf_set_tuning(const cf_tuning *t) {
+    if (!t) return fail(CF_EINVAL, "NULL argument");
+    if (!tuning_valid(t)) return fail(CF_EINVAL, "tuning out of range");
+    int dev = 0;
+    CF_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(CF_EINVAL, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[dev] = Tuning{t->query_poses_per_block, t->score_tuples_per_grab, t->score_blocks_per_sm};
+    g_tune_set[dev] = true;
+    return CF_OK;
+}
+
+extern "C" int cf_autotune(const cf_batch_item *items, int32_t n_items, int32_t reps, cf_tuning *out,
+                           double *best_ms) {
+    if (!items || n_items < 1) return fail(CF_EINVAL, "no items");
+    if (reps < 1 || reps > 64) return fail(CF_EINVAL, "reps=%d not in [1,64]", reps);
+    for (int i = 0; i < n_items; ++i)
+        if (!items[i].field || items[i].prm.tuples_given) return fail(CF_EINVAL, "item %d: no field or tuples given", i);
+    cf_tuning saved;
+    int rc = cf_get_tuning(&saved);
+    if (rc) return rc;
+    cudaStream_t st = nullptr;
+    CF_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "stream");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    // time one full pass of `phase` (0: queries, 1: sampling + scoring) under tuning t; median of reps
+    auto run = [&](const cf_tuning &t, int phase, double *ms) -> int {
+        int r = cf_set_tuning(&t);
+        if (r) return r;
+        std::vector<double> v;
+        for (int rep = 0; rep < reps + 1; ++rep) {  // the first pass warms up
+            CF_TRY(cudaEventRecord(e0, st), "event");
+            for (int i = 0; i < n_items && !r; ++i) {
+                const cf_batch_item &it = items[i];
+                if (phase == 0)
+                    r = cf_query_domains(it.field, &it.obj, it.d_poses, it.n_poses, it.d_masks, it.d_counts, st);
+                else
+                    r = cf_score_tuples(&it.obj, it.field->F, it.d_masks, it.d_counts, it.n_poses, &it.prm, it.d_tuples,
+                                        it.d_fingers, it.d_margin, it.d_accept, st);
+            }
+            if (r) return r;
+            CF_TRY(cudaEventRecord(e1, st), "event");
+            CF_TRY(cudaEventSynchronize(e1), "autotune run");
+            float f = 0.f;
+            cudaEventElapsedTime(&f, e0, e1);
+            if (rep > 0) v.push_back(f);
+        }
+        std::sort(v.begin(), v.end());
+        *ms = v[v.size() / 2];
+        return CF_OK;
+    };
+    cf_tuning best = saved;
+    double bq = 1e300, bs = 1e300;
+    for (int ppb : {4, 8, 16}) {
+        cf_tuning t = saved;
+        t.query_poses_per_block = ppb;
+        double ms = 0;
+        if ((rc = run(t, 0, &ms))) break;
+        if (ms < bq) { bq = ms; best.query_poses_per_block = ppb; }
+    }
+    for (int batch : {1, 2, 4, 8}) {
+        if (rc) break;
+        for (int bpsm : {0, 1, 2}) {
+            cf_tuning t = best;
+            t.score_tuples_per_grab = batch;
+            t.score_blocks_per_sm = bpsm;
+            double ms = 0;
+            if ((rc = run(t, 1, &ms))) break;
+            if (ms < bs) { bs = ms; best.score_tuples_per_grab = batch; best.score_blocks_per_sm = bpsm; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(st);
+    if (rc) {
+        cf_set_tuning(&saved);
+        return rc;
+    }
+    if ((rc = cf_set_tuning(&best))) return rc;
+    if (out) *out = best;
+    if (best_ms) { best_ms[0] = bq; best_ms[1] = bs; }
     return CF_OK;
 }
 

@@ -88,6 +88,7 @@ struct cf_engine {
     void *d_round = nullptr;
     size_t round_bytes = 0;
     std::string worker_error;
+    Tuning tune{8, 4, 0};  // launch shapes (the tuning at creation)
 
     double now() const {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -167,6 +168,8 @@ int run_round(cf_engine *e, std::vector<EngReq *> &act) {
                                  r->d_fingers, r->d_margin, r->d_accept, &sargs[i]);
         if (rc) return rc;
         sargs[i].pose_base = (uint32_t)r->pose_next;
+        sargs[i].batch = e->tune.score_batch;
+        sargs[i].bpsm = e->tune.score_bpsm;
     }
     auto geom_of = [&](int i) {
         for (size_t f = 0; f < e->fields.size(); ++f)
@@ -201,7 +204,7 @@ int run_round(cf_engine *e, std::vector<EngReq *> &act) {
             d.table = act[i]->fd->d_table;
             d.geom = geom_of(i);
             d.block0 = blocks;
-            blocks += query_blocks(d.P);
+            blocks += query_blocks(d.P, e->tune.query_ppb);
             g0 = d.geom;
             qd.push_back(d);
         }
@@ -261,7 +264,7 @@ int run_round(cf_engine *e, std::vector<EngReq *> &act) {
     int launches = 0;
     for (size_t g = 0; g < qkeys.size(); ++g) {
         CF_TRY(launch_query_batch(e->geoms[q_geom[g]], (const QueryDesc *)(base + o_q) + q_off[g], d_geoms, q_n[g],
-                                  q_blocks[g], e->st), "round query");
+                                  q_blocks[g], e->tune.query_ppb, e->st), "round query");
         ++launches;
     }
     CF_TRY(launch_sample_batch((const ScoreArgs *)(base + o_a), (const long long *)(base + o_p), n, pose0[n], smem,
@@ -389,6 +392,7 @@ extern "C" int cf_engine_create(const cf_engine_params *prm, cf_engine **out) {
     }
     e->prm.fields = nullptr;
     CF_TRY(cudaGetDevice(&e->dev), "cudaGetDevice");
+    e->tune = current_tuning();
     cudaError_t err = cudaStreamCreateWithFlags(&e->st, cudaStreamNonBlocking);
     if (err != cudaSuccess) { delete e; return cuda_fail(err, "stream"); }
     e->t0 = std::chrono::steady_clock::now();

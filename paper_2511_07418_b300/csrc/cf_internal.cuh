@@ -218,7 +218,7 @@ cudaError_t launch_popcount(const uint32_t *table, long long words, unsigned lon
 cudaError_t launch_fk_rep(const HandDev &h, const float *links, int S, const FieldGeom &g, RepTable t,
                           unsigned int *status, cudaStream_t st);
 cudaError_t launch_query(const FieldGeom &g, const uint32_t *table, const cf_points &obj, const float *poses,
-                         int P, uint32_t *masks, uint32_t *counts, cudaStream_t st);
+                         int P, uint32_t *masks, uint32_t *counts, int ppb, cudaStream_t st);
 
 // One object's domain query (the plain call uses one by value; a batch keeps an
 // array of them in device memory, block0 = first grid block of the object).
@@ -234,8 +234,17 @@ struct QueryDesc {
 
 // All objects of a batch group share F, bits and the binning method.
 cudaError_t launch_query_batch(const FieldGeom &g0, const QueryDesc *d_descs, const FieldGeom *d_geoms, int n_desc,
-                               int total_blocks, cudaStream_t st);
-int query_blocks(int P);  // grid blocks one object of P poses needs
+                               int total_blocks, int ppb, cudaStream_t st);
+int query_blocks(int P, int ppb);  // grid blocks one object of P poses needs at ppb poses per block
+constexpr int kMaxPosesPerBlock = 16;
+
+// Launch shapes picked by the autotuner (per device); results do not depend on them.
+struct Tuning {
+    int query_ppb;    // poses per query block: 4, 8 or 16
+    int score_batch;  // tuples a scoring warp takes per work-counter grab: 1, 2, 4 or 8
+    int score_bpsm;   // scoring blocks per SM (0: as many as fit)
+};
+Tuning current_tuning();
 
 struct ScoreArgs {
     const float *px, *py, *pz, *nx, *ny, *nz;
@@ -254,6 +263,8 @@ struct ScoreArgs {
     unsigned int *work;  // scratch: tuple work counter, zero at launch
     unsigned int *status;          // device status word (CF_DEV_* bits)
     unsigned long long *counters;  // [0] pivots, [1] LPs, [2] tuples
+    int batch;                     // tuples per work-counter grab (launch-level)
+    int bpsm;                      // scoring blocks per SM, 0 = as many as fit (launch-level)
 };
 // k_sample_tuples (unless tuples_given) then k_score_tuples
 cudaError_t launch_score(const ScoreArgs &a, cudaStream_t st);

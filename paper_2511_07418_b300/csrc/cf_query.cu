@@ -9,7 +9,8 @@
 // (R p_x + t, -(R n_x)); it hits finger f iff the finger's table has a word at
 // cell(R p_x + t) whose bit bin(-(R n_x)) is set.
 //
-// Launch: one block per 8 consecutive poses; each warp walks the mask words
+// Launch: one block per ppb consecutive poses (4, 8 or 16, picked by the
+// autotuner); each warp walks the mask words
 // of the object (32 points per word, one point per lane, held in registers),
 // and for each pose of the block transforms its point, bins the normal, loads
 // the cell's record (the bin sets of all fingers, one vector load from the
@@ -32,7 +33,6 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kPosesPerBlock = 8;
 
 template <int RW>
 __device__ __forceinline__ void load_record(const uint32_t *__restrict__ r, uint32_t (&rec)[RW]) {
@@ -60,6 +60,7 @@ struct QueryArgs {
     const QueryDesc *descs;    // batch: requests (device)
     const FieldGeom *geoms;    // batch: geometries (device)
     int n_desc;
+    int ppb;                   // poses per block (<= kMaxPosesPerBlock)
 };
 
 // MULTI: the block's object is found from the descriptors (blocks of object d
@@ -67,8 +68,8 @@ struct QueryArgs {
 // are copied to shared memory.
 template <int F, int BITS, bool CAND, bool MULTI>
 __global__ void __launch_bounds__(kThreads) k_query_domains(const QueryArgs a) {
-    __shared__ __align__(16) float s_pose[kPosesPerBlock][12];
-    __shared__ unsigned s_cnt[kPosesPerBlock][F];
+    __shared__ __align__(16) float s_pose[kMaxPosesPerBlock][12];
+    __shared__ unsigned s_cnt[kMaxPosesPerBlock][F];
     __shared__ float4 s_dir[CF_MAX_BINS];
     __shared__ uint32_t s_dil[CF_MAX_BINS];
     __shared__ uint32_t s_cand[CAND ? kCandCells : 1];
@@ -97,10 +98,11 @@ __global__ void __launch_bounds__(kThreads) k_query_domains(const QueryArgs a) {
     uint32_t *__restrict__ masks = D.masks;
     uint32_t *__restrict__ counts = D.counts;
     const uint32_t *__restrict__ table = D.table;
-    const int i0 = ((int)blockIdx.x - (MULTI ? D.block0 : 0)) * kPosesPerBlock;
-    const int np = min(kPosesPerBlock, P - i0);
+    const int ppb = a.ppb;
+    const int i0 = ((int)blockIdx.x - (MULTI ? D.block0 : 0)) * ppb;
+    const int np = min(ppb, P - i0);
     for (int e = threadIdx.x; e < np * 12; e += kThreads) s_pose[e / 12][e % 12] = poses[(size_t)i0 * 12 + e];
-    for (int e = threadIdx.x; e < kPosesPerBlock * F; e += kThreads) s_cnt[e / F][e % F] = 0u;
+    for (int e = threadIdx.x; e < kMaxPosesPerBlock * F; e += kThreads) s_cnt[e / F][e % F] = 0u;
     if (threadIdx.x < CF_MAX_BINS) s_dil[threadIdx.x] = g.dil[threadIdx.x];
     if (CAND) {
         for (int e = threadIdx.x; e < kCandCells; e += kThreads) s_cand[e] = __ldg(g.cand + e);
@@ -202,13 +204,15 @@ cudaError_t launch_any(const QueryArgs &a, const FieldGeom &g, int grid, cudaStr
 
 }  // namespace
 
-int query_blocks(int P) { return (P + kPosesPerBlock - 1) / kPosesPerBlock; }
+int query_blocks(int P, int ppb) { return (P + ppb - 1) / ppb; }
 
 cudaError_t launch_query(const FieldGeom &g, const uint32_t *table, const cf_points &obj, const float *poses, int P,
-                         uint32_t *masks, uint32_t *counts, cudaStream_t st) {
+                         uint32_t *masks, uint32_t *counts, int ppb, cudaStream_t st) {
     if (P <= 0) return cudaSuccess;
+    if (ppb < 1 || ppb > kMaxPosesPerBlock) return cudaErrorInvalidValue;
     QueryArgs a;
     memset(&a, 0, sizeof a);
+    a.ppb = ppb;
     a.g = g;
     a.one.obj = obj;
     a.one.poses = poses;
@@ -217,14 +221,16 @@ cudaError_t launch_query(const FieldGeom &g, const uint32_t *table, const cf_poi
     a.one.masks = masks;
     a.one.counts = counts;
     a.one.table = table;
-    return launch_any<false>(a, g, query_blocks(P), st);
+    return launch_any<false>(a, g, query_blocks(P, ppb), st);
 }
 
 cudaError_t launch_query_batch(const FieldGeom &g0, const QueryDesc *d_descs, const FieldGeom *d_geoms, int n_desc,
-                               int total_blocks, cudaStream_t st) {
+                               int total_blocks, int ppb, cudaStream_t st) {
     if (total_blocks <= 0) return cudaSuccess;
+    if (ppb < 1 || ppb > kMaxPosesPerBlock) return cudaErrorInvalidValue;
     QueryArgs a;
     memset(&a, 0, sizeof a);
+    a.ppb = ppb;
     a.descs = d_descs;
     a.geoms = d_geoms;
     a.n_desc = n_desc;

@@ -178,7 +178,6 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_tuples(const ScoreArg
 // ---------------------------------------------------------------------------
 constexpr int kScoreThreads = 256;
 constexpr int kScoreWarps = kScoreThreads / 32;
-constexpr int kTupleBatch = 4;        // tuples per work-counter grab
 constexpr int kMaxPivots = 64;        // per LP, after the two start pivots
 constexpr int kDegenerateToBland = 16;
 constexpr float kDTol = 1e-6f;        // reduced-cost tolerance
@@ -374,10 +373,10 @@ __global__ void __launch_bounds__(kScoreThreads, 3) k_score_tuples(const ScoreAr
 
     for (;;) {
         unsigned u0 = 0;
-        if (lane == 0) u0 = atomicAdd(a1.work, (unsigned)kTupleBatch);
+        if (lane == 0) u0 = atomicAdd(a1.work, (unsigned)a1.batch);
         u0 = __shfl_sync(kFull, u0, 0);
         if (u0 >= total) break;
-        const unsigned uend = min(u0 + (unsigned)kTupleBatch, total);
+        const unsigned uend = min(u0 + (unsigned)a1.batch, total);
         for (unsigned ug = u0; ug < uend; ++ug) {
             unsigned u = ug;
             if (MULTI) {
@@ -674,7 +673,9 @@ cudaError_t launch_score_grid(const ScoreArgs &a1, const ScoreArgs *descs, const
         cudaSuccess)
         return err;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const long long warps_needed = (total + kTupleBatch - 1) / kTupleBatch;
+    if (a1.batch < 1) return cudaErrorInvalidValue;
+    if (a1.bpsm > 0) per_sm = std::min(per_sm, a1.bpsm);
+    const long long warps_needed = (total + a1.batch - 1) / a1.batch;
     const int grid = (int)std::min<long long>((long long)sms * per_sm, (warps_needed + kScoreWarps - 1) / kScoreWarps);
     k_score_tuples<MULTI><<<grid, kScoreThreads, 0, st>>>(a1, descs, tuple0, n_desc, (unsigned)total);
     return cudaGetLastError();
