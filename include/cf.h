@@ -100,9 +100,9 @@ typedef struct cf_field_params {
     const float *bin_dirs;    /* host [B][3] */
     int32_t want_rep;         /* 1: also keep, per (cell, finger, bin) code, the smallest s * M + m of the
                                  samples that produced it (reverse lookup, Sec. 5.5) */
-    float dilate_cos;         /* theta-dilated bins (the leaf test -x^T n >= theta_hit of Sec. 4.3): a query
-                                 of bin b accepts every bin b' with d_b . d_b' >= dilate_cos (FP64 on the
-                                 host); > 1 (e.g. 2) = same bin only */
+    float dilate_deg;         /* theta-dilated bins (the leaf test -x^T n >= theta_hit of Sec. 4.3): a query
+                                 of bin b accepts every bin b' with d_b . d_b' >= cos(dilate_deg * (pi / 180))
+                                 (FP64 on the host); 0 = the same bin only */
 } cf_field_params;
 
 typedef struct cf_field cf_field;
@@ -124,7 +124,7 @@ typedef struct cf_field_info {
     int64_t table_words;               /* total uint32 words of the bit table */
     int64_t device_bytes;              /* device memory held by the field */
     float build_ms;                    /* device time of the two build kernels */
-    float dilate_cos;                  /* bin dilation of queries (> 1: none) */
+    float dilate_deg;                  /* bin dilation of queries (0: none) */
     uint32_t dilation[CF_MAX_BINS];    /* bins accepted by a query of bin b */
 } cf_field_info;
 

@@ -165,7 +165,7 @@ class Field:
     sets used to flag ambiguous entries (tau metres, bin_tol in cosine)."""
 
     def __init__(self, hand, q: np.ndarray, inv_h, bins: np.ndarray, band: bool = False,
-                 tau: float = 1e-5, bin_tol: float = 1e-6, dilate_cos=None):
+                 tau: float = 1e-5, bin_tol: float = 1e-6, dilate_deg=None):
         self.F, self.J, self.M = hand.F, hand.J, hand.M
         self.B = int(bins.shape[0])
         self.inv_h = np.float32(inv_h)
@@ -177,7 +177,7 @@ class Field:
         self._h = lib().orc_field_create(self.F, self.J, self.M, *ptrs, _p(qq, c_float), S, c_float(self.inv_h),
                                          self.B, _p(self._bins, c_float), int(band), tau, bin_tol)
         del keep
-        self.dilation = dilation_masks(self._bins, dilate_cos) if dilate_cos is not None else None
+        self.dilation = dilation_masks(self._bins, dilate_deg) if dilate_deg is not None else None
         if self.dilation is not None:
             lib().orc_field_set_dilation(self._h, _p(self.dilation, c_uint32))
 
@@ -229,24 +229,27 @@ class Field:
         return tuple(out)
 
 
-def dilation_masks(bins: np.ndarray, dilate_cos: float) -> np.ndarray:
+def dilation_masks(bins: np.ndarray, dilate_deg: float) -> np.ndarray:
     """Theta-dilated bins (the leaf test -x^T n >= theta_hit of Sec. 4.3): bit b'
-    of entry b is set when d_b . d_b' >= dilate_cos (FP64 dot of the FP32
-    directions, x + y + z in that order); bit b always."""
+    of entry b is set when d_b . d_b' >= cos(theta), theta = dilate_deg degrees
+    (FP64 dot of the FP32 directions, x + y + z in that order); bit b always;
+    theta = 0 keeps the same bin only."""
     d = np.asarray(bins, np.float32).astype(np.float64)
     B = d.shape[0]
+    deg = float(np.float32(dilate_deg))
+    c = math.cos(deg * (math.pi / 180.0))
     out = np.zeros(B, np.uint32)
     for b in range(B):
         m = 1 << b
         for b2 in range(B):
             dot = float(d[b, 0]) * float(d[b2, 0]) + float(d[b, 1]) * float(d[b2, 1]) + float(d[b, 2]) * float(d[b2, 2])
-            if dot >= float(np.float32(dilate_cos)):
+            if deg > 0.0 and dot >= c:
                 m |= 1 << b2
         out[b] = m
     return out
 
 
-def query_masks_brute(hand, q, inv_h, bins, soa, poses, dilate_cos=None) -> np.ndarray:
+def query_masks_brute(hand, q, inv_h, bins, soa, poses, dilate_deg=None) -> np.ndarray:
     keep, ptrs = _hand_args(hand)
     qq = _c(q, np.float32)
     bb = _c(bins, np.float32)
@@ -255,7 +258,7 @@ def query_masks_brute(hand, q, inv_h, bins, soa, poses, dilate_cos=None) -> np.n
     N, P = int(soa.shape[1]), int(poses.shape[0])
     W = (N + 31) // 32
     masks = np.zeros((P, hand.F, W), np.uint32)
-    dil = dilation_masks(bb, dilate_cos) if dilate_cos is not None else None
+    dil = dilation_masks(bb, dilate_deg) if dilate_deg is not None else None
     lib().orc_query_masks_brute(hand.F, hand.J, hand.M, *ptrs, _p(qq, c_float), int(qq.shape[2]),
                                 c_float(np.float32(inv_h)), int(bb.shape[0]), _p(bb, c_float), N,
                                 _p(soa, c_float), P, _p(poses, c_float),

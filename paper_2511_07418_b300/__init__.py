@@ -55,7 +55,7 @@ class HandDesc(Structure):
 
 class FieldParams(Structure):
     _fields_ = [("inv_h", c_float), ("n_bins", c_int32), ("bin_dirs", POINTER(c_float)), ("want_rep", c_int32),
-                ("dilate_cos", c_float)]
+                ("dilate_deg", c_float)]
 
 
 class IkParams(Structure):
@@ -83,7 +83,7 @@ class FieldInfo(Structure):
                 ("box_lo", c_int32 * 3), ("box_dims", c_int32 * 3), ("bits_per_finger", c_int32),
                 ("fingers_per_word", c_int32), ("record_words", c_int32),
                 ("finger_lo", (c_int32 * 3) * CF_MAX_FINGERS), ("finger_dims", (c_int32 * 3) * CF_MAX_FINGERS),
-                ("table_words", c_int64), ("device_bytes", c_int64), ("build_ms", c_float), ("dilate_cos", c_float),
+                ("table_words", c_int64), ("device_bytes", c_int64), ("build_ms", c_float), ("dilate_deg", c_float),
                 ("dilation", c_uint32 * CF_MAX_BINS)]
 
 
@@ -291,7 +291,7 @@ class Field:
             pass
 
 
-def build(hand, inv_h, bin_dirs, q, stream=None, want_rep: bool = False, dilate_cos: float = 2.0) -> Field:
+def build(hand, inv_h, bin_dirs, q, stream=None, want_rep: bool = False, dilate_deg: float = 0.0) -> Field:
     """cf_build: hand is any object with base/axis/offset/surf_p/surf_n/surf_link
     arrays (host) and optionally lo/hi/radius, q a [F, J, S] float32 CUDA tensor
     of joint samples.  want_rep keeps the reverse-lookup table (needs limits)."""
@@ -310,7 +310,7 @@ def build(hand, inv_h, bin_dirs, q, stream=None, want_rep: bool = False, dilate_
                   *([_fp(a) for a in lim] if lim else [None, None, None]))
     dirs = _np(bin_dirs, np.float32)
     prm = FieldParams(float(np.float32(inv_h)), int(dirs.shape[0]), _fp(dirs), 1 if want_rep else 0,
-                      float(dilate_cos))
+                      float(dilate_deg))
     qp = _dev(q, torch.float32, "q")
     if q.dim() != 3 or tuple(q.shape[:2]) != (F, J):
         raise ValueError(f"q must be [F={F}, J={J}, S]")

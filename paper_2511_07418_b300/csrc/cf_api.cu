@@ -201,15 +201,17 @@ int geom_from_params(cf_field *fd, const cf_field_params *prm) {
     g.clamp = (float)(2097152.0 / (double)prm->inv_h);  // |x * inv_h| <= 2^21
     for (int b = 0; b < g.B; ++b)
         for (int c = 0; c < 3; ++c) g.dirs[b][c] = prm->bin_dirs[3 * b + c];
-    if (!(prm->dilate_cos == prm->dilate_cos)) return fail(CF_EINVAL, "dilate_cos is NaN");
-    g.dilate_cos = prm->dilate_cos;
+    if (!(prm->dilate_deg >= 0.f && prm->dilate_deg <= 180.f)) return fail(CF_EINVAL, "dilate_deg not in [0, 180]");
+    g.dilate_deg = prm->dilate_deg;
+    const double dcos = cos((double)prm->dilate_deg * (M_PI / 180.0));
     for (int b = 0; b < CF_MAX_BINS; ++b) g.dil[b] = 0u;
     for (int b = 0; b < g.B; ++b) {
         g.dil[b] = 1u << b;
+        if (!(prm->dilate_deg > 0.f)) continue;
         for (int b2 = 0; b2 < g.B; ++b2) {
             const double d = (double)g.dirs[b][0] * g.dirs[b2][0] + (double)g.dirs[b][1] * g.dirs[b2][1] +
                              (double)g.dirs[b][2] * g.dirs[b2][2];
-            if (d >= (double)prm->dilate_cos) g.dil[b] |= 1u << b2;
+            if (d >= dcos) g.dil[b] |= 1u << b2;
         }
     }
     fd->B = g.B;
@@ -452,7 +454,7 @@ extern "C" int cf_field_get_info(const cf_field *fd, cf_field_info *info) {
         cudaEventElapsedTime(&mfd->build_ms, mfd->ev0, mfd->ev1);
     }
     info->build_ms = fd->build_ms < 0.f ? 0.f : fd->build_ms;
-    info->dilate_cos = fd->geom.dilate_cos;
+    info->dilate_deg = fd->geom.dilate_deg;
     for (int b = 0; b < CF_MAX_BINS; ++b) info->dilation[b] = fd->geom.dil[b];
     return CF_OK;
 }

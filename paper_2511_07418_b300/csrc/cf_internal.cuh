@@ -75,8 +75,8 @@ struct FieldGeom {
     int bits, fpw, rw;       // bits per finger slot, slots per word, words per record
     int flo[CF_MAX_FINGERS][3], fdims[CF_MAX_FINGERS][3];  // tight per-finger bounds (reported only)
     float dirs[CF_MAX_BINS][3];
-    uint32_t dil[CF_MAX_BINS];  // bins a query of bin b accepts: d_b . d_b' >= dilate_cos (bit b always)
-    float dilate_cos;
+    uint32_t dil[CF_MAX_BINS];  // bins a query of bin b accepts: d_b . d_b' >= cos(dilate_deg) (bit b always)
+    float dilate_deg;           // 0: no dilation
     int use_cand;            // 1: candidate table valid (every cell has <= 4 candidates)
     const uint32_t *cand;    // device [kCandCells]
 };

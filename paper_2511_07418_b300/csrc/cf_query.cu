@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(kThreads) k_query_domains(const QueryArgs a) {
     for (int e = threadIdx.x; e < np * 12; e += kThreads) s_pose[e / 12][e % 12] = poses[(size_t)i0 * 12 + e];
     for (int e = threadIdx.x; e < kMaxPosesPerBlock * F; e += kThreads) s_cnt[e / F][e % F] = 0u;
     if (threadIdx.x < CF_MAX_BINS) s_dil[threadIdx.x] = g.dil[threadIdx.x];
-    const bool dilated = !(g.dilate_cos > 1.f);  // block-uniform
+    const bool dilated = g.dilate_deg > 0.f;  // block-uniform
     if (CAND) {
         for (int e = threadIdx.x; e < kCandCells; e += kThreads) s_cand[e] = __ldg(g.cand + e);
         if (threadIdx.x < g.B) s_dir[threadIdx.x] = make_float4(g.dirs[threadIdx.x][0], g.dirs[threadIdx.x][1],

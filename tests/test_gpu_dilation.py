@@ -25,12 +25,12 @@ def cf():
     return cf
 
 
-def _cos_between_levels(bins, target_deg):
+def _deg_between_levels(bins, target_deg):
+    """A dilation angle near target_deg that no pair of bins sits on."""
     d = bins.astype(np.float64)
-    dots = np.unique(np.round(d @ d.T, 12))
-    c = math.cos(math.radians(target_deg))
-    lo = dots[dots < c].max() if (dots < c).any() else -1.0
-    hi = dots[dots >= c].min()
+    ang = np.unique(np.round(np.degrees(np.arccos(np.clip(d @ d.T, -1, 1))), 9))
+    lo = ang[ang <= target_deg].max()
+    hi = ang[ang > target_deg].min() if (ang > target_deg).any() else 180.0
     return float(np.float32(0.5 * (lo + hi)))
 
 
@@ -43,11 +43,11 @@ def _bits(m, N):
                                           ("hand20_tool", 2, 8192, 36)])
 def test_dilated_masks(cf, name, P, S, deg):
     w = synth.workload(name, P=P, S=S)
-    c = _cos_between_levels(w.bins, deg)
+    c = _deg_between_levels(w.bins, deg)
     q = torch.from_numpy(w.q).cuda()
     soa = torch.from_numpy(w.obj.soa()).cuda()
     poses = torch.from_numpy(w.poses).cuda()
-    field = cf.build(w.hand, w.inv_h, w.bins, q, dilate_cos=c)
+    field = cf.build(w.hand, w.inv_h, w.bins, q, dilate_deg=c)
     inf = field.info()
     want = oracle.dilation_masks(w.bins, c)
     assert np.array_equal(np.array(inf.dilation[:w.B], np.uint32), want)
@@ -58,7 +58,7 @@ def test_dilated_masks(cf, name, P, S, deg):
     gm = gm.cpu().numpy().view(np.uint32)
     gc = gc.cpu().numpy().view(np.uint32)
     pm = pm.cpu().numpy().view(np.uint32)
-    ofd = oracle.Field(w.hand, w.q, w.inv_h, w.bins, band=True, dilate_cos=c)
+    ofd = oracle.Field(w.hand, w.q, w.inv_h, w.bins, band=True, dilate_deg=c)
     om, oc, amb = ofd.query(w.obj.soa(), w.poses, amb=True)
     gb, ob = _bits(gm, w.obj.N), _bits(om, w.obj.N)
     diff = gb != ob
@@ -74,9 +74,9 @@ def test_dilated_reverse_lookup_ik(cf):
     """With dilated bins a domain point may hit through a neighbouring bin; the
     reverse lookup then takes the lowest accepted bin present, on both sides."""
     w = synth.workload("hand16_superquadric", P=3, S=8192)
-    c = _cos_between_levels(w.bins, 50)
-    field = cf.build(w.hand, w.inv_h, w.bins, torch.from_numpy(w.q).cuda(), want_rep=True, dilate_cos=c)
-    ofd = oracle.Field(w.hand, w.q, w.inv_h, w.bins, dilate_cos=c)
+    c = _deg_between_levels(w.bins, 50)
+    field = cf.build(w.hand, w.inv_h, w.bins, torch.from_numpy(w.q).cuda(), want_rep=True, dilate_deg=c)
+    ofd = oracle.Field(w.hand, w.q, w.inv_h, w.bins, dilate_deg=c)
     soa = w.obj.soa()
     m, cnt = ofd.query(soa, w.poses)
     tup, fing = oracle.sample_tuples(m, cnt, w.obj.N, w.T, w.k, w.seed)

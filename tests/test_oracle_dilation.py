@@ -18,26 +18,25 @@ def small():
     return w, w.obj.soa()
 
 
-def _cos_between_levels(bins, target_deg):
-    """A threshold near cos(target) that no pair of bins sits on."""
+def _deg_between_levels(bins, target_deg):
+    """A dilation angle near target_deg that no pair of bins sits on."""
     d = bins.astype(np.float64)
-    dots = np.unique(np.round(d @ d.T, 12))
-    c = math.cos(math.radians(target_deg))
-    lo = dots[dots < c].max() if (dots < c).any() else -1.0
-    hi = dots[dots >= c].min()
+    ang = np.unique(np.round(np.degrees(np.arccos(np.clip(d @ d.T, -1, 1))), 9))
+    lo = ang[ang <= target_deg].max()
+    hi = ang[ang > target_deg].min() if (ang > target_deg).any() else 180.0
     return float(np.float32(0.5 * (lo + hi)))
 
 
 def test_dilation_masks_definition(small):
     w, _ = small
-    assert np.array_equal(oracle.dilation_masks(w.bins, 2.0), np.uint32(1) << np.arange(w.B, dtype=np.uint32))
-    full = oracle.dilation_masks(w.bins, -1.0)
+    assert np.array_equal(oracle.dilation_masks(w.bins, 0.0), np.uint32(1) << np.arange(w.B, dtype=np.uint32))
+    full = oracle.dilation_masks(w.bins, 180.0)
     assert np.all(full == np.uint32((1 << w.B) - 1))
-    c = _cos_between_levels(w.bins, 60)
-    m = oracle.dilation_masks(w.bins, c)
+    deg = _deg_between_levels(w.bins, 80)
+    m = oracle.dilation_masks(w.bins, deg)
     d = w.bins.astype(np.float64)
     for b in range(w.B):
-        want = sum(1 << b2 for b2 in range(w.B) if d[b] @ d[b2] >= c) | (1 << b)
+        want = sum(1 << b2 for b2 in range(w.B) if np.degrees(np.arccos(np.clip(d[b] @ d[b2], -1, 1))) <= deg) | (1 << b)
         assert m[b] == want
         assert all(((m[b] >> b2) & 1) == ((m[b2] >> b) & 1) for b2 in range(w.B))  # symmetric
 
@@ -45,9 +44,9 @@ def test_dilation_masks_definition(small):
 def test_no_and_full_dilation(small):
     w, soa = small
     base, _ = oracle.Field(w.hand, w.q, w.inv_h, w.bins).query(soa, w.poses)
-    same, _ = oracle.Field(w.hand, w.q, w.inv_h, w.bins, dilate_cos=2.0).query(soa, w.poses)
+    same, _ = oracle.Field(w.hand, w.q, w.inv_h, w.bins, dilate_deg=0.0).query(soa, w.poses)
     assert np.array_equal(base, same)
-    fd = oracle.Field(w.hand, w.q, w.inv_h, w.bins, dilate_cos=-1.0)
+    fd = oracle.Field(w.hand, w.q, w.inv_h, w.bins, dilate_deg=180.0)
     full, _ = fd.query(soa, w.poses)
     # full dilation: a hit iff the finger's field occupies the cell at all
     pi = np.repeat(np.arange(w.P), w.obj.N)
@@ -64,15 +63,15 @@ def test_dilation_monotone_and_brute_force(small):
     w, soa = small
     prev = None
     for deg in (20, 70, 110):
-        c = _cos_between_levels(w.bins, deg)
-        m, _ = oracle.Field(w.hand, w.q, w.inv_h, w.bins, dilate_cos=c).query(soa, w.poses)
+        c = _deg_between_levels(w.bins, deg)
+        m, _ = oracle.Field(w.hand, w.q, w.inv_h, w.bins, dilate_deg=c).query(soa, w.poses)
         if prev is not None:
             assert np.all((prev & ~m) == 0)  # a wider angle only adds hits
             assert (m & ~prev).any()         # and past the bin spacing it does add some
         prev = m
-    c = _cos_between_levels(w.bins, 70)
+    c = _deg_between_levels(w.bins, 70)
     q = np.ascontiguousarray(w.q[:, :, :64])
-    idx, _ = oracle.Field(w.hand, q, w.inv_h, w.bins, dilate_cos=c).query(soa, w.poses[:2])
-    brute = oracle.query_masks_brute(w.hand, q, w.inv_h, w.bins, soa, w.poses[:2], dilate_cos=c)
+    idx, _ = oracle.Field(w.hand, q, w.inv_h, w.bins, dilate_deg=c).query(soa, w.poses[:2])
+    brute = oracle.query_masks_brute(w.hand, q, w.inv_h, w.bins, soa, w.poses[:2], dilate_deg=c)
     assert np.array_equal(idx, brute)
     assert idx.any()
