@@ -91,6 +91,7 @@ def lib():
         L.orc_field_set_dilation.argtypes = [c_void_p, u32p]
         L.orc_sample_tuples.argtypes = [c_int, c_int, c_int, u32p, u32p, c_int, c_int, c_uint64, i32p, u8p]
         L.orc_num_threads.restype = c_int
+        L.orc_set_threads.argtypes = [c_int]
         L.orc_rep_codes.restype = c_int64
         L.orc_rep_codes.argtypes = [c_int, c_int, c_int, fp, fp, fp, fp, fp, i32p, fp, c_int, c_float, c_int, fp,
                                     c_int, POINTER(c_uint64), u32p, c_int64]
@@ -109,6 +110,10 @@ def _c(a, dtype):
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_threads(n: int) -> None:
+    lib().orc_set_threads(int(n))
 
 
 def philox4x32_10(ctr, key) -> np.ndarray:

@@ -579,6 +579,15 @@ int orc_num_threads(void) {
 #endif
 }
 
+/* OpenMP threads of the following calls (for a single-core timing) */
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
+}
+
 /* ------------------------------------------------------------------------ */
 /* Reverse lookup (Sec. 5.5 "Kinematics Optimization")                       */
 /* ------------------------------------------------------------------------ */
