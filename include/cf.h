@@ -397,6 +397,45 @@ int cf_batch_launches(const cf_batch *batch, int32_t *n_launches, int32_t *n_gro
 
 int cf_batch_destroy(cf_batch *batch);
 
+/* ---- object placement (Sec. 5.2) and preprocessing (Sec. 5.1) ------------ */
+
+typedef struct cf_place_params {
+    int32_t exhaustive;   /* 0: canonical placement, 1: exhaustive placement */
+    float centroid[3];    /* canonical: the object's centroid (object frame) */
+    float g[3], up[3];    /* canonical: anchor point and unit palm normal (palm frame) */
+    float d_lo, d_hi;     /* canonical: offset of the centroid along up */
+    uint64_t seed;        /* key of the draws */
+    uint32_t pose_base;   /* added to the pose index in the draws' counter */
+} cf_place_params;
+
+/* Palm poses d_poses [n_poses][12] (object -> palm, row-major (R | t)), FP64
+ * arithmetic rounded to FP32, from Philox4x32-10 words at counter (pose +
+ * pose_base, tag, 0, 0), key seed; u = (w >> 8) 2^-24.
+ * Canonical (tag 0x91AC): R = the unit quaternion (sqrt(1-u1) sin 2 pi u2,
+ * sqrt(1-u1) cos 2 pi u2, sqrt(u1) sin 2 pi u3, sqrt(u1) cos 2 pi u3) (x, y, z, w;
+ * Shoemake), t = g + (d_lo + u4 (d_hi - d_lo)) up - R centroid.
+ * Exhaustive (tag 0xE7A1; needs `field` and `obj`): the r-th code of the field
+ * in table order (cell, finger, bin), r = floor(w0 n_codes / 2^32), gives the
+ * point c = (k + 1/2) / inv_h (its cell centre) and the normal d_b (its bin
+ * direction); object point x = floor(w1 N / 2^32); R = Rot(d_b, 2 pi u2) R_align
+ * with R_align the shortest rotation taking n_x to -d_b (a half turn about
+ * (n_x x e) / |...| when opposite, e = e_x or e_y), t = c - R p_x.  The first
+ * exhaustive call on a field counts its codes per table chunk (one wait).
+ * Errors: CF_EINVAL, CF_ENOMEM, CF_ECUDA. */
+int cf_place(const cf_field *field, const cf_points *obj, int32_t n_poses, const cf_place_params *prm,
+             float *d_poses, cf_stream stream);
+
+/* Concave-point removal: point x is kept (d_keep[x] = 1) unless the object SDF
+ * (trilinear, cf_sdf_build) is below -tau at the centre or at a corner of the
+ * upper half of the cube of side `side` resting on the tangent plane outside x
+ * (centre p_x + (side / 2) n_x, axes (t1, t2, n_x), t1, t2 the Duff et al. 2017
+ * basis of n_x; samples at heights side/2 and side, lateral +-side/2).  The kept points
+ * are written to d_out [6][n] (px..nz rows of stride n, original order; may be
+ * NULL) and their number to *d_n_out (device).  Errors: CF_EINVAL, CF_ENOMEM,
+ * CF_ECUDA.  Asynchronous. */
+int cf_concave_filter(const cf_points *obj, const cf_sdf *sdf, float side, float tau, uint8_t *d_keep,
+                      float *d_out, int32_t *d_n_out, cf_stream stream);
+
 /* ---- launch shapes and the autotuner ------------------------------------- */
 
 /* Launch shapes of the query and scoring kernels on the current device.  The

@@ -278,7 +278,8 @@ def sdf_grid(soa, lo, h, dims, rel_tie: float = 1e-5):
     """Signed distance of the oriented point set on the grid lo + (i,j,k) h
     (brute force, FP64).  Returns grid [dz,dy,dx] and a per-node ambiguity flag:
     the sign decision is ambiguous when points within a relative distance
-    rel_tie of the nearest disagree on it, or (x - p) . n is ~0."""
+    rel_tie of the nearest disagree on it, or (x - p) . n is ~0, at a node more
+    than 1e-6 m from the nearest point."""
     soa = np.asarray(soa, np.float64)
     pts, nrm = soa[:3].T, soa[3:].T
     lo = np.asarray(lo, np.float32).astype(np.float64)
@@ -305,7 +306,8 @@ def sdf_grid(soa, lo, h, dims, rel_tie: float = 1e-5):
         near = d2 <= d2m[:, None] * (1.0 + rel_tie) ** 2 + 1e-18
         pos_near = np.any(near & (side >= 0), axis=1)
         neg_near = np.any(near & (side < 0), axis=1)
-        amb[a:a + chunk] = (pos_near & neg_near) | (np.abs(sm) <= 1e-9)
+        # a node within 1e-6 m of the surface has |value| ~ 0, so its sign cannot matter
+        amb[a:a + chunk] = ((pos_near & neg_near) | (np.abs(sm) <= 1e-9)) & (d2m > 1e-12)
     return val.reshape(dz, dy, dx), amb.reshape(dz, dy, dx)
 
 

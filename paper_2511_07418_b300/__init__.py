@@ -73,6 +73,11 @@ class Tuning(Structure):
                 ("score_blocks_per_sm", c_int32)]
 
 
+class PlaceParams(Structure):
+    _fields_ = [("exhaustive", c_int32), ("centroid", c_float * 3), ("g", c_float * 3), ("up", c_float * 3),
+                ("d_lo", c_float), ("d_hi", c_float), ("seed", c_uint64), ("pose_base", c_uint32)]
+
+
 class RealizeParams(Structure):
     _fields_ = [("pen_margin", c_float), ("axis_step", c_float), ("seed", c_uint64)]
 
@@ -175,6 +180,9 @@ _cf_sdf_destroy = _sig("cf_sdf_destroy", [c_void_p])
 _cf_realize = _sig("cf_realize", [c_void_p, c_void_p, c_void_p, c_int32, c_int32, POINTER(RealizeParams), c_void_p,
                                   c_void_p, c_void_p, c_void_p, c_void_p, c_void_p])
 _cf_fp32_peak = _sig("cf_fp32_peak", [POINTER(c_double)])
+_cf_place = _sig("cf_place", [c_void_p, POINTER(Points), c_int32, POINTER(PlaceParams), c_void_p, c_void_p])
+_cf_concave = _sig("cf_concave_filter", [POINTER(Points), c_void_p, c_float, c_float, c_void_p, c_void_p, c_void_p,
+                                         c_void_p])
 _cf_get_tuning = _sig("cf_get_tuning", [POINTER(Tuning)])
 _cf_set_tuning = _sig("cf_set_tuning", [POINTER(Tuning)])
 _cf_autotune = _sig("cf_autotune", [POINTER(BatchItem), c_int32, c_int32, POINTER(Tuning), POINTER(c_double)])
@@ -193,7 +201,7 @@ EXPORTED = ["cf_build", "cf_field_get_info", "cf_field_copy_table", "cf_field_de
             "cf_engine_create", "cf_engine_submit", "cf_engine_poll", "cf_engine_result_free", "cf_engine_get_stats",
             "cf_engine_drain", "cf_engine_destroy", "cf_field_rep_slots", "cf_field_copy_rep", "cf_ik_dls",
             "cf_sdf_build", "cf_sdf_copy", "cf_sdf_destroy", "cf_realize", "cf_fp32_peak", "cf_optimize_tuples", "cf_score_gswo",
-            "cf_get_tuning", "cf_set_tuning", "cf_autotune"]
+            "cf_get_tuning", "cf_set_tuning", "cf_autotune", "cf_place", "cf_concave_filter"]
 
 
 def _check(rc: int):
@@ -692,6 +700,42 @@ def realize(field: Field, sdf: Sdf, poses, T: int, q, used, gate_a, gate_b, prm:
                        _dev(q, torch.float32, "q"), _dev(used, torch.uint8, "used"),
                        _dev(flags, torch.uint8, "flags"), _stream(stream)))
     return flags
+
+
+def place_canonical(n_poses: int, centroid, g, up, d_lo=0.08, d_hi=0.12, seed=0, pose_base=0, device="cuda",
+                    stream=None):
+    """cf_place (canonical placement) -> poses [n_poses, 12] float32."""
+    import torch
+    f3 = lambda v: (c_float * 3)(*[float(x) for x in np.asarray(v, np.float32)])
+    prm = PlaceParams(0, f3(centroid), f3(g), f3(up), float(d_lo), float(d_hi), int(seed), int(pose_base))
+    poses = torch.empty((int(n_poses), 12), dtype=torch.float32, device=device)
+    _check(_cf_place(None, None, int(n_poses), byref(prm), _dev(poses, torch.float32, "poses"), _stream(stream)))
+    return poses
+
+
+def place_exhaustive(field: Field, soa, n_poses: int, seed=0, pose_base=0, stream=None):
+    """cf_place (exhaustive placement: a random field code aligned with a random object point)."""
+    import torch
+    z = (c_float * 3)(0.0, 0.0, 0.0)
+    prm = PlaceParams(1, z, z, z, 0.0, 0.0, int(seed), int(pose_base))
+    obj = points_struct(soa)
+    poses = torch.empty((int(n_poses), 12), dtype=torch.float32, device=soa.device)
+    _check(_cf_place(field.handle, byref(obj), int(n_poses), byref(prm), _dev(poses, torch.float32, "poses"),
+                     _stream(stream)))
+    return poses
+
+
+def concave_filter(soa, sdf: "Sdf", side: float = 0.004, tau: float = 0.001, stream=None):
+    """cf_concave_filter -> (keep [N] uint8, kept points [6, N] (first n_kept columns valid), n_kept int32 [1])."""
+    import torch
+    obj = points_struct(soa)
+    N = int(soa.shape[1])
+    keep = torch.empty((N,), dtype=torch.uint8, device=soa.device)
+    out = torch.empty((6, N), dtype=torch.float32, device=soa.device)
+    n = torch.zeros((1,), dtype=torch.int32, device=soa.device)
+    _check(_cf_concave(byref(obj), sdf.handle, float(side), float(tau), _dev(keep, torch.uint8, "keep"),
+                       _dev(out, torch.float32, "out"), _dev(n, torch.int32, "n"), _stream(stream)))
+    return keep, out, n
 
 
 def get_tuning() -> dict:

@@ -14,7 +14,7 @@ SRC_DIR = os.path.join(HERE, "csrc")
 INC_DIR = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcf.so")
-SOURCES = ["cf_api.cu", "cf_build.cu", "cf_query.cu", "cf_score.cu", "cf_bincand.cu", "cf_engine.cu", "cf_kin.cu", "cf_peak.cu", "cf_gswo.cu"]
+SOURCES = ["cf_api.cu", "cf_build.cu", "cf_query.cu", "cf_score.cu", "cf_bincand.cu", "cf_engine.cu", "cf_kin.cu", "cf_peak.cu", "cf_gswo.cu", "cf_place.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 

@@ -146,6 +146,7 @@ void field_release(cf_field *fd) {
     if (fd->d_cand) cudaFreeAsync(fd->d_cand, fd->st);
     if (fd->d_rep) cudaFreeAsync(fd->d_rep, fd->st);
     if (fd->d_qs) cudaFreeAsync(fd->d_qs, fd->st);
+    if (fd->d_prefix) cudaFreeAsync(fd->d_prefix, fd->st);
     if (fd->ev0) cudaEventDestroy(fd->ev0);
     if (fd->ev1) cudaEventDestroy(fd->ev1);
     delete fd;
@@ -1022,6 +1023,98 @@ extern "C" int cf_batch_destroy(cf_batch *b) {
 }
 
 // ---------------------------------------------------------------------------
+// object placement (Sec. 5.2) and preprocessing (Sec. 5.1)
+// ---------------------------------------------------------------------------
+namespace {
+// exclusive set-bit prefix per table chunk, built on first use and kept with the field
+int field_prefix(cf_field *fd) {
+    if (fd->d_prefix || fd->table_words == 0) return CF_OK;
+    const int n = (int)((fd->table_words + kChunkWords - 1) / kChunkWords);
+    unsigned long long *d_counts = nullptr;
+    int rc = pool_alloc((void **)&d_counts, sizeof(unsigned long long) * n, fd->st, "alloc chunk counts");
+    if (rc) return rc;
+    std::vector<unsigned long long> h(n + 1, 0);
+    cudaError_t e = launch_chunk_counts(fd->d_table, fd->table_words, d_counts, fd->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h.data() + 1, d_counts, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, fd->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(fd->st);
+    cudaFreeAsync(d_counts, fd->st);
+    if (e != cudaSuccess) return cuda_fail(e, "chunk counts");
+    for (int i = 0; i < n; ++i) h[i + 1] += h[i];
+    if ((rc = pool_alloc((void **)&fd->d_prefix, sizeof(unsigned long long) * (n + 1), fd->st, "alloc prefix"))) return rc;
+    CF_TRY(cudaMemcpyAsync(fd->d_prefix, h.data(), sizeof(unsigned long long) * (n + 1), cudaMemcpyHostToDevice, fd->st),
+           "copy prefix");
+    CF_TRY(cudaStreamSynchronize(fd->st), "prefix upload");
+    fd->n_chunks = n;
+    fd->n_codes = h[n];
+    return CF_OK;
+}
+}  // namespace
+
+extern "C" int cf_place(const cf_field *field, const cf_points *obj, int32_t n_poses, const cf_place_params *prm,
+                        float *d_poses, cf_stream stream) {
+    if (!prm) return fail(CF_EINVAL, "NULL argument");
+    if (n_poses < 0) return fail(CF_EINVAL, "n_poses < 0");
+    if (n_poses == 0) return CF_OK;
+    if (!d_poses) return fail(CF_EINVAL, "poses pointer is NULL");
+    PlaceArgs a;
+    memset(&a, 0, sizeof a);
+    a.P = n_poses;
+    a.seed_lo = (uint32_t)prm->seed;
+    a.seed_hi = (uint32_t)(prm->seed >> 32);
+    a.pose_base = prm->pose_base;
+    for (int c = 0; c < 3; ++c) {
+        a.centroid[c] = prm->centroid[c];
+        a.g[c] = prm->g[c];
+        a.up[c] = prm->up[c];
+    }
+    a.d_lo = prm->d_lo;
+    a.d_hi = prm->d_hi;
+    a.poses = d_poses;
+    const bool ex = prm->exhaustive != 0;
+    if (ex) {
+        if (!field) return fail(CF_EINVAL, "exhaustive placement needs the field");
+        int rc = check_points(obj);
+        if (rc) return rc;
+        if (obj->n < 1) return fail(CF_EINVAL, "exhaustive placement needs object points");
+        cf_field *fd = const_cast<cf_field *>(field);
+        if ((rc = field_prefix(fd))) return rc;
+        if (fd->n_codes == 0) return fail(CF_EINVAL, "the field holds no code");
+        a.table = fd->d_table;
+        a.prefix = fd->d_prefix;
+        a.n_chunks = fd->n_chunks;
+        a.n_codes = fd->n_codes;
+        a.table_words = fd->table_words;
+        a.g_field = fd->geom;
+        a.obj = *obj;
+    } else if (!(prm->d_hi >= prm->d_lo) || !isfinite(prm->d_lo) || !isfinite(prm->d_hi)) {
+        return fail(CF_EINVAL, "d_lo / d_hi must be finite with d_lo <= d_hi");
+    }
+    CF_TRY(launch_place(a, ex, (cudaStream_t)stream), "launch placement");
+    return CF_OK;
+}
+
+extern "C" int cf_concave_filter(const cf_points *obj, const cf_sdf *sdf, float side, float tau, uint8_t *d_keep,
+                                 float *d_out, int32_t *d_n_out, cf_stream stream) {
+    int rc = check_points(obj);
+    if (rc) return rc;
+    if (!sdf) return fail(CF_EINVAL, "sdf is NULL");
+    if (!(side > 0.f) || !isfinite(side) || !(tau >= 0.f) || !isfinite(tau))
+        return fail(CF_EINVAL, "side must be > 0 and tau >= 0");
+    if (obj->n == 0) return CF_OK;
+    if (!d_keep || !d_n_out) return fail(CF_EINVAL, "keep / n_out pointer is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned int *counts = nullptr;
+    const int blocks = (obj->n + 1023) / 1024;
+    if ((rc = pool_alloc((void **)&counts, sizeof(unsigned int) * blocks, st, "alloc block counts"))) return rc;
+    cudaError_t e = launch_concave(*obj, sdf->g, side, tau, d_keep, counts, d_out, d_n_out, st);
+    cudaError_t e2 = cudaFreeAsync(counts, st);
+    if (e != cudaSuccess) return cuda_fail(e, "launch k_concave / k_compact");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "free block counts");
+    return CF_OK;
+}
+
+// ---------------------------------------------------------------------------
 // launch shapes and the autotuner
 // ---------------------------------------------------------------------------
 namespace {
@@ -1228,13 +1321,6 @@ extern "C" int cf_plan_destroy(cf_plan *pl) {
 // ---------------------------------------------------------------------------
 // a6: reverse lookup + DLS IK;  a7: object SDF grid and realization filter
 // ---------------------------------------------------------------------------
-struct cf_sdf {
-    int dev = 0;
-    cudaStream_t st = nullptr;
-    cf::SdfGrid g{};
-    float *d_grid = nullptr;
-    int64_t nodes = 0;
-};
 
 extern "C" int cf_ik_dls(const cf_field *fd, const cf_points *obj, const float *d_poses, int32_t n_slots,
                          int32_t n_tuples, int32_t k, const int32_t *d_tuples, const uint8_t *d_fingers,

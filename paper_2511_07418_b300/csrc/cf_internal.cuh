@@ -189,6 +189,25 @@ struct SdfGrid {
     int dims[3];
 };
 
+// Trilinear object SDF at (x, y, z) (object frame); +inf outside the grid.
+__device__ __forceinline__ float sdf_at(const SdfGrid &g, float x, float y, float z) {
+    const float u = (x - g.lo[0]) * g.inv_h, v = (y - g.lo[1]) * g.inv_h, w = (z - g.lo[2]) * g.inv_h;
+    const float fu = floorf(u), fv = floorf(v), fw = floorf(w);
+    const int i = (int)fu, j = (int)fv, kk = (int)fw;
+    if (!(fu >= 0.f && fv >= 0.f && fw >= 0.f) || i + 1 >= g.dims[0] || j + 1 >= g.dims[1] || kk + 1 >= g.dims[2])
+        return INFINITY;  // outside the grid: farther from the object than its margin
+    const float a = u - fu, b = v - fv, c = w - fw;
+    const size_t sx = 1, sy = (size_t)g.dims[0], sz = (size_t)g.dims[0] * g.dims[1];
+    const float *p = g.v + (size_t)kk * sz + (size_t)j * sy + i;
+    const float v000 = __ldg(p), v100 = __ldg(p + sx), v010 = __ldg(p + sy), v110 = __ldg(p + sy + sx);
+    const float v001 = __ldg(p + sz), v101 = __ldg(p + sz + sx), v011 = __ldg(p + sz + sy),
+                v111 = __ldg(p + sz + sy + sx);
+    const float x00 = fmaf(a, v100 - v000, v000), x10 = fmaf(a, v110 - v010, v010);
+    const float x01 = fmaf(a, v101 - v001, v001), x11 = fmaf(a, v111 - v011, v011);
+    const float y0 = fmaf(b, x10 - x00, x00), y1 = fmaf(b, x11 - x01, x01);
+    return fmaf(c, y1 - y0, y0);
+}
+
 constexpr int kMaxCapsules = CF_MAX_FINGERS * CF_MAX_JOINTS;
 struct RealizeArgs {
     HandDev h;
@@ -211,6 +230,29 @@ struct RealizeArgs {
 cudaError_t launch_ik(const IkArgs &a, int *list, unsigned int *count, cudaStream_t st);
 cudaError_t launch_sdf(const cf_points &obj, const SdfGrid &g, float *grid, cudaStream_t st);
 cudaError_t launch_realize(const RealizeArgs &a, cudaStream_t st);
+
+// ---- placement (Sec. 5.2) and object preprocessing (Sec. 5.1) ----
+struct PlaceArgs {
+    int P;
+    uint32_t seed_lo, seed_hi, pose_base;
+    float centroid[3];
+    float g[3], up[3];  // canonical: anchor point and palm normal
+    float d_lo, d_hi;   // canonical: offset range along up
+    // exhaustive: the field's table, its chunk prefix counts and the object's points
+    const uint32_t *table;
+    const unsigned long long *prefix;  // [n_chunks + 1] exclusive prefix of set bits per chunk
+    int n_chunks;
+    unsigned long long n_codes;
+    long long table_words;
+    FieldGeom g_field;
+    cf_points obj;
+    float *poses;
+};
+constexpr int kChunkWords = 256;
+cudaError_t launch_chunk_counts(const uint32_t *table, long long words, unsigned long long *counts, cudaStream_t st);
+cudaError_t launch_place(const PlaceArgs &a, bool exhaustive, cudaStream_t st);
+cudaError_t launch_concave(const cf_points &obj, const SdfGrid &sdf, float side, float tau, uint8_t *keep,
+                           unsigned int *block_counts, float *out, int *n_out, cudaStream_t st);
 
 cudaError_t launch_gswo(const float *const pts[6], int N, long long n, int k, float mu, const float c[3], float rho,
                         float eps, int n_iter, const int32_t *tuples, float *value, uint8_t *accept, cudaStream_t st);
@@ -321,4 +363,15 @@ struct cf_field {
     float *d_qs = nullptr;                  // joint samples [F][J][S] (kept with the representative table)
     bool has_limits = false;
     std::vector<float> h_lo, h_hi, h_radius, h_offset;  // host copies for realization planning
+    unsigned long long *d_prefix = nullptr;  // exclusive set-bit prefix per table chunk (exhaustive placement)
+    int n_chunks = 0;
+    unsigned long long n_codes = 0;
+};
+
+struct cf_sdf {
+    int dev = 0;
+    cudaStream_t st = nullptr;
+    cf::SdfGrid g{};
+    float *d_grid = nullptr;
+    int64_t nodes = 0;
 };

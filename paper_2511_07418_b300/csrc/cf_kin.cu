@@ -509,24 +509,6 @@ __global__ void __launch_bounds__(kSdfThreads) k_sdf_build(const cf_points obj, 
 }
 
 // ---- realization filter --------------------------------------------------------
-__device__ __forceinline__ float sdf_at(const SdfGrid &g, float x, float y, float z) {
-    const float u = (x - g.lo[0]) * g.inv_h, v = (y - g.lo[1]) * g.inv_h, w = (z - g.lo[2]) * g.inv_h;
-    const float fu = floorf(u), fv = floorf(v), fw = floorf(w);
-    const int i = (int)fu, j = (int)fv, kk = (int)fw;
-    if (!(fu >= 0.f && fv >= 0.f && fw >= 0.f) || i + 1 >= g.dims[0] || j + 1 >= g.dims[1] || kk + 1 >= g.dims[2])
-        return INFINITY;  // outside the grid: farther from the object than its margin
-    const float a = u - fu, b = v - fv, c = w - fw;
-    const size_t sx = 1, sy = (size_t)g.dims[0], sz = (size_t)g.dims[0] * g.dims[1];
-    const float *p = g.v + (size_t)kk * sz + (size_t)j * sy + i;
-    const float v000 = __ldg(p), v100 = __ldg(p + sx), v010 = __ldg(p + sy), v110 = __ldg(p + sy + sx);
-    const float v001 = __ldg(p + sz), v101 = __ldg(p + sz + sx), v011 = __ldg(p + sz + sy),
-                v111 = __ldg(p + sz + sy + sx);
-    const float x00 = fmaf(a, v100 - v000, v000), x10 = fmaf(a, v110 - v010, v010);
-    const float x01 = fmaf(a, v101 - v001, v001), x11 = fmaf(a, v111 - v011, v011);
-    const float y0 = fmaf(b, x10 - x00, x00), y1 = fmaf(b, x11 - x01, x01);
-    return fmaf(c, y1 - y0, y0);
-}
-
 // Distance between segments [p0, p0 + d1] and [q0, q0 + d2] (both of positive
 // length): minimum of the convex quadratic |p0 + s d1 - q0 - t d2|^2 over the
 // unit square -- the unconstrained s for the unconstrained t, clamped, then t
