@@ -328,7 +328,9 @@ int cf_realize(const cf_field *field, const cf_sdf *sdf, const float *d_poses, i
  * d_accept = d_value <= eps_g.  Each J_j is the value after n_iter projected
  * gradient steps with Nesterov momentum (FISTA), step 1 / (2 tr(A^T A)), from
  * alpha = e_j, beta = 0 (an upper bound that tightens with n_iter).  Invalid
- * tuples (an id < 0) get +inf.  Errors: CF_EINVAL, CF_ECUDA.  Asynchronous. */
+ * tuples (an id < 0) get +inf.  The first call with a given n_iter on a device
+ * uploads its momentum table (synchronously, kept for the process).
+ * Errors: CF_EINVAL, CF_ECUDA.  Asynchronous otherwise. */
 int cf_score_gswo(const cf_points *obj, int32_t n_poses, const cf_score_params *prm, int32_t n_iter, float eps_g,
                   const int32_t *d_tuples, float *d_value, uint8_t *d_accept, cf_stream stream);
 

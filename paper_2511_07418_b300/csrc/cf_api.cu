@@ -675,6 +675,33 @@ extern "C" int cf_score_tuples(const cf_points *obj, int32_t n_fingers, const ui
     return CF_OK;
 }
 
+namespace {
+std::mutex g_beta_mu;
+std::vector<std::pair<std::pair<int, int>, float *>> g_beta;  // (device, n_iter) -> device table
+
+int momentum_table(int n_iter, const float **out) {
+    int dev = 0;
+    CF_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+    std::lock_guard<std::mutex> lk(g_beta_mu);
+    for (auto &e : g_beta)
+        if (e.first.first == dev && e.first.second == n_iter) { *out = e.second; return CF_OK; }
+    std::vector<float> beta((size_t)std::max(n_iter, 1), 0.f);
+    double t = 1.0;
+    for (int it = 0; it < n_iter; ++it) {
+        const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+        beta[it] = (float)((t - 1.0) / tn);
+        t = tn;
+    }
+    float *d = nullptr;
+    CF_TRY(cudaMalloc((void **)&d, sizeof(float) * beta.size()), "alloc momentum table");
+    cudaError_t e = cudaMemcpy(d, beta.data(), sizeof(float) * beta.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { cudaFree(d); return cuda_fail(e, "upload momentum table"); }
+    g_beta.push_back({{dev, n_iter}, d});
+    *out = d;
+    return CF_OK;
+}
+}  // namespace
+
 extern "C" int cf_score_gswo(const cf_points *obj, int32_t n_poses, const cf_score_params *prm, int32_t n_iter,
                              float eps_g, const int32_t *d_tuples, float *d_value, uint8_t *d_accept,
                              cf_stream stream) {
@@ -691,8 +718,12 @@ extern "C" int cf_score_gswo(const cf_points *obj, int32_t n_poses, const cf_sco
     if (n == 0) return CF_OK;
     if (!d_tuples || !d_value || !d_accept) return fail(CF_EINVAL, "array pointer is NULL");
     const float *pts[6] = {obj->px, obj->py, obj->pz, obj->nx, obj->ny, obj->nz};
-    CF_TRY(launch_gswo(pts, obj->n, n, prm->k, prm->mu, prm->centroid, prm->rho, eps_g, n_iter, d_tuples, d_value,
-                       d_accept, (cudaStream_t)stream),
+    // FISTA momentum coefficients (t_k - 1) / t_{k+1}, t_1 = 1, computed in FP64 once per
+    // (device, n_iter) and kept for the process
+    const float *d_beta = nullptr;
+    if ((rc = momentum_table(n_iter, &d_beta))) return rc;
+    CF_TRY(launch_gswo(pts, obj->n, n, prm->k, prm->mu, prm->centroid, prm->rho, eps_g, n_iter, d_beta, d_tuples,
+                       d_value, d_accept, (cudaStream_t)stream),
            "launch k_gswo");
     return CF_OK;
 }

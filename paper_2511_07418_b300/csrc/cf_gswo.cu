@@ -25,22 +25,24 @@ struct GswoArgs {
     int k;
     float mu, cx, cy, cz, inv_rho, eps;
     int n_iter;
+    const float *beta;   // [n_iter] momentum coefficients (t_k - 1) / t_{k+1}, from the host in FP64
     const int32_t *tuples;
     float *value;
     uint8_t *accept;
 };
 
-// Projection of (a, b1, b2) onto |b| <= mu a.
-__device__ __forceinline__ void project_soc(float &a, float &b1, float &b2, float mu) {
-    const float s = sqrtf(b1 * b1 + b2 * b2);
-    if (s <= mu * a) return;
-    if (mu * s <= -a) {
-        a = 0.f; b1 = 0.f; b2 = 0.f;
-        return;
-    }
-    const float a2 = (a + mu * s) / (1.f + mu * mu);
-    const float f = mu * a2 / s;
-    a = a2; b1 *= f; b2 *= f;
+// Projection of (a, b1, b2) onto |b| <= mu a, without branches: inside the cone
+// the point stays, inside the polar cone it goes to 0, otherwise to
+// a' = (a + mu s) / (1 + mu^2), b' = (mu a' / s) b.  inv1m = 1 / (1 + mu^2).
+__device__ __forceinline__ void project_soc(float &a, float &b1, float &b2, float mu, float inv1m) {
+    const float s2 = b1 * b1 + b2 * b2;
+    const float s = sqrtf(s2);
+    const bool inside = s <= mu * a, polar = mu * s <= -a;
+    const float a2 = (a + mu * s) * inv1m;
+    const float f = mu * a2 * rsqrtf(fmaxf(s2, 1e-30f));
+    const float fa = inside ? a : (polar ? 0.f : a2);
+    const float fb = inside ? 1.f : (polar ? 0.f : f);
+    a = fa; b1 *= fb; b2 *= fb;
 }
 
 template <int K>
@@ -105,8 +107,7 @@ __global__ void __launch_bounds__(kGswoThreads) k_gswo(const GswoArgs g) {
 #pragma unroll
         for (int i = 0; i < K; ++i)
             if (i == j) z[3 * i] = y[3 * i] = 1.f;
-        float t = 1.f;
-        const float mu = g.mu;
+        const float mu = g.mu, inv1m = 1.f / (1.f + g.mu * g.mu);
         for (int it = 0; it < g.n_iter; ++it) {
             float zn[V];
 #pragma unroll
@@ -118,26 +119,22 @@ __global__ void __launch_bounds__(kGswoThreads) k_gswo(const GswoArgs g) {
             }
 #pragma unroll
             for (int i = 0; i < K; ++i) {
-                if (i == j) {  // alpha_j = 1, friction in the disc |b| <= mu
-                    zn[3 * i] = 1.f;
-                    const float s = sqrtf(zn[3 * i + 1] * zn[3 * i + 1] + zn[3 * i + 2] * zn[3 * i + 2]);
-                    if (s > mu) {
-                        const float f = mu / s;
-                        zn[3 * i + 1] *= f;
-                        zn[3 * i + 2] *= f;
-                    }
-                } else {
-                    project_soc(zn[3 * i], zn[3 * i + 1], zn[3 * i + 2], mu);
-                }
+                // contact j: alpha_j = 1, friction in the disc |b| <= mu; the others: the cone
+                float a = zn[3 * i], b1 = zn[3 * i + 1], b2 = zn[3 * i + 2];
+                project_soc(a, b1, b2, mu, inv1m);
+                const float s2 = zn[3 * i + 1] * zn[3 * i + 1] + zn[3 * i + 2] * zn[3 * i + 2];
+                const float fd = fminf(1.f, mu * rsqrtf(fmaxf(s2, 1e-30f)));
+                const bool mine = i == j;
+                zn[3 * i] = mine ? 1.f : a;
+                zn[3 * i + 1] = mine ? zn[3 * i + 1] * fd : b1;
+                zn[3 * i + 2] = mine ? zn[3 * i + 2] * fd : b2;
             }
-            const float tn = 0.5f * (1.f + sqrtf(1.f + 4.f * t * t));
-            const float beta = (t - 1.f) / tn;
+            const float beta = __ldg(g.beta + it);
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 y[v] = zn[v] + beta * (zn[v] - z[v]);
                 z[v] = zn[v];
             }
-            t = tn;
         }
         // J_j = |A z|^2
         J = 0.f;
@@ -166,10 +163,11 @@ __global__ void __launch_bounds__(kGswoThreads) k_gswo(const GswoArgs g) {
 }  // namespace
 
 cudaError_t launch_gswo(const float *const pts[6], int N, long long n, int k, float mu, const float c[3], float rho,
-                        float eps, int n_iter, const int32_t *tuples, float *value, uint8_t *accept, cudaStream_t st) {
+                        float eps, int n_iter, const float *beta, const int32_t *tuples, float *value, uint8_t *accept,
+                        cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     GswoArgs g{pts[0], pts[1], pts[2], pts[3], pts[4], pts[5], N, n, k, mu, c[0], c[1], c[2], 1.f / rho, eps, n_iter,
-               tuples, value, accept};
+               beta, tuples, value, accept};
     const long long per_warp = 32 / k;
     const long long warps = (n + per_warp - 1) / per_warp;
     const unsigned blocks = (unsigned)((warps * 32 + kGswoThreads - 1) / kGswoThreads);

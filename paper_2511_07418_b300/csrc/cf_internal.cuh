@@ -255,7 +255,8 @@ cudaError_t launch_concave(const cf_points &obj, const SdfGrid &sdf, float side,
                            unsigned int *block_counts, float *out, int *n_out, cudaStream_t st);
 
 cudaError_t launch_gswo(const float *const pts[6], int N, long long n, int k, float mu, const float c[3], float rho,
-                        float eps, int n_iter, const int32_t *tuples, float *value, uint8_t *accept, cudaStream_t st);
+                        float eps, int n_iter, const float *beta, const int32_t *tuples, float *value, uint8_t *accept,
+                        cudaStream_t st);
 cudaError_t launch_popcount(const uint32_t *table, long long words, unsigned long long *count, cudaStream_t st);
 cudaError_t launch_fk_rep(const HandDev &h, const float *links, int S, const FieldGeom &g, RepTable t,
                           unsigned int *status, cudaStream_t st);
