@@ -101,16 +101,20 @@ __device__ __forceinline__ int bin_by_candidates(float mx, float my, float mz, c
     const int iv = min(max((int)__fmaf_rn(mb, inv * (0.5f * kCandG), 0.5f * kCandG), 0), kCandG - 1);
     const uint32_t word = s_cand[(face * kCandG + iu) * kCandG + iv];
     const int cnt = (int)(word >> 24);
-    int bin = (int)(word & 63u);
-    if (cnt > 1) {
-        float4 d = s_dir[bin];
-        float best = __fmaf_rn(d.z, mz, __fmaf_rn(d.y, my, __fmul_rn(d.x, mx)));
-        for (int c = 1; c < cnt; ++c) {
-            const int b = (int)((word >> (6 * c)) & 63u);
-            d = s_dir[b];
-            const float sc = __fmaf_rn(d.z, mz, __fmaf_rn(d.y, my, __fmul_rn(d.x, mx)));
-            if (sc > best) { best = sc; bin = b; }
-        }
+    // the first two candidates (ascending) without a branch: a one-candidate cell
+    // compares its bin with itself; most cells have one or two
+    const int b0 = (int)(word & 63u);
+    const int b1 = cnt > 1 ? (int)((word >> 6) & 63u) : b0;
+    const float4 d0 = s_dir[b0], d1 = s_dir[b1];
+    float best = __fmaf_rn(d0.z, mz, __fmaf_rn(d0.y, my, __fmul_rn(d0.x, mx)));
+    const float s1 = __fmaf_rn(d1.z, mz, __fmaf_rn(d1.y, my, __fmul_rn(d1.x, mx)));
+    int bin = b0;
+    if (s1 > best) { best = s1; bin = b1; }
+    for (int c = 2; c < cnt; ++c) {  // rare
+        const int b = (int)((word >> (6 * c)) & 63u);
+        const float4 d = s_dir[b];
+        const float sc = __fmaf_rn(d.z, mz, __fmaf_rn(d.y, my, __fmul_rn(d.x, mx)));
+        if (sc > best) { best = sc; bin = b; }
     }
     return bin;
 }
