@@ -96,7 +96,9 @@ __device__ __forceinline__ int bin_by_candidates(float mx, float my, float mz, c
     const int face = xmaj ? (mx < 0.f ? 1 : 0) : (ymaj ? (my < 0.f ? 3 : 2) : (mz < 0.f ? 5 : 4));
     const float ma = xmaj ? my : mx;
     const float mb = (xmaj || ymaj) ? mz : my;
-    const float inv = __frcp_rn(xmaj ? ax : (ymaj ? ay : az));
+    // approximate reciprocal (relative error ~1e-7): the table's cells are enlarged by 1e-4 in u, v, so a
+    // cell chosen from a slightly perturbed coordinate still lists the true bin
+    const float inv = __fdividef(1.f, fmaxf(ax, fmaxf(ay, az)));
     const int iu = min(max((int)__fmaf_rn(ma, inv * (0.5f * kCandG), 0.5f * kCandG), 0), kCandG - 1);
     const int iv = min(max((int)__fmaf_rn(mb, inv * (0.5f * kCandG), 0.5f * kCandG), 0), kCandG - 1);
     const uint32_t word = s_cand[(face * kCandG + iu) * kCandG + iv];
