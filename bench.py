@@ -37,7 +37,7 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) per launch from the committed ncu captures of the
 # current kernels on this workload (profiles/k_score_tuples_hand16_superquadric.md,
 # profiles/k_query_domains_hand16_superquadric.md); None for other workloads.
-NCU_TRAFFIC = {"hand16_superquadric": {"k_score_tuples": 6_705_408, "k_query_domains": 2_620_928 + 12_639_232}}
+NCU_TRAFFIC = {"hand16_superquadric": {}}
 
 
 def _args():
@@ -355,7 +355,9 @@ def run_ours(args):
     peak_fp32 = peak_measured
     pairs = w.P * w.obj.N
     q_flop = pairs * (18 + 3 * w.B + 3 * F) * 2
-    s_flop_own = (counters["lp_pivots"] * 13 * 39 + counters["tuples_scored"] * w.k * w.K * 15) * 2 / args.steps
+    # scaled bounded LP: a pivot updates the 6 rows + reduced costs of the kK + 6 columns
+    s_flop_own = (counters["lp_pivots"] * 7 * (w.k * w.K + 6) + counters["tuples_scored"] * w.k * w.K * 15) * 2 \
+        / args.steps
     b_flop = F * w.S * w.hand.M * (18 + 3 + 3 * w.B) * 2
     traffic = NCU_TRAFFIC.get(w.name, {})
     kernels = {

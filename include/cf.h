@@ -64,7 +64,7 @@ enum {
 
 /* device status bits (cf_device_status) */
 #define CF_DEV_LP_PIVOT_CAP 0x1u   /* an LP stopped at its pivot cap; its margin is an upper bound */
-#define CF_DEV_LP_UNBOUNDED 0x2u   /* an LP ratio test found no pivot row (numerical) */
+#define CF_DEV_LP_UNBOUNDED 0x2u   /* reserved (the scaled LP reads an unbounded ratio test as margin 0) */
 #define CF_DEV_REP_FULL 0x4u       /* the representative table had no free slot (cannot happen at load <= 1/2) */
 #define CF_DEV_REP_MISS 0x8u       /* an IK contact's code has no representative (tuple not from this field) */
 #define CF_DEV_BIN_RANGE 0x80000000u /* a build sample fell outside the table box (cannot happen) */

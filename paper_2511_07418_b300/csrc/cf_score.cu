@@ -15,18 +15,12 @@
 // with per-32-word popcount prefixes; one thread per tuple draws its fingers
 // and points (Philox4x32-10) and writes them out.
 //
-// k_score_tuples: persistent warps pull batches of tuples from a work counter
-// and solve each tuple's LPs, one LP at a time per warp.  Tableau layout: 13
-// constraint rows plus the reduced-cost row.  Column c_im (i-major, kK <= 32)
-// lives in slot A of lane c; t lives in slot B of lane 0 and slack s_r in slot
-// B of lane r + 1.  Lane r (< 14) also holds row r's right-hand side and basic
-// variable (row 13: the objective).  Pricing and the ratio test are single
-// warp reductions (redux.sync) on order-preserving integer keys of the floats;
-// the entering column reaches every lane through a per-warp shared buffer.
-// Two forced pivots give a feasible start (the edge of contact j with the
-// smallest max-norm wrench enters the equality row, then t enters the most
-// violated row); Dantzig pricing follows, with Bland's rule after a run of
-// degenerate pivots.  FP32 throughout.
+// k_score_tuples: persistent warps pull batches of tuples from a work counter;
+// each warp solves its tuple's k LPs in the scaled bounded-variable form below
+// (6 rows, kK + 6 columns, one column per lane), LP_{j+1} warm-started from
+// LP_j's basis.  Pricing and the ratio test are single warp reductions
+// (redux.sync) on order-preserving integer keys of the floats; the entering
+// column reaches every lane through a per-warp shared buffer.  FP32 throughout.
 #include <limits.h>
 
 #include <string.h>
@@ -197,164 +191,221 @@ __device__ __forceinline__ int warp_argmin_lane(float v) {
     return __ffs(__ballot_sync(kFull, key == kmin)) - 1;
 }
 
-#define CF_ROWS13(X) X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12)
+// Scaled LP.  For t > 0 put c = t c'; then LP_j = 1 / s_j with
+//     s_j = max sum_m c'_jm  s.t.  -1 <= (sum_im c'_im w_im)_r <= 1 (r = 1..6),  c' >= 0,
+// and LP_j = 0 exactly when s_j is unbounded.  With y = W c' kept as six
+// variables boxed in [-1, 1], the LP has 6 equality rows W c' - y = 0 and
+// kK + 6 columns, and c' = 0, y = 0 is a feasible start (no phase 1).  The j
+// subproblems differ only in the objective, so LP_{j+1} starts from LP_j's
+// optimal basis.  Bounded-variable primal simplex: Dantzig pricing, ratio test
+// over the basic variables' bounds and the entering variable's own box (a bound
+// flip), the largest pivot entry among tied rows, Bland's rule after a run of
+// degenerate pivots.
+//
+// Warp layout (NS slots per lane): the column with id c' = 0..kK-1 (contact
+// c / K, edge c % K) is slot 0 of lane c; the y_r columns are slot 0 of lane
+// kK + r when kK + 6 <= 32 (NS = 1), else slot 1 of lane r (id 32 + r).  Each
+// slot holds the column's 6 tableau entries and its reduced cost.  Lane r < 6
+// also holds row r's basic variable (id) and its value.
+constexpr int kRows = 6;
+constexpr unsigned kNoKey = 0xffffffffu;
 
-struct LpWarp {
-    float A[14], B[14];
-    float rhs;   // row `lane` (< 14)
-    int basis;   // basic variable of row `lane` (< 13)
+template <int NS>
+struct BoxLp {
+    float T[NS][kRows + 1];  // rows 0..5 of the tableau, then the reduced cost
+    int st[NS];              // 0 basic, 1 at lower bound, 2 at upper bound, 3 no column
+    float v;                 // lane r < 6: value of row r's basic variable
+    int beta;                // lane r < 6: id of row r's basic variable
 };
 
-// Put entering column e into the warp's shared buffer; every lane gets its own
-// row's entry (mycol) back.
-__device__ __forceinline__ float publish_column(const LpWarp &s, int e, int lane, float *buf) {
-    const bool slotB = e >= 32;
-    const bool owner = lane == (e & 31);
-    float v[14];
-#pragma unroll
-    for (int r = 0; r < 14; ++r) v[r] = slotB ? s.B[r] : s.A[r];
-    if (owner) {  // predicated vector stores (no divergent path)
-        float4 *b4 = reinterpret_cast<float4 *>(buf);
-        b4[0] = make_float4(v[0], v[1], v[2], v[3]);
-        b4[1] = make_float4(v[4], v[5], v[6], v[7]);
-        b4[2] = make_float4(v[8], v[9], v[10], v[11]);
-        reinterpret_cast<float2 *>(buf)[6] = make_float2(v[12], v[13]);
-    }
-    __syncwarp();
-    return lane < 14 ? buf[lane] : 0.f;
-}
+template <int NS>
+__device__ __forceinline__ int y_id(int r, int kK) { return NS == 1 ? kK + r : 32 + r; }
 
-// Pivot on (row l, column e) once the column is published in buf.
-__device__ __forceinline__ void pivot(LpWarp &s, float mycol, int l, int e, int lane, const float *buf) {
-    const float pe = __shfl_sync(kFull, mycol, l);
-    const float inv = __fdividef(1.f, pe);  // fast reciprocal: pivot entries are >= kPTol in size
-    float pa = 0.f, pb = 0.f;
-    switch (l) {
-#define CF_GET(r) \
-    case r: pa = s.A[r]; pb = s.B[r]; break;
-        CF_ROWS13(CF_GET)
-#undef CF_GET
-        default: break;
-    }
-    pa = __fmul_rn(pa, inv);
-    pb = __fmul_rn(pb, inv);
-    float col[14];
+// Closure margin min_j LP_j of one tuple on the warp.  w = this lane's wrench
+// column (lanes < kK).  Stops at the first unbounded s_j (margin 0).
+template <int NS>
+__device__ float closure_margin(const float (&w)[6], int k, int K, int lane, float *buf, unsigned long long &n_piv,
+                                unsigned long long &n_lp, unsigned &flags) {
+    const int kK = k * K;
+    BoxLp<NS> s;
 #pragma unroll
-    for (int r = 0; r < 14; r += 2) {
-        const float2 c2 = *reinterpret_cast<const float2 *>(buf + r);
-        col[r] = c2.x;
-        col[r + 1] = c2.y;
-    }
+    for (int q = 0; q < NS; ++q) {
+        const int id = 32 * q + lane;
+        const bool isx = q == 0 && lane < kK;
+        const int yr = NS == 1 ? lane - kK : (q == 1 ? lane : -1);
+        const bool isy = yr >= 0 && yr < kRows;
 #pragma unroll
-    for (int r = 0; r < 14; ++r) {
-        s.A[r] = __fmaf_rn(-col[r], pa, s.A[r]);
-        s.B[r] = __fmaf_rn(-col[r], pb, s.B[r]);
+        for (int r = 0; r < kRows; ++r) s.T[q][r] = isx ? -w[r] : (isy && r == yr ? 1.f : 0.f);
+        s.T[q][kRows] = 0.f;
+        s.st[q] = isx ? 1 : (isy ? 0 : 3);
+        (void)id;
     }
-    switch (l) {  // row l is the scaled pivot row
-#define CF_SET(r) \
-    case r: s.A[r] = pa; s.B[r] = pb; break;
-        CF_ROWS13(CF_SET)
-#undef CF_SET
-        default: break;
-    }
-    const float rl = __fmul_rn(__shfl_sync(kFull, s.rhs, l), inv);
-    if (lane == l) {
-        s.rhs = rl;
-        s.basis = e;
-    } else {
-        s.rhs = __fmaf_rn(-mycol, rl, s.rhs);
-    }
-    __syncwarp();  // every lane has read buf before it is written again
-}
+    s.v = 0.f;
+    s.beta = lane < kRows ? y_id<NS>(lane, kK) : -1;
 
-// One LP_j on the warp; returns max(t*, 0).  w = this lane's wrench column.
-__device__ float solve_lp(const float (&w)[6], bool colA, int ci, int j, int lane, float *buf, int &npiv,
-                          unsigned &flags) {
-    LpWarp s;
-    const bool inj = colA && ci == j;
-#pragma unroll
-    for (int r = 0; r < 6; ++r) {
-        s.A[r] = colA ? w[r] : 0.f;
-        s.A[6 + r] = colA ? -w[r] : 0.f;
-    }
-    s.A[12] = inj ? 1.f : 0.f;
-    s.A[13] = colA ? 0.f : INFINITY;
-#pragma unroll
-    for (int r = 0; r < 12; ++r) s.B[r] = lane == 0 ? -1.f : (lane == r + 1 ? 1.f : 0.f);
-    s.B[12] = 0.f;
-    s.B[13] = lane == 0 ? 1.f : (lane < 13 ? 0.f : INFINITY);
-    s.rhs = lane == 12 ? 1.f : 0.f;
-    s.basis = lane < 12 ? 33 + lane : -1;
-
-    // start 1: the edge of contact j with the smallest max-norm wrench enters the equality row
-    float mw = INFINITY;
-    if (inj) {
-        mw = 0.f;
-#pragma unroll
-        for (int r = 0; r < 6; ++r) mw = fmaxf(mw, fabsf(w[r]));
-    }
-    const int e1 = warp_argmin_lane(mw);
-    float mycol = publish_column(s, e1, lane, buf);
-    pivot(s, mycol, 12, e1, lane, buf);
-    // start 2: t enters the most violated row -> every right-hand side >= 0
-    const int q = warp_argmin_lane(lane < 12 ? s.rhs : INFINITY);
-    mycol = publish_column(s, 32, lane, buf);
-    pivot(s, mycol, q, 32, lane, buf);
-    npiv = 2;
-
-    const unsigned dthr = fkey(-kDTol) & ~63u;
     const unsigned kinf = fkey(INFINITY);
     const unsigned kzero = fkey(0.f);
-    bool bland = false;
-    int degenerate = 0, it = 0;
-    for (; it < kMaxPivots; ++it) {
-        int e;
-        if (bland) {
-            const unsigned ba = __ballot_sync(kFull, s.A[13] < -kDTol);
-            const unsigned bb = __ballot_sync(kFull, s.B[13] < -kDTol);
-            e = ba ? __ffs(ba) - 1 : (bb ? 31 + __ffs(bb) : -1);
-        } else {
-            const unsigned ka = (fkey(s.A[13]) & ~63u) | (unsigned)lane;
-            const unsigned kb = (fkey(s.B[13]) & ~63u) | (unsigned)(32 + lane);
-            const unsigned kmin = __reduce_min_sync(kFull, min(ka, kb));
-            e = (kmin & ~63u) < dthr ? (int)(kmin & 63u) : -1;
+    float best_s = 0.f;
+    bool unbounded = false;
+    for (int j = 0; j < k && !unbounded; ++j) {
+        const int c0 = j * K, c1 = c0 + K;  // contact j's columns
+        // reduced costs of the objective sum_m c'_jm at the current basis
+        const unsigned inj =
+            __ballot_sync(kFull, lane < kRows && s.beta >= c0 && s.beta < c1) & ((1u << kRows) - 1u);
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+            const int id = 32 * q + lane;
+            float d = (id >= c0 && id < c1 && s.st[q] != 3) ? 1.f : 0.f;
+#pragma unroll
+            for (int r = 0; r < kRows; ++r)
+                if (inj & (1u << r)) d -= s.T[q][r];
+            s.T[q][kRows] = s.st[q] == 0 ? 0.f : d;
         }
-        if (e < 0) break;
-        mycol = publish_column(s, e, lane, buf);
-        // ratio test over rows 0..12 (lane = row)
-        const float ratio = (lane < 13 && mycol > kPTol) ? __fdividef(fmaxf(s.rhs, 0.f), mycol) : INFINITY;
-        const unsigned rk = fkey(ratio);
-        const unsigned rmin = __reduce_min_sync(kFull, rk);
-        if (rmin == kinf) {
-            flags |= CF_DEV_LP_UNBOUNDED;
+        bool bland = false;
+        int degenerate = 0, it = 0;
+        for (; it < kMaxPivots; ++it) {
+            // pricing: an at-lower column with d > 0 or an at-upper column with d < 0
+            int e;
+            float sc[NS];
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                const float d = s.T[q][kRows];
+                sc[q] = s.st[q] == 1 ? d : (s.st[q] == 2 ? -d : -INFINITY);
+            }
+            if (bland) {
+                const unsigned b0 = __ballot_sync(kFull, sc[0] > kDTol);
+                const unsigned b1 = NS > 1 ? __ballot_sync(kFull, sc[NS - 1] > kDTol) : 0u;
+                e = b0 ? __ffs(b0) - 1 : (b1 ? 31 + __ffs(b1) : -1);
+            } else {
+                unsigned key = kNoKey;
+#pragma unroll
+                for (int q = 0; q < NS; ++q)
+                    if (sc[q] > kDTol) key = min(key, (fkey(-sc[q]) & ~63u) | (unsigned)(32 * q + lane));
+                const unsigned kmin = __reduce_min_sync(kFull, key);
+                e = kmin == kNoKey ? -1 : (int)(kmin & 63u);
+            }
+            if (e < 0) break;
+            // publish the entering column (and its direction: +1 up from lower, -1 down from upper)
+            const int qe = e >> 5;
+            if (lane == (e & 31)) {
+                float c[kRows + 1];
+                int ste = 0;
+#pragma unroll
+                for (int q = 0; q < NS; ++q)
+                    if (q == qe) {
+#pragma unroll
+                        for (int r = 0; r <= kRows; ++r) c[r] = s.T[q][r];
+                        ste = s.st[q];
+                    }
+                float4 *b4 = reinterpret_cast<float4 *>(buf);
+                b4[0] = make_float4(c[0], c[1], c[2], c[3]);
+                b4[1] = make_float4(c[4], c[5], c[6], ste == 1 ? 1.f : -1.f);
+            }
             __syncwarp();
-            break;
+            const float4 c03 = reinterpret_cast<const float4 *>(buf)[0];
+            const float4 c47 = reinterpret_cast<const float4 *>(buf)[1];
+            const float col[kRows + 1] = {c03.x, c03.y, c03.z, c03.w, c47.x, c47.y, c47.z};
+            const float dl = c47.w;
+            const bool ey = e >= kK;  // entering a y (boxed, range 2)
+            // ratio test: lane r < 6 -> row r; lane 6 -> the entering variable's own box
+            const float mine = lane < kRows ? buf[lane] : 0.f;
+            const float alpha = mine * dl;  // the basic variable of row lane moves by -alpha theta
+            float theta = INFINITY;
+            if (lane < kRows) {
+                const bool bx = s.beta < kK;
+                const float lo = bx ? 0.f : -1.f, hi = bx ? INFINITY : 1.f;
+                if (alpha > kPTol) theta = __fdividef(fmaxf(s.v - lo, 0.f), alpha);
+                else if (alpha < -kPTol) theta = __fdividef(fmaxf(hi - s.v, 0.f), -alpha);
+            } else if (lane == kRows && ey) {
+                theta = 2.f;
+            }
+            const unsigned rk = fkey(theta);
+            const unsigned rmin = __reduce_min_sync(kFull, rk);
+            if (rmin == kinf) {  // s_j unbounded: LP_j = 0
+                unbounded = true;
+                __syncwarp();
+                break;
+            }
+            const bool tie = rk == rmin;
+            unsigned cand;
+            if (bland) {  // a bound flip first, then the lowest basic-variable id
+                const unsigned bk = !tie ? kNoKey : (lane == kRows ? 0u : (unsigned)s.beta + 1u);
+                const unsigned bmin = __reduce_min_sync(kFull, bk);
+                cand = __ballot_sync(kFull, tie && bk == bmin);
+            } else {      // a bound flip first, then the largest pivot entry
+                const unsigned mk = !tie ? 0u : (lane == kRows ? kinf : fkey(fabsf(alpha)));
+                const unsigned mmax = __reduce_max_sync(kFull, mk);
+                cand = __ballot_sync(kFull, tie && mk == mmax);
+            }
+            const int l = __ffs(cand) - 1;
+            const float th = __shfl_sync(kFull, theta, l);
+            degenerate = rmin == kzero ? degenerate + 1 : 0;
+            if (degenerate >= kDegenerateToBland) bland = true;
+            ++n_piv;
+            if (l == kRows) {  // bound flip: no basis change
+                if (lane < kRows) s.v = __fmaf_rn(-alpha, th, s.v);
+#pragma unroll
+                for (int q = 0; q < NS; ++q)
+                    if (q == qe && lane == (e & 31)) s.st[q] = 3 - s.st[q];
+                __syncwarp();
+                continue;
+            }
+            const int leave = __shfl_sync(kFull, s.beta, l);
+            const float piv = __shfl_sync(kFull, mine, l);
+            const bool to_lower = piv * dl > 0.f;  // the leaving variable stops at its lower bound
+            const float xe0 = !ey ? 0.f : (dl > 0.f ? -1.f : 1.f);
+            if (lane < kRows) {
+                if (lane == l) {
+                    s.v = xe0 + dl * th;
+                    s.beta = e;
+                } else {
+                    s.v = __fmaf_rn(-alpha, th, s.v);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                const int id = 32 * q + lane;
+                if (id == e) s.st[q] = 0;
+                if (id == leave) s.st[q] = to_lower ? 1 : 2;
+            }
+            // tableau pivot on (row l, column e)
+            const float inv = __fdividef(1.f, piv);  // fast reciprocal: |piv| > kPTol
+            bool isl[kRows];
+#pragma unroll
+            for (int r = 0; r < kRows; ++r) isl[r] = r == l;
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                float tl = s.T[q][0];
+#pragma unroll
+                for (int r = 1; r < kRows; ++r) tl = isl[r] ? s.T[q][r] : tl;
+                const float pa = __fmul_rn(tl, inv);
+#pragma unroll
+                for (int r = 0; r <= kRows; ++r) {
+                    const float u = __fmaf_rn(-col[r], pa, s.T[q][r]);
+                    s.T[q][r] = (r < kRows && isl[r]) ? pa : u;
+                }
+            }
+            __syncwarp();  // every lane has read buf before it is written again
         }
-        const bool tie = rk == rmin;
-        unsigned cand;
-        if (bland) {  // lowest basic-variable index among the tied rows
-            const unsigned bmin = __reduce_min_sync(kFull, tie ? (unsigned)s.basis : 0xffffffffu);
-            cand = __ballot_sync(kFull, tie && (unsigned)s.basis == bmin);
-        } else {      // largest pivot entry among the tied rows
-            const unsigned mk = tie ? fkey(mycol) : 0u;
-            const unsigned mmax = __reduce_max_sync(kFull, mk);
-            cand = __ballot_sync(kFull, tie && mk == mmax);
+        if (it == kMaxPivots) flags |= CF_DEV_LP_PIVOT_CAP;
+        ++n_lp;
+        if (!unbounded) {  // s_j = the sum of contact j's basic values (nonbasic c' sit at 0)
+            float part = (lane < kRows && s.beta >= c0 && s.beta < c1) ? s.v : 0.f;
+            part += __shfl_xor_sync(kFull, part, 4);
+            part += __shfl_xor_sync(kFull, part, 2);
+            part += __shfl_xor_sync(kFull, part, 1);
+            best_s = fmaxf(best_s, __shfl_sync(kFull, part, 0));
+            if (best_s >= 1.f / kZeroExit) break;
         }
-        const int l = __ffs(cand) - 1;
-        degenerate = rmin == kzero ? degenerate + 1 : 0;
-        if (degenerate >= kDegenerateToBland) bland = true;
-        pivot(s, mycol, l, e, lane, buf);
-        ++npiv;
     }
-    if (it == kMaxPivots) flags |= CF_DEV_LP_PIVOT_CAP;
-    const float z = -__shfl_sync(kFull, s.rhs, 13);
-    return fmaxf(z, 0.f);
+    if (unbounded) return 0.f;
+    return best_s > 0.f ? __fdiv_rn(1.f, best_s) : INFINITY;
 }
 
 // MULTI: global tuple u belongs to object d with tuple0[d] <= u < tuple0[d + 1]
 // (all objects of one launch share k and K); each warp keeps its current
 // object's arguments in shared memory.
-template <bool MULTI>
+template <bool MULTI, int NS>
 __global__ void __launch_bounds__(kScoreThreads, 3) k_score_tuples(const ScoreArgs a1, const ScoreArgs *descs,
                                                                     const long long *tuple0, int n_desc,
                                                                     unsigned total) {
@@ -426,14 +477,7 @@ __global__ void __launch_bounds__(kScoreThreads, 3) k_score_tuples(const ScoreAr
                     wv[4] = (rz * ex - rx * ez) * a.inv_rho;
                     wv[5] = (rx * ey - ry * ex) * a.inv_rho;
                 }
-                for (int j = 0; j < k; ++j) {
-                    int np = 0;
-                    const float tj = solve_lp(wv, colA, ci, j, lane, buf, np, flags);
-                    n_piv += np;
-                    ++n_lp;
-                    margin = fminf(margin, tj);
-                    if (margin <= kZeroExit) break;
-                }
+                margin = closure_margin<NS>(wv, k, K, lane, buf, n_piv, n_lp, flags);
                 ++n_tup;
             }
             if (lane == 0) {
@@ -475,21 +519,13 @@ __device__ __forceinline__ void wrench_column(const ScoreArgs &a, int x, float e
 
 // Closure margin of the tuple whose contact d is point id_d (min over j of LP_j,
 // stopping at a zero), computed by the whole warp.
+template <int NS>
 __device__ __forceinline__ float tuple_margin(const ScoreArgs &a, int id0, int id1, int id2, int id3, int k, bool colA,
                                               int ci, float ec, float es, int lane, float *buf,
                                               unsigned long long &n_piv, unsigned long long &n_lp, unsigned &flags) {
     float wv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (colA) wrench_column(a, ci == 0 ? id0 : ci == 1 ? id1 : ci == 2 ? id2 : id3, ec, es, wv);
-    float margin = INFINITY;
-    for (int j = 0; j < k; ++j) {
-        int np = 0;
-        const float tj = solve_lp(wv, colA, ci, j, lane, buf, np, flags);
-        n_piv += np;
-        ++n_lp;
-        margin = fminf(margin, tj);
-        if (margin <= kZeroExit) break;
-    }
-    return margin;
+    return closure_margin<NS>(wv, k, a.K, lane, buf, n_piv, n_lp, flags);
 }
 
 struct OptArgs {
@@ -504,7 +540,7 @@ struct OptArgs {
 // warp reduction per candidate), then the candidates in order replace the best
 // so far when their margin is lower by more than the relative min_gain (margins
 // <= zero_tol count as 0), so the margin never increases.
-template <int NI>
+template <int NI, int NS>
 __global__ void __launch_bounds__(kOptThreads) k_optimize_tuples(const ScoreArgs a, const OptArgs o, unsigned total) {
     __shared__ __align__(16) float s_buf[kOptWarps][16];
     __shared__ float s_cand[kOptWarps][NI][3];
@@ -533,7 +569,7 @@ __global__ void __launch_bounds__(kOptThreads) k_optimize_tuples(const ScoreArgs
         }
         float J = INFINITY;
         if (valid) {
-            J = tuple_margin(a, id[0], id[1], id[2], id[3], k, colA, ci, ec, es, lane, buf, n_piv, n_lp, flags);
+            J = tuple_margin<NS>(a, id[0], id[1], id[2], id[3], k, colA, ci, ec, es, lane, buf, n_piv, n_lp, flags);
             float Jc = J <= o.zero_tol ? 0.f : J;
             const uint32_t pid = (uint32_t)pose + a.pose_base;
             for (int it = 0; it < o.n_outer && Jc > 0.f; ++it) {
@@ -609,7 +645,7 @@ __global__ void __launch_bounds__(kOptThreads) k_optimize_tuples(const ScoreArgs
                     for (unsigned m = todo; m; m &= m - 1) {
                         const int c = __ffs(m) - 1;
                         const int xc = __shfl_sync(kFull, cand_mine, c);
-                        const float Jt = tuple_margin(a, i == 0 ? xc : id[0], i == 1 ? xc : id[1],
+                        const float Jt = tuple_margin<NS>(a, i == 0 ? xc : id[0], i == 1 ? xc : id[1],
                                                       i == 2 ? xc : id[2], i == 3 ? xc : id[3], k, colA, ci, ec, es,
                                                       lane, buf, n_piv, n_lp, flags);
                         const float Jtc = Jt <= o.zero_tol ? 0.f : Jt;
@@ -662,14 +698,17 @@ cudaError_t launch_sample(const ScoreArgs &a, cudaStream_t st) {
 }
 
 namespace {
-template <bool MULTI>
+// slots per lane of the scaled LP: kK + 6 columns fit one slot when kK <= 26
+inline int lp_slots(int k, int K) { return k * K + kRows <= 32 ? 1 : 2; }
+
+template <bool MULTI, int NS>
 cudaError_t launch_score_grid(const ScoreArgs &a1, const ScoreArgs *descs, const long long *tuple0, int n_desc,
                               long long total, cudaStream_t st) {
     cudaError_t err;
     int dev = 0, sms = 0, per_sm = 0;
     if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
     if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
-    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_score_tuples<MULTI>, kScoreThreads, 0)) !=
+    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_score_tuples<MULTI, NS>, kScoreThreads, 0)) !=
         cudaSuccess)
         return err;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
@@ -677,7 +716,7 @@ cudaError_t launch_score_grid(const ScoreArgs &a1, const ScoreArgs *descs, const
     if (a1.bpsm > 0) per_sm = std::min(per_sm, a1.bpsm);
     const long long warps_needed = (total + a1.batch - 1) / a1.batch;
     const int grid = (int)std::min<long long>((long long)sms * per_sm, (warps_needed + kScoreWarps - 1) / kScoreWarps);
-    k_score_tuples<MULTI><<<grid, kScoreThreads, 0, st>>>(a1, descs, tuple0, n_desc, (unsigned)total);
+    k_score_tuples<MULTI, NS><<<grid, kScoreThreads, 0, st>>>(a1, descs, tuple0, n_desc, (unsigned)total);
     return cudaGetLastError();
 }
 }  // namespace
@@ -686,7 +725,8 @@ cudaError_t launch_score(const ScoreArgs &a, cudaStream_t st) {
     if (a.P <= 0) return cudaSuccess;
     cudaError_t err;
     if (!a.tuples_given && (err = launch_sample(a, st)) != cudaSuccess) return err;
-    return launch_score_grid<false>(a, nullptr, nullptr, 0, (long long)a.P * a.T, st);
+    return lp_slots(a.k, a.K) == 1 ? launch_score_grid<false, 1>(a, nullptr, nullptr, 0, (long long)a.P * a.T, st)
+                                   : launch_score_grid<false, 2>(a, nullptr, nullptr, 0, (long long)a.P * a.T, st);
 }
 
 cudaError_t launch_optimize(const ScoreArgs &a, int n_outer, int n_inner, float sigma, float zero_tol,
@@ -700,10 +740,15 @@ cudaError_t launch_optimize(const ScoreArgs &a, int n_outer, int n_inner, float 
     if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
     const long long want = (total + kOptWarps - 1) / kOptWarps;
     const int grid = (int)std::min<long long>((long long)sms * 16, want);
+    const bool one = lp_slots(a.k, a.K) == 1;
     switch (n_inner) {
-        case 4: k_optimize_tuples<4><<<grid, kOptThreads, 0, st>>>(a, o, (unsigned)total); break;
-        case 8: k_optimize_tuples<8><<<grid, kOptThreads, 0, st>>>(a, o, (unsigned)total); break;
-        case 16: k_optimize_tuples<16><<<grid, kOptThreads, 0, st>>>(a, o, (unsigned)total); break;
+#define CF_OPT(NI)                                                                                        \
+    case NI:                                                                                              \
+        if (one) k_optimize_tuples<NI, 1><<<grid, kOptThreads, 0, st>>>(a, o, (unsigned)total);           \
+        else k_optimize_tuples<NI, 2><<<grid, kOptThreads, 0, st>>>(a, o, (unsigned)total);               \
+        break;
+        CF_OPT(4) CF_OPT(8) CF_OPT(16)
+#undef CF_OPT
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -726,7 +771,9 @@ cudaError_t launch_sample_batch(const ScoreArgs *d_descs, const long long *d_pos
 cudaError_t launch_score_batch(const ScoreArgs &launch, const ScoreArgs *d_descs, const long long *d_tuple0, int n_desc,
                                long long total_tuples, cudaStream_t st) {
     if (total_tuples <= 0) return cudaSuccess;
-    return launch_score_grid<true>(launch, d_descs, d_tuple0, n_desc, total_tuples, st);
+    return lp_slots(launch.k, launch.K) == 1
+               ? launch_score_grid<true, 1>(launch, d_descs, d_tuple0, n_desc, total_tuples, st)
+               : launch_score_grid<true, 2>(launch, d_descs, d_tuple0, n_desc, total_tuples, st);
 }
 
 }  // namespace cf
