@@ -199,8 +199,8 @@ __device__ __forceinline__ int warp_argmin_lane(float v) {
 // subproblems differ only in the objective, so LP_{j+1} starts from LP_j's
 // optimal basis.  Bounded-variable primal simplex: Dantzig pricing, ratio test
 // over the basic variables' bounds and the entering variable's own box (a bound
-// flip), the largest pivot entry among tied rows, Bland's rule after a run of
-// degenerate pivots.
+// flip), the largest pivot entry among degenerate rows (ratio 0) and the lowest
+// row among other exact ties, Bland's rule after a run of degenerate pivots.
 //
 // Warp layout (NS slots per lane): the column with id c' = 0..kK-1 (contact
 // c / K, edge c % K) is slot 0 of lane c; the y_r columns are slot 0 of lane
@@ -245,6 +245,7 @@ __device__ float closure_margin(const float (&w)[6], int k, int K, int lane, flo
 
     const unsigned kinf = fkey(INFINITY);
     const unsigned kzero = fkey(0.f);
+    unsigned npv = 0;
     float best_s = 0.f;
     bool unbounded = false;
     for (int j = 0; j < k && !unbounded; ++j) {
@@ -319,7 +320,9 @@ __device__ float closure_margin(const float (&w)[6], int k, int K, int lane, flo
             } else if (lane == kRows && ey) {
                 theta = 2.f;
             }
-            const unsigned rk = fkey(theta);
+            // degenerate rows (theta = 0) key below every positive ratio, by decreasing |pivot entry|
+            const unsigned rk =
+                (!bland && theta == 0.f) ? (~__float_as_uint(fabsf(alpha)) & 0x7fffffffu) : fkey(theta);
             const unsigned rmin = __reduce_min_sync(kFull, rk);
             if (rmin == kinf) {  // s_j unbounded: LP_j = 0
                 unbounded = true;
@@ -332,16 +335,14 @@ __device__ float closure_margin(const float (&w)[6], int k, int K, int lane, flo
                 const unsigned bk = !tie ? kNoKey : (lane == kRows ? 0u : (unsigned)s.beta + 1u);
                 const unsigned bmin = __reduce_min_sync(kFull, bk);
                 cand = __ballot_sync(kFull, tie && bk == bmin);
-            } else {      // a bound flip first, then the largest pivot entry
-                const unsigned mk = !tie ? 0u : (lane == kRows ? kinf : fkey(fabsf(alpha)));
-                const unsigned mmax = __reduce_max_sync(kFull, mk);
-                cand = __ballot_sync(kFull, tie && mk == mmax);
+            } else {
+                cand = __ballot_sync(kFull, tie);
             }
             const int l = __ffs(cand) - 1;
             const float th = __shfl_sync(kFull, theta, l);
-            degenerate = rmin == kzero ? degenerate + 1 : 0;
+            degenerate = rmin <= kzero ? degenerate + 1 : 0;
             if (degenerate >= kDegenerateToBland) bland = true;
-            ++n_piv;
+            ++npv;
             if (l == kRows) {  // bound flip: no basis change
                 if (lane < kRows) s.v = __fmaf_rn(-alpha, th, s.v);
 #pragma unroll
@@ -398,6 +399,7 @@ __device__ float closure_margin(const float (&w)[6], int k, int K, int lane, flo
             if (best_s >= 1.f / kZeroExit) break;
         }
     }
+    n_piv += npv;
     if (unbounded) return 0.f;
     return best_s > 0.f ? __fdiv_rn(1.f, best_s) : INFINITY;
 }
