@@ -27,7 +27,8 @@
  *
  * Precision: kinematics and geometry are FP64.  The integer codes that
  * the GPU decides in FP32 (voxel cell, normal bin) are decided here in the same
- * precision, from FP32-rounded link transforms with single-rounding fused
+ * precision, from link transforms evaluated in FP32 (joint sin / cos in FP64
+ * rounded to FP32, every chain operation rounded) and single-rounding fused
  * multiply-adds in the natural component order; an FP64 evaluation of the same
  * codes is kept beside them to count the entries that sit within a tolerance
  * band of a cell or bin boundary (the "ambiguous" entries).
@@ -111,6 +112,39 @@ void orc_fk_links(int J, const float *base12, const float *axis, const float *of
     }
 }
 
+/* Link frames in the decision precision: sin and cos of each joint angle in
+ * FP64 rounded to FP32, then the same chain as orc_fk_links in FP32 with every
+ * operation rounded (translation t + R o as nested fmaf in component order;
+ * Rodrigues' Q = c I + s [a]x + v a a^T with v = 1 - c; R Q as nested fmaf). */
+void orc_fk_links32(int J, const float *base12, const float *axis, const float *offset,
+                    const double *q, float *Rout, float *tout) {
+    float R[9] = {base12[0], base12[1], base12[2], base12[4], base12[5], base12[6],
+                  base12[8], base12[9], base12[10]};
+    float t[3] = {base12[3], base12[7], base12[11]};
+    for (int j = 0; j < J; ++j) {
+        if (j > 0) {
+            const float *o = offset + 3 * (j - 1);
+            for (int r = 0; r < 3; ++r)
+                t[r] = fmaf(R[3 * r + 2], o[2], fmaf(R[3 * r + 1], o[1], fmaf(R[3 * r], o[0], t[r])));
+        }
+        const float ax = axis[3 * j + 0], ay = axis[3 * j + 1], az = axis[3 * j + 2];
+        const float s = (float)sin(q[j]), c = (float)cos(q[j]);
+        const float v = 1.0f - c;
+        const float xs = ax * s, ys = ay * s, zs = az * s;
+        const float xy = (ax * ay) * v, xz = (ax * az) * v, yz = (ay * az) * v;
+        const float Q[9] = {fmaf(ax * ax, v, c), xy - zs, xz + ys,
+                            xy + zs, fmaf(ay * ay, v, c), yz - xs,
+                            xz - ys, yz + xs, fmaf(az * az, v, c)};
+        float Rn[9];
+        for (int r = 0; r < 3; ++r)
+            for (int cc = 0; cc < 3; ++cc)
+                Rn[3 * r + cc] = fmaf(R[3 * r + 2], Q[6 + cc], fmaf(R[3 * r + 1], Q[3 + cc], R[3 * r] * Q[cc]));
+        memcpy(R, Rn, sizeof R);
+        memcpy(Rout + 9 * j, R, sizeof R);
+        memcpy(tout + 3 * j, t, sizeof t);
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* FP32 decision arithmetic: single-rounding fmaf in component order x, y, z. */
 /* ------------------------------------------------------------------------ */
@@ -145,7 +179,7 @@ static inline int bin32(const float m[3], int B, const float *dirs) {
 }
 
 /* Contact vectors of one (finger, sample): p32/n32 are the FP32 decision values
- * (FP32-rounded link transforms, fmaf transform), p64/n64 the FP64 values.
+ * (orc_fk_links32 frames, fmaf transform), p64/n64 the FP64 values.
  * Any output pointer may be NULL. */
 void orc_contact_vectors(int J, int M, const float *base12, const float *axis, const float *offset,
                          const float *surf_p, const float *surf_n, const int32_t *surf_link,
@@ -153,8 +187,7 @@ void orc_contact_vectors(int J, int M, const float *base12, const float *axis, c
     double R[8 * 9], t[8 * 3];
     orc_fk_links(J, base12, axis, offset, q, R, t);
     float Rf[8 * 9], tf[8 * 3];
-    for (int i = 0; i < J * 9; ++i) Rf[i] = (float)R[i];
-    for (int i = 0; i < J * 3; ++i) tf[i] = (float)t[i];
+    orc_fk_links32(J, base12, axis, offset, q, Rf, tf);
     for (int m = 0; m < M; ++m) {
         int l = surf_link[m];
         const float *ps = surf_p + 3 * m, *ns = surf_n + 3 * m;

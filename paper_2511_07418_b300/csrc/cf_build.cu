@@ -12,8 +12,9 @@
 // The table is one box of cells over all fingers; a cell's record holds the
 // bin sets of all fingers (finger f: bits (f % fpw) * bits .. of word f / fpw).
 //
-// Thread per (finger, joint sample).  The kinematic chain is evaluated in FP64
-// and rounded to FP32 once per link; each surface point is then transformed
+// Thread per (finger, joint sample).  The kinematic chain is evaluated in FP32
+// with explicitly rounded operations (joint sin / cos from FP64, rounded once);
+// each surface point is then transformed
 // with single-rounding FP32 FMAs (component order x, y, z).  Two passes:
 // k_fk_cell_bounds evaluates the chain, stores the FP32 link frames
 // ([F][J][12][S], coalesced over samples) and reduces the per-finger cell AABB
@@ -32,46 +33,52 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// Link frames of finger f for sample s: FP64 chain, FP32 result per link.
+// Link frames of finger f for sample s: the chain base * prod_j [Trans(o_j) Rot(a_j, q_j)]
+// in FP32 with explicitly rounded operations (no contraction left to the
+// compiler), so every build evaluates it bit for bit the same way; the joint's
+// sin and cos come from FP64 and are rounded to FP32 once.
 template <int J>
 __device__ __forceinline__ void link_frames(const HandDev &h, int f, const float *__restrict__ q, int S, int s,
                                             float R[J][9], float t[J][3]) {
     const float *b = h.base + 12 * f;
-    double Rd[9] = {b[0], b[1], b[2], b[4], b[5], b[6], b[8], b[9], b[10]};
-    double td[3] = {b[3], b[7], b[11]};
+    float Rc[9] = {b[0], b[1], b[2], b[4], b[5], b[6], b[8], b[9], b[10]};
+    float tc[3] = {b[3], b[7], b[11]};
 #pragma unroll
     for (int j = 0; j < J; ++j) {
         if (j > 0) {
             const float *o = h.offset + 3 * (f * J + j - 1);
-            const double o0 = o[0], o1 = o[1], o2 = o[2];
-            const double t0 = td[0] + Rd[0] * o0 + Rd[1] * o1 + Rd[2] * o2;
-            const double t1 = td[1] + Rd[3] * o0 + Rd[4] * o1 + Rd[5] * o2;
-            const double t2 = td[2] + Rd[6] * o0 + Rd[7] * o1 + Rd[8] * o2;
-            td[0] = t0; td[1] = t1; td[2] = t2;
+            const float o0 = o[0], o1 = o[1], o2 = o[2];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+                tc[r] = __fmaf_rn(Rc[3 * r + 2], o2, __fmaf_rn(Rc[3 * r + 1], o1, __fmaf_rn(Rc[3 * r], o0, tc[r])));
         }
         const float *a = h.axis + 3 * (f * J + j);
-        const double ax = a[0], ay = a[1], az = a[2];
-        double sq, cq;
-        sincos((double)q[((size_t)f * J + j) * S + s], &sq, &cq);
-        const double v = 1.0 - cq;
+        const float ax = a[0], ay = a[1], az = a[2];
+        double sd, cd;  // sin and cos in FP64, rounded once: the FP32 values are those of a correctly
+        sincos((double)q[((size_t)f * J + j) * S + s], &sd, &cd);  // rounded sin / cos in all but rare ties
+        const float sq = (float)sd, cq = (float)cd;
+        const float v = __fsub_rn(1.f, cq);
         // axis-angle rotation (Rodrigues)
-        const double Q[9] = {cq + ax * ax * v,      ax * ay * v - az * sq, ax * az * v + ay * sq,
-                             ay * ax * v + az * sq, cq + ay * ay * v,      ay * az * v - ax * sq,
-                             az * ax * v - ay * sq, az * ay * v + ax * sq, cq + az * az * v};
-        double Rn[9];
+        const float xs = __fmul_rn(ax, sq), ys = __fmul_rn(ay, sq), zs = __fmul_rn(az, sq);
+        const float xy = __fmul_rn(__fmul_rn(ax, ay), v), xz = __fmul_rn(__fmul_rn(ax, az), v),
+                    yz = __fmul_rn(__fmul_rn(ay, az), v);
+        const float Q[9] = {__fmaf_rn(__fmul_rn(ax, ax), v, cq), __fsub_rn(xy, zs), __fadd_rn(xz, ys),
+                            __fadd_rn(xy, zs), __fmaf_rn(__fmul_rn(ay, ay), v, cq), __fsub_rn(yz, xs),
+                            __fsub_rn(xz, ys), __fadd_rn(yz, xs), __fmaf_rn(__fmul_rn(az, az), v, cq)};
+        float Rn[9];
 #pragma unroll
         for (int r = 0; r < 3; ++r)
 #pragma unroll
             for (int c = 0; c < 3; ++c)
-                Rn[3 * r + c] = Rd[3 * r] * Q[c] + Rd[3 * r + 1] * Q[3 + c] + Rd[3 * r + 2] * Q[6 + c];
+                Rn[3 * r + c] = __fmaf_rn(Rc[3 * r + 2], Q[6 + c], __fmaf_rn(Rc[3 * r + 1], Q[3 + c], __fmul_rn(Rc[3 * r], Q[c])));
 #pragma unroll
         for (int e = 0; e < 9; ++e) {
-            Rd[e] = Rn[e];
-            R[j][e] = (float)Rn[e];
+            Rc[e] = Rn[e];
+            R[j][e] = Rn[e];
         }
-        t[j][0] = (float)td[0];
-        t[j][1] = (float)td[1];
-        t[j][2] = (float)td[2];
+        t[j][0] = tc[0];
+        t[j][1] = tc[1];
+        t[j][2] = tc[2];
     }
 }
 
@@ -158,37 +165,52 @@ __global__ void __launch_bounds__(kThreads) k_fk_bin(HandDev h, const float *__r
     const unsigned dx = (unsigned)g.dims[0], dy = (unsigned)g.dims[1], dz = (unsigned)g.dims[2];
     uint32_t *tab = table + f / g.fpw;
     const int shift = (f % g.fpw) * g.bits;
+    constexpr int kBatch = 4;  // table words loaded together, then the atomics they call for
 #pragma unroll
     for (int l = 0; l < J; ++l) {
-        for (int m = s_lb[l]; m < s_lb[l + 1]; ++m) {
-            const float *sp = s_surf + 8 * m;
-            const float x = xf_row(R[l][0], R[l][1], R[l][2], t[l][0], sp[0], sp[1], sp[2]);
-            const float y = xf_row(R[l][3], R[l][4], R[l][5], t[l][1], sp[0], sp[1], sp[2]);
-            const float z = xf_row(R[l][6], R[l][7], R[l][8], t[l][2], sp[0], sp[1], sp[2]);
-            const float nx = rot_row(R[l][0], R[l][1], R[l][2], sp[3], sp[4], sp[5]);
-            const float ny = rot_row(R[l][3], R[l][4], R[l][5], sp[3], sp[4], sp[5]);
-            const float nz = rot_row(R[l][6], R[l][7], R[l][8], sp[3], sp[4], sp[5]);
-            int bin = 0;
-            if (CAND) {
-                bin = bin_by_candidates(nx, ny, nz, s_cand, s_dir);
-            } else {
-                float best = -INFINITY;
-                for (int b = 0; b < g.B; ++b) {
-                    const float sc =
-                        __fmaf_rn(g.dirs[b][2], nz, __fmaf_rn(g.dirs[b][1], ny, __fmul_rn(g.dirs[b][0], nx)));
-                    if (sc > best) { best = sc; bin = b; }
+        const int me = s_lb[l + 1];
+        for (int m0 = s_lb[l]; m0 < me; m0 += kBatch) {
+            uint32_t *wp[kBatch];
+            uint32_t bit[kBatch];
+#pragma unroll
+            for (int i = 0; i < kBatch; ++i) {
+                wp[i] = nullptr;
+                bit[i] = 0u;
+                if (m0 + i >= me) continue;
+                const float *sp = s_surf + 8 * (m0 + i);
+                const float x = xf_row(R[l][0], R[l][1], R[l][2], t[l][0], sp[0], sp[1], sp[2]);
+                const float y = xf_row(R[l][3], R[l][4], R[l][5], t[l][1], sp[0], sp[1], sp[2]);
+                const float z = xf_row(R[l][6], R[l][7], R[l][8], t[l][2], sp[0], sp[1], sp[2]);
+                const float nx = rot_row(R[l][0], R[l][1], R[l][2], sp[3], sp[4], sp[5]);
+                const float ny = rot_row(R[l][3], R[l][4], R[l][5], sp[3], sp[4], sp[5]);
+                const float nz = rot_row(R[l][6], R[l][7], R[l][8], sp[3], sp[4], sp[5]);
+                int bin = 0;
+                if (CAND) {
+                    bin = bin_by_candidates(nx, ny, nz, s_cand, s_dir);
+                } else {
+                    float best = -INFINITY;
+                    for (int b = 0; b < g.B; ++b) {
+                        const float sc =
+                            __fmaf_rn(g.dirs[b][2], nz, __fmaf_rn(g.dirs[b][1], ny, __fmul_rn(g.dirs[b][0], nx)));
+                        if (sc > best) { best = sc; bin = b; }
+                    }
                 }
+                const unsigned ux = (unsigned)(cell_floor(x, g.inv_h, g.clamp) - lx);
+                const unsigned uy = (unsigned)(cell_floor(y, g.inv_h, g.clamp) - ly);
+                const unsigned uz = (unsigned)(cell_floor(z, g.inv_h, g.clamp) - lz);
+                if (ux >= dx || uy >= dy || uz >= dz) {  // cannot happen: extents come from the same arithmetic
+                    atomicOr(status, CF_DEV_BIN_RANGE);
+                    continue;
+                }
+                wp[i] = tab + (((size_t)uz * dy + uy) * dx + ux) * g.rw;
+                bit[i] = 1u << (shift + bin);
             }
-            const unsigned ux = (unsigned)(cell_floor(x, g.inv_h, g.clamp) - lx);
-            const unsigned uy = (unsigned)(cell_floor(y, g.inv_h, g.clamp) - ly);
-            const unsigned uz = (unsigned)(cell_floor(z, g.inv_h, g.clamp) - lz);
-            if (ux >= dx || uy >= dy || uz >= dz) {  // cannot happen: extents come from the same arithmetic
-                atomicOr(status, CF_DEV_BIN_RANGE);
-                continue;
-            }
-            uint32_t *word = tab + (((size_t)uz * dy + uy) * dx + ux) * g.rw;
-            const uint32_t bit = 1u << (shift + bin);
-            if (!(__ldcg(word) & bit)) atomicOr(word, bit);
+            uint32_t cur[kBatch];
+#pragma unroll
+            for (int i = 0; i < kBatch; ++i) cur[i] = wp[i] ? __ldcg(wp[i]) : 0u;
+#pragma unroll
+            for (int i = 0; i < kBatch; ++i)
+                if (wp[i] && !(cur[i] & bit[i])) atomicOr(wp[i], bit[i]);
         }
     }
 }
