@@ -314,6 +314,7 @@ struct ScoreArgs {
     unsigned long long *counters;  // [0] pivots, [1] LPs, [2] tuples
     int batch;                     // tuples per work-counter grab (launch-level)
     int bpsm;                      // scoring blocks per SM, 0 = as many as fit (launch-level)
+    unsigned long long *n_accept;  // optional: accepted tuples of the launch are added here
 };
 // k_sample_tuples (unless tuples_given) then k_score_tuples
 cudaError_t launch_score(const ScoreArgs &a, cudaStream_t st);

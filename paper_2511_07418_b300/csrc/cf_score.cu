@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(kScoreThreads, 3) k_score_tuples(const ScoreAr
     int cur = -1;
     long long cur0 = 0, cur1 = 0;
     unsigned long long n_piv = 0, n_lp = 0, n_tup = 0;
-    unsigned flags = 0;
+    unsigned flags = 0, n_acc = 0;
 
     for (;;) {
         unsigned u0 = 0;
@@ -485,6 +485,7 @@ __global__ void __launch_bounds__(kScoreThreads, 3) k_score_tuples(const ScoreAr
             if (lane == 0) {
                 a.margin[u] = margin;
                 a.accept[u] = (uint8_t)(margin <= a.eps);
+                n_acc += margin <= a.eps;
             }
         }
     }
@@ -493,6 +494,7 @@ __global__ void __launch_bounds__(kScoreThreads, 3) k_score_tuples(const ScoreAr
         atomicAdd(a1.counters + 1, n_lp);
         atomicAdd(a1.counters + 2, n_tup);
         if (flags) atomicOr(a1.status, flags);
+        if (a1.n_accept && n_acc) atomicAdd(a1.n_accept, (unsigned long long)n_acc);
     }
 }
 

@@ -236,6 +236,26 @@ def test_scoring_given_tuples_and_invalid_ids(cf):
     assert np.all(np.isinf(mar.cpu().numpy()[0, :3]))
 
 
+def test_plan_chunked_host_path_equals_device_path(cf):
+    """4,096 poses run in four pose chunks with overlapped copies: tuples,
+    margins, accepts and the device-side accept count equal those of the
+    device-resident path (one launch per kernel)."""
+    w = synth.workload("tiny_sphere", P=4096)
+    r = _gpu_path(cf, w)
+    plan = cf.Plan(w.hand.F, w.obj.N, w.P, r["prm"])
+    pin = lambda shape, dt: torch.empty(shape, dtype=dt).pin_memory().numpy()
+    soa_h, poses_h = pin((6, w.obj.N), torch.float32), pin((w.P, 12), torch.float32)
+    soa_h[:] = w.obj.soa()
+    poses_h[:] = w.poses
+    ht, hm, ha = pin((w.P, w.T, w.k), torch.int32), pin((w.P, w.T), torch.float32), pin((w.P, w.T), torch.uint8)
+    nacc = plan.run_host(r["field"], soa_h, poses_h, ht, hm, ha)
+    assert np.array_equal(ht, r["tuples"].cpu().numpy())
+    assert np.array_equal(hm, r["margin"].cpu().numpy())
+    assert np.array_equal(ha, r["accept"].cpu().numpy())
+    assert nacc == int(r["accept"].sum()) > 0
+    assert plan.run_host(r["field"], soa_h, poses_h) == nacc  # outputs optional, count still returned
+
+
 def test_closure_closed_forms_on_gpu(cf):
     """Antipodal pair on a sphere -> margin 0; a single axis-aligned contact
     (k = 1) -> margin 1 (Eq. GSWO with alpha_j = 1)."""
