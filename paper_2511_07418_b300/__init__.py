@@ -744,7 +744,7 @@ def get_tuning() -> dict:
     return {f: getattr(t, f) for f, _ in Tuning._fields_}
 
 
-def set_tuning(query_poses_per_block=8, score_tuples_per_grab=4, score_blocks_per_sm=0):
+def set_tuning(query_poses_per_block=4, score_tuples_per_grab=4, score_blocks_per_sm=0):
     _check(_cf_set_tuning(byref(Tuning(int(query_poses_per_block), int(score_tuples_per_grab),
                                        int(score_blocks_per_sm)))))
 

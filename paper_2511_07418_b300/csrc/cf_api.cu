@@ -55,7 +55,7 @@ DevState g_state[64];
 std::mutex g_tune_mu;
 Tuning g_tune[64];
 bool g_tune_set[64] = {};
-constexpr Tuning kDefaultTuning{8, 4, 0};
+constexpr Tuning kDefaultTuning{4, 4, 0};
 
 int device_state(DevState *out) {
     int dev = 0;
@@ -847,7 +847,7 @@ struct cf_batch {
     std::vector<FieldGeom> geoms;
     FieldGeom *d_geoms = nullptr;
     int launches = 0;
-    int ppb = 8;                        // query poses per block (the tuning at creation)
+    int ppb = 4;                        // query poses per block (the tuning at creation)
 };
 
 extern "C" int cf_batch_create(const cf_batch_item *items, int32_t n_items, cf_batch **out) {

@@ -88,7 +88,7 @@ struct cf_engine {
     void *d_round = nullptr;
     size_t round_bytes = 0;
     std::string worker_error;
-    Tuning tune{8, 4, 0};  // launch shapes (the tuning at creation)
+    Tuning tune{4, 4, 0};  // launch shapes (the tuning at creation)
 
     double now() const {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
