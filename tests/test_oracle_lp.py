@@ -191,3 +191,36 @@ def test_oracle_workload_margins_are_never_nan():
     mar, _, piv = oracle.score_tuples(soa, tup, w.mu, w.K, w.obj.centroid, w.obj.rho, w.eps)
     assert not np.isnan(mar).any()
     assert (piv >= 0).all()
+
+
+def test_scaled_box_form_gives_the_same_margin():
+    """The GPU solves LP_j in a scaled form: with c = t c', LP_j = 1 / s_j where
+    s_j = max sum_m c'_jm s.t. -1 <= (W c')_r <= 1, c' >= 0, and s_j unbounded
+    exactly when LP_j = 0.  Solved here with the library LP solver on random
+    tuples (both closing and non-closing), the reciprocal matches LP_j as
+    defined."""
+    from scipy.optimize import linprog
+    rng = np.random.default_rng(21)
+    n_zero = n_pos = 0
+    for rep in range(60):
+        k = 3 if rep % 3 else 2
+        K = 8
+        p = rng.normal(size=(k, 3)) * 0.03
+        n = -p / np.linalg.norm(p, axis=1, keepdims=True) + 0.6 * rng.normal(size=(k, 3))
+        n /= np.linalg.norm(n, axis=1, keepdims=True)
+        W = oracle.wrench_matrix(p, n, 0.5, K, np.zeros(3), 0.05)
+        for j in range(k):
+            t, _ = oracle.lp_subproblem(W, K, j)
+            cost = np.zeros(W.shape[1])
+            cost[j * K:(j + 1) * K] = -1.0  # maximise sum_m c'_jm
+            res = linprog(cost, A_ub=np.vstack([W, -W]), b_ub=np.ones(12), bounds=[(0, None)] * W.shape[1],
+                          method="highs")
+            if res.status == 3:  # unbounded
+                assert t <= 1e-9
+                n_zero += 1
+            else:
+                assert res.status == 0
+                s = -res.fun
+                assert s > 0 and abs(1.0 / s - t) <= 1e-9 * max(1.0, t)
+                n_pos += 1
+    assert n_zero > 0 and n_pos > 0
