@@ -9,10 +9,15 @@
 //      through one launch per query group (same finger count, slot bits and
 //      binning method), one sampling launch and one launch per score group
 //      (same k, K), exactly as a cf_batch does;
-//   3. results: the chunk's tuples, margins and accept flags come back; the
-//      accepted ones are appended to the request; a request that reached its
-//      grasp count or ran out of poses completes, frees its device state and
-//      its slot, and the next round admits whoever is waiting.
+//   3. results: a compaction kernel gathers every request's accepted tuples
+//      (pose, margin, point ids), in tuple order, into one contiguous run per
+//      request; two copies bring the runs' extents and the runs themselves
+//      back into page-locked memory, and they are appended to the requests; a
+//      request that reached its grasp count or ran out of poses completes,
+//      frees its device state and its slot, and the next round admits whoever
+//      is waiting.
+// Request arrays are copied at submission into page-locked blocks from a pool
+// the engine keeps, so admission uploads are plain DMA.
 // Tuple draws use the request's seed and the GLOBAL pose index (pose_base), so
 // a request's result is independent of the rounds it shares.
 #include <math.h>
@@ -23,6 +28,7 @@
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <thread>
 #include <vector>
@@ -37,7 +43,8 @@ struct EngReq {
     uint64_t id = 0;
     cf_request req{};
     const cf_field *fd = nullptr;
-    std::vector<float> soa, poses;
+    float *h_in = nullptr;  // page-locked: soa [6][n] then poses [n_poses][12]
+    size_t h_in_bytes = 0;
     int limit = 0;  // poses this request may use
     // device state
     void *d_block = nullptr;
@@ -48,15 +55,125 @@ struct EngReq {
     uint8_t *d_fingers = nullptr, *d_accept = nullptr;
     // progress
     int pose_next = 0, chunk = 0;
-    std::vector<int32_t> h_tuples;
-    std::vector<float> h_margin;
-    std::vector<uint8_t> h_accept;
+    unsigned rec_off = 0, rec_cnt = 0;  // this round's accepted records in the engine's host buffer
     std::vector<int32_t> res_pose, res_tuples;
     std::vector<float> res_margin;
     double t_submit = 0, t_admit = 0;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Page-locked host blocks in power-of-two size classes (>= 64 KiB), reused
+// across requests.
+struct PinnedPool {
+    std::mutex mu;
+    std::multimap<size_t, void *> free_blocks;
+    std::vector<std::pair<void *, size_t>> all;
+    static size_t size_class(size_t b) {
+        size_t c = (size_t)1 << 16;
+        while (c < b) c <<= 1;
+        return c;
+    }
+    // allocates on `dev` without changing the calling thread's current device
+    void *get(size_t bytes, int dev, size_t *cap) {
+        const size_t c = size_class(bytes);
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            auto it = free_blocks.find(c);
+            if (it != free_blocks.end()) {
+                void *p = it->second;
+                free_blocks.erase(it);
+                *cap = c;
+                return p;
+            }
+        }
+        int old = 0;
+        if (cudaGetDevice(&old) != cudaSuccess) return nullptr;
+        void *p = nullptr;
+        const bool sw = old != dev && cudaSetDevice(dev) == cudaSuccess;
+        const cudaError_t err = cudaHostAlloc(&p, c, cudaHostAllocPortable);
+        if (sw) cudaSetDevice(old);
+        if (err != cudaSuccess) return nullptr;
+        std::lock_guard<std::mutex> lk(mu);
+        all.emplace_back(p, c);
+        *cap = c;
+        return p;
+    }
+    void put(void *p, size_t cap) {
+        if (!p) return;
+        std::lock_guard<std::mutex> lk(mu);
+        free_blocks.emplace(cap, p);
+    }
+    ~PinnedPool() {
+        for (auto &b : all) cudaFreeHost(b.first);
+    }
+};
+
+// One accepted tuple as the engine returns it.
+struct AccRecord {
+    int32_t pose;
+    float margin;
+    int32_t t[CF_MAX_K];
+};
+
+struct CompactDesc {
+    const uint8_t *accept;
+    const int32_t *tuples;
+    const float *margin;
+    int nt, T, k, pose_base;
+};
+
+constexpr int kCompactThreads = 256;
+constexpr int kCompactWarps = kCompactThreads / 32;
+
+// Block i gathers request i's accepted tuples, in tuple order, into one
+// contiguous run of `out`: the run's start is reserved with one atomic on the
+// round's cursor; the start and length are reported in off[i] / cnt[i].
+__global__ void __launch_bounds__(kCompactThreads) k_compact_accepted(const CompactDesc *descs, AccRecord *out,
+                                                                     unsigned *cursor, unsigned *off,
+                                                                     unsigned *cnt) {
+    __shared__ unsigned s_warp[kCompactWarps];
+    __shared__ unsigned s_base;
+    const CompactDesc d = descs[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned c = 0;
+    for (int u = threadIdx.x; u < d.nt; u += kCompactThreads) c += d.accept[u] != 0;
+    c = __reduce_add_sync(0xffffffffu, c);
+    if (lane == 0) s_warp[warp] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned tot = 0;
+        for (int w = 0; w < kCompactWarps; ++w) tot += s_warp[w];
+        s_base = atomicAdd(cursor, tot);
+        off[blockIdx.x] = s_base;
+        cnt[blockIdx.x] = tot;
+    }
+    __syncthreads();
+    unsigned run = s_base;
+    for (int t0 = 0; t0 < d.nt; t0 += kCompactThreads) {
+        const int u = t0 + threadIdx.x;
+        const bool a = u < d.nt && d.accept[u] != 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, a);
+        __syncthreads();  // the previous tile's counts have been read
+        if (lane == 0) s_warp[warp] = __popc(bal);
+        __syncthreads();
+        unsigned before = 0, tile = 0;
+        for (int w = 0; w < kCompactWarps; ++w) {
+            const unsigned x = s_warp[w];
+            before += w < warp ? x : 0u;
+            tile += x;
+        }
+        if (a) {
+            AccRecord r;
+            r.pose = d.pose_base + u / d.T;
+            r.margin = d.margin[u];
+#pragma unroll
+            for (int q = 0; q < CF_MAX_K; ++q) r.t[q] = q < d.k ? d.tuples[(size_t)u * d.k + q] : -1;
+            out[run + before + __popc(bal & ((1u << lane) - 1u))] = r;
+        }
+        run += tile;
+    }
+}
 
 size_t state_bytes(const cf_request &r, int F, int chunk) {
     const size_t W = (size_t)(r.n + 31) / 32, T = r.prm.n_tuples, k = r.prm.k;
@@ -84,9 +201,17 @@ struct cf_engine {
     uint64_t next_id = 1;
     cf_engine_stats stats{};
     std::chrono::steady_clock::time_point t0;
-    // round scratch (device): geoms | query descs | score descs | all descs | prefixes | counters
+    // round scratch (device): geoms | query descs | score descs | all descs | prefixes | counters |
+    // compaction descs | cursor, offsets, counts
     void *d_round = nullptr;
     size_t round_bytes = 0;
+    void *d_rec = nullptr;  // accepted records of a round (capacity: every tuple of the round)
+    size_t rec_bytes = 0;
+    AccRecord *h_rec = nullptr;  // page-locked copy of the used part
+    size_t h_rec_bytes = 0;
+    unsigned *h_meta = nullptr;  // page-locked: cursor, offsets [n], counts [n]
+    size_t h_meta_bytes = 0;
+    PinnedPool pinned;
     std::string worker_error;
     Tuning tune{4, 4, 0};  // launch shapes (the tuning at creation)
 
@@ -119,6 +244,7 @@ void finish(cf_engine *e, EngReq *r, int status, bool partial) {
         memcpy(res.margin, r->res_margin.data(), sizeof(float) * res.n_accepted);
     }
     if (r->d_block) cudaFreeAsync(r->d_block, e->st);
+    e->pinned.put(r->h_in, r->h_in_bytes);  // its upload was followed by a stream wait
     std::lock_guard<std::mutex> lk(e->mu);
     if (r->d_block) e->stats.bytes_in_use -= (int64_t)r->bytes;
     e->done.push_back(res);
@@ -142,14 +268,11 @@ int admit_one(cf_engine *e, EngReq *r) {
     r->d_fingers = (uint8_t *)p; p += align256(c * T * k);
     r->d_margin = (float *)p; p += align256(sizeof(float) * c * T);
     r->d_accept = (uint8_t *)p;
-    if (q.n > 0) CF_TRY(cudaMemcpyAsync(r->d_soa, r->soa.data(), sizeof(float) * 6 * q.n, cudaMemcpyHostToDevice, e->st),
+    if (q.n > 0) CF_TRY(cudaMemcpyAsync(r->d_soa, r->h_in, sizeof(float) * 6 * q.n, cudaMemcpyHostToDevice, e->st),
                         "upload points");
     if (q.n_poses > 0)
-        CF_TRY(cudaMemcpyAsync(r->d_poses, r->poses.data(), sizeof(float) * 12 * (size_t)q.n_poses,
+        CF_TRY(cudaMemcpyAsync(r->d_poses, r->h_in + 6 * (size_t)q.n, sizeof(float) * 12 * (size_t)q.n_poses,
                                cudaMemcpyHostToDevice, e->st), "upload poses");
-    r->h_tuples.resize(c * T * k);
-    r->h_margin.resize(c * T);
-    r->h_accept.resize(c * T);
     return CF_OK;
 }
 
@@ -242,7 +365,34 @@ int run_round(cf_engine *e, std::vector<EngReq *> &act) {
     const size_t o_p = align256(o_a + sizeof(ScoreArgs) * n);
     const size_t o_t = align256(o_p + sizeof(long long) * pose0.size());
     const size_t o_w = align256(o_t + sizeof(long long) * t0.size());
-    const size_t total = align256(o_w + sizeof(unsigned int) * skeys.size());
+    const size_t o_c = align256(o_w + sizeof(unsigned int) * skeys.size());
+    const size_t o_m = align256(o_c + sizeof(CompactDesc) * n);
+    const size_t meta_bytes = sizeof(unsigned) * (1 + 2 * (size_t)n);  // cursor, offsets, counts
+    const size_t total = align256(o_m + meta_bytes);
+    std::vector<CompactDesc> cd(n);
+    size_t rec_need = 0;
+    for (int i = 0; i < n; ++i) {
+        EngReq *r = act[i];
+        const int T = r->req.prm.n_tuples;
+        cd[i] = CompactDesc{r->d_accept, r->d_tuples, r->d_margin, r->chunk * T, T, r->req.prm.k, r->pose_next};
+        rec_need += (size_t)r->chunk * T;
+    }
+    rec_need *= sizeof(AccRecord);
+    if (rec_need > e->rec_bytes) {
+        if (e->d_rec) cudaFreeAsync(e->d_rec, e->st);
+        e->d_rec = nullptr;
+        e->rec_bytes = 0;
+        int rc = pool_alloc(&e->d_rec, 2 * rec_need, e->st, "alloc round records");
+        if (rc) return rc;
+        e->rec_bytes = 2 * rec_need;
+    }
+    if (meta_bytes > e->h_meta_bytes) {
+        if (e->h_meta) cudaFreeHost(e->h_meta);
+        e->h_meta = nullptr;
+        e->h_meta_bytes = 0;
+        CF_TRY(cudaHostAlloc((void **)&e->h_meta, 2 * meta_bytes, cudaHostAllocDefault), "alloc round meta");
+        e->h_meta_bytes = 2 * meta_bytes;
+    }
     if (total > e->round_bytes) {
         if (e->d_round) cudaFreeAsync(e->d_round, e->st);
         e->d_round = nullptr;
@@ -257,6 +407,7 @@ int run_round(cf_engine *e, std::vector<EngReq *> &act) {
     memcpy(img.data() + o_a, sargs.data(), sizeof(ScoreArgs) * n);
     memcpy(img.data() + o_p, pose0.data(), sizeof(long long) * pose0.size());
     memcpy(img.data() + o_t, t0.data(), sizeof(long long) * t0.size());
+    memcpy(img.data() + o_c, cd.data(), sizeof(CompactDesc) * n);  // the meta region stays zero: cursor = 0
     char *base = (char *)e->d_round;
     CF_TRY(cudaMemcpyAsync(base, img.data(), total, cudaMemcpyHostToDevice, e->st), "upload round");
     const FieldGeom *d_geoms = (const FieldGeom *)(base + o_g);
@@ -278,15 +429,26 @@ int run_round(cf_engine *e, std::vector<EngReq *> &act) {
                                   s_n[g], s_tuples[g], e->st), "round score");
         ++launches;
     }
+    unsigned *d_meta = (unsigned *)(base + o_m);
+    k_compact_accepted<<<n, kCompactThreads, 0, e->st>>>((const CompactDesc *)(base + o_c), (AccRecord *)e->d_rec,
+                                                        d_meta, d_meta + 1, d_meta + 1 + n);
+    CF_TRY(cudaGetLastError(), "round compaction");
+    ++launches;
+    CF_TRY(cudaMemcpyAsync(e->h_meta, d_meta, meta_bytes, cudaMemcpyDeviceToHost, e->st), "download round extents");
+    CF_TRY(cudaStreamSynchronize(e->st), "round");
+    const size_t used = sizeof(AccRecord) * (size_t)e->h_meta[0];
+    if (used > e->h_rec_bytes) {
+        if (e->h_rec) cudaFreeHost(e->h_rec);
+        e->h_rec = nullptr;
+        e->h_rec_bytes = 0;
+        CF_TRY(cudaHostAlloc((void **)&e->h_rec, 2 * used, cudaHostAllocDefault), "alloc round records (host)");
+        e->h_rec_bytes = 2 * used;
+    }
+    if (used > 0)
+        CF_TRY(cudaMemcpyAsync(e->h_rec, e->d_rec, used, cudaMemcpyDeviceToHost, e->st), "download accepted records");
     for (int i = 0; i < n; ++i) {
-        EngReq *r = act[i];
-        const size_t nt = (size_t)r->chunk * r->req.prm.n_tuples;
-        if (nt == 0) continue;
-        CF_TRY(cudaMemcpyAsync(r->h_tuples.data(), r->d_tuples, sizeof(int32_t) * nt * r->req.prm.k,
-                               cudaMemcpyDeviceToHost, e->st), "download tuples");
-        CF_TRY(cudaMemcpyAsync(r->h_margin.data(), r->d_margin, sizeof(float) * nt, cudaMemcpyDeviceToHost, e->st),
-               "download margins");
-        CF_TRY(cudaMemcpyAsync(r->h_accept.data(), r->d_accept, nt, cudaMemcpyDeviceToHost, e->st), "download accept");
+        act[i]->rec_off = e->h_meta[1 + i];
+        act[i]->rec_cnt = e->h_meta[1 + n + i];
     }
     CF_TRY(cudaStreamSynchronize(e->st), "round");
     std::lock_guard<std::mutex> lk(e->mu);
@@ -331,6 +493,7 @@ void worker_main(cf_engine *e) {
         for (EngReq *r : act) {
             const int arc = admit_one(e, r);
             if (arc != CF_OK) {  // the request ends with the error; its budget share is returned by finish
+                cudaStreamSynchronize(e->st);  // no upload of its block may still be running
                 {
                     std::lock_guard<std::mutex> lk(e->mu);
                     e->active.erase(std::find(e->active.begin(), e->active.end(), r));
@@ -350,15 +513,13 @@ void worker_main(cf_engine *e) {
         for (EngReq *r : round) {
             bool done = rc != CF_OK;
             if (rc == CF_OK) {
-                const int T = r->req.prm.n_tuples, k = r->req.prm.k;
-                for (int i = 0; i < r->chunk; ++i)
-                    for (int t = 0; t < T; ++t) {
-                        const size_t u = (size_t)i * T + t;
-                        if (!r->h_accept[u]) continue;
-                        r->res_pose.push_back(r->pose_next + i);
-                        r->res_margin.push_back(r->h_margin[u]);
-                        for (int d = 0; d < k; ++d) r->res_tuples.push_back(r->h_tuples[u * k + d]);
-                    }
+                const int k = r->req.prm.k;
+                const AccRecord *rec = e->h_rec + r->rec_off;
+                for (unsigned a = 0; a < r->rec_cnt; ++a) {
+                    r->res_pose.push_back(rec[a].pose);
+                    r->res_margin.push_back(rec[a].margin);
+                    for (int d = 0; d < k; ++d) r->res_tuples.push_back(rec[a].t[d]);
+                }
                 r->pose_next += r->chunk;
                 done = (int)r->res_margin.size() >= r->req.n_grasps || r->pose_next >= r->limit;
             }
@@ -412,8 +573,14 @@ extern "C" int cf_engine_submit(cf_engine *e, const cf_request *q, uint64_t *id)
     EngReq *r = new EngReq();
     r->req = *q;
     r->fd = e->fields[q->field];
-    r->soa.assign(q->h_soa, q->h_soa + 6 * (size_t)q->n);
-    r->poses.assign(q->h_poses, q->h_poses + 12 * (size_t)q->n_poses);
+    const size_t in_bytes = sizeof(float) * (6 * (size_t)q->n + 12 * (size_t)q->n_poses);
+    r->h_in = (float *)e->pinned.get(in_bytes, e->dev, &r->h_in_bytes);
+    if (!r->h_in) {
+        delete r;
+        return fail(CF_ENOMEM, "page-locked host memory for a request of %zu bytes", in_bytes);
+    }
+    memcpy(r->h_in, q->h_soa, sizeof(float) * 6 * (size_t)q->n);
+    memcpy(r->h_in + 6 * (size_t)q->n, q->h_poses, sizeof(float) * 12 * (size_t)q->n_poses);
     r->req.h_soa = nullptr;
     r->req.h_poses = nullptr;
     r->limit = std::min(q->n_poses, e->prm.pose_cap);
@@ -490,8 +657,11 @@ extern "C" int cf_engine_destroy(cf_engine *e) {
     for (EngReq *r : e->queue) delete r;
     for (cf_result &r : e->done) cf_engine_result_free(&r);
     if (e->d_round) cudaFreeAsync(e->d_round, e->st);
+    if (e->d_rec) cudaFreeAsync(e->d_rec, e->st);
     cudaStreamSynchronize(e->st);
     cudaStreamDestroy(e->st);
-    delete e;
+    if (e->h_rec) cudaFreeHost(e->h_rec);
+    if (e->h_meta) cudaFreeHost(e->h_meta);
+    delete e;  // the page-locked request blocks go with the pool
     return CF_OK;
 }
