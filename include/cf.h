@@ -384,9 +384,11 @@ typedef struct cf_batch cf_batch;
 /* Plan a batch of objects (fields may differ): items are grouped by kernel
  * variant, and each group runs as ONE launch per step (domain query, tuple
  * sampling, LP scoring), its blocks and tuples spread over the group's
- * objects.  Results equal the per-object calls bit for bit.  The items'
- * buffers are used in place by every run.  Errors: CF_EINVAL, CF_ENOMEM,
- * CF_ECUDA. */
+ * objects.  An item whose query (>= 2^25 pose-point pairs) or sampling +
+ * scoring (>= 2^17 tuples) fills the GPU by itself runs that step with the
+ * single-object kernels instead, inside the same graph.  Results equal the
+ * per-object calls bit for bit.  The items' buffers are used in place by every
+ * run.  Errors: CF_EINVAL, CF_ENOMEM, CF_ECUDA. */
 int cf_batch_create(const cf_batch_item *items, int32_t n_items, cf_batch **out);
 
 /* Run the batch after the work already queued on `stream`.  The first run

@@ -848,7 +848,14 @@ struct cf_batch {
     FieldGeom *d_geoms = nullptr;
     int launches = 0;
     int ppb = 4;                        // query poses per block (the tuning at creation)
+    // items big enough to fill the GPU alone run the single-object kernels (inside the same graph)
+    std::vector<cf_batch_item> q_single;
+    std::vector<ScoreArgs> s_single;    // work counters in d_block
 };
+
+// an item's query / sampling + scoring fills the GPU by itself from these sizes on
+constexpr long long kBatchAlonePairs = 1LL << 25;
+constexpr long long kBatchAloneTuples = 1LL << 17;
 
 extern "C" int cf_batch_create(const cf_batch_item *items, int32_t n_items, cf_batch **out) {
     if (!items || !out || n_items < 1) return fail(CF_EINVAL, "items / out NULL or n_items < 1");
@@ -881,6 +888,13 @@ extern "C" int cf_batch_create(const cf_batch_item *items, int32_t n_items, cf_b
         }
         geom_of[i] = gi;
     }
+    std::vector<char> alone_q(n_items), alone_s(n_items);
+    for (int i = 0; i < n_items; ++i) {
+        alone_q[i] = (long long)items[i].n_poses * items[i].obj.n >= kBatchAlonePairs;
+        alone_s[i] = (long long)items[i].n_poses * sargs[i].T >= kBatchAloneTuples;
+        if (alone_q[i]) b->q_single.push_back(items[i]);
+        if (alone_s[i]) b->s_single.push_back(sargs[i]);
+    }
     // query groups: same F, bits and binning method
     auto qkey = [&](int i) {
         const FieldGeom &g = b->geoms[geom_of[i]];
@@ -906,7 +920,7 @@ extern "C" int cf_batch_create(const cf_batch_item *items, int32_t n_items, cf_b
         q_off.push_back(qdesc_all.size());
         int blocks = 0;
         for (int i = 0; i < n_items; ++i) {
-            if (qkey(i) != key || items[i].n_poses == 0) continue;
+            if (qkey(i) != key || items[i].n_poses == 0 || alone_q[i]) continue;
             QueryDesc d;
             memset(&d, 0, sizeof d);
             d.obj = items[i].obj;
@@ -924,29 +938,37 @@ extern "C" int cf_batch_create(const cf_batch_item *items, int32_t n_items, cf_b
         }
         qg.n = (int)(qdesc_all.size() - q_off.back());
         qg.blocks = blocks;
-        b->qgroups.push_back(qg);
+        if (qg.n > 0) b->qgroups.push_back(qg);
+        else q_off.pop_back();
     }
+    std::vector<ScoreArgs> sgrouped;  // items sampled and scored by the grouped launches
+    for (int i = 0; i < n_items; ++i)
+        if (!alone_s[i]) sgrouped.push_back(sargs[i]);
+    const int n_sg = (int)sgrouped.size();
+    pose0.assign(n_sg + 1, 0);
     size_t smem = 0;
-    for (int i = 0; i < n_items; ++i) {
-        pose0[i + 1] = pose0[i] + items[i].n_poses;
-        smem = std::max(smem, score_smem_bytes(sargs[i].F, sargs[i].W, sargs[i].T, sargs[i].k, true));
+    for (int i = 0; i < n_sg; ++i) {
+        pose0[i + 1] = pose0[i] + sgrouped[i].P;
+        smem = std::max(smem, score_smem_bytes(sgrouped[i].F, sgrouped[i].W, sgrouped[i].T, sgrouped[i].k, true));
     }
-    b->total_poses = pose0[n_items];
+    b->total_poses = pose0[n_sg];
     b->sample_smem = smem;
     for (int key : skeys) {
         cf_batch::SGroup sg{};
-        s_off.push_back(sdesc_all.size());
-        t_off.push_back(tuple0_all.size());
+        const size_t so = sdesc_all.size(), to = tuple0_all.size();
         long long tuples = 0;
-        for (int i = 0; i < n_items; ++i) {
-            if (sargs[i].k * 100 + sargs[i].K != key) continue;
+        for (int i = 0; i < n_sg; ++i) {
+            if (sgrouped[i].k * 100 + sgrouped[i].K != key) continue;
             tuple0_all.push_back(tuples);
-            tuples += (long long)sargs[i].P * sargs[i].T;
-            sdesc_all.push_back(sargs[i]);
-            sg.launch = sargs[i];
+            tuples += (long long)sgrouped[i].P * sgrouped[i].T;
+            sdesc_all.push_back(sgrouped[i]);
+            sg.launch = sgrouped[i];
         }
+        if (sdesc_all.size() == so) continue;  // every item of this (k, K) runs alone
+        s_off.push_back(so);
+        t_off.push_back(to);
         tuple0_all.push_back(tuples);
-        sg.n = (int)(sdesc_all.size() - s_off.back());
+        sg.n = (int)(sdesc_all.size() - so);
         sg.tuples = tuples;
         if (tuples >= (1LL << 32)) { delete b; return fail(CF_EINVAL, "a score group holds >= 2^32 tuples"); }
         b->sgroups.push_back(sg);
@@ -955,11 +977,11 @@ extern "C" int cf_batch_create(const cf_batch_item *items, int32_t n_items, cf_b
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t o_geom = 0, o_q = al(o_geom + sizeof(FieldGeom) * b->geoms.size());
     const size_t o_s = al(o_q + sizeof(QueryDesc) * std::max<size_t>(1, qdesc_all.size()));
-    const size_t o_sa = al(o_s + sizeof(ScoreArgs) * sdesc_all.size());
-    const size_t o_p0 = al(o_sa + sizeof(ScoreArgs) * n_items);
+    const size_t o_sa = al(o_s + sizeof(ScoreArgs) * std::max<size_t>(1, sdesc_all.size()));
+    const size_t o_p0 = al(o_sa + sizeof(ScoreArgs) * std::max(1, n_sg));
     const size_t o_t0 = al(o_p0 + sizeof(long long) * pose0.size());
-    const size_t o_w = al(o_t0 + sizeof(long long) * tuple0_all.size());
-    const size_t total = al(o_w + sizeof(unsigned int) * b->sgroups.size());
+    const size_t o_w = al(o_t0 + sizeof(long long) * std::max<size_t>(1, tuple0_all.size()));
+    const size_t total = al(o_w + sizeof(unsigned int) * (b->sgroups.size() + b->s_single.size()));
     CF_TRY(cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking), "stream");
     CF_TRY(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming), "event");
     CF_TRY(cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming), "event");
@@ -976,28 +998,38 @@ extern "C" int cf_batch_create(const cf_batch_item *items, int32_t n_items, cf_b
         b->sgroups[g].d_tuple0 = (long long *)(base + o_t0) + t_off[g];
         b->sgroups[g].launch.work = d_work + g;
     }
+    for (size_t i = 0; i < b->s_single.size(); ++i) b->s_single[i].work = d_work + b->sgroups.size() + i;
     std::vector<char> img(total, 0);
     memcpy(img.data() + o_geom, b->geoms.data(), sizeof(FieldGeom) * b->geoms.size());
     if (!qdesc_all.empty()) memcpy(img.data() + o_q, qdesc_all.data(), sizeof(QueryDesc) * qdesc_all.size());
-    memcpy(img.data() + o_s, sdesc_all.data(), sizeof(ScoreArgs) * sdesc_all.size());
-    memcpy(img.data() + o_sa, sargs.data(), sizeof(ScoreArgs) * n_items);
+    if (!sdesc_all.empty()) memcpy(img.data() + o_s, sdesc_all.data(), sizeof(ScoreArgs) * sdesc_all.size());
+    if (n_sg > 0) memcpy(img.data() + o_sa, sgrouped.data(), sizeof(ScoreArgs) * n_sg);
     memcpy(img.data() + o_p0, pose0.data(), sizeof(long long) * pose0.size());
     memcpy(img.data() + o_t0, tuple0_all.data(), sizeof(long long) * tuple0_all.size());
     cudaError_t e = cudaMemcpyAsync(b->d_block, img.data(), total, cudaMemcpyHostToDevice, b->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
     if (e != cudaSuccess) { cf_batch_destroy(b); return cuda_fail(e, "upload batch"); }
-    b->n_items = n_items;
-    b->launches = (int)b->qgroups.size() + (b->total_poses > 0 ? 1 : 0) + (int)b->sgroups.size();
+    b->n_items = n_sg;  // items of the grouped sampling launch
+    b->launches = (int)b->qgroups.size() + (b->total_poses > 0 ? 1 : 0) + (int)b->sgroups.size() +
+                  (int)b->q_single.size() + 2 * (int)b->s_single.size();
     *out = b;
     return CF_OK;
 }
 
 namespace {
 int batch_enqueue(cf_batch *b, cudaStream_t st) {
+    for (const cf_batch_item &it : b->q_single)
+        CF_TRY(launch_query(it.field->geom, it.field->d_table, it.obj, it.d_poses, it.n_poses, it.d_masks, it.d_counts,
+                            b->ppb, st), "batch query (alone)");
     for (const auto &qg : b->qgroups)
         CF_TRY(launch_query_batch(qg.g0, qg.d_descs, b->d_geoms, qg.n, qg.blocks, b->ppb, st), "batch query");
-    CF_TRY(launch_sample_batch(b->d_sdescs, b->d_pose0, b->n_items, b->total_poses, b->sample_smem, st),
-           "batch sample");
+    for (const ScoreArgs &a : b->s_single) {
+        CF_TRY(cudaMemsetAsync(a.work, 0, sizeof(unsigned int), st), "batch work counter");
+        CF_TRY(launch_score(a, st), "batch sample + score (alone)");
+    }
+    if (b->total_poses > 0)
+        CF_TRY(launch_sample_batch(b->d_sdescs, b->d_pose0, b->n_items, b->total_poses, b->sample_smem, st),
+               "batch sample");
     for (const auto &sg : b->sgroups) {
         CF_TRY(cudaMemsetAsync(sg.launch.work, 0, sizeof(unsigned int), st), "batch work counter");
         CF_TRY(launch_score_batch(sg.launch, sg.d_descs, sg.d_tuple0, sg.n, sg.tuples, st), "batch score");
