@@ -19,7 +19,8 @@
 // k_fk_cell_bounds evaluates the chain, stores the FP32 link frames
 // ([F][J][12][S], coalesced over samples) and reduces the per-finger cell AABB
 // (-> table extents); k_fk_bin reads the frames back and sets the sample's bin
-// in its cell word (atomicOr, skipped when the bit is already set).  Bins come
+// in its cell word (atomicOr without a return value: a fire-and-forget
+// reduction, cheaper than reading the word first to skip bits already set).  Bins come
 // from the same cube-map candidate lists as the query when they are valid.
 #include <limits.h>
 
@@ -165,7 +166,7 @@ __global__ void __launch_bounds__(kThreads) k_fk_bin(HandDev h, const float *__r
     const unsigned dx = (unsigned)g.dims[0], dy = (unsigned)g.dims[1], dz = (unsigned)g.dims[2];
     uint32_t *tab = table + f / g.fpw;
     const int shift = (f % g.fpw) * g.bits;
-    constexpr int kBatch = 4;  // table words loaded together, then the atomics they call for
+    constexpr int kBatch = 4;  // points transformed and binned together, then their table updates
 #pragma unroll
     for (int l = 0; l < J; ++l) {
         const int me = s_lb[l + 1];
@@ -205,12 +206,9 @@ __global__ void __launch_bounds__(kThreads) k_fk_bin(HandDev h, const float *__r
                 wp[i] = tab + (((size_t)uz * dy + uy) * dx + ux) * g.rw;
                 bit[i] = 1u << (shift + bin);
             }
-            uint32_t cur[kBatch];
-#pragma unroll
-            for (int i = 0; i < kBatch; ++i) cur[i] = wp[i] ? __ldcg(wp[i]) : 0u;
 #pragma unroll
             for (int i = 0; i < kBatch; ++i)
-                if (wp[i] && !(cur[i] & bit[i])) atomicOr(wp[i], bit[i]);
+                if (wp[i]) atomicOr(wp[i], bit[i]);  // result unused: a reduction, no round trip
         }
     }
 }

@@ -35,6 +35,16 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 
+// Offset of x's cell from the box origin lo, as unsigned: floor(x * inv_h) - lo
+// (the same rounding as cell_floor) whenever |x * inv_h| < 2^22.  No clamp is
+// needed here: beyond that range, and for inf / NaN, the sum lands outside the
+// [2^23, 2^24) binade and the offset is >= 2^22 - lo or wraps below zero, so it
+// exceeds every box the build admits (|cell| < 2^20) and the range test that
+// follows rejects the point.  base = 0x4B400000 + lo.
+__device__ __forceinline__ unsigned cell_offset(float x, float inv_h, unsigned base) {
+    return __float_as_uint(__fmaf_rd(x, inv_h, 12582912.0f)) - base;
+}
+
 template <int RW>
 __device__ __forceinline__ void load_record(const uint32_t *__restrict__ r, uint32_t (&rec)[RW]) {
     if (RW == 1) {
@@ -118,6 +128,8 @@ __global__ void __launch_bounds__(kThreads) k_query_domains(const QueryArgs a) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int N = obj.n;
     const int B = g.B;
+    const unsigned base_x = 0x4B400000u + (unsigned)g.lo[0], base_y = 0x4B400000u + (unsigned)g.lo[1],
+                   base_z = 0x4B400000u + (unsigned)g.lo[2];
     for (int w = warp; w < W; w += kWarps) {
         const int x = 32 * w + lane;
         const bool valid = x < N;
@@ -136,12 +148,9 @@ __global__ void __launch_bounds__(kThreads) k_query_domains(const QueryArgs a) {
             const float mx = -rot_row(T0.x, T0.y, T0.z, nx, ny, nz);
             const float my = -rot_row(T1.x, T1.y, T1.z, nx, ny, nz);
             const float mz = -rot_row(T2.x, T2.y, T2.z, nx, ny, nz);
-            const int kx = cell_floor(qx, g.inv_h, g.clamp);
-            const int ky = cell_floor(qy, g.inv_h, g.clamp);
-            const int kz = cell_floor(qz, g.inv_h, g.clamp);
-            const unsigned ux = (unsigned)(kx - g.lo[0]);
-            const unsigned uy = (unsigned)(ky - g.lo[1]);
-            const unsigned uz = (unsigned)(kz - g.lo[2]);
+            const unsigned ux = cell_offset(qx, g.inv_h, base_x);
+            const unsigned uy = cell_offset(qy, g.inv_h, base_y);
+            const unsigned uz = cell_offset(qz, g.inv_h, base_z);
             uint32_t rec[RW];
 #pragma unroll
             for (int i = 0; i < RW; ++i) rec[i] = 0u;

@@ -184,13 +184,6 @@ __device__ __forceinline__ unsigned fkey(float x) {
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
-// lane holding the smallest value (exact ties -> lowest lane)
-__device__ __forceinline__ int warp_argmin_lane(float v) {
-    const unsigned key = fkey(v);
-    const unsigned kmin = __reduce_min_sync(kFull, key);
-    return __ffs(__ballot_sync(kFull, key == kmin)) - 1;
-}
-
 // Scaled LP.  For t > 0 put c = t c'; then LP_j = 1 / s_j with
 //     s_j = max sum_m c'_jm  s.t.  -1 <= (sum_im c'_im w_im)_r <= 1 (r = 1..6),  c' >= 0,
 // and LP_j = 0 exactly when s_j is unbounded.  With y = W c' kept as six

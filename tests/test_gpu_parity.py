@@ -256,6 +256,31 @@ def test_plan_chunked_host_path_equals_device_path(cf):
     assert plan.run_host(r["field"], soa_h, poses_h) == nacc  # outputs optional, count still returned
 
 
+def test_far_and_non_finite_points_hit_nothing(cf):
+    """Object points far outside the field (|x / h| far beyond 2^22 cells),
+    infinite or NaN hit no finger, and the other points' mask bits and the
+    counts are those of the object without them."""
+    w = synth.workload("tiny_sphere", P=32)
+    q = torch.from_numpy(w.q).cuda()
+    field = cf.build(w.hand, w.inv_h, w.bins, q)
+    soa = w.obj.soa()
+    extra = np.zeros((6, 6), np.float32)
+    extra[0] = [1e30, -1e30, np.inf, -np.inf, np.nan, 3e5]
+    extra[1] = [0.0, 2e9, 0.0, np.nan, 0.0, -3e5]
+    extra[2] = [0.0, 0.0, -np.inf, 0.0, 1.0, 0.0]
+    extra[5] = 1.0
+    both = np.ascontiguousarray(np.concatenate([soa, extra], axis=1))
+    pz = torch.from_numpy(w.poses).cuda()
+    m0, c0 = cf.query_domains(field, torch.from_numpy(soa).cuda(), pz)
+    m1, c1 = cf.query_domains(field, torch.from_numpy(both).cuda(), pz)
+    torch.cuda.synchronize()
+    N = soa.shape[1]
+    b0, b1 = _bits(_u32(m0), N), _bits(_u32(m1), N + 6)
+    assert np.array_equal(b1[:, :, :N], b0)
+    assert not b1[:, :, N:].any()
+    assert torch.equal(c0, c1)
+
+
 def test_closure_closed_forms_on_gpu(cf):
     """Antipodal pair on a sphere -> margin 0; a single axis-aligned contact
     (k = 1) -> margin 1 (Eq. GSWO with alpha_j = 1)."""
