@@ -236,6 +236,24 @@ def test_scoring_given_tuples_and_invalid_ids(cf):
     assert np.all(np.isinf(mar.cpu().numpy()[0, :3]))
 
 
+@pytest.mark.parametrize("k,K", [(4, 8), (3, 9), (2, 13), (4, 6), (2, 4), (1, 16), (3, 3)])
+def test_lp_shapes_parity(cf, k, K):
+    """Closure margins for (k, K) shapes beyond the workloads' (3, 8): the LP's
+    columns fill one slot per lane when k K + 6 <= 32 ((2, 13) is the edge) and
+    two slots otherwise ((4, 8), (3, 9)); every margin matches the oracle."""
+    w = synth.workload("hand16_superquadric", P=4, S=4096)
+    rng = np.random.default_rng(100 + 10 * k + K)
+    tup = np.stack([rng.choice(w.obj.N, k, replace=False) for _ in range(4 * 48)]).astype(np.int32).reshape(4, 48, k)
+    soa_h = w.obj.soa()
+    soa = torch.from_numpy(soa_h).cuda()
+    prm = cf.score_params(48, k, w.mu, K, w.eps, w.obj.centroid, w.obj.rho, 0, tuples_given=True)
+    _, _, mar, acc = cf.score_tuples(soa, w.hand.F, None, None, prm, tuples=torch.from_numpy(tup).cuda())
+    torch.cuda.synchronize()
+    om, _, _ = oracle.score_tuples(soa_h, tup, w.mu, K, w.obj.centroid, w.obj.rho, w.eps)
+    check_scores(mar.cpu().numpy(), acc.cpu().numpy(), om, w.eps)
+    assert cf.device_status() == 0
+
+
 def test_plan_chunked_host_path_equals_device_path(cf):
     """4,096 poses run in four pose chunks with overlapped copies: tuples,
     margins, accepts and the device-side accept count equal those of the
