@@ -15,12 +15,12 @@
 // with per-32-word popcount prefixes; one thread per tuple draws its fingers
 // and points (Philox4x32-10) and writes them out.
 //
-// k_score_tuples: persistent warps pull batches of tuples from a work counter;
-// each warp solves its tuple's k LPs in the scaled bounded-variable form below
-// (6 rows, kK + 6 columns, one column per lane), LP_{j+1} warm-started from
-// LP_j's basis.  Pricing and the ratio test are single warp reductions
-// (redux.sync) on order-preserving integer keys of the floats; the entering
-// column reaches every lane through a per-warp shared buffer.  FP32 throughout.
+// k_score_lanes: each lane scores its own tuples, the k LPs of a tuple in the
+// scaled bounded-variable form below, solved by a revised simplex whose state
+// (a 6 x 6 basis inverse and the simplex multipliers) lives in the lane's
+// registers; LP_{j+1} starts from LP_j's basis.  The warp-per-LP form of the
+// same simplex (closure_margin) scores the candidates of Alg. 2.  FP32
+// throughout.
 #include <limits.h>
 
 #include <string.h>
@@ -170,8 +170,6 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_tuples(const ScoreArg
 // ---------------------------------------------------------------------------
 // scoring
 // ---------------------------------------------------------------------------
-constexpr int kScoreThreads = 256;
-constexpr int kScoreWarps = kScoreThreads / 32;
 constexpr int kMaxPivots = 64;        // per LP, after the two start pivots
 constexpr int kDegenerateToBland = 16;
 constexpr float kDTol = 1e-6f;        // reduced-cost tolerance
@@ -397,100 +395,6 @@ __device__ float closure_margin(const float (&w)[6], int k, int K, int lane, flo
     return best_s > 0.f ? __fdiv_rn(1.f, best_s) : INFINITY;
 }
 
-// MULTI: global tuple u belongs to object d with tuple0[d] <= u < tuple0[d + 1]
-// (all objects of one launch share k and K); each warp keeps its current
-// object's arguments in shared memory.
-template <bool MULTI, int NS>
-__global__ void __launch_bounds__(kScoreThreads, 3) k_score_tuples(const ScoreArgs a1, const ScoreArgs *descs,
-                                                                    const long long *tuple0, int n_desc,
-                                                                    unsigned total) {
-    __shared__ __align__(16) float s_buf[kScoreWarps][16];
-    __shared__ ScoreArgs s_obj[MULTI ? kScoreWarps : 1];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int k = a1.k, K = a1.K, kK = k * K;
-    const bool colA = lane < kK;
-    const int ci = colA ? lane / K : 0, cm = colA ? lane % K : 0;
-    float ec = a1.cs[cm] * a1.mu, es = a1.sn[cm] * a1.mu;
-    float *buf = s_buf[warp];
-    int cur = -1;
-    long long cur0 = 0, cur1 = 0;
-    unsigned long long n_piv = 0, n_lp = 0, n_tup = 0;
-    unsigned flags = 0, n_acc = 0;
-
-    for (;;) {
-        unsigned u0 = 0;
-        if (lane == 0) u0 = atomicAdd(a1.work, (unsigned)a1.batch);
-        u0 = __shfl_sync(kFull, u0, 0);
-        if (u0 >= total) break;
-        const unsigned uend = min(u0 + (unsigned)a1.batch, total);
-        for (unsigned ug = u0; ug < uend; ++ug) {
-            unsigned u = ug;
-            if (MULTI) {
-                if ((long long)ug < cur0 || (long long)ug >= cur1) {  // switch object
-                    int lo = 0, hi = n_desc - 1;
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (__ldg(tuple0 + mid) <= (long long)ug) lo = mid; else hi = mid - 1;
-                    }
-                    cur = lo;
-                    cur0 = __ldg(tuple0 + lo);
-                    cur1 = __ldg(tuple0 + lo + 1);
-                    __syncwarp();
-                    const int *src = reinterpret_cast<const int *>(descs + cur);
-                    int *dst = reinterpret_cast<int *>(&s_obj[warp]);
-                    for (int e = lane; e < (int)(sizeof(ScoreArgs) / sizeof(int)); e += 32) dst[e] = src[e];
-                    __syncwarp();
-                    ec = s_obj[warp].cs[cm] * s_obj[warp].mu;
-                    es = s_obj[warp].sn[cm] * s_obj[warp].mu;
-                }
-                u = (unsigned)((long long)ug - cur0);
-            }
-            const ScoreArgs &a = MULTI ? s_obj[warp] : a1;
-            const int32_t *st = a.tuples + (size_t)u * k;
-            bool valid = true;
-            for (int d = 0; d < k; ++d) {
-                const int x = __ldg(st + d);
-                valid = valid && x >= 0 && x < a.N;
-            }
-            float margin = INFINITY;
-            if (valid) {
-                float wv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                if (colA) {
-                    const int x = __ldg(st + ci);
-                    const float px = __ldg(a.px + x), py = __ldg(a.py + x), pz = __ldg(a.pz + x);
-                    const float vx = -__ldg(a.nx + x), vy = -__ldg(a.ny + x), vz = -__ldg(a.nz + x);
-                    // tangent basis of nu (Duff et al. 2017)
-                    const float sgn = copysignf(1.f, vz);
-                    const float aa = -1.f / (sgn + vz);
-                    const float bb = vx * vy * aa;
-                    const float xx = 1.f + sgn * vx * vx * aa, xy = sgn * bb, xz = -sgn * vx;
-                    const float yx = bb, yy = sgn + vy * vy * aa, yz = -vy;
-                    const float ex = vx + ec * xx + es * yx, ey = vy + ec * xy + es * yy, ez = vz + ec * xz + es * yz;
-                    const float rx = px - a.cx, ry = py - a.cy, rz = pz - a.cz;
-                    wv[0] = ex; wv[1] = ey; wv[2] = ez;
-                    wv[3] = (ry * ez - rz * ey) * a.inv_rho;
-                    wv[4] = (rz * ex - rx * ez) * a.inv_rho;
-                    wv[5] = (rx * ey - ry * ex) * a.inv_rho;
-                }
-                margin = closure_margin<NS>(wv, k, K, lane, buf, n_piv, n_lp, flags);
-                ++n_tup;
-            }
-            if (lane == 0) {
-                a.margin[u] = margin;
-                a.accept[u] = (uint8_t)(margin <= a.eps);
-                n_acc += margin <= a.eps;
-            }
-        }
-    }
-    if (lane == 0) {
-        atomicAdd(a1.counters + 0, n_piv);
-        atomicAdd(a1.counters + 1, n_lp);
-        atomicAdd(a1.counters + 2, n_tup);
-        if (flags) atomicOr(a1.status, flags);
-        if (a1.n_accept && n_acc) atomicAdd(a1.n_accept, (unsigned long long)n_acc);
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Alg. 2: blockwise zeroth-order contact optimisation
 // ---------------------------------------------------------------------------
@@ -673,6 +577,396 @@ __global__ void __launch_bounds__(kOptThreads) k_optimize_tuples(const ScoreArgs
     }
 }
 
+// ---------------------------------------------------------------------------
+// Lane-per-tuple scoring
+// ---------------------------------------------------------------------------
+// Each lane solves its own tuple's k LPs (the scaled bounded form above) with a
+// revised simplex.  The 6 x 6 basis inverse B^-1 (of the rows -W c' + y = 0,
+// starting from the y basis, B = I), the basic values and the simplex
+// multipliers pi = c_B B^-1 live in registers.  The columns are never stored:
+// column (i, m) is w_im = [nu_i + ec_m x_i + es_m y_i ; t_nu + ec_m t_x + es_m t_y]
+// (ec_m, es_m = mu cos, mu sin of edge m; t_* = r_i x (*) / rho), so the lane keeps
+// the 18 numbers of each contact in its own stretch of shared memory, and
+// pricing needs three 6-term dot products per contact, alpha_i, beta_i,
+// gamma_i, after which d_im = [i = j] + alpha_i + ec_m beta_i + es_m gamma_i
+// costs two FMAs.  d = -pi_r for y_r.  Dantzig pricing (the lowest id on
+// ties; Bland after a run of degenerate pivots); the entering column is
+// u = B^-1 a_e; the ratio test, bound flips and tie rules are those of the warp
+// solver; a pivot updates B^-1, the basic values and pi in place.  Lanes run
+// independently; lanes that finished a tuple take new ones together, when half
+// the warp waits or no lane is in an LP, so the tuple set-up mostly runs
+// converged.  Each block scores a contiguous share of the tuples.
+constexpr int kLaneThreads = 128;
+constexpr int kLaneRefill = 16;
+constexpr float kDTolRel = 4e-6f;  // reduced-cost tolerance per unit of max |pi_r|
+constexpr int kContactFloats = 20;                             // 18 used, padded to five float4
+constexpr int kLaneStride = kContactFloats * CF_MAX_K + 4;     // 84 floats: stride / 4 odd, float4 loads conflict-free
+
+// An object's arguments as a lane needs them (the kernel's own, or its object's descriptor).
+struct LaneObj {
+    const float *px, *py, *pz, *nx, *ny, *nz;
+    float cx, cy, cz, inv_rho, mu, eps;
+    int N;
+    const int32_t *tuples;
+    float *margin;
+    uint8_t *accept;
+};
+
+__device__ __forceinline__ LaneObj lane_obj(const ScoreArgs &a) {
+    return LaneObj{a.px, a.py, a.pz, a.nx, a.ny, a.nz, a.cx, a.cy, a.cz, a.inv_rho, a.mu, a.eps, a.N,
+                   a.tuples, a.margin, a.accept};
+}
+
+// The contact's 18 numbers (nu, x, y, t_nu, t_x, t_y), rounded like wrench_column.
+__device__ __forceinline__ void contact_frame(const LaneObj &a, int x, float *dst) {
+    const float px = __ldg(a.px + x), py = __ldg(a.py + x), pz = __ldg(a.pz + x);
+    const float vx = -__ldg(a.nx + x), vy = -__ldg(a.ny + x), vz = -__ldg(a.nz + x);
+    const float sgn = copysignf(1.f, vz);
+    const float aa = -1.f / (sgn + vz);
+    const float bb = vx * vy * aa;
+    const float xx = 1.f + sgn * vx * vx * aa, xy = sgn * bb, xz = -sgn * vx;
+    const float yx = bb, yy = sgn + vy * vy * aa, yz = -vy;
+    const float rx = px - a.cx, ry = py - a.cy, rz = pz - a.cz, ir = a.inv_rho;
+    float4 *d4 = reinterpret_cast<float4 *>(dst);
+    d4[0] = make_float4(vx, vy, vz, xx);
+    d4[1] = make_float4(xy, xz, yx, yy);
+    d4[2] = make_float4(yz, (ry * vz - rz * vy) * ir, (rz * vx - rx * vz) * ir, (rx * vy - ry * vx) * ir);
+    d4[3] = make_float4((ry * xz - rz * xy) * ir, (rz * xx - rx * xz) * ir, (rx * xy - ry * xx) * ir,
+                        (ry * yz - rz * yy) * ir);
+    d4[4] = make_float4((rz * yx - rx * yz) * ir, (rx * yy - ry * yx) * ir, 0.f, 0.f);
+}
+
+struct Frame {
+    float v[18];
+};
+
+__device__ __forceinline__ Frame load_frame(const float *src) {
+    const float4 *s4 = reinterpret_cast<const float4 *>(src);
+    const float4 f0 = s4[0], f1 = s4[1], f2 = s4[2], f3 = s4[3], f4 = s4[4];
+    return Frame{{f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w, f2.x, f2.y, f2.z, f2.w, f3.x, f3.y, f3.z, f3.w, f4.x,
+                  f4.y}};
+}
+
+// KT: the edge count when known at compile time (0: a.K at run time, <= CF_MAX_EDGES).
+// MULTI: global tuple u belongs to object d with tuple0[d] <= u < tuple0[d + 1]
+// (all objects share k and K); a lane reads its object's arguments from descs[d].
+template <int KT, bool MULTI>
+__global__ void __launch_bounds__(kLaneThreads) k_score_lanes(const ScoreArgs a, const ScoreArgs *__restrict__ descs,
+                                                              const long long *__restrict__ tuple0, int n_desc,
+                                                              unsigned total) {
+    __shared__ __align__(16) float s_c[kLaneThreads * kLaneStride];
+    __shared__ unsigned s_next;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int k = a.k, K = KT > 0 ? KT : a.K, kK = k * K;
+    constexpr int KM = KT > 0 ? KT : CF_MAX_EDGES;
+    float *cf = s_c + tid * kLaneStride;
+    float ec[KM], es[KM];
+#pragma unroll
+    for (int m = 0; m < KM; ++m) {
+        ec[m] = m < K ? a.cs[m] * a.mu : 0.f;
+        es[m] = m < K ? a.sn[m] * a.mu : 0.f;
+    }
+    const unsigned per = (total + gridDim.x - 1) / gridDim.x;
+    const unsigned u_lo = min(total, blockIdx.x * per), u_hi = min(total, u_lo + per);
+    if (tid == 0) s_next = u_lo;
+    __syncthreads();
+
+    constexpr int kIdle = 0, kInLp = 1, kDone = 2;
+    int state = kIdle;
+    unsigned u = 0;  // the lane's tuple within its object
+    int od = 0;      // MULTI: the lane's object
+    float B[kRows][kRows], xb[kRows], pi[kRows];
+    int beta[kRows];
+    unsigned basic_x = 0;  // bit c: column c' basic
+    unsigned ystat = 0;    // bit r: y_r basic; bit 8 + r: y_r nonbasic at its upper bound
+    int j = 0, it = 0, degenerate = 0;
+    bool bland = false, lp_start = false, unbounded = false;
+    float best_s = 0.f;
+    unsigned n_piv = 0, n_lp = 0, n_tup = 0, n_acc = 0, flags = 0;
+
+    for (;;) {
+        // ---- idle lanes take tuples together
+        const unsigned idle = __ballot_sync(kFull, state == kIdle);
+        const unsigned busy = __ballot_sync(kFull, state == kInLp);
+        if (idle && (__popc(idle) >= kLaneRefill || busy == 0)) {
+            const int leader = __ffs(idle) - 1;
+            unsigned base = 0;
+            if (lane == leader) base = atomicAdd(&s_next, (unsigned)__popc(idle));
+            base = __shfl_sync(kFull, base, leader);
+            if (state == kIdle) {
+                u = base + (unsigned)__popc(idle & ((1u << lane) - 1u));
+                if (u >= u_hi) {
+                    state = kDone;
+                } else {
+                    if (MULTI) {
+                        int lo = 0, hi = n_desc - 1;
+                        while (lo < hi) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            if (__ldg(tuple0 + mid) <= (long long)u) lo = mid; else hi = mid - 1;
+                        }
+                        od = lo;
+                        u = (unsigned)((long long)u - __ldg(tuple0 + lo));
+                    }
+                    const LaneObj o = lane_obj(MULTI ? descs[od] : a);
+                    if (MULTI) {
+#pragma unroll
+                        for (int m = 0; m < KM; ++m) {
+                            ec[m] = m < K ? a.cs[m] * o.mu : 0.f;
+                            es[m] = m < K ? a.sn[m] * o.mu : 0.f;
+                        }
+                    }
+                    const int32_t *tp = o.tuples + (size_t)u * k;
+                    bool valid = true;
+                    for (int d = 0; d < k; ++d) {
+                        const int x = __ldg(tp + d);
+                        valid = valid && x >= 0 && x < o.N;
+                        if (valid) contact_frame(o, x, cf + kContactFloats * d);
+                    }
+                    if (!valid) {
+                        o.margin[u] = INFINITY;
+                        o.accept[u] = 0;
+                    } else {
+#pragma unroll
+                        for (int r = 0; r < kRows; ++r) {
+#pragma unroll
+                            for (int c = 0; c < kRows; ++c) B[r][c] = r == c ? 1.f : 0.f;
+                            xb[r] = 0.f;
+                            beta[r] = kK + r;
+                        }
+                        basic_x = 0;
+                        ystat = (1u << kRows) - 1u;
+                        j = 0;
+                        best_s = 0.f;
+                        unbounded = false;
+                        lp_start = true;
+                        state = kInLp;
+                    }
+                }
+            }
+        }
+        if (__all_sync(kFull, state == kDone)) break;
+        if (state != kInLp) continue;
+
+        const int c0 = j * K, c1 = c0 + K;  // contact j's columns
+        if (lp_start) {
+#pragma unroll
+            for (int c = 0; c < kRows; ++c) {
+                float acc = 0.f;
+#pragma unroll
+                for (int r = 0; r < kRows; ++r) acc += (beta[r] >= c0 && beta[r] < c1) ? B[r][c] : 0.f;
+                pi[c] = acc;
+            }
+            it = 0;
+            degenerate = 0;
+            bland = false;
+            lp_start = false;
+        }
+        // ---- pricing.  d is a sum of terms of size up to |pi| |w| (|w| <= 1 + mu), so its rounding
+        // error grows with |pi| (= the LP's objective at the optimum): the tolerance scales with it,
+        // or rounding noise would keep letting columns that do not improve enter.
+        int e = -1;
+        float pmax = 0.f;
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) pmax = fmaxf(pmax, fabsf(pi[r]));
+        const float tol = __fmaf_rn(kDTolRel, pmax, kDTol);
+        float best = tol, de = 0.f;
+        for (int i = 0; i < k; ++i) {
+            const Frame f = load_frame(cf + kContactFloats * i);
+            const float al = (i == j ? 1.f : 0.f) + pi[0] * f.v[0] + pi[1] * f.v[1] + pi[2] * f.v[2] +
+                             pi[3] * f.v[9] + pi[4] * f.v[10] + pi[5] * f.v[11];
+            const float be = pi[0] * f.v[3] + pi[1] * f.v[4] + pi[2] * f.v[5] + pi[3] * f.v[12] + pi[4] * f.v[13] +
+                             pi[5] * f.v[14];
+            const float ga = pi[0] * f.v[6] + pi[1] * f.v[7] + pi[2] * f.v[8] + pi[3] * f.v[15] + pi[4] * f.v[16] +
+                             pi[5] * f.v[17];
+            const unsigned bx = basic_x >> (i * K);
+#pragma unroll
+            for (int m = 0; m < KM; ++m) {
+                if (KT == 0 && m >= K) break;
+                const float d = __fmaf_rn(es[m], ga, __fmaf_rn(ec[m], be, al));
+                const bool elig = !((bx >> m) & 1u) && d > (bland ? tol : best);
+                if (elig && (!bland || e < 0)) {
+                    best = bland ? best : d;
+                    e = i * K + m;
+                    de = d;
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+            const bool up = (ystat >> (8 + r)) & 1u;
+            const float d = -pi[r];
+            const float sc = up ? -d : d;
+            const bool elig = !((ystat >> r) & 1u) && sc > (bland ? tol : best);
+            if (elig && (!bland || e < 0)) {
+                best = bland ? best : sc;
+                e = kK + r;
+                de = d;
+            }
+        }
+        bool lp_end = e < 0;
+        if (!lp_end && it == kMaxPivots) {
+            flags |= CF_DEV_LP_PIVOT_CAP;
+            lp_end = true;
+        }
+        if (!lp_end) {
+            // ---- entering column u = B^-1 a_e (a = -w_e for c', the unit vector e_r for y_r)
+            const bool ey = e >= kK;
+            const int re = e - kK;
+            float ae[kRows];
+            float dl = 1.f;
+            if (!ey) {
+                const int ie = e / K, me = e - ie * K;
+                const Frame f = load_frame(cf + kContactFloats * ie);
+                float cm = 0.f, sm = 0.f;
+#pragma unroll
+                for (int m = 0; m < KM; ++m)
+                    if (m == me) {
+                        cm = ec[m];
+                        sm = es[m];
+                    }
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    ae[q] = -__fmaf_rn(sm, f.v[6 + q], __fmaf_rn(cm, f.v[3 + q], f.v[q]));
+                    ae[3 + q] = -__fmaf_rn(sm, f.v[15 + q], __fmaf_rn(cm, f.v[12 + q], f.v[9 + q]));
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < kRows; ++c) ae[c] = c == re ? 1.f : 0.f;
+                dl = ((ystat >> (8 + re)) & 1u) ? -1.f : 1.f;
+            }
+            float uu[kRows];
+#pragma unroll
+            for (int r = 0; r < kRows; ++r) {
+                float acc = 0.f;
+#pragma unroll
+                for (int c = 0; c < kRows; ++c) acc = __fmaf_rn(B[r][c], ae[c], acc);
+                uu[r] = acc;
+            }
+            // ---- ratio test: the basic variable of row r moves by -dl u_r theta; the entering variable's own
+            // box (y: width 2) is candidate kRows, preferred on equal ratios
+            int l = ey ? kRows : -1;
+            float th = ey ? 2.f : INFINITY, big = 0.f;
+            int lbeta = INT_MAX;
+#pragma unroll
+            for (int r = 0; r < kRows; ++r) {
+                const float al = dl * uu[r];
+                const bool bx = beta[r] < kK;
+                const float lo = bx ? 0.f : -1.f, hi = bx ? INFINITY : 1.f;
+                float t = INFINITY;
+                if (al > kPTol) t = __fdividef(fmaxf(xb[r] - lo, 0.f), al);
+                else if (al < -kPTol) t = __fdividef(fmaxf(hi - xb[r], 0.f), -al);
+                const float aa = fabsf(al);
+                bool take;
+                if (t < th) take = true;
+                else if (t > th || l == kRows || !(t < INFINITY)) take = false;
+                else if (bland) take = beta[r] < lbeta;          // lowest basic-variable id
+                else take = t == 0.f && aa > big;                 // degenerate: largest pivot entry
+                if (take) {
+                    th = t;
+                    l = r;
+                    big = aa;
+                    lbeta = beta[r];
+                }
+            }
+            if (l < 0) {  // s_j unbounded: LP_j = 0
+                unbounded = true;
+                lp_end = true;
+            } else {
+                degenerate = th == 0.f ? degenerate + 1 : 0;
+                if (degenerate >= kDegenerateToBland) bland = true;
+                ++it;
+                ++n_piv;
+                if (l == kRows) {  // bound flip
+#pragma unroll
+                    for (int r = 0; r < kRows; ++r) xb[r] = __fmaf_rn(-dl * uu[r], th, xb[r]);
+                    ystat ^= 1u << (8 + re);
+                } else {
+                    float ul = 0.f;
+                    int leave = 0;
+#pragma unroll
+                    for (int r = 0; r < kRows; ++r)
+                        if (r == l) {
+                            ul = uu[r];
+                            leave = beta[r];
+                        }
+                    const float all = dl * ul;
+                    const float xe = (!ey ? 0.f : (dl > 0.f ? -1.f : 1.f)) + dl * th;
+#pragma unroll
+                    for (int r = 0; r < kRows; ++r) {
+                        xb[r] = r == l ? xe : __fmaf_rn(-dl * uu[r], th, xb[r]);
+                        beta[r] = r == l ? e : beta[r];
+                    }
+                    if (leave < kK) {
+                        basic_x &= ~(1u << leave);
+                    } else {
+                        ystat &= ~(1u << (leave - kK));
+                        if (all < 0.f) ystat |= 1u << (8 + leave - kK);  // it rose to its upper bound
+                    }
+                    if (!ey) basic_x |= 1u << e;
+                    else ystat = (ystat | (1u << re)) & ~(1u << (8 + re));
+                    // B^-1: row l / u_l, other rows minus u_r times it; pi += d_e times the new row l
+                    const float inv = __fdividef(1.f, ul);
+                    float rowl[kRows];
+#pragma unroll
+                    for (int c = 0; c < kRows; ++c) {
+                        float v = 0.f;
+#pragma unroll
+                        for (int r = 0; r < kRows; ++r) v = r == l ? B[r][c] : v;
+                        rowl[c] = __fmul_rn(v, inv);
+                    }
+#pragma unroll
+                    for (int r = 0; r < kRows; ++r)
+#pragma unroll
+                        for (int c = 0; c < kRows; ++c)
+                            B[r][c] = r == l ? rowl[c] : __fmaf_rn(-uu[r], rowl[c], B[r][c]);
+#pragma unroll
+                    for (int c = 0; c < kRows; ++c) pi[c] = __fmaf_rn(de, rowl[c], pi[c]);
+                }
+            }
+        }
+        if (lp_end) {
+            ++n_lp;
+            if (!unbounded) {
+                float sj = 0.f;
+#pragma unroll
+                for (int r = 0; r < kRows; ++r) sj += (beta[r] >= c0 && beta[r] < c1) ? xb[r] : 0.f;
+                best_s = fmaxf(best_s, sj);
+            }
+            if (unbounded || best_s >= 1.f / kZeroExit || j + 1 == k) {
+                const float margin = unbounded ? 0.f : (best_s > 0.f ? __fdiv_rn(1.f, best_s) : INFINITY);
+                float *mg = MULTI ? descs[od].margin : a.margin;
+                uint8_t *ac = MULTI ? descs[od].accept : a.accept;
+                const float eps = MULTI ? descs[od].eps : a.eps;
+                mg[u] = margin;
+                ac[u] = (uint8_t)(margin <= eps);
+                n_acc += margin <= eps;
+                ++n_tup;
+                state = kIdle;
+            } else {
+                ++j;
+                lp_start = true;
+            }
+        }
+    }
+    // every lane has left the loop together
+    unsigned long long v0 = n_piv, v1 = n_lp, v2 = n_tup;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        v0 += __shfl_xor_sync(kFull, v0, o);
+        v1 += __shfl_xor_sync(kFull, v1, o);
+        v2 += __shfl_xor_sync(kFull, v2, o);
+    }
+    const unsigned acc_all = __reduce_add_sync(kFull, n_acc);
+    const unsigned fl = __reduce_or_sync(kFull, flags);
+    if (lane == 0) {
+        atomicAdd(a.counters + 0, v0);
+        atomicAdd(a.counters + 1, v1);
+        atomicAdd(a.counters + 2, v2);
+        if (fl) atomicOr(a.status, fl);
+        if (a.n_accept && acc_all) atomicAdd(a.n_accept, (unsigned long long)acc_all);
+    }
+}
+
 }  // namespace
 
 size_t score_smem_bytes(int F, int W, int T, int k, bool sampling) {
@@ -698,23 +992,32 @@ namespace {
 // slots per lane of the scaled LP: kK + 6 columns fit one slot when kK <= 26
 inline int lp_slots(int k, int K) { return k * K + kRows <= 32 ? 1 : 2; }
 
-template <bool MULTI, int NS>
-cudaError_t launch_score_grid(const ScoreArgs &a1, const ScoreArgs *descs, const long long *tuple0, int n_desc,
-                              long long total, cudaStream_t st) {
+}  // namespace
+
+namespace {
+template <int KT, bool MULTI>
+cudaError_t launch_score_lanes_k(const ScoreArgs &a, const ScoreArgs *descs, const long long *tuple0, int n_desc,
+                                 long long total, cudaStream_t st) {
     cudaError_t err;
     int dev = 0, sms = 0, per_sm = 0;
     if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
     if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
-    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_score_tuples<MULTI, NS>, kScoreThreads, 0)) !=
+    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_score_lanes<KT, MULTI>, kLaneThreads, 0)) !=
         cudaSuccess)
         return err;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    if (a1.batch < 1) return cudaErrorInvalidValue;
-    if (a1.bpsm > 0) per_sm = std::min(per_sm, a1.bpsm);
-    const long long warps_needed = (total + a1.batch - 1) / a1.batch;
-    const int grid = (int)std::min<long long>((long long)sms * per_sm, (warps_needed + kScoreWarps - 1) / kScoreWarps);
-    k_score_tuples<MULTI, NS><<<grid, kScoreThreads, 0, st>>>(a1, descs, tuple0, n_desc, (unsigned)total);
+    if (a.bpsm > 0) per_sm = std::min(per_sm, a.bpsm);
+    const int grid = (int)std::min<long long>((long long)sms * per_sm, (total + kLaneThreads - 1) / kLaneThreads);
+    k_score_lanes<KT, MULTI><<<grid, kLaneThreads, 0, st>>>(a, descs, tuple0, n_desc, (unsigned)total);
     return cudaGetLastError();
+}
+
+template <bool MULTI>
+cudaError_t launch_score_lanes(const ScoreArgs &a, const ScoreArgs *descs, const long long *tuple0, int n_desc,
+                               long long total, cudaStream_t st) {
+    if (total <= 0) return cudaSuccess;
+    return a.K == 8 ? launch_score_lanes_k<8, MULTI>(a, descs, tuple0, n_desc, total, st)
+                    : launch_score_lanes_k<0, MULTI>(a, descs, tuple0, n_desc, total, st);
 }
 }  // namespace
 
@@ -722,8 +1025,7 @@ cudaError_t launch_score(const ScoreArgs &a, cudaStream_t st) {
     if (a.P <= 0) return cudaSuccess;
     cudaError_t err;
     if (!a.tuples_given && (err = launch_sample(a, st)) != cudaSuccess) return err;
-    return lp_slots(a.k, a.K) == 1 ? launch_score_grid<false, 1>(a, nullptr, nullptr, 0, (long long)a.P * a.T, st)
-                                   : launch_score_grid<false, 2>(a, nullptr, nullptr, 0, (long long)a.P * a.T, st);
+    return launch_score_lanes<false>(a, nullptr, nullptr, 0, (long long)a.P * a.T, st);
 }
 
 cudaError_t launch_optimize(const ScoreArgs &a, int n_outer, int n_inner, float sigma, float zero_tol,
@@ -768,9 +1070,8 @@ cudaError_t launch_sample_batch(const ScoreArgs *d_descs, const long long *d_pos
 cudaError_t launch_score_batch(const ScoreArgs &launch, const ScoreArgs *d_descs, const long long *d_tuple0, int n_desc,
                                long long total_tuples, cudaStream_t st) {
     if (total_tuples <= 0) return cudaSuccess;
-    return lp_slots(launch.k, launch.K) == 1
-               ? launch_score_grid<true, 1>(launch, d_descs, d_tuple0, n_desc, total_tuples, st)
-               : launch_score_grid<true, 2>(launch, d_descs, d_tuple0, n_desc, total_tuples, st);
+    if (total_tuples >= (1LL << 32)) return cudaErrorInvalidValue;
+    return launch_score_lanes<true>(launch, d_descs, d_tuple0, n_desc, total_tuples, st);
 }
 
 }  // namespace cf
