@@ -37,7 +37,7 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) per launch from the committed ncu captures of the
 # current kernels on this workload (profiles/k_score_lanes_hand16_superquadric.md,
 # profiles/k_query_domains_hand16_superquadric.md); None for other workloads.
-NCU_TRAFFIC = {"hand16_superquadric": {"k_query_domains": 2_767_104 + 12_197_120}}
+NCU_TRAFFIC = {"hand16_superquadric": {"k_query_domains": 2_196_736 + 11_403_008, "k_score_lanes": 6_722_560}}
 
 
 def _args():
