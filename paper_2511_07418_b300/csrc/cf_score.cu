@@ -593,11 +593,11 @@ __global__ void __launch_bounds__(kOptThreads) k_optimize_tuples(const ScoreArgs
 // ties; Bland after a run of degenerate pivots); the entering column is
 // u = B^-1 a_e; the ratio test, bound flips and tie rules are those of the warp
 // solver; a pivot updates B^-1, the basic values and pi in place.  Lanes run
-// independently; lanes that finished a tuple take new ones together, when half
-// the warp waits or no lane is in an LP, so the tuple set-up mostly runs
-// converged.  Each block scores a contiguous share of the tuples.
+// independently; lanes that finished a tuple take new ones together, when a
+// quarter of the warp waits or no lane is in an LP, so the tuple set-up mostly
+// runs converged.  Each block scores a contiguous share of the tuples.
 constexpr int kLaneThreads = 128;
-constexpr int kLaneRefill = 16;
+constexpr int kLaneRefill = 8;
 constexpr float kDTolRel = 4e-6f;  // reduced-cost tolerance per unit of max |pi_r|
 constexpr int kContactFloats = 20;                             // 18 used, padded to five float4
 constexpr int kLaneStride = kContactFloats * CF_MAX_K + 4;     // 84 floats: stride / 4 odd, float4 loads conflict-free
@@ -660,12 +660,7 @@ __global__ void __launch_bounds__(kLaneThreads) k_score_lanes(const ScoreArgs a,
     const int k = a.k, K = KT > 0 ? KT : a.K, kK = k * K;
     constexpr int KM = KT > 0 ? KT : CF_MAX_EDGES;
     float *cf = s_c + tid * kLaneStride;
-    float ec[KM], es[KM];
-#pragma unroll
-    for (int m = 0; m < KM; ++m) {
-        ec[m] = m < K ? a.cs[m] * a.mu : 0.f;
-        es[m] = m < K ? a.sn[m] * a.mu : 0.f;
-    }
+    float mu = a.mu;  // the lane's object's mu (edge m is mu (cos, sin) of its angle: a.cs[m], a.sn[m])
     const unsigned per = (total + gridDim.x - 1) / gridDim.x;
     const unsigned u_lo = min(total, blockIdx.x * per), u_hi = min(total, u_lo + per);
     if (tid == 0) s_next = u_lo;
@@ -708,13 +703,7 @@ __global__ void __launch_bounds__(kLaneThreads) k_score_lanes(const ScoreArgs a,
                         u = (unsigned)((long long)u - __ldg(tuple0 + lo));
                     }
                     const LaneObj o = lane_obj(MULTI ? descs[od] : a);
-                    if (MULTI) {
-#pragma unroll
-                        for (int m = 0; m < KM; ++m) {
-                            ec[m] = m < K ? a.cs[m] * o.mu : 0.f;
-                            es[m] = m < K ? a.sn[m] * o.mu : 0.f;
-                        }
-                    }
+                    if (MULTI) mu = o.mu;
                     const int32_t *tp = o.tuples + (size_t)u * k;
                     bool valid = true;
                     for (int d = 0; d < k; ++d) {
@@ -779,10 +768,11 @@ __global__ void __launch_bounds__(kLaneThreads) k_score_lanes(const ScoreArgs a,
             const float ga = pi[0] * f.v[6] + pi[1] * f.v[7] + pi[2] * f.v[8] + pi[3] * f.v[15] + pi[4] * f.v[16] +
                              pi[5] * f.v[17];
             const unsigned bx = basic_x >> (i * K);
+            const float bem = mu * be, gam = mu * ga;
 #pragma unroll
             for (int m = 0; m < KM; ++m) {
                 if (KT == 0 && m >= K) break;
-                const float d = __fmaf_rn(es[m], ga, __fmaf_rn(ec[m], be, al));
+                const float d = __fmaf_rn(a.sn[m], gam, __fmaf_rn(a.cs[m], bem, al));
                 const bool elig = !((bx >> m) & 1u) && d > (bland ? tol : best);
                 if (elig && (!bland || e < 0)) {
                     best = bland ? best : d;
@@ -817,13 +807,7 @@ __global__ void __launch_bounds__(kLaneThreads) k_score_lanes(const ScoreArgs a,
             if (!ey) {
                 const int ie = e / K, me = e - ie * K;
                 const Frame f = load_frame(cf + kContactFloats * ie);
-                float cm = 0.f, sm = 0.f;
-#pragma unroll
-                for (int m = 0; m < KM; ++m)
-                    if (m == me) {
-                        cm = ec[m];
-                        sm = es[m];
-                    }
+                const float cm = a.cs[me] * mu, sm = a.sn[me] * mu;
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
                     ae[q] = -__fmaf_rn(sm, f.v[6 + q], __fmaf_rn(cm, f.v[3 + q], f.v[q]));
@@ -906,19 +890,28 @@ __global__ void __launch_bounds__(kLaneThreads) k_score_lanes(const ScoreArgs a,
                     else ystat = (ystat | (1u << re)) & ~(1u << (8 + re));
                     // B^-1: row l / u_l, other rows minus u_r times it; pi += d_e times the new row l
                     const float inv = __fdividef(1.f, ul);
+                    // one-hot row weights: row l is read out with exact FMAs (one nonzero term) and
+                    // rewritten as 0 * B + 1 * rowl, the other rows as 1 * B - u_r * rowl
+                    float oh[kRows], keep[kRows], g[kRows];
+#pragma unroll
+                    for (int r = 0; r < kRows; ++r) {
+                        oh[r] = r == l ? 1.f : 0.f;
+                        keep[r] = r == l ? 0.f : 1.f;
+                        g[r] = r == l ? -1.f : uu[r];
+                    }
                     float rowl[kRows];
 #pragma unroll
                     for (int c = 0; c < kRows; ++c) {
                         float v = 0.f;
 #pragma unroll
-                        for (int r = 0; r < kRows; ++r) v = r == l ? B[r][c] : v;
+                        for (int r = 0; r < kRows; ++r) v = __fmaf_rn(oh[r], B[r][c], v);
                         rowl[c] = __fmul_rn(v, inv);
                     }
 #pragma unroll
                     for (int r = 0; r < kRows; ++r)
 #pragma unroll
                         for (int c = 0; c < kRows; ++c)
-                            B[r][c] = r == l ? rowl[c] : __fmaf_rn(-uu[r], rowl[c], B[r][c]);
+                            B[r][c] = __fmaf_rn(-g[r], rowl[c], __fmul_rn(keep[r], B[r][c]));
 #pragma unroll
                     for (int c = 0; c < kRows; ++c) pi[c] = __fmaf_rn(de, rowl[c], pi[c]);
                 }
