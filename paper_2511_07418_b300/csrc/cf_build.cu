@@ -153,22 +153,21 @@ __global__ void __launch_bounds__(kThreads) k_fk_bin(HandDev h, const float *__r
     __syncthreads();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
-    float R[J][9], t[J][3];
-#pragma unroll
-    for (int l = 0; l < J; ++l) {
-        const float *lk = links + ((size_t)(f * J + l) * 12) * S + s;
-#pragma unroll
-        for (int e = 0; e < 9; ++e) R[l][e] = __ldg(lk + (size_t)e * S);
-#pragma unroll
-        for (int e = 0; e < 3; ++e) t[l][e] = __ldg(lk + (size_t)(9 + e) * S);
-    }
     const int lx = g.lo[0], ly = g.lo[1], lz = g.lo[2];
     const unsigned dx = (unsigned)g.dims[0], dy = (unsigned)g.dims[1], dz = (unsigned)g.dims[2];
     uint32_t *tab = table + f / g.fpw;
     const int shift = (f % g.fpw) * g.bits;
     constexpr int kBatch = 4;  // points transformed and binned together, then their table updates
-#pragma unroll
+#pragma unroll 1
     for (int l = 0; l < J; ++l) {
+        float Rl[9], tl[3];
+        {
+            const float *lk = links + ((size_t)(f * J + l) * 12) * S + s;
+#pragma unroll
+            for (int e = 0; e < 9; ++e) Rl[e] = __ldg(lk + (size_t)e * S);
+#pragma unroll
+            for (int e = 0; e < 3; ++e) tl[e] = __ldg(lk + (size_t)(9 + e) * S);
+        }
         const int me = s_lb[l + 1];
         for (int m0 = s_lb[l]; m0 < me; m0 += kBatch) {
             uint32_t *wp[kBatch];
@@ -179,12 +178,12 @@ __global__ void __launch_bounds__(kThreads) k_fk_bin(HandDev h, const float *__r
                 bit[i] = 0u;
                 if (m0 + i >= me) continue;
                 const float *sp = s_surf + 8 * (m0 + i);
-                const float x = xf_row(R[l][0], R[l][1], R[l][2], t[l][0], sp[0], sp[1], sp[2]);
-                const float y = xf_row(R[l][3], R[l][4], R[l][5], t[l][1], sp[0], sp[1], sp[2]);
-                const float z = xf_row(R[l][6], R[l][7], R[l][8], t[l][2], sp[0], sp[1], sp[2]);
-                const float nx = rot_row(R[l][0], R[l][1], R[l][2], sp[3], sp[4], sp[5]);
-                const float ny = rot_row(R[l][3], R[l][4], R[l][5], sp[3], sp[4], sp[5]);
-                const float nz = rot_row(R[l][6], R[l][7], R[l][8], sp[3], sp[4], sp[5]);
+                const float x = xf_row(Rl[0], Rl[1], Rl[2], tl[0], sp[0], sp[1], sp[2]);
+                const float y = xf_row(Rl[3], Rl[4], Rl[5], tl[1], sp[0], sp[1], sp[2]);
+                const float z = xf_row(Rl[6], Rl[7], Rl[8], tl[2], sp[0], sp[1], sp[2]);
+                const float nx = rot_row(Rl[0], Rl[1], Rl[2], sp[3], sp[4], sp[5]);
+                const float ny = rot_row(Rl[3], Rl[4], Rl[5], sp[3], sp[4], sp[5]);
+                const float nz = rot_row(Rl[6], Rl[7], Rl[8], sp[3], sp[4], sp[5]);
                 int bin = 0;
                 if (CAND) {
                     bin = bin_by_candidates(nx, ny, nz, s_cand, s_dir);

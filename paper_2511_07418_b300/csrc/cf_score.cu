@@ -12,8 +12,8 @@
 // and the margin is min_j LP_j.
 //
 // k_sample_tuples: one block per pose stages the F mask rows in shared memory
-// with per-32-word popcount prefixes; one thread per tuple draws its fingers
-// and points (Philox4x32-10) and writes them out.
+// with popcount prefixes per 8-word group; one thread per tuple draws its
+// fingers and points (Philox4x32-10) and writes them out.
 //
 // k_score_lanes: each lane scores its own tuples, the k LPs of a tuple in the
 // scaled bounded-variable form below, solved by a revised simplex whose state
@@ -56,6 +56,9 @@ __device__ __forceinline__ int select_in_word(uint32_t v, uint32_t r) {
 }
 
 // r-th set bit (ascending) of a staged mask row, -1 if the row has <= r bits.
+// words per prefix group of a staged mask row
+constexpr int kGroupWords = 8;
+
 __device__ __forceinline__ int select_in_row(const uint32_t *row, const uint32_t *gp, int W, int G, uint32_t r) {
     if (r >= gp[G]) return -1;
     int lo = 0, hi = G - 1;  // largest g with gp[g] <= r
@@ -64,8 +67,8 @@ __device__ __forceinline__ int select_in_row(const uint32_t *row, const uint32_t
         if (gp[mid] <= r) lo = mid; else hi = mid - 1;
     }
     uint32_t rr = r - gp[lo];
-    const int wend = min(32 * lo + 32, W);
-    for (int w = 32 * lo; w < wend; ++w) {
+    const int wend = min(kGroupWords * lo + kGroupWords, W);
+    for (int w = kGroupWords * lo; w < wend; ++w) {
         const uint32_t v = row[w];
         const uint32_t c = __popc(v);
         if (rr < c) return 32 * w + select_in_word(v, rr);
@@ -110,7 +113,7 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_tuples(const ScoreArg
     }
     const ScoreArgs &a = MULTI ? s_args : a1;
     const int F = a.F, W = a.W, T = a.T, k = a.k;
-    const int G = (W + 31) / 32;
+    const int G = (W + kGroupWords - 1) / kGroupWords;
     uint32_t *s_mask = s_dyn;           // [F][W]
     uint32_t *s_gpre = s_mask + F * W;  // [F][G + 1]
     const int i = MULTI ? s_i : (int)blockIdx.x;
@@ -118,19 +121,34 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_tuples(const ScoreArg
     const uint32_t *src = a.masks + (size_t)i * F * W;
     for (int e = threadIdx.x; e < F * W; e += blockDim.x) s_mask[e] = src[e];
     __syncthreads();
-    for (int e = threadIdx.x; e < F * G; e += blockDim.x) {
-        const int f = e / G, g = e % G;
-        const uint32_t *row = s_mask + f * W;
-        uint32_t c = 0;
-        const int wend = min(32 * g + 32, W);
-        for (int w = 32 * g; w < wend; ++w) c += __popc(row[w]);
-        s_gpre[f * (G + 1) + g + 1] = c;
+    // group sums: a warp popcounts 32 consecutive words of a row (one per lane, no bank conflicts)
+    // and adds them in groups of kGroupWords lanes
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const int CW = (W + 31) / 32;
+    for (int ch = warp; ch < F * CW; ch += nwarps) {
+        const int f = ch / CW, w = (ch % CW) * 32 + lane;
+        uint32_t c = w < W ? __popc(s_mask[f * W + w]) : 0u;
+#pragma unroll
+        for (int o = 1; o < kGroupWords; o <<= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (lane % kGroupWords == 0 && w < W) s_gpre[f * (G + 1) + 1 + w / kGroupWords] = c;
     }
     __syncthreads();
-    if (threadIdx.x < F) {
-        uint32_t *gp = s_gpre + threadIdx.x * (G + 1);
-        gp[0] = 0;
-        for (int g = 1; g <= G; ++g) gp[g] += gp[g - 1];
+    // exclusive prefix of the group sums per row: one warp per row, 32 groups per step
+    for (int f = warp; f < F; f += nwarps) {
+        uint32_t *gp = s_gpre + f * (G + 1);
+        uint32_t carry = 0;
+        for (int g0 = 0; g0 < G; g0 += 32) {
+            const int g = g0 + lane;
+            uint32_t v = g < G ? gp[1 + g] : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += t;
+            }
+            if (g < G) gp[1 + g] = v + carry;
+            carry += __shfl_sync(0xffffffffu, v, 31);
+        }
+        if (lane == 0) gp[0] = 0;
     }
     __syncthreads();
     uint32_t pk0 = 0;  // non-empty fingers, 4 bits each, ascending
@@ -965,7 +983,7 @@ __global__ void __launch_bounds__(kLaneThreads) k_score_lanes(const ScoreArgs a,
 size_t score_smem_bytes(int F, int W, int T, int k, bool sampling) {
     (void)T;
     (void)k;
-    const int G = (W + 31) / 32;
+    const int G = (W + kGroupWords - 1) / kGroupWords;
     return sampling ? sizeof(uint32_t) * ((size_t)F * W + (size_t)F * (G + 1)) : 0;
 }
 
