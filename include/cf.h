@@ -217,11 +217,13 @@ int cf_score_tuples(const cf_points *obj, int32_t n_fingers, const uint32_t *d_m
  * have given a fixed budget of device memory to other work on the same GPU
  * (a robot controller or renderer sharing the device).  Some must not risk a
  * failed or blocking allocation in the middle of a control loop.  Some run
- * where the allocator belongs to another framework.  The only scratch the
- * kernel needs is its 4-byte tuple work counter.  Here it lives in a
- * library-wide device array of CF_NOALLOC_SCRATCH_BYTES bytes; every GPU that
- * loads libcf holds that array until the process exits.  A call whose scratch
- * need exceeds that size is rejected with CF_EINVAL.  The first call on each
+ * where the allocator belongs to another framework.  Unlike cf_score_tuples,
+ * this entry point promises to allocate nothing, whichever scoring kernel the
+ * library runs.  Its scratch is a 4-byte tuple work counter (the current
+ * scoring kernels take tuples from per-block shared-memory counters and do not
+ * read it) in a library-wide device array of CF_NOALLOC_SCRATCH_BYTES bytes;
+ * every GPU that loads libcf holds that array until the process exits.  A call
+ * whose scratch need exceeds that size is rejected with CF_EINVAL.  The first call on each
  * device looks up the array's device address.  Make that first call before
  * any stream capture.  Every call shares the array and clears the counter
  * before its kernel runs.  Calls whose work overlaps on the GPU (different
@@ -447,7 +449,8 @@ int cf_concave_filter(const cf_points *obj, const cf_sdf *sdf, float side, float
  * Batches and engines take the shapes current at their creation. */
 typedef struct cf_tuning {
     int32_t query_poses_per_block;  /* poses per domain-query block: 4, 8 or 16 (default 4) */
-    int32_t score_tuples_per_grab;  /* tuples a scoring warp takes per work-counter grab: 1, 2, 4 or 8 (default 4) */
+    int32_t score_refill;           /* scoring lanes of a warp that wait before they take new tuples together:
+                                       4, 8 or 16 (default 8) */
     int32_t score_blocks_per_sm;    /* scoring blocks per SM: 1, 2, 3, or 0 = as many as fit (default 0) */
 } cf_tuning;
 
@@ -455,8 +458,8 @@ int cf_get_tuning(cf_tuning *out);
 int cf_set_tuning(const cf_tuning *tuning);
 
 /* Autotuner: runs the items' query launches under every poses-per-block
- * candidate, then their sampling + scoring under every (tuples per grab,
- * blocks per SM) candidate, `reps` times each (median of the summed CUDA-event
+ * candidate, then their sampling + scoring under every (refill, blocks per SM)
+ * candidate, `reps` times each (median of the summed CUDA-event
  * times), keeps the fastest and makes it the device's tuning; *out (if not
  * NULL) receives it and best_ms[0..1] the query and scoring times it measured.
  * The items' output buffers are written by the trial runs.  Synchronous.

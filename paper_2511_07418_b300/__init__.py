@@ -69,7 +69,7 @@ class OptParams(Structure):
 
 
 class Tuning(Structure):
-    _fields_ = [("query_poses_per_block", c_int32), ("score_tuples_per_grab", c_int32),
+    _fields_ = [("query_poses_per_block", c_int32), ("score_refill", c_int32),
                 ("score_blocks_per_sm", c_int32)]
 
 
@@ -744,8 +744,8 @@ def get_tuning() -> dict:
     return {f: getattr(t, f) for f, _ in Tuning._fields_}
 
 
-def set_tuning(query_poses_per_block=4, score_tuples_per_grab=4, score_blocks_per_sm=0):
-    _check(_cf_set_tuning(byref(Tuning(int(query_poses_per_block), int(score_tuples_per_grab),
+def set_tuning(query_poses_per_block=4, score_refill=8, score_blocks_per_sm=0):
+    _check(_cf_set_tuning(byref(Tuning(int(query_poses_per_block), int(score_refill),
                                        int(score_blocks_per_sm)))))
 
 

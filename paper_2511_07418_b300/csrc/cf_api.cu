@@ -55,7 +55,7 @@ DevState g_state[64];
 std::mutex g_tune_mu;
 Tuning g_tune[64];
 bool g_tune_set[64] = {};
-constexpr Tuning kDefaultTuning{4, 4, 0};
+constexpr Tuning kDefaultTuning{4, 8, 0};
 
 int device_state(DevState *out) {
     int dev = 0;
@@ -645,7 +645,7 @@ int fill_score_args(const cf_points *obj, int32_t F, const uint32_t *d_masks, co
     a->status = ds.status;
     a->counters = ds.counters;
     const Tuning tu = current_tuning();
-    a->batch = tu.score_batch;
+    a->refill = tu.score_refill;
     a->bpsm = tu.score_bpsm;
     return CF_OK;
 }
@@ -661,17 +661,8 @@ extern "C" int cf_score_tuples(const cf_points *obj, int32_t n_fingers, const ui
                              d_accept, &a);
     if (rc) return rc;
     if (n_poses == 0) return CF_OK;
-    cudaStream_t st = (cudaStream_t)stream;
-    unsigned int *work = nullptr;
-    if ((rc = pool_alloc((void **)&work, sizeof(unsigned int), st, "alloc work counter"))) return rc;
-    cudaError_t e = cudaMemsetAsync(work, 0, sizeof(unsigned int), st);
-    if (e == cudaSuccess) {
-        a.work = work;
-        e = launch_score(a, st);
-    }
-    cudaError_t e2 = cudaFreeAsync(work, st);
-    if (e != cudaSuccess) return cuda_fail(e, "launch k_sample_tuples / k_score_tuples");
-    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync(work counter)");
+    // the lane scorer takes tuples from per-block shared-memory counters: no global scratch
+    CF_TRY(launch_score(a, (cudaStream_t)stream), "launch k_sample_tuples / k_score_lanes");
     return CF_OK;
 }
 
@@ -812,7 +803,7 @@ extern "C" int cf_score_tuples_noalloc(const cf_points *obj, int32_t n_fingers, 
     int rc = fill_score_args(obj, n_fingers, d_masks, d_counts, n_poses, prm, d_tuples, d_fingers, d_margin,
                              d_accept, &a);
     if (rc) return rc;
-    const size_t need = sizeof(unsigned int);  // the tuple work counter
+    const size_t need = sizeof(unsigned int);  // a tuple work counter (read by no current scoring kernel)
     if (need > (size_t)CF_NOALLOC_SCRATCH_BYTES)
         return fail(CF_EINVAL, "scratch need %zu B exceeds the %d B no-allocation scratch", need,
                     CF_NOALLOC_SCRATCH_BYTES);
@@ -1182,8 +1173,8 @@ extern "C" int cf_concave_filter(const cf_points *obj, const cf_sdf *sdf, float 
 // ---------------------------------------------------------------------------
 namespace {
 bool tuning_valid(const cf_tuning *t) {
-    const int p = t->query_poses_per_block, b = t->score_tuples_per_grab, s = t->score_blocks_per_sm;
-    return (p == 4 || p == 8 || p == 16) && (b == 1 || b == 2 || b == 4 || b == 8) && s >= 0 && s <= 3;
+    const int p = t->query_poses_per_block, r = t->score_refill, s = t->score_blocks_per_sm;
+    return (p == 4 || p == 8 || p == 16) && (r == 4 || r == 8 || r == 16) && s >= 0 && s <= 3;
 }
 }  // namespace
 
@@ -1191,7 +1182,7 @@ extern "C" int cf_get_tuning(cf_tuning *out) {
     if (!out) return fail(CF_EINVAL, "NULL argument");
     const Tuning t = current_tuning();
     out->query_poses_per_block = t.query_ppb;
-    out->score_tuples_per_grab = t.score_batch;
+    out->score_refill = t.score_refill;
     out->score_blocks_per_sm = t.score_bpsm;
     return CF_OK;
 }
@@ -1203,7 +1194,7 @@ extern "C" int cf_set_tuning(const cf_tuning *t) {
     CF_TRY(cudaGetDevice(&dev), "cudaGetDevice");
     if (dev < 0 || dev >= 64) return fail(CF_EINVAL, "device ordinal %d out of range", dev);
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune[dev] = Tuning{t->query_poses_per_block, t->score_tuples_per_grab, t->score_blocks_per_sm};
+    g_tune[dev] = Tuning{t->query_poses_per_block, t->score_refill, t->score_blocks_per_sm};
     g_tune_set[dev] = true;
     return CF_OK;
 }
@@ -1257,15 +1248,15 @@ extern "C" int cf_autotune(const cf_batch_item *items, int32_t n_items, int32_t 
         if ((rc = run(t, 0, &ms))) break;
         if (ms < bq) { bq = ms; best.query_poses_per_block = ppb; }
     }
-    for (int batch : {1, 2, 4, 8}) {
+    for (int refill : {4, 8, 16}) {
         if (rc) break;
         for (int bpsm : {0, 1, 2}) {
             cf_tuning t = best;
-            t.score_tuples_per_grab = batch;
+            t.score_refill = refill;
             t.score_blocks_per_sm = bpsm;
             double ms = 0;
             if ((rc = run(t, 1, &ms))) break;
-            if (ms < bs) { bs = ms; best.score_tuples_per_grab = batch; best.score_blocks_per_sm = bpsm; }
+            if (ms < bs) { bs = ms; best.score_refill = refill; best.score_blocks_per_sm = bpsm; }
         }
     }
     cudaEventDestroy(e0);

@@ -213,7 +213,7 @@ struct cf_engine {
     size_t h_meta_bytes = 0;
     PinnedPool pinned;
     std::string worker_error;
-    Tuning tune{4, 4, 0};  // launch shapes (the tuning at creation)
+    Tuning tune{4, 8, 0};  // launch shapes (the tuning at creation)
 
     double now() const {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -291,7 +291,7 @@ int run_round(cf_engine *e, std::vector<EngReq *> &act) {
                                  r->d_fingers, r->d_margin, r->d_accept, &sargs[i]);
         if (rc) return rc;
         sargs[i].pose_base = (uint32_t)r->pose_next;
-        sargs[i].batch = e->tune.score_batch;
+        sargs[i].refill = e->tune.score_refill;
         sargs[i].bpsm = e->tune.score_bpsm;
     }
     auto geom_of = [&](int i) {

@@ -290,7 +290,7 @@ constexpr int kMaxPosesPerBlock = 16;
 // Launch shapes picked by the autotuner (per device); results do not depend on them.
 struct Tuning {
     int query_ppb;    // poses per query block: 4, 8 or 16
-    int score_batch;  // tuples a scoring warp takes per work-counter grab: 1, 2, 4 or 8
+    int score_refill; // idle lanes of a scoring warp before they take new tuples together: 4, 8 or 16
     int score_bpsm;   // scoring blocks per SM (0: as many as fit)
 };
 Tuning current_tuning();
@@ -312,7 +312,7 @@ struct ScoreArgs {
     unsigned int *work;  // scratch: tuple work counter, zero at launch
     unsigned int *status;          // device status word (CF_DEV_* bits)
     unsigned long long *counters;  // [0] pivots, [1] LPs, [2] tuples
-    int batch;                     // tuples per work-counter grab (launch-level)
+    int refill;                    // idle lanes of a scoring warp before a group refill (launch-level)
     int bpsm;                      // scoring blocks per SM, 0 = as many as fit (launch-level)
     unsigned long long *n_accept;  // optional: accepted tuples of the launch are added here
 };

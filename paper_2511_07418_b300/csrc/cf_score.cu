@@ -611,11 +611,10 @@ __global__ void __launch_bounds__(kOptThreads) k_optimize_tuples(const ScoreArgs
 // ties; Bland after a run of degenerate pivots); the entering column is
 // u = B^-1 a_e; the ratio test, bound flips and tie rules are those of the warp
 // solver; a pivot updates B^-1, the basic values and pi in place.  Lanes run
-// independently; lanes that finished a tuple take new ones together, when a
-// quarter of the warp waits or no lane is in an LP, so the tuple set-up mostly
-// runs converged.  Each block scores a contiguous share of the tuples.
+// independently; lanes that finished a tuple take new ones together, when
+// `refill` lanes of the warp wait (8 by default) or no lane is in an LP, so the
+// tuple set-up mostly runs converged.  Each block scores a contiguous share of the tuples.
 constexpr int kLaneThreads = 128;
-constexpr int kLaneRefill = 8;
 constexpr float kDTolRel = 4e-6f;  // reduced-cost tolerance per unit of max |pi_r|
 constexpr int kContactFloats = 20;                             // 18 used, padded to five float4
 constexpr int kLaneStride = kContactFloats * CF_MAX_K + 4;     // 84 floats: stride / 4 odd, float4 loads conflict-free
@@ -677,6 +676,7 @@ __global__ void __launch_bounds__(kLaneThreads) k_score_lanes(const ScoreArgs a,
     const int tid = threadIdx.x, lane = tid & 31;
     const int k = a.k, K = KT > 0 ? KT : a.K, kK = k * K;
     constexpr int KM = KT > 0 ? KT : CF_MAX_EDGES;
+    const int refill = min(max(a.refill, 1), 32);  // idle lanes before a group refill
     float *cf = s_c + tid * kLaneStride;
     float mu = a.mu;  // the lane's object's mu (edge m is mu (cos, sin) of its angle: a.cs[m], a.sn[m])
     const unsigned per = (total + gridDim.x - 1) / gridDim.x;
@@ -701,7 +701,7 @@ __global__ void __launch_bounds__(kLaneThreads) k_score_lanes(const ScoreArgs a,
         // ---- idle lanes take tuples together
         const unsigned idle = __ballot_sync(kFull, state == kIdle);
         const unsigned busy = __ballot_sync(kFull, state == kInLp);
-        if (idle && (__popc(idle) >= kLaneRefill || busy == 0)) {
+        if (idle && (__popc(idle) >= refill || busy == 0)) {
             const int leader = __ffs(idle) - 1;
             unsigned base = 0;
             if (lane == leader) base = atomicAdd(&s_next, (unsigned)__popc(idle));

@@ -17,7 +17,7 @@ def cf():
         pytest.skip("no CUDA device")
     import paper_2511_07418_b300 as cf
     yield cf
-    cf.set_tuning(8, 4, 0)
+    cf.set_tuning(4, 8, 0)
 
 
 def _run(cf, w, field, soa, poses):
@@ -29,13 +29,13 @@ def _run(cf, w, field, soa, poses):
 
 
 def test_tuning_accessors(cf):
-    cf.set_tuning(16, 2, 1)
-    assert cf.get_tuning() == {"query_poses_per_block": 16, "score_tuples_per_grab": 2, "score_blocks_per_sm": 1}
-    for bad in ((5, 4, 0), (8, 3, 0), (8, 4, 4), (0, 4, 0)):
+    cf.set_tuning(16, 4, 1)
+    assert cf.get_tuning() == {"query_poses_per_block": 16, "score_refill": 4, "score_blocks_per_sm": 1}
+    for bad in ((5, 8, 0), (8, 3, 0), (8, 8, 4), (0, 8, 0), (8, 2, 0)):
         with pytest.raises(cf.CfError):
             cf.set_tuning(*bad)
     assert cf.get_tuning()["query_poses_per_block"] == 16
-    cf.set_tuning(8, 4, 0)
+    cf.set_tuning(4, 8, 0)
 
 
 @pytest.mark.parametrize("name,P", [("tiny_sphere", 37), ("hand16_superquadric", 45)])
@@ -45,7 +45,7 @@ def test_results_do_not_depend_on_shape(cf, name, P):
     soa = torch.from_numpy(w.obj.soa()).cuda()
     poses = torch.from_numpy(w.poses).cuda()
     ref = None
-    for shape in ((8, 4, 0), (4, 1, 1), (16, 8, 2), (16, 2, 3)):
+    for shape in ((8, 8, 0), (4, 4, 1), (16, 16, 2), (16, 4, 3)):
         cf.set_tuning(*shape)
         out = _run(cf, w, field, soa, poses)
         if ref is None:
@@ -53,7 +53,7 @@ def test_results_do_not_depend_on_shape(cf, name, P):
         else:
             for a, b in zip(ref, out):
                 assert np.array_equal(a, b), shape
-    cf.set_tuning(8, 4, 0)
+    cf.set_tuning(4, 8, 0)
 
 
 def test_autotune_and_batch_shapes(cf):
@@ -68,11 +68,11 @@ def test_autotune_and_batch_shapes(cf):
         items.append(it)
         keep.append((field, soa, poses, it))
     tuning, ms = cf.autotune(items, reps=2)
-    assert tuning["query_poses_per_block"] in (4, 8, 16) and tuning["score_tuples_per_grab"] in (1, 2, 4, 8)
+    assert tuning["query_poses_per_block"] in (4, 8, 16) and tuning["score_refill"] in (4, 8, 16)
     assert cf.get_tuning() == tuning and ms[0] > 0 and ms[1] > 0
     # a batch created under two different tunings gives identical outputs
     res = []
-    for shape in ((4, 1, 0), (16, 8, 0)):
+    for shape in ((4, 4, 0), (16, 16, 0)):
         cf.set_tuning(*shape)
         b = cf.Batch(items)
         b.run()
@@ -82,4 +82,4 @@ def test_autotune_and_batch_shapes(cf):
         b.close()
     for a, c in zip(*res):
         assert np.array_equal(a, c)
-    cf.set_tuning(8, 4, 0)
+    cf.set_tuning(4, 8, 0)
