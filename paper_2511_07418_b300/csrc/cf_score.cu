@@ -777,7 +777,48 @@ __global__ void __launch_bounds__(kLaneThreads) k_score_lanes(const ScoreArgs a,
         for (int r = 0; r < kRows; ++r) pmax = fmaxf(pmax, fabsf(pi[r]));
         const float tol = __fmaf_rn(kDTolRel, pmax, kDTol);
         float best = tol, de = 0.f;
-        for (int i = 0; i < k; ++i) {
+        // Dantzig pricing without the basic-column test: a basic column's reduced cost is zero up to
+        // rounding, below tol, so it can only win by rounding noise; then, and in Bland mode, the
+        // masked scan below redoes the choice
+        bool masked = bland;
+        if (!bland) {
+            for (int i = 0; i < k; ++i) {
+                const Frame f = load_frame(cf + kContactFloats * i);
+                const float al = (i == j ? 1.f : 0.f) + pi[0] * f.v[0] + pi[1] * f.v[1] + pi[2] * f.v[2] +
+                                 pi[3] * f.v[9] + pi[4] * f.v[10] + pi[5] * f.v[11];
+                const float be = pi[0] * f.v[3] + pi[1] * f.v[4] + pi[2] * f.v[5] + pi[3] * f.v[12] +
+                                 pi[4] * f.v[13] + pi[5] * f.v[14];
+                const float ga = pi[0] * f.v[6] + pi[1] * f.v[7] + pi[2] * f.v[8] + pi[3] * f.v[15] +
+                                 pi[4] * f.v[16] + pi[5] * f.v[17];
+                const float bem = mu * be, gam = mu * ga;
+                const int ci = i * K;
+#pragma unroll
+                for (int m = 0; m < KM; ++m) {
+                    if (KT == 0 && m >= K) break;
+                    const float d = __fmaf_rn(a.sn[m], gam, __fmaf_rn(a.cs[m], bem, al));
+                    if (d > best) {
+                        best = d;
+                        e = ci + m;
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < kRows; ++r) {
+                const float sc = ((ystat >> (8 + r)) & 1u) ? pi[r] : -pi[r];
+                if (!((ystat >> r) & 1u) && sc > best) {
+                    best = sc;
+                    e = kK + r;
+                }
+            }
+            if (e >= 0 && e < kK && ((basic_x >> e) & 1u)) {
+                masked = true;
+                best = tol;
+                e = -1;
+            } else {
+                de = (e >= kK && ((ystat >> (8 + e - kK)) & 1u)) ? -best : best;
+            }
+        }
+        if (masked) for (int i = 0; i < k; ++i) {
             const Frame f = load_frame(cf + kContactFloats * i);
             const float al = (i == j ? 1.f : 0.f) + pi[0] * f.v[0] + pi[1] * f.v[1] + pi[2] * f.v[2] +
                              pi[3] * f.v[9] + pi[4] * f.v[10] + pi[5] * f.v[11];
@@ -801,6 +842,7 @@ __global__ void __launch_bounds__(kLaneThreads) k_score_lanes(const ScoreArgs a,
         }
 #pragma unroll
         for (int r = 0; r < kRows; ++r) {
+            if (!masked) break;
             const bool up = (ystat >> (8 + r)) & 1u;
             const float d = -pi[r];
             const float sc = up ? -d : d;
