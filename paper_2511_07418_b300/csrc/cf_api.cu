@@ -372,7 +372,7 @@ extern "C" int cf_build(const cf_hand_desc *hand, const cf_field_params *prm, co
             return rc;
         }
         CF_STEP(cudaMemsetAsync(fd->d_table, 0, sizeof(uint32_t) * (size_t)words, st), "memset table");
-        CF_STEP(launch_fk_bin(fd->hand, d_links, n_samples, fd->geom, fd->d_table, ds.status, st), "launch k_fk_bin");
+        CF_STEP(launch_fk_bin(fd->hand, h_lb, d_links, n_samples, fd->geom, fd->d_table, ds.status, st), "launch k_fk_bin");
     }
     int64_t rep_bytes = 0;
     if (want_rep) {

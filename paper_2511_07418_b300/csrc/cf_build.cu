@@ -12,15 +12,16 @@
 // The table is one box of cells over all fingers; a cell's record holds the
 // bin sets of all fingers (finger f: bits (f % fpw) * bits .. of word f / fpw).
 //
-// Thread per (finger, joint sample).  The kinematic chain is evaluated in FP32
-// with explicitly rounded operations (joint sin / cos from FP64, rounded once);
-// each surface point is then transformed
-// with single-rounding FP32 FMAs (component order x, y, z).  Two passes:
-// k_fk_cell_bounds evaluates the chain, stores the FP32 link frames
-// ([F][J][12][S], coalesced over samples) and reduces the per-finger cell AABB
-// (-> table extents); k_fk_bin reads the frames back and sets the sample's bin
-// in its cell word (atomicOr without a return value: a fire-and-forget
-// reduction, cheaper than reading the word first to skip bits already set).  Bins come
+// k_fk_cell_bounds: thread per (finger, joint sample).  The kinematic chain is
+// evaluated in FP32 with explicitly rounded operations (joint sin / cos from FP64,
+// rounded once); each surface point is then transformed with single-rounding FP32
+// FMAs (component order x, y, z).  Two passes: k_fk_cell_bounds evaluates the
+// chain, stores the FP32 link frames ([F][J][12][S], coalesced over samples) and
+// reduces the per-finger cell AABB (-> table extents); k_fk_bin, a persistent grid
+// over (finger, point group, sample chunk) items, reads the frames back and sets
+// each sample's bin in its cell word.  Most vectors repeat a code already set, so
+// k_fk_bin reads the word first (an L1-cached read) and issues the atomicOr only
+// when its bit is missing.  Bins come
 // from the same cube-map candidate lists as the query when they are valid.
 #include <limits.h>
 
@@ -136,30 +137,75 @@ __global__ void __launch_bounds__(kThreads) k_fk_cell_bounds(HandDev h, const fl
     }
 }
 
+// Work items of the binning pass: (finger, point group, chunk of kThreads samples), the
+// chunk index fastest.  A point group is kGroupPts consecutive surface points of one
+// link (a link's points are cut into groups; G = the most groups of any finger), so a
+// thread loads one link frame per item.  A persistent grid walks the items with a
+// static stride, which spreads them evenly over the SMs whatever the sample count.
+constexpr int kGroupPts = 16;
+
+// A plain (weak, L1-cached) read of a table word that other threads are setting bits
+// in.  It returns the word as it was at some point of the pass: the table starts at
+// zero and bits are only ever set, so a stale read shows a subset of the final bits
+// and only costs an update that was not needed; a bit it shows is set for good.
+// Inline PTX keeps the compiler from reasoning about the concurrent updates.
+__device__ __forceinline__ uint32_t table_peek(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.global.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+// Offset of x's cell from the box origin, as floor(x * inv_h) - lo (the same
+// rounding as cell_floor).  The binning pass needs no clamp: the bounds pass saw
+// these exact coordinates and the box was accepted only if every cell satisfied
+// |k| < 2^20, so no coordinate reached the clamp (|x * inv_h| = 2^21).
+__device__ __forceinline__ unsigned bin_cell_offset(float x, float inv_h, unsigned base) {
+    return __float_as_uint(__fmaf_rd(x, inv_h, 12582912.0f)) - base;
+}
+
 template <int J, bool CAND>
 __global__ void __launch_bounds__(kThreads) k_fk_bin(HandDev h, const float *__restrict__ links, int S, FieldGeom g,
-                                                     uint32_t *table, unsigned int *status) {
+                                                     int G, uint32_t *table, unsigned int *status) {
     extern __shared__ float s_surf[];
     __shared__ int s_lb[CF_MAX_JOINTS + 1];
     __shared__ float4 s_dir[CF_MAX_BINS];
     __shared__ uint32_t s_cand[CAND ? kCandCells : 1];
-    const int f = blockIdx.y;
-    stage_surface(h, f, s_surf, s_lb);
     if (CAND) {
         for (int e = threadIdx.x; e < kCandCells; e += blockDim.x) s_cand[e] = __ldg(g.cand + e);
         if (threadIdx.x < g.B)
             s_dir[threadIdx.x] = make_float4(g.dirs[threadIdx.x][0], g.dirs[threadIdx.x][1], g.dirs[threadIdx.x][2], 0.f);
     }
-    __syncthreads();
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S) return;
-    const int lx = g.lo[0], ly = g.lo[1], lz = g.lo[2];
+    const int chunks = (S + kThreads - 1) / kThreads;
+    const long long items = (long long)h.F * G * chunks;
+    const unsigned base_x = 0x4B400000u + (unsigned)g.lo[0], base_y = 0x4B400000u + (unsigned)g.lo[1],
+                   base_z = 0x4B400000u + (unsigned)g.lo[2];
     const unsigned dx = (unsigned)g.dims[0], dy = (unsigned)g.dims[1], dz = (unsigned)g.dims[2];
-    uint32_t *tab = table + f / g.fpw;
-    const int shift = (f % g.fpw) * g.bits;
     constexpr int kBatch = 4;  // points transformed and binned together, then their table updates
-#pragma unroll 1
-    for (int l = 0; l < J; ++l) {
+    int cur_f = -1;
+    for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+        const int chunk = (int)(it % chunks);
+        const int fg = (int)(it / chunks);
+        const int f = fg / G, grp = fg - f * G;
+        if (f != cur_f) {  // block-uniform: stage the finger's surface points
+            __syncthreads();
+            stage_surface(h, f, s_surf, s_lb);
+            __syncthreads();
+            cur_f = f;
+        }
+        int l = -1, mb = 0, me = 0;  // the group's link and point range
+        for (int ll = 0, acc = 0; ll < J; ++ll) {
+            const int b0 = s_lb[ll], n = s_lb[ll + 1] - b0, ng = (n + kGroupPts - 1) / kGroupPts;
+            if (grp >= acc && grp < acc + ng) {
+                l = ll;
+                mb = b0 + (grp - acc) * kGroupPts;
+                me = min(mb + kGroupPts, b0 + n);
+            }
+            acc += ng;
+        }
+        const int s = chunk * kThreads + threadIdx.x;
+        if (l < 0 || s >= S) continue;
+        uint32_t *tab = table + f / g.fpw;
+        const int shift = (f % g.fpw) * g.bits;
         float Rl[9], tl[3];
         {
             const float *lk = links + ((size_t)(f * J + l) * 12) * S + s;
@@ -168,8 +214,7 @@ __global__ void __launch_bounds__(kThreads) k_fk_bin(HandDev h, const float *__r
 #pragma unroll
             for (int e = 0; e < 3; ++e) tl[e] = __ldg(lk + (size_t)(9 + e) * S);
         }
-        const int me = s_lb[l + 1];
-        for (int m0 = s_lb[l]; m0 < me; m0 += kBatch) {
+        for (int m0 = mb; m0 < me; m0 += kBatch) {
             uint32_t *wp[kBatch];
             uint32_t bit[kBatch];
 #pragma unroll
@@ -195,9 +240,9 @@ __global__ void __launch_bounds__(kThreads) k_fk_bin(HandDev h, const float *__r
                         if (sc > best) { best = sc; bin = b; }
                     }
                 }
-                const unsigned ux = (unsigned)(cell_floor(x, g.inv_h, g.clamp) - lx);
-                const unsigned uy = (unsigned)(cell_floor(y, g.inv_h, g.clamp) - ly);
-                const unsigned uz = (unsigned)(cell_floor(z, g.inv_h, g.clamp) - lz);
+                const unsigned ux = bin_cell_offset(x, g.inv_h, base_x);
+                const unsigned uy = bin_cell_offset(y, g.inv_h, base_y);
+                const unsigned uz = bin_cell_offset(z, g.inv_h, base_z);
                 if (ux >= dx || uy >= dy || uz >= dz) {  // cannot happen: extents come from the same arithmetic
                     atomicOr(status, CF_DEV_BIN_RANGE);
                     continue;
@@ -205,9 +250,15 @@ __global__ void __launch_bounds__(kThreads) k_fk_bin(HandDev h, const float *__r
                 wp[i] = tab + (((size_t)uz * dy + uy) * dx + ux) * g.rw;
                 bit[i] = 1u << (shift + bin);
             }
+            // most contact vectors repeat a code that is already set (65,536 samples give ~14 vectors per
+            // distinct code on a 4-finger hand), so the word is read first and the update skipped when
+            // its bit is there
+            uint32_t cur[kBatch];
+#pragma unroll
+            for (int i = 0; i < kBatch; ++i) cur[i] = wp[i] ? table_peek(wp[i]) : 0xffffffffu;
 #pragma unroll
             for (int i = 0; i < kBatch; ++i)
-                if (wp[i]) atomicOr(wp[i], bit[i]);  // result unused: a reduction, no round trip
+                if (!(cur[i] & bit[i])) atomicOr(wp[i], bit[i]);  // result unused: a reduction, no round trip
         }
     }
 }
@@ -305,17 +356,42 @@ cudaError_t launch_fk_cell_bounds(const HandDev &h, const float *q, int S, float
     return cudaGetLastError();
 }
 
-cudaError_t launch_fk_bin(const HandDev &h, const float *links, int S, const FieldGeom &g, uint32_t *table,
-                          unsigned int *status, cudaStream_t st) {
-    if (S <= 0) return cudaSuccess;
-    const dim3 grid((S + kThreads - 1) / kThreads, h.F);
+template <int J, bool CAND>
+static cudaError_t launch_fk_bin_t(const HandDev &h, const float *links, int S, const FieldGeom &g, int G,
+                                   uint32_t *table, unsigned int *status, cudaStream_t st) {
     const size_t smem = sizeof(float) * 8 * h.M;
-    if (g.use_cand && g.B > 8) {
-        CF_J_DISPATCH(h.J, (k_fk_bin<JJ, true><<<grid, kThreads, smem, st>>>(h, links, S, g, table, status)));
-    } else {
-        CF_J_DISPATCH(h.J, (k_fk_bin<JJ, false><<<grid, kThreads, smem, st>>>(h, links, S, g, table, status)));
-    }
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t err;
+    if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
+    if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
+    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fk_bin<J, CAND>, kThreads, smem)) !=
+        cudaSuccess)
+        return err;
+    const long long items = (long long)h.F * G * ((S + kThreads - 1) / kThreads);
+    const int grid = (int)std::min<long long>(items, (long long)std::max(per_sm, 1) * sms);
+    k_fk_bin<J, CAND><<<grid, kThreads, smem, st>>>(h, links, S, g, G, table, status);
     return cudaGetLastError();
+}
+
+cudaError_t launch_fk_bin(const HandDev &h, const int *h_link_begin, const float *links, int S, const FieldGeom &g,
+                          uint32_t *table, unsigned int *status, cudaStream_t st) {
+    if (S <= 0) return cudaSuccess;
+    int G = 0;  // the most point groups of any finger
+    for (int f = 0; f < h.F; ++f) {
+        int n = 0;
+        for (int l = 0; l < h.J; ++l) {
+            const int c = h_link_begin[f * (h.J + 1) + l + 1] - h_link_begin[f * (h.J + 1) + l];
+            n += (c + kGroupPts - 1) / kGroupPts;
+        }
+        G = std::max(G, n);
+    }
+    if (G == 0) return cudaSuccess;
+    if (g.use_cand && g.B > 8) {
+        CF_J_DISPATCH(h.J, return (launch_fk_bin_t<JJ, true>(h, links, S, g, G, table, status, st)));
+    } else {
+        CF_J_DISPATCH(h.J, return (launch_fk_bin_t<JJ, false>(h, links, S, g, G, table, status, st)));
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_popcount(const uint32_t *table, long long words, unsigned long long *count, cudaStream_t st) {

@@ -162,8 +162,8 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 // ---------------------------------------------------------------------------
 cudaError_t launch_fk_cell_bounds(const HandDev &h, const float *q, int S, float inv_h, float clamp,
                                   int *bounds, float *links, cudaStream_t st);
-cudaError_t launch_fk_bin(const HandDev &h, const float *links, int S, const FieldGeom &g, uint32_t *table,
-                          unsigned int *status, cudaStream_t st);
+cudaError_t launch_fk_bin(const HandDev &h, const int *h_link_begin, const float *links, int S, const FieldGeom &g,
+                          uint32_t *table, unsigned int *status, cudaStream_t st);
 // ---- a6 / a7: reverse lookup + DLS IK, object SDF grid, realization ----------
 struct IkArgs {
     HandDev h;
