@@ -548,12 +548,13 @@ typedef struct cf_plan cf_plan;
  * up to n_fingers fingers, and prm's T and k.  Errors: CF_EINVAL, CF_ENOMEM. */
 int cf_plan_create(int32_t n_fingers, int32_t n_max, int32_t p_max, const cf_score_params *prm, cf_plan **out);
 
-/* One request against `field`: h_soa [6][n] (px..nz), h_poses [P][12] are copied to the device, domains,
+/* One request against `field`: h_soa [6][n] (px..nz), h_poses [P][12] are copied to the device (on a
+ * plan-owned stream, so the copies overlap work still queued on `stream`, such as the field build; the
+ * host buffers must not change until the call returns), domains,
  * tuples and margins computed, results copied back: h_tuples [P][T][k],
  * h_margin [P][T], h_accept [P][T] (each may be NULL), *h_n_accepted (counted
- * on the device).  Sampling and scoring run in up to 4 pose chunks; a chunk's
- * results are copied back on a plan-owned stream while the next chunk
- * computes, and every result equals that of one unchunked run.  Host buffers should be page-locked
+ * on the device).  The tuples are copied back while the scoring kernel runs,
+ * the margins and flags after it.  Host buffers should be page-locked
  * for full copy speed.  Synchronises `stream`. */
 int cf_plan_run_host(cf_plan *plan, const cf_field *field, const float *h_soa, int32_t n, const float *h_poses,
                      int32_t n_poses,

@@ -1275,10 +1275,10 @@ extern "C" int cf_autotune(const cf_batch_item *items, int32_t n_items, int32_t 
 // ---------------------------------------------------------------------------
 // plan: one object request from host buffers
 // ---------------------------------------------------------------------------
-// A plan samples and scores a request in up to kPlanChunks pose chunks: chunk
-// c's results are copied back on a second stream while chunk c + 1 computes.
-constexpr int kPlanChunks = 4;
-constexpr int kPlanChunkMinPoses = 1024;
+// A plan runs a request's query, sampling and scoring as one launch each; its
+// inputs go up, and its results come back, on a second stream: the tuples while
+// the scoring kernel runs, the margins and flags after it.
+constexpr int kPlanEvents = 2;  // tuples sampled; tuples scored
 
 struct cf_plan {
     int n_max = 0, p_max = 0, T = 0, k = 0, F = 0;
@@ -1287,11 +1287,11 @@ struct cf_plan {
     uint32_t *d_masks = nullptr, *d_counts = nullptr;
     int32_t *d_tuples = nullptr;
     uint8_t *d_fingers = nullptr, *d_accept = nullptr;
-    unsigned int *d_work = nullptr;         // one work counter per chunk
     unsigned long long *d_n_acc = nullptr;  // accepted tuples of the request
     unsigned long long *h_n_acc = nullptr;  // page-locked copy
     cudaStream_t copy_st = nullptr;
-    cudaEvent_t ev[kPlanChunks] = {};
+    cudaEvent_t ev[kPlanEvents] = {};
+    cudaEvent_t ev_in = nullptr;            // the request's inputs are on the device
 };
 
 extern "C" int cf_plan_create(int32_t n_fingers, int32_t n_max, int32_t p_max, const cf_score_params *prm,
@@ -1308,8 +1308,8 @@ extern "C" int cf_plan_create(int32_t n_fingers, int32_t n_max, int32_t p_max, c
     const size_t b_soa = al(sizeof(float) * 6 * n_max), b_pose = al(sizeof(float) * 12 * P),
                  b_mask = al(sizeof(uint32_t) * P * pl->F * W), b_cnt = al(sizeof(uint32_t) * P * pl->F),
                  b_tup = al(sizeof(int32_t) * PT * pl->k), b_fin = al(PT * pl->k), b_mar = al(sizeof(float) * PT),
-                 b_acc = al(PT), b_work = 256, b_nacc = 256;
-    const size_t total = b_soa + b_pose + b_mask + b_cnt + b_tup + b_fin + b_mar + b_acc + b_work + b_nacc;
+                 b_acc = al(PT), b_nacc = 256;
+    const size_t total = b_soa + b_pose + b_mask + b_cnt + b_tup + b_fin + b_mar + b_acc + b_nacc;
     cudaError_t e = cudaMalloc(&pl->d_block, total);
     if (e != cudaSuccess) { delete pl; return cuda_fail(e, "cudaMalloc(plan)"); }
     auto undo = [&](cudaError_t err, const char *what) {
@@ -1320,9 +1320,11 @@ extern "C" int cf_plan_create(int32_t n_fingers, int32_t n_max, int32_t p_max, c
         return undo(e, "cudaMallocHost(plan)");
     if ((e = cudaStreamCreateWithFlags(&pl->copy_st, cudaStreamNonBlocking)) != cudaSuccess)
         return undo(e, "cudaStreamCreate(plan)");
-    for (int c = 0; c < kPlanChunks; ++c)
+    for (int c = 0; c < kPlanEvents; ++c)
         if ((e = cudaEventCreateWithFlags(&pl->ev[c], cudaEventDisableTiming)) != cudaSuccess)
             return undo(e, "cudaEventCreate(plan)");
+    if ((e = cudaEventCreateWithFlags(&pl->ev_in, cudaEventDisableTiming)) != cudaSuccess)
+        return undo(e, "cudaEventCreate(plan)");
     char *p = (char *)pl->d_block;
     pl->d_soa = (float *)p; p += b_soa;
     pl->d_poses = (float *)p; p += b_pose;
@@ -1332,7 +1334,6 @@ extern "C" int cf_plan_create(int32_t n_fingers, int32_t n_max, int32_t p_max, c
     pl->d_fingers = (uint8_t *)p; p += b_fin;
     pl->d_margin = (float *)p; p += b_mar;
     pl->d_accept = (uint8_t *)p; p += b_acc;
-    pl->d_work = (unsigned int *)p; p += b_work;
     pl->d_n_acc = (unsigned long long *)p;
     *out = pl;
     return CF_OK;
@@ -1348,53 +1349,47 @@ extern "C" int cf_plan_run_host(cf_plan *pl, const cf_field *fd, const float *h_
     if (prm->n_tuples != pl->T || prm->k != pl->k) return fail(CF_EINVAL, "T / k differ from the plan's");
     if (prm->tuples_given) return fail(CF_EINVAL, "a plan samples its own tuples");
     cudaStream_t st = (cudaStream_t)stream;
-    if (n > 0) CF_TRY(cudaMemcpyAsync(pl->d_soa, h_soa, sizeof(float) * 6 * n, cudaMemcpyHostToDevice, st), "H2D points");
+    // the inputs go up on the copy stream, which holds no earlier work of the plan (each call ends by
+    // waiting for both streams), so they overlap whatever the caller's stream is still running (the
+    // field build); the query waits for them
+    if (n > 0)
+        CF_TRY(cudaMemcpyAsync(pl->d_soa, h_soa, sizeof(float) * 6 * n, cudaMemcpyHostToDevice, pl->copy_st),
+               "H2D points");
     if (n_poses > 0)
-        CF_TRY(cudaMemcpyAsync(pl->d_poses, h_poses, sizeof(float) * 12 * n_poses, cudaMemcpyHostToDevice, st),
-               "H2D poses");
-    CF_TRY(cudaMemsetAsync(pl->d_work, 0, sizeof(unsigned int) * kPlanChunks, st), "memset work");
+        CF_TRY(cudaMemcpyAsync(pl->d_poses, h_poses, sizeof(float) * 12 * n_poses, cudaMemcpyHostToDevice,
+                               pl->copy_st), "H2D poses");
+    CF_TRY(cudaEventRecord(pl->ev_in, pl->copy_st), "event record");
+    CF_TRY(cudaStreamWaitEvent(st, pl->ev_in, 0), "stream wait");
     CF_TRY(cudaMemsetAsync(pl->d_n_acc, 0, sizeof(unsigned long long), st), "memset accept count");
     cf_points obj{pl->d_soa, pl->d_soa + n, pl->d_soa + 2 * n, pl->d_soa + 3 * n, pl->d_soa + 4 * n,
                   pl->d_soa + 5 * n, n};
     const int F = fd->F, T = pl->T, k = pl->k;
-    const size_t W = (size_t)(n + 31) / 32;
-    const int chunks = n_poses >= kPlanChunks * kPlanChunkMinPoses ? kPlanChunks
-                                                                   : (n_poses >= 2 * kPlanChunkMinPoses ? 2 : 1);
-    // one query launch over all poses (a chunk's poses alone would not fill the GPU), then sampling and
-    // scoring by chunk
     int rc = cf_query_domains(fd, &obj, pl->d_poses, n_poses, pl->d_masks, pl->d_counts, stream);
     if (rc) return rc;
-    for (int c = 0; c < chunks; ++c) {
-        // the chunk's poses keep their request index in the tuple draws (pose_base), so the results do not
-        // depend on the chunking
-        const int p0 = (int)((int64_t)n_poses * c / chunks), p1 = (int)((int64_t)n_poses * (c + 1) / chunks);
-        const int np = p1 - p0;
-        ScoreArgs a;
-        const size_t t0 = (size_t)p0 * T;
-        rc = fill_score_args(&obj, F, pl->d_masks + (size_t)p0 * F * W, pl->d_counts + (size_t)p0 * F, np, prm,
-                             pl->d_tuples + t0 * k, pl->d_fingers + t0 * k, pl->d_margin + t0, pl->d_accept + t0, &a);
-        if (rc) return rc;
-        if (np > 0) {
-            a.work = pl->d_work + c;
-            a.pose_base = (uint32_t)p0;
-            a.n_accept = pl->d_n_acc;
-            CF_TRY(launch_score(a, st), "launch k_sample_tuples / k_score_tuples");
-        }
-        CF_TRY(cudaEventRecord(pl->ev[c], st), "event record");
-        CF_TRY(cudaStreamWaitEvent(pl->copy_st, pl->ev[c], 0), "stream wait");
-        const size_t pt = (size_t)np * T;
-        if (pt > 0) {
-            if (h_tuples)
-                CF_TRY(cudaMemcpyAsync(h_tuples + t0 * k, pl->d_tuples + t0 * k, sizeof(int32_t) * pt * k,
-                                       cudaMemcpyDeviceToHost, pl->copy_st), "D2H tuples");
-            if (h_margin)
-                CF_TRY(cudaMemcpyAsync(h_margin + t0, pl->d_margin + t0, sizeof(float) * pt, cudaMemcpyDeviceToHost,
-                                       pl->copy_st), "D2H margin");
-            if (h_accept)
-                CF_TRY(cudaMemcpyAsync(h_accept + t0, pl->d_accept + t0, pt, cudaMemcpyDeviceToHost, pl->copy_st),
-                       "D2H accept");
-        }
+    ScoreArgs a;
+    rc = fill_score_args(&obj, F, pl->d_masks, pl->d_counts, n_poses, prm, pl->d_tuples, pl->d_fingers, pl->d_margin,
+                         pl->d_accept, &a);
+    if (rc) return rc;
+    a.n_accept = pl->d_n_acc;
+    const size_t pt = (size_t)n_poses * T;
+    if (n_poses > 0) CF_TRY(launch_sample(a, st), "launch k_sample_tuples");
+    // the tuples (most of the result bytes) go back while the scoring kernel runs; margins and flags follow
+    CF_TRY(cudaEventRecord(pl->ev[0], st), "event record");
+    CF_TRY(cudaStreamWaitEvent(pl->copy_st, pl->ev[0], 0), "stream wait");
+    if (pt > 0 && h_tuples)
+        CF_TRY(cudaMemcpyAsync(h_tuples, pl->d_tuples, sizeof(int32_t) * pt * k, cudaMemcpyDeviceToHost, pl->copy_st),
+               "D2H tuples");
+    if (n_poses > 0) {
+        a.tuples_given = 1;  // sampled above
+        CF_TRY(launch_score(a, st), "launch k_score_lanes");
     }
+    CF_TRY(cudaEventRecord(pl->ev[1], st), "event record");
+    CF_TRY(cudaStreamWaitEvent(pl->copy_st, pl->ev[1], 0), "stream wait");
+    if (pt > 0 && h_margin)
+        CF_TRY(cudaMemcpyAsync(h_margin, pl->d_margin, sizeof(float) * pt, cudaMemcpyDeviceToHost, pl->copy_st),
+               "D2H margin");
+    if (pt > 0 && h_accept)
+        CF_TRY(cudaMemcpyAsync(h_accept, pl->d_accept, pt, cudaMemcpyDeviceToHost, pl->copy_st), "D2H accept");
     CF_TRY(cudaMemcpyAsync(pl->h_n_acc, pl->d_n_acc, sizeof(unsigned long long), cudaMemcpyDeviceToHost, pl->copy_st),
            "D2H accept count");
     CF_TRY(cudaStreamSynchronize(pl->copy_st), "plan copies");
@@ -1406,8 +1401,9 @@ extern "C" int cf_plan_run_host(cf_plan *pl, const cf_field *fd, const float *h_
 extern "C" int cf_plan_destroy(cf_plan *pl) {
     if (!pl) return CF_OK;
     if (pl->copy_st) cudaStreamSynchronize(pl->copy_st);
-    for (int c = 0; c < kPlanChunks; ++c)
+    for (int c = 0; c < kPlanEvents; ++c)
         if (pl->ev[c]) cudaEventDestroy(pl->ev[c]);
+    if (pl->ev_in) cudaEventDestroy(pl->ev_in);
     if (pl->copy_st) cudaStreamDestroy(pl->copy_st);
     if (pl->h_n_acc) cudaFreeHost(pl->h_n_acc);
     if (pl->d_block) cudaFree(pl->d_block);

@@ -254,10 +254,11 @@ def test_lp_shapes_parity(cf, k, K):
     assert cf.device_status() == 0
 
 
-def test_plan_chunked_host_path_equals_device_path(cf):
-    """4,096 poses run in four pose chunks with overlapped copies: tuples,
-    margins, accepts and the device-side accept count equal those of the
-    device-resident path (one launch per kernel)."""
+def test_plan_host_path_equals_device_path(cf):
+    """4,096 poses from host buffers, the tuples copied back while scoring
+    runs: tuples, margins, accepts and the device-side accept count equal
+    those of the device-resident path.  A second run without outputs still
+    returns the count."""
     w = synth.workload("tiny_sphere", P=4096)
     r = _gpu_path(cf, w)
     plan = cf.Plan(w.hand.F, w.obj.N, w.P, r["prm"])
