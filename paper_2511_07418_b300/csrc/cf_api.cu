@@ -222,6 +222,38 @@ int geom_from_params(cf_field *fd, const cf_field_params *prm) {
 }  // namespace
 
 namespace cf {
+cudaError_t launch_shape(const void *func, int threads, size_t smem, int *per_sm, int *sms) {
+    struct Entry {
+        int dev;
+        const void *func;
+        int threads;
+        size_t smem;
+        int per_sm, sms;
+    };
+    static std::mutex mu;
+    static std::vector<Entry> cache;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        for (const Entry &c : cache)
+            if (c.dev == dev && c.func == func && c.threads == threads && c.smem == smem) {
+                *per_sm = c.per_sm;
+                *sms = c.sms;
+                return cudaSuccess;
+            }
+    }
+    Entry c{dev, func, threads, smem, 0, 0};
+    if ((e = cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.per_sm, func, threads, smem)) != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    cache.push_back(c);
+    *per_sm = c.per_sm;
+    *sms = c.sms;
+    return cudaSuccess;
+}
+
 Tuning current_tuning() {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return kDefaultTuning;

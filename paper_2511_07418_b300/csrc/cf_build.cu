@@ -360,13 +360,9 @@ template <int J, bool CAND>
 static cudaError_t launch_fk_bin_t(const HandDev &h, const float *links, int S, const FieldGeom &g, int G,
                                    uint32_t *table, unsigned int *status, cudaStream_t st) {
     const size_t smem = sizeof(float) * 8 * h.M;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaError_t err;
-    if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
-    if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
-    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fk_bin<J, CAND>, kThreads, smem)) !=
-        cudaSuccess)
-        return err;
+    int sms = 0, per_sm = 0;
+    const cudaError_t err = launch_shape((const void *)k_fk_bin<J, CAND>, kThreads, smem, &per_sm, &sms);
+    if (err != cudaSuccess) return err;
     const long long items = (long long)h.F * G * ((S + kThreads - 1) / kThreads);
     const int grid = (int)std::min<long long>(items, (long long)std::max(per_sm, 1) * sms);
     k_fk_bin<J, CAND><<<grid, kThreads, smem, st>>>(h, links, S, g, G, table, status);

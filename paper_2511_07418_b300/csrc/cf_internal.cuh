@@ -285,6 +285,9 @@ struct QueryDesc {
 cudaError_t launch_query_batch(const FieldGeom &g0, const QueryDesc *d_descs, const FieldGeom *d_geoms, int n_desc,
                                int total_blocks, int ppb, cudaStream_t st);
 int query_blocks(int P, int ppb);  // grid blocks one object of P poses needs at ppb poses per block
+// The current device's SM count and the resident blocks per SM of kernel `func` at `threads` threads
+// and `smem` dynamic shared bytes, queried once per (device, kernel, shape) and then served from a cache.
+cudaError_t launch_shape(const void *func, int threads, size_t smem, int *per_sm, int *sms);
 constexpr int kMaxPosesPerBlock = 16;
 
 // Launch shapes picked by the autotuner (per device); results do not depend on them.

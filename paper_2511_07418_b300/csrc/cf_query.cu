@@ -15,8 +15,10 @@
 // and for each pose of the block transforms its point, loads the cell's record
 // (the bin sets of all fingers, one vector load from the L2-resident table),
 // bins the normal where the record is not empty and ballots the hits into the
-// F mask words of that (pose, word).  Counts are accumulated per (pose, finger)
-// in shared memory.
+// F mask words of that (pose, word).  When the block's poses x F fit in a warp,
+// lane p * F + f keeps the word of (pose p, finger f) and stores it once per word
+// index, adding its popcount to a register count; otherwise lanes 0..F-1 store
+// each pose's words.  Counts are summed per (pose, finger) in shared memory.
 // With theta-dilated bins (Sec. 4.3 leaf test -x^T n >= theta_hit) the query of
 // bin b hits when the cell holds any bin b' with d_b . d_b' >= cos(theta).
 //
@@ -78,7 +80,7 @@ struct QueryArgs {
 // are [descs[d].block0, descs[d + 1].block0)); its request and field geometry
 // are copied to shared memory.
 template <int F, int BITS, bool CAND, bool MULTI>
-__global__ void __launch_bounds__(kThreads) k_query_domains(const QueryArgs a) {
+__global__ void __launch_bounds__(kThreads, 5) k_query_domains(const QueryArgs a) {
     __shared__ __align__(16) float s_pose[kMaxPosesPerBlock][12];
     __shared__ unsigned s_cnt[kMaxPosesPerBlock][F];
     __shared__ float4 s_dir[CF_MAX_BINS];
@@ -130,7 +132,12 @@ __global__ void __launch_bounds__(kThreads) k_query_domains(const QueryArgs a) {
     const int B = g.B;
     const unsigned base_x = 0x4B400000u + (unsigned)g.lo[0], base_y = 0x4B400000u + (unsigned)g.lo[1],
                    base_z = 0x4B400000u + (unsigned)g.lo[2];
+    // with ppb * F <= 32 each lane keeps one (pose, finger) word of the block's poses: one store per
+    // word index and counts in registers
+    const bool own = np * F <= 32;
+    unsigned cnt = 0;
     for (int w = warp; w < W; w += kWarps) {
+        uint32_t owned = 0u;
         const int x = 32 * w + lane;
         const bool valid = x < N;
         const float px = valid ? __ldg(obj.px + x) : 0.f, py = valid ? __ldg(obj.py + x) : 0.f,
@@ -144,10 +151,6 @@ __global__ void __launch_bounds__(kThreads) k_query_domains(const QueryArgs a) {
             const float qx = xf_row(T0.x, T0.y, T0.z, T0.w, px, py, pz);
             const float qy = xf_row(T1.x, T1.y, T1.z, T1.w, px, py, pz);
             const float qz = xf_row(T2.x, T2.y, T2.z, T2.w, px, py, pz);
-            // contact-surface normal -(R n): exact negation of the rotated normal
-            const float mx = -rot_row(T0.x, T0.y, T0.z, nx, ny, nz);
-            const float my = -rot_row(T1.x, T1.y, T1.z, nx, ny, nz);
-            const float mz = -rot_row(T2.x, T2.y, T2.z, nx, ny, nz);
             const unsigned ux = cell_offset(qx, g.inv_h, base_x);
             const unsigned uy = cell_offset(qy, g.inv_h, base_y);
             const unsigned uz = cell_offset(qz, g.inv_h, base_z);
@@ -166,6 +169,10 @@ __global__ void __launch_bounds__(kThreads) k_query_domains(const QueryArgs a) {
             if (__any_sync(0xffffffffu, occ != 0u)) {
                 int bin = 0;
                 if (occ != 0u) {
+                    // contact-surface normal -(R n): exact negation of the rotated normal
+                    const float mx = -rot_row(T0.x, T0.y, T0.z, nx, ny, nz);
+                    const float my = -rot_row(T1.x, T1.y, T1.z, nx, ny, nz);
+                    const float mz = -rot_row(T2.x, T2.y, T2.z, nx, ny, nz);
                     if (CAND) {
                         bin = bin_by_candidates(mx, my, mz, s_cand, s_dir);
                     } else {
@@ -180,18 +187,26 @@ __global__ void __launch_bounds__(kThreads) k_query_domains(const QueryArgs a) {
                 }
                 const uint32_t dm = dilated ? s_dil[bin] : (1u << bin);  // the bins this query accepts
 #pragma unroll
+                const int lf = own ? lane - pi * F : lane;  // the finger whose word this lane keeps
                 for (int f = 0; f < F; ++f) {
                     const bool hit = ((rec[f / FPW] >> ((f % FPW) * BITS)) & dm) != 0u;
                     const uint32_t bal = __ballot_sync(0xffffffffu, hit);
-                    if (lane == f) mine = bal;
+                    if (lf == f) mine = bal;
                 }
             }
-            if (lane < F) {
+            if (own) {
+                if (lane - pi * F >= 0 && lane - pi * F < F) owned = mine;  // this lane's (pose, finger) word
+            } else if (lane < F) {
                 if (masks) masks[((size_t)(i0 + pi) * F + lane) * W + w] = mine;
                 if (mine) atomicAdd(&s_cnt[pi][lane], (unsigned)__popc(mine));
             }
         }
+        if (own && lane < np * F) {  // lane = pose * F + finger
+            if (masks) masks[((size_t)i0 * F + lane) * W + w] = owned;
+            cnt += (unsigned)__popc(owned);
+        }
     }
+    if (own && lane < np * F && cnt) atomicAdd(&s_cnt[lane / F][lane % F], cnt);
     __syncthreads();
     for (int e = threadIdx.x; e < np * F; e += kThreads) counts[(size_t)(i0 + e / F) * F + e % F] = s_cnt[e / F][e % F];
 }

@@ -1052,11 +1052,8 @@ template <int KT, bool MULTI>
 cudaError_t launch_score_lanes_k(const ScoreArgs &a, const ScoreArgs *descs, const long long *tuple0, int n_desc,
                                  long long total, cudaStream_t st) {
     cudaError_t err;
-    int dev = 0, sms = 0, per_sm = 0;
-    if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
-    if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
-    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_score_lanes<KT, MULTI>, kLaneThreads, 0)) !=
-        cudaSuccess)
+    int sms = 0, per_sm = 0;
+    if ((err = launch_shape((const void *)k_score_lanes<KT, MULTI>, kLaneThreads, 0, &per_sm, &sms)) != cudaSuccess)
         return err;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     if (a.bpsm > 0) per_sm = std::min(per_sm, a.bpsm);
