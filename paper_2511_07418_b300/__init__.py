@@ -249,12 +249,29 @@ def points_struct(soa):
 class Field:
     """Library-owned contact field (cf_field)."""
 
-    def __init__(self, handle: int):
+    def __init__(self, handle: int, n_fingers: int | None = None, n_joints: int | None = None):
         self._h = c_void_p(handle)
+        self._shape = (n_fingers, n_joints) if n_fingers is not None and n_joints is not None else None
 
     @property
     def handle(self):
         return self._h
+
+    def _fj(self):
+        """(fingers, joints) without waiting for the build: known from the hand when the field was built
+        here (info() waits for the build to finish, to report its time)."""
+        if self._shape is None:
+            inf = self.info()
+            self._shape = (int(inf.n_fingers), int(inf.n_joints))
+        return self._shape
+
+    @property
+    def n_fingers(self) -> int:
+        return self._fj()[0]
+
+    @property
+    def n_joints(self) -> int:
+        return self._fj()[1]
 
     def info(self) -> FieldInfo:
         inf = FieldInfo()
@@ -324,14 +341,13 @@ def build(hand, inv_h, bin_dirs, q, stream=None, want_rep: bool = False, dilate_
         raise ValueError(f"q must be [F={F}, J={J}, S]")
     h = c_void_p()
     _check(_cf_build(byref(hd), byref(prm), qp, int(q.shape[2]), _stream(stream), byref(h)))
-    return Field(h.value)
+    return Field(h.value, F, J)
 
 
 def query_domains(field: Field, soa, poses, masks=None, counts=None, want_masks: bool = True, stream=None):
     """cf_query_domains -> (masks [P, F, W] int32 view of uint32 words or None, counts [P, F] int32)."""
     import torch
-    inf = field.info()
-    F = int(inf.n_fingers)
+    F = field.n_fingers
     obj = points_struct(soa)
     P = int(poses.shape[0])
     _dev(poses, torch.float32, "poses")
@@ -463,7 +479,7 @@ class Batch:
 def batch_item(field: Field, soa, poses, prm: ScoreParams):
     """Allocate the outputs of one batch item (torch, on soa's device)."""
     import torch
-    F = int(field.info().n_fingers)
+    F = field.n_fingers
     P = int(poses.shape[0])
     W = (int(soa.shape[1]) + 31) // 32
     T, k = int(prm.n_tuples), int(prm.k)
@@ -617,8 +633,7 @@ def ik_dls(field: Field, soa, poses, T: int, k: int, tuples, fingers, accept, pr
     """cf_ik_dls over n = tuples.numel() // k slots -> dict of q [n,F,J] f32, used [n,F,J] u8,
     contacts [6, n*k] f32 (object frame), rtuples [n,k] i32, resid [n,k,2] f32, ok [n] u8."""
     import torch
-    inf = field.info()
-    F, J = int(inf.n_fingers), int(inf.n_joints)
+    F, J = field.n_fingers, field.n_joints
     obj = points_struct(soa)
     n = int(tuples.numel()) // int(k)
     dev = soa.device
