@@ -36,8 +36,10 @@ UNIT = "grasps/s"
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) per launch from the committed ncu captures of the
 # current kernels on this workload (profiles/k_score_lanes_hand16_superquadric.md,
-# profiles/k_query_domains_hand16_superquadric.md); None for other workloads.
-NCU_TRAFFIC = {"hand16_superquadric": {"k_query_domains": 2_196_736 + 11_403_008, "k_score_lanes": 6_722_560}}
+# profiles/k_query_domains_hand16_superquadric.md, profiles/k_fk_bin_hand16_superquadric.md); None for
+# other workloads.
+NCU_TRAFFIC = {"hand16_superquadric": {"k_query_domains": 2_217_984 + 10_959_360, "k_score_lanes": 6_725_376,
+                                       "k_fk_bin": 41_116_672 + 824_064}}
 
 
 def _args():
@@ -371,7 +373,8 @@ def run_ours(args):
     b_flop = F * w.S * w.hand.M * (18 + 3 + 3 * w.B) * 2
     traffic = NCU_TRAFFIC.get(w.name, {})
     kernels = {
-        "k_fk_cell_bounds+k_fk_bin": {"ms": per[0], "tflops": b_flop / (per[0] * 1e-3) / 1e12},
+        "k_fk_cell_bounds+k_fk_bin": {"ms": per[0], "tflops": b_flop / (per[0] * 1e-3) / 1e12,
+                                      "traffic_k_fk_bin": traffic.get("k_fk_bin")},
         "k_query_domains": {"ms": per[1], "tflops": q_flop / (per[1] * 1e-3) / 1e12,
                             "traffic": traffic.get("k_query_domains")},
         "k_sample_tuples": {"ms": per[2]},
