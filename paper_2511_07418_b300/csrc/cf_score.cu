@@ -639,7 +639,7 @@ __device__ __forceinline__ void contact_frame(const LaneObj &a, int x, float *ds
     const float px = __ldg(a.px + x), py = __ldg(a.py + x), pz = __ldg(a.pz + x);
     const float vx = -__ldg(a.nx + x), vy = -__ldg(a.ny + x), vz = -__ldg(a.nz + x);
     const float sgn = copysignf(1.f, vz);
-    const float aa = -1.f / (sgn + vz);
+    const float aa = -__frcp_rn(sgn + vz);  // = -1 / (sgn + vz), correctly rounded
     const float bb = vx * vy * aa;
     const float xx = 1.f + sgn * vx * vx * aa, xy = sgn * bb, xz = -sgn * vx;
     const float yx = bb, yy = sgn + vy * vy * aa, yz = -vy;
@@ -756,11 +756,16 @@ __global__ void __launch_bounds__(kLaneThreads) k_score_lanes(const ScoreArgs a,
 
         const int c0 = j * K, c1 = c0 + K;  // contact j's columns
         if (lp_start) {
+            // pi = c_B B^-1, c_B = 1 on the basic columns of contact j: 0 / 1 row weights through exact FMAs
+            // (fma(1, b, acc) rounds like acc + b, fma(0, b, acc) = acc)
+            float wr[kRows];
+#pragma unroll
+            for (int r = 0; r < kRows; ++r) wr[r] = (beta[r] >= c0 && beta[r] < c1) ? 1.f : 0.f;
 #pragma unroll
             for (int c = 0; c < kRows; ++c) {
                 float acc = 0.f;
 #pragma unroll
-                for (int r = 0; r < kRows; ++r) acc += (beta[r] >= c0 && beta[r] < c1) ? B[r][c] : 0.f;
+                for (int r = 0; r < kRows; ++r) acc = __fmaf_rn(wr[r], B[r][c], acc);
                 pi[c] = acc;
             }
             it = 0;
@@ -896,10 +901,10 @@ __global__ void __launch_bounds__(kLaneThreads) k_score_lanes(const ScoreArgs a,
                 const float al = dl * uu[r];
                 const bool bx = beta[r] < kK;
                 const float lo = bx ? 0.f : -1.f, hi = bx ? INFINITY : 1.f;
-                float t = INFINITY;
-                if (al > kPTol) t = __fdividef(fmaxf(xb[r] - lo, 0.f), al);
-                else if (al < -kPTol) t = __fdividef(fmaxf(hi - xb[r], 0.f), -al);
+                // rising basic variable (al > 0) meets its lower bound, a falling one its upper bound
                 const float aa = fabsf(al);
+                const float num = al > 0.f ? xb[r] - lo : hi - xb[r];
+                const float t = aa > kPTol ? __fdividef(fmaxf(num, 0.f), aa) : INFINITY;
                 bool take;
                 if (t < th) take = true;
                 else if (t > th || l == kRows || !(t < INFINITY)) take = false;
@@ -982,11 +987,11 @@ __global__ void __launch_bounds__(kLaneThreads) k_score_lanes(const ScoreArgs a,
             if (!unbounded) {
                 float sj = 0.f;
 #pragma unroll
-                for (int r = 0; r < kRows; ++r) sj += (beta[r] >= c0 && beta[r] < c1) ? xb[r] : 0.f;
+                for (int r = 0; r < kRows; ++r) sj = __fmaf_rn((beta[r] >= c0 && beta[r] < c1) ? 1.f : 0.f, xb[r], sj);
                 best_s = fmaxf(best_s, sj);
             }
             if (unbounded || best_s >= 1.f / kZeroExit || j + 1 == k) {
-                const float margin = unbounded ? 0.f : (best_s > 0.f ? __fdiv_rn(1.f, best_s) : INFINITY);
+                const float margin = unbounded ? 0.f : (best_s > 0.f ? __frcp_rn(best_s) : INFINITY);
                 float *mg = MULTI ? descs[od].margin : a.margin;
                 uint8_t *ac = MULTI ? descs[od].accept : a.accept;
                 const float eps = MULTI ? descs[od].eps : a.eps;
