@@ -119,7 +119,18 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_tuples(const ScoreArg
     const int i = MULTI ? s_i : (int)blockIdx.x;
     if (threadIdx.x < F) s_cnt[threadIdx.x] = a.counts[(size_t)i * F + threadIdx.x];
     const uint32_t *src = a.masks + (size_t)i * F * W;
-    for (int e = threadIdx.x; e < F * W; e += blockDim.x) s_mask[e] = src[e];
+    // stage the pose's F x W mask words: asynchronous 16-byte copies when the row block is 16-byte
+    // aligned (every load in flight before the first wait), word loads otherwise
+    const int FW = F * W;
+    const unsigned s_base = (unsigned)__cvta_generic_to_shared(s_mask);
+    if ((FW & 3) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0 && (s_base & 15u) == 0) {
+        for (int e = 4 * threadIdx.x; e < FW; e += 4 * blockDim.x)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s_base + 4u * (unsigned)e), "l"(src + e)
+                         : "memory");
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    } else {
+        for (int e = threadIdx.x; e < FW; e += blockDim.x) s_mask[e] = src[e];
+    }
     __syncthreads();
     // group sums: a warp popcounts 32 consecutive words of a row (one per lane, no bank conflicts)
     // and adds them in groups of kGroupWords lanes
