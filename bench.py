@@ -36,10 +36,10 @@ UNIT = "grasps/s"
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) per launch from the committed ncu captures of the
 # current kernels on this workload (profiles/k_score_lanes_hand16_superquadric.md,
-# profiles/k_query_domains_hand16_superquadric.md, profiles/k_fk_bin_hand16_superquadric.md); None for
-# other workloads.
-NCU_TRAFFIC = {"hand16_superquadric": {"k_query_domains": 2_217_984 + 10_959_360, "k_score_lanes": 6_725_376,
-                                       "k_fk_bin": 41_116_672 + 824_064}}
+# profiles/k_query_domains_hand16_superquadric.md, profiles/k_fk_bin_hand16_superquadric.md,
+# profiles/k_sample_tuples_hand16_superquadric.md); None for other workloads.
+NCU_TRAFFIC = {"hand16_superquadric": {"k_query_domains": 2_217_984 + 10_959_360, "k_score_lanes": 6_723_072,
+                                       "k_fk_bin": 41_116_672 + 824_064, "k_sample_tuples": 67_269_376 + 928_512}}
 
 
 def _args():
@@ -377,7 +377,7 @@ def run_ours(args):
                                       "traffic_k_fk_bin": traffic.get("k_fk_bin")},
         "k_query_domains": {"ms": per[1], "tflops": q_flop / (per[1] * 1e-3) / 1e12,
                             "traffic": traffic.get("k_query_domains")},
-        "k_sample_tuples": {"ms": per[2]},
+        "k_sample_tuples": {"ms": per[2], "traffic": traffic.get("k_sample_tuples")},
         "k_score_lanes": {"ms": per[3], "tflops": s_flop_own / (per[3] * 1e-3) / 1e12,
                           "traffic": traffic.get("k_score_lanes")},
     }
