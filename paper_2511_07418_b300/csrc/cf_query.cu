@@ -186,8 +186,8 @@ __global__ void __launch_bounds__(kThreads, 5) k_query_domains(const QueryArgs a
                     }
                 }
                 const uint32_t dm = dilated ? s_dil[bin] : (1u << bin);  // the bins this query accepts
-#pragma unroll
                 const int lf = own ? lane - pi * F : lane;  // the finger whose word this lane keeps
+#pragma unroll
                 for (int f = 0; f < F; ++f) {
                     const bool hit = ((rec[f / FPW] >> ((f % FPW) * BITS)) & dm) != 0u;
                     const uint32_t bal = __ballot_sync(0xffffffffu, hit);
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_query_domains(const QueryArgs a
                 }
             }
             if (own) {
-                if (lane - pi * F >= 0 && lane - pi * F < F) owned = mine;  // this lane's (pose, finger) word
+                owned |= mine;  // nonzero only on lane pi * F + f: this lane's (pose, finger) word
             } else if (lane < F) {
                 if (masks) masks[((size_t)(i0 + pi) * F + lane) * W + w] = mine;
                 if (mine) atomicAdd(&s_cnt[pi][lane], (unsigned)__popc(mine));
