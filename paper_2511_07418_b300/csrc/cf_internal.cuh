@@ -99,8 +99,16 @@ __device__ __forceinline__ int bin_by_candidates(float mx, float my, float mz, c
     // approximate reciprocal (relative error ~1e-7): the table's cells are enlarged by 1e-4 in u, v, so a
     // cell chosen from a slightly perturbed coordinate still lists the true bin
     const float inv = __fdividef(1.f, fmaxf(ax, fmaxf(ay, az)));
-    const int iu = min(max((int)__fmaf_rn(ma, inv * (0.5f * kCandG), 0.5f * kCandG), 0), kCandG - 1);
-    const int iv = min(max((int)__fmaf_rn(mb, inv * (0.5f * kCandG), 0.5f * kCandG), 0), kCandG - 1);
+    // the cell of c = ma / major in [-1, 1] (up to the reciprocal's error): c * G/2 + G/2 + 1.5 * 2^23,
+    // rounded toward zero, keeps the integer part in its low mantissa bits (an FMA, no conversion
+    // instruction); the clamp keeps c = +-1 (and a non-finite normal) inside the table.  Near a cell
+    // edge this may name the neighbouring cell, which lists the bin all the same (cells are enlarged by
+    // 1e-4)
+    const float sc = inv * (0.5f * kCandG);
+    const int iu =
+        min(max(__float_as_int(__fmaf_rz(ma, sc, 0.5f * kCandG + 12582912.0f)) - 0x4B400000, 0), kCandG - 1);
+    const int iv =
+        min(max(__float_as_int(__fmaf_rz(mb, sc, 0.5f * kCandG + 12582912.0f)) - 0x4B400000, 0), kCandG - 1);
     const uint32_t word = s_cand[(face * kCandG + iu) * kCandG + iv];
     const int cnt = (int)(word >> 24);
     // the first two candidates (ascending) without a branch: a one-candidate cell
