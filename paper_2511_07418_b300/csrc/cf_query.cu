@@ -187,9 +187,12 @@ __global__ void __launch_bounds__(kThreads, 5) k_query_domains(const QueryArgs a
                 }
                 const uint32_t dm = dilated ? s_dil[bin] : (1u << bin);  // the bins this query accepts
                 const int lf = own ? lane - pi * F : lane;  // the finger whose word this lane keeps
+                uint32_t dmf[FPW];  // the accepted bins at each finger's slot of a record word
+#pragma unroll
+                for (int q = 0; q < FPW; ++q) dmf[q] = dm << (q * BITS);
 #pragma unroll
                 for (int f = 0; f < F; ++f) {
-                    const bool hit = ((rec[f / FPW] >> ((f % FPW) * BITS)) & dm) != 0u;
+                    const bool hit = (rec[f / FPW] & dmf[f % FPW]) != 0u;
                     const uint32_t bal = __ballot_sync(0xffffffffu, hit);
                     if (lf == f) mine = bal;
                 }
