@@ -39,7 +39,7 @@ L2_FLUSH_BYTES = 256 << 20
 # profiles/k_query_domains_hand16_superquadric.md, profiles/k_fk_bin_hand16_superquadric.md,
 # profiles/k_sample_tuples_hand16_superquadric.md); None for other workloads.
 NCU_TRAFFIC = {"hand16_superquadric": {"k_query_domains": 2_243_328 + 11_180_800, "k_score_lanes": 6_723_072,
-                                       "k_fk_bin": 41_116_160 + 777_472, "k_sample_tuples": 67_269_376 + 928_512}}
+                                       "k_fk_bin": 41_115_392 + 737_536, "k_sample_tuples": 67_269_376 + 928_512}}
 
 
 def _args():

@@ -257,8 +257,8 @@ __global__ void __launch_bounds__(kThreads) k_fk_bin(HandDev h, const float *__r
 #pragma unroll
             for (int i = 0; i < kBatch; ++i) cur[i] = wp[i] ? table_peek(wp[i]) : 0xffffffffu;
 #pragma unroll
-            for (int i = 0; i < kBatch; ++i)
-                if (!(cur[i] & bit[i])) atomicOr(wp[i], bit[i]);  // result unused: a reduction, no round trip
+            for (int i = 0; i < kBatch; ++i)  // (an empty slot of a batch tail has no word: wp == nullptr)
+                if (wp[i] && !(cur[i] & bit[i])) atomicOr(wp[i], bit[i]);  // result unused: a reduction
         }
     }
 }

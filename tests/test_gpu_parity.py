@@ -339,6 +339,27 @@ def test_field_save_load_and_plan_host_path(cf, tmp_path):
     assert nacc == int(ha.sum())
 
 
+def test_field_with_ragged_link_point_counts(cf):
+    """Links holding point counts that are not multiples of the binning pass's 4-point batches (and
+    of its 16-point groups): the tail batches have empty slots.  The field equals the oracle's."""
+    import dataclasses
+    w = synth.workload("hand16_superquadric", P=8, N=512, S=3001)
+    h = w.hand
+    keep = []
+    for l in np.unique(h.surf_link[0]):
+        idx = np.nonzero(h.surf_link[0] == l)[0]
+        keep.extend(idx[: len(idx) - 1 - int(l) % 3].tolist())  # 31 / 29 / 47-style counts
+    keep = np.array(keep)
+    assert any(int(np.sum(h.surf_link[0][keep] == l)) % 4 for l in np.unique(h.surf_link[0]))
+    hr = dataclasses.replace(h, surf_p=np.ascontiguousarray(h.surf_p[:, keep]),
+                             surf_n=np.ascontiguousarray(h.surf_n[:, keep]),
+                             surf_link=np.ascontiguousarray(h.surf_link[:, keep]))
+    field = cf.build(hr, w.inv_h, w.bins, torch.from_numpy(w.q).cuda())
+    torch.cuda.synchronize()
+    check_field(field, oracle.Field(hr, w.q, w.inv_h, w.bins), hr.F)
+    assert cf.device_status() == 0
+
+
 def test_repeatable_bits(cf):
     w = synth.workload("hand16_superquadric", P=32, S=8192)
     a = _gpu_path(cf, w)
