@@ -222,6 +222,36 @@ int geom_from_params(cf_field *fd, const cf_field_params *prm) {
 }  // namespace
 
 namespace cf {
+// Page-locked buffers for cf_build's cell-bounds read-back (a copy into pageable memory goes through a
+// driver staging buffer and completes later): taken and returned under a lock, allocated on first need
+// and kept for the life of the process.
+std::mutex g_bnd_mu;
+std::vector<int *> g_bnd_free;
+constexpr int kBoundsInts = 6 * CF_MAX_FINGERS;
+
+struct BoundsBuffer {
+    int *p = nullptr;
+    BoundsBuffer() {
+        {
+            std::lock_guard<std::mutex> lk(g_bnd_mu);
+            if (!g_bnd_free.empty()) {
+                p = g_bnd_free.back();
+                g_bnd_free.pop_back();
+                return;
+            }
+        }
+        if (cudaHostAlloc((void **)&p, sizeof(int) * kBoundsInts, cudaHostAllocPortable) != cudaSuccess) {
+            cudaGetLastError();  // the caller falls back to pageable memory
+            p = nullptr;
+        }
+    }
+    ~BoundsBuffer() {
+        if (!p) return;
+        std::lock_guard<std::mutex> lk(g_bnd_mu);
+        g_bnd_free.push_back(p);
+    }
+};
+
 cudaError_t launch_shape(const void *func, int threads, size_t smem, int *per_sm, int *sms) {
     struct Entry {
         int dev;
@@ -361,8 +391,13 @@ extern "C" int cf_build(const cf_hand_desc *hand, const cf_field_params *prm, co
                 "launch k_fk_cell_bounds");
     }
     std::vector<int> bnd(n_bnd);
-    CF_STEP(cudaMemcpyAsync(bnd.data(), d_bounds, sizeof(int) * n_bnd, cudaMemcpyDeviceToHost, st), "copy bounds");
-    CF_STEP(cudaStreamSynchronize(st), "k_fk_cell_bounds");  // the table's size depends on these bounds
+    {
+        BoundsBuffer hb;  // page-locked when it can be had
+        int *dst = hb.p && n_bnd <= (size_t)kBoundsInts ? hb.p : bnd.data();
+        CF_STEP(cudaMemcpyAsync(dst, d_bounds, sizeof(int) * n_bnd, cudaMemcpyDeviceToHost, st), "copy bounds");
+        CF_STEP(cudaStreamSynchronize(st), "k_fk_cell_bounds");  // the table's size depends on these bounds
+        if (dst != bnd.data()) memcpy(bnd.data(), dst, sizeof(int) * n_bnd);
+    }
 
     // one box over all fingers' samples; per-finger tight bounds are kept for reporting
     FieldGeom &g = fd->geom;
