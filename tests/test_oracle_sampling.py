@@ -77,3 +77,24 @@ def test_rank_draw_is_uniform_over_a_domain():
     h = np.bincount(pts // 3, minlength=22)
     e = pts.size / 22
     assert ((h - e) ** 2 / e).sum() < 46.8  # chi-square df=21, 99.9%
+
+
+def test_finger_choice_is_a_uniform_ordered_k_subset():
+    """Sec. 5.3 draws k distinct fingers at random.  With all F = 5 domains
+    non-empty, every ordered triple of distinct fingers has probability
+    1 / (5 * 4 * 3).  A shuffle that swaps with any position (not only the
+    not-yet-chosen ones) still yields distinct fingers but puts up to 2.4x the
+    mass on some triples, which this chi-square test rejects."""
+    P, F, N, T, k = 4, 5, 64, 2000, 3
+    bits = np.zeros((P, F, 64), bool)
+    bits[:, :, 0] = True
+    masks = np.packbits(bits, axis=2, bitorder="little").view(np.uint32).copy()
+    counts = bits.sum(axis=2).astype(np.uint32)
+    _, fin = oracle.sample_tuples(masks, counts, N, T, k, seed=11)
+    code = (fin[..., 0].astype(int) * F + fin[..., 1]) * F + fin[..., 2]
+    h = np.bincount(code.ravel(), minlength=F ** 3)
+    triples = [(a * F + b) * F + c for a in range(F) for b in range(F) for c in range(F)
+               if len({a, b, c}) == 3]
+    assert h.sum() == h[triples].sum() == P * T
+    e = P * T / len(triples)
+    assert ((h[triples] - e) ** 2 / e).sum() < 98.3  # chi-square df=59, 99.9%
