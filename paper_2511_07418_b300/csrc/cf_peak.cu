@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "cf.h"
+#include "cf_internal.cuh"
 
 namespace cf {
 namespace {
@@ -30,11 +31,11 @@ __global__ void __launch_bounds__(kPeakThreads) k_fma_peak(float *out, int iters
 }  // namespace cf
 
 extern "C" int cf_fp32_peak(double *tflops) {
-    if (!tflops) return CF_EINVAL;
+    if (!tflops) return cf::fail(CF_EINVAL, "tflops is NULL");
     int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        return CF_ECUDA;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cf::cuda_fail(e, "cf_fp32_peak: device query");
     cudaStream_t st = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     float *out = nullptr;
@@ -59,5 +60,7 @@ extern "C" int cf_fp32_peak(double *tflops) {
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (st) cudaStreamDestroy(st);
+    if (rc != CF_OK) return cf::fail(rc, "cf_fp32_peak: the timed FMA launch failed (%s)",
+                                     cudaGetErrorString(cudaGetLastError()));
     return rc;
 }

@@ -54,3 +54,58 @@ def test_oracle_and_library_share_no_source():
     assert '#include "cf' not in s
     py = open(os.path.join(ROOT, "paper_2511_07418_b300", "__init__.py")).read()
     assert "import oracle" not in py and "from oracle" not in py
+
+
+def test_every_entry_point_rejects_missing_arguments_on_the_host():
+    """Null handles, null outputs and out-of-range launch shapes come back as
+    CF_EINVAL (a missing field file as CF_EIO) with a message, before any CUDA
+    work; destroying a NULL handle is a no-op that succeeds."""
+    import paper_2511_07418_b300 as cf
+    from ctypes import byref, c_int32, c_int64, c_uint64, c_void_p
+    out, n = c_void_p(), c_int32()
+    pts = cf.Points(None, None, None, None, None, None, 0)
+    bad_k = cf.score_params(T=4, k=7, mu=0.5, K=8, eps=0.01, centroid=[0, 0, 0], rho=0.05, seed=0)
+    calls = {
+        "cf_field_get_info": lambda: cf._cf_field_get_info(None, byref(cf.FieldInfo())),
+        "cf_field_copy_table": lambda: cf._cf_field_copy_table(None, None, 0),
+        "cf_field_save": lambda: cf._cf_field_save(None, b"unused"),
+        "cf_field_load": lambda: cf._cf_field_load(None, byref(out)),
+        "cf_field_rep_slots": lambda: cf._cf_field_rep_slots(None, byref(c_int64())),
+        "cf_sample_tuples": lambda: cf._cf_sample(byref(pts), 3, None, None, 1, byref(bad_k), None, None, None),
+        "cf_score_tuples_noalloc": lambda: cf._cf_score_noalloc(byref(pts), 3, None, None, 1, byref(bad_k),
+                                                                None, None, None, None, None),
+        "cf_batch_create": lambda: cf._cf_batch_create(None, 0, byref(out)),
+        "cf_batch_run": lambda: cf._cf_batch_run(None, None),
+        "cf_engine_create": lambda: cf._cf_engine_create(None, byref(out)),
+        "cf_engine_create(no fields)": lambda: cf._cf_engine_create(
+            byref(cf.EngineParams(None, 0, 1 << 30, 4, 1024, 4096)), byref(out)),
+        "cf_engine_submit": lambda: cf._cf_engine_submit(None, None, byref(c_uint64())),
+        "cf_engine_poll": lambda: cf._cf_engine_poll(None, None, 0, byref(n)),
+        "cf_plan_create": lambda: cf._cf_plan_create(0, 0, 0, None, byref(out)),
+        "cf_plan_run_host": lambda: cf._cf_plan_run_host(None, None, None, 0, None, 0, None, None, None, None,
+                                                         None, None),
+        "cf_ik_dls": lambda: cf._cf_ik_dls(None, None, None, 0, 0, 0, *([None] * 11)),
+        "cf_sdf_build": lambda: cf._cf_sdf_build(None, None, 0.0, None, None, byref(out)),
+        "cf_sdf_copy": lambda: cf._cf_sdf_copy(None, None, 0),
+        "cf_realize": lambda: cf._cf_realize(None, None, None, 0, 0, *([None] * 7)),
+        "cf_place": lambda: cf._cf_place(None, None, 0, None, None, None),
+        "cf_concave_filter": lambda: cf._cf_concave(None, None, 0.0, 0.0, None, None, None, None),
+        "cf_set_tuning(NULL)": lambda: cf._cf_set_tuning(None),
+        "cf_set_tuning(3 poses per block)": lambda: cf._cf_set_tuning(byref(cf.Tuning(3, 8, 0))),
+        "cf_set_tuning(refill 5)": lambda: cf._cf_set_tuning(byref(cf.Tuning(4, 5, 0))),
+        "cf_get_tuning": lambda: cf._cf_get_tuning(None),
+        "cf_autotune": lambda: cf._cf_autotune(None, 0, 1, None, None),
+        "cf_score_gswo": lambda: cf._cf_gswo(None, 0, None, 0, 0.0, None, None, None, None),
+        "cf_optimize_tuples": lambda: cf._cf_optimize(None, 0, None, 0, None, None, None, None, None, None, None),
+        "cf_fp32_peak": lambda: cf._cf_fp32_peak(None),
+        "cf_device_status": lambda: cf._cf_device_status(None),
+        "cf_device_counters": lambda: cf._cf_device_counters(None, 0),
+    }
+    for name, call in calls.items():
+        assert call() == 1, name
+        assert cf._cf_last_error(), name
+    assert cf._cf_field_load(b"/nonexistent/field.cf", byref(out)) == 7  # CF_EIO
+    assert "cannot open" in cf._cf_last_error().decode()
+    for destroy in (cf._cf_field_destroy, cf._cf_batch_destroy, cf._cf_engine_destroy, cf._cf_plan_destroy,
+                    cf._cf_sdf_destroy, cf._cf_engine_result_free):
+        assert destroy(None) == 0
