@@ -93,7 +93,7 @@ typedef struct cf_hand_desc {
 /* Field parameters.  Cells live on one global lattice: cell k covers
  * [k / inv_h, (k + 1) / inv_h) per axis, k = floor(x * inv_h) of the exact
  * product.  Normal bin of a unit vector v = argmax_b bin_dirs[b] . v (first
- * maximum), the fixed direction set of Sec. 4.3 "Memory Consumption". */
+ * maximum), the fixed direction set of Sec. 4.4 "Memory Consumption". */
 typedef struct cf_field_params {
     float inv_h;              /* 1 / voxel edge, cells per metre (> 0) */
     int32_t n_bins;           /* B, 1..CF_MAX_BINS */

@@ -7,7 +7,7 @@
 // normals that fall in it.  Here the grid cover is a dense per-finger table of
 // voxels on one global lattice (cell k = floor(x * inv_h)) and a box's normal
 // set is a B-bit word: bit b is set iff some sample in the cell has normal bin
-// b (the fixed-direction normal index of Sec. 4.3 "Memory Consumption").
+// b (the fixed-direction normal index of Sec. 4.4 "Memory Consumption").
 //
 // The table is one box of cells over all fingers; a cell's record holds the
 // bin sets of all fingers (finger f: bits (f % fpw) * bits .. of word f / fpw).

@@ -33,7 +33,7 @@ __all__ = [
 
 # ---------------------------------------------------------------------------
 # normal-bin directions (the fixed direction set that quantises normals;
-# Sec. 4.3 "Memory Consumption": normals become an index on a fixed sphere set)
+# Sec. 4.4 "Memory Consumption": normals become an index on a fixed sphere set)
 # ---------------------------------------------------------------------------
 
 def fibonacci_dirs(B: int) -> np.ndarray:
