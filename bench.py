@@ -88,8 +88,9 @@ class ClockSampler:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
                                           "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL,
                                          stderr=subprocess.DEVNULL)
-        except OSError:
+        except OSError:  # no nvidia-smi on this host: no clock record
             self.proc = None
+            os.unlink(self.path)
 
     def stop(self):
         if self.proc is None:
