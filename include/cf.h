@@ -148,9 +148,10 @@ typedef struct cf_score_params {
     int32_t tuples_given;  /* 1: d_tuples holds the tuples (sampling skipped) */
 } cf_score_params;
 
-/* ---- a1 + a2: build the field ------------------------------------------- */
+/* ---- the contact field (Def. Contact Field; Sec. 4.3, Alg. 1) ------------ */
 
-/* Build the sampled contact field of `hand` from n_samples joint
+/* Def. Contact Field (Point) and (Hand), Sec. 4.3 "Implementation", Alg. 1.
+ * Build the sampled contact field of `hand` from n_samples joint
  * configurations d_q [F][J][n_samples] (device, FP32, SoA per joint).
  * Every (finger, sample, surface point) contact vector is transformed to the
  * palm frame and sets bit bin(n) of its cell's word in the finger's table.
@@ -161,6 +162,7 @@ typedef struct cf_score_params {
 int cf_build(const cf_hand_desc *hand, const cf_field_params *prm, const float *d_q, int32_t n_samples,
              cf_stream stream, cf_field **out);
 
+/* Sizes, layout and build time of a field (waits for its build to finish). */
 int cf_field_get_info(const cf_field *field, cf_field_info *info);
 
 /* Copy the bit table (table_words uint32 words) to host memory. */
@@ -183,9 +185,10 @@ int cf_field_destroy(cf_field *field);
 int cf_field_save(const cf_field *field, const char *path);
 int cf_field_load(const char *path, cf_field **out);
 
-/* ---- a3: contact domains ------------------------------------------------- */
+/* ---- contact domains (Sec. 4.3 Object Contact Query; Sec. 5.3) ---------- */
 
-/* For every pose i (d_poses [P][12], object -> palm) and object point x, the
+/* Def. Contact Surface Representation, Sec. 4.3 "Object Contact Query",
+ * Sec. 5.3.  For every pose i (d_poses [P][12], object -> palm) and object point x, the
  * contact-surface vector (R p_x + t, -(R n_x)) is looked up in every finger's
  * table: bit x of d_masks[i][f][W] (W = ceil(N/32) words, bit x & 31 of word
  * x >> 5) is set iff its cell holds its normal bin.  Bits past N are 0.
@@ -194,9 +197,10 @@ int cf_field_load(const char *path, cf_field **out);
 int cf_query_domains(const cf_field *field, const cf_points *obj, const float *d_poses, int32_t n_poses,
                      uint32_t *d_masks, uint32_t *d_counts, cf_stream stream);
 
-/* ---- a4 + a5: tuple sampling and closure margin -------------------------- */
+/* ---- tuple sampling and closure margin (Sec. 5.3; Alg. 2; Eq. GSWO) ----- */
 
-/* Per pose i and tuple tau (u = i*T + tau): unless prm->tuples_given, choose k
+/* Sec. 5.3 and Alg. 2 (Random(D_i)) for the tuples, Eq. GSWO (Sec. 3.2),
+ * linearised, for the margin.  Per pose i and tuple tau (u = i*T + tau): unless prm->tuples_given, choose k
  * distinct fingers among those with d_counts[i][f] > 0 and one random point of
  * each domain (Philox4x32-10, key = seed, counter = (i, tau, draw/4, 0)); write
  * d_tuples [P][T][k] (point ids, -1 if fewer than k fingers are non-empty) and
@@ -206,8 +210,9 @@ int cf_query_domains(const cf_field *field, const cf_points *obj, const float *d
  * e_im = nu_i + mu (cos(2 pi m/K) x_i + sin(2 pi m/K) y_i), nu_i = -n_i,
  * (x_i, y_i) the Duff et al. 2017 basis of nu_i.  d_margin [P][T] (+inf when
  * invalid), d_accept [P][T] = margin <= eps.  d_masks / d_counts / d_fingers
- * may be NULL when tuples_given.  Scratch: a 4-byte tuple work counter,
- * allocated stream-ordered per call.  Errors: CF_EINVAL, CF_ENOMEM, CF_ECUDA. */
+ * may be NULL when tuples_given.  No global scratch: the scoring kernel
+ * hands out tuples from per-block shared-memory counters.  Errors: CF_EINVAL,
+ * CF_ECUDA (launch).  Asynchronous on `stream`. */
 int cf_score_tuples(const cf_points *obj, int32_t n_fingers, const uint32_t *d_masks, const uint32_t *d_counts,
                     int32_t n_poses, const cf_score_params *prm, int32_t *d_tuples, uint8_t *d_fingers,
                     float *d_margin, uint8_t *d_accept, cf_stream stream);
@@ -243,7 +248,7 @@ int cf_sample_tuples(const cf_points *obj, int32_t n_fingers, const uint32_t *d_
                      int32_t n_poses, const cf_score_params *prm, int32_t *d_tuples, uint8_t *d_fingers,
                      cf_stream stream);
 
-/* ---- a6: reverse lookup + damped-least-squares IK (Sec. 5.5) ------------- */
+/* ---- reverse lookup + damped-least-squares IK (Sec. 5.5) ---------------- */
 
 typedef struct cf_ik_params {
     float beta;         /* lever of the normal target (m): p~ + beta n~ -> p + beta n */
@@ -284,7 +289,7 @@ int cf_ik_dls(const cf_field *field, const cf_points *obj, const float *d_poses,
               const cf_ik_params *prm, float *d_q, uint8_t *d_used, float *d_contacts, int32_t *d_rtuples,
               float *d_resid, uint8_t *d_ok, cf_stream stream);
 
-/* ---- a7: object SDF grid and the realization filter (Sec. 5.6) ----------- */
+/* ---- object SDF grid and the realization filter (Sec. 5.6) -------------- */
 
 typedef struct cf_sdf cf_sdf;
 
@@ -364,7 +369,7 @@ int cf_optimize_tuples(const cf_points *obj, int32_t n_fingers, const uint32_t *
                        const cf_score_params *prm, const cf_opt_params *opt, int32_t *d_tuples,
                        const uint8_t *d_fingers, float *d_margin, uint8_t *d_accept, cf_stream stream);
 
-/* ---- many objects in one graph launch ------------------------------------ */
+/* ---- many objects in one graph launch (no paper counterpart) ------------ */
 
 /* One object request of a batch: the same inputs and caller-owned outputs as
  * cf_query_domains + cf_score_tuples (prm.tuples_given must be 0). */
@@ -442,7 +447,7 @@ int cf_place(const cf_field *field, const cf_points *obj, int32_t n_poses, const
 int cf_concave_filter(const cf_points *obj, const cf_sdf *sdf, float side, float tau, uint8_t *d_keep,
                       float *d_out, int32_t *d_n_out, cf_stream stream);
 
-/* ---- launch shapes and the autotuner ------------------------------------- */
+/* ---- launch shapes and the autotuner (no paper counterpart) ------------- */
 
 /* Launch shapes of the query and scoring kernels on the current device.  The
  * results of every call are the same under any shape; only the time changes.
@@ -466,7 +471,7 @@ int cf_set_tuning(const cf_tuning *tuning);
  * Errors: CF_EINVAL, CF_ENOMEM, CF_ECUDA. */
 int cf_autotune(const cf_batch_item *items, int32_t n_items, int32_t reps, cf_tuning *out, double *best_ms);
 
-/* ---- served form: continuous batching over arriving requests -------------- */
+/* ---- served form: continuous batching (no paper counterpart) ------------ */
 
 typedef struct cf_engine cf_engine;
 
@@ -540,7 +545,7 @@ int cf_engine_drain(cf_engine *eng, int32_t timeout_ms);
 /* Stops the worker after the current round; unfinished requests are dropped. */
 int cf_engine_destroy(cf_engine *eng);
 
-/* ---- one object request from host buffers -------------------------------- */
+/* ---- one object request from host buffers (no paper counterpart) -------- */
 
 typedef struct cf_plan cf_plan;
 
@@ -563,7 +568,7 @@ int cf_plan_run_host(cf_plan *plan, const cf_field *field, const float *h_soa, i
 
 int cf_plan_destroy(cf_plan *plan);
 
-/* ---- diagnostics --------------------------------------------------------- */
+/* ---- diagnostics (no paper counterpart) --------------------------------- */
 
 /* FP32 FMA throughput of the current device in TFLOP/s (2 flop per FMA),
  * measured by a kernel of independent FMA chains timed with CUDA events: the

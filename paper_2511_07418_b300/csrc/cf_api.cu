@@ -1479,7 +1479,7 @@ extern "C" int cf_plan_destroy(cf_plan *pl) {
 }
 
 // ---------------------------------------------------------------------------
-// a6: reverse lookup + DLS IK;  a7: object SDF grid and realization filter
+// reverse lookup + DLS IK (Sec. 5.5); object SDF grid and realization filter (Sec. 5.6)
 // ---------------------------------------------------------------------------
 
 extern "C" int cf_ik_dls(const cf_field *fd, const cf_points *obj, const float *d_poses, int32_t n_slots,

@@ -1,4 +1,4 @@
-// Contact-field build kernels (rows a1 + a2 of the hot path).
+// Contact-field build kernels (Def. Contact Field; Sec. 4.3 "Implementation", Alg. 1).
 //
 // Def. "Contact Field (Point)" / "Contact Field (Hand)": the field of a hand is
 // the set of contact vectors FK((p, n); i, q) of its surface points over the

@@ -172,7 +172,7 @@ cudaError_t launch_fk_cell_bounds(const HandDev &h, const float *q, int S, float
                                   int *bounds, float *links, cudaStream_t st);
 cudaError_t launch_fk_bin(const HandDev &h, const int *h_link_begin, const float *links, int S, const FieldGeom &g,
                           uint32_t *table, unsigned int *status, cudaStream_t st);
-// ---- a6 / a7: reverse lookup + DLS IK, object SDF grid, realization ----------
+// ---- reverse lookup + DLS IK (Sec. 5.5), object SDF grid, realization (Sec. 5.6) ----
 struct IkArgs {
     HandDev h;
     FieldGeom g;

@@ -1,4 +1,4 @@
-// Kinematics optimisation and post-processing (rows a6, a7 of the path).
+// Kinematics optimisation and post-processing (Sec. 5.5, Sec. 5.6).
 //
 // k_ik_dls (Sec. 5.5 "Kinematics Optimization"): for every contact of an
 // accepted tuple, the reverse lookup finds the hand-surface sample that put

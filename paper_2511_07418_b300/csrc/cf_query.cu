@@ -1,4 +1,4 @@
-// Contact-domain query kernel (row a3 of the hot path).
+// Contact-domain query kernel (Def. Contact Surface Representation; Sec. 4.3 "Object Contact Query"; Sec. 5.3).
 //
 // Def. "Contact Surface Representation": an object contributes the vectors
 // (p, -n) of its surface points; Sec. 4.2 defines the contact domain as the

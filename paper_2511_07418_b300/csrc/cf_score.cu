@@ -1,4 +1,4 @@
-// Tuple sampling + closure margin kernels (rows a4 + a5 of the hot path).
+// Tuple sampling + closure margin kernels (Sec. 5.3, Alg. 2 Random(D_i); Eq. GSWO, Sec. 3.2).
 //
 // Sec. 5.3: a k-contact grasp takes k contact domains of different fingers
 // (independent dependency groups) chosen at random; Alg. 2 starts from
