@@ -5,6 +5,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -109,3 +110,33 @@ def test_every_entry_point_rejects_missing_arguments_on_the_host():
     for destroy in (cf._cf_field_destroy, cf._cf_batch_destroy, cf._cf_engine_destroy, cf._cf_plan_destroy,
                     cf._cf_sdf_destroy, cf._cf_engine_result_free):
         assert destroy(None) == 0
+
+
+def test_binding_without_the_library_fails_loudly(tmp_path):
+    """The package has no CPU path: a copy of the binding without libcf.so
+    refuses to import."""
+    import shutil
+    import subprocess
+    import sys
+    pkg = tmp_path / "cfcopy"
+    pkg.mkdir()
+    shutil.copy(os.path.join(ROOT, "paper_2511_07418_b300", "__init__.py"), pkg / "__init__.py")
+    r = subprocess.run([sys.executable, "-c", "import cfcopy"], cwd=tmp_path, capture_output=True, text=True,
+                       timeout=120)
+    assert r.returncode != 0
+    assert "ImportError" in r.stderr and "no CPU path" in r.stderr
+
+
+def test_binding_rejects_host_tensors():
+    """Device tensors only: host tensors, wrong dtypes and wrong shapes are
+    refused before any library call."""
+    import torch
+    import paper_2511_07418_b300 as cf
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        cf.points_struct(torch.zeros(6, 64))
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        cf.points_struct(np.zeros((6, 64), np.float32))
+    prm = cf.score_params(T=4, k=3, mu=0.5, K=8, eps=0.01, centroid=[0, 0, 0], rho=0.05, seed=0)
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        cf.score_tuples(torch.zeros(6, 64), 3, torch.zeros(2, 3, 2, dtype=torch.int32),
+                        torch.zeros(2, 3, dtype=torch.int32), prm)
