@@ -584,6 +584,16 @@ int cf_device_status(uint32_t *status);
  * [0] LP pivots performed, [1] LPs solved, [2] tuples scored. */
 int cf_device_counters(uint64_t counters[3], int reset);
 
+/* Device memory of the library's stream-ordered pool on the current device,
+ * from which every library-owned buffer (fields, batches, requests, temporary
+ * work lists) is drawn: usage[0] bytes in use now, usage[1] bytes reserved
+ * from the driver, usage[2] the largest use since the last reset.
+ * reset_high != 0 restarts that high-water mark at the current use (after
+ * reading it).  The first call on a device creates the pool.  Synchronous
+ * with respect to nothing: allocations still queued on a stream count once
+ * they run.  The paper has no counterpart.  Errors: CF_EINVAL, CF_ECUDA. */
+int cf_pool_usage(uint64_t usage[3], int reset_high);
+
 #ifdef __cplusplus
 }
 #endif

@@ -34,6 +34,11 @@ _lib = ctypes.CDLL(LIB_PATH)
 CF_MAX_FINGERS = 8
 CF_MAX_BINS = 32
 CF_OK = 0
+CF_EINVAL = 1
+CF_ENOMEM = 2
+CF_ECUDA = 3
+CF_ETIMEOUT = 4
+CF_EBUSY = 5
 CF_DEV_LP_PIVOT_CAP = 0x1
 CF_DEV_LP_UNBOUNDED = 0x2
 CF_DEV_REP_FULL = 0x4
@@ -193,10 +198,11 @@ _cf_optimize = _sig("cf_optimize_tuples", [POINTER(Points), c_int32, c_void_p, c
 _cf_last_error = _sig("cf_last_error", [], c_char_p)
 _cf_device_status = _sig("cf_device_status", [POINTER(c_uint32)])
 _cf_device_counters = _sig("cf_device_counters", [POINTER(c_uint64), c_int])
+_cf_pool_usage = _sig("cf_pool_usage", [POINTER(c_uint64), c_int])
 
 EXPORTED = ["cf_build", "cf_field_get_info", "cf_field_copy_table", "cf_field_destroy", "cf_field_save",
             "cf_field_load", "cf_query_domains", "cf_score_tuples", "cf_plan_create", "cf_plan_run_host",
-            "cf_plan_destroy", "cf_last_error", "cf_device_status", "cf_device_counters", "cf_score_tuples_noalloc",
+            "cf_plan_destroy", "cf_last_error", "cf_device_status", "cf_device_counters", "cf_pool_usage", "cf_score_tuples_noalloc",
             "cf_sample_tuples", "cf_batch_create", "cf_batch_run", "cf_batch_launches", "cf_batch_destroy",
             "cf_engine_create", "cf_engine_submit", "cf_engine_poll", "cf_engine_result_free", "cf_engine_get_stats",
             "cf_engine_drain", "cf_engine_destroy", "cf_field_rep_slots", "cf_field_copy_rep", "cf_ik_dls",
@@ -244,6 +250,34 @@ def points_struct(soa):
     base = soa.data_ptr()
     step = 4 * n
     return Points(*[c_void_p(base + r * step) for r in range(6)], n)
+
+
+def _check_score_shapes(soa, n_fingers, masks, counts, prm, P, tuples=None, fingers=None, margin=None, accept=None):
+    """Shapes and devices of the scoring calls' tensors, checked before any
+    launch: the C side receives bare pointers and cannot see an undersized
+    buffer, which the kernels would overrun."""
+    T, k = int(prm.n_tuples), int(prm.k)
+    if soa.dim() != 2 or soa.shape[0] != 6:
+        raise ValueError("soa must be [6, N]")
+    N = int(soa.shape[1])
+    W = (N + 31) // 32
+    want = {"tuples": (P, T, k), "fingers": (P, T, k), "margin": (P, T), "accept": (P, T)}
+    if not prm.tuples_given:
+        F = int(n_fingers)
+        want["counts"] = (P, F)
+        want["masks"] = (P, F, W)
+    given = {"tuples": tuples, "fingers": fingers, "margin": margin, "accept": accept, "counts": counts,
+             "masks": masks}
+    for name, shape in want.items():
+        t = given[name]
+        if t is None:
+            if name in ("counts", "masks"):
+                raise ValueError(f"{name} is required when tuples are sampled")
+            continue
+        if tuple(t.shape) != shape:
+            raise ValueError(f"{name} must be {list(shape)}, got {list(t.shape)}")
+        if t.device != soa.device:
+            raise ValueError(f"{name} is on {t.device}, soa on {soa.device}")
 
 
 class Field:
@@ -382,6 +416,7 @@ def score_tuples(soa, n_fingers: int, masks, counts, prm: ScoreParams, tuples=No
     else:
         P = int(counts.shape[0])
     T, k = int(prm.n_tuples), int(prm.k)
+    _check_score_shapes(soa, n_fingers, masks, counts, prm, P, tuples, fingers)
     if tuples is None:
         tuples = torch.empty((P, T, k), dtype=torch.int32, device=dev)
     if fingers is None and not prm.tuples_given:
@@ -402,6 +437,7 @@ def sample_tuples(soa, n_fingers: int, masks, counts, prm: ScoreParams, tuples=N
     obj = points_struct(soa)
     P = int(counts.shape[0])
     T, k = int(prm.n_tuples), int(prm.k)
+    _check_score_shapes(soa, n_fingers, masks, counts, prm, P, tuples, fingers)
     if tuples is None:
         tuples = torch.empty((P, T, k), dtype=torch.int32, device=soa.device)
     if fingers is None:
@@ -419,8 +455,9 @@ def score_tuples_noalloc(soa, n_fingers: int, masks, counts, prm: ScoreParams, t
     (its work counter lives in a library-wide device array; calls that overlap
     on the GPU must be serialised by the caller)."""
     import torch
-    obj = points_struct(soa)
     P = int(tuples.shape[0])
+    _check_score_shapes(soa, n_fingers, masks, counts, prm, P, tuples, fingers, margin, accept)
+    obj = points_struct(soa)
     mp = _dev(masks, torch.int32, "masks") if masks is not None else None
     cp = _dev(counts, torch.int32, "counts") if counts is not None else None
     fp = _dev(fingers, torch.uint8, "fingers") if fingers is not None else None
@@ -790,3 +827,11 @@ def device_counters(reset: bool = False):
     v = (c_uint64 * 3)()
     _check(_cf_device_counters(v, 1 if reset else 0))
     return {"lp_pivots": int(v[0]), "lps": int(v[1]), "tuples_scored": int(v[2])}
+
+
+def pool_usage(reset_high: bool = False):
+    """cf_pool_usage: bytes of the library's device pool in use, reserved, and
+    the high-water mark of use since the last reset."""
+    v = (c_uint64 * 3)()
+    _check(_cf_pool_usage(v, 1 if reset_high else 0))
+    return {"used": int(v[0]), "reserved": int(v[1]), "high": int(v[2])}

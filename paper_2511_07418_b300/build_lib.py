@@ -4,6 +4,7 @@ Usage: python paper_2511_07418_b300/build_lib.py [--force] [--verbose]
 """
 from __future__ import annotations
 
+import concurrent.futures
 import os
 import subprocess
 import sys
@@ -32,14 +33,19 @@ def build(force: bool = False, verbose: bool = False) -> str:
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INC_DIR, "-I", SRC_DIR]
     if verbose:
         common += ["-Xptxas", "-v"]
-    for src in SOURCES:
+    def compile_one(src):
         obj = os.path.join(BUILD_DIR, os.path.splitext(src)[0] + ".o")
         cmd = [NVCC, *common, "-c", os.path.join(SRC_DIR, src), "-o", obj]
-        r = subprocess.run(cmd, capture_output=True, text=True)
+        return src, obj, subprocess.run(cmd, capture_output=True, text=True)
+
+    # the translation units are independent: compile them concurrently
+    with concurrent.futures.ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 1)) as ex:
+        results = list(ex.map(compile_one, SOURCES))
+    for src, obj, r in results:
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")
         if verbose and r.stderr:
-            sys.stderr.write(r.stderr)
+            sys.stderr.write(f"--- {src}\n{r.stderr}")
         objs.append(obj)
     tmp = LIB + f".tmp{os.getpid()}"
     r = subprocess.run([NVCC, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs], capture_output=True, text=True)

@@ -673,6 +673,9 @@ int fill_score_args(const cf_points *obj, int32_t F, const uint32_t *d_masks, co
         return fail(CF_EINVAL, "n_edges=%d not in [3,%d]", prm->n_edges, CF_MAX_EDGES);
     if (prm->k * prm->n_edges > 32) return fail(CF_EINVAL, "k * n_edges = %d > 32", prm->k * prm->n_edges);
     if (prm->n_tuples < 1) return fail(CF_EINVAL, "n_tuples < 1");
+    // the kernels index tuples with 32-bit counters
+    if ((long long)P * prm->n_tuples >= (1LL << 32))
+        return fail(CF_EINVAL, "n_poses * n_tuples = %lld >= 2^32", (long long)P * prm->n_tuples);
     if (!(prm->mu >= 0.f) || !isfinite(prm->mu)) return fail(CF_EINVAL, "mu must be finite and >= 0");
     if (!(prm->rho > 0.f) || !isfinite(prm->rho)) return fail(CF_EINVAL, "rho must be finite and > 0");
     if (P > 0 && (!d_tuples || !d_margin || !d_accept)) return fail(CF_EINVAL, "output pointer is NULL");
@@ -1676,6 +1679,25 @@ extern "C" int cf_device_counters(uint64_t counters[3], int reset) {
     if (reset) {
         const unsigned long long z[3] = {0, 0, 0};
         CF_TRY(cudaMemcpy(ds.counters, z, sizeof z, cudaMemcpyHostToDevice), "reset counters");
+    }
+    return CF_OK;
+}
+
+extern "C" int cf_pool_usage(uint64_t usage[3], int reset_high) {
+    if (!usage) return fail(CF_EINVAL, "NULL argument");
+    cudaMemPool_t pool;
+    int rc = device_pool(&pool);
+    if (rc) return rc;
+    unsigned long long used = 0, reserved = 0, high = 0;  // the attributes are 64-bit
+    CF_TRY(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used), "pool used");
+    CF_TRY(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved), "pool reserved");
+    CF_TRY(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &high), "pool high-water");
+    usage[0] = used;
+    usage[1] = reserved;
+    usage[2] = high;
+    if (reset_high) {
+        unsigned long long zero = 0;  // the high-water mark restarts at the current use
+        CF_TRY(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero), "reset pool high-water");
     }
     return CF_OK;
 }

@@ -140,3 +140,51 @@ def test_binding_rejects_host_tensors():
     with pytest.raises(TypeError, match="CUDA tensor"):
         cf.score_tuples(torch.zeros(6, 64), 3, torch.zeros(2, 3, 2, dtype=torch.int32),
                         torch.zeros(2, 3, dtype=torch.int32), prm)
+
+
+def test_scoring_wrappers_reject_bad_shapes_before_any_launch():
+    """Every scoring wrapper checks the shapes of the tensors it passes on (the
+    C side sees bare pointers): tuples / fingers [P, T, k], margin / accept
+    [P, T], counts [P, F] and masks [P, F, ceil(N/32)] when sampling.  The
+    check runs first, so host tensors suffice to exercise it."""
+    import torch
+    import paper_2511_07418_b300 as cf
+    P, T, k, F, N = 3, 4, 3, 4, 70
+    W = (N + 31) // 32
+    soa = torch.zeros(6, N)
+    prm = cf.score_params(T=T, k=k, mu=0.5, K=8, eps=0.01, centroid=[0, 0, 0], rho=0.05, seed=0)
+    good = dict(masks=torch.zeros(P, F, W, dtype=torch.int32), counts=torch.zeros(P, F, dtype=torch.int32),
+                tuples=torch.zeros(P, T, k, dtype=torch.int32), fingers=torch.zeros(P, T, k, dtype=torch.uint8),
+                margin=torch.zeros(P, T), accept=torch.zeros(P, T, dtype=torch.uint8))
+    bad = {"masks": torch.zeros(P, F, W - 1, dtype=torch.int32), "counts": torch.zeros(P, F + 1, dtype=torch.int32),
+           "tuples": torch.zeros(P, T, k - 1, dtype=torch.int32), "fingers": torch.zeros(P, T - 1, k, dtype=torch.uint8),
+           "margin": torch.zeros(P, T + 1), "accept": torch.zeros(P - 1, T, dtype=torch.uint8)}
+    for name, t in bad.items():
+        args = dict(good)
+        args[name] = t
+        with pytest.raises(ValueError, match=name):
+            cf.score_tuples_noalloc(soa, F, args["masks"], args["counts"], prm, args["tuples"], args["fingers"],
+                                    args["margin"], args["accept"])
+    with pytest.raises(ValueError, match="counts is required"):
+        cf.score_tuples_noalloc(soa, F, None, None, prm, good["tuples"], good["fingers"], good["margin"],
+                                good["accept"])
+    # shapes right: the next check (device tensors only) speaks
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        cf.score_tuples_noalloc(soa, F, **{k_: v for k_, v in good.items() if k_ not in ("masks", "counts")},
+                                masks=good["masks"], counts=good["counts"], prm=prm)
+
+
+def test_scoring_rejects_tuple_counts_beyond_32_bits():
+    """n_poses * n_tuples >= 2^32 is refused with CF_EINVAL before any launch
+    (the kernels count tuples in 32 bits); the pointers are never touched."""
+    import paper_2511_07418_b300 as cf
+    from ctypes import byref, c_void_p
+    fake = [c_void_p(256 * (i + 1)) for i in range(6)]
+    pts = cf.Points(*fake, 64)
+    prm = cf.score_params(T=1 << 16, k=3, mu=0.5, K=8, eps=0.01, centroid=[0, 0, 0], rho=0.05, seed=0,
+                          tuples_given=True)
+    p = c_void_p(4096)
+    for fn in (cf._cf_score, cf._cf_score_noalloc):
+        rc = fn(byref(pts), 4, None, None, 1 << 16, byref(prm), p, None, p, p, None)
+        assert rc == cf.CF_EINVAL
+        assert "2^32" in cf._cf_last_error().decode()
