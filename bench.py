@@ -30,14 +30,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD = "hand16_superquadric"
+WORKLOAD = "hand20_tool"
 METRIC = "valid grasps/s"
 UNIT = "grasps/s"
 L2_FLUSH_BYTES = 256 << 20
-# DRAM bytes (read + write) per launch from the committed ncu captures of the
-# current kernels on this workload (profiles/k_score_lanes_hand16_superquadric.md,
-# profiles/k_query_domains_hand16_superquadric.md, profiles/k_fk_bin_hand16_superquadric.md,
-# profiles/k_sample_tuples_hand16_superquadric.md); None for other workloads.
+# DRAM bytes (read + write) per launch of each kernel, from one ncu capture of
+# the current kernels per workload (dram__bytes_read.sum + dram__bytes_write.sum);
+# a workload or kernel without a capture of its current code reports None.
 NCU_TRAFFIC = {"hand16_superquadric": {"k_query_domains": 2_243_328 + 11_180_800, "k_score_lanes": 6_723_072,
                                        "k_fk_bin": 41_115_392 + 737_536, "k_sample_tuples": 67_269_376 + 928_512}}
 
@@ -58,6 +57,11 @@ def _args():
     ap.add_argument("--realized-steps", type=int, default=20, help="steps of the IK + realization leg (0: skip)")
     ap.add_argument("--optimized-steps", type=int, default=5, help="steps of the Alg. 2 optimisation leg (0: skip)")
     ap.add_argument("--gswo-steps", type=int, default=10, help="steps of the Eq. GSWO scoring leg (0: skip)")
+    ap.add_argument("--extra-workload", default="hand16_superquadric",
+                    help="a second workload whose main step is reported under its own key ('' to skip)")
+    ap.add_argument("--extra-steps", type=int, default=100)
+    ap.add_argument("--parity-poses", type=int, default=4,
+                    help="poses of the timed step checked against the FP64 oracle (0: skip)")
     return ap.parse_args()
 
 
@@ -149,6 +153,8 @@ def oracle_sample(w, n_poses: int, single_core: bool = False, fd=None):
     """The oracle on a bounded sample: field build (once per hand) and the
     per-pose path on the first n_poses poses.  Returns the sample's timings.
     single_core: one OpenMP thread and no LP process pool."""
+    import numpy as np
+
     import oracle
     n_threads = oracle.num_threads()
     if single_core:
@@ -163,13 +169,54 @@ def oracle_sample(w, n_poses: int, single_core: bool = False, fd=None):
         t1 = time.perf_counter()
         masks, counts = fd.query(soa, poses)
         tup, _ = oracle.sample_tuples(masks, counts, w.obj.N, w.T, w.k, w.seed)
-        mar, acc, _ = oracle.score_tuples(soa, tup, w.mu, w.K, w.obj.centroid, w.obj.rho, w.eps,
-                                          workers=not single_core)
+        mar, acc, its = oracle.score_tuples(soa, tup, w.mu, w.K, w.obj.centroid, w.obj.rho, w.eps,
+                                            workers=not single_core)
         t_pose = time.perf_counter() - t1
     finally:
         oracle.set_threads(n_threads)
+    valid = np.isfinite(mar)
     return {"t_build": t_build, "t_pose": t_pose, "accepted": int(acc.sum()), "n_poses": n_poses,
-            "cores": 1 if single_core else max(n_threads, os.cpu_count() or 1), "field": fd}
+            "cores": 1 if single_core else max(n_threads, os.cpu_count() or 1), "field": fd,
+            "lp_iterations_per_tuple": float(its[valid].mean()) if valid.any() else None}
+
+
+def parity_leg(w, masks, counts, tuples, margin, accept, n_poses: int = 4):
+    """The timed step's outputs on its first n_poses poses against the FP64
+    oracle: mask entries that differ (each must lie inside the 1e-5 m / 1e-6
+    band) and entries inside the band, then tuples on the poses whose masks
+    agree and their margins and accept decisions.  Counts only; the GPU tests
+    assert the rule."""
+    import numpy as np
+
+    import oracle
+    t0 = time.perf_counter()
+    fd = oracle.Field(w.hand, w.q, w.inv_h, w.bins, band=True)
+    soa = w.obj.soa()
+    om, oc, amb = fd.query(soa, w.poses[:n_poses], amb=True)
+    N = w.obj.N
+    gm = masks[:n_poses].cpu().numpy().view(np.uint32)
+    unpack = lambda m: np.unpackbits(np.ascontiguousarray(m).view(np.uint8), bitorder="little").reshape(
+        m.shape[0], m.shape[1], -1)[:, :, :N]
+    diff = unpack(gm) != unpack(om)
+    same = np.all(gm.reshape(n_poses, -1) == om.reshape(n_poses, -1), axis=1)
+    ot, _ = oracle.sample_tuples(om, oc, N, w.T, w.k, w.seed)
+    gt = tuples[:n_poses].cpu().numpy()
+    omar, _, _ = oracle.score_tuples(soa, ot[same], w.mu, w.K, w.obj.centroid, w.obj.rho, w.eps)
+    gmar = margin[:n_poses].cpu().numpy()[same].astype(np.float64).ravel()
+    gacc = accept[:n_poses].cpu().numpy()[same].astype(bool).ravel()
+    omar = omar.ravel()
+    fin = np.isfinite(omar)
+    rel = np.abs(gmar[fin] - np.maximum(omar[fin], 0)) / np.maximum(omar[fin], w.eps)
+    dec = gacc != (omar <= w.eps)
+    return {"poses": n_poses, "mask_entries": int(diff.size), "mask_differ": int(diff.sum()),
+            "mask_differ_outside_band": int(np.sum(diff & (amb == 0))), "mask_in_band": int(np.count_nonzero(amb)),
+            "mask_in_band_frac": float(np.count_nonzero(amb) / diff.size),
+            "poses_masks_equal": int(same.sum()), "tuples_equal": bool(np.array_equal(gt[same], ot[same])),
+            "tuples_scored": int(omar.size), "decisions_differ": int(dec.sum()),
+            "decisions_in_band": int(np.sum(np.abs(omar - w.eps) <= 1e-4)),
+            "margin_max_rel_err": float(rel.max(initial=0.0)), "seconds": time.perf_counter() - t0,
+            "rule": "GPU vs FP64 oracle: differences allowed only inside the band (1e-5 m, 1e-6 cosine; 1e-4 of "
+                    "eps for decisions) and below 1e-4 of all entries; margins within 1e-4 relative"}
 
 
 def cpu_baseline(w, n_poses: int):
@@ -186,6 +233,7 @@ def cpu_baseline(w, n_poses: int):
                 "sample": "per-pose path of the first 2 poses on one thread (no LP pool); the build at "
                           f"{s['cores']} x its all-core time"}
     return {"value": value, "unit": UNIT, "cores": s["cores"], "kind": "oracle", "one_core": one_core,
+            "lp_iterations_per_tuple": s["lp_iterations_per_tuple"],
             "sample": f"oracle field build over all {w.S} joint samples x {w.hand.F} fingers "
                       f"({s['t_build']:.2f} s) + query/sample/score of the first {n_poses} of {w.P} poses "
                       f"({s['t_pose']:.2f} s); a full step projected as build + {scale:.0f} x sample; "
@@ -199,7 +247,8 @@ def run_reference(args):
     import oracle
     import synth
     w = synth.workload(args.workload)
-    n = 4
+    # poses per step: about 0.1-0.3 s of host work (4 at 16,384 points x 64 tuples, 1 at 65,536 x 128)
+    n = max(1, min(4, int(4 * 16384 * 64 // (w.obj.N * w.T))))
     t0 = time.perf_counter()
     fd = oracle.Field(w.hand, w.q, w.inv_h, w.bins)
     t_build = time.perf_counter() - t0
@@ -238,6 +287,120 @@ def run_reference(args):
 # our arm
 # ---------------------------------------------------------------------------
 
+def main_leg(cf, torch, dev, w, steps, warmup, flush, barrier, sampler=None):
+    """The timed main step (field build + query + sampling + scoring) on
+    workload w: W untimed warm-up steps, then K steps timed with CUDA events on
+    the launch stream, L2 flushed between them (untimed)."""
+    import numpy as np
+    F = w.hand.F
+    q = torch.from_numpy(w.q).to(dev)
+    soa = torch.from_numpy(w.obj.soa()).to(dev)
+    poses = torch.from_numpy(w.poses).to(dev)
+    W = (w.obj.N + 31) // 32
+    masks = torch.empty((w.P, F, W), dtype=torch.int32, device=dev)
+    counts = torch.empty((w.P, F), dtype=torch.int32, device=dev)
+    tuples = torch.empty((w.P, w.T, w.k), dtype=torch.int32, device=dev)
+    fingers = torch.empty((w.P, w.T, w.k), dtype=torch.uint8, device=dev)
+    prm = cf.score_params(w.T, w.k, w.mu, w.K, w.eps, w.obj.centroid, w.obj.rho, w.seed)
+    prm_given = cf.score_params(w.T, w.k, w.mu, w.K, w.eps, w.obj.centroid, w.obj.rho, w.seed, tuples_given=True)
+    acc_total = torch.zeros((), dtype=torch.int64, device=dev)
+    margin = torch.empty((w.P, w.T), dtype=torch.float32, device=dev)
+    accept = torch.empty((w.P, w.T), dtype=torch.uint8, device=dev)
+    n_ev = 5
+
+    def step(ev):
+        ev[0].record()
+        field = cf.build(w.hand, w.inv_h, w.bins, q)
+        ev[1].record()
+        cf.query_domains(field, soa, poses, masks, counts)
+        ev[2].record()
+        cf.sample_tuples(soa, F, masks, counts, prm, tuples, fingers)
+        ev[3].record()
+        cf.score_tuples(soa, F, None, None, prm_given, tuples, margin=margin, accept=accept)
+        ev[4].record()
+        acc_total.add_(accept.sum())
+        return field
+
+    for _ in range(max(3, warmup)):
+        step([torch.cuda.Event(enable_timing=True) for _ in range(n_ev)])
+    acc_total.zero_()
+    barrier()
+    cf.device_counters(reset=True)
+    cf.device_status()
+    if sampler is not None:
+        sampler.start()
+        time.sleep(0.3)
+    evs = []
+    t_wall = time.perf_counter()
+    for i in range(steps):
+        flush.fill_(float(i))  # evict L2 between steps (not timed)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(n_ev)]
+        step(ev)
+        evs.append(ev)
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    clocks = sampler.stop() if sampler is not None else None
+    status = cf.device_status()
+    counters = cf.device_counters()
+    ms = np.array([[e[j].elapsed_time(e[j + 1]) for j in range(n_ev - 1)] for e in evs])
+    return dict(ms=ms, total_ms=float(ms.sum()), accepted=int(acc_total.item()), t_wall=t_wall, clocks=clocks,
+                status=status, counters=counters, masks=masks, counts=counts, tuples=tuples, fingers=fingers,
+                margin=margin, accept=accept, launches_per_step=5)
+
+
+# FP32 work counts (FMA = 2 flop) of the graded kernels, per unit:
+#  - query, per (pose, point): the full-scan definition, 18 (rotate p and n) + 3B (bin argmax over B
+#    directions) + 3F (cell index per finger), and the kernel's own count, 18 + 3 + 6 (the cube map names
+#    <= 4 candidate bins, 2 on average: 6 FMA), an upper bound since it bins only where the cell's record
+#    is not empty;
+#  - score, per tuple: the dense two-phase tableau definition, pivots x 13 x 39 + 360 (wrench set-up,
+#    k K x 15), with the pivots of the oracle's LP solver on the bench's own tuples, and the kernel's own
+#    count, its pivots x 7 x (kK + 6) + 360 (one dense pivot of its scaled 6-row LP).
+QUERY_FMA_OWN = 18 + 3 + 6
+
+
+def roofline(w, per, counters, steps, peak_fp32, n_sm, sm_mhz, nominal_fp32, oracle_pivots_per_tuple=None):
+    F = w.hand.F
+    pairs = w.P * w.obj.N
+    q_flop = pairs * (18 + 3 * w.B + 3 * F) * 2
+    q_flop_own = pairs * QUERY_FMA_OWN * 2
+    tuples = counters["tuples_scored"] / steps
+    setup = w.k * w.K * 15
+    s_flop_own = (counters["lp_pivots"] / steps * 7 * (w.k * w.K + 6) + tuples * setup) * 2
+    s_flop_survey = None
+    if oracle_pivots_per_tuple is not None:
+        s_flop_survey = tuples * (oracle_pivots_per_tuple * 13 * 39 + setup) * 2
+    b_flop = F * w.S * w.hand.M * (18 + 3 + 3 * w.B) * 2
+    traffic = NCU_TRAFFIC.get(w.name, {})
+    tf = lambda flop, ms: flop / (ms * 1e-3) / 1e12
+    kernels = {
+        "k_fk_cell_bounds+k_fk_bin": {"ms": per[0], "tflops": tf(b_flop, per[0]),
+                                      "traffic_k_fk_bin": traffic.get("k_fk_bin")},
+        "k_query_domains": {"ms": per[1], "tflops": tf(q_flop, per[1]), "tflops_kernel_count": tf(q_flop_own, per[1]),
+                            "fma_per_pair": 18 + 3 * w.B + 3 * F, "fma_per_pair_kernel_count": QUERY_FMA_OWN,
+                            "traffic": traffic.get("k_query_domains")},
+        "k_sample_tuples": {"ms": per[2], "traffic": traffic.get("k_sample_tuples")},
+        "k_score_lanes": {"ms": per[3], "tflops": tf(s_flop_own, per[3]),
+                          "tflops_survey_count": tf(s_flop_survey, per[3]) if s_flop_survey else None,
+                          "oracle_pivots_per_tuple": oracle_pivots_per_tuple,
+                          "kernel_pivots_per_tuple": counters["lp_pivots"] / max(1, counters["tuples_scored"]),
+                          "traffic": traffic.get("k_score_lanes")},
+    }
+    for v in kernels.values():
+        for key in ("tflops", "tflops_kernel_count", "tflops_survey_count"):
+            if v.get(key) is not None:
+                v["frac" + key[6:]] = v[key] / peak_fp32
+    dom = max(["k_query_domains", "k_score_lanes"], key=lambda k: kernels[k]["ms"])
+    return {"kernel": dom, "bound": "alu", "achieved": kernels[dom]["tflops"], "peak": peak_fp32,
+            "unit": "TFLOP/s", "frac": kernels[dom]["frac"], "traffic": kernels[dom].get("traffic"),
+            "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+            "peak_basis": "measured: cf_fp32_peak (independent FP32 FMA chains, CUDA events) on this GPU before the "
+                          f"timed region; nominal {n_sm} SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz = {nominal_fp32:.1f}",
+            "achieved_basis": "algorithmic FLOP per launch (full-scan / dense-tableau definition) / CUDA-event time; "
+                              "frac_kernel_count uses the kernel's own work count",
+            "kernels": kernels}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -258,30 +421,9 @@ def run_ours(args):
     q = torch.from_numpy(w.q).to(dev)
     soa = torch.from_numpy(w.obj.soa()).to(dev)
     poses = torch.from_numpy(w.poses).to(dev)
-    W = (w.obj.N + 31) // 32
-    masks = torch.empty((w.P, F, W), dtype=torch.int32, device=dev)
-    counts = torch.empty((w.P, F), dtype=torch.int32, device=dev)
-    tuples = torch.empty((w.P, w.T, w.k), dtype=torch.int32, device=dev)
-    fingers = torch.empty((w.P, w.T, w.k), dtype=torch.uint8, device=dev)
     prm = cf.score_params(w.T, w.k, w.mu, w.K, w.eps, w.obj.centroid, w.obj.rho, w.seed)
     prm_given = cf.score_params(w.T, w.k, w.mu, w.K, w.eps, w.obj.centroid, w.obj.rho, w.seed, tuples_given=True)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    acc_total = torch.zeros((), dtype=torch.int64, device=dev)
-
-    n_ev = 5
-
-    def step(ev):
-        ev[0].record()
-        field = cf.build(w.hand, w.inv_h, w.bins, q)
-        ev[1].record()
-        cf.query_domains(field, soa, poses, masks, counts)
-        ev[2].record()
-        cf.sample_tuples(soa, F, masks, counts, prm, tuples, fingers)
-        ev[3].record()
-        _, _, _, accept = cf.score_tuples(soa, F, None, None, prm_given, tuples)
-        ev[4].record()
-        acc_total.add_(accept.sum())
-        return field
 
     def barrier():
         torch.cuda.synchronize()
@@ -289,31 +431,12 @@ def run_ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    for _ in range(max(3, args.warmup)):
-        step([torch.cuda.Event(enable_timing=True) for _ in range(n_ev)])
     peak_measured = cf.fp32_peak()
-    acc_total.zero_()
-    barrier()
-    cf.device_counters(reset=True)
-    cf.device_status()
     sampler = ClockSampler(str(props.uuid) if hasattr(props, "uuid") else None)
-    sampler.start()
-    time.sleep(0.3)
-    evs = []
-    t_wall = time.perf_counter()
-    for i in range(args.steps):
-        flush.fill_(float(i))  # evict L2 between steps (not timed)
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(n_ev)]
-        step(ev)
-        evs.append(ev)
-    barrier()
-    t_wall = time.perf_counter() - t_wall
-    clocks = sampler.stop()
-    status = cf.device_status()
-    counters = cf.device_counters()
-    ms = np.array([[e[j].elapsed_time(e[j + 1]) for j in range(n_ev - 1)] for e in evs])
-    total_ms = float(ms.sum())
-    accepted = int(acc_total.item())
+    main = main_leg(cf, torch, dev, w, args.steps, args.warmup, flush, barrier, sampler)
+    masks, counts, tuples, fingers = main["masks"], main["counts"], main["tuples"], main["fingers"]
+    ms, total_ms, accepted, t_wall = main["ms"], main["total_ms"], main["accepted"], main["t_wall"]
+    clocks, status, counters = main["clocks"], main["status"], main["counters"]
 
     # ---- e2e: the same step through the host-buffer plan ----------------
     # page-locked inputs written by one thread (np.copyto), as a caller filling its buffers would.  Filled
@@ -366,32 +489,6 @@ def run_ours(args):
     n_sm = props.multi_processor_count
     nominal_fp32 = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s: FP32 lanes x FMA x clock
     peak_fp32 = peak_measured
-    pairs = w.P * w.obj.N
-    q_flop = pairs * (18 + 3 * w.B + 3 * F) * 2
-    # scaled bounded LP: a pivot updates the 6 rows + reduced costs of the kK + 6 columns
-    s_flop_own = (counters["lp_pivots"] * 7 * (w.k * w.K + 6) + counters["tuples_scored"] * w.k * w.K * 15) * 2 \
-        / args.steps
-    b_flop = F * w.S * w.hand.M * (18 + 3 + 3 * w.B) * 2
-    traffic = NCU_TRAFFIC.get(w.name, {})
-    kernels = {
-        "k_fk_cell_bounds+k_fk_bin": {"ms": per[0], "tflops": b_flop / (per[0] * 1e-3) / 1e12,
-                                      "traffic_k_fk_bin": traffic.get("k_fk_bin")},
-        "k_query_domains": {"ms": per[1], "tflops": q_flop / (per[1] * 1e-3) / 1e12,
-                            "traffic": traffic.get("k_query_domains")},
-        "k_sample_tuples": {"ms": per[2], "traffic": traffic.get("k_sample_tuples")},
-        "k_score_lanes": {"ms": per[3], "tflops": s_flop_own / (per[3] * 1e-3) / 1e12,
-                          "traffic": traffic.get("k_score_lanes")},
-    }
-    for v in kernels.values():
-        if "tflops" in v:
-            v["frac"] = v["tflops"] / peak_fp32
-    dom = max(["k_query_domains", "k_score_lanes"], key=lambda k: kernels[k]["ms"])
-    roof = {"kernel": dom, "bound": "alu", "achieved": kernels[dom]["tflops"], "peak": peak_fp32,
-            "unit": "TFLOP/s", "frac": kernels[dom]["frac"], "traffic": kernels[dom].get("traffic"),
-            "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
-            "peak_basis": "measured: cf_fp32_peak (independent FP32 FMA chains, CUDA events) on this GPU before the "
-                          f"timed region; nominal {n_sm} SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz = {nominal_fp32:.1f}",
-            "kernels": kernels}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -406,7 +503,7 @@ def run_ours(args):
                    "lps_per_tuple": counters["lps"] / max(1, counters["tuples_scored"])},
             "e2e": {"value": e2e_acc / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": n_e2e, "ms_per_step": 1e3 * e2e_s / n_e2e},
-            "roofline": roof, "clocks": clocks}
+            "clocks": clocks}
     if world == 1 and args.realized_steps > 0:
         line["realized"] = run_realized(cf, torch, dev, w, args.realized_steps, soa, poses, masks, counts, tuples,
                                         fingers, prm, prm_given, flush)
@@ -427,8 +524,25 @@ def run_ours(args):
         if args.served_seconds > 0:
             rates = [float(x) for x in args.served_rates.split(",") if x]
             line["served"] = run_served(cf, torch, dev, ws, fields, rates, args.served_seconds)
+    if world == 1 and args.extra_workload and args.extra_workload != w.name:
+        we = synth.workload(args.extra_workload)
+        ex = main_leg(cf, torch, dev, we, args.extra_steps, args.warmup, flush, barrier)
+        per_e = ex["ms"].mean(axis=0)
+        line[we.name] = {"value": ex["accepted"] / (ex["total_ms"] / 1e3), "unit": UNIT, "steps": args.extra_steps,
+                         "ms_per_step": ex["total_ms"] / args.extra_steps, "config": _config(we),
+                         "accept_rate": ex["accepted"] / (args.extra_steps * we.P * we.T),
+                         "breakdown_ms": {"build": per_e[0], "query": per_e[1], "sample": per_e[2], "score": per_e[3]},
+                         "roofline": roofline(we, per_e, ex["counters"], args.extra_steps, peak_fp32, n_sm, sm_mhz,
+                                              nominal_fp32),
+                         "device_status": ex["status"]}
+        del ex
+    if world == 1 and args.parity_poses > 0:
+        line["parity"] = parity_leg(w, masks, counts, tuples, main["margin"], main["accept"], args.parity_poses)
+    piv = None
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_poses)
+        piv = line["cpu_baseline"].get("lp_iterations_per_tuple")
+    line["roofline"] = roofline(w, per, counters, args.steps, peak_fp32, n_sm, sm_mhz, nominal_fp32, piv)
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

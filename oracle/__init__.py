@@ -20,9 +20,17 @@ Functions (paper passages they follow are cited in ``cf_oracle.c``):
   closure_lp          linearised GSWO margin of one tuple (Eq. GSWO): k LPs
   score_tuples        margins / accept flags of many tuples (process pool)
   rep_codes           reverse-lookup representatives of a finger's codes (Sec. 5.5)
-  point_codes         FP32 code of an object point under a pose (the query's decision)
+  point_codes         FP64 code of an object point under a pose (the query's decision)
   kinematics.*        FP64 numpy FK / Jacobian / DLS IK / SDF grid / realization
                       checks (Sec. 5.5, Sec. 5.6)
+
+Precision: geometry and every integer decision (voxel cell, normal bin, and
+from them field codes, masks, representatives and contact codes) are FP64.
+Beside a decision the oracle can flag it as ambiguous when a perturbation of
+at most tau = 1e-5 m of any coordinate involved, or 1e-6 in cosine on a bin
+tie, could change it; those are the only entries where a correct FP32
+implementation may decide otherwise.  The same codes decided in FP32
+(``codes(f, "fp32")``, ``query(..., mask32=True)``) are diagnostics only.
 
 Parity status: every function is pinned by tests under ``tests/`` against
 closed forms, an independent library routine (triton's Philox in
@@ -83,8 +91,8 @@ def lib():
                                        c_int, fp, c_int, c_double, c_double]
         L.orc_field_free.argtypes = [c_void_p]
         L.orc_field_sizes.argtypes = [c_void_p, POINTER(c_int64)]
-        L.orc_field_codes.restype = c_int64
-        L.orc_field_codes.argtypes = [c_void_p, c_int, POINTER(c_uint64), c_int64]
+        L.orc_field_code_set.restype = c_int64
+        L.orc_field_code_set.argtypes = [c_void_p, c_int, c_int, POINTER(c_uint64), c_int64]
         L.orc_query_masks.argtypes = [c_void_p, c_int, fp, c_int, fp, u32p, u32p, u8p, u32p]
         L.orc_query_masks_brute.argtypes = [c_int, c_int, c_int, fp, fp, fp, fp, fp, i32p, fp, c_int, c_float,
                                             c_int, fp, c_int, fp, c_int, fp, u32p, u32p]
@@ -94,8 +102,9 @@ def lib():
         L.orc_set_threads.argtypes = [c_int]
         L.orc_rep_codes.restype = c_int64
         L.orc_rep_codes.argtypes = [c_int, c_int, c_int, fp, fp, fp, fp, fp, i32p, fp, c_int, c_float, c_int, fp,
-                                    c_int, POINTER(c_uint64), u32p, c_int64]
-        L.orc_point_codes.argtypes = [c_int, fp, fp, c_int, i32p, i32p, c_float, c_int, fp, POINTER(c_int64)]
+                                    c_int, c_double, c_double, POINTER(c_uint64), u32p, u8p, c_int64]
+        L.orc_point_codes.argtypes = [c_int, fp, fp, c_int, i32p, i32p, c_float, c_int, fp, c_double, c_double,
+                                      POINTER(c_int64), u8p]
         _lib = L
     return _lib
 
@@ -197,11 +206,19 @@ class Field:
         lib().orc_field_sizes(self._h, out.ctypes.data_as(POINTER(c_int64)))
         return out
 
-    def codes(self, f: int) -> np.ndarray:
-        """Sorted distinct (kx, ky, kz, bin) codes of finger f, int64 [n,4]."""
-        n = int(self.n_codes()[f])
+    def codes(self, f: int, which: str = "fp64") -> np.ndarray:
+        """Sorted distinct (kx, ky, kz, bin) codes of finger f, int64 [n,4].
+        which: "fp64" (the oracle's decisions, which the acceptance tests use),
+        "fp32" (the same codes decided in FP32: a diagnostic), "possible" (codes
+        some sample takes somewhere in the tolerance band), "sure" (codes of
+        samples whose code is the same everywhere in the band); the last three
+        need band=True."""
+        sel = {"fp32": 0, "fp64": 1, "possible": 2, "sure": 3}[which]
+        n = int(lib().orc_field_code_set(self._h, f, sel, None, 0))
+        if n < 0:
+            raise ValueError(f"code set {which!r} needs Field(..., band=True)")
         raw = np.zeros(n, np.uint64)
-        lib().orc_field_codes(self._h, f, raw.ctypes.data_as(POINTER(c_uint64)), n)
+        lib().orc_field_code_set(self._h, f, sel, raw.ctypes.data_as(POINTER(c_uint64)), n)
         off = 32768
         kx = ((raw >> np.uint64(40)) & np.uint64(0xFFFF)).astype(np.int64) - off
         ky = ((raw >> np.uint64(24)) & np.uint64(0xFFFF)).astype(np.int64) - off
@@ -209,9 +226,10 @@ class Field:
         b = (raw & np.uint64(0xFF)).astype(np.int64)
         return np.stack([kx, ky, kz, b], axis=1)
 
-    def query(self, soa: np.ndarray, poses: np.ndarray, amb: bool = False, mask64: bool = False):
-        """Domain masks [P,F,W] uint32 and counts [P,F] uint32 (plus optional
-        ambiguity flags [P,F,N] uint8 and FP64-decision masks [P,F,W])."""
+    def query(self, soa: np.ndarray, poses: np.ndarray, amb: bool = False, mask32: bool = False):
+        """Domain masks [P,F,W] uint32 and counts [P,F] uint32, decided in FP64
+        (plus optional ambiguity flags [P,F,N] uint8, which need band=True, and
+        the FP32-decision masks [P,F,W] as a diagnostic)."""
         soa = _c(soa, np.float32)
         poses = _c(poses, np.float32).reshape(-1, 12)
         N = int(soa.shape[1])
@@ -220,17 +238,17 @@ class Field:
         masks = np.zeros((P, self.F, W), np.uint32)
         counts = np.zeros((P, self.F), np.uint32)
         a = np.zeros((P, self.F, N), np.uint8) if amb else None
-        m64 = np.zeros((P, self.F, W), np.uint32) if mask64 else None
-        if (amb or mask64) and not self.band:
-            raise ValueError("ambiguity / FP64 outputs need Field(..., band=True)")
+        m32 = np.zeros((P, self.F, W), np.uint32) if mask32 else None
+        if amb and not self.band:
+            raise ValueError("ambiguity flags need Field(..., band=True)")
         lib().orc_query_masks(self._h, N, _p(soa, c_float), P, _p(poses, c_float), _p(masks, c_uint32),
                               _p(counts, c_uint32), _p(a, c_uint8) if a is not None else None,
-                              _p(m64, c_uint32) if m64 is not None else None)
+                              _p(m32, c_uint32) if m32 is not None else None)
         out = [masks, counts]
         if amb:
             out.append(a)
-        if mask64:
-            out.append(m64)
+        if mask32:
+            out.append(m32)
         return tuple(out)
 
 
@@ -281,9 +299,11 @@ def pack_code(f, kx, ky, kz, b) -> int:
     return (int(f) << 56) | ((int(kx) + o) << 40) | ((int(ky) + o) << 24) | ((int(kz) + o) << 8) | int(b)
 
 
-def rep_codes(hand, q, inv_h, bins, f: int) -> dict:
-    """Reverse lookup table of finger f (Sec. 5.5): packed code -> smallest
-    s * M + m over the field samples producing it (m in the hand's order)."""
+def rep_codes(hand, q, inv_h, bins, f: int, with_sure: bool = False, tau: float = 1e-5, bin_tol: float = 1e-6):
+    """Reverse lookup table of finger f (Sec. 5.5): packed FP64 code -> smallest
+    s * M + m over the field samples producing it (m in the hand's order).
+    with_sure: also the set of codes whose representative no perturbation
+    within the band (tau metres, bin_tol in cosine) can change."""
     keep, ptrs = _hand_args(hand)
     qq = _c(q, np.float32)
     bb = _c(bins, np.float32)
@@ -291,26 +311,35 @@ def rep_codes(hand, q, inv_h, bins, f: int) -> dict:
     cap = S * hand.M
     keys = np.zeros(max(cap, 1), np.uint64)
     vals = np.zeros(max(cap, 1), np.uint32)
+    sure = np.zeros(max(cap, 1), np.uint8) if with_sure else None
     n = lib().orc_rep_codes(hand.F, hand.J, hand.M, *ptrs, _p(qq, c_float), S, c_float(np.float32(inv_h)),
-                            int(bb.shape[0]), _p(bb, c_float), int(f), keys.ctypes.data_as(POINTER(c_uint64)),
-                            _p(vals, c_uint32), cap)
+                            int(bb.shape[0]), _p(bb, c_float), int(f), float(tau), float(bin_tol),
+                            keys.ctypes.data_as(POINTER(c_uint64)), _p(vals, c_uint32),
+                            _p(sure, c_uint8) if sure is not None else None, cap)
     del keep
-    return dict(zip(keys[:n].tolist(), vals[:n].tolist()))
+    rep = dict(zip(keys[:n].tolist(), vals[:n].tolist()))
+    if not with_sure:
+        return rep
+    return rep, set(keys[:n][sure[:n].astype(bool)].tolist())
 
 
-def point_codes(soa, poses, pose_idx, pt_idx, inv_h, bins) -> np.ndarray:
-    """FP32 (kx, ky, kz, bin) of the contact-surface vector of points pt_idx
-    under poses pose_idx, as the domain query decides it: int64 [n, 4]."""
+def point_codes(soa, poses, pose_idx, pt_idx, inv_h, bins, with_amb: bool = False, tau: float = 1e-5,
+                bin_tol: float = 1e-6):
+    """FP64 (kx, ky, kz, bin) of the contact-surface vector of points pt_idx
+    under poses pose_idx, as the domain query decides it: int64 [n, 4]
+    (with_amb: also uint8 [n] flags of codes that a perturbation within the
+    band could change)."""
     soa = _c(soa, np.float32)
     poses = _c(poses, np.float32).reshape(-1, 12)
     pi = _c(pose_idx, np.int32).ravel()
     xi = _c(pt_idx, np.int32).ravel()
     bb = _c(bins, np.float32)
     out = np.zeros((pi.size, 4), np.int64)
+    amb = np.zeros(pi.size, np.uint8)
     lib().orc_point_codes(int(soa.shape[1]), _p(soa, c_float), _p(poses, c_float), int(pi.size), _p(pi, c_int32),
                           _p(xi, c_int32), c_float(np.float32(inv_h)), int(bb.shape[0]), _p(bb, c_float),
-                          out.ctypes.data_as(POINTER(c_int64)))
-    return out
+                          float(tau), float(bin_tol), out.ctypes.data_as(POINTER(c_int64)), _p(amb, c_uint8))
+    return (out, amb) if with_amb else out
 
 
 def sample_tuples(masks: np.ndarray, counts: np.ndarray, N: int, T: int, k: int, seed: int):

@@ -25,13 +25,16 @@
  *   (the closure margin's linear programs are written out and solved in
  *   oracle/__init__.py with a library LP solver).
  *
- * Precision: kinematics and geometry are FP64.  The integer codes that
- * the GPU decides in FP32 (voxel cell, normal bin) are decided here in the same
- * precision, from link transforms evaluated in FP32 (joint sin / cos in FP64
- * rounded to FP32, every chain operation rounded) and single-rounding fused
- * multiply-adds in the natural component order; an FP64 evaluation of the same
- * codes is kept beside them to count the entries that sit within a tolerance
- * band of a cell or bin boundary (the "ambiguous" entries).
+ * Precision: kinematics, geometry and every integer decision (voxel cell,
+ * normal bin, hence field codes, domain masks, reverse-lookup representatives
+ * and contact codes) are FP64: the FP32 inputs are widened and the chain, the
+ * transforms and the dot products are evaluated in double precision.  Beside
+ * each FP64 decision the oracle keeps a tolerance band (tau metres on every
+ * coordinate, bin_tol in cosine on the bin argmax) to flag the entries whose
+ * decision could change under a perturbation that small: the "ambiguous"
+ * entries, where a correct FP32 implementation may legitimately decide
+ * otherwise.  An FP32 evaluation of the codes (orc_fk_links32 and the fmaf
+ * helpers) is kept only as a diagnostic: no acceptance test relies on it.
  */
 #include <math.h>
 #include <stdint.h>
@@ -291,6 +294,9 @@ static int band_bins(const double m[3], int B, const float *dirs, double tol, in
     return n;
 }
 
+/* FP64 cell index along one axis: floor(x * inv_h) of the FP64 coordinate */
+static inline int64_t cell64(double x, float inv_h) { return (int64_t)floor(x * (double)inv_h); }
+
 static int bin64(const double m[3], int B, const float *dirs) {
     int best_b = 0;
     double best = -INFINITY;
@@ -330,24 +336,23 @@ void *orc_field_create(int F, int J, int M, const float *base, const float *axis
         double qs[8];
         for (int s = 0; s < S; ++s) {
             for (int j = 0; j < J; ++j) qs[j] = (double)q[((size_t)f * J + j) * S + s];
-            orc_contact_vectors(J, M, bf, af, of, spf, snf, slf, qs, p32, n32,
-                                with_band ? p64 : NULL, with_band ? n64 : NULL);
+            orc_contact_vectors(J, M, bf, af, of, spf, snf, slf, qs, p32, n32, p64, n64);
             for (int m = 0; m < M; ++m) {
+                const double *pp = p64 + 3 * m, *nn = n64 + 3 * m;
+                int64_t ex = cell64(pp[0], inv_h), ey = cell64(pp[1], inv_h), ez = cell64(pp[2], inv_h);
+                if (!in_key_range(ex) || !in_key_range(ey) || !in_key_range(ez)) { ++oor; continue; }
+                kv_push(&fd->k64[f], pack_key(f, ex, ey, ez, bin64(nn, B, dirs)));
+                /* diagnostic: the same code decided in FP32 */
                 int64_t kx = cell_axis(p32[3 * m], inv_h), ky = cell_axis(p32[3 * m + 1], inv_h),
                         kz = cell_axis(p32[3 * m + 2], inv_h);
-                if (!in_key_range(kx) || !in_key_range(ky) || !in_key_range(kz)) { ++oor; continue; }
-                int b = bin32(n32 + 3 * m, B, dirs);
-                kv_push(&fd->k32[f], pack_key(f, kx, ky, kz, b));
+                if (in_key_range(kx) && in_key_range(ky) && in_key_range(kz))
+                    kv_push(&fd->k32[f], pack_key(f, kx, ky, kz, bin32(n32 + 3 * m, B, dirs)));
                 if (!with_band) continue;
-                const double *pp = p64 + 3 * m, *nn = n64 + 3 * m;
                 int64_t cx[2], cy[2], cz[2];
                 int nx = band_cells(pp[0], tau, inv_h, cx), ny = band_cells(pp[1], tau, inv_h, cy),
                     nz = band_cells(pp[2], tau, inv_h, cz);
                 int bins[64];
                 int nb = band_bins(nn, B, dirs, bin_tol, bins);
-                kv_push(&fd->k64[f], pack_key(f, (int64_t)floor(pp[0] * (double)inv_h),
-                                              (int64_t)floor(pp[1] * (double)inv_h),
-                                              (int64_t)floor(pp[2] * (double)inv_h), bin64(nn, B, dirs)));
                 for (int a = 0; a < nx; ++a)
                     for (int c = 0; c < ny; ++c)
                         for (int d = 0; d < nz; ++d)
@@ -383,37 +388,46 @@ void orc_field_free(void *h) {
     free(fd);
 }
 
-/* number of distinct (cell, bin) codes per finger, FP32 decisions */
+/* number of distinct (cell, bin) codes per finger (FP64 decisions) */
 void orc_field_sizes(const void *h, int64_t *n_codes) {
     const orc_field *fd = (const orc_field *)h;
-    for (int f = 0; f < fd->F; ++f) n_codes[f] = fd->k32[f].n;
+    for (int f = 0; f < fd->F; ++f) n_codes[f] = fd->k64[f].n;
 }
 
-/* copy finger f's sorted FP32 code set (packed keys) into out (capacity cap) */
-int64_t orc_field_codes(const void *h, int f, uint64_t *out, int64_t cap) {
+/* copy one of finger f's sorted code sets: which = 0 FP32 decisions, 1 FP64
+ * decisions, 2 codes some sample could take within the band (possible), 3 codes
+ * of samples whose code is the same everywhere in the band (sure).  Sets 1-3
+ * need with_band; returns the set's size, or -1 if it was not built. */
+int64_t orc_field_code_set(const void *h, int f, int which, uint64_t *out, int64_t cap) {
     const orc_field *fd = (const orc_field *)h;
-    int64_t n = fd->k32[f].n < cap ? fd->k32[f].n : cap;
-    memcpy(out, fd->k32[f].v, (size_t)n * sizeof(uint64_t));
-    return fd->k32[f].n;
+    const keyvec *kv = which == 0 ? &fd->k32[f] : which == 1 ? &fd->k64[f] : which == 2 ? &fd->kpos[f]
+                     : which == 3 ? &fd->ksure[f] : NULL;
+    if (!kv || (which >= 2 && !fd->with_band)) return -1;
+    int64_t n = kv->n < cap ? kv->n : cap;
+    if (n > 0) memcpy(out, kv->v, (size_t)n * sizeof(uint64_t));
+    return kv->n;
 }
 
 /* Contact domains (Sec. 4.2: CF(H) intersected with S(O); Sec. 4.3 object
  * contact query).  For pose i = (R_i, t_i) (object -> palm) and object point x
  * with outward normal n_x, the contact-surface vector is (R p_x + t, -(R n_x))
- * (Def. "Contact Surface Representation" flips the normal).  Bit x of
- * masks[i][f] is set iff finger f's field contains its (cell, bin) code.
+ * (Def. "Contact Surface Representation" flips the normal), evaluated in FP64.
+ * Bit x of masks[i][f] is set iff finger f's FP64 code set contains its FP64
+ * (cell, bin) code (or, with theta-dilated bins, the cell with any accepted bin).
  * soa is [6][N] (px,py,pz,nx,ny,nz); poses [P][12] row-major (R | t).
- * masks [P][F][W] with W = ceil(N/32), bit (x & 31) of word x >> 5.
- * Optional outputs (NULL to skip; need with_band):
- *   amb    [P][F][N] uint8: 1 if the decision is not the same everywhere within
- *          the tolerance band (tau metres, bin_tol in cosine);
- *   mask64 [P][F][W]: decisions with FP64 codes on both sides. */
+ * masks [P][F][W] with W = ceil(N/32), bit (x & 31) of word x >> 5; counts are
+ * the row popcounts.  Optional outputs (NULL to skip):
+ *   amb    [P][F][N] uint8 (needs with_band): 1 if the decision is not the same
+ *          everywhere within the tolerance band (tau metres on the query point
+ *          and on the field samples, bin_tol in cosine);
+ *   mask32 [P][F][W]: diagnostic, the decisions taken in FP32 on both sides. */
 void orc_query_masks(const void *h, int N, const float *soa, int P, const float *poses,
-                     uint32_t *masks, uint32_t *counts, uint8_t *amb, uint32_t *mask64) {
+                     uint32_t *masks, uint32_t *counts, uint8_t *amb, uint32_t *mask32) {
     const orc_field *fd = (const orc_field *)h;
     const int F = fd->F, B = fd->B, W = (N + 31) / 32;
     const float inv_h = fd->inv_h;
     const double tau = fd->tau;
+    if (amb && !fd->with_band) amb = NULL;
 #pragma omp parallel for schedule(dynamic, 4)
     for (int i = 0; i < P; ++i) {
         const float *T = poses + 12 * i;
@@ -421,39 +435,40 @@ void orc_query_masks(const void *h, int N, const float *soa, int P, const float 
         const float t[3] = {T[3], T[7], T[11]};
         uint32_t *mrow = masks + (size_t)i * F * W;
         memset(mrow, 0, sizeof(uint32_t) * F * W);
-        if (mask64) memset(mask64 + (size_t)i * F * W, 0, sizeof(uint32_t) * F * W);
+        if (mask32) memset(mask32 + (size_t)i * F * W, 0, sizeof(uint32_t) * F * W);
         for (int x = 0; x < N; ++x) {
             const float p[3] = {soa[x], soa[N + x], soa[2 * N + x]};
             const float n[3] = {soa[3 * N + x], soa[4 * N + x], soa[5 * N + x]};
-            float pq[3], nq[3];
-            xform_point32(R, t, p, pq);
-            rotate32(R, n, nq);
-            const float mq[3] = {-nq[0], -nq[1], -nq[2]};
-            int64_t kx = cell_axis(pq[0], inv_h), ky = cell_axis(pq[1], inv_h), kz = cell_axis(pq[2], inv_h);
-            int ok = in_key_range(kx) && in_key_range(ky) && in_key_range(kz);
-            int b = bin32(mq, B, fd->dirs);
-            for (int f = 0; f < F; ++f)
-                if (ok && has_any_bin(&fd->k32[f], f, kx, ky, kz, fd->dil[b]))
-                    mrow[(size_t)f * W + (x >> 5)] |= 1u << (x & 31);
-            if (!fd->with_band || (!amb && !mask64)) continue;
             double p64[3], m64[3];
             for (int r = 0; r < 3; ++r) {
                 p64[r] = (double)t[r] + (double)R[3 * r] * p[0] + (double)R[3 * r + 1] * p[1] + (double)R[3 * r + 2] * p[2];
                 m64[r] = -((double)R[3 * r] * n[0] + (double)R[3 * r + 1] * n[1] + (double)R[3 * r + 2] * n[2]);
             }
+            const int64_t ex = cell64(p64[0], inv_h), ey = cell64(p64[1], inv_h), ez = cell64(p64[2], inv_h);
+            const int b64 = bin64(m64, B, fd->dirs);
+            const int ok64 = in_key_range(ex) && in_key_range(ey) && in_key_range(ez);
+            for (int f = 0; f < F; ++f)
+                if (ok64 && has_any_bin(&fd->k64[f], f, ex, ey, ez, fd->dil[b64]))
+                    mrow[(size_t)f * W + (x >> 5)] |= 1u << (x & 31);
+            if (mask32) {  /* diagnostic: FP32 decisions on both sides */
+                float pq[3], nq[3];
+                xform_point32(R, t, p, pq);
+                rotate32(R, n, nq);
+                const float mq[3] = {-nq[0], -nq[1], -nq[2]};
+                const int64_t kx = cell_axis(pq[0], inv_h), ky = cell_axis(pq[1], inv_h), kz = cell_axis(pq[2], inv_h);
+                const int ok = in_key_range(kx) && in_key_range(ky) && in_key_range(kz);
+                const int b = bin32(mq, B, fd->dirs);
+                for (int f = 0; f < F; ++f)
+                    if (ok && has_any_bin(&fd->k32[f], f, kx, ky, kz, fd->dil[b]))
+                        mask32[((size_t)i * F + f) * W + (x >> 5)] |= 1u << (x & 31);
+            }
+            if (!amb) continue;
             int64_t cx[2], cy[2], cz[2];
             int nx = band_cells(p64[0], tau, inv_h, cx), ny = band_cells(p64[1], tau, inv_h, cy),
                 nz = band_cells(p64[2], tau, inv_h, cz);
             int bins[64];
             int nb = band_bins(m64, B, fd->dirs, fd->bin_tol, bins);
-            int64_t ex = (int64_t)floor(p64[0] * (double)inv_h), ey = (int64_t)floor(p64[1] * (double)inv_h),
-                    ez = (int64_t)floor(p64[2] * (double)inv_h);
-            int b64 = bin64(m64, B, fd->dirs);
-            int ok64 = in_key_range(ex) && in_key_range(ey) && in_key_range(ez);
             for (int f = 0; f < F; ++f) {
-                if (mask64 && ok64 && has_any_bin(&fd->k64[f], f, ex, ey, ez, fd->dil[b64]))
-                    mask64[((size_t)i * F + f) * W + (x >> 5)] |= 1u << (x & 31);
-                if (!amb) continue;
                 int possible = 0, sure = 1;
                 for (int a = 0; a < nx; ++a)
                     for (int c = 0; c < ny; ++c)
@@ -491,18 +506,18 @@ void orc_query_masks_brute(int F, int J, int M, const float *base, const float *
     /* per (f, s, m) codes of the samples, recomputed from FK */
     int64_t *scode = (int64_t *)malloc(sizeof(int64_t) * 4 * (size_t)F * S * M);
     for (int f = 0; f < F; ++f) {
-        float p32[3 * 128], n32[3 * 128];
+        double p64[3 * 128], n64[3 * 128];
         double qs[8];
         for (int s = 0; s < S; ++s) {
             for (int j = 0; j < J; ++j) qs[j] = (double)q[((size_t)f * J + j) * S + s];
             orc_contact_vectors(J, M, base + 12 * f, axis + 3 * J * f, offset + 3 * J * f, surf_p + 3 * M * f,
-                                surf_n + 3 * M * f, surf_link + M * f, qs, p32, n32, NULL, NULL);
+                                surf_n + 3 * M * f, surf_link + M * f, qs, NULL, NULL, p64, n64);
             for (int m = 0; m < M; ++m) {
                 int64_t *c = scode + 4 * (((size_t)f * S + s) * M + m);
-                c[0] = cell_axis(p32[3 * m], inv_h);
-                c[1] = cell_axis(p32[3 * m + 1], inv_h);
-                c[2] = cell_axis(p32[3 * m + 2], inv_h);
-                c[3] = bin32(n32 + 3 * m, B, dirs);
+                c[0] = cell64(p64[3 * m], inv_h);
+                c[1] = cell64(p64[3 * m + 1], inv_h);
+                c[2] = cell64(p64[3 * m + 2], inv_h);
+                c[3] = bin64(n64 + 3 * m, B, dirs);
             }
         }
     }
@@ -514,12 +529,12 @@ void orc_query_masks_brute(int F, int J, int M, const float *base, const float *
         for (int x = 0; x < N; ++x) {
             const float p[3] = {soa[x], soa[N + x], soa[2 * N + x]};
             const float n[3] = {soa[3 * N + x], soa[4 * N + x], soa[5 * N + x]};
-            float pq[3], nq[3];
-            xform_point32(R, t, p, pq);
-            rotate32(R, n, nq);
-            const float mq[3] = {-nq[0], -nq[1], -nq[2]};
-            int64_t qc[4] = {cell_axis(pq[0], inv_h), cell_axis(pq[1], inv_h), cell_axis(pq[2], inv_h),
-                             bin32(mq, B, dirs)};
+            double pq[3], mq[3];
+            for (int r = 0; r < 3; ++r) {
+                pq[r] = (double)t[r] + (double)R[3 * r] * p[0] + (double)R[3 * r + 1] * p[1] + (double)R[3 * r + 2] * p[2];
+                mq[r] = -((double)R[3 * r] * n[0] + (double)R[3 * r + 1] * n[1] + (double)R[3 * r + 2] * n[2]);
+            }
+            int64_t qc[4] = {cell64(pq[0], inv_h), cell64(pq[1], inv_h), cell64(pq[2], inv_h), bin64(mq, B, dirs)};
             const uint32_t acc = dil ? (dil[qc[3]] | (1u << qc[3])) : (1u << qc[3]);
             for (int f = 0; f < F; ++f) {
                 const int64_t *c = scode + 4 * (size_t)f * S * M;
@@ -632,49 +647,88 @@ static int cmp_keyval(const void *a, const void *b) {
     return x->val < y->val ? -1 : (x->val > y->val);
 }
 
-/* For every FP32 (cell, bin) code of finger f: the smallest s * M + m over the
+/* For every FP64 (cell, bin) code of finger f: the smallest s * M + m over the
  * field samples (joint sample s, surface point m in the caller's order) whose
  * contact vector has that code -- the sample the reverse lookup retrieves.
  * Writes up to cap (packed key, value) pairs sorted by key; returns the number
- * of distinct codes. */
+ * of distinct codes.  sure (optional, [cap]) flags the representatives no
+ * perturbation within the band (tau metres, bin_tol in cosine) can change:
+ * no sample with a smaller index takes the code anywhere in its band, and the
+ * representative's own code is the same everywhere in its band. */
 int64_t orc_rep_codes(int F, int J, int M, const float *base, const float *axis, const float *offset,
                       const float *surf_p, const float *surf_n, const int32_t *surf_link, const float *q, int S,
-                      float inv_h, int B, const float *dirs, int f, uint64_t *keys, uint32_t *vals, int64_t cap) {
+                      float inv_h, int B, const float *dirs, int f, double tau, double bin_tol,
+                      uint64_t *keys, uint32_t *vals, uint8_t *sure, int64_t cap) {
     (void)F;
     const float *bf = base + 12 * f, *af = axis + 3 * J * f, *of = offset + 3 * J * f;
     const float *spf = surf_p + 3 * M * f, *snf = surf_n + 3 * M * f;
     const int32_t *slf = surf_link + M * f;
     keyval *kv = (keyval *)malloc(sizeof(keyval) * (size_t)S * M + 1);
-    float *p32 = (float *)malloc(sizeof(float) * 3 * M), *n32 = (float *)malloc(sizeof(float) * 3 * M);
+    uint8_t *exact = (uint8_t *)malloc((size_t)S * M + 1); /* [s*M+m]: the sample's code is band-stable */
+    int64_t pcap = 16 * (int64_t)S * M / 8 + 1024, np_ = 0; /* band codes of all samples (grown as needed) */
+    keyval *pk = (keyval *)malloc(sizeof(keyval) * (size_t)pcap);
+    double *p64 = (double *)malloc(sizeof(double) * 3 * M), *n64 = (double *)malloc(sizeof(double) * 3 * M);
     int64_t n = 0;
     double qs[8];
     for (int s = 0; s < S; ++s) {
         for (int j = 0; j < J; ++j) qs[j] = (double)q[((size_t)f * J + j) * S + s];
-        orc_contact_vectors(J, M, bf, af, of, spf, snf, slf, qs, p32, n32, NULL, NULL);
+        orc_contact_vectors(J, M, bf, af, of, spf, snf, slf, qs, NULL, NULL, p64, n64);
         for (int m = 0; m < M; ++m) {
-            int64_t kx = cell_axis(p32[3 * m], inv_h), ky = cell_axis(p32[3 * m + 1], inv_h),
-                    kz = cell_axis(p32[3 * m + 2], inv_h);
+            const double *pp = p64 + 3 * m, *nn = n64 + 3 * m;
+            const uint32_t val = (uint32_t)s * (uint32_t)M + (uint32_t)m;
+            int64_t kx = cell64(pp[0], inv_h), ky = cell64(pp[1], inv_h), kz = cell64(pp[2], inv_h);
+            exact[val] = 0;
             if (!in_key_range(kx) || !in_key_range(ky) || !in_key_range(kz)) continue;
-            kv[n].key = pack_key(f, kx, ky, kz, bin32(n32 + 3 * m, B, dirs));
-            kv[n].val = (uint32_t)s * (uint32_t)M + (uint32_t)m;
+            kv[n].key = pack_key(f, kx, ky, kz, bin64(nn, B, dirs));
+            kv[n].val = val;
             ++n;
+            if (!sure) continue;
+            int64_t cx[2], cy[2], cz[2];
+            int bins[64];
+            const int nx = band_cells(pp[0], tau, inv_h, cx), ny = band_cells(pp[1], tau, inv_h, cy),
+                      nz = band_cells(pp[2], tau, inv_h, cz), nb = band_bins(nn, B, dirs, bin_tol, bins);
+            exact[val] = (uint8_t)(nx * ny * nz * nb == 1);
+            for (int a = 0; a < nx; ++a)
+                for (int c = 0; c < ny; ++c)
+                    for (int d = 0; d < nz; ++d)
+                        for (int e = 0; e < nb; ++e) {
+                            if (!in_key_range(cx[a]) || !in_key_range(cy[c]) || !in_key_range(cz[d])) continue;
+                            if (np_ == pcap) {
+                                pcap *= 2;
+                                pk = (keyval *)realloc(pk, sizeof(keyval) * (size_t)pcap);
+                            }
+                            pk[np_].key = pack_key(f, cx[a], cy[c], cz[d], bins[e]);
+                            pk[np_].val = val;
+                            ++np_;
+                        }
         }
     }
     qsort(kv, (size_t)n, sizeof(keyval), cmp_keyval);
-    int64_t u = 0;
+    if (sure) qsort(pk, (size_t)np_, sizeof(keyval), cmp_keyval);
+    int64_t u = 0, ip = 0;
     for (int64_t i = 0; i < n; ++i) {
         if (i > 0 && kv[i].key == kv[i - 1].key) continue;  /* first of each key = smallest value */
-        if (u < cap) { keys[u] = kv[i].key; vals[u] = kv[i].val; }
+        if (u < cap) {
+            keys[u] = kv[i].key;
+            vals[u] = kv[i].val;
+            if (sure) {
+                while (ip < np_ && pk[ip].key < kv[i].key) ++ip;  /* first band entry of this key: its smallest value */
+                sure[u] = (uint8_t)(ip < np_ && pk[ip].key == kv[i].key && pk[ip].val == kv[i].val && exact[kv[i].val]);
+            }
+        }
         ++u;
     }
-    free(kv); free(p32); free(n32);
+    free(kv); free(pk); free(exact); free(p64); free(n64);
     return u;
 }
 
-/* FP32 (cell, bin) code of the contact-surface vector of point pt[i] under pose
- * pose[i], exactly as the domain query decides it: out[i] = (kx, ky, kz, bin). */
+/* FP64 (cell, bin) code of the contact-surface vector of point pt[i] under pose
+ * pose[i] (the domain query's decision): out[i] = (kx, ky, kz, bin).  amb
+ * (optional) flags the points whose code is not the same everywhere within the
+ * band (tau metres, bin_tol in cosine). */
 void orc_point_codes(int N, const float *soa, const float *poses, int n, const int32_t *pose_idx,
-                     const int32_t *pt_idx, float inv_h, int B, const float *dirs, int64_t *out) {
+                     const int32_t *pt_idx, float inv_h, int B, const float *dirs, double tau, double bin_tol,
+                     int64_t *out, uint8_t *amb) {
     for (int i = 0; i < n; ++i) {
         const float *T = poses + 12 * (size_t)pose_idx[i];
         const float R[9] = {T[0], T[1], T[2], T[4], T[5], T[6], T[8], T[9], T[10]};
@@ -682,13 +736,20 @@ void orc_point_codes(int N, const float *soa, const float *poses, int n, const i
         const int x = pt_idx[i];
         const float p[3] = {soa[x], soa[N + x], soa[2 * N + x]};
         const float nv[3] = {soa[3 * N + x], soa[4 * N + x], soa[5 * N + x]};
-        float pq[3], nq[3];
-        xform_point32(R, t, p, pq);
-        rotate32(R, nv, nq);
-        const float mq[3] = {-nq[0], -nq[1], -nq[2]};
-        out[4 * i] = cell_axis(pq[0], inv_h);
-        out[4 * i + 1] = cell_axis(pq[1], inv_h);
-        out[4 * i + 2] = cell_axis(pq[2], inv_h);
-        out[4 * i + 3] = bin32(mq, B, dirs);
+        double pq[3], mq[3];
+        for (int r = 0; r < 3; ++r) {
+            pq[r] = (double)t[r] + (double)R[3 * r] * p[0] + (double)R[3 * r + 1] * p[1] + (double)R[3 * r + 2] * p[2];
+            mq[r] = -((double)R[3 * r] * nv[0] + (double)R[3 * r + 1] * nv[1] + (double)R[3 * r + 2] * nv[2]);
+        }
+        out[4 * i] = cell64(pq[0], inv_h);
+        out[4 * i + 1] = cell64(pq[1], inv_h);
+        out[4 * i + 2] = cell64(pq[2], inv_h);
+        out[4 * i + 3] = bin64(mq, B, dirs);
+        if (amb) {
+            int64_t c[2];
+            int bins[64];
+            amb[i] = (uint8_t)(band_cells(pq[0], tau, inv_h, c) * band_cells(pq[1], tau, inv_h, c) *
+                                   band_cells(pq[2], tau, inv_h, c) * band_bins(mq, B, dirs, bin_tol, bins) != 1);
+        }
     }
 }

@@ -10,10 +10,8 @@ The steps of Alg. 2 in the paper's order, for one tuple (p_1, ..., p_k):
     [p_i'] = p_i + [dx] + [dy]
     [p_i', n_i'] = Project([p_i'], D_i)          nearest point of the domain
 
-The projection decides an index, so it is taken in the kernel's precision: the
-normals in FP64 rounded to FP32, the tangent basis, mutated point and squared
-distances in FP32 with the same operations in the same order (no fused
-multiply-adds), which makes it bit-exact.
+The whole iteration is FP64: the tangent basis of the (FP32-given) normal, the
+Box-Muller pair, the mutated point and the distances of the projection.
     (p_i, n_i) = argmin J over the candidates     J = closure margin (closure_lp)
 
 Readings (the paper leaves them open): the current point competes with the
@@ -27,11 +25,13 @@ counter (pose, tau, (it k + i) ceil(n_in / 2) + c / 2, 0xA162), key seed, words
 (2 (c mod 2), 2 (c mod 2) + 1) -> u1 = ((w >> 8) + 1) 2^-24,
 u2 = (w' >> 8) 2^-24, (g1, g2) = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2).
 
-Each decision the two sides could take differently is recorded: a normal whose
-FP64 value lies within a few FP64 ulps of an FP32 rounding boundary, a
+Each decision that a correct FP32 evaluation could take differently is
+recorded as ambiguous: a projection whose nearest and second-nearest domain
+points lie within PROJ_GAP = 1e-7 m of the same distance from the mutated
+point (far above the FP32 rounding of coordinates near 0.1 m, ~1e-8 m), a
 replacement test within 2e-4 max(J, eps) of its threshold (the closure-margin
-parity tolerance on each side), or a margin within a factor 2 of zero_tol.  Tests compare
-only tuples whose whole path is clear of those.
+parity tolerance on each side), or a margin within a factor 2 of zero_tol.
+Tests compare only tuples whose whole path is clear of those.
 """
 from __future__ import annotations
 
@@ -44,16 +44,7 @@ from . import _get_pool, closure_lp, philox4x32_10
 OPT_TAG = 0xA162
 
 
-def _f32_checked(v: float):
-    """FP32 rounding of an FP64 value, and whether the value lies so close to a
-    rounding boundary (within a few FP64 ulps) that another correctly rounded
-    FP64 evaluation of the same expression could round the other way."""
-    f = np.float32(v)
-    lo = np.nextafter(f, np.float32(-np.inf))
-    hi = np.nextafter(f, np.float32(np.inf))
-    tol = 8.0 * float(np.spacing(abs(v))) if v != 0.0 else 0.0
-    amb = any(abs(v - (float(f) + float(b)) / 2.0) <= tol for b in (lo, hi))
-    return f, amb
+PROJ_GAP = 1e-7  # metres: distance gap below which a projection is ambiguous
 
 
 def box_muller(w0: int, w1: int):
@@ -76,31 +67,33 @@ def mutation_normals(pose: int, tau: int, it: int, i: int, k: int, n_in: int, se
     return out
 
 
-def tangent_basis32(n):
-    """Duff et al. 2017 basis (x, y) of nu = -n, every operation rounded to FP32."""
-    f = np.float32
-    vx, vy, vz = -f(n[0]), -f(n[1]), -f(n[2])
-    sgn = f(math.copysign(1.0, float(vz)))
-    aa = f(-1.0) / (sgn + vz)
-    bb = (vx * vy) * aa
-    x = (f(1.0) + ((sgn * vx) * vx) * aa, sgn * bb, -(sgn * vx))
-    y = (bb, sgn + (vy * vy) * aa, -vy)
+def tangent_basis(n):
+    """Duff et al. 2017 branchless orthonormal basis (x, y) of nu = -n, FP64."""
+    vx, vy, vz = -float(n[0]), -float(n[1]), -float(n[2])
+    sgn = math.copysign(1.0, vz)
+    aa = -1.0 / (sgn + vz)
+    bb = vx * vy * aa
+    x = (1.0 + sgn * vx * vx * aa, sgn * bb, -sgn * vx)
+    y = (bb, sgn + vy * vy * aa, -vy)
     return x, y
 
 
-def mutate32(p, xv, yv, g1, g2, sigma):
-    """p + sigma (g1 x + g2 y) in FP32, operation by operation."""
-    f = np.float32
-    s = f(sigma)
-    return tuple(f(p[d]) + s * (g1 * xv[d] + g2 * yv[d]) for d in range(3))
+def mutate(p, xv, yv, g1, g2, sigma):
+    """p + sigma (g1 x + g2 y), FP64."""
+    return tuple(float(p[d]) + float(sigma) * (g1 * xv[d] + g2 * yv[d]) for d in range(3))
 
 
-def project_to_domain(pts32: np.ndarray, dom: np.ndarray, q):
-    """Nearest domain point to q by FP32 squared distance ((dx dx + dy dy) + dz dz,
-    dx = x - q, each operation rounded), lowest index on ties."""
-    d = [pts32[dom, j] - np.float32(q[j]) for j in range(3)]
-    d2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]
-    return int(dom[int(np.argmin(d2))])
+def project_to_domain(pts64: np.ndarray, dom: np.ndarray, q, gap: float = PROJ_GAP):
+    """Nearest domain point to q by FP64 Euclidean distance, lowest index on
+    exact ties; also whether a domain point at another location lies within
+    `gap` of the same distance (then an FP32 evaluation may pick it instead;
+    copies of the nearest point tie in every precision and go to the lowest
+    index on both sides)."""
+    P = pts64[dom]
+    d = np.sqrt(((P - np.asarray(q, np.float64)[None, :]) ** 2).sum(axis=1))
+    j = int(np.argmin(d))
+    other = np.any(P != P[j][None, :], axis=1)
+    return int(dom[j]), bool(np.any(other & (d <= d[j] + gap)))
 
 
 def _margin(soa64, ids, mu, K, c, rho):
@@ -121,8 +114,8 @@ def optimize_tuple(soa, masks_pose, ids, fingers, pose, tau, mu, K, c, rho, eps,
     if any(x < 0 or x >= N for x in ids):
         return ids, math.inf, False
     amb = False
-    pts32 = np.ascontiguousarray(np.asarray(soa, np.float32)[0:3].T)
-    nrm32 = np.asarray(soa, np.float32)[3:6].T
+    pts64 = np.ascontiguousarray(soa64[0:3].T)
+    nrm64 = soa64[3:6].T
     J = _margin(soa64, ids, mu, K, c, rho)
 
     def cls(v):
@@ -140,14 +133,12 @@ def optimize_tuple(soa, masks_pose, ids, fingers, pose, tau, mu, K, c, rho, eps,
                 break
             x0 = ids[i]
             dom = np.nonzero(bits[i][:N])[0]
-            xv, yv = tangent_basis32(nrm32[x0])
+            xv, yv = tangent_basis(nrm64[x0])
             cands = []
             for (g1, g2) in mutation_normals(pose, tau, it, i, k, n_inner, seed):
-                g1f, a1 = _f32_checked(g1)
-                g2f, a2 = _f32_checked(g2)
-                amb |= a1 or a2
-                q = mutate32(pts32[x0], xv, yv, g1f, g2f, sigma)
-                cands.append(project_to_domain(pts32, dom, q))
+                xc, a = project_to_domain(pts64, dom, mutate(pts64[x0], xv, yv, g1, g2, sigma))
+                amb |= a
+                cands.append(xc)
             best_c, best_raw, best_x = Jc, J, x0
             seen = {x0}
             for xc in cands:

@@ -174,11 +174,15 @@ def _pose_targets(soa, poses, pose_idx, x):
 
 def ik_dls(hand, qs, inv_h, bins, soa, poses, T: int, k: int, tuples, fingers, accept, beta=0.01, lam=1e-4,
            n_phase1=16, n_rounds=4, n_phase2=4, tol_pos=2e-3, tol_cos=None, tol_deg=20.0, rep=None,
-           perturb: float = 0.0, dilation=None):
+           perturb: float = 0.0, dilation=None, rep_sure=None):
     """Kinematics optimisation of tuple slots (Sec. 5.5), same outputs as the
     library call: dict(q [n,F,J], used, contacts [6,n*k], rtuples [n,k],
-    resid [n,k,2], ok [n], miss [n,k] (contact code without representative)).
-    ``rep`` maps finger -> {packed code: s*M + m}; computed when None.
+    resid [n,k,2], ok [n], miss [n,k] (contact code without representative),
+    start_amb [n,k] (the contact's FP64 code, or its representative, could
+    change under a perturbation within the 1e-5 m / 1e-6 band, so a correct
+    FP32 lookup may start from another sample)).
+    ``rep`` maps finger -> {packed code: s*M + m}; ``rep_sure`` finger -> set
+    of codes whose representative is band-stable; both computed when None.
     ``perturb`` shifts targets by that many metres and the starting joints by
     that many radians (a sensitivity probe)."""
     tuples = np.asarray(tuples, np.int64).reshape(-1, k)
@@ -196,7 +200,7 @@ def ik_dls(hand, qs, inv_h, bins, soa, poses, T: int, k: int, tuples, fingers, a
     out = dict(q=np.zeros((n, F, J), np.float64), used=np.zeros((n, F, J), np.uint8),
                contacts=np.zeros((6, n * k)), rtuples=np.full((n, k), -1, np.int64),
                resid=np.tile(np.array([np.inf, -2.0]), (n, k, 1)), ok=np.zeros(n, np.uint8),
-               miss=np.zeros((n, k), bool))
+               miss=np.zeros((n, k), bool), start_amb=np.zeros((n, k), bool))
     slots = np.nonzero(valid)[0]
     if slots.size == 0:
         return out
@@ -206,8 +210,11 @@ def ik_dls(hand, qs, inv_h, bins, soa, poses, T: int, k: int, tuples, fingers, a
     f = fingers[sl, cc]
     pose_idx = sl // T
     if rep is None:
-        rep = {ff: rep_codes(hand, qs, inv_h, bins, ff) for ff in np.unique(f).tolist()}
-    codes = point_codes(soa, poses, pose_idx, x, inv_h, bins)
+        both = {ff: rep_codes(hand, qs, inv_h, bins, ff, with_sure=True) for ff in np.unique(f).tolist()}
+        rep = {ff: v[0] for ff, v in both.items()}
+        rep_sure = {ff: v[1] for ff, v in both.items()}
+    codes, camb = point_codes(soa, poses, pose_idx, x, inv_h, bins, with_amb=True)
+
     def lookup(ff, cd):
         # the contact's own bin first; with dilated bins, then the lowest other accepted bin present
         kx, ky, kz, b = cd
@@ -215,12 +222,15 @@ def ik_dls(hand, qs, inv_h, bins, soa, poses, T: int, k: int, tuples, fingers, a
         if dilation is not None:
             order += [b2 for b2 in range(32) if (int(dilation[b]) >> b2) & 1 and b2 != b]
         for b2 in order:
-            v = rep[int(ff)].get(pack_code(ff, kx, ky, kz, b2))
+            key = pack_code(ff, kx, ky, kz, b2)
+            v = rep[int(ff)].get(key)
             if v is not None:
-                return v
-        return -1
+                return v, rep_sure is not None and key not in rep_sure[int(ff)]
+        return -1, False
 
-    v = np.array([lookup(ff, cd) for ff, cd in zip(f.tolist(), codes.tolist())], np.int64)
+    found = [lookup(ff, cd) for ff, cd in zip(f.tolist(), codes.tolist())]
+    v = np.array([r[0] for r in found], np.int64)
+    out["start_amb"][sl, cc] = camb.astype(bool) | np.array([r[1] for r in found], bool)
     miss = v < 0
     vv = np.where(miss, 0, v)
     s_idx, m_idx = vv // M, vv % M

@@ -403,9 +403,11 @@ def score_params(T, k, mu, K, eps, centroid, rho, seed, tuples_given=False) -> S
                        1 if tuples_given else 0)
 
 
-def score_tuples(soa, n_fingers: int, masks, counts, prm: ScoreParams, tuples=None, fingers=None, stream=None):
+def score_tuples(soa, n_fingers: int, masks, counts, prm: ScoreParams, tuples=None, fingers=None, stream=None,
+                 margin=None, accept=None):
     """cf_score_tuples -> (tuples [P,T,k] int32, fingers [P,T,k] uint8, margin [P,T] f32, accept [P,T] uint8).
-    With prm.tuples_given the given ``tuples`` tensor is scored (masks/counts may be None)."""
+    With prm.tuples_given the given ``tuples`` tensor is scored (masks/counts may be None).
+    Output tensors not given are allocated."""
     import torch
     obj = points_struct(soa)
     dev = soa.device
@@ -416,13 +418,15 @@ def score_tuples(soa, n_fingers: int, masks, counts, prm: ScoreParams, tuples=No
     else:
         P = int(counts.shape[0])
     T, k = int(prm.n_tuples), int(prm.k)
-    _check_score_shapes(soa, n_fingers, masks, counts, prm, P, tuples, fingers)
+    _check_score_shapes(soa, n_fingers, masks, counts, prm, P, tuples, fingers, margin, accept)
     if tuples is None:
         tuples = torch.empty((P, T, k), dtype=torch.int32, device=dev)
     if fingers is None and not prm.tuples_given:
         fingers = torch.empty((P, T, k), dtype=torch.uint8, device=dev)
-    margin = torch.empty((P, T), dtype=torch.float32, device=dev)
-    accept = torch.empty((P, T), dtype=torch.uint8, device=dev)
+    if margin is None:
+        margin = torch.empty((P, T), dtype=torch.float32, device=dev)
+    if accept is None:
+        accept = torch.empty((P, T), dtype=torch.uint8, device=dev)
     mp = _dev(masks, torch.int32, "masks") if masks is not None else None
     cp = _dev(counts, torch.int32, "counts") if counts is not None else None
     fp = _dev(fingers, torch.uint8, "fingers") if fingers is not None else None

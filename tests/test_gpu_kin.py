@@ -72,15 +72,27 @@ def _decode_rep(field):
 
 
 @pytest.mark.parametrize("name,S", [("tiny_sphere", 2048), ("hand16_superquadric", 4096)])
-def test_rep_table_bit_exact(cf, name, S):
+def test_rep_table_against_fp64(cf, name, S):
+    """Representatives equal the FP64 oracle's on every code whose
+    representative no perturbation within the band can change; the others
+    (and codes present on one side only, which the field check bounds) are
+    counted and stay rare."""
     w = synth.workload(name, P=2, S=S)
     field = cf.build(w.hand, w.inv_h, w.bins, torch.from_numpy(w.q).cuda(), want_rep=True)
     g = _decode_rep(field)
-    o = {}
+    o, sure = {}, set()
     for f in range(w.hand.F):
-        o.update(oracle.rep_codes(w.hand, w.q, w.inv_h, w.bins, f))
-    assert len(g) == len(o)
-    assert g == o
+        r, s_ = oracle.rep_codes(w.hand, w.q, w.inv_h, w.bins, f, with_sure=True)
+        o.update(r)
+        sure |= s_
+    both = set(g) & set(o)
+    bad = [c for c in both if g[c] != o[c] and c in sure]
+    differ = sum(1 for c in both if g[c] != o[c]) + len(set(g) ^ set(o))
+    print(f"{name}: {len(o)} representatives, differ {differ}, not band-stable {len(o) - len(sure)}")
+    assert not bad, f"{len(bad)} band-stable representatives differ"
+    assert set(o) - set(g) <= set(o) - sure  # a code missing on the GPU is never a stable one
+    assert differ <= 1e-3 * len(o)
+    assert len(o) - len(sure) <= 0.05 * len(o)
     assert cf.device_status() == 0
 
 
@@ -91,8 +103,10 @@ def _ik_both(cf, w, field, soa, tup, fing, valid, prm_kw=None):
                   cf.ik_params(**prm_kw))
     torch.cuda.synchronize()
     g = {k: v.cpu().numpy() for k, v in g.items()}
-    rep = {f: oracle.rep_codes(w.hand, w.q, w.inv_h, w.bins, f) for f in range(w.hand.F)}
-    okw = dict(beta=prm_kw.get("beta", 0.01), lam=prm_kw.get("lam", 1e-4), n_phase1=prm_kw.get("n_phase1", 16),
+    both = {f: oracle.rep_codes(w.hand, w.q, w.inv_h, w.bins, f, with_sure=True) for f in range(w.hand.F)}
+    rep = {f: v[0] for f, v in both.items()}
+    okw = dict(rep_sure={f: v[1] for f, v in both.items()}, beta=prm_kw.get("beta", 0.01),
+               lam=prm_kw.get("lam", 1e-4), n_phase1=prm_kw.get("n_phase1", 16),
                n_rounds=prm_kw.get("n_rounds", 4), n_phase2=prm_kw.get("n_phase2", 4),
                tol_pos=prm_kw.get("tol_pos", 2e-3), tol_deg=prm_kw.get("tol_deg", 20.0), rep=rep)
     o = K.ik_dls(w.hand, w.q, w.inv_h, w.bins, soa, w.poses, w.T, w.k, tup, fing, valid, **okw)
@@ -111,7 +125,8 @@ def _sensitive(w, o, pr, tup, fing, valid):
         fc = np.minimum(f[:, c], w.hand.F - 1)
         dq = np.abs(o["q"][np.arange(n), fc] - pr["q"][np.arange(n), fc]).max(axis=1)
         sens[:, c] = (dq > SENS_Q) | (np.abs(o["resid"][:, c, 0] - tol_pos) <= SENS_POS) | \
-                     (np.abs(o["resid"][:, c, 1] - tol_cos) <= SENS_COS) | o["miss"][:, c] | pr["miss"][:, c]
+                     (np.abs(o["resid"][:, c, 1] - tol_cos) <= SENS_COS) | o["miss"][:, c] | pr["miss"][:, c] | \
+                     o["start_amb"][:, c]
     return sens & valid.astype(bool)[:, None]
 
 
@@ -142,8 +157,9 @@ def test_ik_parity(cf, name, P, S):
             f"max diffs q {d['q']:.3g} pos {d['pos']:.3g} cos {d['cos']:.3g} point {d['cp']:.3g} "
             f"normal {d['cn']:.3g}, ok gpu {int(g['ok'].sum())} oracle {int(o['ok'].sum())}")
     print(info)
-    # structure: bit-exact
-    assert np.array_equal(g["used"], o["used"]), info
+    # structure: bit-exact wherever the starting sample is decided clear of the band
+    firm = ~o["start_amb"].any(axis=1)
+    assert np.array_equal(g["used"][firm], o["used"][firm]), info
     assert not g["ok"][~att].any(), info
     e = np.arange(n * k).reshape(n, k)
     assert np.array_equal(g["rtuples"], np.where(g["ok"][:, None].astype(bool), e, -1)), info
@@ -214,8 +230,7 @@ def test_sdf_parity(cf, name):
 
 def _realize_inputs(w):
     soa, tup, fing, valid = _oracle_tuples(w)
-    rep = {f: oracle.rep_codes(w.hand, w.q, w.inv_h, w.bins, f) for f in range(w.hand.F)}
-    o = K.ik_dls(w.hand, w.q, w.inv_h, w.bins, soa, w.poses, w.T, w.k, tup, fing, valid, rep=rep)
+    o = K.ik_dls(w.hand, w.q, w.inv_h, w.bins, soa, w.poses, w.T, w.k, tup, fing, valid)
     return soa, tup, fing, valid, o
 
 

@@ -8,6 +8,7 @@ import pytest
 
 import oracle
 import synth
+from parity_checks import GivenCodes
 from oracle import kinematics as K
 from oracle import placement as PL
 
@@ -35,8 +36,10 @@ def test_canonical_placement(cf):
 @pytest.mark.parametrize("name", ["tiny_sphere", "hand16_superquadric"])
 def test_exhaustive_placement(cf, name):
     w = synth.workload(name, P=1, S=2048)
-    fd = oracle.Field(w.hand, w.q, w.inv_h, w.bins)
     field = cf.build(w.hand, w.inv_h, w.bins, torch.from_numpy(w.q).cuda())
+    # placement draws a code by its rank in the table, so it is checked given the GPU's own table
+    # (the table itself is checked against the FP64 field in the parity tests)
+    fd = GivenCodes(field, w.hand.F)
     soa = torch.from_numpy(w.obj.soa()).cuda()
     P = 512
     gp = cf.place_exhaustive(field, soa, P, seed=3)

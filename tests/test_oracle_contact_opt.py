@@ -35,37 +35,42 @@ def test_box_muller_extremes():
 
 def test_projection_is_nearest_domain_point():
     rng = np.random.default_rng(1)
-    pts = rng.normal(size=(500, 3)).astype(np.float32)
+    pts = rng.normal(size=(500, 3))
     dom = np.sort(rng.choice(500, 120, replace=False))
     for _ in range(50):
-        q = rng.normal(size=3).astype(np.float32)
-        x = CO.project_to_domain(pts, dom, q)
+        q = rng.normal(size=3)
+        x, amb = CO.project_to_domain(pts, dom, q)
         assert x in dom
-        d = np.linalg.norm(pts[dom].astype(np.float64) - q, axis=1)
-        assert np.linalg.norm(pts[x].astype(np.float64) - q) <= d.min() * (1 + 1e-6)
-    # exact copies of the nearest point: the lowest index
+        d = np.linalg.norm(pts[dom] - q, axis=1)  # brute force over the domain
+        assert x == dom[int(np.argmin(d))]
+        assert amb == (np.sort(d)[1] - d.min() <= CO.PROJ_GAP)
+    # exact copies of the nearest point: the lowest index, and no ambiguity
+    # (a copy ties in every precision)
     pts2 = np.vstack([pts, pts[dom[5]][None]])
     dom2 = np.append(dom, 500)
-    assert CO.project_to_domain(pts2, dom2, pts[dom[5]]) == dom[5]
+    assert CO.project_to_domain(pts2, dom2, pts[dom[5]]) == (dom[5], False)
+    # a distinct point at the same distance is ambiguous
+    q = pts[dom[5]] + np.array([0.0, 0.0, 1e-3])
+    pts4 = np.vstack([pts, q + np.array([0.0, 0.0, 1e-3])])
+    assert CO.project_to_domain(pts4, dom2, q) == (dom[5], True)
+    # a point 2e-7 m nearer than the next one is clear of the band
+    q = pts[dom[7]] + np.array([1e-3, 0.0, 0.0])
+    pts3 = np.vstack([pts, q + np.array([-1e-3 - 2e-7, 0.0, 0.0])])
+    pts3[dom[7]] = q + np.array([-1e-3, 0.0, 0.0])
+    assert CO.project_to_domain(pts3, np.append(dom, 500), q)[1] is False
 
 
-def test_tangent_basis32_is_orthonormal():
+def test_tangent_basis_is_orthonormal():
     rng = np.random.default_rng(2)
     for _ in range(200):
         n = rng.normal(size=3)
         n /= np.linalg.norm(n)
-        x, y = CO.tangent_basis32(n.astype(np.float32))
-        x, y = np.array(x, np.float64), np.array(y, np.float64)
-        assert abs(x @ y) < 1e-6 and abs(x @ n) < 1e-6 and abs(y @ n) < 1e-6
-        assert abs(np.linalg.norm(x) - 1) < 1e-6 and abs(np.linalg.norm(y) - 1) < 1e-6
-
-
-def test_f32_rounding_check():
-    f, amb = CO._f32_checked(0.1)
-    assert f == np.float32(0.1) and not amb
-    one = np.float32(1.0)
-    mid = (1.0 + float(np.nextafter(one, np.float32(2.0)))) / 2.0  # a tie between two floats
-    assert CO._f32_checked(mid)[1]
+        x, y = CO.tangent_basis(n)
+        x, y = np.array(x), np.array(y)
+        assert abs(x @ y) < 1e-12 and abs(x @ n) < 1e-12 and abs(y @ n) < 1e-12
+        assert abs(np.linalg.norm(x) - 1) < 1e-12 and abs(np.linalg.norm(y) - 1) < 1e-12
+        # right-handed: x cross y = nu = -n
+        assert np.allclose(np.cross(x, y), -n, atol=1e-12)
 
 
 @pytest.fixture(scope="module")

@@ -112,35 +112,41 @@ def test_identity_pose_on_pretransformed_points_gives_the_same_masks(tiny):
     ident = np.array([[1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0]], np.float32)
     for i in range(3):
         T = w.poses[i].reshape(3, 4)
-        R, t = T[:, :3], T[:, 3]
-        # FP32 single-rounding fma evaluation, x then y then z, like the oracle
+        R, t = T[:, :3].astype(np.float64), T[:, 3].astype(np.float64)
+        # the moved points and normals in FP64, rounded once to the FP32 inputs
         pre = np.empty_like(soa)
-        for r in range(3):
-            acc = np.float32(t[r])
-            accn = np.float32(0)
-            for c in range(3):
-                acc = np.float32(np.float64(R[r, c]) * np.float64(soa[c]) + np.float64(acc))
-            pre[r] = acc
-            pre[3 + r] = np.float32(np.float64(R[r, 2]) * np.float64(soa[5]) +
-                                    np.float64(np.float32(np.float64(R[r, 1]) * np.float64(soa[4]) +
-                                                          np.float64(np.float32(R[r, 0] * soa[3])))))
+        pre[:3] = (R @ soa[:3].astype(np.float64) + t[:, None]).astype(np.float32)
+        pre[3:] = (R @ soa[3:].astype(np.float64)).astype(np.float32)
         mi, _ = fd.query(pre, ident)
-        # double rounding in the numpy emulation may move a handful of points by one ulp
+        # rounding the moved points to FP32 may move a handful across a cell face
         diff = np.unpackbits((mi[0] ^ m[i]).view(np.uint8)).sum()
         assert diff <= 2
 
 
 def test_ambiguity_band_brackets_the_fp32_decision(tiny):
-    """hit_sure <= FP32 decision <= hit_possible entry by entry: every entry the
-    FP32 decision could get wrong is flagged ambiguous, and the FP64-decided
-    masks differ from the FP32 ones only on flagged entries."""
+    """Every entry on which an FP32 evaluation of the same definition (the
+    oracle's own diagnostic chain) decides otherwise than the FP64 oracle is
+    flagged ambiguous; the flagged entries stay a small fraction."""
     w = synth.workload("tiny_sphere", P=32, S=1024)
     fd = oracle.Field(w.hand, w.q, w.inv_h, w.bins, band=True)
-    m32, c32, amb, m64 = fd.query(w.obj.soa(), w.poses, amb=True, mask64=True)
+    m64, c64, amb, m32 = fd.query(w.obj.soa(), w.poses, amb=True, mask32=True)
     N = w.obj.N
     b32, b64 = _bits(m32, N), _bits(m64, N)
     assert np.all(amb[b32 != b64] == 1)
     assert amb.mean() < 0.05
+    assert np.array_equal(c64, b64.sum(axis=2).astype(np.uint32))
+
+
+def test_field_code_sets_nest():
+    """The band's code sets bracket the FP64 decisions: sure <= fp64 <= possible,
+    and the FP32 diagnostic codes lie within the same brackets."""
+    w = synth.workload("hand16_superquadric", P=1, S=2048)
+    fd = oracle.Field(w.hand, w.q, w.inv_h, w.bins, band=True)
+    for f in range(w.hand.F):
+        sets = {k: set(map(tuple, fd.codes(f, k).tolist())) for k in ("fp64", "fp32", "possible", "sure")}
+        assert sets["sure"] <= sets["fp64"] <= sets["possible"]
+        assert sets["sure"] <= sets["fp32"] <= sets["possible"]
+        assert len(sets["possible"] - sets["sure"]) < 0.05 * len(sets["fp64"])
 
 
 def test_paper_normal_bin_cone_half_angle():
@@ -162,11 +168,11 @@ def test_paper_normal_bin_cone_half_angle():
     q = np.zeros((hand.F, hand.J, 1), np.float32)
     fd = oracle.Field(hand, q, np.float32(100.0), bins)
     ident = np.array([[1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0]], np.float32)
-    p32, n32, _, _ = oracle.contact_vectors(hand, 0, np.zeros(hand.J))
+    _, _, p64, n64 = oracle.contact_vectors(hand, 0, np.zeros(hand.J))
     codes = fd.codes(0)
     for m in range(hand.M):
-        cm = codes[np.all(codes[:, :3] == np.floor(p32[m].astype(np.float64) * 100.0).astype(np.int64), axis=1)]
+        cm = codes[np.all(codes[:, :3] == np.floor(p64[m] * np.float64(np.float32(100.0))).astype(np.int64), axis=1)]
         d = bins[cm[:, 3]].astype(np.float64)
-        ang.append(np.degrees(np.arccos(np.clip(d @ n32[m].astype(np.float64), -1, 1))).min())
+        ang.append(np.degrees(np.arccos(np.clip(d @ n64[m], -1, 1))).min())
     ang = np.array(ang)
     assert ang.max() < 1.5 * cap and np.median(ang) < cap
