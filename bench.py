@@ -521,6 +521,9 @@ def run_ours(args):
         ws, fields = _hand_fields(cf, torch, dev)
         if args.batch_objects > 0:
             line["batched"] = run_batched(cf, torch, dev, args.batch_objects, ws, fields)
+            # a mix where most objects leave the GPU idle in a launch of their own
+            line["batched_small_objects"] = run_batched(cf, torch, dev, 4 * args.batch_objects, ws, fields,
+                                                        n_range=(1024, 8192), p_range=(256, 2048), tune=False)
         if args.served_seconds > 0:
             rates = [float(x) for x in args.served_rates.split(",") if x]
             line["served"] = run_served(cf, torch, dev, ws, fields, rates, args.served_seconds)
@@ -767,15 +770,17 @@ def _hand_fields(cf, torch, dev):
     return ws, fields
 
 
-def run_batched(cf, torch, dev, n_objects, ws, fields):
+def run_batched(cf, torch, dev, n_objects, ws, fields, n_range=(2048, 131072), p_range=(4096, 32768),
+                tune=True):
     """The many-object batch: every object's query + sampling + scoring, once as
-    plain per-object calls on one stream, once as the batch's graph replay."""
+    plain per-object calls on one stream, once as the batch's graph replay
+    (one persistent launch per stage)."""
     import numpy as np
 
     import synth
     names = ["tiny_sphere", "hand16_superquadric", "hand20_tool"]
     t_gen = time.perf_counter()
-    specs = synth.batch_objects(n_objects, seed=0)
+    specs = synth.batch_objects(n_objects, seed=0, n_range=n_range, p_range=p_range)
     items = []
     for j, sp in enumerate(specs):
         hi = names.index(sp["hand"])
@@ -814,25 +819,32 @@ def run_batched(cf, torch, dev, n_objects, ws, fields):
     batch = cf.Batch(items)
     t_batch_default = timed(batch.run)
     batch.close()
-    # the autotuner picks the launch shapes on these objects; the batch is re-created under them
-    t_tune = time.perf_counter()
-    tuning, tune_ms = cf.autotune(items, reps=2)
-    t_tune = time.perf_counter() - t_tune
-    t_plain_tuned = timed(plain)
+    out = {"objects": n_objects, "pose_point_pairs": pairs, "tuples": tuples,
+           "plain_ms": t_plain, "default_tuning": default_tuning, "batched_ms_default_tuning": t_batch_default,
+           "plain_launches": 3 * n_objects, "generate_s": t_gen,
+           "workload": f"{n_objects} objects (superquadrics / tool composites), points log-uniform "
+                       f"{n_range[0]:,}-{n_range[1]:,}, poses log-uniform {p_range[0]:,}-{p_range[1]:,}, hand per "
+                       "object from the 3/4/5-finger hands (fields cached)"}
+    t_batch = t_batch_default
+    if tune:
+        # the autotuner picks the launch shapes on these objects; the batch is re-created under them
+        t_tune = time.perf_counter()
+        tuning, tune_ms = cf.autotune(items, reps=2)
+        out.update(autotuned=tuning, autotune_s=time.perf_counter() - t_tune, autotune_query_score_ms=list(tune_ms),
+                   plain_ms_autotuned=timed(plain))
+        batch = cf.Batch(items)
+        t_batch = timed(batch.run)
+        batch.close()
+        cf.set_tuning(*default_tuning.values())
     batch = cf.Batch(items)
-    t_batch = timed(batch.run)
+    batch.run()
+    torch.cuda.synchronize()
     accepted = sum(int(it["accept"].sum()) for it in items)
     n_launch, n_groups = batch.launches()
     batch.close()
-    return {"objects": n_objects, "pose_point_pairs": pairs, "tuples": tuples, "accepted": accepted,
-            "plain_ms": t_plain, "batched_ms": t_batch, "plain_grasps_per_s": accepted / (t_plain / 1e3),
-            "batched_grasps_per_s": accepted / (t_batch / 1e3), "batched_launches": n_launch,
-            "default_tuning": default_tuning, "batched_ms_default_tuning": t_batch_default,
-            "autotuned": tuning, "plain_ms_autotuned": t_plain_tuned, "autotune_s": t_tune,
-            "autotune_query_score_ms": list(tune_ms),
-            "plain_launches": 3 * n_objects, "generate_s": t_gen,
-            "workload": "64 objects (superquadrics / tool composites), points log-uniform 2,048-131,072, poses "
-                        "log-uniform 4,096-32,768, hand per object from the 3/4/5-finger hands (fields cached)"}
+    out.update(accepted=accepted, batched_ms=t_batch, plain_grasps_per_s=accepted / (t_plain / 1e3),
+               batched_grasps_per_s=accepted / (t_batch / 1e3), batched_launches=n_launch)
+    return out
 
 
 def run_served(cf, torch, dev, ws, fields, rates, seconds, pool=24):

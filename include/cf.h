@@ -388,14 +388,15 @@ typedef struct cf_batch_item {
 
 typedef struct cf_batch cf_batch;
 
-/* Plan a batch of objects (fields may differ): items are grouped by kernel
- * variant, and each group runs as ONE launch per step (domain query, tuple
- * sampling, LP scoring), its blocks and tuples spread over the group's
- * objects.  An item whose query (>= 2^25 pose-point pairs) or sampling +
- * scoring (>= 2^17 tuples) fills the GPU by itself runs that step with the
- * single-object kernels instead, inside the same graph.  Results equal the
- * per-object calls bit for bit.  The items' buffers are used in place by every
- * run.  Errors: CF_EINVAL, CF_ENOMEM, CF_ECUDA. */
+/* Plan a batch of objects (fields, hands, sizes and pose counts may differ).
+ * A run is three persistent launches whatever the mix: the domain query of
+ * every object (one grid whose blocks take (object, block of poses) items from
+ * a device work counter and pick the kernel body for the object's hand at run
+ * time), the tuple sampling of every pose, and the LP scoring of every tuple
+ * (one scoring launch per distinct (k, K)).  No kernel waits on another block.
+ * Results equal the per-object calls bit for bit.  The items' buffers are used
+ * in place by every run.  The paper has no counterpart (its forward pass
+ * handles one object).  Errors: CF_EINVAL, CF_ENOMEM, CF_ECUDA. */
 int cf_batch_create(const cf_batch_item *items, int32_t n_items, cf_batch **out);
 
 /* Run the batch after the work already queued on `stream`.  The first run

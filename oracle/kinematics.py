@@ -174,13 +174,14 @@ def _pose_targets(soa, poses, pose_idx, x):
 
 def ik_dls(hand, qs, inv_h, bins, soa, poses, T: int, k: int, tuples, fingers, accept, beta=0.01, lam=1e-4,
            n_phase1=16, n_rounds=4, n_phase2=4, tol_pos=2e-3, tol_cos=None, tol_deg=20.0, rep=None,
-           perturb: float = 0.0, dilation=None, rep_sure=None):
+           perturb: float = 0.0, dilation=None, rep_sure=None, start_tau: float = 1e-6):
     """Kinematics optimisation of tuple slots (Sec. 5.5), same outputs as the
     library call: dict(q [n,F,J], used, contacts [6,n*k], rtuples [n,k],
     resid [n,k,2], ok [n], miss [n,k] (contact code without representative),
     start_amb [n,k] (the contact's FP64 code, or its representative, could
-    change under a perturbation within the 1e-5 m / 1e-6 band, so a correct
-    FP32 lookup may start from another sample)).
+    change under a perturbation of start_tau metres (1e-6 in cosine on a bin
+    tie), so a correct FP32 lookup may start from another sample; 1e-6 m is
+    some 20 times the FP32 rounding of the kinematic chain)).
     ``rep`` maps finger -> {packed code: s*M + m}; ``rep_sure`` finger -> set
     of codes whose representative is band-stable; both computed when None.
     ``perturb`` shifts targets by that many metres and the starting joints by
@@ -210,10 +211,11 @@ def ik_dls(hand, qs, inv_h, bins, soa, poses, T: int, k: int, tuples, fingers, a
     f = fingers[sl, cc]
     pose_idx = sl // T
     if rep is None:
-        both = {ff: rep_codes(hand, qs, inv_h, bins, ff, with_sure=True) for ff in np.unique(f).tolist()}
+        both = {ff: rep_codes(hand, qs, inv_h, bins, ff, with_sure=True, tau=start_tau)
+                for ff in np.unique(f).tolist()}
         rep = {ff: v[0] for ff, v in both.items()}
         rep_sure = {ff: v[1] for ff, v in both.items()}
-    codes, camb = point_codes(soa, poses, pose_idx, x, inv_h, bins, with_amb=True)
+    codes, camb = point_codes(soa, poses, pose_idx, x, inv_h, bins, with_amb=True, tau=start_tau)
 
     def lookup(ff, cd):
         # the contact's own bin first; with dilated bins, then the lowest other accepted bin present

@@ -895,11 +895,12 @@ struct cf_batch {
     cudaStream_t st = nullptr;          // internal stream the graph runs on
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     cudaGraphExec_t exec = nullptr;
-    void *d_block = nullptr;            // descriptors, prefix sums, work counters
-    struct QGroup { FieldGeom g0; QueryDesc *d_descs; int n; int blocks; };
+    void *d_block = nullptr;            // descriptors, prefix sums, the query work counter
+    QueryDesc *d_qdescs = nullptr;      // every object's query
+    int n_q = 0, q_items = 0;
+    unsigned int *d_qwork = nullptr;    // 2 words: the query kernel's item counter (left zero by each launch)
     struct SGroup { ScoreArgs launch; ScoreArgs *d_descs; long long *d_tuple0; int n; long long tuples; };
-    std::vector<QGroup> qgroups;
-    std::vector<SGroup> sgroups;
+    std::vector<SGroup> sgroups;        // one scoring launch per (k, K)
     ScoreArgs *d_sdescs = nullptr;      // all items, for sampling
     long long *d_pose0 = nullptr;
     int n_items = 0;
@@ -908,15 +909,8 @@ struct cf_batch {
     std::vector<FieldGeom> geoms;
     FieldGeom *d_geoms = nullptr;
     int launches = 0;
-    int ppb = 4;                        // query poses per block (the tuning at creation)
-    // items big enough to fill the GPU alone run the single-object kernels (inside the same graph)
-    std::vector<cf_batch_item> q_single;
-    std::vector<ScoreArgs> s_single;    // work counters in d_block
+    int ppb = 4;                        // query poses per item (the tuning at creation)
 };
-
-// an item's query / sampling + scoring fills the GPU by itself from these sizes on
-constexpr long long kBatchAlonePairs = 1LL << 25;
-constexpr long long kBatchAloneTuples = 1LL << 17;
 
 extern "C" int cf_batch_create(const cf_batch_item *items, int32_t n_items, cf_batch **out) {
     if (!items || !out || n_items < 1) return fail(CF_EINVAL, "items / out NULL or n_items < 1");
@@ -949,83 +943,56 @@ extern "C" int cf_batch_create(const cf_batch_item *items, int32_t n_items, cf_b
         }
         geom_of[i] = gi;
     }
-    std::vector<char> alone_q(n_items), alone_s(n_items);
+    // the query: every object in one persistent launch, items = (object, block of ppb poses)
+    std::vector<QueryDesc> qdesc_all;
+    long long q_items = 0;
     for (int i = 0; i < n_items; ++i) {
-        alone_q[i] = (long long)items[i].n_poses * items[i].obj.n >= kBatchAlonePairs;
-        alone_s[i] = (long long)items[i].n_poses * sargs[i].T >= kBatchAloneTuples;
-        if (alone_q[i]) b->q_single.push_back(items[i]);
-        if (alone_s[i]) b->s_single.push_back(sargs[i]);
+        if (items[i].n_poses == 0) continue;
+        QueryDesc d;
+        memset(&d, 0, sizeof d);
+        d.obj = items[i].obj;
+        d.poses = items[i].d_poses;
+        d.P = items[i].n_poses;
+        d.W = (items[i].obj.n + 31) / 32;
+        d.masks = items[i].d_masks;
+        d.counts = items[i].d_counts;
+        d.table = items[i].field->d_table;
+        d.geom = geom_of[i];
+        d.block0 = (int)q_items;
+        q_items += query_blocks(d.P, b->ppb);
+        qdesc_all.push_back(d);
     }
-    // query groups: same F, bits and binning method
-    auto qkey = [&](int i) {
-        const FieldGeom &g = b->geoms[geom_of[i]];
-        const int cand = (g.bits > 8 && g.use_cand && g.B > 8) ? 1 : 0;
-        return g.F * 1000 + g.bits * 10 + cand;
-    };
-    std::vector<int> qkeys;
-    for (int i = 0; i < n_items; ++i)
-        if (std::find(qkeys.begin(), qkeys.end(), qkey(i)) == qkeys.end()) qkeys.push_back(qkey(i));
-    // score groups: same k and K (the LP lane layout)
+    if (q_items >= INT_MAX) { delete b; return fail(CF_EINVAL, "the batch holds >= 2^31 query items"); }
+    b->n_q = (int)qdesc_all.size();
+    b->q_items = (int)q_items;
+    // sampling: one launch over every pose; scoring: one launch per (k, K) (the LP lane layout)
+    std::vector<long long> pose0(n_items + 1, 0);
+    size_t smem = 0;
+    for (int i = 0; i < n_items; ++i) {
+        pose0[i + 1] = pose0[i] + sargs[i].P;
+        smem = std::max(smem, score_smem_bytes(sargs[i].F, sargs[i].W, sargs[i].T, sargs[i].k, true));
+    }
+    b->total_poses = pose0[n_items];
+    b->sample_smem = smem;
     std::vector<int> skeys;
     for (int i = 0; i < n_items; ++i) {
         const int key = sargs[i].k * 100 + sargs[i].K;
         if (std::find(skeys.begin(), skeys.end(), key) == skeys.end()) skeys.push_back(key);
     }
-    // host images of everything uploaded
-    std::vector<QueryDesc> qdesc_all;
     std::vector<ScoreArgs> sdesc_all;
-    std::vector<long long> tuple0_all, pose0(n_items + 1, 0);
-    std::vector<size_t> q_off, s_off, t_off;
-    for (int key : qkeys) {
-        cf_batch::QGroup qg{};
-        q_off.push_back(qdesc_all.size());
-        int blocks = 0;
-        for (int i = 0; i < n_items; ++i) {
-            if (qkey(i) != key || items[i].n_poses == 0 || alone_q[i]) continue;
-            QueryDesc d;
-            memset(&d, 0, sizeof d);
-            d.obj = items[i].obj;
-            d.poses = items[i].d_poses;
-            d.P = items[i].n_poses;
-            d.W = (items[i].obj.n + 31) / 32;
-            d.masks = items[i].d_masks;
-            d.counts = items[i].d_counts;
-            d.table = items[i].field->d_table;
-            d.geom = geom_of[i];
-            d.block0 = blocks;
-            blocks += query_blocks(d.P, b->ppb);
-            qdesc_all.push_back(d);
-            qg.g0 = b->geoms[geom_of[i]];
-        }
-        qg.n = (int)(qdesc_all.size() - q_off.back());
-        qg.blocks = blocks;
-        if (qg.n > 0) b->qgroups.push_back(qg);
-        else q_off.pop_back();
-    }
-    std::vector<ScoreArgs> sgrouped;  // items sampled and scored by the grouped launches
-    for (int i = 0; i < n_items; ++i)
-        if (!alone_s[i]) sgrouped.push_back(sargs[i]);
-    const int n_sg = (int)sgrouped.size();
-    pose0.assign(n_sg + 1, 0);
-    size_t smem = 0;
-    for (int i = 0; i < n_sg; ++i) {
-        pose0[i + 1] = pose0[i] + sgrouped[i].P;
-        smem = std::max(smem, score_smem_bytes(sgrouped[i].F, sgrouped[i].W, sgrouped[i].T, sgrouped[i].k, true));
-    }
-    b->total_poses = pose0[n_sg];
-    b->sample_smem = smem;
+    std::vector<long long> tuple0_all;
+    std::vector<size_t> s_off, t_off;
     for (int key : skeys) {
         cf_batch::SGroup sg{};
         const size_t so = sdesc_all.size(), to = tuple0_all.size();
         long long tuples = 0;
-        for (int i = 0; i < n_sg; ++i) {
-            if (sgrouped[i].k * 100 + sgrouped[i].K != key) continue;
+        for (int i = 0; i < n_items; ++i) {
+            if (sargs[i].k * 100 + sargs[i].K != key) continue;
             tuple0_all.push_back(tuples);
-            tuples += (long long)sgrouped[i].P * sgrouped[i].T;
-            sdesc_all.push_back(sgrouped[i]);
-            sg.launch = sgrouped[i];
+            tuples += (long long)sargs[i].P * sargs[i].T;
+            sdesc_all.push_back(sargs[i]);
+            sg.launch = sargs[i];
         }
-        if (sdesc_all.size() == so) continue;  // every item of this (k, K) runs alone
         s_off.push_back(so);
         t_off.push_back(to);
         tuple0_all.push_back(tuples);
@@ -1034,15 +1001,15 @@ extern "C" int cf_batch_create(const cf_batch_item *items, int32_t n_items, cf_b
         if (tuples >= (1LL << 32)) { delete b; return fail(CF_EINVAL, "a score group holds >= 2^32 tuples"); }
         b->sgroups.push_back(sg);
     }
-    // one device block: geoms | query descs | score descs (grouped) | sample descs (all) | pose0 | tuple0 | counters
+    // one device block: geoms | query descs | score descs (grouped) | sample descs (all) | pose0 | tuple0 | counter
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t o_geom = 0, o_q = al(o_geom + sizeof(FieldGeom) * b->geoms.size());
     const size_t o_s = al(o_q + sizeof(QueryDesc) * std::max<size_t>(1, qdesc_all.size()));
     const size_t o_sa = al(o_s + sizeof(ScoreArgs) * std::max<size_t>(1, sdesc_all.size()));
-    const size_t o_p0 = al(o_sa + sizeof(ScoreArgs) * std::max(1, n_sg));
+    const size_t o_p0 = al(o_sa + sizeof(ScoreArgs) * n_items);
     const size_t o_t0 = al(o_p0 + sizeof(long long) * pose0.size());
     const size_t o_w = al(o_t0 + sizeof(long long) * std::max<size_t>(1, tuple0_all.size()));
-    const size_t total = al(o_w + sizeof(unsigned int) * (b->sgroups.size() + b->s_single.size()));
+    const size_t total = al(o_w + 2 * sizeof(unsigned int));
     CF_TRY(cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking), "stream");
     CF_TRY(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming), "event");
     CF_TRY(cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming), "event");
@@ -1050,51 +1017,40 @@ extern "C" int cf_batch_create(const cf_batch_item *items, int32_t n_items, cf_b
     if (rc) { cf_batch_destroy(b); return rc; }
     char *base = (char *)b->d_block;
     b->d_geoms = (FieldGeom *)(base + o_geom);
+    b->d_qdescs = (QueryDesc *)(base + o_q);
     b->d_sdescs = (ScoreArgs *)(base + o_sa);
     b->d_pose0 = (long long *)(base + o_p0);
-    unsigned int *d_work = (unsigned int *)(base + o_w);
-    for (size_t g = 0; g < b->qgroups.size(); ++g) b->qgroups[g].d_descs = (QueryDesc *)(base + o_q) + q_off[g];
+    b->d_qwork = (unsigned int *)(base + o_w);
     for (size_t g = 0; g < b->sgroups.size(); ++g) {
         b->sgroups[g].d_descs = (ScoreArgs *)(base + o_s) + s_off[g];
         b->sgroups[g].d_tuple0 = (long long *)(base + o_t0) + t_off[g];
-        b->sgroups[g].launch.work = d_work + g;
     }
-    for (size_t i = 0; i < b->s_single.size(); ++i) b->s_single[i].work = d_work + b->sgroups.size() + i;
-    std::vector<char> img(total, 0);
+    std::vector<char> img(total, 0);  // the work counter starts at zero
     memcpy(img.data() + o_geom, b->geoms.data(), sizeof(FieldGeom) * b->geoms.size());
     if (!qdesc_all.empty()) memcpy(img.data() + o_q, qdesc_all.data(), sizeof(QueryDesc) * qdesc_all.size());
     if (!sdesc_all.empty()) memcpy(img.data() + o_s, sdesc_all.data(), sizeof(ScoreArgs) * sdesc_all.size());
-    if (n_sg > 0) memcpy(img.data() + o_sa, sgrouped.data(), sizeof(ScoreArgs) * n_sg);
+    memcpy(img.data() + o_sa, sargs.data(), sizeof(ScoreArgs) * n_items);
     memcpy(img.data() + o_p0, pose0.data(), sizeof(long long) * pose0.size());
     memcpy(img.data() + o_t0, tuple0_all.data(), sizeof(long long) * tuple0_all.size());
     cudaError_t e = cudaMemcpyAsync(b->d_block, img.data(), total, cudaMemcpyHostToDevice, b->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
     if (e != cudaSuccess) { cf_batch_destroy(b); return cuda_fail(e, "upload batch"); }
-    b->n_items = n_sg;  // items of the grouped sampling launch
-    b->launches = (int)b->qgroups.size() + (b->total_poses > 0 ? 1 : 0) + (int)b->sgroups.size() +
-                  (int)b->q_single.size() + 2 * (int)b->s_single.size();
+    b->n_items = n_items;
+    b->launches = (b->q_items > 0 ? 1 : 0) + (b->total_poses > 0 ? 1 : 0) + (int)b->sgroups.size();
     *out = b;
     return CF_OK;
 }
 
 namespace {
 int batch_enqueue(cf_batch *b, cudaStream_t st) {
-    for (const cf_batch_item &it : b->q_single)
-        CF_TRY(launch_query(it.field->geom, it.field->d_table, it.obj, it.d_poses, it.n_poses, it.d_masks, it.d_counts,
-                            b->ppb, st), "batch query (alone)");
-    for (const auto &qg : b->qgroups)
-        CF_TRY(launch_query_batch(qg.g0, qg.d_descs, b->d_geoms, qg.n, qg.blocks, b->ppb, st), "batch query");
-    for (const ScoreArgs &a : b->s_single) {
-        CF_TRY(cudaMemsetAsync(a.work, 0, sizeof(unsigned int), st), "batch work counter");
-        CF_TRY(launch_score(a, st), "batch sample + score (alone)");
-    }
+    if (b->q_items > 0)
+        CF_TRY(launch_query_batch(b->d_qdescs, b->d_geoms, b->n_q, b->q_items, b->ppb, b->d_qwork, st), "batch query");
     if (b->total_poses > 0)
         CF_TRY(launch_sample_batch(b->d_sdescs, b->d_pose0, b->n_items, b->total_poses, b->sample_smem, st),
                "batch sample");
-    for (const auto &sg : b->sgroups) {
-        CF_TRY(cudaMemsetAsync(sg.launch.work, 0, sizeof(unsigned int), st), "batch work counter");
-        CF_TRY(launch_score_batch(sg.launch, sg.d_descs, sg.d_tuple0, sg.n, sg.tuples, st), "batch score");
-    }
+    for (const auto &sg : b->sgroups)
+        if (sg.tuples > 0)
+            CF_TRY(launch_score_batch(sg.launch, sg.d_descs, sg.d_tuple0, sg.n, sg.tuples, st), "batch score");
     return CF_OK;
 }
 }  // namespace
@@ -1127,7 +1083,7 @@ extern "C" int cf_batch_run(cf_batch *b, cf_stream stream) {
 extern "C" int cf_batch_launches(const cf_batch *b, int32_t *n_launches, int32_t *n_groups) {
     if (!b) return fail(CF_EINVAL, "batch is NULL");
     if (n_launches) *n_launches = b->launches;
-    if (n_groups) *n_groups = (int)(b->qgroups.size() + b->sgroups.size());
+    if (n_groups) *n_groups = (b->q_items > 0 ? 1 : 0) + (int)b->sgroups.size();
     return CF_OK;
 }
 

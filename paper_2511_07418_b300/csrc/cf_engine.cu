@@ -299,41 +299,28 @@ int run_round(cf_engine *e, std::vector<EngReq *> &act) {
             if (e->fields[f] == act[i]->fd) return (int)f;
         return 0;
     };
-    auto qkey = [&](int i) {
-        const FieldGeom &g = e->geoms[geom_of(i)];
-        return g.F * 1000 + g.bits * 10 + ((g.bits > 8 && g.use_cand && g.B > 8) ? 1 : 0);
-    };
-    std::vector<int> qkeys, skeys;
+    std::vector<int> skeys;
     for (int i = 0; i < n; ++i) {
-        if (std::find(qkeys.begin(), qkeys.end(), qkey(i)) == qkeys.end()) qkeys.push_back(qkey(i));
         const int sk = sargs[i].k * 100 + sargs[i].K;
         if (std::find(skeys.begin(), skeys.end(), sk) == skeys.end()) skeys.push_back(sk);
     }
+    // every request's query chunk in one persistent launch (any hand)
     std::vector<QueryDesc> qd;
-    std::vector<int> q_off, q_n, q_blocks, q_geom;
-    for (int key : qkeys) {
-        q_off.push_back((int)qd.size());
-        int blocks = 0, g0 = 0;
-        for (int i = 0; i < n; ++i) {
-            if (qkey(i) != key) continue;
-            QueryDesc d;
-            memset(&d, 0, sizeof d);
-            d.obj = objs[i];
-            d.poses = act[i]->d_poses + 12 * (size_t)act[i]->pose_next;
-            d.P = act[i]->chunk;
-            d.W = (objs[i].n + 31) / 32;
-            d.masks = act[i]->d_masks;
-            d.counts = act[i]->d_counts;
-            d.table = act[i]->fd->d_table;
-            d.geom = geom_of(i);
-            d.block0 = blocks;
-            blocks += query_blocks(d.P, e->tune.query_ppb);
-            g0 = d.geom;
-            qd.push_back(d);
-        }
-        q_n.push_back((int)qd.size() - q_off.back());
-        q_blocks.push_back(blocks);
-        q_geom.push_back(g0);
+    int q_items = 0;
+    for (int i = 0; i < n; ++i) {
+        QueryDesc d;
+        memset(&d, 0, sizeof d);
+        d.obj = objs[i];
+        d.poses = act[i]->d_poses + 12 * (size_t)act[i]->pose_next;
+        d.P = act[i]->chunk;
+        d.W = (objs[i].n + 31) / 32;
+        d.masks = act[i]->d_masks;
+        d.counts = act[i]->d_counts;
+        d.table = act[i]->fd->d_table;
+        d.geom = geom_of(i);
+        d.block0 = q_items;
+        q_items += query_blocks(d.P, e->tune.query_ppb);
+        qd.push_back(d);
     }
     std::vector<ScoreArgs> sd;
     std::vector<long long> t0, pose0(n + 1, 0);
@@ -365,7 +352,7 @@ int run_round(cf_engine *e, std::vector<EngReq *> &act) {
     const size_t o_p = align256(o_a + sizeof(ScoreArgs) * n);
     const size_t o_t = align256(o_p + sizeof(long long) * pose0.size());
     const size_t o_w = align256(o_t + sizeof(long long) * t0.size());
-    const size_t o_c = align256(o_w + sizeof(unsigned int) * skeys.size());
+    const size_t o_c = align256(o_w + 2 * sizeof(unsigned int));  // the query's item counter, zero
     const size_t o_m = align256(o_c + sizeof(CompactDesc) * n);
     const size_t meta_bytes = sizeof(unsigned) * (1 + 2 * (size_t)n);  // cursor, offsets, counts
     const size_t total = align256(o_m + meta_bytes);
@@ -413,20 +400,16 @@ int run_round(cf_engine *e, std::vector<EngReq *> &act) {
     const FieldGeom *d_geoms = (const FieldGeom *)(base + o_g);
     unsigned int *d_work = (unsigned int *)(base + o_w);
     int launches = 0;
-    for (size_t g = 0; g < qkeys.size(); ++g) {
-        CF_TRY(launch_query_batch(e->geoms[q_geom[g]], (const QueryDesc *)(base + o_q) + q_off[g], d_geoms, q_n[g],
-                                  q_blocks[g], e->tune.query_ppb, e->st), "round query");
-        ++launches;
-    }
+    CF_TRY(launch_query_batch((const QueryDesc *)(base + o_q), d_geoms, n, q_items, e->tune.query_ppb, d_work, e->st),
+           "round query");
+    ++launches;
     CF_TRY(launch_sample_batch((const ScoreArgs *)(base + o_a), (const long long *)(base + o_p), n, pose0[n], smem,
                                e->st), "round sample");
     ++launches;
     for (size_t g = 0; g < skeys.size(); ++g) {
-        ScoreArgs launch = sd[s_off[g]];
-        launch.work = d_work + g;
-        CF_TRY(cudaMemsetAsync(launch.work, 0, sizeof(unsigned int), e->st), "round work counter");
-        CF_TRY(launch_score_batch(launch, (const ScoreArgs *)(base + o_s) + s_off[g], (const long long *)(base + o_t) + t_off[g],
-                                  s_n[g], s_tuples[g], e->st), "round score");
+        CF_TRY(launch_score_batch(sd[s_off[g]], (const ScoreArgs *)(base + o_s) + s_off[g],
+                                  (const long long *)(base + o_t) + t_off[g], s_n[g], s_tuples[g], e->st),
+               "round score");
         ++launches;
     }
     unsigned *d_meta = (unsigned *)(base + o_m);

@@ -289,9 +289,12 @@ struct QueryDesc {
     int block0;   // first block of this object in the batch grid
 };
 
-// All objects of a batch group share F, bits and the binning method.
-cudaError_t launch_query_batch(const FieldGeom &g0, const QueryDesc *d_descs, const FieldGeom *d_geoms, int n_desc,
-                               int total_blocks, int ppb, cudaStream_t st);
+// Every object of a batch in one persistent launch (any hand): items are
+// (object, block of ppb poses), object d's first item is descs[d].block0
+// (ascending).  d_work: 2 device words, zero before the first launch; each
+// launch leaves them zero again.
+cudaError_t launch_query_batch(const QueryDesc *d_descs, const FieldGeom *d_geoms, int n_desc, int total_items,
+                               int ppb, unsigned int *d_work, cudaStream_t st);
 int query_blocks(int P, int ppb);  // grid blocks one object of P poses needs at ppb poses per block
 // The current device's SM count and the resident blocks per SM of kernel `func` at `threads` threads
 // and `smem` dynamic shared bytes, queried once per (device, kernel, shape) and then served from a cache.

@@ -28,6 +28,8 @@
 // so the bin is identical to the full scan's.
 #include <string.h>
 
+#include <algorithm>
+
 #include "cf_internal.cuh"
 
 namespace cf {
@@ -68,62 +70,45 @@ __device__ __forceinline__ void load_record(const uint32_t *__restrict__ r, uint
 }
 
 struct QueryArgs {
-    FieldGeom g;               // single object: geometry
-    QueryDesc one;             // single object: request
-    const QueryDesc *descs;    // batch: requests (device)
-    const FieldGeom *geoms;    // batch: geometries (device)
-    int n_desc;
+    FieldGeom g;               // geometry
+    QueryDesc one;             // request
     int ppb;                   // poses per block (<= kMaxPosesPerBlock)
 };
 
-// MULTI: the block's object is found from the descriptors (blocks of object d
-// are [descs[d].block0, descs[d + 1].block0)); its request and field geometry
-// are copied to shared memory.
-template <int F, int BITS, bool CAND, bool MULTI>
-__global__ void __launch_bounds__(kThreads, 5) k_query_domains(const QueryArgs a) {
-    __shared__ __align__(16) float s_pose[kMaxPosesPerBlock][12];
-    __shared__ unsigned s_cnt[kMaxPosesPerBlock][F];
-    __shared__ float4 s_dir[CF_MAX_BINS];
-    __shared__ uint32_t s_dil[CF_MAX_BINS];
-    __shared__ uint32_t s_cand[CAND ? kCandCells : 1];
-    __shared__ FieldGeom s_geom;
-    __shared__ QueryDesc s_desc;
-    if (MULTI) {
-        if (threadIdx.x == 0) {
-            int lo = 0, hi = a.n_desc - 1;  // last descriptor with block0 <= blockIdx.x
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (a.descs[mid].block0 <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
-            }
-            s_desc = a.descs[lo];
-        }
-        __syncthreads();
-        const int *src = reinterpret_cast<const int *>(a.geoms + s_desc.geom);
-        int *dst = reinterpret_cast<int *>(&s_geom);
-        for (int e = threadIdx.x; e < (int)(sizeof(FieldGeom) / sizeof(int)); e += kThreads) dst[e] = src[e];
-        __syncthreads();
-    }
-    const FieldGeom &g = MULTI ? s_geom : a.g;
-    const QueryDesc &D = MULTI ? s_desc : a.one;
+// Shared memory of one query block: its poses, per-(pose, finger) counts and
+// the field's bin directions and dilation sets.
+struct QuerySmem {
+    __align__(16) float pose[kMaxPosesPerBlock][12];
+    unsigned cnt[kMaxPosesPerBlock][CF_MAX_FINGERS];
+    float4 dir[CF_MAX_BINS];
+    uint32_t dil[CF_MAX_BINS];
+};
+
+// Poses i0 .. i0 + np - 1 of request D against field g, by the whole block
+// (kThreads threads).  load_geom: stage g's directions, dilation sets and
+// candidate table (s_cand, kCandCells words when CAND) before the poses.
+// Ends with every thread past the block's last shared-memory read.
+template <int F, int BITS, bool CAND>
+__device__ __forceinline__ void query_poses(const FieldGeom &g, const QueryDesc &D, int i0, int np, QuerySmem &s,
+                                            uint32_t *s_cand, bool load_geom) {
     const cf_points &obj = D.obj;
     const float *__restrict__ poses = D.poses;
-    const int P = D.P, W = D.W;
+    const int W = D.W;
     uint32_t *__restrict__ masks = D.masks;
     uint32_t *__restrict__ counts = D.counts;
     const uint32_t *__restrict__ table = D.table;
-    const int ppb = a.ppb;
-    const int i0 = ((int)blockIdx.x - (MULTI ? D.block0 : 0)) * ppb;
-    const int np = min(ppb, P - i0);
-    for (int e = threadIdx.x; e < np * 12; e += kThreads) s_pose[e / 12][e % 12] = poses[(size_t)i0 * 12 + e];
-    for (int e = threadIdx.x; e < kMaxPosesPerBlock * F; e += kThreads) s_cnt[e / F][e % F] = 0u;
-    if (threadIdx.x < CF_MAX_BINS) s_dil[threadIdx.x] = g.dil[threadIdx.x];
-    const bool dilated = g.dilate_deg > 0.f;  // block-uniform
-    if (CAND) {
-        for (int e = threadIdx.x; e < kCandCells; e += kThreads) s_cand[e] = __ldg(g.cand + e);
-        if (threadIdx.x < g.B) s_dir[threadIdx.x] = make_float4(g.dirs[threadIdx.x][0], g.dirs[threadIdx.x][1],
-                                                                g.dirs[threadIdx.x][2], 0.f);
+    for (int e = threadIdx.x; e < np * 12; e += kThreads) s.pose[e / 12][e % 12] = poses[(size_t)i0 * 12 + e];
+    for (int e = threadIdx.x; e < kMaxPosesPerBlock * F; e += kThreads) s.cnt[e / F][e % F] = 0u;
+    if (load_geom) {
+        if (threadIdx.x < CF_MAX_BINS) s.dil[threadIdx.x] = g.dil[threadIdx.x];
+        if (CAND) {
+            for (int e = threadIdx.x; e < kCandCells; e += kThreads) s_cand[e] = __ldg(g.cand + e);
+            if (threadIdx.x < g.B) s.dir[threadIdx.x] = make_float4(g.dirs[threadIdx.x][0], g.dirs[threadIdx.x][1],
+                                                                    g.dirs[threadIdx.x][2], 0.f);
+        }
     }
     __syncthreads();
+    const bool dilated = g.dilate_deg > 0.f;  // block-uniform
 
     constexpr int FPW = 32 / BITS;
     constexpr int RW = (F + FPW - 1) / FPW;
@@ -145,9 +130,9 @@ __global__ void __launch_bounds__(kThreads, 5) k_query_domains(const QueryArgs a
         const float nx = valid ? __ldg(obj.nx + x) : 0.f, ny = valid ? __ldg(obj.ny + x) : 0.f,
                     nz = valid ? __ldg(obj.nz + x) : 0.f;
         for (int pi = 0; pi < np; ++pi) {
-            const float4 T0 = reinterpret_cast<const float4 *>(s_pose[pi])[0];
-            const float4 T1 = reinterpret_cast<const float4 *>(s_pose[pi])[1];
-            const float4 T2 = reinterpret_cast<const float4 *>(s_pose[pi])[2];
+            const float4 T0 = reinterpret_cast<const float4 *>(s.pose[pi])[0];
+            const float4 T1 = reinterpret_cast<const float4 *>(s.pose[pi])[1];
+            const float4 T2 = reinterpret_cast<const float4 *>(s.pose[pi])[2];
             const float qx = xf_row(T0.x, T0.y, T0.z, T0.w, px, py, pz);
             const float qy = xf_row(T1.x, T1.y, T1.z, T1.w, px, py, pz);
             const float qz = xf_row(T2.x, T2.y, T2.z, T2.w, px, py, pz);
@@ -174,7 +159,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_query_domains(const QueryArgs a
                     const float my = -rot_row(T1.x, T1.y, T1.z, nx, ny, nz);
                     const float mz = -rot_row(T2.x, T2.y, T2.z, nx, ny, nz);
                     if (CAND) {
-                        bin = bin_by_candidates(mx, my, mz, s_cand, s_dir);
+                        bin = bin_by_candidates(mx, my, mz, s_cand, s.dir);
                     } else {
                         float best = -INFINITY;
 #pragma unroll 4
@@ -185,7 +170,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_query_domains(const QueryArgs a
                         }
                     }
                 }
-                const uint32_t dm = dilated ? s_dil[bin] : (1u << bin);  // the bins this query accepts
+                const uint32_t dm = dilated ? s.dil[bin] : (1u << bin);  // the bins this query accepts
                 const int lf = own ? lane - pi * F : lane;  // the finger whose word this lane keeps
                 uint32_t dmf[FPW];  // the accepted bins at each finger's slot of a record word
 #pragma unroll
@@ -201,7 +186,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_query_domains(const QueryArgs a
                 owned |= mine;  // nonzero only on lane pi * F + f: this lane's (pose, finger) word
             } else if (lane < F) {
                 if (masks) masks[((size_t)(i0 + pi) * F + lane) * W + w] = mine;
-                if (mine) atomicAdd(&s_cnt[pi][lane], (unsigned)__popc(mine));
+                if (mine) atomicAdd(&s.cnt[pi][lane], (unsigned)__popc(mine));
             }
         }
         if (own && lane < np * F) {  // lane = pose * F + finger
@@ -209,29 +194,113 @@ __global__ void __launch_bounds__(kThreads, 5) k_query_domains(const QueryArgs a
             cnt += (unsigned)__popc(owned);
         }
     }
-    if (own && lane < np * F && cnt) atomicAdd(&s_cnt[lane / F][lane % F], cnt);
+    if (own && lane < np * F && cnt) atomicAdd(&s.cnt[lane / F][lane % F], cnt);
     __syncthreads();
-    for (int e = threadIdx.x; e < np * F; e += kThreads) counts[(size_t)(i0 + e / F) * F + e % F] = s_cnt[e / F][e % F];
+    for (int e = threadIdx.x; e < np * F; e += kThreads) counts[(size_t)(i0 + e / F) * F + e % F] = s.cnt[e / F][e % F];
+    __syncthreads();
 }
 
-template <int F, int BITS, bool MULTI>
+template <int F, int BITS, bool CAND>
+__global__ void __launch_bounds__(kThreads, 5) k_query_domains(const QueryArgs a) {
+    __shared__ QuerySmem s;
+    __shared__ uint32_t s_cand[CAND ? kCandCells : 1];
+    const int i0 = (int)blockIdx.x * a.ppb;
+    query_poses<F, BITS, CAND>(a.g, a.one, i0, min(a.ppb, a.one.P - i0), s, s_cand, true);
+}
+
+// The binning method of a field: a full scan of <= 8 bins costs no more than the candidate lookup.
+__host__ __device__ __forceinline__ bool use_candidates(const FieldGeom &g) {
+    return g.bits > 8 && g.use_cand && g.B > 8;
+}
+
+template <int F, int BITS>
+__device__ __forceinline__ void query_poses_any_cand(const FieldGeom &g, const QueryDesc &D, int i0, int np,
+                                                     QuerySmem &s, uint32_t *s_cand, bool load_geom) {
+    if (BITS > 8 && use_candidates(g)) query_poses<F, BITS, (BITS > 8)>(g, D, i0, np, s, s_cand, load_geom);
+    else query_poses<F, BITS, false>(g, D, i0, np, s, s_cand, load_geom);
+}
+
+// One launch for every object of a batch, whatever its hand: a persistent grid
+// whose blocks take (object, pose-block) items in order from a device work
+// counter (work[0]; object d owns items descs[d].block0 .. descs[d + 1].block0 - 1)
+// and run the query body specialised for the object's finger count and slot
+// width, picked at run time.  A block re-stages the field's directions and
+// candidate table only when its object's field changes.  The last block to
+// finish returns both counters (work[0], work[1]) to zero for the next launch;
+// nothing waits on another block.
+__global__ void __launch_bounds__(kThreads, 4) k_query_batch(const QueryDesc *__restrict__ descs,
+                                                             const FieldGeom *__restrict__ geoms, int n_desc,
+                                                             int total_items, int ppb, unsigned int *work) {
+    __shared__ QuerySmem s;
+    __shared__ uint32_t s_cand[kCandCells];
+    __shared__ FieldGeom s_geom;
+    __shared__ QueryDesc s_desc;
+    __shared__ int s_item, s_geom_idx;
+    if (threadIdx.x == 0) s_geom_idx = -1;
+    for (;;) {
+        __syncthreads();  // the previous item's shared data is no longer read
+        if (threadIdx.x == 0) {
+            const int item = (int)atomicAdd(work, 1u);
+            s_item = item;
+            if (item < total_items) {
+                int lo = 0, hi = n_desc - 1;  // last descriptor with block0 <= item
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (descs[mid].block0 <= item) lo = mid; else hi = mid - 1;
+                }
+                s_desc = descs[lo];
+            }
+        }
+        __syncthreads();
+        const int item = s_item;
+        if (item >= total_items) break;
+        const bool new_geom = s_desc.geom != s_geom_idx;  // block-uniform
+        if (new_geom) {
+            const int *src = reinterpret_cast<const int *>(geoms + s_desc.geom);
+            int *dst = reinterpret_cast<int *>(&s_geom);
+            for (int e = threadIdx.x; e < (int)(sizeof(FieldGeom) / sizeof(int)); e += kThreads) dst[e] = src[e];
+            __syncthreads();
+            if (threadIdx.x == 0) s_geom_idx = s_desc.geom;
+        }
+        const int i0 = (item - s_desc.block0) * ppb;
+        const int np = min(ppb, s_desc.P - i0);
+#define CF_QB(FF)                                                                                   \
+    case FF:                                                                                        \
+        if (s_geom.bits == 8) query_poses_any_cand<FF, 8>(s_geom, s_desc, i0, np, s, s_cand, new_geom);        \
+        else if (s_geom.bits == 16) query_poses_any_cand<FF, 16>(s_geom, s_desc, i0, np, s, s_cand, new_geom); \
+        else query_poses_any_cand<FF, 32>(s_geom, s_desc, i0, np, s, s_cand, new_geom);                        \
+        break;
+        switch (s_geom.F) {
+            CF_QB(1) CF_QB(2) CF_QB(3) CF_QB(4) CF_QB(5) CF_QB(6) CF_QB(7) CF_QB(8)
+            default: break;
+        }
+#undef CF_QB
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(work + 1, 1u) == gridDim.x - 1) {  // every block has taken its last item
+            atomicExch(work, 0u);
+            atomicExch(work + 1, 0u);
+        }
+    }
+}
+
+template <int F, int BITS>
 cudaError_t launch_fb(const QueryArgs &a, const FieldGeom &g, int grid, cudaStream_t st) {
-    // a full scan of <= 8 bins costs no more than the candidate lookup
-    if (BITS > 8 && g.use_cand && g.B > 8)
-        k_query_domains<F, BITS, (BITS > 8), MULTI><<<grid, kThreads, 0, st>>>(a);
+    if (BITS > 8 && use_candidates(g))
+        k_query_domains<F, BITS, (BITS > 8)><<<grid, kThreads, 0, st>>>(a);
     else
-        k_query_domains<F, BITS, false, MULTI><<<grid, kThreads, 0, st>>>(a);
+        k_query_domains<F, BITS, false><<<grid, kThreads, 0, st>>>(a);
     return cudaGetLastError();
 }
 
-template <bool MULTI>
 cudaError_t launch_any(const QueryArgs &a, const FieldGeom &g, int grid, cudaStream_t st) {
 #define CF_QF(FF)                                                          \
     case FF:                                                               \
         switch (g.bits) {                                                  \
-            case 8: return launch_fb<FF, 8, MULTI>(a, g, grid, st);       \
-            case 16: return launch_fb<FF, 16, MULTI>(a, g, grid, st);     \
-            case 32: return launch_fb<FF, 32, MULTI>(a, g, grid, st);     \
+            case 8: return launch_fb<FF, 8>(a, g, grid, st);              \
+            case 16: return launch_fb<FF, 16>(a, g, grid, st);            \
+            case 32: return launch_fb<FF, 32>(a, g, grid, st);            \
             default: return cudaErrorInvalidValue;                         \
         }
     switch (g.F) {
@@ -260,20 +329,20 @@ cudaError_t launch_query(const FieldGeom &g, const uint32_t *table, const cf_poi
     a.one.masks = masks;
     a.one.counts = counts;
     a.one.table = table;
-    return launch_any<false>(a, g, query_blocks(P, ppb), st);
+    return launch_any(a, g, query_blocks(P, ppb), st);
 }
 
-cudaError_t launch_query_batch(const FieldGeom &g0, const QueryDesc *d_descs, const FieldGeom *d_geoms, int n_desc,
-                               int total_blocks, int ppb, cudaStream_t st) {
-    if (total_blocks <= 0) return cudaSuccess;
-    if (ppb < 1 || ppb > kMaxPosesPerBlock) return cudaErrorInvalidValue;
-    QueryArgs a;
-    memset(&a, 0, sizeof a);
-    a.ppb = ppb;
-    a.descs = d_descs;
-    a.geoms = d_geoms;
-    a.n_desc = n_desc;
-    return launch_any<true>(a, g0, total_blocks, st);
+cudaError_t launch_query_batch(const QueryDesc *d_descs, const FieldGeom *d_geoms, int n_desc, int total_items,
+                               int ppb, unsigned int *d_work, cudaStream_t st) {
+    if (total_items <= 0) return cudaSuccess;
+    if (ppb < 1 || ppb > kMaxPosesPerBlock || !d_work) return cudaErrorInvalidValue;
+    int per_sm = 0, sms = 0;
+    cudaError_t err = launch_shape((const void *)k_query_batch, kThreads, 0, &per_sm, &sms);
+    if (err != cudaSuccess) return err;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int grid = std::min(total_items, sms * per_sm);
+    k_query_batch<<<grid, kThreads, 0, st>>>(d_descs, d_geoms, n_desc, total_items, ppb, d_work);
+    return cudaGetLastError();
 }
 
 }  // namespace cf

@@ -30,8 +30,9 @@ DECISION_BAND = 1e-4
 # 6.8e-4 (hand16_superquadric, 2.5 mm) and 1.1e-3 (hand20_tool, 2 mm); bound
 # at about 1.7x, since pose subsets vary
 AMB_BOUND = {"tiny_sphere": 1e-2, "hand16_superquadric": 1.5e-3, "hand20_tool": 2e-3}
-# the same for field codes: codes some sample takes only inside the band
-CODE_AMB_BOUND = 0.05
+# the same for field codes (codes some sample takes only inside the band): measured 8.3 % at tiny_sphere,
+# whose finger 0 moves in the plane y = 0, a cell face, and 1-2 % at hand16_superquadric / hand20_tool
+CODE_AMB_BOUND = {"tiny_sphere": 0.12, "hand16_superquadric": 0.05, "hand20_tool": 0.05}
 
 
 def bits(masks_u32, N):
@@ -86,7 +87,7 @@ def _keyset(c):
     return set(map(tuple, c.tolist()))
 
 
-def check_field(field, ofd, F):
+def check_field(field, ofd, F, name=None):
     """GPU field codes against the oracle's FP64 code set: every code whose
     samples decide it the same way everywhere in the band ("sure") is present,
     every GPU code is one some sample takes within the band ("possible"), and
@@ -103,7 +104,7 @@ def check_field(field, ofd, F):
         st["differ"] += len(g ^ o)
         st["ambiguous"] += len(pos - sure)
     assert st["differ"] <= DIFF_BUDGET * max(st["codes"], 1), st
-    assert st["ambiguous"] <= CODE_AMB_BOUND * max(st["codes"], 1), st
+    assert st["ambiguous"] <= CODE_AMB_BOUND.get(name, 0.05) * max(st["codes"], 1), st
     print(f"field codes: {st['codes']}, differ from FP64 {st['differ']}, in band {st['ambiguous']}")
     return st
 
