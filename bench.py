@@ -52,7 +52,7 @@ def _args():
     ap.add_argument("--cpu-poses", type=int, default=32, help="poses in the oracle's timed sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-objects", type=int, default=64, help="objects of the batched-form leg (0: skip)")
-    ap.add_argument("--served-seconds", type=float, default=4.0, help="seconds per offered rate (0: skip)")
+    ap.add_argument("--served-seconds", type=float, default=30.0, help="seconds per offered rate (0: skip)")
     ap.add_argument("--served-rates", default="10,100,1000")
     ap.add_argument("--realized-steps", type=int, default=20, help="steps of the IK + realization leg (0: skip)")
     ap.add_argument("--optimized-steps", type=int, default=5, help="steps of the Alg. 2 optimisation leg (0: skip)")
@@ -692,6 +692,7 @@ def run_optimized(cf, torch, dev, w, steps, soa, poses, masks, counts, tuples, f
             "accept_rate": acc / (steps * w.P * w.T), "params": OPT,
             "lp_per_tuple": counters["lps"] / max(1, counters["tuples_scored"]),
             "pivots_per_lp": counters["lp_pivots"] / max(1, counters["lps"]),
+            "warm_starts_per_tuple": counters["warm_starts"] / max(1, counters["tuples_scored"]),
             "gpu_launches_per_step": 4, "device_status": cf.device_status()}
 
 
@@ -864,8 +865,8 @@ def run_served(cf, torch, dev, ws, fields, rates, seconds, pool=24):
         poses = synth.palm_poses(8192, 4000 + o, ws[hi].hand.grasp_centre, obj.centroid)
         objs.append((hi, obj.soa(), poses, obj))
 
-    def stream(max_active, rate):
-        eng = cf.Engine(fields, hbm_budget_bytes=64 << 30, max_active=max_active, pose_chunk=256, pose_cap=65536)
+    def stream(max_active, rate, seconds=seconds, budget=64 << 30):
+        eng = cf.Engine(fields, hbm_budget_bytes=budget, max_active=max_active, pose_chunk=256, pose_cap=65536)
         r = np.random.default_rng(int(rate) * 7 + max_active)
         t = 0.0
         arrivals = []
@@ -889,10 +890,24 @@ def run_served(cf, torch, dev, ws, fields, rates, seconds, pool=24):
         eng.close()
         lat = np.array([d["t_done"] - d["t_submit"] for d in done]) * 1e3
         acc = sum(d["n_accepted"] for d in done)
-        return {"rate": rate, "requests": len(arrivals), "completed": len(done),
+        # where a request's time goes: waiting for admission, its upload until its first round, its rounds
+        wait = np.array([d["t_admit"] - d["t_submit"] for d in done]) * 1e3
+        upload = np.array([d["t_first_round"] - d["t_admit"] for d in done]) * 1e3
+        inrounds = np.array([d["t_done"] - d["t_first_round"] for d in done]) * 1e3
+        nr = np.array([d["n_rounds"] for d in done])
+        tail = lat >= np.percentile(lat, 99)
+        pct = lambda a: {"p50": float(np.percentile(a, 50)), "p99": float(np.percentile(a, 99))}
+        return {"rate": rate, "seconds": seconds, "requests": len(arrivals), "completed": len(done),
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "grasps_per_s": acc / wall, "rounds": st["rounds"], "peak_active": st["peak_active"],
-                "peak_gb": st["peak_bytes_in_use"] / 1e9}
+                "peak_gb": st["peak_bytes_in_use"] / 1e9, "hbm_budget_gb": budget / 1e9,
+                "breakdown_ms": {"queue_wait": pct(wait), "admission_upload": pct(upload), "in_rounds": pct(inrounds),
+                                 "rounds_per_request": pct(nr)},
+                "tail_mean_ms": {"queue_wait": float(wait[tail].mean()), "admission_upload": float(upload[tail].mean()),
+                                 "in_rounds": float(inrounds[tail].mean()), "rounds": float(nr[tail].mean())},
+                "worker_s": {"admit": st["admit_s"], "round_host": st["round_host_s"], "round_wait": st["round_wait_s"],
+                             "wall": wall},
+                "round_ms_mean": 1e3 * (st["round_host_s"] + st["round_wait_s"]) / max(1, st["rounds"])}
 
     out = {"continuous_batching": [], "one_at_a_time": [],
            "workload": f"Poisson arrivals, {seconds:g} s per rate; objects drawn from {pool} generated objects "
@@ -900,7 +915,9 @@ def run_served(cf, torch, dev, ws, fields, rates, seconds, pool=24):
                        "8,192 candidate poses per request (pose cap 65,536), chunk 256 poses, HBM budget 64 GiB"}
     for rate in rates:
         out["continuous_batching"].append(stream(64, rate))
-        out["one_at_a_time"].append(stream(1, rate))
+        out["one_at_a_time"].append(stream(1, rate, seconds=min(seconds, 5.0)))
+    # admission by HBM budget that binds: a 128 MiB budget holds only ~10 requests' device state
+    out["budget_gated"] = stream(64, max(rates), seconds=min(seconds, 10.0), budget=128 << 20)
     return out
 
 

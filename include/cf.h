@@ -507,6 +507,8 @@ typedef struct cf_result {
     int32_t *pose;                  /* [n_accepted] pose index of each accepted tuple */
     int32_t *tuples;                /* [n_accepted][k] object point ids */
     float *margin;                  /* [n_accepted] closure margins */
+    int32_t n_rounds;               /* rounds the request took part in */
+    double t_first_round;           /* start of its first round (engine clock; t_done if none) */
 } cf_result;
 
 typedef struct cf_engine_stats {
@@ -514,6 +516,9 @@ typedef struct cf_engine_stats {
     int32_t queued, active;
     int64_t bytes_in_use, peak_bytes_in_use;
     int32_t peak_active;
+    /* cumulative worker seconds: admission uploads, round preparation and
+     * launches on the host, waiting for the round's GPU work and result copies */
+    double admit_s, round_host_s, round_wait_s;
 } cf_engine_stats;
 
 /* Start an engine: a worker thread on the current device admits queued
@@ -582,8 +587,10 @@ const char *cf_last_error(void);
 int cf_device_status(uint32_t *status);
 
 /* Cumulative device counters of the current device since the last reset:
- * [0] LP pivots performed, [1] LPs solved, [2] tuples scored. */
-int cf_device_counters(uint64_t counters[3], int reset);
+ * [0] LP pivots performed, [1] LPs solved, [2] tuples scored, [3] candidate
+ * tuples of cf_optimize_tuples whose LPs started from the current tuple's
+ * basis (the warm start of Sec. 5.4) instead of c' = 0. */
+int cf_device_counters(uint64_t counters[4], int reset);
 
 /* Device memory of the library's stream-ordered pool on the current device,
  * from which every library-owned buffer (fields, batches, requests, temporary

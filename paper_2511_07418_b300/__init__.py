@@ -127,13 +127,14 @@ class Result(Structure):
     _fields_ = [("id", c_uint64), ("tag", c_uint64), ("status", c_int32), ("partial", c_int32), ("k", c_int32),
                 ("n_accepted", c_int32), ("n_poses_used", c_int32), ("t_submit", c_double), ("t_admit", c_double),
                 ("t_done", c_double), ("pose", POINTER(c_int32)), ("tuples", POINTER(c_int32)),
-                ("margin", POINTER(c_float))]
+                ("margin", POINTER(c_float)), ("n_rounds", c_int32), ("t_first_round", c_double)]
 
 
 class EngineStats(Structure):
     _fields_ = [("submitted", c_int64), ("completed", c_int64), ("rounds", c_int64), ("launches", c_int64),
                 ("queued", c_int32), ("active", c_int32), ("bytes_in_use", c_int64), ("peak_bytes_in_use", c_int64),
-                ("peak_active", c_int32)]
+                ("peak_active", c_int32), ("admit_s", c_double), ("round_host_s", c_double),
+                ("round_wait_s", c_double)]
 
 
 def _sig(name, args, res=c_int):
@@ -568,7 +569,7 @@ class Engine:
             na, k = int(r.n_accepted), int(r.k)
             d = dict(id=int(r.id), tag=int(r.tag), status=int(r.status), partial=bool(r.partial),
                      n_accepted=na, n_poses_used=int(r.n_poses_used), t_submit=r.t_submit, t_admit=r.t_admit,
-                     t_done=r.t_done,
+                     t_done=r.t_done, n_rounds=int(r.n_rounds), t_first_round=r.t_first_round,
                      pose=np.ctypeslib.as_array(r.pose, (na,)).copy() if na else np.zeros(0, np.int32),
                      tuples=np.ctypeslib.as_array(r.tuples, (na * k,)).reshape(na, k).copy() if na
                      else np.zeros((0, k), np.int32),
@@ -828,9 +829,9 @@ def device_status() -> int:
 
 
 def device_counters(reset: bool = False):
-    v = (c_uint64 * 3)()
+    v = (c_uint64 * 4)()
     _check(_cf_device_counters(v, 1 if reset else 0))
-    return {"lp_pivots": int(v[0]), "lps": int(v[1]), "tuples_scored": int(v[2])}
+    return {"lp_pivots": int(v[0]), "lps": int(v[1]), "tuples_scored": int(v[2]), "warm_starts": int(v[3])}
 
 
 def pool_usage(reset_high: bool = False):

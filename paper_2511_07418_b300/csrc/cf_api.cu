@@ -42,7 +42,7 @@ int cuda_fail(cudaError_t e, const char *what) {
 // device status word and counters (one copy per device that loads libcf)
 // ---------------------------------------------------------------------------
 __device__ unsigned int g_status;
-__device__ unsigned long long g_counters[3];
+__device__ unsigned long long g_counters[4];
 
 struct DevState {
     unsigned int *status = nullptr;
@@ -1624,16 +1624,16 @@ extern "C" int cf_device_status(uint32_t *status) {
     return CF_OK;
 }
 
-extern "C" int cf_device_counters(uint64_t counters[3], int reset) {
+extern "C" int cf_device_counters(uint64_t counters[4], int reset) {
     if (!counters) return fail(CF_EINVAL, "NULL argument");
     DevState ds;
     int rc = device_state(&ds);
     if (rc) return rc;
-    unsigned long long v[3];
+    unsigned long long v[4];
     CF_TRY(cudaMemcpy(v, ds.counters, sizeof v, cudaMemcpyDeviceToHost), "read counters");
-    for (int i = 0; i < 3; ++i) counters[i] = v[i];
+    for (int i = 0; i < 4; ++i) counters[i] = v[i];
     if (reset) {
-        const unsigned long long z[3] = {0, 0, 0};
+        const unsigned long long z[4] = {0, 0, 0, 0};
         CF_TRY(cudaMemcpy(ds.counters, z, sizeof z, cudaMemcpyHostToDevice), "reset counters");
     }
     return CF_OK;

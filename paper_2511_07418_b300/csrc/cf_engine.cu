@@ -58,7 +58,8 @@ struct EngReq {
     unsigned rec_off = 0, rec_cnt = 0;  // this round's accepted records in the engine's host buffer
     std::vector<int32_t> res_pose, res_tuples;
     std::vector<float> res_margin;
-    double t_submit = 0, t_admit = 0;
+    double t_submit = 0, t_admit = 0, t_first_round = -1;
+    int n_rounds = 0;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -235,6 +236,8 @@ void finish(cf_engine *e, EngReq *r, int status, bool partial) {
     res.t_submit = r->t_submit;
     res.t_admit = r->t_admit;
     res.t_done = e->now();
+    res.n_rounds = r->n_rounds;
+    res.t_first_round = r->t_first_round >= 0 ? r->t_first_round : res.t_done;
     if (res.n_accepted > 0) {
         res.pose = (int32_t *)malloc(sizeof(int32_t) * res.n_accepted);
         res.tuples = (int32_t *)malloc(sizeof(int32_t) * res.n_accepted * res.k);
@@ -279,6 +282,11 @@ int admit_one(cf_engine *e, EngReq *r) {
 // One round over the active requests.  Returns CF_OK or an error code.
 int run_round(cf_engine *e, std::vector<EngReq *> &act) {
     const int n = (int)act.size();
+    const double t_start = e->now();
+    for (EngReq *r : act) {
+        if (r->t_first_round < 0) r->t_first_round = t_start;
+        ++r->n_rounds;
+    }
     std::vector<ScoreArgs> sargs(n);
     std::vector<cf_points> objs(n);
     for (int i = 0; i < n; ++i) {
@@ -418,6 +426,7 @@ int run_round(cf_engine *e, std::vector<EngReq *> &act) {
     CF_TRY(cudaGetLastError(), "round compaction");
     ++launches;
     CF_TRY(cudaMemcpyAsync(e->h_meta, d_meta, meta_bytes, cudaMemcpyDeviceToHost, e->st), "download round extents");
+    const double t_launched = e->now();
     CF_TRY(cudaStreamSynchronize(e->st), "round");
     const size_t used = sizeof(AccRecord) * (size_t)e->h_meta[0];
     if (used > e->h_rec_bytes) {
@@ -434,9 +443,12 @@ int run_round(cf_engine *e, std::vector<EngReq *> &act) {
         act[i]->rec_cnt = e->h_meta[1 + n + i];
     }
     CF_TRY(cudaStreamSynchronize(e->st), "round");
+    const double t_end = e->now();
     std::lock_guard<std::mutex> lk(e->mu);
     e->stats.rounds++;
     e->stats.launches += launches;
+    e->stats.round_host_s += t_launched - t_start;
+    e->stats.round_wait_s += t_end - t_launched;
     return CF_OK;
 }
 
@@ -473,6 +485,7 @@ void worker_main(cf_engine *e) {
         }
         for (EngReq *r : rejected) finish(e, r, CF_ENOMEM, false);
         rejected.clear();
+        const double t_adm = e->now();
         for (EngReq *r : act) {
             const int arc = admit_one(e, r);
             if (arc != CF_OK) {  // the request ends with the error; its budget share is returned by finish
@@ -484,6 +497,11 @@ void worker_main(cf_engine *e) {
                 }
                 finish(e, r, arc, false);
             }
+        }
+        if (!act.empty()) {
+            const double dt = e->now() - t_adm;
+            std::lock_guard<std::mutex> lk(e->mu);
+            e->stats.admit_s += dt;
         }
         std::vector<EngReq *> round;
         {

@@ -325,7 +325,7 @@ struct ScoreArgs {
     uint8_t *accept;
     unsigned int *work;  // scratch: tuple work counter, zero at launch
     unsigned int *status;          // device status word (CF_DEV_* bits)
-    unsigned long long *counters;  // [0] pivots, [1] LPs, [2] tuples
+    unsigned long long *counters;  // [0] pivots, [1] LPs, [2] tuples, [3] warm-started Alg. 2 candidates
     int refill;                    // idle lanes of a scoring warp before a group refill (launch-level)
     int bpsm;                      // scoring blocks per SM, 0 = as many as fit (launch-level)
     unsigned long long *n_accept;  // optional: accepted tuples of the launch are added here

@@ -241,13 +241,10 @@ struct BoxLp {
 template <int NS>
 __device__ __forceinline__ int y_id(int r, int kK) { return NS == 1 ? kK + r : 32 + r; }
 
-// Closure margin min_j LP_j of one tuple on the warp.  w = this lane's wrench
-// column (lanes < kK).  Stops at the first unbounded s_j (margin 0).
+// The feasible start c' = 0, y = 0 (every y_r basic, B = I) of the tuple whose
+// wrench column on this lane is w (lanes < kK).
 template <int NS>
-__device__ float closure_margin(const float (&w)[6], int k, int K, int lane, float *buf, unsigned long long &n_piv,
-                                unsigned long long &n_lp, unsigned &flags) {
-    const int kK = k * K;
-    BoxLp<NS> s;
+__device__ __forceinline__ void lp_init_cold(BoxLp<NS> &s, const float (&w)[6], int kK, int lane) {
 #pragma unroll
     for (int q = 0; q < NS; ++q) {
         const int id = 32 * q + lane;
@@ -262,7 +259,52 @@ __device__ float closure_margin(const float (&w)[6], int k, int K, int lane, flo
     }
     s.v = 0.f;
     s.beta = lane < kRows ? y_id<NS>(lane, kK) : -1;
+}
 
+// Warm start (Sec. 5.4, "A Free Lunch"): the tuple of state s with contact ci
+// replaced, whose new wrench column on this lane is w (lanes of contact ci).
+// Valid only when none of contact ci's columns is basic in s: then the basis
+// matrix and the basic values do not involve them, so s stays a feasible basis
+// and only contact ci's tableau columns change, to B^-1 (-w).  B^-1's column r
+// is the tableau column of y_r.  Returns false (s untouched) when a column of
+// contact ci is basic.
+template <int NS>
+__device__ __forceinline__ bool lp_replace_contact(BoxLp<NS> &s, const float (&w)[6], int ci, int k, int K, int lane,
+                                                   float *buf) {
+    const int kK = k * K, c0 = ci * K, c1 = c0 + K;
+    const unsigned basic_ci = __ballot_sync(kFull, lane < kRows && s.beta >= c0 && s.beta < c1);
+    if (basic_ci & ((1u << kRows) - 1u)) return false;
+    // stage B^-1 = [T(y_0) .. T(y_5)] as buf[r' * 6 + r] (column r' = y_r')
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+        const int yr = NS == 1 ? lane - kK : (q == 1 ? lane : -1);
+        if (yr >= 0 && yr < kRows) {
+#pragma unroll
+            for (int r = 0; r < kRows; ++r) buf[yr * kRows + r] = s.T[q][r];
+        }
+    }
+    __syncwarp();
+    if (lane >= c0 && lane < c1) {  // slot 0 of lane c is column c
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+            float acc = 0.f;
+#pragma unroll
+            for (int rr = 0; rr < kRows; ++rr) acc = __fmaf_rn(buf[rr * kRows + r], -w[rr], acc);
+            s.T[0][r] = acc;
+        }
+        s.st[0] = 1;  // nonbasic at its lower bound, c' = 0
+    }
+    __syncwarp();  // buf is read before it is written again
+    return true;
+}
+
+// Closure margin min_j LP_j from the feasible state s (each LP_j starts from
+// the basis the previous one ended in).  Stops at the first unbounded s_j
+// (margin 0).  s ends in the last LP's final basis.
+template <int NS>
+__device__ float lp_solve_margin(BoxLp<NS> &s, int k, int K, int lane, float *buf, unsigned long long &n_piv,
+                                 unsigned long long &n_lp, unsigned &flags) {
+    const int kK = k * K;
     const unsigned kinf = fkey(INFINITY);
     const unsigned kzero = fkey(0.f);
     unsigned npv = 0;
@@ -424,6 +466,15 @@ __device__ float closure_margin(const float (&w)[6], int k, int K, int lane, flo
     return best_s > 0.f ? __fdiv_rn(1.f, best_s) : INFINITY;
 }
 
+// Closure margin min_j LP_j of one tuple on the warp, from the cold start.
+template <int NS>
+__device__ float closure_margin(const float (&w)[6], int k, int K, int lane, float *buf, unsigned long long &n_piv,
+                                unsigned long long &n_lp, unsigned &flags) {
+    BoxLp<NS> s;
+    lp_init_cold<NS>(s, w, k * K, lane);
+    return lp_solve_margin<NS>(s, k, K, lane, buf, n_piv, n_lp, flags);
+}
+
 // ---------------------------------------------------------------------------
 // Alg. 2: blockwise zeroth-order contact optimisation
 // ---------------------------------------------------------------------------
@@ -447,17 +498,6 @@ __device__ __forceinline__ void wrench_column(const ScoreArgs &a, int x, float e
     wv[5] = (rx * ey - ry * ex) * a.inv_rho;
 }
 
-// Closure margin of the tuple whose contact d is point id_d (min over j of LP_j,
-// stopping at a zero), computed by the whole warp.
-template <int NS>
-__device__ __forceinline__ float tuple_margin(const ScoreArgs &a, int id0, int id1, int id2, int id3, int k, bool colA,
-                                              int ci, float ec, float es, int lane, float *buf,
-                                              unsigned long long &n_piv, unsigned long long &n_lp, unsigned &flags) {
-    float wv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (colA) wrench_column(a, ci == 0 ? id0 : ci == 1 ? id1 : ci == 2 ? id2 : id3, ec, es, wv);
-    return closure_margin<NS>(wv, k, a.K, lane, buf, n_piv, n_lp, flags);
-}
-
 struct OptArgs {
     int n_outer, n_inner;
     float sigma, zero_tol, min_gain;
@@ -469,10 +509,13 @@ struct OptArgs {
 // object point whose mask bit is set; all lanes scan the mask words, then one
 // warp reduction per candidate), then the candidates in order replace the best
 // so far when their margin is lower by more than the relative min_gain (margins
-// <= zero_tol count as 0), so the margin never increases.
+// <= zero_tol count as 0), so the margin never increases.  A candidate's LPs
+// start from the current tuple's final basis whenever the moved contact's
+// columns are nonbasic there (the warm start of Sec. 5.4, "A Free Lunch"),
+// else from c' = 0.
 template <int NI, int NS>
 __global__ void __launch_bounds__(kOptThreads) k_optimize_tuples(const ScoreArgs a, const OptArgs o, unsigned total) {
-    __shared__ __align__(16) float s_buf[kOptWarps][16];
+    __shared__ __align__(16) float s_buf[kOptWarps][kRows * kRows];  // entering column; B^-1 for warm starts
     __shared__ float s_cand[kOptWarps][NI][3];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int k = a.k, K = a.K, kK = k * K, F = a.F, W = a.W;
@@ -480,7 +523,7 @@ __global__ void __launch_bounds__(kOptThreads) k_optimize_tuples(const ScoreArgs
     const int ci = colA ? lane / K : 0, cm = colA ? lane % K : 0;
     const float ec = a.cs[cm] * a.mu, es = a.sn[cm] * a.mu;
     float *buf = s_buf[warp];
-    unsigned long long n_piv = 0, n_lp = 0, n_tup = 0;
+    unsigned long long n_piv = 0, n_lp = 0, n_tup = 0, n_warm = 0;
     unsigned flags = 0;
     const uint2 key = make_uint2(a.seed_lo, a.seed_hi);
     const int blocks_per_draw = (NI + 1) / 2;
@@ -499,7 +542,14 @@ __global__ void __launch_bounds__(kOptThreads) k_optimize_tuples(const ScoreArgs
         }
         float J = INFINITY;
         if (valid) {
-            J = tuple_margin<NS>(a, id[0], id[1], id[2], id[3], k, colA, ci, ec, es, lane, buf, n_piv, n_lp, flags);
+            // the current tuple's final simplex state: the warm start of its candidates (Sec. 5.4)
+            BoxLp<NS> cur, win;
+            {
+                float wv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                if (colA) wrench_column(a, ci == 0 ? id[0] : ci == 1 ? id[1] : ci == 2 ? id[2] : id[3], ec, es, wv);
+                lp_init_cold<NS>(cur, wv, kK, lane);
+                J = lp_solve_margin<NS>(cur, k, K, lane, buf, n_piv, n_lp, flags);
+            }
             float Jc = J <= o.zero_tol ? 0.f : J;
             const uint32_t pid = (uint32_t)pose + a.pose_base;
             for (int it = 0; it < o.n_outer && Jc > 0.f; ++it) {
@@ -575,16 +625,30 @@ __global__ void __launch_bounds__(kOptThreads) k_optimize_tuples(const ScoreArgs
                     for (unsigned m = todo; m; m &= m - 1) {
                         const int c = __ffs(m) - 1;
                         const int xc = __shfl_sync(kFull, cand_mine, c);
-                        const float Jt = tuple_margin<NS>(a, i == 0 ? xc : id[0], i == 1 ? xc : id[1],
-                                                      i == 2 ? xc : id[2], i == 3 ? xc : id[3], k, colA, ci, ec, es,
-                                                      lane, buf, n_piv, n_lp, flags);
+                        // the trial tuple's wrench column on this lane (contact i moved to xc)
+                        float wt[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                        if (colA)
+                            wrench_column(a, ci == i ? xc : (ci == 0 ? id[0] : ci == 1 ? id[1] : ci == 2 ? id[2] : id[3]),
+                                          ec, es, wt);
+                        // warm start from the current tuple's final basis when contact i is nonbasic there,
+                        // else from c' = 0
+                        BoxLp<NS> st = cur;
+                        if (lp_replace_contact<NS>(st, wt, i, k, K, lane, buf)) ++n_warm;
+                        else lp_init_cold<NS>(st, wt, kK, lane);
+                        const float Jt = lp_solve_margin<NS>(st, k, K, lane, buf, n_piv, n_lp, flags);
                         const float Jtc = Jt <= o.zero_tol ? 0.f : Jt;
-                        if (Jtc < (1.f - o.min_gain) * best) { best = Jtc; bestJ = Jt; bestc = xc; }
+                        if (Jtc < (1.f - o.min_gain) * best) {
+                            best = Jtc;
+                            bestJ = Jt;
+                            bestc = xc;
+                            win = st;
+                        }
                     }
                     if (bestc >= 0) {
                         if (i == 0) id[0] = bestc; else if (i == 1) id[1] = bestc; else if (i == 2) id[2] = bestc; else id[3] = bestc;
                         Jc = best;
                         J = bestJ;
+                        cur = win;
                     }
                 }
             }
@@ -602,6 +666,7 @@ __global__ void __launch_bounds__(kOptThreads) k_optimize_tuples(const ScoreArgs
         atomicAdd(a.counters + 0, n_piv);
         atomicAdd(a.counters + 1, n_lp);
         atomicAdd(a.counters + 2, n_tup);
+        atomicAdd(a.counters + 3, n_warm);
         if (flags) atomicOr(a.status, flags);
     }
 }

@@ -128,8 +128,7 @@ def _sensitive(w, o, pr, tup, fing, valid):
         fc = np.minimum(f[:, c], w.hand.F - 1)
         dq = np.abs(o["q"][np.arange(n), fc] - pr["q"][np.arange(n), fc]).max(axis=1)
         sens[:, c] = (dq > SENS_Q) | (np.abs(o["resid"][:, c, 0] - tol_pos) <= SENS_POS) | \
-                     (np.abs(o["resid"][:, c, 1] - tol_cos) <= SENS_COS) | o["miss"][:, c] | pr["miss"][:, c] | \
-                     o["start_amb"][:, c]
+                     (np.abs(o["resid"][:, c, 1] - tol_cos) <= SENS_COS) | o["miss"][:, c] | pr["miss"][:, c]
     return sens & valid.astype(bool)[:, None]
 
 
@@ -144,9 +143,27 @@ def test_ik_parity(cf, name, P, S):
     assert cf.device_status() == 0
     sens = _sensitive(w, o, pr, tup, fing, valid).any(axis=1)
     att = valid.astype(bool)
-    clear = att & ~sens
-    rows = np.nonzero(clear)[0]
     fc = fing.reshape(n, k).astype(np.int64)
+    # a slot whose starting sample is decided inside the band (start_amb) may start elsewhere on the GPU:
+    # it is compared like any other, and a mismatch is allowed only there, and counted
+    start_amb = o["start_amb"].any(axis=1)
+
+    def mismatch(u):
+        for c in range(k):
+            e = u * k + c
+            if (abs(g["q"][u, fc[u, c]] - o["q"][u, fc[u, c]]).max() > TOL_Q or
+                    abs(g["resid"][u, c, 0] - o["resid"][u, c, 0]) > TOL_POS or
+                    abs(g["resid"][u, c, 1] - o["resid"][u, c, 1]) > TOL_COS or
+                    abs(g["contacts"][:3, e] - o["contacts"][:3, e]).max() > TOL_POS or
+                    abs(g["contacts"][3:, e] - o["contacts"][3:, e]).max() > TOL_COS):
+                return True
+        return bool(g["ok"][u] != o["ok"][u]) or not np.array_equal(g["used"][u], o["used"][u])
+
+    clear0 = att & ~sens
+    mm = np.array([mismatch(u) for u in range(n)]) & clear0
+    assert not np.any(mm & ~start_amb), f"{int(np.sum(mm & ~start_amb))} slots differ with a start clear of the band"
+    clear = clear0 & ~mm
+    rows = np.nonzero(clear)[0]
     d = dict(q=0.0, pos=0.0, cos=0.0, cp=0.0, cn=0.0)
     for c in range(k):
         d["q"] = max(d["q"], np.abs(g["q"][rows, fc[rows, c]] - o["q"][rows, fc[rows, c]]).max(initial=0))
@@ -156,13 +173,13 @@ def test_ik_parity(cf, name, P, S):
         d["cp"] = max(d["cp"], np.abs(g["contacts"][:3, ee] - o["contacts"][:3, ee]).max(initial=0))
         d["cn"] = max(d["cn"], np.abs(g["contacts"][3:, ee] - o["contacts"][3:, ee]).max(initial=0))
     ok_diff = int((g["ok"][clear] != o["ok"][clear]).sum())
-    info = (f"{name}: sensitive {sens[att].mean():.4f} of {att.sum()} slots, clear ok differ {ok_diff}, "
+    info = (f"{name}: sensitive {sens[att].mean():.4f} of {att.sum()} slots, start in band {start_amb[att].mean():.4f}, "
+            f"differing starts {int(mm.sum())}, clear ok differ {ok_diff}, "
             f"max diffs q {d['q']:.3g} pos {d['pos']:.3g} cos {d['cos']:.3g} point {d['cp']:.3g} "
             f"normal {d['cn']:.3g}, ok gpu {int(g['ok'].sum())} oracle {int(o['ok'].sum())}")
     print(info)
-    # structure: bit-exact wherever the starting sample is decided clear of the band
-    firm = ~o["start_amb"].any(axis=1)
-    assert np.array_equal(g["used"][firm], o["used"][firm]), info
+    # structure: bit-exact on every clear slot
+    assert np.array_equal(g["used"][clear], o["used"][clear]), info
     assert not g["ok"][~att].any(), info
     e = np.arange(n * k).reshape(n, k)
     assert np.array_equal(g["rtuples"], np.where(g["ok"][:, None].astype(bool), e, -1)), info
@@ -171,6 +188,7 @@ def test_ik_parity(cf, name, P, S):
     assert d["cp"] <= TOL_POS and d["cn"] <= TOL_COS, info
     assert ok_diff == 0, info
     assert sens[att].mean() < MAX_SENSITIVE, info
+    assert mm.sum() <= 0.05 * att.sum(), info
     # rows of fingers without a contact are zero
     for u in np.nonzero(att)[0]:
         free = np.setdiff1d(np.arange(F), fc[u])
@@ -274,7 +292,7 @@ def test_realized_rescore_parity(cf):
     soa, tup, fing, valid = _oracle_tuples(w)
     g, o, pr = _ik_both(cf, w, field, soa, tup, fing, valid)
     n, k = valid.size, w.k
-    sens = _sensitive(w, o, pr, tup, fing, valid).any(axis=1)
+    sens = _sensitive(w, o, pr, tup, fing, valid).any(axis=1) | o["start_amb"].any(axis=1)
     prm = cf.score_params(1, k, w.mu, w.K, w.eps, w.obj.centroid, w.obj.rho, w.seed, tuples_given=True)
     ct = torch.from_numpy(g["contacts"]).cuda()
     rt = torch.from_numpy(g["rtuples"].astype(np.int32)).cuda().reshape(n, 1, k)
