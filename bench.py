@@ -48,6 +48,7 @@ def _args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--poses", type=int, default=0, help="override the workload's pose count (profiling captures)")
     ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--cpu-poses", type=int, default=32, help="poses in the oracle's timed sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -416,7 +417,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     props = torch.cuda.get_device_properties(dev)
 
-    w = synth.workload(args.workload, seed=rank)
+    w = synth.workload(args.workload, seed=rank, P=args.poses or None)
     F = w.hand.F
     q = torch.from_numpy(w.q).to(dev)
     soa = torch.from_numpy(w.obj.soa()).to(dev)
