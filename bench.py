@@ -514,6 +514,9 @@ def run_ours(args):
     if world == 1 and args.optimized_steps > 0:
         line["optimized"] = run_optimized(cf, torch, dev, w, args.optimized_steps, soa, poses, masks, counts, tuples,
                                           fingers, prm, flush)
+        # the same without the warm start (every candidate's LPs from c' = 0): the free lunch's effect
+        line["optimized"]["cold_start"] = run_optimized(cf, torch, dev, w, 1, soa, poses, masks, counts, tuples,
+                                                        fingers, prm, flush, warm_start=False)
     if world == 1 and args.gswo_steps > 0:
         line["gswo"] = run_gswo(cf, torch, dev, w, args.gswo_steps, soa, poses, masks, counts, tuples, fingers, prm,
                                 prm_given, flush)
@@ -647,7 +650,7 @@ def run_realized(cf, torch, dev, w, steps, soa, poses, masks, counts, tuples, fi
 OPT = dict(n_outer=2, n_inner=8, sigma=0.005, zero_tol=1e-6, min_gain=1e-2)
 
 
-def run_optimized(cf, torch, dev, w, steps, soa, poses, masks, counts, tuples, fingers, prm, flush):
+def run_optimized(cf, torch, dev, w, steps, soa, poses, masks, counts, tuples, fingers, prm, flush, warm_start=True):
     """Valid grasps/s when every sampled tuple goes through the blockwise
     zeroth-order contact optimisation of Alg. 2 (which scores the tuples it
     starts from).  One step = domain query, tuple sampling, optimisation; the
@@ -657,7 +660,7 @@ def run_optimized(cf, torch, dev, w, steps, soa, poses, masks, counts, tuples, f
     q = torch.from_numpy(w.q).to(dev)
     field = cf.build(w.hand, w.inv_h, w.bins, q)
     prm_opt = cf.score_params(w.T, w.k, w.mu, w.K, w.eps, w.obj.centroid, w.obj.rho, w.seed, tuples_given=True)
-    opt = cf.opt_params(**OPT)
+    opt = cf.opt_params(**OPT, warm_start=warm_start)
     tot = torch.zeros(1, dtype=torch.int64, device=dev)
     n_ev = 4
 
@@ -690,7 +693,7 @@ def run_optimized(cf, torch, dev, w, steps, soa, poses, masks, counts, tuples, f
     return {"metric": "valid grasps/s with Alg. 2 contact optimisation", "value": acc / (total_ms / 1e3),
             "unit": UNIT, "steps": steps, "ms_per_step": total_ms / steps,
             "breakdown_ms": {"query": float(per[0]), "sample": float(per[1]), "optimize": float(per[2])},
-            "accept_rate": acc / (steps * w.P * w.T), "params": OPT,
+            "accept_rate": acc / (steps * w.P * w.T), "params": dict(OPT, warm_start=warm_start),
             "lp_per_tuple": counters["lps"] / max(1, counters["tuples_scored"]),
             "pivots_per_lp": counters["lp_pivots"] / max(1, counters["lps"]),
             "warm_starts_per_tuple": counters["warm_starts"] / max(1, counters["tuples_scored"]),

@@ -45,6 +45,7 @@ extern "C" {
 #endif
 
 #define CF_MAX_FINGERS 8
+#define CF_MAX_SLOTS 16   /* table slots: one per finger, or one per (finger, link) patch */
 #define CF_MAX_JOINTS 8
 #define CF_MAX_SURF 256
 #define CF_MAX_BINS 32
@@ -103,14 +104,22 @@ typedef struct cf_field_params {
     float dilate_deg;         /* theta-dilated bins (the leaf test -x^T n >= theta_hit of Sec. 4.3): a query
                                  of bin b accepts every bin b' with d_b . d_b' >= cos(dilate_deg * (pi / 180))
                                  (FP64 on the host); 0 = the same bin only */
+    int32_t patches;          /* 0: one table slot per finger; 1: the fine-grained field of Sec. 4.4 ("break
+                                 down the whole hand surface into m patches, and compute the contact field for
+                                 each patch"), a patch being the surface points of one link of one finger: one
+                                 slot per (finger, link with surface points), fingers in order, links
+                                 ascending, at most CF_MAX_SLOTS; the query then returns per-patch domains,
+                                 which cf_merge_domains combines per finger.  Not with want_rep. */
 } cf_field_params;
 
 typedef struct cf_field cf_field;
 
 /* Table layout: one box of cells covering every finger's samples.  Cell
  * (x, y, z) of the box (x fastest) owns a record of record_words uint32 words;
- * finger f's normal-bin set is bits [(f % fingers_per_word) * bits_per_finger,
- * + n_bins) of word f / fingers_per_word of the record. */
+ * slot s's normal-bin set is bits [(s % fingers_per_word) * bits_per_finger,
+ * + n_bins) of word s / fingers_per_word of the record.  Slot s holds the
+ * samples of finger slot_finger[s] (link slot_link[s] in a patch field, -1:
+ * every link). */
 typedef struct cf_field_info {
     int32_t n_fingers, n_joints, n_surf, n_bins, n_samples;
     float inv_h;
@@ -118,7 +127,7 @@ typedef struct cf_field_info {
     int32_t box_dims[3];               /* cells per axis (0 when the field is empty) */
     int32_t bits_per_finger;           /* 8, 16 or 32 */
     int32_t fingers_per_word;          /* 32 / bits_per_finger */
-    int32_t record_words;              /* ceil(n_fingers / fingers_per_word) */
+    int32_t record_words;              /* ceil(n_slots / fingers_per_word) */
     int32_t finger_lo[CF_MAX_FINGERS][3];   /* tight cell bounds of finger f's samples */
     int32_t finger_dims[CF_MAX_FINGERS][3]; /* (0 if the finger has no sample) */
     int64_t table_words;               /* total uint32 words of the bit table */
@@ -126,6 +135,9 @@ typedef struct cf_field_info {
     float build_ms;                    /* device time of the two build kernels */
     float dilate_deg;                  /* bin dilation of queries (0: none) */
     uint32_t dilation[CF_MAX_BINS];    /* bins accepted by a query of bin b */
+    int32_t n_slots;                   /* table slots: n_fingers, or the patch count of a patch field */
+    int32_t slot_finger[CF_MAX_SLOTS]; /* finger of slot s */
+    int32_t slot_link[CF_MAX_SLOTS];   /* link of slot s in a patch field, -1 otherwise */
 } cf_field_info;
 
 /* Object surface points + outward unit normals, device SoA, N each. */
@@ -189,13 +201,26 @@ int cf_field_load(const char *path, cf_field **out);
 
 /* Def. Contact Surface Representation, Sec. 4.3 "Object Contact Query",
  * Sec. 5.3.  For every pose i (d_poses [P][12], object -> palm) and object point x, the
- * contact-surface vector (R p_x + t, -(R n_x)) is looked up in every finger's
- * table: bit x of d_masks[i][f][W] (W = ceil(N/32) words, bit x & 31 of word
- * x >> 5) is set iff its cell holds its normal bin.  Bits past N are 0.
- * d_counts[i][f] = popcount of the row.  d_masks may be NULL (counts only).
+ * contact-surface vector (R p_x + t, -(R n_x)) is looked up in every slot of
+ * the table (a finger, or a patch of a patch field): bit x of d_masks[i][s][W]
+ * (W = ceil(N/32) words, bit x & 31 of word x >> 5) is set iff its cell holds
+ * its normal bin in slot s.  Bits past N are 0.  d_counts[i][s] = popcount of
+ * the row.  d_masks may be NULL (counts only).  Rows: n_slots per pose.
  * Errors: CF_EINVAL, CF_ECUDA (launch). Asynchronous on `stream`. */
 int cf_query_domains(const cf_field *field, const cf_points *obj, const float *d_poses, int32_t n_poses,
                      uint32_t *d_masks, uint32_t *d_counts, cf_stream stream);
+
+/* Sec. 5.3 "Contact Domain Generation": the domains of one dependency group (a
+ * finger: the connected component of the kinematic tree once the static palm
+ * is removed) are merged.  For a patch field (cf_field_params.patches),
+ * d_group_masks[i][f][W] = OR over the slots s of finger f of
+ * d_slot_masks[i][s][W] (as cf_query_domains wrote them, n_slots rows per
+ * pose), and d_group_counts[i][f] its popcount: the per-finger domains that
+ * cf_score_tuples samples from.  For a plain field the rows are copied.  n_words
+ * = ceil(N/32) of the object queried.  Caller-owned device arrays, no
+ * allocation.  Errors: CF_EINVAL, CF_ECUDA.  Asynchronous on `stream`. */
+int cf_merge_domains(const cf_field *field, const uint32_t *d_slot_masks, int32_t n_poses, int32_t n_words,
+                     uint32_t *d_group_masks, uint32_t *d_group_counts, cf_stream stream);
 
 /* ---- tuple sampling and closure margin (Sec. 5.3; Alg. 2; Eq. GSWO) ----- */
 
@@ -349,6 +374,9 @@ typedef struct cf_opt_params {
     float sigma;        /* standard deviation of each tangent-plane mutation component (m) */
     float zero_tol;     /* margins <= zero_tol count as 0 (a closed grasp): optimisation stops there */
     float min_gain;     /* a candidate replaces the best so far only when its margin is < (1 - min_gain) x best */
+    int32_t warm_start; /* 1: a candidate's LPs start from the current tuple's final basis when the moved contact
+                           is nonbasic there (Sec. 5.4 "A Free Lunch"); 0: every candidate starts from c' = 0.
+                           Margins agree either way (each LP is solved to its optimum). */
 } cf_opt_params;
 
 /* Improves every valid tuple of d_tuples [P][T][k] in place (prm->tuples_given

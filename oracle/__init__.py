@@ -15,6 +15,8 @@ Functions (paper passages they follow are cited in ``cf_oracle.c``):
   Field               the sampled hand contact field as a set of codes
                       (Sec. 4.3, Alg. 1; Def. Contact Field (Hand))
   Field.query         contact domains as bitmasks (Sec. 4.2, Sec. 4.3 query)
+  PatchFields         fine-grained field: one field per (finger, link) patch,
+                      and the merge of a finger's patch domains (Sec. 4.4, 5.3)
   query_masks_brute   literal existential check, tiny inputs only
   sample_tuples       random k-tuples from k distinct finger domains (Sec. 5.3)
   closure_lp          linearised GSWO margin of one tuple (Eq. GSWO): k LPs
@@ -54,7 +56,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "cf_oracle.c")
 _LIB = os.path.join(_HERE, "liborc.so")
 
-__all__ = ["build", "lib", "philox4x32_10", "fk_links", "contact_vectors", "Field",
+__all__ = ["build", "lib", "philox4x32_10", "fk_links", "contact_vectors", "Field", "PatchFields",
            "query_masks_brute", "sample_tuples", "closure_lp", "score_tuples", "num_threads", "pack_code",
            "rep_codes", "point_codes", "dilation_masks"]
 
@@ -250,6 +252,60 @@ class Field:
         if mask32:
             out.append(m32)
         return tuple(out)
+
+
+class _SubHand:
+    """One finger of a hand restricted to the surface points of one link."""
+
+    def __init__(self, hand, f: int, link: int):
+        sel = np.asarray(hand.surf_link[f]) == link
+        self.F, self.J, self.M = 1, hand.J, int(sel.sum())
+        self.base = np.asarray(hand.base)[f:f + 1]
+        self.axis = np.asarray(hand.axis)[f:f + 1]
+        self.offset = np.asarray(hand.offset)[f:f + 1]
+        self.surf_p = np.asarray(hand.surf_p)[f:f + 1, sel]
+        self.surf_n = np.asarray(hand.surf_n)[f:f + 1, sel]
+        self.surf_link = np.asarray(hand.surf_link)[f:f + 1, sel]
+
+
+class PatchFields:
+    """The fine-grained contact field of Sec. 4.4: the hand surface broken into
+    patches, one field per patch, queried separately.  A patch is the surface
+    points of one link of one finger; patches are ordered by finger, then link
+    (ascending), skipping links without surface points.  Sec. 5.3 merges the
+    domains of a dependency group (a finger): ``merge``."""
+
+    def __init__(self, hand, q, inv_h, bins, band: bool = False, **kw):
+        q = np.asarray(q, np.float32)
+        self.F = hand.F
+        self.slots = []  # (finger, link)
+        self.fields = []
+        for f in range(hand.F):
+            for link in np.unique(np.asarray(hand.surf_link[f])).tolist():
+                self.slots.append((f, int(link)))
+                self.fields.append(Field(_SubHand(hand, f, link), q[f:f + 1], inv_h, bins, band=band, **kw))
+
+    def codes(self, s: int, which: str = "fp64") -> np.ndarray:
+        """Codes of slot s (as Field.codes of one finger)."""
+        return self.fields[s].codes(0, which)
+
+    def query(self, soa, poses, amb: bool = False):
+        """Per-patch domains [P, n_slots, W] and counts [P, n_slots] (plus band flags [P, n_slots, N])."""
+        outs = [fd.query(soa, poses, amb=amb) for fd in self.fields]
+        masks = np.concatenate([o[0] for o in outs], axis=1)
+        counts = np.concatenate([o[1] for o in outs], axis=1)
+        if amb:
+            return masks, counts, np.concatenate([o[2] for o in outs], axis=1)
+        return masks, counts
+
+    def merge(self, masks):
+        """Sec. 5.3: OR of each finger's patch rows -> [P, F, W] and the counts [P, F]."""
+        P, _, W = masks.shape
+        out = np.zeros((P, self.F, W), np.uint32)
+        for s, (f, _) in enumerate(self.slots):
+            out[:, f] |= masks[:, s]
+        counts = np.unpackbits(out.view(np.uint8), axis=2).sum(axis=2).astype(np.uint32)
+        return out, counts
 
 
 def dilation_masks(bins: np.ndarray, dilate_deg: float) -> np.ndarray:

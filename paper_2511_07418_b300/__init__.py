@@ -32,6 +32,7 @@ if not os.path.exists(LIB_PATH):
 _lib = ctypes.CDLL(LIB_PATH)
 
 CF_MAX_FINGERS = 8
+CF_MAX_SLOTS = 16
 CF_MAX_BINS = 32
 CF_OK = 0
 CF_EINVAL = 1
@@ -60,7 +61,7 @@ class HandDesc(Structure):
 
 class FieldParams(Structure):
     _fields_ = [("inv_h", c_float), ("n_bins", c_int32), ("bin_dirs", POINTER(c_float)), ("want_rep", c_int32),
-                ("dilate_deg", c_float)]
+                ("dilate_deg", c_float), ("patches", c_int32)]
 
 
 class IkParams(Structure):
@@ -70,7 +71,7 @@ class IkParams(Structure):
 
 class OptParams(Structure):
     _fields_ = [("n_outer", c_int32), ("n_inner", c_int32), ("sigma", c_float), ("zero_tol", c_float),
-                ("min_gain", c_float)]
+                ("min_gain", c_float), ("warm_start", c_int32)]
 
 
 class Tuning(Structure):
@@ -94,7 +95,8 @@ class FieldInfo(Structure):
                 ("fingers_per_word", c_int32), ("record_words", c_int32),
                 ("finger_lo", (c_int32 * 3) * CF_MAX_FINGERS), ("finger_dims", (c_int32 * 3) * CF_MAX_FINGERS),
                 ("table_words", c_int64), ("device_bytes", c_int64), ("build_ms", c_float), ("dilate_deg", c_float),
-                ("dilation", c_uint32 * CF_MAX_BINS)]
+                ("dilation", c_uint32 * CF_MAX_BINS), ("n_slots", c_int32), ("slot_finger", c_int32 * CF_MAX_SLOTS),
+                ("slot_link", c_int32 * CF_MAX_SLOTS)]
 
 
 class Points(Structure):
@@ -200,10 +202,11 @@ _cf_last_error = _sig("cf_last_error", [], c_char_p)
 _cf_device_status = _sig("cf_device_status", [POINTER(c_uint32)])
 _cf_device_counters = _sig("cf_device_counters", [POINTER(c_uint64), c_int])
 _cf_pool_usage = _sig("cf_pool_usage", [POINTER(c_uint64), c_int])
+_cf_merge = _sig("cf_merge_domains", [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p])
 
 EXPORTED = ["cf_build", "cf_field_get_info", "cf_field_copy_table", "cf_field_destroy", "cf_field_save",
             "cf_field_load", "cf_query_domains", "cf_score_tuples", "cf_plan_create", "cf_plan_run_host",
-            "cf_plan_destroy", "cf_last_error", "cf_device_status", "cf_device_counters", "cf_pool_usage", "cf_score_tuples_noalloc",
+            "cf_plan_destroy", "cf_last_error", "cf_device_status", "cf_device_counters", "cf_pool_usage", "cf_merge_domains", "cf_score_tuples_noalloc",
             "cf_sample_tuples", "cf_batch_create", "cf_batch_run", "cf_batch_launches", "cf_batch_destroy",
             "cf_engine_create", "cf_engine_submit", "cf_engine_poll", "cf_engine_result_free", "cf_engine_get_stats",
             "cf_engine_drain", "cf_engine_destroy", "cf_field_rep_slots", "cf_field_copy_rep", "cf_ik_dls",
@@ -284,9 +287,11 @@ def _check_score_shapes(soa, n_fingers, masks, counts, prm, P, tuples=None, fing
 class Field:
     """Library-owned contact field (cf_field)."""
 
-    def __init__(self, handle: int, n_fingers: int | None = None, n_joints: int | None = None):
+    def __init__(self, handle: int, n_fingers: int | None = None, n_joints: int | None = None,
+                 n_slots: int | None = None):
         self._h = c_void_p(handle)
         self._shape = (n_fingers, n_joints) if n_fingers is not None and n_joints is not None else None
+        self._slots = n_slots
 
     @property
     def handle(self):
@@ -307,6 +312,13 @@ class Field:
     @property
     def n_joints(self) -> int:
         return self._fj()[1]
+
+    @property
+    def n_slots(self) -> int:
+        """Table slots = rows per pose of the query: the fingers, or the patches of a patch field."""
+        if self._slots is None:
+            self._slots = int(self.info().n_slots)
+        return self._slots
 
     def info(self) -> FieldInfo:
         inf = FieldInfo()
@@ -351,10 +363,12 @@ class Field:
             pass
 
 
-def build(hand, inv_h, bin_dirs, q, stream=None, want_rep: bool = False, dilate_deg: float = 0.0) -> Field:
+def build(hand, inv_h, bin_dirs, q, stream=None, want_rep: bool = False, dilate_deg: float = 0.0,
+          patches: bool = False) -> Field:
     """cf_build: hand is any object with base/axis/offset/surf_p/surf_n/surf_link
     arrays (host) and optionally lo/hi/radius, q a [F, J, S] float32 CUDA tensor
-    of joint samples.  want_rep keeps the reverse-lookup table (needs limits)."""
+    of joint samples.  want_rep keeps the reverse-lookup table (needs limits).
+    patches: one table slot per (finger, link with surface points)."""
     import torch
     keep = [_np(hand.base, np.float32), _np(hand.axis, np.float32), _np(hand.offset, np.float32),
             _np(hand.surf_p, np.float32), _np(hand.surf_n, np.float32), _np(hand.surf_link, np.int32)]
@@ -370,19 +384,21 @@ def build(hand, inv_h, bin_dirs, q, stream=None, want_rep: bool = False, dilate_
                   *([_fp(a) for a in lim] if lim else [None, None, None]))
     dirs = _np(bin_dirs, np.float32)
     prm = FieldParams(float(np.float32(inv_h)), int(dirs.shape[0]), _fp(dirs), 1 if want_rep else 0,
-                      float(dilate_deg))
+                      float(dilate_deg), 1 if patches else 0)
     qp = _dev(q, torch.float32, "q")
     if q.dim() != 3 or tuple(q.shape[:2]) != (F, J):
         raise ValueError(f"q must be [F={F}, J={J}, S]")
     h = c_void_p()
     _check(_cf_build(byref(hd), byref(prm), qp, int(q.shape[2]), _stream(stream), byref(h)))
-    return Field(h.value, F, J)
+    n_slots = sum(len(np.unique(keep[5][f])) for f in range(F)) if patches else F
+    return Field(h.value, F, J, n_slots)
 
 
 def query_domains(field: Field, soa, poses, masks=None, counts=None, want_masks: bool = True, stream=None):
-    """cf_query_domains -> (masks [P, F, W] int32 view of uint32 words or None, counts [P, F] int32)."""
+    """cf_query_domains -> (masks [P, S, W] int32 view of uint32 words or None, counts [P, S] int32),
+    S = field.n_slots (the fingers, or the patches of a patch field)."""
     import torch
-    F = field.n_fingers
+    F = field.n_slots
     obj = points_struct(soa)
     P = int(poses.shape[0])
     _dev(poses, torch.float32, "poses")
@@ -395,6 +411,26 @@ def query_domains(field: Field, soa, poses, masks=None, counts=None, want_masks:
     mp = _dev(masks, torch.int32, "masks") if masks is not None else None
     _check(_cf_query(field.handle, byref(obj), c_void_p(poses.data_ptr()), P, mp, _dev(counts, torch.int32, "counts"),
                      _stream(stream)))
+    return masks, counts
+
+
+def merge_domains(field: Field, slot_masks, n_words: int, masks=None, counts=None, stream=None):
+    """cf_merge_domains: per-finger domains [P, F, W] and counts [P, F] from a
+    query's slot rows [P, n_slots, W] (Sec. 5.3 dependency groups)."""
+    import torch
+    P = int(slot_masks.shape[0])
+    F = field.n_fingers
+    if tuple(slot_masks.shape) != (P, field.n_slots, n_words):
+        raise ValueError(f"slot_masks must be [{P}, {field.n_slots}, {n_words}], got {list(slot_masks.shape)}")
+    dev = slot_masks.device
+    if masks is None:
+        masks = torch.empty((P, F, n_words), dtype=torch.int32, device=dev)
+    if counts is None:
+        counts = torch.empty((P, F), dtype=torch.int32, device=dev)
+    if tuple(masks.shape) != (P, F, n_words) or tuple(counts.shape) != (P, F):
+        raise ValueError("masks / counts must be [P, F, W] / [P, F]")
+    _check(_cf_merge(field.handle, _dev(slot_masks, torch.int32, "slot_masks"), P, int(n_words),
+                     _dev(masks, torch.int32, "masks"), _dev(counts, torch.int32, "counts"), _stream(stream)))
     return masks, counts
 
 
@@ -648,8 +684,9 @@ def score_gswo(soa, prm: ScoreParams, tuples, n_iter: int = 256, eps_g: float = 
     return value, accept
 
 
-def opt_params(n_outer=2, n_inner=8, sigma=0.005, zero_tol=1e-6, min_gain=1e-2) -> OptParams:
-    return OptParams(int(n_outer), int(n_inner), float(sigma), float(zero_tol), float(min_gain))
+def opt_params(n_outer=2, n_inner=8, sigma=0.005, zero_tol=1e-6, min_gain=1e-2, warm_start=True) -> OptParams:
+    return OptParams(int(n_outer), int(n_inner), float(sigma), float(zero_tol), float(min_gain),
+                     1 if warm_start else 0)
 
 
 def optimize_tuples(soa, n_fingers: int, masks, prm: ScoreParams, opt: OptParams, tuples, fingers, stream=None):

@@ -189,6 +189,42 @@ int setup_candidates(cf_field *fd) {
     return CF_OK;
 }
 
+// Table slots: one per finger, or (patch field, Sec. 4.4) one per (finger, link with surface points),
+// fingers in order and links ascending.
+int slot_map(cf_field *fd, const cf_hand_desc *hand, const cf_field_params *prm) {
+    if (prm->patches != 0 && prm->patches != 1) return fail(CF_EINVAL, "patches=%d not in {0, 1}", prm->patches);
+    if (prm->patches && prm->want_rep)
+        return fail(CF_EINVAL, "patch fields keep no representative table (want_rep needs patches = 0)");
+    FieldGeom &g = fd->geom;
+    g.patches = prm->patches;
+    memset(g.slot_of, -1, sizeof g.slot_of);
+    memset(g.slot_finger, -1, sizeof g.slot_finger);
+    memset(g.slot_link, -1, sizeof g.slot_link);
+    const int F = hand->n_fingers, J = hand->n_joints, M = hand->n_surf;
+    int ns = 0;
+    for (int f = 0; f < F; ++f) {
+        if (!g.patches) {
+            for (int l = 0; l < J; ++l) g.slot_of[f][l] = (int8_t)f;
+            g.slot_finger[f] = (int8_t)f;
+            ++ns;
+            continue;
+        }
+        for (int l = 0; l < J; ++l) {
+            bool has = false;
+            for (int m = 0; m < M && !has; ++m) has = hand->surf_link[(size_t)f * M + m] == l;
+            if (!has) continue;
+            if (ns == CF_MAX_SLOTS)
+                return fail(CF_EINVAL, "the hand has more than %d (finger, link) patches", CF_MAX_SLOTS);
+            g.slot_of[f][l] = (int8_t)ns;
+            g.slot_finger[ns] = (int8_t)f;
+            g.slot_link[ns] = (int8_t)l;
+            ++ns;
+        }
+    }
+    g.F = ns;
+    return CF_OK;
+}
+
 int geom_from_params(cf_field *fd, const cf_field_params *prm) {
     if (!prm) return fail(CF_EINVAL, "params is NULL");
     if (!(prm->inv_h > 0.f) || !isfinite(prm->inv_h)) return fail(CF_EINVAL, "inv_h must be finite and > 0");
@@ -309,6 +345,7 @@ extern "C" int cf_build(const cf_hand_desc *hand, const cf_field_params *prm, co
     fd->st = st;
     CF_TRY(cudaGetDevice(&fd->dev), "cudaGetDevice");
     if ((rc = geom_from_params(fd, prm)) || (rc = setup_candidates(fd))) { field_release(fd); return rc; }
+    if ((rc = slot_map(fd, hand, prm))) { field_release(fd); return rc; }
 
     const bool want_rep = prm->want_rep != 0;
     if (want_rep && !hand->lo) { field_release(fd); return fail(CF_EINVAL, "want_rep needs the joint limits"); }
@@ -423,7 +460,7 @@ extern "C" int cf_build(const cf_hand_desc *hand, const cf_field_params *prm, co
     }
     g.bits = slot_bits_for(g.B);
     g.fpw = 32 / g.bits;
-    g.rw = (F + g.fpw - 1) / g.fpw;
+    g.rw = (g.F + g.fpw - 1) / g.fpw;  // slots per record
     int64_t words = 0;
     if (lo[0] <= hi[0]) {
         for (int c = 0; c < 3; ++c) { g.lo[c] = lo[c]; g.dims[c] = hi[c] - lo[c] + 1; }
@@ -524,6 +561,23 @@ extern "C" int cf_field_get_info(const cf_field *fd, cf_field_info *info) {
     info->build_ms = fd->build_ms < 0.f ? 0.f : fd->build_ms;
     info->dilate_deg = fd->geom.dilate_deg;
     for (int b = 0; b < CF_MAX_BINS; ++b) info->dilation[b] = fd->geom.dil[b];
+    info->n_slots = fd->geom.F;
+    for (int sl = 0; sl < CF_MAX_SLOTS; ++sl) {
+        info->slot_finger[sl] = sl < fd->geom.F ? fd->geom.slot_finger[sl] : -1;
+        info->slot_link[sl] = sl < fd->geom.F ? fd->geom.slot_link[sl] : -1;
+    }
+    return CF_OK;
+}
+
+extern "C" int cf_merge_domains(const cf_field *fd, const uint32_t *d_slot_masks, int32_t n_poses, int32_t n_words,
+                                uint32_t *d_group_masks, uint32_t *d_group_counts, cf_stream stream) {
+    if (!fd) return fail(CF_EINVAL, "field is NULL");
+    if (n_poses < 0 || n_words < 0) return fail(CF_EINVAL, "n_poses / n_words < 0");
+    if (n_poses == 0) return CF_OK;
+    if (!d_slot_masks || !d_group_masks || !d_group_counts) return fail(CF_EINVAL, "array pointer is NULL");
+    CF_TRY(launch_merge_domains(fd->geom, fd->F, d_slot_masks, n_poses, n_words, d_group_masks, d_group_counts,
+                                (cudaStream_t)stream),
+           "launch k_merge_domains");
     return CF_OK;
 }
 
@@ -563,7 +617,7 @@ extern "C" int cf_field_destroy(cf_field *fd) {
 }
 
 namespace {
-const char kMagic[8] = {'C', 'F', 'F', 'I', 'E', 'L', 'D', '3'};
+const char kMagic[8] = {'C', 'F', 'F', 'I', 'E', 'L', 'D', '4'};
 }
 
 extern "C" int cf_field_save(const cf_field *fd, const char *path) {
@@ -802,6 +856,7 @@ extern "C" int cf_optimize_tuples(const cf_points *obj, int32_t n_fingers, const
     if (!(opt->sigma >= 0.f) || !isfinite(opt->sigma)) return fail(CF_EINVAL, "sigma must be finite and >= 0");
     if (!(opt->zero_tol >= 0.f) || !isfinite(opt->zero_tol)) return fail(CF_EINVAL, "zero_tol must be >= 0");
     if (!(opt->min_gain >= 0.f && opt->min_gain < 1.f)) return fail(CF_EINVAL, "min_gain must be in [0, 1)");
+    if (opt->warm_start != 0 && opt->warm_start != 1) return fail(CF_EINVAL, "warm_start not in {0, 1}");
     ScoreArgs a;
     int rc = fill_score_args(obj, n_fingers, d_masks, nullptr, n_poses, prm, d_tuples, const_cast<uint8_t *>(d_fingers),
                              d_margin, d_accept, &a);
@@ -816,7 +871,7 @@ extern "C" int cf_optimize_tuples(const cf_points *obj, int32_t n_fingers, const
     cudaError_t e = cudaMemsetAsync(work, 0, sizeof(unsigned int), st);
     if (e == cudaSuccess) {
         a.work = work;
-        e = launch_optimize(a, opt->n_outer, opt->n_inner, opt->sigma, opt->zero_tol, opt->min_gain, st);
+        e = launch_optimize(a, opt->n_outer, opt->n_inner, opt->sigma, opt->zero_tol, opt->min_gain, opt->warm_start, st);
     }
     cudaError_t e2 = cudaFreeAsync(work, st);
     if (e != cudaSuccess) return cuda_fail(e, "launch k_optimize_tuples");
@@ -925,6 +980,10 @@ extern "C" int cf_batch_create(const cf_batch_item *items, int32_t n_items, cf_b
         if (!it.field) { delete b; return fail(CF_EINVAL, "item %d: field is NULL", i); }
         if (it.prm.tuples_given) { delete b; return fail(CF_EINVAL, "item %d: batches sample their own tuples", i); }
         if (it.field->table_words == 0) { delete b; return fail(CF_EINVAL, "item %d: empty field", i); }
+        if (it.field->geom.patches) {
+            delete b;
+            return fail(CF_EINVAL, "item %d: a patch field's domains need cf_merge_domains before sampling", i);
+        }
         int rc = check_points(&it.obj);
         if (!rc) rc = fill_score_args(&it.obj, it.field->F, it.d_masks, it.d_counts, it.n_poses, &it.prm, it.d_tuples,
                                       it.d_fingers, it.d_margin, it.d_accept, &sargs[i]);
@@ -1229,8 +1288,10 @@ extern "C" int cf_autotune(const cf_batch_item *items, int32_t n_items, int32_t 
                            double *best_ms) {
     if (!items || n_items < 1) return fail(CF_EINVAL, "no items");
     if (reps < 1 || reps > 64) return fail(CF_EINVAL, "reps=%d not in [1,64]", reps);
-    for (int i = 0; i < n_items; ++i)
+    for (int i = 0; i < n_items; ++i) {
         if (!items[i].field || items[i].prm.tuples_given) return fail(CF_EINVAL, "item %d: no field or tuples given", i);
+        if (items[i].field->geom.patches) return fail(CF_EINVAL, "item %d: patch fields are not tuned", i);
+    }
     cf_tuning saved;
     int rc = cf_get_tuning(&saved);
     if (rc) return rc;
@@ -1370,6 +1431,7 @@ extern "C" int cf_plan_run_host(cf_plan *pl, const cf_field *fd, const float *h_
                                 uint8_t *h_accept, int64_t *h_n_accepted, cf_stream stream) {
     if (!pl || !fd || !prm || (n > 0 && !h_soa) || (n_poses > 0 && !h_poses)) return fail(CF_EINVAL, "NULL argument");
     if (fd->F > pl->F) return fail(CF_EINVAL, "field has %d fingers, plan holds %d", fd->F, pl->F);
+    if (fd->geom.patches) return fail(CF_EINVAL, "a plan samples from finger domains: not a patch field");
     if (n < 0 || n > pl->n_max) return fail(CF_EINVAL, "n=%d not in [0,%d]", n, pl->n_max);
     if (n_poses < 0 || n_poses > pl->p_max) return fail(CF_EINVAL, "n_poses=%d not in [0,%d]", n_poses, pl->p_max);
     if (prm->n_tuples != pl->T || prm->k != pl->k) return fail(CF_EINVAL, "T / k differ from the plan's");

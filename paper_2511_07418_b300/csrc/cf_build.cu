@@ -204,8 +204,9 @@ __global__ void __launch_bounds__(kThreads) k_fk_bin(HandDev h, const float *__r
         }
         const int s = chunk * kThreads + threadIdx.x;
         if (l < 0 || s >= S) continue;
-        uint32_t *tab = table + f / g.fpw;
-        const int shift = (f % g.fpw) * g.bits;
+        const int slot = g.slot_of[f][l];  // the finger's slot, or its link's patch slot
+        uint32_t *tab = table + slot / g.fpw;
+        const int shift = (slot % g.fpw) * g.bits;
         float Rl[9], tl[3];
         {
             const float *lk = links + ((size_t)(f * J + l) * 12) * S + s;

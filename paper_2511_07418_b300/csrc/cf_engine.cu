@@ -549,6 +549,10 @@ extern "C" int cf_engine_create(const cf_engine_params *prm, cf_engine **out) {
             delete e;
             return fail(CF_EINVAL, "field %d is NULL or empty", i);
         }
+        if (prm->fields[i]->geom.patches) {
+            delete e;
+            return fail(CF_EINVAL, "field %d is a patch field: the engine samples from finger domains", i);
+        }
         e->fields.push_back(prm->fields[i]);
         e->geoms.push_back(prm->fields[i]->geom);
     }

@@ -67,7 +67,8 @@ constexpr int kCandCells = 6 * kCandG * kCandG;
 // box of cells over all fingers; each cell owns a record of `rw` words and
 // finger f's bin set sits at bit (f % fpw) * bits of word f / fpw.
 struct FieldGeom {
-    int F, B;
+    int F;                   // table slots (record rows of a query): the fingers, or the patches of a patch field
+    int B;
     float inv_h;
     float clamp;             // |x| is clamped to this before the cell floor
     int lo[3];               // box: first cell
@@ -79,6 +80,9 @@ struct FieldGeom {
     float dilate_deg;           // 0: no dilation
     int use_cand;            // 1: candidate table valid (every cell has <= 4 candidates)
     const uint32_t *cand;    // device [kCandCells]
+    int patches;             // 1: one slot per (finger, link) patch (Sec. 4.4 fine-grained field)
+    int8_t slot_of[CF_MAX_FINGERS][CF_MAX_JOINTS];  // slot of (finger, link); -1: a link without surface points
+    int8_t slot_finger[CF_MAX_SLOTS], slot_link[CF_MAX_SLOTS];  // owner of each slot (link -1: every link)
 };
 
 inline int slot_bits_for(int B) { return B <= 8 ? 8 : (B <= 16 ? 16 : 32); }
@@ -296,6 +300,10 @@ struct QueryDesc {
 cudaError_t launch_query_batch(const QueryDesc *d_descs, const FieldGeom *d_geoms, int n_desc, int total_items,
                                int ppb, unsigned int *d_work, cudaStream_t st);
 int query_blocks(int P, int ppb);  // grid blocks one object of P poses needs at ppb poses per block
+// Sec. 5.3 dependency-group merge: group_masks[i][f] = OR of slot_masks[i][s] over g.slot_finger[s] == f
+// (n_fingers groups), group_counts its popcount.
+cudaError_t launch_merge_domains(const FieldGeom &g, int n_fingers, const uint32_t *slot_masks, int P, int W,
+                                 uint32_t *group_masks, uint32_t *group_counts, cudaStream_t st);
 // The current device's SM count and the resident blocks per SM of kernel `func` at `threads` threads
 // and `smem` dynamic shared bytes, queried once per (device, kernel, shape) and then served from a cache.
 cudaError_t launch_shape(const void *func, int threads, size_t smem, int *per_sm, int *sms);
@@ -344,7 +352,7 @@ size_t score_smem_bytes(int F, int W, int T, int k, bool sampling);
 // Alg. 2 contact optimisation of the tuples in place (a.tuples / a.fingers given;
 // a.masks, a.work zeroed, margin / accept out); n_inner in {4, 8, 16}
 cudaError_t launch_optimize(const ScoreArgs &a, int n_outer, int n_inner, float sigma, float zero_tol,
-                            float min_gain, cudaStream_t st);
+                            float min_gain, int warm_start, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // host helpers shared by the ABI translation units

@@ -26,6 +26,7 @@
 // cell names at most 4 bins, evaluated in ascending order with the same FP32
 // dot products and first-maximum rule as a full scan over the B directions,
 // so the bin is identical to the full scan's.
+#include <limits.h>
 #include <string.h>
 
 #include <algorithm>
@@ -79,7 +80,7 @@ struct QueryArgs {
 // the field's bin directions and dilation sets.
 struct QuerySmem {
     __align__(16) float pose[kMaxPosesPerBlock][12];
-    unsigned cnt[kMaxPosesPerBlock][CF_MAX_FINGERS];
+    unsigned cnt[kMaxPosesPerBlock][CF_MAX_SLOTS];
     float4 dir[CF_MAX_BINS];
     uint32_t dil[CF_MAX_BINS];
 };
@@ -272,6 +273,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_query_batch(const QueryDesc *__
         break;
         switch (s_geom.F) {
             CF_QB(1) CF_QB(2) CF_QB(3) CF_QB(4) CF_QB(5) CF_QB(6) CF_QB(7) CF_QB(8)
+            CF_QB(9) CF_QB(10) CF_QB(11) CF_QB(12) CF_QB(13) CF_QB(14) CF_QB(15) CF_QB(16)
             default: break;
         }
 #undef CF_QB
@@ -305,12 +307,61 @@ cudaError_t launch_any(const QueryArgs &a, const FieldGeom &g, int grid, cudaStr
         }
     switch (g.F) {
         CF_QF(1) CF_QF(2) CF_QF(3) CF_QF(4) CF_QF(5) CF_QF(6) CF_QF(7) CF_QF(8)
+        CF_QF(9) CF_QF(10) CF_QF(11) CF_QF(12) CF_QF(13) CF_QF(14) CF_QF(15) CF_QF(16)
         default: return cudaErrorInvalidValue;
     }
 #undef CF_QF
 }
 
+// Sec. 5.3: merge the domains of one dependency group (a finger's patch slots).
+// Block per (pose, finger): each thread ORs the group's slot rows word by word
+// (coalesced over words) and the popcounts are summed in the block.
+constexpr int kMergeThreads = 256;
+__global__ void __launch_bounds__(kMergeThreads) k_merge_domains(const uint32_t *__restrict__ slot_masks, int S, int W,
+                                                                 int F, uint32_t slot_set0, uint32_t slot_set1,
+                                                                 uint32_t slot_set2, uint32_t slot_set3,
+                                                                 uint32_t slot_set4, uint32_t slot_set5,
+                                                                 uint32_t slot_set6, uint32_t slot_set7,
+                                                                 uint32_t *__restrict__ group_masks,
+                                                                 uint32_t *__restrict__ group_counts) {
+    __shared__ unsigned s_cnt[kMergeThreads / 32];
+    const int i = blockIdx.x / F, f = blockIdx.x - i * F;
+    const uint32_t sets[8] = {slot_set0, slot_set1, slot_set2, slot_set3, slot_set4, slot_set5, slot_set6, slot_set7};
+    const uint32_t mine = sets[f];  // slots of finger f
+    const uint32_t *src = slot_masks + (size_t)i * S * W;
+    uint32_t *dst = group_masks + ((size_t)i * F + f) * W;
+    unsigned c = 0;
+    for (int w = threadIdx.x; w < W; w += kMergeThreads) {
+        uint32_t v = 0u;
+        for (uint32_t m = mine; m; m &= m - 1) v |= __ldg(src + (size_t)(__ffs(m) - 1) * W + w);
+        dst[w] = v;
+        c += __popc(v);
+    }
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0) s_cnt[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned t = 0;
+        for (int j = 0; j < kMergeThreads / 32; ++j) t += s_cnt[j];
+        group_counts[(size_t)i * F + f] = t;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_merge_domains(const FieldGeom &g, int n_fingers, const uint32_t *slot_masks, int P, int W,
+                                 uint32_t *group_masks, uint32_t *group_counts, cudaStream_t st) {
+    if (P <= 0) return cudaSuccess;
+    if (n_fingers < 1 || n_fingers > CF_MAX_FINGERS || g.F < 1 || g.F > CF_MAX_SLOTS) return cudaErrorInvalidValue;
+    uint32_t sets[CF_MAX_FINGERS] = {};
+    for (int s = 0; s < g.F; ++s) sets[(int)g.slot_finger[s]] |= 1u << s;
+    const long long blocks = (long long)P * n_fingers;
+    if (blocks > INT_MAX) return cudaErrorInvalidValue;
+    k_merge_domains<<<(unsigned)blocks, kMergeThreads, 0, st>>>(slot_masks, g.F, W, n_fingers, sets[0], sets[1], sets[2],
+                                                              sets[3], sets[4], sets[5], sets[6], sets[7], group_masks,
+                                                              group_counts);
+    return cudaGetLastError();
+}
 
 int query_blocks(int P, int ppb) { return (P + ppb - 1) / ppb; }
 

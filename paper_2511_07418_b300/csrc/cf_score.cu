@@ -501,6 +501,7 @@ __device__ __forceinline__ void wrench_column(const ScoreArgs &a, int x, float e
 struct OptArgs {
     int n_outer, n_inner;
     float sigma, zero_tol, min_gain;
+    int warm_start;
 };
 
 // One warp per tuple (persistent warps, work counter).  Per outer iteration and
@@ -633,7 +634,7 @@ __global__ void __launch_bounds__(kOptThreads) k_optimize_tuples(const ScoreArgs
                         // warm start from the current tuple's final basis when contact i is nonbasic there,
                         // else from c' = 0
                         BoxLp<NS> st = cur;
-                        if (lp_replace_contact<NS>(st, wt, i, k, K, lane, buf)) ++n_warm;
+                        if (o.warm_start && lp_replace_contact<NS>(st, wt, i, k, K, lane, buf)) ++n_warm;
                         else lp_init_cold<NS>(st, wt, kK, lane);
                         const float Jt = lp_solve_margin<NS>(st, k, K, lane, buf, n_piv, n_lp, flags);
                         const float Jtc = Jt <= o.zero_tol ? 0.f : Jt;
@@ -1160,9 +1161,9 @@ cudaError_t launch_score(const ScoreArgs &a, cudaStream_t st) {
 }
 
 cudaError_t launch_optimize(const ScoreArgs &a, int n_outer, int n_inner, float sigma, float zero_tol,
-                            float min_gain, cudaStream_t st) {
+                            float min_gain, int warm_start, cudaStream_t st) {
     if (a.P <= 0) return cudaSuccess;
-    const OptArgs o{n_outer, n_inner, sigma, zero_tol, min_gain};
+    const OptArgs o{n_outer, n_inner, sigma, zero_tol, min_gain, warm_start};
     const long long total = (long long)a.P * a.T;
     cudaError_t err;
     int dev = 0, sms = 0;

@@ -47,13 +47,20 @@ def _gpu(cf, w, soa, m, tup, fing, **kw):
     return t.cpu().numpy(), margin.cpu().numpy(), accept.cpu().numpy()
 
 
-@pytest.mark.parametrize("name,P,S,n_inner", [("hand16_superquadric", 4, 8192, 8), ("tiny_sphere", 16, 4096, 8),
-                                              ("hand20_tool", 2, 8192, 8), ("hand16_superquadric", 2, 4096, 4),
-                                              ("tiny_sphere", 8, 2048, 16)])
-def test_optimize_parity(cf, name, P, S, n_inner):
+@pytest.mark.parametrize("name,P,S,n_inner,warm", [("hand16_superquadric", 4, 8192, 8, True),
+                                                   ("tiny_sphere", 16, 4096, 8, True),
+                                                   ("hand20_tool", 2, 8192, 8, True),
+                                                   ("hand16_superquadric", 2, 4096, 4, True),
+                                                   ("tiny_sphere", 8, 2048, 16, True),
+                                                   ("hand16_superquadric", 4, 8192, 8, False)])
+def test_optimize_parity(cf, name, P, S, n_inner, warm):
+    """Warm start or not, every LP is solved to its optimum: the same oracle path holds."""
     w, soa, m, tup, fing = _inputs(name, P, S)
     kw = dict(n_outer=2, n_inner=n_inner, sigma=0.005, zero_tol=1e-6, min_gain=1e-2)
-    gt, gm, ga = _gpu(cf, w, soa, m, tup, fing, **kw)
+    cf.device_counters(reset=True)
+    gt, gm, ga = _gpu(cf, w, soa, m, tup, fing, warm_start=warm, **kw)
+    warm_starts = cf.device_counters()["warm_starts"]
+    assert (warm_starts > 0) == warm
     ot, om, oa, amb = CO.optimize_tuples(soa, m, tup, fing, w.T, w.mu, w.K, w.obj.centroid, w.obj.rho, w.eps, w.seed,
                                          **kw)
     assert cf.device_status() == 0
