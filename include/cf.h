@@ -465,6 +465,39 @@ typedef struct cf_place_params {
 int cf_place(const cf_field *field, const cf_points *obj, int32_t n_poses, const cf_place_params *prm,
              float *d_poses, cf_stream stream);
 
+/* Static-link placement (Sec. 5.2, last paragraph): poses that put the object
+ * against the palm, for grasps such as the power grasp.  The palm is the box
+ * [lo, hi] of the palm frame; its top face z = hi[2] is the contact surface,
+ * outward normal +z.  Pose i draws Philox4x32-10 words (w0..w3) at counter
+ * (i + pose_base, 0x57A7, 0, 0), key seed: object point x = floor(w0 N / 2^32);
+ * palm point c = (lo_x + u1 (hi_x - lo_x), lo_y + u2 (hi_y - lo_y), hi_z),
+ * u = (w >> 8) 2^-24; R = Rot(+z, 2 pi u3) R_align with R_align the shortest
+ * rotation taking n_x to -z (the object's outward normal at x faces into the
+ * palm; a half turn about (n_x x e) / |...| when n_x = +z, e = e_x); t = c - R
+ * p_x.  FP64, rounded to FP32 into d_poses [P][12].  d_static_pt[i] = x.
+ * The penetration filter: d_valid[i] = 0 when some object point q = R p + t
+ * (FP32, with the stored pose) lies inside the palm's xy rectangle with
+ * lo_z <= q_z < hi_z - pen_margin (the placement "causes penetration"), else 1.
+ * A valid pose's static contact (x, and the palm's force along -n_x) joins the
+ * finger contacts through cf_append_contact.  Errors: CF_EINVAL, CF_ECUDA.
+ * Asynchronous on `stream`. */
+typedef struct cf_palm_desc {
+    float lo[3], hi[3];  /* palm box, palm frame (lo < hi per axis) */
+} cf_palm_desc;
+int cf_place_static(const cf_palm_desc *palm, const cf_points *obj, int32_t n_poses, uint64_t seed,
+                    uint32_t pose_base, float pen_margin, float *d_poses, int32_t *d_static_pt, uint8_t *d_valid,
+                    cf_stream stream);
+
+/* Tuples with one more contact in front: d_out[i][t] = (d_first[i],
+ * d_tuples[i][t][0 .. k-1]) for [P][T][k] tuples, d_out [P][T][k+1]; a pose
+ * whose d_first is < 0 or whose d_valid (may be NULL) is 0 gets an invalid
+ * tuple (all -1), as does an invalid input tuple.  With cf_place_static this
+ * scores the static contact with the sampled finger contacts (the "contact
+ * vectors" that placement advances, Sec. 5.2).  Errors: CF_EINVAL, CF_ECUDA.
+ * Asynchronous on `stream`. */
+int cf_append_contact(const int32_t *d_tuples, int32_t n_poses, int32_t n_tuples, int32_t k, const int32_t *d_first,
+                      const uint8_t *d_valid, int32_t *d_out, cf_stream stream);
+
 /* Concave-point removal: point x is kept (d_keep[x] = 1) unless the object SDF
  * (trilinear, cf_sdf_build) is below -tau at the centre or at a corner of the
  * upper half of the cube of side `side` resting on the tangent plane outside x

@@ -9,6 +9,11 @@ library).
   place_exhaustive  a random field code's cell centre and bin direction aligned
                     with a random object point and its flipped normal, spun by a
                     random angle about the normal
+  place_static      the object against the palm (a static link): a random point
+                    of the palm's top face meets a random object point whose
+                    outward normal faces into the palm, spun by a random angle
+                    about the palm normal; rejected when some object point sinks
+                    into the palm deeper than the penetration margin
   concave_keep      the small-box test: a cube of side s resting on the tangent
                     plane outside each point; the point goes when the SDF at the
                     cube's centre or a corner of its upper half is below -tau
@@ -26,6 +31,7 @@ from .kinematics import sdf_trilinear
 
 TAG_CANONICAL = 0x91AC
 TAG_EXHAUSTIVE = 0xE7A1
+TAG_STATIC = 0x57A7
 
 
 def _words(i, tag, seed):
@@ -122,6 +128,58 @@ def place_exhaustive(field, bins, inv_h, soa, P, seed, pose_base=0):
         chosen[i] = (kx, ky, kz, f, b)
         pts[i] = x
     return out, chosen, pts
+
+
+def place_static(palm_lo, palm_hi, soa, P, seed, pose_base=0, pen_margin=2e-3, band=1e-6):
+    """Sec. 5.2, static links.  Returns (poses [P,12] float32, static point [P],
+    valid [P] uint8, ambiguous [P] bool).  The penetration test uses the stored
+    FP32 pose evaluated in FP64; a pose is ambiguous when a point's depth below
+    the face, or its distance to the rectangle's edges, is within `band` of a
+    decision boundary."""
+    lo = np.asarray(palm_lo, np.float32).astype(np.float64)
+    hi = np.asarray(palm_hi, np.float32).astype(np.float64)
+    soa = np.asarray(soa, np.float32)
+    N = soa.shape[1]
+    pts = soa[0:3].T.astype(np.float64)
+    top = float(np.float32(np.float32(hi[2]) - np.float32(pen_margin)))  # the kernel's threshold, in FP32
+    out = np.zeros((P, 12), np.float32)
+    xs = np.zeros(P, np.int64)
+    valid = np.zeros(P, np.uint8)
+    amb = np.zeros(P, bool)
+    z = np.array([0.0, 0.0, 1.0])
+    for i in range(P):
+        w = _words(i + pose_base, TAG_STATIC, seed)
+        x = (int(w[0]) * N) >> 32
+        c = np.array([lo[0] + _u(w[1]) * (hi[0] - lo[0]), lo[1] + _u(w[2]) * (hi[1] - lo[1]), hi[2]])
+        a = soa[3:6, x].astype(np.float64)
+        a = a / np.linalg.norm(a)
+        b = -z
+        v = np.cross(a, b)
+        sv = float(np.linalg.norm(v))
+        cdot = float(a @ b)
+        if sv > 1e-12:
+            Ra = _rodrigues(v / sv, math.atan2(sv, cdot))
+        elif cdot < 0:  # n_x = +z
+            Ra = _rodrigues(np.array([0.0, 1.0, 0.0]), math.pi)
+        else:
+            Ra = np.eye(3)
+        R = _rodrigues(z, 2 * math.pi * _u(w[3])) @ Ra
+        t = c - R @ soa[0:3, x].astype(np.float64)
+        out[i] = _pose32(R, t)
+        xs[i] = x
+        T = out[i].astype(np.float64).reshape(3, 4)
+        q = pts @ T[:, :3].T + T[:, 3]
+        inside = np.all((q[:, :2] >= lo[:2]) & (q[:, :2] <= hi[:2]), axis=1) & (q[:, 2] >= lo[2])
+        pen = inside & (q[:, 2] < top)
+        valid[i] = 0 if pen.any() else 1
+        # decisions within the band of a boundary: depth at the threshold, or a rectangle / bottom edge
+        near = (np.abs(q[:, 2] - top) <= band) | np.any(np.abs(q[:, :2] - lo[:2]) <= band, axis=1) | \
+            np.any(np.abs(q[:, :2] - hi[:2]) <= band, axis=1) | (np.abs(q[:, 2] - lo[2]) <= band)
+        close = near & (q[:, 2] < top + band) & (q[:, 2] >= lo[2] - band) & \
+            np.all((q[:, :2] >= lo[:2] - band) & (q[:, :2] <= hi[:2] + band), axis=1)
+        # firm when some penetrating point is clear of the band; otherwise a close point may flip it
+        amb[i] = bool(close.any()) and not bool((pen & ~close).any())
+    return out, xs, valid, amb
 
 
 def concave_keep(soa, grid, amb, lo, h, side, tau, band=1e-6):

@@ -88,6 +88,10 @@ class RealizeParams(Structure):
     _fields_ = [("pen_margin", c_float), ("axis_step", c_float), ("seed", c_uint64)]
 
 
+class PalmDesc(Structure):
+    _fields_ = [("lo", c_float * 3), ("hi", c_float * 3)]
+
+
 class FieldInfo(Structure):
     _fields_ = [("n_fingers", c_int32), ("n_joints", c_int32), ("n_surf", c_int32), ("n_bins", c_int32),
                 ("n_samples", c_int32), ("inv_h", c_float),
@@ -203,10 +207,13 @@ _cf_device_status = _sig("cf_device_status", [POINTER(c_uint32)])
 _cf_device_counters = _sig("cf_device_counters", [POINTER(c_uint64), c_int])
 _cf_pool_usage = _sig("cf_pool_usage", [POINTER(c_uint64), c_int])
 _cf_merge = _sig("cf_merge_domains", [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p])
+_cf_place_static = _sig("cf_place_static", [POINTER(PalmDesc), POINTER(Points), c_int32, c_uint64, c_uint32, c_float,
+                                            c_void_p, c_void_p, c_void_p, c_void_p])
+_cf_append = _sig("cf_append_contact", [c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p])
 
 EXPORTED = ["cf_build", "cf_field_get_info", "cf_field_copy_table", "cf_field_destroy", "cf_field_save",
             "cf_field_load", "cf_query_domains", "cf_score_tuples", "cf_plan_create", "cf_plan_run_host",
-            "cf_plan_destroy", "cf_last_error", "cf_device_status", "cf_device_counters", "cf_pool_usage", "cf_merge_domains", "cf_score_tuples_noalloc",
+            "cf_plan_destroy", "cf_last_error", "cf_device_status", "cf_device_counters", "cf_pool_usage", "cf_merge_domains", "cf_place_static", "cf_append_contact", "cf_score_tuples_noalloc",
             "cf_sample_tuples", "cf_batch_create", "cf_batch_run", "cf_batch_launches", "cf_batch_destroy",
             "cf_engine_create", "cf_engine_submit", "cf_engine_poll", "cf_engine_result_free", "cf_engine_get_stats",
             "cf_engine_drain", "cf_engine_destroy", "cf_field_rep_slots", "cf_field_copy_rep", "cf_ik_dls",
@@ -877,3 +884,36 @@ def pool_usage(reset_high: bool = False):
     v = (c_uint64 * 3)()
     _check(_cf_pool_usage(v, 1 if reset_high else 0))
     return {"used": int(v[0]), "reserved": int(v[1]), "high": int(v[2])}
+
+
+def place_static(palm_lo, palm_hi, soa, n_poses: int, seed: int, pose_base: int = 0, pen_margin: float = 2e-3,
+                 stream=None):
+    """cf_place_static -> (poses [P, 12] f32, static point [P] int32, valid [P] uint8): the object placed
+    against the palm box's top face (Sec. 5.2 static links), with the penetration filter."""
+    import torch
+    obj = points_struct(soa)
+    dev = soa.device
+    P = int(n_poses)
+    poses = torch.empty((P, 12), dtype=torch.float32, device=dev)
+    pt = torch.empty((P,), dtype=torch.int32, device=dev)
+    valid = torch.empty((P,), dtype=torch.uint8, device=dev)
+    palm = PalmDesc((c_float * 3)(*[float(x) for x in np.asarray(palm_lo, np.float32)]),
+                    (c_float * 3)(*[float(x) for x in np.asarray(palm_hi, np.float32)]))
+    _check(_cf_place_static(byref(palm), byref(obj), P, c_uint64(int(seed)), int(pose_base), float(pen_margin),
+                            c_void_p(poses.data_ptr()), c_void_p(pt.data_ptr()), c_void_p(valid.data_ptr()),
+                            _stream(stream)))
+    return poses, pt, valid
+
+
+def append_contact(tuples, first, valid=None, stream=None):
+    """cf_append_contact: [P, T, k] tuples -> [P, T, k + 1] with first[i] in front (invalid -> -1)."""
+    import torch
+    P, T, k = (int(x) for x in tuples.shape)
+    if tuple(first.shape) != (P,) or (valid is not None and tuple(valid.shape) != (P,)):
+        raise ValueError("first / valid must be [P]")
+    out = torch.empty((P, T, k + 1), dtype=torch.int32, device=tuples.device)
+    _check(_cf_append(_dev(tuples, torch.int32, "tuples"), P, T, k, _dev(first, torch.int32, "first"),
+                      _dev(valid, torch.uint8, "valid") if valid is not None else None,
+                      _dev(out, torch.int32, "out"), _stream(stream)))
+    return out
+

@@ -1719,3 +1719,34 @@ extern "C" int cf_pool_usage(uint64_t usage[3], int reset_high) {
     }
     return CF_OK;
 }
+
+extern "C" int cf_place_static(const cf_palm_desc *palm, const cf_points *obj, int32_t n_poses, uint64_t seed,
+                               uint32_t pose_base, float pen_margin, float *d_poses, int32_t *d_static_pt,
+                               uint8_t *d_valid, cf_stream stream) {
+    if (!palm) return fail(CF_EINVAL, "palm is NULL");
+    int rc = check_points(obj);
+    if (rc) return rc;
+    if (n_poses < 0) return fail(CF_EINVAL, "n_poses < 0");
+    if (n_poses > 0 && obj->n < 1) return fail(CF_EINVAL, "the object has no points");
+    for (int c = 0; c < 3; ++c)
+        if (!(palm->lo[c] < palm->hi[c]) || !isfinite(palm->lo[c]) || !isfinite(palm->hi[c]))
+            return fail(CF_EINVAL, "palm box axis %d: [%g, %g] is not a finite interval", c, palm->lo[c], palm->hi[c]);
+    if (!(pen_margin >= 0.f) || !isfinite(pen_margin)) return fail(CF_EINVAL, "pen_margin must be finite and >= 0");
+    if (n_poses == 0) return CF_OK;
+    if (!d_poses || !d_static_pt || !d_valid) return fail(CF_EINVAL, "output pointer is NULL");
+    CF_TRY(launch_place_static(palm->lo, palm->hi, *obj, n_poses, (uint32_t)seed, (uint32_t)(seed >> 32), pose_base,
+                               pen_margin, d_poses, d_static_pt, d_valid, (cudaStream_t)stream),
+           "launch k_place_static");
+    return CF_OK;
+}
+
+extern "C" int cf_append_contact(const int32_t *d_tuples, int32_t n_poses, int32_t n_tuples, int32_t k,
+                                 const int32_t *d_first, const uint8_t *d_valid, int32_t *d_out, cf_stream stream) {
+    if (n_poses < 0 || n_tuples < 1 || k < 1 || k + 1 > CF_MAX_K)
+        return fail(CF_EINVAL, "n_poses >= 0, n_tuples >= 1 and 1 <= k < %d needed", CF_MAX_K);
+    if (n_poses == 0) return CF_OK;
+    if (!d_tuples || !d_first || !d_out) return fail(CF_EINVAL, "array pointer is NULL");
+    CF_TRY(launch_append_contact(d_tuples, n_poses, n_tuples, k, d_first, d_valid, d_out, (cudaStream_t)stream),
+           "launch k_append_contact");
+    return CF_OK;
+}

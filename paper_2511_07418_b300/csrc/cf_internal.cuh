@@ -269,6 +269,11 @@ struct PlaceArgs {
 constexpr int kChunkWords = 256;
 cudaError_t launch_chunk_counts(const uint32_t *table, long long words, unsigned long long *counts, cudaStream_t st);
 cudaError_t launch_place(const PlaceArgs &a, bool exhaustive, cudaStream_t st);
+cudaError_t launch_place_static(const float lo[3], const float hi[3], const cf_points &obj, int P, uint32_t seed_lo,
+                                uint32_t seed_hi, uint32_t pose_base, float pen_margin, float *poses, int32_t *static_pt,
+                                uint8_t *valid, cudaStream_t st);
+cudaError_t launch_append_contact(const int32_t *tuples, int P, int T, int k, const int32_t *first, const uint8_t *valid,
+                                  int32_t *out, cudaStream_t st);
 cudaError_t launch_concave(const cf_points &obj, const SdfGrid &sdf, float side, float tau, uint8_t *keep,
                            unsigned int *block_counts, float *out, int *n_out, cudaStream_t st);
 

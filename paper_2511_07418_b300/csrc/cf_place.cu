@@ -233,6 +233,95 @@ __global__ void __launch_bounds__(kConcaveThreads) k_compact(const cf_points obj
     out[5 * N + off] = __ldg(obj.nz + x);
 }
 
+// Static-link placement (Sec. 5.2): block per pose.  Thread 0 draws the pose in
+// FP64 (rounded to FP32 in shared memory and in the output); then every thread
+// tests its share of the object points against the palm box with the stored
+// FP32 pose, and the block stops at the first penetrating point it sees.
+constexpr int kStaticThreads = 256;
+struct StaticArgs {
+    float lo[3], hi[3];
+    cf_points obj;
+    int P;
+    uint32_t seed_lo, seed_hi, pose_base;
+    float pen_margin;
+    float *poses;
+    int32_t *static_pt;
+    uint8_t *valid;
+};
+
+__global__ void __launch_bounds__(kStaticThreads) k_place_static(const StaticArgs a) {
+    __shared__ float s_pose[12];
+    __shared__ int s_hit;
+    const int i = blockIdx.x;
+    if (threadIdx.x == 0) {
+        s_hit = 0;
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)i + a.pose_base, 0x57A7u, 0u, 0u),
+                                      make_uint2(a.seed_lo, a.seed_hi));
+        const int x = (int)(((unsigned long long)w.x * (unsigned long long)a.obj.n) >> 32);
+        const double c[3] = {(double)a.lo[0] + unit24(w.y) * ((double)a.hi[0] - (double)a.lo[0]),
+                             (double)a.lo[1] + unit24(w.z) * ((double)a.hi[1] - (double)a.lo[1]), (double)a.hi[2]};
+        double av[3] = {__ldg(a.obj.nx + x), __ldg(a.obj.ny + x), __ldg(a.obj.nz + x)};
+        const double an = sqrt(av[0] * av[0] + av[1] * av[1] + av[2] * av[2]);
+        for (int k = 0; k < 3; ++k) av[k] /= an;
+        // R_align: n_x -> -z
+        double v[3] = {-av[1], av[0], 0.0};  // n_x x (-z)
+        const double sv = sqrt(v[0] * v[0] + v[1] * v[1]);
+        const double cdot = -av[2];
+        double Ra[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+        if (sv > 1e-12) {
+            for (int k = 0; k < 3; ++k) v[k] /= sv;
+            rodrigues(v, atan2(sv, cdot), Ra);
+        } else if (cdot < 0.0) {  // n_x = +z: a half turn about n_x x e_x / |...| = (0, 1, 0)
+            const double k2[3] = {0.0, 1.0, 0.0};
+            rodrigues(k2, M_PI, Ra);
+        }
+        const double zk[3] = {0.0, 0.0, 1.0};
+        double Rs[9];
+        rodrigues(zk, 2.0 * M_PI * unit24(w.w), Rs);
+        double R[9];
+        for (int r = 0; r < 3; ++r)
+            for (int cc = 0; cc < 3; ++cc)
+                R[3 * r + cc] = Rs[3 * r] * Ra[cc] + Rs[3 * r + 1] * Ra[3 + cc] + Rs[3 * r + 2] * Ra[6 + cc];
+        const double px[3] = {__ldg(a.obj.px + x), __ldg(a.obj.py + x), __ldg(a.obj.pz + x)};
+        double t[3];
+        for (int r = 0; r < 3; ++r) t[r] = c[r] - (R[3 * r] * px[0] + R[3 * r + 1] * px[1] + R[3 * r + 2] * px[2]);
+        store_pose(s_pose, R, t);
+        store_pose(a.poses + 12 * (size_t)i, R, t);
+        a.static_pt[i] = x;
+    }
+    __syncthreads();
+    const float top = a.hi[2] - a.pen_margin;
+    for (int j0 = 0; j0 < a.obj.n; j0 += kStaticThreads) {
+        const int j = j0 + threadIdx.x;
+        bool pen = false;
+        if (j < a.obj.n) {
+            const float px = __ldg(a.obj.px + j), py = __ldg(a.obj.py + j), pz = __ldg(a.obj.pz + j);
+            const float qx = xf_row(s_pose[0], s_pose[1], s_pose[2], s_pose[3], px, py, pz);
+            const float qy = xf_row(s_pose[4], s_pose[5], s_pose[6], s_pose[7], px, py, pz);
+            const float qz = xf_row(s_pose[8], s_pose[9], s_pose[10], s_pose[11], px, py, pz);
+            pen = qx >= a.lo[0] && qx <= a.hi[0] && qy >= a.lo[1] && qy <= a.hi[1] && qz >= a.lo[2] && qz < top;
+        }
+        if (__any_sync(0xffffffffu, pen) && (threadIdx.x & 31) == 0) s_hit = 1;
+        __syncthreads();
+        if (s_hit) break;  // block-uniform
+    }
+    if (threadIdx.x == 0) a.valid[i] = (uint8_t)(s_hit == 0);
+}
+
+__global__ void k_append_contact(const int32_t *__restrict__ tuples, long long n, int T, int k,
+                                 const int32_t *__restrict__ first, const uint8_t *__restrict__ valid,
+                                 int32_t *__restrict__ out) {
+    const long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    const long long i = u / T;
+    const int32_t f0 = __ldg(first + i);
+    bool ok = f0 >= 0 && (!valid || __ldg(valid + i) != 0);
+    for (int d = 0; d < k; ++d) ok = ok && __ldg(tuples + u * k + d) >= 0;
+    int32_t *o = out + u * (k + 1);
+    o[0] = ok ? f0 : -1;
+    for (int d = 0; d < k; ++d) o[1 + d] = ok ? __ldg(tuples + u * k + d) : -1;
+}
+
 }  // namespace
 
 cudaError_t launch_chunk_counts(const uint32_t *table, long long words, unsigned long long *counts, cudaStream_t st) {
@@ -259,6 +348,33 @@ cudaError_t launch_concave(const cf_points &obj, const SdfGrid &sdf, float side,
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_compact<<<grid, kConcaveThreads, 0, st>>>(obj, keep, block_counts, out, n_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_place_static(const float lo[3], const float hi[3], const cf_points &obj, int P, uint32_t seed_lo,
+                                uint32_t seed_hi, uint32_t pose_base, float pen_margin, float *poses, int32_t *static_pt,
+                                uint8_t *valid, cudaStream_t st) {
+    if (P <= 0) return cudaSuccess;
+    StaticArgs a;
+    for (int c = 0; c < 3; ++c) { a.lo[c] = lo[c]; a.hi[c] = hi[c]; }
+    a.obj = obj;
+    a.P = P;
+    a.seed_lo = seed_lo;
+    a.seed_hi = seed_hi;
+    a.pose_base = pose_base;
+    a.pen_margin = pen_margin;
+    a.poses = poses;
+    a.static_pt = static_pt;
+    a.valid = valid;
+    k_place_static<<<P, kStaticThreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_append_contact(const int32_t *tuples, int P, int T, int k, const int32_t *first, const uint8_t *valid,
+                                  int32_t *out, cudaStream_t st) {
+    const long long n = (long long)P * T;
+    if (n <= 0) return cudaSuccess;
+    k_append_contact<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(tuples, n, T, k, first, valid, out);
     return cudaGetLastError();
 }
 

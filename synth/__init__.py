@@ -72,6 +72,8 @@ class Hand:
     surf_n: np.ndarray     # [F,M,3] float32
     surf_link: np.ndarray  # [F,M] int32
     grasp_centre: np.ndarray  # [3] float64: mean of finger bases (placement anchor)
+    palm_lo: np.ndarray = None  # [3] float32: the palm body, a box of the palm frame whose top face is z = 0
+    palm_hi: np.ndarray = None  # [3] float32
 
     @property
     def F(self) -> int:
@@ -146,7 +148,7 @@ def _rot_z(a: float) -> np.ndarray:
     return np.array([[c, -s, 0.0], [s, c, 0.0], [0.0, 0.0, 1.0]])
 
 
-def _pack_hand(name, bases_R, bases_t, axes, offsets, lo, hi, radii) -> Hand:
+def _pack_hand(name, bases_R, bases_t, axes, offsets, lo, hi, radii, palm_lo=None, palm_hi=None) -> Hand:
     F = len(bases_R)
     J = len(axes[0])
     base = np.zeros((F, 12), np.float64)
@@ -171,7 +173,9 @@ def _pack_hand(name, bases_R, bases_t, axes, offsets, lo, hi, radii) -> Hand:
                 lo=f32(lo), hi=f32(hi), radius=f32(radii),
                 surf_p=f32(sp), surf_n=f32(sn),
                 surf_link=np.ascontiguousarray(np.asarray(sl, np.int32)),
-                grasp_centre=g)
+                grasp_centre=g,
+                palm_lo=None if palm_lo is None else np.asarray(palm_lo, np.float32),
+                palm_hi=None if palm_hi is None else np.asarray(palm_hi, np.float32))
 
 
 def hand_three_finger(base_radius: float = 0.06) -> Hand:
@@ -194,7 +198,9 @@ def hand_three_finger(base_radius: float = 0.06) -> Hand:
         lo.append([0.0] * J)
         hi.append([1.6] * J)
         rad.append([0.008] * J)
-    return _pack_hand("three_finger_9dof", R, t, ax, off, lo, hi, rad)
+    # palm: a 15 mm slab under the bases, reaching the finger bases' circle
+    r = base_radius
+    return _pack_hand("three_finger_9dof", R, t, ax, off, lo, hi, rad, palm_lo=[-r, -r, -0.015], palm_hi=[r, r, 0.0])
 
 
 def hand_anthropomorphic(n_fingers: int) -> Hand:
@@ -222,7 +228,11 @@ def hand_anthropomorphic(n_fingers: int) -> Hand:
         lo.append([-0.35, 0.0, 0.0, 0.0])
         hi.append([0.35, 1.6, 1.6, 1.6])
         rad.append([0.0, 0.009, 0.009, 0.009])
-    return _pack_hand(f"anthropomorphic_{F}f_{F * J}dof", R, t, ax, off, lo, hi, rad)
+    # palm: a 20 mm slab from the thumb side (y = -0.05) to the finger bases (y = 0.045), 25 mm past the
+    # outer fingers
+    xr = ((nf - 1) / 2.0) * 0.045 + 0.025
+    return _pack_hand(f"anthropomorphic_{F}f_{F * J}dof", R, t, ax, off, lo, hi, rad,
+                      palm_lo=[-xr, -0.05, -0.02], palm_hi=[xr, 0.045, 0.0])
 
 
 def joint_samples(hand: Hand, S: int, seed: int) -> np.ndarray:

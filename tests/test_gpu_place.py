@@ -74,3 +74,46 @@ def test_concave_filter(cf, name, side):
     assert np.array_equal(out.cpu().numpy()[:, :nk], soa_h[:, gk.astype(bool)])  # kept points, original order
     if name == "hand20_tool":
         assert 0 < nk < soa_h.shape[1]  # the composite has concave seams and a torus hole
+
+
+@pytest.mark.parametrize("name", ["hand16_superquadric", "hand20_tool"])
+def test_static_link_placement(cf, name):
+    """Sec. 5.2 static links: poses against the palm and the penetration filter
+    match the FP64 oracle (poses within FP32 rounding of FP64, flags equal off
+    the oracle's band); the static contact then joins sampled finger tuples and
+    the (k+1)-contact closure margins match the oracle's LPs."""
+    w = synth.workload(name, P=1, S=4096)
+    soa_h = w.obj.soa()
+    soa = torch.from_numpy(soa_h).cuda()
+    P = 384
+    gp, gx, gv = cf.place_static(w.hand.palm_lo, w.hand.palm_hi, soa, P, seed=21, pose_base=5)
+    torch.cuda.synchronize()
+    op, ox, ov, amb = PL.place_static(w.hand.palm_lo, w.hand.palm_hi, soa_h, P, seed=21, pose_base=5)
+    assert np.array_equal(gx.cpu().numpy(), ox)
+    assert np.abs(gp.cpu().numpy() - op).max() <= 4e-6
+    g_v = gv.cpu().numpy()
+    assert np.array_equal(g_v[~amb], ov[~amb])
+    assert amb.mean() < 0.02
+    if name == "hand20_tool":
+        assert 0 < ov.sum() < P  # the composite's seams and hole make some placements penetrate
+    # the static contact in front of 2 sampled finger contacts: k = 3 tuples with the palm contact
+    field = cf.build(w.hand, w.inv_h, w.bins, torch.from_numpy(w.q).cuda())
+    masks, counts = cf.query_domains(field, soa, gp)
+    prm2 = cf.score_params(8, 2, w.mu, w.K, w.eps, w.obj.centroid, w.obj.rho, 4)
+    t2, f2 = cf.sample_tuples(soa, w.hand.F, masks, counts, prm2)
+    t3 = cf.append_contact(t2, gx, gv)
+    prm3 = cf.score_params(8, 3, w.mu, w.K, w.eps, w.obj.centroid, w.obj.rho, 4, tuples_given=True)
+    _, _, mar, acc = cf.score_tuples(soa, w.hand.F, None, None, prm3, tuples=t3)
+    torch.cuda.synchronize()
+    t3h, t2h = t3.cpu().numpy(), t2.cpu().numpy()
+    ok = (g_v.astype(bool)[:, None]) & np.all(t2h >= 0, axis=2)
+    assert np.array_equal(t3h[..., 0][ok], np.broadcast_to(gx.cpu().numpy()[:, None], ok.shape)[ok])
+    assert np.array_equal(t3h[..., 1:][ok], t2h[ok])
+    assert np.all(t3h[~ok] == -1)
+    om, oa, _ = oracle.score_tuples(soa_h, t3h, w.mu, w.K, w.obj.centroid, w.obj.rho, w.eps)
+    g = mar.cpu().numpy().astype(np.float64)
+    fin = np.isfinite(om)
+    assert np.array_equal(fin, np.isfinite(g))
+    assert np.all(np.abs(g[fin] - np.maximum(om[fin], 0)) <= 1e-4 * np.maximum(om[fin], w.eps))
+    assert fin.sum() > 0
+    assert cf.device_status() == 0
