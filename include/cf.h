@@ -249,16 +249,17 @@ int cf_score_tuples(const cf_points *obj, int32_t n_fingers, const uint32_t *d_m
  * failed or blocking allocation in the middle of a control loop.  Some run
  * where the allocator belongs to another framework.  Unlike cf_score_tuples,
  * this entry point promises to allocate nothing, whichever scoring kernel the
- * library runs.  Its scratch is a 4-byte tuple work counter (the current
- * scoring kernels take tuples from per-block shared-memory counters and do not
- * read it) in a library-wide device array of CF_NOALLOC_SCRATCH_BYTES bytes;
- * every GPU that loads libcf holds that array until the process exits.  A call
- * whose scratch need exceeds that size is rejected with CF_EINVAL.  The first call on each
- * device looks up the array's device address.  Make that first call before
- * any stream capture.  Every call shares the array and clears the counter
- * before its kernel runs.  Calls whose work overlaps on the GPU (different
- * streams, or different host threads on one device) race on the counter and
- * must be serialised by the caller.  The paper has no counterpart to this
+ * library runs.  Global scratch, where a scoring kernel needs any, comes from a
+ * library-wide device array of CF_NOALLOC_SCRATCH_BYTES bytes; every GPU that
+ * loads libcf holds that array until the process exits.  The current kernels
+ * need none (sampling stages each pose's masks in shared memory and the scorer
+ * hands out tuples from per-block shared-memory counters), so today no call is
+ * rejected for size and nothing is cleared; a call whose need exceeded the
+ * array would be rejected with CF_EINVAL.  The first call on each device looks
+ * up the array's device address.  Make that first call before any stream
+ * capture.  Every call shares the array: calls whose work overlaps on the GPU
+ * (different streams, or different host threads on one device) would race on
+ * it and must be serialised by the caller.  The paper has no counterpart to this
  * entry point.  Errors: as cf_score_tuples, except CF_ENOMEM. */
 #define CF_NOALLOC_SCRATCH_BYTES 256
 int cf_score_tuples_noalloc(const cf_points *obj, int32_t n_fingers, const uint32_t *d_masks,

@@ -500,8 +500,8 @@ def score_tuples_noalloc(soa, n_fingers: int, masks, counts, prm: ScoreParams, t
                          stream=None):
     """cf_score_tuples_noalloc: like score_tuples, but every output tensor is
     supplied by the caller and libcf allocates no device memory during the call
-    (its work counter lives in a library-wide device array; calls that overlap
-    on the GPU must be serialised by the caller)."""
+    (any global scratch comes from a library-wide device array; calls that
+    overlap on the GPU must be serialised by the caller)."""
     import torch
     P = int(tuples.shape[0])
     _check_score_shapes(soa, n_fingers, masks, counts, prm, P, tuples, fingers, margin, accept)

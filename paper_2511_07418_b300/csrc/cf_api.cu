@@ -928,17 +928,18 @@ extern "C" int cf_score_tuples_noalloc(const cf_points *obj, int32_t n_fingers, 
     int rc = fill_score_args(obj, n_fingers, d_masks, d_counts, n_poses, prm, d_tuples, d_fingers, d_margin,
                              d_accept, &a);
     if (rc) return rc;
-    const size_t need = sizeof(unsigned int);  // a tuple work counter (read by no current scoring kernel)
+    // global scratch of the scoring kernels: none today (sampling stages each pose's masks in shared
+    // memory; the lane scorer hands out tuples from per-block shared-memory counters), so nothing is
+    // cleared; a kernel that needs some takes it from the static array, within its size
+    const size_t need = 0;
     if (need > (size_t)CF_NOALLOC_SCRATCH_BYTES)
         return fail(CF_EINVAL, "scratch need %zu B exceeds the %d B no-allocation scratch", need,
                     CF_NOALLOC_SCRATCH_BYTES);
     unsigned int *scratch = nullptr;
     if ((rc = noalloc_scratch(&scratch))) return rc;
     if (n_poses == 0) return CF_OK;
-    cudaStream_t st = (cudaStream_t)stream;
-    CF_TRY(cudaMemsetAsync(scratch, 0, need, st), "clear no-allocation scratch");
     a.work = scratch;
-    CF_TRY(launch_score(a, st), "launch k_sample_tuples / k_score_tuples");
+    CF_TRY(launch_score(a, (cudaStream_t)stream), "launch k_sample_tuples / k_score_tuples");
     return CF_OK;
 }
 
