@@ -375,9 +375,11 @@ typedef struct cf_opt_params {
     float sigma;        /* standard deviation of each tangent-plane mutation component (m) */
     float zero_tol;     /* margins <= zero_tol count as 0 (a closed grasp): optimisation stops there */
     float min_gain;     /* a candidate replaces the best so far only when its margin is < (1 - min_gain) x best */
-    int32_t warm_start; /* 1: a candidate's LPs start from the current tuple's final basis when the moved contact
-                           is nonbasic there (Sec. 5.4 "A Free Lunch"); 0: every candidate starts from c' = 0.
-                           Margins agree either way (each LP is solved to its optimum). */
+    int32_t warm_start; /* 1: a candidate's LP_j starts from the current tuple's optimal LP_j basis, its moved
+                           contact's columns replaced by their new values (a column-replacement pivot where they
+                           are basic), when that basis stays feasible (Sec. 5.4 "A Free Lunch"); 0: from c' = 0
+                           or the previous LP's basis.  Margins agree either way (each LP is solved to its
+                           optimum). */
 } cf_opt_params;
 
 /* Improves every valid tuple of d_tuples [P][T][k] in place (prm->tuples_given
@@ -649,9 +651,10 @@ const char *cf_last_error(void);
 int cf_device_status(uint32_t *status);
 
 /* Cumulative device counters of the current device since the last reset:
- * [0] LP pivots performed, [1] LPs solved, [2] tuples scored, [3] candidate
- * tuples of cf_optimize_tuples whose LPs started from the current tuple's
- * basis (the warm start of Sec. 5.4) instead of c' = 0. */
+ * [0] LP pivots performed, [1] LPs solved, [2] tuples scored, [3] LPs of
+ * cf_optimize_tuples' candidates that started from the current tuple's
+ * optimal basis of the same LP, repaired for the moved contact (the warm
+ * start of Sec. 5.4). */
 int cf_device_counters(uint64_t counters[4], int reset);
 
 /* Device memory of the library's stream-ordered pool on the current device,

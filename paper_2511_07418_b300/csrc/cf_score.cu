@@ -261,20 +261,19 @@ __device__ __forceinline__ void lp_init_cold(BoxLp<NS> &s, const float (&w)[6], 
     s.beta = lane < kRows ? y_id<NS>(lane, kK) : -1;
 }
 
-// Warm start (Sec. 5.4, "A Free Lunch"): the tuple of state s with contact ci
-// replaced, whose new wrench column on this lane is w (lanes of contact ci).
-// Valid only when none of contact ci's columns is basic in s: then the basis
-// matrix and the basic values do not involve them, so s stays a feasible basis
-// and only contact ci's tableau columns change, to B^-1 (-w).  B^-1's column r
-// is the tableau column of y_r.  Returns false (s untouched) when a column of
-// contact ci is basic.
+// Warm start with repair (Sec. 5.4, "A Free Lunch"): state s is an optimal
+// basis of the current tuple; the trial tuple moves contact ci, whose new wrench
+// column on this lane is w (lanes of contact ci).  Contact ci's columns get
+// their new tableau B^-1 (-w); each of them that is basic is then swapped for
+// its own new version by a pivot on its row (a column-replacement pivot), so
+// the basis keeps its variables with contact ci's new columns; the basic values
+// are recomputed from the nonbasic bounds (c' = 0, y = -1 or +1).  Returns false
+// when a replacement pivot is too small (the new basis is near singular) or the
+// recomputed basis is infeasible; s is then unusable and the caller starts cold.
 template <int NS>
-__device__ __forceinline__ bool lp_replace_contact(BoxLp<NS> &s, const float (&w)[6], int ci, int k, int K, int lane,
-                                                   float *buf) {
+__device__ bool lp_warm_repair(BoxLp<NS> &s, const float (&w)[6], int ci, int k, int K, int lane, float *buf) {
     const int kK = k * K, c0 = ci * K, c1 = c0 + K;
-    const unsigned basic_ci = __ballot_sync(kFull, lane < kRows && s.beta >= c0 && s.beta < c1);
-    if (basic_ci & ((1u << kRows) - 1u)) return false;
-    // stage B^-1 = [T(y_0) .. T(y_5)] as buf[r' * 6 + r] (column r' = y_r')
+    // stage B^-1 = [T(y_0) .. T(y_5)] as buf[r' * 6 + r]
 #pragma unroll
     for (int q = 0; q < NS; ++q) {
         const int yr = NS == 1 ? lane - kK : (q == 1 ? lane : -1);
@@ -292,25 +291,82 @@ __device__ __forceinline__ bool lp_replace_contact(BoxLp<NS> &s, const float (&w
             for (int rr = 0; rr < kRows; ++rr) acc = __fmaf_rn(buf[rr * kRows + r], -w[rr], acc);
             s.T[0][r] = acc;
         }
-        s.st[0] = 1;  // nonbasic at its lower bound, c' = 0
     }
-    __syncwarp();  // buf is read before it is written again
-    return true;
+    __syncwarp();
+    // column-replacement pivots on the rows whose basic variable is a column of contact ci
+    unsigned rows = __ballot_sync(kFull, lane < kRows && s.beta >= c0 && s.beta < c1) & ((1u << kRows) - 1u);
+    bool ok = true;
+    while (rows) {
+        const int l = __ffs(rows) - 1;
+        rows &= rows - 1;
+        const int e = __shfl_sync(kFull, s.beta, l);  // the variable (lane e, slot 0)
+        if (lane == e) {
+#pragma unroll
+            for (int r = 0; r < kRows; ++r) buf[r] = s.T[0][r];
+        }
+        __syncwarp();
+        float col[kRows];
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) col[r] = buf[r];
+        __syncwarp();
+        float piv = col[0];
+#pragma unroll
+        for (int r = 1; r < kRows; ++r) piv = r == l ? col[r] : piv;
+        if (!(fabsf(piv) > 1e-4f)) { ok = false; break; }  // warp-uniform
+        const float inv = __frcp_rn(piv);
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+            float tl = s.T[q][0];
+#pragma unroll
+            for (int r = 1; r < kRows; ++r) tl = r == l ? s.T[q][r] : tl;
+            const float pa = __fmul_rn(tl, inv);
+#pragma unroll
+            for (int r = 0; r < kRows; ++r) s.T[q][r] = r == l ? pa : __fmaf_rn(-col[r], pa, s.T[q][r]);
+        }
+    }
+    if (!ok) return false;
+    // basic values: B x_B = -N x_N, x_N = -1 / +1 for nonbasic y at the lower / upper bound, 0 for c'
+    float contrib[kRows];
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) contrib[r] = 0.f;
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+        const int yr = NS == 1 ? lane - kK : (q == 1 ? lane : -1);
+        if (yr >= 0 && yr < kRows && s.st[q] != 0) {
+            const float val = s.st[q] == 2 ? 1.f : -1.f;
+#pragma unroll
+            for (int r = 0; r < kRows; ++r) contrib[r] = __fmaf_rn(-s.T[q][r], val, contrib[r]);
+        }
+    }
+    float vr = 0.f;
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+        float x = contrib[r];
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+        if (lane == r) vr = x;
+    }
+    bool feas = true;
+    if (lane < kRows) {
+        const bool bx = s.beta < kK;
+        if (bx) { feas = vr >= -1e-6f; vr = fmaxf(vr, 0.f); }
+        else { feas = vr >= -1.f - 1e-6f && vr <= 1.f + 1e-6f; vr = fminf(fmaxf(vr, -1.f), 1.f); }
+        s.v = vr;
+    }
+    return __all_sync(kFull, feas);
 }
 
-// Closure margin min_j LP_j from the feasible state s (each LP_j starts from
-// the basis the previous one ended in).  Stops at the first unbounded s_j
-// (margin 0).  s ends in the last LP's final basis.
+// LP_j from the feasible state s: returns s_j (+inf when unbounded, i.e.
+// LP_j = 0); s ends in its final basis.
 template <int NS>
-__device__ float lp_solve_margin(BoxLp<NS> &s, int k, int K, int lane, float *buf, unsigned long long &n_piv,
-                                 unsigned long long &n_lp, unsigned &flags) {
+__device__ float lp_solve_one(BoxLp<NS> &s, int j, int k, int K, int lane, float *buf, unsigned long long &n_piv,
+                              unsigned long long &n_lp, unsigned &flags) {
     const int kK = k * K;
     const unsigned kinf = fkey(INFINITY);
     const unsigned kzero = fkey(0.f);
     unsigned npv = 0;
-    float best_s = 0.f;
     bool unbounded = false;
-    for (int j = 0; j < k && !unbounded; ++j) {
+    {
         const int c0 = j * K, c1 = c0 + K;  // contact j's columns
         // reduced costs of the objective sum_m c'_jm at the current basis
         const unsigned inj =
@@ -451,18 +507,32 @@ __device__ float lp_solve_margin(BoxLp<NS> &s, int k, int K, int lane, float *bu
             __syncwarp();  // every lane has read buf before it is written again
         }
         if (it == kMaxPivots) flags |= CF_DEV_LP_PIVOT_CAP;
-        ++n_lp;
-        if (!unbounded) {  // s_j = the sum of contact j's basic values (nonbasic c' sit at 0)
-            float part = (lane < kRows && s.beta >= c0 && s.beta < c1) ? s.v : 0.f;
-            part += __shfl_xor_sync(kFull, part, 4);
-            part += __shfl_xor_sync(kFull, part, 2);
-            part += __shfl_xor_sync(kFull, part, 1);
-            best_s = fmaxf(best_s, __shfl_sync(kFull, part, 0));
-            if (best_s >= 1.f / kZeroExit) break;
-        }
     }
+    ++n_lp;
     n_piv += npv;
-    if (unbounded) return 0.f;
+    if (unbounded) return INFINITY;
+    // s_j = the sum of contact j's basic values (nonbasic c' sit at 0)
+    const int c0 = j * K, c1 = c0 + K;
+    float part = (lane < kRows && s.beta >= c0 && s.beta < c1) ? s.v : 0.f;
+    part += __shfl_xor_sync(kFull, part, 4);
+    part += __shfl_xor_sync(kFull, part, 2);
+    part += __shfl_xor_sync(kFull, part, 1);
+    return __shfl_sync(kFull, part, 0);
+}
+
+// Closure margin min_j LP_j from the feasible state s (each LP_j starts from
+// the basis the previous one ended in).  Stops at the first unbounded s_j
+// (margin 0).  s ends in the last LP's final basis.
+template <int NS>
+__device__ float lp_solve_margin(BoxLp<NS> &s, int k, int K, int lane, float *buf, unsigned long long &n_piv,
+                                 unsigned long long &n_lp, unsigned &flags) {
+    float best_s = 0.f;
+    for (int j = 0; j < k; ++j) {
+        const float sj = lp_solve_one<NS>(s, j, k, K, lane, buf, n_piv, n_lp, flags);
+        if (!(sj < INFINITY)) return 0.f;
+        best_s = fmaxf(best_s, sj);
+        if (best_s >= 1.f / kZeroExit) break;
+    }
     return best_s > 0.f ? __fdiv_rn(1.f, best_s) : INFINITY;
 }
 
@@ -478,6 +548,34 @@ __device__ float closure_margin(const float (&w)[6], int k, int K, int lane, flo
 // ---------------------------------------------------------------------------
 // Alg. 2: blockwise zeroth-order contact optimisation
 // ---------------------------------------------------------------------------
+// A warp's simplex state in shared memory: word w of lane l at p[w * 32 + l]
+// (conflict-free), kStateWords(NS) words per lane.
+template <int NS>
+__host__ __device__ constexpr int state_words() { return NS * (kRows + 2) + 2; }
+
+template <int NS>
+__device__ __forceinline__ void state_store(float *p, int lane, const BoxLp<NS> &s) {
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+#pragma unroll
+        for (int r = 0; r <= kRows; ++r) p[(q * (kRows + 2) + r) * 32 + lane] = s.T[q][r];
+        p[(q * (kRows + 2) + kRows + 1) * 32 + lane] = __int_as_float(s.st[q]);
+    }
+    p[(NS * (kRows + 2)) * 32 + lane] = s.v;
+    p[(NS * (kRows + 2) + 1) * 32 + lane] = __int_as_float(s.beta);
+}
+
+template <int NS>
+__device__ __forceinline__ void state_load(const float *p, int lane, BoxLp<NS> &s) {
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+#pragma unroll
+        for (int r = 0; r <= kRows; ++r) s.T[q][r] = p[(q * (kRows + 2) + r) * 32 + lane];
+        s.st[q] = __float_as_int(p[(q * (kRows + 2) + kRows + 1) * 32 + lane]);
+    }
+    s.v = p[(NS * (kRows + 2)) * 32 + lane];
+    s.beta = __float_as_int(p[(NS * (kRows + 2) + 1) * 32 + lane]);
+}
 constexpr int kOptThreads = 128;
 constexpr int kOptWarps = kOptThreads / 32;
 
@@ -510,14 +608,20 @@ struct OptArgs {
 // object point whose mask bit is set; all lanes scan the mask words, then one
 // warp reduction per candidate), then the candidates in order replace the best
 // so far when their margin is lower by more than the relative min_gain (margins
-// <= zero_tol count as 0), so the margin never increases.  A candidate's LPs
-// start from the current tuple's final basis whenever the moved contact's
-// columns are nonbasic there (the warm start of Sec. 5.4, "A Free Lunch"),
-// else from c' = 0.
+// <= zero_tol count as 0), so the margin never increases.  The free lunch of
+// Sec. 5.4: the current tuple's optimal basis of each LP_j stays in shared
+// memory, and a candidate's LP_j starts from it, repaired for the moved
+// contact (lp_warm_repair), whenever the repaired basis is feasible; else from
+// the candidate's previous LP's basis, or c' = 0.  Three state buffers per
+// warp: the current tuple's, the best candidate's so far, the trial's.
 template <int NI, int NS>
 __global__ void __launch_bounds__(kOptThreads) k_optimize_tuples(const ScoreArgs a, const OptArgs o, unsigned total) {
     __shared__ __align__(16) float s_buf[kOptWarps][kRows * kRows];  // entering column; B^-1 for warm starts
     __shared__ float s_cand[kOptWarps][NI][3];
+    extern __shared__ float s_states[];  // [warp][3 buffers][k][state_words][32]
+    constexpr int SW = state_words<NS>();
+    float *const states = s_states + (size_t)(threadIdx.x >> 5) * 3 * a.k * SW * 32;
+    auto slot = [&](int b, int j) { return states + ((size_t)b * a.k + j) * SW * 32; };
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int k = a.k, K = a.K, kK = k * K, F = a.F, W = a.W;
     const bool colA = lane < kK;
@@ -543,13 +647,24 @@ __global__ void __launch_bounds__(kOptThreads) k_optimize_tuples(const ScoreArgs
         }
         float J = INFINITY;
         if (valid) {
-            // the current tuple's final simplex state: the warm start of its candidates (Sec. 5.4)
-            BoxLp<NS> cur, win;
+            // the current tuple's optimal basis of each LP_j: the warm starts of its candidates (Sec. 5.4)
+            int b_cur = 0, b_best = 1, b_trial = 2, n_cur = 0, n_best = 0;
             {
                 float wv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                 if (colA) wrench_column(a, ci == 0 ? id[0] : ci == 1 ? id[1] : ci == 2 ? id[2] : id[3], ec, es, wv);
-                lp_init_cold<NS>(cur, wv, kK, lane);
-                J = lp_solve_margin<NS>(cur, k, K, lane, buf, n_piv, n_lp, flags);
+                BoxLp<NS> st;
+                lp_init_cold<NS>(st, wv, kK, lane);
+                float bs = 0.f;
+                bool zero = false;
+                for (int j = 0; j < k; ++j) {
+                    const float sj = lp_solve_one<NS>(st, j, k, K, lane, buf, n_piv, n_lp, flags);
+                    state_store<NS>(slot(b_cur, j), lane, st);
+                    n_cur = j + 1;
+                    if (!(sj < INFINITY)) { zero = true; break; }
+                    bs = fmaxf(bs, sj);
+                    if (bs >= 1.f / kZeroExit) break;
+                }
+                J = zero ? 0.f : (bs > 0.f ? __fdiv_rn(1.f, bs) : INFINITY);
             }
             float Jc = J <= o.zero_tol ? 0.f : J;
             const uint32_t pid = (uint32_t)pose + a.pose_base;
@@ -557,9 +672,8 @@ __global__ void __launch_bounds__(kOptThreads) k_optimize_tuples(const ScoreArgs
                 for (int i = 0; i < k && Jc > 0.f; ++i) {
                     const int x0 = i == 0 ? id[0] : i == 1 ? id[1] : i == 2 ? id[2] : id[3];
                     const int fi = i == 0 ? fg[0] : i == 1 ? fg[1] : i == 2 ? fg[2] : fg[3];
-                    // tangent basis of nu = -n at the current point (Duff et al. 2017); this
-                    // and the mutated points use explicitly rounded FP32 operations, so the
-                    // projection below (an index decision) is reproducible operation by operation
+                    // tangent basis of nu = -n at the current point (Duff et al. 2017) and the mutated
+                    // points in explicitly rounded FP32 operations (no contraction left to the compiler)
                     const float px = __ldg(a.px + x0), py = __ldg(a.py + x0), pz = __ldg(a.pz + x0);
                     const float vx = -__ldg(a.nx + x0), vy = -__ldg(a.ny + x0), vz = -__ldg(a.nz + x0);
                     const float sgn = copysignf(1.f, vz);
@@ -631,25 +745,46 @@ __global__ void __launch_bounds__(kOptThreads) k_optimize_tuples(const ScoreArgs
                         if (colA)
                             wrench_column(a, ci == i ? xc : (ci == 0 ? id[0] : ci == 1 ? id[1] : ci == 2 ? id[2] : id[3]),
                                           ec, es, wt);
-                        // warm start from the current tuple's final basis when contact i is nonbasic there,
-                        // else from c' = 0
-                        BoxLp<NS> st = cur;
-                        if (o.warm_start && lp_replace_contact<NS>(st, wt, i, k, K, lane, buf)) ++n_warm;
-                        else lp_init_cold<NS>(st, wt, kK, lane);
-                        const float Jt = lp_solve_margin<NS>(st, k, K, lane, buf, n_piv, n_lp, flags);
+                        // each LP_j from the current tuple's optimal LP_j basis repaired for the moved contact
+                        // (warm), else from this candidate's previous LP's basis, else from c' = 0
+                        float bs = 0.f;
+                        bool zero = false;
+                        int nt = 0;
+                        BoxLp<NS> chain;
+                        for (int j = 0; j < k; ++j) {
+                            BoxLp<NS> st;
+                            bool warm = false;
+                            if (o.warm_start && j < n_cur) {
+                                state_load<NS>(slot(b_cur, j), lane, st);
+                                warm = lp_warm_repair<NS>(st, wt, i, k, K, lane, buf);
+                            }
+                            if (warm) ++n_warm;
+                            else if (j > 0) st = chain;
+                            else lp_init_cold<NS>(st, wt, kK, lane);
+                            const float sj = lp_solve_one<NS>(st, j, k, K, lane, buf, n_piv, n_lp, flags);
+                            state_store<NS>(slot(b_trial, j), lane, st);
+                            nt = j + 1;
+                            chain = st;
+                            if (!(sj < INFINITY)) { zero = true; break; }
+                            bs = fmaxf(bs, sj);
+                            if (bs >= 1.f / kZeroExit) break;
+                        }
+                        const float Jt = zero ? 0.f : (bs > 0.f ? __fdiv_rn(1.f, bs) : INFINITY);
                         const float Jtc = Jt <= o.zero_tol ? 0.f : Jt;
                         if (Jtc < (1.f - o.min_gain) * best) {
                             best = Jtc;
                             bestJ = Jt;
                             bestc = xc;
-                            win = st;
+                            const int t = b_best; b_best = b_trial; b_trial = t;  // the trial's states: the best's
+                            n_best = nt;
                         }
                     }
                     if (bestc >= 0) {
                         if (i == 0) id[0] = bestc; else if (i == 1) id[1] = bestc; else if (i == 2) id[2] = bestc; else id[3] = bestc;
                         Jc = best;
                         J = bestJ;
-                        cur = win;
+                        const int t = b_cur; b_cur = b_best; b_best = t;  // the winner's states: the current tuple's
+                        n_cur = n_best;
                     }
                 }
             }
@@ -1172,11 +1307,20 @@ cudaError_t launch_optimize(const ScoreArgs &a, int n_outer, int n_inner, float 
     const long long want = (total + kOptWarps - 1) / kOptWarps;
     const int grid = (int)std::min<long long>((long long)sms * 16, want);
     const bool one = lp_slots(a.k, a.K) == 1;
+    const size_t smem1 = (size_t)kOptWarps * 3 * a.k * state_words<1>() * 32 * sizeof(float);
+    const size_t smem2 = (size_t)kOptWarps * 3 * a.k * state_words<2>() * 32 * sizeof(float);
     switch (n_inner) {
 #define CF_OPT(NI)                                                                                        \
     case NI:                                                                                              \
-        if (one) k_optimize_tuples<NI, 1><<<grid, kOptThreads, 0, st>>>(a, o, (unsigned)total);           \
-        else k_optimize_tuples<NI, 2><<<grid, kOptThreads, 0, st>>>(a, o, (unsigned)total);               \
+        if (one) {                                                                                        \
+            if ((err = cudaFuncSetAttribute(k_optimize_tuples<NI, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                            (int)smem1)) != cudaSuccess) return err;                      \
+            k_optimize_tuples<NI, 1><<<grid, kOptThreads, smem1, st>>>(a, o, (unsigned)total);            \
+        } else {                                                                                          \
+            if ((err = cudaFuncSetAttribute(k_optimize_tuples<NI, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                            (int)smem2)) != cudaSuccess) return err;                      \
+            k_optimize_tuples<NI, 2><<<grid, kOptThreads, smem2, st>>>(a, o, (unsigned)total);            \
+        }                                                                                                 \
         break;
         CF_OPT(4) CF_OPT(8) CF_OPT(16)
 #undef CF_OPT
