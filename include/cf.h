@@ -319,6 +319,13 @@ int cf_ik_dls(const cf_field *field, const cf_points *obj, const float *d_poses,
 
 typedef struct cf_sdf cf_sdf;
 
+/* The grid box that covers host points h_soa [6][n] (px, py, pz rows first)
+ * with a margin: lo = min - margin (FP64, rounded to FP32), dims = ceil((max +
+ * margin - lo) / h) + 1 per axis (h rounded to FP32 first).  Host only, no
+ * device work.  Errors: CF_EINVAL (n < 1, h <= 0, margin < 0, non-finite
+ * point, a box beyond 2^20 nodes per axis). */
+int cf_sdf_box(const float *h_soa, int32_t n, float h, float margin, float lo[3], int32_t dims[3]);
+
 /* Signed distance of the object's oriented point set on the grid
  * lo + (i, j, k) h, i < dims[0] ... (x fastest): distance to the nearest point
  * (first on ties), negative when (x - p) . n of that point is < 0.  Brute force

@@ -206,6 +206,7 @@ _cf_last_error = _sig("cf_last_error", [], c_char_p)
 _cf_device_status = _sig("cf_device_status", [POINTER(c_uint32)])
 _cf_device_counters = _sig("cf_device_counters", [POINTER(c_uint64), c_int])
 _cf_pool_usage = _sig("cf_pool_usage", [POINTER(c_uint64), c_int])
+_cf_sdf_box = _sig("cf_sdf_box", [POINTER(c_float), c_int32, c_float, c_float, POINTER(c_float), POINTER(c_int32)])
 _cf_merge = _sig("cf_merge_domains", [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p])
 _cf_place_static = _sig("cf_place_static", [POINTER(PalmDesc), POINTER(Points), c_int32, c_uint64, c_uint32, c_float,
                                             c_void_p, c_void_p, c_void_p, c_void_p])
@@ -213,7 +214,7 @@ _cf_append = _sig("cf_append_contact", [c_void_p, c_int32, c_int32, c_int32, c_v
 
 EXPORTED = ["cf_build", "cf_field_get_info", "cf_field_copy_table", "cf_field_destroy", "cf_field_save",
             "cf_field_load", "cf_query_domains", "cf_score_tuples", "cf_plan_create", "cf_plan_run_host",
-            "cf_plan_destroy", "cf_last_error", "cf_device_status", "cf_device_counters", "cf_pool_usage", "cf_merge_domains", "cf_place_static", "cf_append_contact", "cf_score_tuples_noalloc",
+            "cf_plan_destroy", "cf_last_error", "cf_device_status", "cf_device_counters", "cf_pool_usage", "cf_sdf_box", "cf_merge_domains", "cf_place_static", "cf_append_contact", "cf_score_tuples_noalloc",
             "cf_sample_tuples", "cf_batch_create", "cf_batch_run", "cf_batch_launches", "cf_batch_destroy",
             "cf_engine_create", "cf_engine_submit", "cf_engine_poll", "cf_engine_result_free", "cf_engine_get_stats",
             "cf_engine_drain", "cf_engine_destroy", "cf_field_rep_slots", "cf_field_copy_rep", "cf_ik_dls",
@@ -740,12 +741,14 @@ def ik_dls(field: Field, soa, poses, T: int, k: int, tuples, fingers, accept, pr
 
 
 def sdf_box(soa_host, h: float, margin: float):
-    """Grid box of cf_sdf_build for host points [6, N]: lo = min - margin, dims to cover max + margin."""
-    p = np.asarray(soa_host, np.float64)[:3]
-    lo = (p.min(axis=1) - margin).astype(np.float32)
-    hi = p.max(axis=1) + margin
-    dims = (np.ceil((hi - lo.astype(np.float64)) / float(np.float32(h))).astype(np.int64) + 1).astype(np.int32)
-    return lo, float(np.float32(h)), dims
+    """cf_sdf_box: the grid box of cf_sdf_build for host points [6, N] -> (lo [3] f32, h, dims [3] int32)."""
+    pts = _np(soa_host, np.float32)
+    if pts.ndim != 2 or pts.shape[0] != 6:
+        raise ValueError("soa_host must be [6, N]")
+    lo = (c_float * 3)()
+    dims = (c_int32 * 3)()
+    _check(_cf_sdf_box(_fp(pts), int(pts.shape[1]), float(np.float32(h)), float(np.float32(margin)), lo, dims))
+    return np.array(lo[:], np.float32), float(np.float32(h)), np.array(dims[:], np.int32)
 
 
 class Sdf:

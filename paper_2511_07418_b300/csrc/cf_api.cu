@@ -1751,3 +1751,26 @@ extern "C" int cf_append_contact(const int32_t *d_tuples, int32_t n_poses, int32
            "launch k_append_contact");
     return CF_OK;
 }
+
+extern "C" int cf_sdf_box(const float *h_soa, int32_t n, float h, float margin, float lo[3], int32_t dims[3]) {
+    if (!h_soa || !lo || !dims) return fail(CF_EINVAL, "NULL argument");
+    if (n < 1) return fail(CF_EINVAL, "n < 1");
+    if (!(h > 0.f) || !isfinite(h)) return fail(CF_EINVAL, "h must be finite and > 0");
+    if (!(margin >= 0.f) || !isfinite(margin)) return fail(CF_EINVAL, "margin must be finite and >= 0");
+    for (int c = 0; c < 3; ++c) {
+        double mn = INFINITY, mx = -INFINITY;
+        for (int i = 0; i < n; ++i) {
+            const double v = h_soa[(size_t)c * n + i];
+            if (!isfinite(v)) return fail(CF_EINVAL, "point %d is not finite", i);
+            mn = v < mn ? v : mn;
+            mx = v > mx ? v : mx;
+        }
+        const float l = (float)(mn - (double)margin);
+        const double cells = ceil((mx + (double)margin - (double)l) / (double)h) + 1.0;
+        if (cells > (double)(1 << 20)) return fail(CF_EINVAL, "axis %d needs %.0f nodes (> 2^20)", c, cells);
+        lo[c] = l;
+        dims[c] = (int32_t)cells;
+    }
+    return CF_OK;
+}
+

@@ -188,3 +188,22 @@ def test_scoring_rejects_tuple_counts_beyond_32_bits():
         rc = fn(byref(pts), 4, None, None, 1 << 16, byref(prm), p, None, p, p, None)
         assert rc == cf.CF_EINVAL
         assert "2^32" in cf._cf_last_error().decode()
+
+
+def test_sdf_box_covers_the_points_with_the_margin():
+    """cf_sdf_box (host only): lo = min - margin, dims nodes spaced h reach past max + margin;
+    bad arguments are refused."""
+    import paper_2511_07418_b300 as cf
+    rng = np.random.default_rng(4)
+    soa = np.ascontiguousarray(rng.normal(scale=0.05, size=(6, 1000)).astype(np.float32))
+    lo, h, dims = cf.sdf_box(soa, 0.004, 0.02)
+    p = soa[:3].astype(np.float64)
+    assert np.allclose(lo, p.min(axis=1) - 0.02, atol=1e-7)
+    top = lo.astype(np.float64) + (dims - 1) * np.float32(0.004)
+    assert np.all(top >= p.max(axis=1) + 0.02 - 1e-7) and np.all(top - np.float32(0.004) < p.max(axis=1) + 0.02)
+    with pytest.raises(cf.CfError):
+        cf.sdf_box(soa, 0.0, 0.02)
+    bad = soa.copy()
+    bad[1, 7] = np.nan
+    with pytest.raises(cf.CfError, match="not finite"):
+        cf.sdf_box(bad, 0.004, 0.02)
