@@ -11,9 +11,11 @@
 //     LP_j = min t  s.t.  -t <= (sum_im c_im w_im)_r <= t,  sum_m c_jm = 1,  c >= 0
 // and the margin is min_j LP_j.
 //
-// k_sample_tuples: one block per pose stages the F mask rows in shared memory
-// with popcount prefixes per 8-word group; one thread per tuple draws its
-// fingers and points (Philox4x32-10) and writes them out.
+// k_sample_tuples: one block per pose builds popcount prefixes per 8-word
+// group of its F mask rows in shared memory (reading the rows once, coalesced);
+// one thread per tuple draws its fingers and points (Philox4x32-10), finds each
+// point's group by binary search and its bit in the group's words, and writes
+// them out.
 //
 // k_score_lanes: each lane scores its own tuples, the k LPs of a tuple in the
 // scaled bounded-variable form below, solved by a revised simplex whose state
@@ -55,11 +57,15 @@ __device__ __forceinline__ int select_in_word(uint32_t v, uint32_t r) {
     return pos;
 }
 
-// r-th set bit (ascending) of a staged mask row, -1 if the row has <= r bits.
-// words per prefix group of a staged mask row
+// words per prefix group of a mask row
 constexpr int kGroupWords = 8;
 
-__device__ __forceinline__ int select_in_row(const uint32_t *row, const uint32_t *gp, int W, int G, uint32_t r) {
+// r-th set bit (ascending) of the mask row `row` (global memory), -1 if the row
+// has <= r bits.  gp = exclusive prefix of the row's group popcounts (shared
+// memory, G + 1 entries): a binary search finds the group, whose <= 8 words are
+// loaded together and scanned.
+__device__ __forceinline__ int select_in_row(const uint32_t *__restrict__ row, const uint32_t *gp, int W, int G,
+                                             uint32_t r) {
     if (r >= gp[G]) return -1;
     int lo = 0, hi = G - 1;  // largest g with gp[g] <= r
     while (lo < hi) {
@@ -67,14 +73,18 @@ __device__ __forceinline__ int select_in_row(const uint32_t *row, const uint32_t
         if (gp[mid] <= r) lo = mid; else hi = mid - 1;
     }
     uint32_t rr = r - gp[lo];
-    const int wend = min(kGroupWords * lo + kGroupWords, W);
-    for (int w = kGroupWords * lo; w < wend; ++w) {
-        const uint32_t v = row[w];
-        const uint32_t c = __popc(v);
-        if (rr < c) return 32 * w + select_in_word(v, rr);
-        rr -= c;
+    const int wb = kGroupWords * lo, n = min(kGroupWords, W - wb);
+    uint32_t v[kGroupWords];
+#pragma unroll
+    for (int q = 0; q < kGroupWords; ++q) v[q] = q < n ? __ldg(row + wb + q) : 0u;
+    int out = -1;
+#pragma unroll
+    for (int q = 0; q < kGroupWords; ++q) {
+        const uint32_t c = __popc(v[q]);
+        if (out < 0 && rr < c) out = 32 * (wb + q) + select_in_word(v[q], rr);
+        if (out < 0) rr -= c;
     }
-    return -1;
+    return out;
 }
 
 __device__ __forceinline__ uint32_t draw_word(const uint4 &a, const uint4 &b, int d) {
@@ -114,34 +124,31 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_tuples(const ScoreArg
     const ScoreArgs &a = MULTI ? s_args : a1;
     const int F = a.F, W = a.W, T = a.T, k = a.k;
     const int G = (W + kGroupWords - 1) / kGroupWords;
-    uint32_t *s_mask = s_dyn;           // [F][W]
-    uint32_t *s_gpre = s_mask + F * W;  // [F][G + 1]
+    uint32_t *s_gpre = s_dyn;  // [F][G + 1]
     const int i = MULTI ? s_i : (int)blockIdx.x;
     if (threadIdx.x < F) s_cnt[threadIdx.x] = a.counts[(size_t)i * F + threadIdx.x];
     const uint32_t *src = a.masks + (size_t)i * F * W;
-    // stage the pose's F x W mask words: asynchronous 16-byte copies when the row block is 16-byte
-    // aligned (every load in flight before the first wait), word loads otherwise
-    const int FW = F * W;
-    const unsigned s_base = (unsigned)__cvta_generic_to_shared(s_mask);
-    if ((FW & 3) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0 && (s_base & 15u) == 0) {
-        for (int e = 4 * threadIdx.x; e < FW; e += 4 * blockDim.x)
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s_base + 4u * (unsigned)e), "l"(src + e)
-                         : "memory");
-        asm volatile("cp.async.wait_all;" ::: "memory");
-    } else {
-        for (int e = threadIdx.x; e < FW; e += blockDim.x) s_mask[e] = src[e];
-    }
-    __syncthreads();
-    // group sums: a warp popcounts 32 consecutive words of a row (one per lane, no bank conflicts)
-    // and adds them in groups of kGroupWords lanes
+    // group sums straight from the masks (no staging): a warp takes 128 consecutive words of a row, four
+    // independent coalesced loads per lane, and adds the popcounts in groups of kGroupWords lanes
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    const int CW = (W + 31) / 32;
+    const int CW = (W + 127) / 128;
     for (int ch = warp; ch < F * CW; ch += nwarps) {
-        const int f = ch / CW, w = (ch % CW) * 32 + lane;
-        uint32_t c = w < W ? __popc(s_mask[f * W + w]) : 0u;
+        const int f = ch / CW, w0 = (ch % CW) * 128;
+        const uint32_t *row = src + (size_t)f * W;
+        uint32_t v[4];
 #pragma unroll
-        for (int o = 1; o < kGroupWords; o <<= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-        if (lane % kGroupWords == 0 && w < W) s_gpre[f * (G + 1) + 1 + w / kGroupWords] = c;
+        for (int q = 0; q < 4; ++q) {
+            const int w = w0 + 32 * q + lane;
+            v[q] = w < W ? __ldg(row + w) : 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int w = w0 + 32 * q + lane;
+            uint32_t c = __popc(v[q]);
+#pragma unroll
+            for (int o = 1; o < kGroupWords; o <<= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+            if (lane % kGroupWords == 0 && w < W) s_gpre[f * (G + 1) + 1 + w / kGroupWords] = c;
+        }
     }
     __syncthreads();
     // exclusive prefix of the group sums per row: one warp per row, 32 groups per step
@@ -190,7 +197,7 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_tuples(const ScoreArg
         for (int d = 0; d < k; ++d) {
             const int f = (pk >> (4 * d)) & 15u;
             const uint32_t r = __umulhi(draw_word(u0, u1, k + d), s_cnt[f]);
-            gt[d] = select_in_row(s_mask + f * W, s_gpre + f * (G + 1), W, G, r);
+            gt[d] = select_in_row(src + (size_t)f * W, s_gpre + f * (G + 1), W, G, r);
             if (gf) gf[d] = (uint8_t)f;
         }
     }
@@ -1243,7 +1250,7 @@ size_t score_smem_bytes(int F, int W, int T, int k, bool sampling) {
     (void)T;
     (void)k;
     const int G = (W + kGroupWords - 1) / kGroupWords;
-    return sampling ? sizeof(uint32_t) * ((size_t)F * W + (size_t)F * (G + 1)) : 0;
+    return sampling ? sizeof(uint32_t) * (size_t)F * (G + 1) : 0;  // the group prefixes
 }
 
 cudaError_t launch_sample(const ScoreArgs &a, cudaStream_t st) {
