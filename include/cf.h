@@ -57,7 +57,7 @@ enum {
     CF_EINVAL = 1,   /* bad argument / shape */
     CF_ENOMEM = 2,   /* device or host allocation failed */
     CF_ECUDA = 3,    /* a CUDA runtime call failed (message has the CUDA error) */
-    CF_ETIMEOUT = 4, /* a bounded device wait ran out */
+    CF_ETIMEOUT = 4, /* a bounded wait ran out (cf_engine_drain's host-side limit; no kernel waits) */
     CF_EBUSY = 5,    /* resource in use */
     CF_EDEVICE = 6,  /* device status word reported a kernel-side condition */
     CF_EIO = 7       /* file read / write failed */

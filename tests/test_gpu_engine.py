@@ -121,3 +121,21 @@ def test_first_chunk_equals_plain_calls(setup):
     assert np.array_equal(r["pose"][sel], pose_idx)
     assert np.array_equal(r["tuples"][sel], t.cpu().numpy()[acc])
     assert np.array_equal(r["margin"][sel], mar.cpu().numpy()[acc])
+
+
+def test_drain_is_a_bounded_wait(setup):
+    """The engine's waits are on the host and bounded: a drain whose limit runs
+    out while requests remain returns CF_ETIMEOUT (the engine keeps working), and
+    a later drain completes every request.  No kernel waits on another block or
+    on the host, so nothing on the GPU can hang."""
+    cf, ws, fields, reqs = setup
+    eng = cf.Engine(fields, max_active=2, pose_chunk=64)
+    for q in reqs:
+        eng.submit(q["field"], q["soa"], q["poses"], q["prm"], 10 ** 9, q["tag"])  # run to the pose limit
+    with pytest.raises(cf.CfError) as ei:
+        eng.drain(0)
+    assert ei.value.code == cf.CF_ETIMEOUT
+    got = _collect(eng, len(reqs))
+    assert sorted(got) == [q["tag"] for q in reqs]
+    assert all(r["status"] == 0 and r["partial"] for r in got.values())
+    eng.close()
