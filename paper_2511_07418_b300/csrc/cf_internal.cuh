@@ -337,6 +337,7 @@ struct ScoreArgs {
     float *margin;
     uint8_t *accept;
     unsigned int *work;  // scratch: tuple work counter, zero at launch
+    float *word_box;     // Alg. 2 scratch: per mask word, the bounding box of its 32 points [W][6] (lo xyz, hi xyz)
     unsigned int *status;          // device status word (CF_DEV_* bits)
     unsigned long long *counters;  // [0] pivots, [1] LPs, [2] tuples, [3] warm-started Alg. 2 candidates
     int refill;                    // idle lanes of a scoring warp before a group refill (launch-level)

@@ -552,6 +552,29 @@ __device__ float closure_margin(const float (&w)[6], int k, int K, int lane, flo
     return lp_solve_margin<NS>(s, k, K, lane, buf, n_piv, n_lp, flags);
 }
 
+// Bounding box of the (up to) 32 points of each mask word: warp per word.
+__global__ void k_word_boxes(const float *__restrict__ px, const float *__restrict__ py, const float *__restrict__ pz,
+                             int N, int W, float *__restrict__ box) {
+    const int w = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (w >= W) return;
+    const int x = 32 * w + lane;
+    const bool ok = x < N;
+    float v[3] = {ok ? __ldg(px + x) : 0.f, ok ? __ldg(py + x) : 0.f, ok ? __ldg(pz + x) : 0.f};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float lo = ok ? v[c] : INFINITY, hi = ok ? v[c] : -INFINITY;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            lo = fminf(lo, __shfl_xor_sync(kFull, lo, o));
+            hi = fmaxf(hi, __shfl_xor_sync(kFull, hi, o));
+        }
+        if (lane == 0) {
+            box[6 * (size_t)w + c] = lo;
+            box[6 * (size_t)w + 3 + c] = hi;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Alg. 2: blockwise zeroth-order contact optimisation
 // ---------------------------------------------------------------------------
@@ -713,8 +736,29 @@ __global__ void __launch_bounds__(kOptThreads) k_optimize_tuples(const ScoreArgs
 #pragma unroll
                     for (int c = 0; c < NI; ++c) { bd[c] = INFINITY; bi[c] = INT_MAX; }
                     const uint32_t *row = a.masks + ((size_t)pose * F + fi) * W;
+                    // exact pruning: the current point x0 lies in the domain, so every candidate q_c has a
+                    // domain point within |q_c - p0| and its nearest lies within R = 2 max_c |q_c - p0| of
+                    // p0; words whose box is farther than R from p0 hold none (R with slack for rounding;
+                    // no pruning when x0's bit is not set, e.g. for given tuples outside the domain)
+                    float rc = 0.f;
+                    if (lane < NI) {
+                        const float dx = s_cand[warp][lane][0] - px, dy = s_cand[warp][lane][1] - py,
+                                    dz = s_cand[warp][lane][2] - pz;
+                        rc = sqrtf(dx * dx + dy * dy + dz * dz);
+                    }
+                    rc = __uint_as_float(__reduce_max_sync(kFull, __float_as_uint(rc)));  // rc >= 0: bits order
+                    const bool in_dom = (__ldg(row + (x0 >> 5)) >> (x0 & 31)) & 1u;
+                    const float R = 2.f * rc * 1.0001f + 1e-6f;
+                    const float R2 = in_dom ? R * R : INFINITY;
                     for (int w = lane; w < W; w += 32) {
                         uint32_t bits = __ldg(row + w);
+                        if (bits && R2 < INFINITY) {
+                            const float *bx = a.word_box + 6 * (size_t)w;
+                            const float ex = fmaxf(fmaxf(__ldg(bx) - px, px - __ldg(bx + 3)), 0.f);
+                            const float ey = fmaxf(fmaxf(__ldg(bx + 1) - py, py - __ldg(bx + 4)), 0.f);
+                            const float ez = fmaxf(fmaxf(__ldg(bx + 2) - pz, pz - __ldg(bx + 5)), 0.f);
+                            if (ex * ex + ey * ey + ez * ez > R2) bits = 0u;  // every point of the word is farther
+                        }
                         while (bits) {
                             const int b = __ffs(bits) - 1;
                             bits &= bits - 1;
@@ -1313,6 +1357,9 @@ cudaError_t launch_optimize(const ScoreArgs &a, int n_outer, int n_inner, float 
     if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
     const long long want = (total + kOptWarps - 1) / kOptWarps;
     const int grid = (int)std::min<long long>((long long)sms * 16, want);
+    if (!a.word_box) return cudaErrorInvalidValue;
+    k_word_boxes<<<(unsigned)((a.W * 32 + 255) / 256), 256, 0, st>>>(a.px, a.py, a.pz, a.N, a.W, a.word_box);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
     const bool one = lp_slots(a.k, a.K) == 1;
     const size_t smem1 = (size_t)kOptWarps * 3 * a.k * state_words<1>() * 32 * sizeof(float);
     const size_t smem2 = (size_t)kOptWarps * 3 * a.k * state_words<2>() * 32 * sizeof(float);
