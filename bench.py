@@ -63,6 +63,8 @@ def _args():
     ap.add_argument("--extra-workload", default="hand16_superquadric",
                     help="a second workload whose main step is reported under its own key ('' to skip)")
     ap.add_argument("--extra-steps", type=int, default=100)
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="time the main step under the default launch shapes instead of the autotuner's")
     ap.add_argument("--parity-poses", type=int, default=4,
                     help="poses of the timed step checked against the FP64 oracle (0: skip)")
     return ap.parse_args()
@@ -435,6 +437,17 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     peak_measured = cf.fp32_peak()
+    tuning = None
+    if args.autotune:
+        # the project's autotuner picks the launch shapes on this request (untimed): poses per query block,
+        # the scorer's refill point and blocks per SM
+        t0 = time.perf_counter()
+        tune_field = cf.build(w.hand, w.inv_h, w.bins, q)
+        item = cf.batch_item(tune_field, soa, poses, prm)
+        shapes, tune_ms = cf.autotune([item], reps=3)
+        tuning = {"shapes": shapes, "query_ms": tune_ms[0], "sample_score_ms": tune_ms[1],
+                  "seconds": time.perf_counter() - t0}
+        del item, tune_field
     sampler = ClockSampler(str(props.uuid) if hasattr(props, "uuid") else None)
     main = main_leg(cf, torch, dev, w, args.steps, args.warmup, flush, barrier, sampler)
     masks, counts, tuples, fingers = main["masks"], main["counts"], main["tuples"], main["fingers"]
@@ -506,7 +519,7 @@ def run_ours(args):
                    "lps_per_tuple": counters["lps"] / max(1, counters["tuples_scored"])},
             "e2e": {"value": e2e_acc / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": n_e2e, "ms_per_step": 1e3 * e2e_s / n_e2e},
-            "clocks": clocks}
+            "clocks": clocks, "tuning": tuning or {"shapes": cf.get_tuning(), "autotuned": False}}
     if world == 1 and args.realized_steps > 0:
         line["realized"] = run_realized(cf, torch, dev, w, args.realized_steps, soa, poses, masks, counts, tuples,
                                         fingers, prm, prm_given, flush)
