@@ -525,7 +525,8 @@ int cf_concave_filter(const cf_points *obj, const cf_sdf *sdf, float side, float
  * results of every call are the same under any shape; only the time changes.
  * Batches and engines take the shapes current at their creation. */
 typedef struct cf_tuning {
-    int32_t query_poses_per_block;  /* poses per domain-query block: 4, 8 or 16 (default 4) */
+    int32_t query_poses_per_block;  /* poses per domain-query block, 1..16 (default 4); with poses x slots
+                                       <= 32 each lane keeps one (pose, slot) mask word */
     int32_t score_refill;           /* scoring lanes of a warp that wait before they take new tuples together:
                                        4, 8 or 16 (default 8) */
     int32_t score_blocks_per_sm;    /* scoring blocks per SM: 1, 2, 3, or 0 = as many as fit (default 0) */

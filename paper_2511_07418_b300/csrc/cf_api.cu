@@ -1264,7 +1264,7 @@ extern "C" int cf_concave_filter(const cf_points *obj, const cf_sdf *sdf, float 
 namespace {
 bool tuning_valid(const cf_tuning *t) {
     const int p = t->query_poses_per_block, r = t->score_refill, s = t->score_blocks_per_sm;
-    return (p == 4 || p == 8 || p == 16) && (r == 4 || r == 8 || r == 16) && s >= 0 && s <= 3;
+    return p >= 1 && p <= kMaxPosesPerBlock && (r == 4 || r == 8 || r == 16) && s >= 0 && s <= 3;
 }
 }  // namespace
 
@@ -1333,7 +1333,14 @@ extern "C" int cf_autotune(const cf_batch_item *items, int32_t n_items, int32_t 
     };
     cf_tuning best = saved;
     double bq = 1e300, bs = 1e300;
-    for (int ppb : {4, 8, 16}) {
+    // 4, 8, 16, and the largest count that lets each lane keep one (pose, slot) word: 32 / slots
+    std::vector<int> ppbs = {4, 8, 16};
+    for (int i = 0; i < n_items; ++i) {
+        const int own = 32 / std::max(1, items[i].field->geom.F);
+        if (own >= 2 && own <= kMaxPosesPerBlock && std::find(ppbs.begin(), ppbs.end(), own) == ppbs.end())
+            ppbs.push_back(own);
+    }
+    for (int ppb : ppbs) {
         cf_tuning t = saved;
         t.query_poses_per_block = ppb;
         double ms = 0;

@@ -92,7 +92,7 @@ def test_every_entry_point_rejects_missing_arguments_on_the_host():
         "cf_place": lambda: cf._cf_place(None, None, 0, None, None, None),
         "cf_concave_filter": lambda: cf._cf_concave(None, None, 0.0, 0.0, None, None, None, None),
         "cf_set_tuning(NULL)": lambda: cf._cf_set_tuning(None),
-        "cf_set_tuning(3 poses per block)": lambda: cf._cf_set_tuning(byref(cf.Tuning(3, 8, 0))),
+        "cf_set_tuning(17 poses per block)": lambda: cf._cf_set_tuning(byref(cf.Tuning(17, 8, 0))),
         "cf_set_tuning(refill 5)": lambda: cf._cf_set_tuning(byref(cf.Tuning(4, 5, 0))),
         "cf_get_tuning": lambda: cf._cf_get_tuning(None),
         "cf_autotune": lambda: cf._cf_autotune(None, 0, 1, None, None),
