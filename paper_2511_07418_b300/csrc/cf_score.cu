@@ -951,6 +951,7 @@ __global__ void __launch_bounds__(kLaneThreads) k_score_lanes(const ScoreArgs a,
     int state = kIdle;
     unsigned u = 0;  // the lane's tuple within its object
     int od = 0;      // MULTI: the lane's object
+    long long od_lo = 0, od_hi = -1;  // MULTI: its global tuple range [tuple0[od], tuple0[od + 1])
     float B[kRows][kRows], xb[kRows], pi[kRows];
     int beta[kRows];
     unsigned basic_x = 0;  // bit c: column c' basic
@@ -975,13 +976,18 @@ __global__ void __launch_bounds__(kLaneThreads) k_score_lanes(const ScoreArgs a,
                     state = kDone;
                 } else {
                     if (MULTI) {
-                        int lo = 0, hi = n_desc - 1;
-                        while (lo < hi) {
-                            const int mid = (lo + hi + 1) >> 1;
-                            if (__ldg(tuple0 + mid) <= (long long)u) lo = mid; else hi = mid - 1;
+                        // tuples come in ascending runs: search only when u leaves the lane's object
+                        if ((long long)u < od_lo || (long long)u >= od_hi) {
+                            int lo = 0, hi = n_desc - 1;
+                            while (lo < hi) {
+                                const int mid = (lo + hi + 1) >> 1;
+                                if (__ldg(tuple0 + mid) <= (long long)u) lo = mid; else hi = mid - 1;
+                            }
+                            od = lo;
+                            od_lo = __ldg(tuple0 + lo);
+                            od_hi = __ldg(tuple0 + lo + 1);
                         }
-                        od = lo;
-                        u = (unsigned)((long long)u - __ldg(tuple0 + lo));
+                        u = (unsigned)((long long)u - od_lo);
                     }
                     const LaneObj o = lane_obj(MULTI ? descs[od] : a);
                     if (MULTI) mu = o.mu;
