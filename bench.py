@@ -57,6 +57,8 @@ def _args():
     ap.add_argument("--batch-objects", type=int, default=64, help="objects of the batched-form leg (0: skip)")
     ap.add_argument("--served-seconds", type=float, default=30.0, help="seconds per offered rate (0: skip)")
     ap.add_argument("--served-rates", default="10,100,1000")
+    ap.add_argument("--served-slots", type=int, default=256, help="engine slots (requests on the GPU at once)")
+    ap.add_argument("--served-chunk", type=int, default=256, help="poses per request per engine round")
     ap.add_argument("--realized-steps", type=int, default=20, help="steps of the IK + realization leg (0: skip)")
     ap.add_argument("--optimized-steps", type=int, default=5, help="steps of the Alg. 2 optimisation leg (0: skip)")
     ap.add_argument("--gswo-steps", type=int, default=10, help="steps of the Eq. GSWO scoring leg (0: skip)")
@@ -545,7 +547,8 @@ def run_ours(args):
                                                         n_range=(1024, 8192), p_range=(256, 2048), tune=False)
         if args.served_seconds > 0:
             rates = [float(x) for x in args.served_rates.split(",") if x]
-            line["served"] = run_served(cf, torch, dev, ws, fields, rates, args.served_seconds)
+            line["served"] = run_served(cf, torch, dev, ws, fields, rates, args.served_seconds,
+                                        max_active=args.served_slots, pose_chunk=args.served_chunk)
     if world == 1 and args.extra_workload and args.extra_workload != w.name:
         we = synth.workload(args.extra_workload)
         ex = main_leg(cf, torch, dev, we, args.extra_steps, args.warmup, flush, barrier)
@@ -867,7 +870,7 @@ def run_batched(cf, torch, dev, n_objects, ws, fields, n_range=(2048, 131072), p
     return out
 
 
-def run_served(cf, torch, dev, ws, fields, rates, seconds, pool=24):
+def run_served(cf, torch, dev, ws, fields, rates, seconds, pool=24, max_active=64, pose_chunk=256):
     """Poisson request streams against the engine (continuous batching) and
     against the same engine with one slot (one request at a time, plain
     per-request launches); p50 / p99 latency and valid grasps/s per rate."""
@@ -885,7 +888,7 @@ def run_served(cf, torch, dev, ws, fields, rates, seconds, pool=24):
         objs.append((hi, obj.soa(), poses, obj))
 
     def stream(max_active, rate, seconds=seconds, budget=64 << 30):
-        eng = cf.Engine(fields, hbm_budget_bytes=budget, max_active=max_active, pose_chunk=256, pose_cap=65536)
+        eng = cf.Engine(fields, hbm_budget_bytes=budget, max_active=max_active, pose_chunk=pose_chunk, pose_cap=65536)
         r = np.random.default_rng(int(rate) * 7 + max_active)
         t = 0.0
         arrivals = []
@@ -931,12 +934,14 @@ def run_served(cf, torch, dev, ws, fields, rates, seconds, pool=24):
     out = {"continuous_batching": [], "one_at_a_time": [],
            "workload": f"Poisson arrivals, {seconds:g} s per rate; objects drawn from {pool} generated objects "
                        "(superquadric / tool, 1,024-65,536 points) with a random hand; 100-5,000 grasps requested; "
-                       "8,192 candidate poses per request (pose cap 65,536), chunk 256 poses, HBM budget 64 GiB"}
+                       f"8,192 candidate poses per request (pose cap 65,536), chunk {pose_chunk} poses, {max_active} slots, "
+                       "HBM budget 64 GiB"}
     for rate in rates:
-        out["continuous_batching"].append(stream(64, rate))
+        out["continuous_batching"].append(stream(max_active, rate))
         out["one_at_a_time"].append(stream(1, rate, seconds=min(seconds, 5.0)))
-    # admission by HBM budget that binds: a 128 MiB budget holds only ~10 requests' device state
-    out["budget_gated"] = stream(64, max(rates), seconds=min(seconds, 10.0), budget=128 << 20)
+    # admission by HBM budget that binds: a 128 MiB budget holds only a few dozen requests' device state
+    out["budget_gated"] = stream(max_active, max(rates), seconds=min(seconds, 10.0), budget=128 << 20)
+    out["engine"] = {"max_active": max_active, "pose_chunk": pose_chunk}
     return out
 
 
