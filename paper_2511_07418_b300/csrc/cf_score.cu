@@ -131,18 +131,19 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_tuples(const ScoreArg
     // group sums straight from the masks (no staging): a warp takes 128 consecutive words of a row, four
     // independent coalesced loads per lane, and adds the popcounts in groups of kGroupWords lanes
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    const int CW = (W + 127) / 128;
+    constexpr int kLoads = 8;  // words per lane in flight
+    const int CW = (W + 32 * kLoads - 1) / (32 * kLoads);
     for (int ch = warp; ch < F * CW; ch += nwarps) {
-        const int f = ch / CW, w0 = (ch % CW) * 128;
+        const int f = ch / CW, w0 = (ch % CW) * 32 * kLoads;
         const uint32_t *row = src + (size_t)f * W;
-        uint32_t v[4];
+        uint32_t v[kLoads];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < kLoads; ++q) {
             const int w = w0 + 32 * q + lane;
             v[q] = w < W ? __ldg(row + w) : 0u;
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < kLoads; ++q) {
             const int w = w0 + 32 * q + lane;
             uint32_t c = __popc(v[q]);
 #pragma unroll
