@@ -68,6 +68,8 @@ enum {
 #define CF_DEV_LP_UNBOUNDED 0x2u   /* reserved (the scaled LP reads an unbounded ratio test as margin 0) */
 #define CF_DEV_REP_FULL 0x4u       /* the representative table had no free slot (cannot happen at load <= 1/2) */
 #define CF_DEV_REP_MISS 0x8u       /* an IK contact's code has no representative (tuple not from this field) */
+#define CF_DEV_OPT_STALL 0x10u     /* an Alg. 2 warp had no LP to run and no step to advance (cannot happen);
+                                      it stopped, leaving its tuples in flight unwritten */
 #define CF_DEV_BIN_RANGE 0x80000000u /* a build sample fell outside the table box (cannot happen) */
 
 typedef void *cf_stream; /* cudaStream_t */

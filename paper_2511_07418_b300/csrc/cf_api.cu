@@ -878,7 +878,7 @@ extern "C" int cf_optimize_tuples(const cf_points *obj, int32_t n_fingers, const
         e = launch_optimize(a, opt->n_outer, opt->n_inner, opt->sigma, opt->zero_tol, opt->min_gain, opt->warm_start, st);
     }
     cudaError_t e2 = cudaFreeAsync(scratch, st);
-    if (e != cudaSuccess) return cuda_fail(e, "launch k_word_boxes / k_optimize_lanes");
+    if (e != cudaSuccess) return cuda_fail(e, "launch k_word_boxes / k_optimize_pool");
     if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync(optimisation scratch)");
     return CF_OK;
 }

@@ -262,6 +262,8 @@ __global__ void k_word_boxes(const float *__restrict__ px, const float *__restri
 // ---------------------------------------------------------------------------
 constexpr int kOptThreads = 128;
 constexpr int kOptWarps = kOptThreads / 32;
+constexpr int kOptSlots = 2;   // tuples in flight per warp
+constexpr int kOptRefill = 8;  // idle lanes before an Alg. 2 warp records results and hands out jobs
 
 struct OptArgs {
     int n_outer, n_inner;
@@ -757,13 +759,14 @@ __global__ void __launch_bounds__(kLaneThreads) k_score_lanes(const ScoreArgs a,
 // Projection of Alg. 2: for each of the NI candidate points cand[c] (c < NI, x y z), the
 // domain point nearest to it (mask bit set in row `row`), lowest index on ties; lane c
 // returns candidate c's (-1 when the domain is empty).  Exact pruning: the current
-// point x0 (p) lies in the domain, so every candidate q_c has a domain point within
-// |q_c - p| and its nearest lies within R = 2 max_c |q_c - p| of p; mask words whose
-// point box is farther than R from p hold none (R with slack for rounding; no pruning
-// when x0's bit is not set, e.g. for given tuples outside the domain).  Lanes test
-// words lane, lane + 32, ...; the warp then takes each surviving word together, lane
-// b on the word's point b, so point loads are coalesced and no lane walks a word's
-// bits alone.
+// point x0 (p) lies in the domain, so candidate q_c's nearest domain point lies within
+// r_c = |q_c - p| of q_c, hence within R = 2 max_c r_c of p.  Lanes test mask words
+// lane, lane + 32, ...: a word whose point box is farther than R from p is skipped, and
+// of the rest each candidate c whose r_c-ball misses the box is left out of the word
+// (radii with slack for rounding; no pruning when x0's bit is not set, e.g. for given
+// tuples outside the domain).  The warp then takes each surviving word together, lane b
+// on the word's point b, for the candidates the word can serve: point loads are
+// coalesced and the candidate test is uniform across the warp.
 template <int NI>
 __device__ __forceinline__ int project_candidates(const ScoreArgs &a, const float *cand, const uint32_t *row, int x0,
                                                   float px, float py, float pz, int lane) {
@@ -788,29 +791,54 @@ __device__ __forceinline__ int project_candidates(const ScoreArgs &a, const floa
         const float dx = cand[3 * lane] - px, dy = cand[3 * lane + 1] - py, dz = cand[3 * lane + 2] - pz;
         rc = sqrtf(dx * dx + dy * dy + dz * dz);
     }
+    // each candidate's pruning radius r_c (squared, with slack)
+    const float rs = rc * 1.0001f + 1e-6f;
+    float r2c[NI];
+#pragma unroll
+    for (int c = 0; c < NI; ++c) r2c[c] = __shfl_sync(kFull, rs * rs, c);
     rc = __uint_as_float(__reduce_max_sync(kFull, __float_as_uint(rc)));  // rc >= 0: bits order
     const bool in_dom = (__ldg(row + (x0 >> 5)) >> (x0 & 31)) & 1u;
     const float R = 2.f * rc * 1.0001f + 1e-6f;
     const float R2 = in_dom ? R * R : INFINITY;
+    constexpr unsigned kAll = NI >= 32 ? 0xffffffffu : (1u << NI) - 1u;
     for (int w0 = 0; w0 < W; w0 += 32) {
         const int w = w0 + lane;
         uint32_t bits = w < W ? __ldg(row + w) : 0u;
+        unsigned cmask = kAll;  // the candidates this word can serve
         if (bits && R2 < INFINITY) {
             const float *bx = a.word_box + 6 * (size_t)w;
-            const float ex = fmaxf(fmaxf(__ldg(bx) - px, px - __ldg(bx + 3)), 0.f);
-            const float ey = fmaxf(fmaxf(__ldg(bx + 1) - py, py - __ldg(bx + 4)), 0.f);
-            const float ez = fmaxf(fmaxf(__ldg(bx + 2) - pz, pz - __ldg(bx + 5)), 0.f);
-            if (ex * ex + ey * ey + ez * ez > R2) bits = 0u;  // every point of the word is farther
+            const float lx = __ldg(bx), ly = __ldg(bx + 1), lz = __ldg(bx + 2);
+            const float hx = __ldg(bx + 3), hy = __ldg(bx + 4), hz = __ldg(bx + 5);
+            const float ex = fmaxf(fmaxf(lx - px, px - hx), 0.f);
+            const float ey = fmaxf(fmaxf(ly - py, py - hy), 0.f);
+            const float ez = fmaxf(fmaxf(lz - pz, pz - hz), 0.f);
+            if (ex * ex + ey * ey + ez * ez > R2) {
+                bits = 0u;  // every point of the word is farther
+            } else {
+                cmask = 0u;
+#pragma unroll
+                for (int c = 0; c < NI; ++c) {
+                    const float *qc = kCandRegs ? cq[kCandRegs ? c : 0] : cand + 3 * c;
+                    const float r2 = r2c[c];
+                    const float fx = fmaxf(fmaxf(lx - qc[0], qc[0] - hx), 0.f);
+                    const float fy = fmaxf(fmaxf(ly - qc[1], qc[1] - hy), 0.f);
+                    const float fz = fmaxf(fmaxf(lz - qc[2], qc[2] - hz), 0.f);
+                    if (fx * fx + fy * fy + fz * fz <= r2) cmask |= 1u << c;
+                }
+                if (!cmask) bits = 0u;
+            }
         }
         // each lane visits its points in ascending index order, as the (distance, index) reduction assumes
         for (unsigned need = __ballot_sync(kFull, bits != 0u); need; need &= need - 1) {
             const int b = __ffs(need) - 1;
             const uint32_t wb = __shfl_sync(kFull, bits, b);
+            const unsigned wc = __shfl_sync(kFull, cmask, b);
             const int x = 32 * (w0 + b) + lane;
             if ((wb >> lane) & 1u) {
                 const float qx = __ldg(a.px + x), qy = __ldg(a.py + x), qz = __ldg(a.pz + x);
 #pragma unroll
                 for (int c = 0; c < NI; ++c) {
+                    if (!((wc >> c) & 1u)) continue;
                     const float *qc = kCandRegs ? cq[kCandRegs ? c : 0] : cand + 3 * c;
                     const float dx = __fsub_rn(qx, qc[0]), dy = __fsub_rn(qy, qc[1]), dz = __fsub_rn(qz, qc[2]);
                     const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
@@ -947,219 +975,348 @@ __device__ __forceinline__ bool lane_lp_repair(LaneLp &s, const float *fi, int i
     return feas;
 }
 
-// Every lane with act runs its LP_j from its started state to the end (the
-// warp loops until the last lane is done); returns s_j (+inf when unbounded).
-template <int KT, class Frames>
-__device__ __forceinline__ float lanes_solve(LaneLp &s, bool act, const Frames &fr, int k, int K, int j, float mu,
-                                             const ScoreArgs &a, unsigned long long &n_piv,
-                                             unsigned long long &n_lp, unsigned &flags) {
-    const int kK = k * K;
-    const bool ran = act;
-    bool unb = false;
-    while (__any_sync(kFull, act)) {
-        if (act) {
-            float de = 0.f;
-            const int e = lane_lp_price<KT>(s, fr, k, K, j, mu, a, de);
-            bool end = e < 0;
-            if (!end && s.it == kMaxPivots) {
-                flags |= CF_DEV_LP_PIVOT_CAP;
-                end = true;
-            }
-            if (!end && !lane_lp_pivot<KT>(s, fr, e, de, K, kK, mu, a)) {
-                unb = true;
-                end = true;
-            }
-            if (end) act = false;
-        }
-    }
-    if (ran) {
-        ++n_lp;
-        n_piv += (unsigned)s.it;
-    }
-    return unb ? INFINITY : lane_lp_value(s, j * K, j * K + K);
-}
-
-// The closure margin of a tuple from its s_j, taken in order j = 0 .. k - 1 as
-// k_score_lanes takes them: the first unbounded s_j gives 0, and a running
-// maximum past 1 / kZeroExit ends the scan.  s_j of lane base + q.
-__device__ __forceinline__ float margin_from_lanes(float sj, int base, int k) {
+// The closure margin of a tuple from its s_j (v[0..k-1]), taken in order j = 0 .. k - 1
+// as k_score_lanes takes them: the first unbounded s_j gives 0, and a running
+// maximum past 1 / kZeroExit ends the scan.
+__device__ __forceinline__ float margin_from(const float *v, int k) {
     float bs = 0.f;
-    bool zero = false, stop = false;
     for (int q = 0; q < k; ++q) {
-        const float v = __shfl_sync(kFull, sj, (base + q) & 31);
-        if (stop) continue;
-        if (!(v < INFINITY)) {
-            zero = true;
-            stop = true;
-            continue;
-        }
-        bs = fmaxf(bs, v);
-        if (bs >= 1.f / kZeroExit) stop = true;
+        if (!(v[q] < INFINITY)) return 0.f;
+        bs = fmaxf(bs, v[q]);
+        if (bs >= 1.f / kZeroExit) break;
     }
-    return zero ? 0.f : (bs > 0.f ? __fdiv_rn(1.f, bs) : INFINITY);
+    return bs > 0.f ? __fdiv_rn(1.f, bs) : INFINITY;
 }
 
-// One warp per tuple (persistent warps, work counter).  Per outer iteration and
-// contact i: NI Gaussian mutations of p_i in its tangent plane (Box-Muller on
-// Philox4x32-10 words), each projected onto finger f_i's domain (the nearest
-// object point whose mask bit is set: the warp tests the mask words against a
-// pruning radius, then takes each surviving word with lane b on its point b).
-// The candidates' closure LPs are independent of one another, so lane
-// g * k + j solves LP_j of the g-th candidate (32 / k candidates per pass) with
-// the lane simplex, starting from the current tuple's optimal LP_j basis
-// repaired for the moved contact (Sec. 5.4, "A Free Lunch"; c' = 0 when the
-// repair fails or warm_start is off).  The candidates then replace the best so
-// far in order when their margin is lower by more than the relative min_gain
-// (margins <= zero_tol count as 0), so the margin never increases; the
-// winner's bases become the current tuple's.
-template <int NI, int KT>
-__global__ void __launch_bounds__(kOptThreads) k_optimize_lanes(const ScoreArgs a, const OptArgs o, unsigned total) {
-    __shared__ __align__(16) float s_fr[kOptWarps][CF_MAX_K][kContactFloats];  // the current tuple's frames
-    __shared__ __align__(16) float s_cf[kOptWarps][NI][kContactFloats];        // the candidates' frames
-    __shared__ float s_cand[kOptWarps][NI][3];
-    __shared__ int s_list[kOptWarps][NI];                                       // the candidates to solve, in order
-    __shared__ LpBasis s_basis[kOptWarps][2][CF_MAX_K];  // optimal LP_j bases: the current tuple's, the best trial's
+// A tuple in flight on an Alg. 2 warp and the LP jobs of its current step.
+struct OptSlot {
+    unsigned u;                          // the tuple
+    int pose, tau;
+    int id[CF_MAX_K], fg[CF_MAX_K];      // its contacts and their fingers
+    float J, Jc;                         // its margin; the margin with values <= zero_tol read as 0
+    int it, i;                           // the step: outer iteration, moved contact
+    int phase;                           // kSlotFree / kSlotRun / kSlotProject / kSlotComplete
+    int init;                            // the step solves the tuple's own LPs (else its candidates')
+    int n_jobs, n_assigned, n_done;      // LP jobs of the step: job g * k + j = LP_j of candidate g
+    int n_todo;                          // candidates of the step
+};
+constexpr int kSlotFree = 0, kSlotRun = 1, kSlotProject = 2, kSlotComplete = 3;
+
+template <int NI>
+struct __align__(16) OptSlotSmem {
+    float cur[CF_MAX_K][kContactFloats];  // the tuple's contact frames
+    float cand[NI][kContactFloats];       // the step's candidates' frames (by rank)
+    LpBasis base[CF_MAX_K];               // the tuple's optimal LP_j bases: the warm starts
+    LpBasis job[NI * CF_MAX_K];           // each job's final basis (the winner's become the tuple's)
+    float sres[NI * CF_MAX_K];            // each job's s_j
+    int cand_pt[NI];                      // each candidate's point
+    OptSlot st;
+};
+
+template <int NI, int M>
+struct OptWarpSmem {
+    OptSlotSmem<NI> slot[M];
+    float xyz[NI][3];  // the mutated points being projected
+};
+
+// Alg. 2 with a job pool per warp (persistent warps, work counter).  A warp keeps M
+// tuples in flight.  Each tuple advances by steps: first its own k closure LPs;
+// then per outer iteration and contact i, NI Gaussian mutations of p_i in its
+// tangent plane (Box-Muller on Philox4x32-10 words) projected onto finger f_i's
+// domain (project_candidates, the whole warp), after which the step's jobs are
+// the candidates' LPs, LP_j of candidate g.  Idle lanes take the next job of any
+// tuple in flight and solve it with the lane simplex: a tuple's own LPs from
+// c' = 0, a candidate's LP_j from the tuple's optimal LP_j basis repaired for
+// the moved contact (Sec. 5.4, "A Free Lunch"; c' = 0 when the repair fails or
+// warm_start is off).  When a step's last job ends, its candidates replace the
+// best so far in order when their margin is lower by more than the relative
+// min_gain (margins <= zero_tol count as 0), so the margin never increases, and
+// the winner's bases become the tuple's.  Lanes thus stay busy while other
+// tuples wait for their slowest LP, and every job's LP runs as it would alone.
+template <int NI, int KT, int M>
+__global__ void __launch_bounds__(kOptThreads) k_optimize_pool(const ScoreArgs a, const OptArgs o, unsigned total) {
+    extern __shared__ __align__(16) unsigned char s_opt[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    OptWarpSmem<NI, M> &ws = reinterpret_cast<OptWarpSmem<NI, M> *>(s_opt)[warp];
     const int k = a.k, K = KT > 0 ? KT : a.K, kK = k * K, F = a.F, W = a.W;
-    const int G = 32 / k;  // candidates per pass
-    const int grp = lane / k, jl = lane - grp * k;
     const float mu = a.mu;
     const LaneObj ob = lane_obj(a);
     unsigned long long n_piv = 0, n_lp = 0, n_tup = 0, n_warm = 0;
     unsigned flags = 0;
     const uint2 key = make_uint2(a.seed_lo, a.seed_hi);
     const int blocks_per_draw = (NI + 1) / 2;
-    float *const cur = &s_fr[warp][0][0];
+    if (lane == 0)
+        for (int m = 0; m < M; ++m) ws.slot[m].st.phase = kSlotFree;
+    __syncwarp();
+
+    LaneLp s;
+    lane_lp_cold(s, kK);
+    bool act = false;   // the lane is solving a job
+    bool pend = false;  // the lane holds a finished job's result, not yet recorded
+    bool unb = false;   // that job's LP was unbounded
+    int jm = 0, jq = 0; // its slot and job
+    int jj = 0;         // its LP's objective (contact j)
+    MovedFrames fr{&ws.slot[0].cur[0][0], &ws.slot[0].cur[0][0], -1};
+    bool exhausted = false;
+
     for (;;) {
-        unsigned u = 0;
-        if (lane == 0) u = atomicAdd(a.work, 1u);
-        u = __shfl_sync(kFull, u, 0);
-        if (u >= total) break;
-        const int pose = (int)(u / (unsigned)a.T), tau = (int)(u % (unsigned)a.T);
-        int id[CF_MAX_K] = {0, 0, 0, 0}, fg[CF_MAX_K] = {0, 0, 0, 0};
-        bool valid = true;
-        for (int d = 0; d < k; ++d) {
-            id[d] = __ldg(a.tuples + (size_t)u * k + d);
-            fg[d] = (int)__ldg(a.fingers + (size_t)u * k + d);
-            valid = valid && id[d] >= 0 && id[d] < a.N && fg[d] < F;
-        }
-        float J = INFINITY;
-        if (valid) {
-            int b_cur = 0, b_best = 1;
-            if (lane < k) contact_frame(ob, lane == 0 ? id[0] : lane == 1 ? id[1] : lane == 2 ? id[2] : id[3],
-                                        cur + kContactFloats * lane);
-            __syncwarp();
-            {  // the tuple's own LPs, lane j on LP_j from c' = 0; their optimal bases seed the candidates
-                LaneLp s;
-                const bool act = lane < k;
-                lane_lp_cold(s, kK);
-                lane_lp_begin(s, lane * K, lane * K + K);
-                const float sj = lanes_solve<KT>(s, act, MovedFrames{cur, cur, -1}, k, K, lane, mu, a, n_piv, n_lp,
-                                                 flags);
-                if (act) basis_store(s_basis[warp][b_cur][lane], s);
-                J = margin_from_lanes(sj, 0, k);
-            }
-            float Jc = J <= o.zero_tol ? 0.f : J;
-            const uint32_t pid = (uint32_t)pose + a.pose_base;
-            for (int it = 0; it < o.n_outer && Jc > 0.f; ++it) {
-                for (int i = 0; i < k && Jc > 0.f; ++i) {
-                    const int x0 = i == 0 ? id[0] : i == 1 ? id[1] : i == 2 ? id[2] : id[3];
-                    const int fi = i == 0 ? fg[0] : i == 1 ? fg[1] : i == 2 ? fg[2] : fg[3];
-                    // tangent basis of nu = -n at the current point (Duff et al. 2017) and the mutated
-                    // points in explicitly rounded FP32 operations (no contraction left to the compiler)
-                    const float px = __ldg(a.px + x0), py = __ldg(a.py + x0), pz = __ldg(a.pz + x0);
-                    const float vx = -__ldg(a.nx + x0), vy = -__ldg(a.ny + x0), vz = -__ldg(a.nz + x0);
-                    const float sgn = copysignf(1.f, vz);
-                    const float aa = __fdiv_rn(-1.f, __fadd_rn(sgn, vz));
-                    const float bb = __fmul_rn(__fmul_rn(vx, vy), aa);
-                    const float xx = __fadd_rn(1.f, __fmul_rn(__fmul_rn(__fmul_rn(sgn, vx), vx), aa));
-                    const float xy = __fmul_rn(sgn, bb), xz = -__fmul_rn(sgn, vx);
-                    const float yx = bb, yy = __fadd_rn(sgn, __fmul_rn(__fmul_rn(vy, vy), aa)), yz = -vy;
-                    if (lane < NI) {  // candidate `lane`: one Box-Muller pair, FP64 then rounded to FP32
-                        const int c = lane;
-                        const uint4 w4 = philox4x32_10(
-                            make_uint4(pid, (uint32_t)tau, (uint32_t)((it * k + i) * blocks_per_draw + c / 2), 0xA162u),
-                            key);
-                        const uint32_t w0 = (c & 1) ? w4.z : w4.x, w1 = (c & 1) ? w4.w : w4.y;
-                        const double u1 = (double)((w0 >> 8) + 1u) * 5.9604644775390625e-8;  // (0, 1]
-                        const double u2 = (double)(w1 >> 8) * 5.9604644775390625e-8;         // [0, 1)
-                        const double r = sqrt(-2.0 * log(u1));
-                        double sd, cd;
-                        sincospi(2.0 * u2, &sd, &cd);
-                        const float g1 = (float)(r * cd), g2 = (float)(r * sd);
-                        const float sg = o.sigma;
-                        s_cand[warp][c][0] = __fadd_rn(px, __fmul_rn(sg, __fadd_rn(__fmul_rn(g1, xx), __fmul_rn(g2, yx))));
-                        s_cand[warp][c][1] = __fadd_rn(py, __fmul_rn(sg, __fadd_rn(__fmul_rn(g1, xy), __fmul_rn(g2, yy))));
-                        s_cand[warp][c][2] = __fadd_rn(pz, __fmul_rn(sg, __fadd_rn(__fmul_rn(g1, xz), __fmul_rn(g2, yz))));
-                    }
-                    __syncwarp();
-                    const int cand_mine = project_candidates<NI>(a, &s_cand[warp][0][0],
-                                                                  a.masks + ((size_t)pose * F + fi) * W, x0, px, py, pz, lane);
-                    // candidates equal to the current point or to an earlier candidate cannot win
-                    const unsigned same = __match_any_sync(kFull, lane < NI ? cand_mine : -2 - lane);
-                    const bool skip = lane >= NI || cand_mine < 0 || cand_mine == x0 ||
-                                      (same & ((1u << lane) - 1u)) != 0u;
-                    const unsigned todo = __ballot_sync(kFull, !skip);
-                    if (!skip) {
-                        contact_frame(ob, cand_mine, &s_cf[warp][lane][0]);
-                        s_list[warp][__popc(todo & ((1u << lane) - 1u))] = lane;
-                    }
-                    __syncwarp();
-                    const int n_todo = __popc(todo);
-                    float best = Jc, bestJ = J;
-                    int win = -1;  // the winning candidate
-                    for (int base = 0; base < n_todo; base += G) {
-                        const bool act = grp < G && base + grp < n_todo;
-                        const int c = act ? s_list[warp][base + grp] : 0;
-                        LaneLp s;
-                        bool warm = false;
-                        if (act && o.warm_start) {
-                            basis_load(s, s_basis[warp][b_cur][jl]);
-                            warm = lane_lp_repair(s, &s_cf[warp][c][0], i, K, kK, mu, a);
-                        }
-                        if (!warm) lane_lp_cold(s, kK);
-                        lane_lp_begin(s, jl * K, jl * K + K);
-                        n_warm += warm;
-                        const float sj = lanes_solve<KT>(s, act, MovedFrames{cur, &s_cf[warp][c][0], i}, k, K, jl, mu,
-                                                         a, n_piv, n_lp, flags);
-                        const float Jt_g = margin_from_lanes(sj, grp * k, k);
-                        const int n_here = min(G, n_todo - base);
-                        int win_g = -1;
-                        for (int q = 0; q < n_here; ++q) {  // in order
-                            const float Jt = __shfl_sync(kFull, Jt_g, q * k);
-                            const float Jtc = Jt <= o.zero_tol ? 0.f : Jt;
-                            if (Jtc < (1.f - o.min_gain) * best) {
-                                best = Jtc;
-                                bestJ = Jt;
-                                win_g = q;
-                            }
-                        }
-                        if (win_g >= 0) {
-                            win = s_list[warp][base + win_g];
-                            if (act && grp == win_g) basis_store(s_basis[warp][b_best][jl], s);
-                        }
-                    }
-                    if (win >= 0) {
-                        const int xc = __shfl_sync(kFull, cand_mine, win);
-                        if (i == 0) id[0] = xc; else if (i == 1) id[1] = xc; else if (i == 2) id[2] = xc; else id[3] = xc;
-                        Jc = best;
-                        J = bestJ;
-                        __syncwarp();
-                        if (lane < kContactFloats) cur[kContactFloats * i + lane] = s_cf[warp][win][lane];
-                        const int t = b_cur; b_cur = b_best; b_best = t;  // the winner's bases: the current tuple's
-                    }
-                    __syncwarp();
-                }
-            }
-            ++n_tup;
-        }
-        if (lane == 0) {
-            if (valid)
-                for (int d = 0; d < k; ++d) a.tuples[(size_t)u * k + d] = id[d];
-            a.margin[u] = J;
-            a.accept[u] = (uint8_t)(J <= a.eps);
+        bool moved = false;  // warp-uniform: some slot advanced, a job started or a trip ran
+        // Bookkeeping runs only when kOptRefill lanes are idle or none is busy, so the
+        // lanes' result stores and job set-ups run together rather than a few lanes at a time.
+        const unsigned idle0 = __ballot_sync(kFull, !act);
+        if (__popc(idle0) >= kOptRefill || idle0 == kFull) {
+        // ---- record the finished jobs: s_j, final basis, and the step's count
+        if (pend) {
+            OptSlotSmem<NI> &sl = ws.slot[jm];
+            sl.sres[jq] = unb ? INFINITY : lane_lp_value(s, jj * K, jj * K + K);
+            basis_store(sl.job[jq], s);
+            ++n_lp;
+            n_piv += (unsigned)s.it;
         }
         __syncwarp();
+        for (int m = 0; m < M; ++m) {
+            const int cnt = __popc(__ballot_sync(kFull, pend && jm == m));
+            if (cnt && lane == 0) {
+                OptSlot &st = ws.slot[m].st;
+                st.n_done += cnt;
+                if (st.n_done == st.n_jobs) st.phase = kSlotComplete;
+            }
+            if (cnt) moved = true;
+        }
+        pend = false;
+        __syncwarp();
+        // ---- A. tuples: fetch, project, complete (warp-uniform per slot)
+        for (int m = 0; m < M; ++m) {
+            OptSlotSmem<NI> &sl = ws.slot[m];
+            if (sl.st.phase == kSlotFree && !exhausted) {
+                unsigned u = 0;
+                if (lane == 0) u = atomicAdd(a.work, 1u);
+                u = __shfl_sync(kFull, u, 0);
+                moved = true;
+                if (u >= total) {
+                    exhausted = true;
+                    continue;
+                }
+                int id[CF_MAX_K] = {0, 0, 0, 0}, fg[CF_MAX_K] = {0, 0, 0, 0};
+                bool valid = true;
+                for (int d = 0; d < k; ++d) {
+                    id[d] = __ldg(a.tuples + (size_t)u * k + d);
+                    fg[d] = (int)__ldg(a.fingers + (size_t)u * k + d);
+                    valid = valid && id[d] >= 0 && id[d] < a.N && fg[d] < F;
+                }
+                if (!valid) {  // scored as unusable; the slot stays free
+                    if (lane == 0) {
+                        a.margin[u] = INFINITY;
+                        a.accept[u] = 0;
+                    }
+                    continue;
+                }
+                if (lane < k) contact_frame(ob, lane == 0 ? id[0] : lane == 1 ? id[1] : lane == 2 ? id[2] : id[3],
+                                            &sl.cur[lane][0]);
+                if (lane == 0) {
+                    sl.st.u = u;
+                    sl.st.pose = (int)(u / (unsigned)a.T);
+                    sl.st.tau = (int)(u % (unsigned)a.T);
+                    for (int d = 0; d < CF_MAX_K; ++d) {
+                        sl.st.id[d] = id[d];
+                        sl.st.fg[d] = fg[d];
+                    }
+                    sl.st.it = 0;
+                    sl.st.i = 0;
+                    sl.st.init = 1;
+                    sl.st.n_jobs = k;
+                    sl.st.n_assigned = 0;
+                    sl.st.n_done = 0;
+                    sl.st.phase = kSlotRun;
+                }
+                __syncwarp();
+                continue;
+            }
+            if (sl.st.phase == kSlotComplete) {
+                moved = true;
+                const int i = sl.st.i;
+                float J = sl.st.J, Jc = sl.st.Jc;
+                int win = -1;  // the winning candidate's rank
+                if (sl.st.init) {
+                    J = margin_from(sl.sres, k);
+                    Jc = J <= o.zero_tol ? 0.f : J;
+                } else {
+                    // the candidates' margins in parallel, then in order against the best so far
+                    const int n_todo = sl.st.n_todo;
+                    const float Jt_mine = lane < n_todo ? margin_from(sl.sres + lane * k, k) : INFINITY;
+                    float best = Jc;
+                    for (int g = 0; g < n_todo; ++g) {
+                        const float Jt = __shfl_sync(kFull, Jt_mine, g);
+                        const float Jtc = Jt <= o.zero_tol ? 0.f : Jt;
+                        if (Jtc < (1.f - o.min_gain) * best) {
+                            best = Jtc;
+                            J = Jt;
+                            win = g;
+                        }
+                    }
+                    if (win >= 0) Jc = best;
+                }
+                // the new current tuple's bases (and contact i's frame)
+                const int src = sl.st.init ? 0 : win * k;
+                if (sl.st.init || win >= 0) {
+                    for (int e = lane; e < k * (int)(sizeof(LpBasis) / 4); e += 32)
+                        reinterpret_cast<uint32_t *>(sl.base)[e] = reinterpret_cast<const uint32_t *>(sl.job + src)[e];
+                }
+                if (win >= 0 && lane < kContactFloats) sl.cur[i][lane] = sl.cand[win][lane];
+                __syncwarp();
+                if (lane == 0) {
+                    if (win >= 0) sl.st.id[i] = sl.cand_pt[win];
+                    sl.st.J = J;
+                    sl.st.Jc = Jc;
+                    int it = sl.st.it, ni = sl.st.i;
+                    if (!sl.st.init && ++ni == k) {
+                        ni = 0;
+                        ++it;
+                    }
+                    sl.st.it = it;
+                    sl.st.i = ni;
+                    sl.st.init = 0;
+                    if (Jc > 0.f && it < o.n_outer) {
+                        sl.st.phase = kSlotProject;
+                    } else {  // done: write the tuple out
+                        const unsigned u = sl.st.u;
+                        for (int d = 0; d < k; ++d) a.tuples[(size_t)u * k + d] = sl.st.id[d];
+                        a.margin[u] = J;
+                        a.accept[u] = (uint8_t)(J <= a.eps);
+                        sl.st.phase = kSlotFree;
+                    }
+                }
+                __syncwarp();
+                if (sl.st.phase == kSlotFree) ++n_tup;
+            }
+            if (sl.st.phase == kSlotProject) {
+                moved = true;
+                const int it = sl.st.it, i = sl.st.i, pose = sl.st.pose, tau = sl.st.tau;
+                const int x0 = sl.st.id[i], fi = sl.st.fg[i];
+                // tangent basis of nu = -n at the current point (Duff et al. 2017) and the mutated
+                // points in explicitly rounded FP32 operations (no contraction left to the compiler)
+                const float px = __ldg(a.px + x0), py = __ldg(a.py + x0), pz = __ldg(a.pz + x0);
+                const float vx = -__ldg(a.nx + x0), vy = -__ldg(a.ny + x0), vz = -__ldg(a.nz + x0);
+                const float sgn = copysignf(1.f, vz);
+                const float aa = __fdiv_rn(-1.f, __fadd_rn(sgn, vz));
+                const float bb = __fmul_rn(__fmul_rn(vx, vy), aa);
+                const float xx = __fadd_rn(1.f, __fmul_rn(__fmul_rn(__fmul_rn(sgn, vx), vx), aa));
+                const float xy = __fmul_rn(sgn, bb), xz = -__fmul_rn(sgn, vx);
+                const float yx = bb, yy = __fadd_rn(sgn, __fmul_rn(__fmul_rn(vy, vy), aa)), yz = -vy;
+                if (lane < NI) {  // candidate `lane`: one Box-Muller pair, FP64 then rounded to FP32
+                    const int c = lane;
+                    const uint32_t pid = (uint32_t)pose + a.pose_base;
+                    const uint4 w4 = philox4x32_10(
+                        make_uint4(pid, (uint32_t)tau, (uint32_t)((it * k + i) * blocks_per_draw + c / 2), 0xA162u),
+                        key);
+                    const uint32_t w0 = (c & 1) ? w4.z : w4.x, w1 = (c & 1) ? w4.w : w4.y;
+                    const double u1 = (double)((w0 >> 8) + 1u) * 5.9604644775390625e-8;  // (0, 1]
+                    const double u2 = (double)(w1 >> 8) * 5.9604644775390625e-8;         // [0, 1)
+                    const double r = sqrt(-2.0 * log(u1));
+                    double sd, cd;
+                    sincospi(2.0 * u2, &sd, &cd);
+                    const float g1 = (float)(r * cd), g2 = (float)(r * sd);
+                    const float sg = o.sigma;
+                    ws.xyz[c][0] = __fadd_rn(px, __fmul_rn(sg, __fadd_rn(__fmul_rn(g1, xx), __fmul_rn(g2, yx))));
+                    ws.xyz[c][1] = __fadd_rn(py, __fmul_rn(sg, __fadd_rn(__fmul_rn(g1, xy), __fmul_rn(g2, yy))));
+                    ws.xyz[c][2] = __fadd_rn(pz, __fmul_rn(sg, __fadd_rn(__fmul_rn(g1, xz), __fmul_rn(g2, yz))));
+                }
+                __syncwarp();
+                const int cand_mine = project_candidates<NI>(a, &ws.xyz[0][0], a.masks + ((size_t)pose * F + fi) * W,
+                                                             x0, px, py, pz, lane);
+                // candidates equal to the current point or to an earlier candidate cannot win
+                const unsigned same = __match_any_sync(kFull, lane < NI ? cand_mine : -2 - lane);
+                const bool skip = lane >= NI || cand_mine < 0 || cand_mine == x0 || (same & ((1u << lane) - 1u)) != 0u;
+                const unsigned todo = __ballot_sync(kFull, !skip);
+                if (!skip) {
+                    const int g = __popc(todo & ((1u << lane) - 1u));  // the candidate's rank
+                    contact_frame(ob, cand_mine, &sl.cand[g][0]);
+                    sl.cand_pt[g] = cand_mine;
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    const int n_todo = __popc(todo);
+                    sl.st.n_todo = n_todo;
+                    sl.st.n_jobs = n_todo * k;
+                    sl.st.n_assigned = 0;
+                    sl.st.n_done = 0;
+                    sl.st.phase = n_todo > 0 ? kSlotRun : kSlotComplete;
+                }
+                __syncwarp();
+            }
+        }
+        // ---- B. idle lanes take the next jobs, tuple by tuple
+        unsigned idle = __ballot_sync(kFull, !act);
+        bool fresh = false;
+        for (int m = 0; m < M && idle; ++m) {
+            OptSlotSmem<NI> &sl = ws.slot[m];
+            if (sl.st.phase != kSlotRun) continue;
+            const int n_assigned = sl.st.n_assigned;
+            const int take = min(sl.st.n_jobs - n_assigned, __popc(idle));
+            if (take <= 0) continue;
+            const int rank = __popc(idle & ((1u << lane) - 1u));
+            const bool mine = ((idle >> lane) & 1u) && rank < take;
+            if (mine) {
+                jm = m;
+                jq = n_assigned + rank;
+                fresh = true;
+            }
+            idle &= ~__ballot_sync(kFull, mine);
+            __syncwarp();
+            if (lane == 0) sl.st.n_assigned = n_assigned + take;
+            __syncwarp();
+            moved = true;
+        }
+        if (fresh) {  // set up the job's LP
+            OptSlotSmem<NI> &sl = ws.slot[jm];
+            bool warm = false;
+            if (sl.st.init) {
+                jj = jq;
+                fr = MovedFrames{&sl.cur[0][0], &sl.cur[0][0], -1};
+            } else {
+                const int g = jq / k, i = sl.st.i;
+                jj = jq - g * k;
+                fr = MovedFrames{&sl.cur[0][0], &sl.cand[g][0], i};
+                if (o.warm_start) {
+                    basis_load(s, sl.base[jj]);
+                    warm = lane_lp_repair(s, &sl.cand[g][0], i, K, kK, mu, a);
+                }
+            }
+            if (!warm) lane_lp_cold(s, kK);
+            n_warm += warm;
+            lane_lp_begin(s, jj * K, jj * K + K);
+            act = true;
+        }
+        }  // bookkeeping
+        // ---- C. one pricing + pivot trip of every lane with a job
+        if (__any_sync(kFull, act)) {
+            moved = true;
+            if (act) {
+                float de = 0.f;
+                const int e = lane_lp_price<KT>(s, fr, k, K, jj, mu, a, de);
+                bool end = e < 0;
+                unb = false;
+                if (!end && s.it == kMaxPivots) {
+                    flags |= CF_DEV_LP_PIVOT_CAP;
+                    end = true;
+                }
+                if (!end && !lane_lp_pivot<KT>(s, fr, e, de, K, kK, mu, a)) {
+                    unb = true;
+                    end = true;
+                }
+                if (end) {
+                    act = false;
+                    pend = true;
+                }
+            }
+        }
+        bool busy = __any_sync(kFull, pend);  // a result or a tuple still in flight
+        for (int m = 0; m < M; ++m) busy = busy || ws.slot[m].st.phase != kSlotFree;
+        if (!busy && exhausted) break;
+        if (!moved) {  // nothing to run and nothing to advance: cannot happen; stop rather than spin
+            flags |= CF_DEV_OPT_STALL;
+            break;
+        }
     }
 #pragma unroll
     for (int off = 16; off >= 1; off >>= 1) {
@@ -1238,23 +1395,32 @@ cudaError_t launch_optimize(const ScoreArgs &a, int n_outer, int n_inner, float 
     k_word_boxes<<<(unsigned)((a.W * 32 + 255) / 256), 256, 0, st>>>(a.px, a.py, a.pz, a.N, a.W, a.word_box);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
-    // persistent warps: as many blocks as fit at once (they take tuples from the work counter)
-    auto go = [&](auto kern) -> cudaError_t {
-        int sms = 0, per_sm = 0;
-        cudaError_t e = launch_shape((const void *)kern, kOptThreads, 0, &per_sm, &sms);
+    // persistent warps, kOptSlots tuples in flight each: as many blocks as fit at once (they take
+    // tuples from the work counter)
+    auto go = [&](auto kern, size_t smem) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
+        int sms = 0, per_sm = 0;
+        if ((e = launch_shape((const void *)kern, kOptThreads, smem, &per_sm, &sms)) != cudaSuccess) return e;
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
-        const int grid = (int)std::min<long long>((long long)sms * per_sm, (total + kOptWarps - 1) / kOptWarps);
-        kern<<<grid, kOptThreads, 0, st>>>(a, o, (unsigned)total);
+        const long long warps = (total + kOptSlots - 1) / kOptSlots;
+        const int grid = (int)std::min<long long>((long long)sms * per_sm, (warps + kOptWarps - 1) / kOptWarps);
+        kern<<<grid, kOptThreads, smem, st>>>(a, o, (unsigned)total);
         return cudaGetLastError();
     };
     const bool k8 = a.K == 8;
+#define CF_OPT(NI)                                                                                     \
+    case NI: {                                                                                         \
+        const size_t smem = sizeof(OptWarpSmem<NI, kOptSlots>) * kOptWarps;                           \
+        return k8 ? go(k_optimize_pool<NI, 8, kOptSlots>, smem) : go(k_optimize_pool<NI, 0, kOptSlots>, smem); \
+    }
     switch (n_inner) {
-        case 4: return k8 ? go(k_optimize_lanes<4, 8>) : go(k_optimize_lanes<4, 0>);
-        case 8: return k8 ? go(k_optimize_lanes<8, 8>) : go(k_optimize_lanes<8, 0>);
-        case 16: return k8 ? go(k_optimize_lanes<16, 8>) : go(k_optimize_lanes<16, 0>);
+        CF_OPT(4)
+        CF_OPT(8)
+        CF_OPT(16)
         default: return cudaErrorInvalidValue;
     }
+#undef CF_OPT
 }
 
 cudaError_t launch_sample_batch(const ScoreArgs *d_descs, const long long *d_pose0, int n_desc, long long total_poses,
