@@ -866,9 +866,11 @@ extern "C" int cf_optimize_tuples(const cf_points *obj, int32_t n_fingers, const
     a.F = n_fingers;
     a.masks = d_masks;
     cudaStream_t st = (cudaStream_t)stream;
-    // scratch: the work counter, then the per-word point boxes of the projections' pruning
+    // scratch: the work counter, then the point boxes of the projections' pruning: one per mask
+    // word, then one per chunk of 32 words
     void *scratch = nullptr;
-    const size_t box_off = 256, bytes = box_off + sizeof(float) * 6 * (size_t)std::max(a.W, 1);
+    const size_t box_off = 256,
+                 bytes = box_off + sizeof(float) * 6 * ((size_t)std::max(a.W, 1) + (size_t)(a.W + 31) / 32);
     if ((rc = pool_alloc(&scratch, bytes, st, "alloc optimisation scratch"))) return rc;
     unsigned int *work = (unsigned int *)scratch;
     cudaError_t e = cudaMemsetAsync(work, 0, sizeof(unsigned int), st);
@@ -878,7 +880,7 @@ extern "C" int cf_optimize_tuples(const cf_points *obj, int32_t n_fingers, const
         e = launch_optimize(a, opt->n_outer, opt->n_inner, opt->sigma, opt->zero_tol, opt->min_gain, opt->warm_start, st);
     }
     cudaError_t e2 = cudaFreeAsync(scratch, st);
-    if (e != cudaSuccess) return cuda_fail(e, "launch k_word_boxes / k_optimize_pool");
+    if (e != cudaSuccess) return cuda_fail(e, "launch k_word_boxes / k_chunk_boxes / k_optimize_pool");
     if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync(optimisation scratch)");
     return CF_OK;
 }

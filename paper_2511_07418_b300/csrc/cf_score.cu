@@ -257,6 +257,29 @@ __global__ void k_word_boxes(const float *__restrict__ px, const float *__restri
     }
 }
 
+// Bounding box of each chunk of 32 mask words (1,024 points) from the word boxes:
+// warp per chunk.  Chunk boxes follow the W word boxes.
+__global__ void k_chunk_boxes(float *__restrict__ box, int W) {
+    const int ch = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    const int n_ch = (W + 31) / 32;
+    if (ch >= n_ch) return;
+    const int w = 32 * ch + lane;
+    const bool ok = w < W;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float lo = ok ? box[6 * (size_t)w + c] : INFINITY, hi = ok ? box[6 * (size_t)w + 3 + c] : -INFINITY;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            lo = fminf(lo, __shfl_xor_sync(kFull, lo, o));
+            hi = fmaxf(hi, __shfl_xor_sync(kFull, hi, o));
+        }
+        if (lane == 0) {
+            box[6 * ((size_t)W + ch) + c] = lo;
+            box[6 * ((size_t)W + ch) + 3 + c] = hi;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Alg. 2: blockwise zeroth-order contact optimisation
 // ---------------------------------------------------------------------------
@@ -801,50 +824,71 @@ __device__ __forceinline__ int project_candidates(const ScoreArgs &a, const floa
     const float R = 2.f * rc * 1.0001f + 1e-6f;
     const float R2 = in_dom ? R * R : INFINITY;
     constexpr unsigned kAll = NI >= 32 ? 0xffffffffu : (1u << NI) - 1u;
-    for (int w0 = 0; w0 < W; w0 += 32) {
-        const int w = w0 + lane;
-        uint32_t bits = w < W ? __ldg(row + w) : 0u;
-        unsigned cmask = kAll;  // the candidates this word can serve
-        if (bits && R2 < INFINITY) {
-            const float *bx = a.word_box + 6 * (size_t)w;
+    // chunks of 32 words (1,024 points) first: a chunk whose box no candidate's ball reaches is skipped
+    const int n_ch = (W + 31) / 32;
+    const float *chunk_box = a.word_box + 6 * (size_t)W;
+    for (int c0 = 0; c0 < n_ch; c0 += 32) {
+        bool hit = c0 + lane < n_ch;
+        if (hit && R2 < INFINITY) {
+            const float *bx = chunk_box + 6 * (size_t)(c0 + lane);
             const float lx = __ldg(bx), ly = __ldg(bx + 1), lz = __ldg(bx + 2);
             const float hx = __ldg(bx + 3), hy = __ldg(bx + 4), hz = __ldg(bx + 5);
-            const float ex = fmaxf(fmaxf(lx - px, px - hx), 0.f);
-            const float ey = fmaxf(fmaxf(ly - py, py - hy), 0.f);
-            const float ez = fmaxf(fmaxf(lz - pz, pz - hz), 0.f);
-            if (ex * ex + ey * ey + ez * ez > R2) {
-                bits = 0u;  // every point of the word is farther
-            } else {
-                cmask = 0u;
+            hit = false;
 #pragma unroll
-                for (int c = 0; c < NI; ++c) {
-                    const float *qc = kCandRegs ? cq[kCandRegs ? c : 0] : cand + 3 * c;
-                    const float r2 = r2c[c];
-                    const float fx = fmaxf(fmaxf(lx - qc[0], qc[0] - hx), 0.f);
-                    const float fy = fmaxf(fmaxf(ly - qc[1], qc[1] - hy), 0.f);
-                    const float fz = fmaxf(fmaxf(lz - qc[2], qc[2] - hz), 0.f);
-                    if (fx * fx + fy * fy + fz * fz <= r2) cmask |= 1u << c;
-                }
-                if (!cmask) bits = 0u;
+            for (int c = 0; c < NI; ++c) {
+                const float *qc = kCandRegs ? cq[kCandRegs ? c : 0] : cand + 3 * c;
+                const float fx = fmaxf(fmaxf(lx - qc[0], qc[0] - hx), 0.f);
+                const float fy = fmaxf(fmaxf(ly - qc[1], qc[1] - hy), 0.f);
+                const float fz = fmaxf(fmaxf(lz - qc[2], qc[2] - hz), 0.f);
+                hit = hit || fx * fx + fy * fy + fz * fz <= r2c[c];
             }
         }
-        // each lane visits its points in ascending index order, as the (distance, index) reduction assumes
-        for (unsigned need = __ballot_sync(kFull, bits != 0u); need; need &= need - 1) {
-            const int b = __ffs(need) - 1;
-            const uint32_t wb = __shfl_sync(kFull, bits, b);
-            const unsigned wc = __shfl_sync(kFull, cmask, b);
-            const int x = 32 * (w0 + b) + lane;
-            if ((wb >> lane) & 1u) {
-                const float qx = __ldg(a.px + x), qy = __ldg(a.py + x), qz = __ldg(a.pz + x);
+        for (unsigned chm = __ballot_sync(kFull, hit); chm; chm &= chm - 1) {
+            const int w0 = 32 * (c0 + __ffs(chm) - 1);
+            const int w = w0 + lane;
+            uint32_t bits = w < W ? __ldg(row + w) : 0u;
+            unsigned cmask = kAll;  // the candidates this word can serve
+            if (bits && R2 < INFINITY) {
+                const float *bx = a.word_box + 6 * (size_t)w;
+                const float lx = __ldg(bx), ly = __ldg(bx + 1), lz = __ldg(bx + 2);
+                const float hx = __ldg(bx + 3), hy = __ldg(bx + 4), hz = __ldg(bx + 5);
+                const float ex = fmaxf(fmaxf(lx - px, px - hx), 0.f);
+                const float ey = fmaxf(fmaxf(ly - py, py - hy), 0.f);
+                const float ez = fmaxf(fmaxf(lz - pz, pz - hz), 0.f);
+                if (ex * ex + ey * ey + ez * ez > R2) {
+                    bits = 0u;  // every point of the word is farther
+                } else {
+                    cmask = 0u;
 #pragma unroll
-                for (int c = 0; c < NI; ++c) {
-                    if (!((wc >> c) & 1u)) continue;
-                    const float *qc = kCandRegs ? cq[kCandRegs ? c : 0] : cand + 3 * c;
-                    const float dx = __fsub_rn(qx, qc[0]), dy = __fsub_rn(qy, qc[1]), dz = __fsub_rn(qz, qc[2]);
-                    const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-                    if (d2 < bd[c]) {
-                        bd[c] = d2;
-                        bi[c] = x;
+                    for (int c = 0; c < NI; ++c) {
+                        const float *qc = kCandRegs ? cq[kCandRegs ? c : 0] : cand + 3 * c;
+                        const float r2 = r2c[c];
+                        const float fx = fmaxf(fmaxf(lx - qc[0], qc[0] - hx), 0.f);
+                        const float fy = fmaxf(fmaxf(ly - qc[1], qc[1] - hy), 0.f);
+                        const float fz = fmaxf(fmaxf(lz - qc[2], qc[2] - hz), 0.f);
+                        if (fx * fx + fy * fy + fz * fz <= r2) cmask |= 1u << c;
+                    }
+                    if (!cmask) bits = 0u;
+                }
+            }
+            // each lane visits its points in ascending index order, as the (distance, index) reduction assumes
+            for (unsigned need = __ballot_sync(kFull, bits != 0u); need; need &= need - 1) {
+                const int b = __ffs(need) - 1;
+                const uint32_t wb = __shfl_sync(kFull, bits, b);
+                const unsigned wc = __shfl_sync(kFull, cmask, b);
+                const int x = 32 * (w0 + b) + lane;
+                if ((wb >> lane) & 1u) {
+                    const float qx = __ldg(a.px + x), qy = __ldg(a.py + x), qz = __ldg(a.pz + x);
+#pragma unroll
+                    for (int c = 0; c < NI; ++c) {
+                        if (!((wc >> c) & 1u)) continue;
+                        const float *qc = kCandRegs ? cq[kCandRegs ? c : 0] : cand + 3 * c;
+                        const float dx = __fsub_rn(qx, qc[0]), dy = __fsub_rn(qy, qc[1]), dz = __fsub_rn(qz, qc[2]);
+                        const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+                        if (d2 < bd[c]) {
+                            bd[c] = d2;
+                            bi[c] = x;
+                        }
                     }
                 }
             }
@@ -1395,6 +1439,8 @@ cudaError_t launch_optimize(const ScoreArgs &a, int n_outer, int n_inner, float 
     k_word_boxes<<<(unsigned)((a.W * 32 + 255) / 256), 256, 0, st>>>(a.px, a.py, a.pz, a.N, a.W, a.word_box);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
+    k_chunk_boxes<<<(unsigned)(((a.W + 31) / 32 * 32 + 255) / 256), 256, 0, st>>>(a.word_box, a.W);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
     // persistent warps, kOptSlots tuples in flight each: as many blocks as fit at once (they take
     // tuples from the work counter)
     auto go = [&](auto kern, size_t smem) -> cudaError_t {
