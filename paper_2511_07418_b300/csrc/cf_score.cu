@@ -956,45 +956,63 @@ __device__ __forceinline__ void basis_load(LaneLp &s, const LpBasis &d) {
 // column of contact i is swapped for its own new version by a column-replacement
 // pivot on its row (B^-1 updated with u = B^-1 a_new), so the basis keeps its
 // variables; the basic values are then recomputed from the nonbasic bounds
-// (c' = 0, y = -1 or +1).  False when a replacement pivot is below 1e-4 (a near
+// (c' = 0, y = -1 or +1); with no basic column of contact i the basis and its
+// values stand as they are.  False when a replacement pivot is below 1e-4 (a near
 // singular basis) or the recomputed basis is infeasible beyond 1e-6.
 __device__ __forceinline__ bool lane_lp_repair(LaneLp &s, const float *fi, int i, int K, int kK, float mu,
                                                const ScoreArgs &a) {
     const int c0 = i * K, c1 = c0 + K;
+    unsigned rows = 0u;  // the rows whose basic variable is a column of contact i
+#pragma unroll
+    for (int r = 0; r < kRows; ++r)
+        if (s.beta[r] >= c0 && s.beta[r] < c1) rows |= 1u << r;
+    if (!rows) return true;  // B and the basic values stay as they are
     const Frame f = load_frame(fi);
+    while (rows) {  // in ascending row order
+        const int l = __ffs(rows) - 1;
+        rows &= rows - 1;
+        int me = 0;
 #pragma unroll
-    for (int l = 0; l < kRows; ++l) {
-        if (s.beta[l] >= c0 && s.beta[l] < c1) {
-            const int me = s.beta[l] - c0;
-            const float cm = a.cs[me] * mu, sm = a.sn[me] * mu;
-            float ae[kRows];
+        for (int r = 0; r < kRows; ++r)
+            if (r == l) me = s.beta[r] - c0;
+        const float cm = a.cs[me] * mu, sm = a.sn[me] * mu;
+        float ae[kRows];
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                ae[q] = -__fmaf_rn(sm, f.v[6 + q], __fmaf_rn(cm, f.v[3 + q], f.v[q]));
-                ae[3 + q] = -__fmaf_rn(sm, f.v[15 + q], __fmaf_rn(cm, f.v[12 + q], f.v[9 + q]));
-            }
-            float uu[kRows];
-#pragma unroll
-            for (int r = 0; r < kRows; ++r) {
-                float acc = 0.f;
-#pragma unroll
-                for (int c = 0; c < kRows; ++c) acc = __fmaf_rn(s.B[r][c], ae[c], acc);
-                uu[r] = acc;
-            }
-            if (!(fabsf(uu[l]) > 1e-4f)) return false;
-            const float inv = __frcp_rn(uu[l]);
-            float rowl[kRows];
-#pragma unroll
-            for (int c = 0; c < kRows; ++c) rowl[c] = __fmul_rn(s.B[l][c], inv);
-#pragma unroll
-            for (int r = 0; r < kRows; ++r) {
-                if (r == l) continue;
-#pragma unroll
-                for (int c = 0; c < kRows; ++c) s.B[r][c] = __fmaf_rn(-uu[r], rowl[c], s.B[r][c]);
-            }
-#pragma unroll
-            for (int c = 0; c < kRows; ++c) s.B[l][c] = rowl[c];
+        for (int q = 0; q < 3; ++q) {
+            ae[q] = -__fmaf_rn(sm, f.v[6 + q], __fmaf_rn(cm, f.v[3 + q], f.v[q]));
+            ae[3 + q] = -__fmaf_rn(sm, f.v[15 + q], __fmaf_rn(cm, f.v[12 + q], f.v[9 + q]));
         }
+        float uu[kRows], ul = 0.f;
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+            float acc = 0.f;
+#pragma unroll
+            for (int c = 0; c < kRows; ++c) acc = __fmaf_rn(s.B[r][c], ae[c], acc);
+            uu[r] = acc;
+            if (r == l) ul = acc;
+        }
+        if (!(fabsf(ul) > 1e-4f)) return false;
+        const float inv = __frcp_rn(ul);
+        // row l / u_l, the other rows minus u_r times it, with one-hot row weights (exact FMAs)
+        float oh[kRows], keep[kRows], g[kRows];
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+            oh[r] = r == l ? 1.f : 0.f;
+            keep[r] = r == l ? 0.f : 1.f;
+            g[r] = r == l ? -1.f : uu[r];
+        }
+        float rowl[kRows];
+#pragma unroll
+        for (int c = 0; c < kRows; ++c) {
+            float v = 0.f;
+#pragma unroll
+            for (int r = 0; r < kRows; ++r) v = __fmaf_rn(oh[r], s.B[r][c], v);
+            rowl[c] = __fmul_rn(v, inv);
+        }
+#pragma unroll
+        for (int r = 0; r < kRows; ++r)
+#pragma unroll
+            for (int c = 0; c < kRows; ++c) s.B[r][c] = __fmaf_rn(-g[r], rowl[c], __fmul_rn(keep[r], s.B[r][c]));
     }
     // B x_B = -N x_N: x_B = -sum over the nonbasic y_r of x_r B^-1 e_r
     float wn[kRows];
