@@ -95,3 +95,74 @@ def test_optimize_degenerate(cf):
     assert np.array_equal(gt2, tup)
     with pytest.raises(cf.CfError):
         _gpu(cf, w, soa, m, tup, fing, n_inner=5)
+
+
+def _parity(cf, w, soa, m, tup, fing, kw, bound=0.10):
+    gt, gm, ga = _gpu(cf, w, soa, m, tup, fing, **kw)
+    ot, om, oa, amb = CO.optimize_tuples(soa, m, tup, fing, w.T, w.mu, w.K, w.obj.centroid, w.obj.rho, w.eps, w.seed,
+                                         **{x: kw[x] for x in ("n_outer", "n_inner", "sigma", "zero_tol", "min_gain")})
+    assert cf.device_status() == 0
+    clear = ~amb
+    info = f"{w.name} k={w.k} K={w.K}: ambiguous {amb.mean():.4f}, changed {(ot != tup).any(-1).mean():.3f}"
+    print(info)
+    assert amb.mean() < bound, info
+    assert np.array_equal(gt[clear], ot[clear]), info
+    assert np.array_equal(np.isfinite(gm), np.isfinite(om)), info
+    fin = clear & np.isfinite(om)
+    err = np.abs(gm[fin] - np.maximum(om[fin], 0))
+    assert np.all(err <= 1e-4 * np.maximum(om[fin], w.eps)), (info, err.max())
+    firm = fin & (np.abs(om - w.eps) > 1e-4 * np.maximum(om, w.eps))
+    assert np.array_equal(ga[firm], oa[firm]), info
+    return gt, gm, ga
+
+
+@pytest.mark.parametrize("name,P,S,k,K", [("tiny_sphere", 8, 2048, 2, 6),    # even K off the K = 8 kernel
+                                          ("tiny_sphere", 8, 2048, 3, 5),    # odd K
+                                          ("hand16_superquadric", 2, 4096, 4, 8)])  # k * K = 32 columns
+def test_optimize_parity_shapes(cf, name, P, S, k, K):
+    """Other tuple sizes and pyramid edge counts: the kernel's run-time-K form and the widest tableau."""
+    w = synth.workload(name, P=P, S=S)
+    w.k, w.K = k, K
+    fd = oracle.Field(w.hand, w.q, w.inv_h, w.bins)
+    soa = w.obj.soa()
+    m, c = fd.query(soa, w.poses)
+    tup, fing = oracle.sample_tuples(m, c, w.obj.N, w.T, k, w.seed)
+    _parity(cf, w, soa, m, tup, fing, dict(n_outer=2, n_inner=8, sigma=0.005, zero_tol=1e-6, min_gain=1e-2,
+                                           warm_start=True))
+
+
+def test_optimize_invalid_tuples(cf):
+    """Tuples with a point outside the object are left as given, with margin +inf and no accept."""
+    w, soa, m, tup, fing = _inputs("tiny_sphere", 8, 2048)
+    tup = tup.copy()
+    bad = np.zeros(tup.shape[:2], bool)
+    bad[0, 3] = bad[2, 0] = bad[5, 7] = True
+    tup[0, 3, 1] = -1
+    tup[2, 0, 0] = w.obj.N
+    tup[5, 7, 2] = -5
+    gt, gm, ga = _parity(cf, w, soa, m, tup, fing, dict(n_outer=2, n_inner=8, sigma=0.005, zero_tol=1e-6,
+                                                        min_gain=1e-2, warm_start=True))
+    assert np.array_equal(gt[bad], tup[bad])
+    assert np.all(np.isinf(gm[bad])) and not ga[bad].any()
+
+
+def test_optimize_schedule_independent(cf):
+    """Each tuple's result depends only on the tuple: one launch over 4,096 tuples (warps recycle
+    their tuple slots many times) equals, bit for bit, launches over its first 8 poses and its
+    first pose alone (the draws' counters use the pose index, so leading subsets keep theirs)."""
+    w, soa, m, tup, fing = _inputs("hand16_superquadric", 64, 4096)
+    kw = dict(n_outer=2, n_inner=8, sigma=0.005, zero_tol=1e-6, min_gain=1e-2, warm_start=True)
+    prm = cf.score_params(w.T, w.k, w.mu, w.K, w.eps, w.obj.centroid, w.obj.rho, w.seed, tuples_given=True)
+    dsoa = torch.from_numpy(soa).cuda()
+    dm = torch.from_numpy(m.view(np.int32)).cuda()
+    f_all = torch.from_numpy(fing).cuda()
+    t_all = torch.from_numpy(tup.copy()).cuda()
+    m_all, a_all = cf.optimize_tuples(dsoa, w.hand.F, dm, prm, cf.opt_params(**kw), t_all, f_all)
+    for n in (8, 1):
+        t_n = torch.from_numpy(tup[:n].copy()).cuda()
+        m_n, a_n = cf.optimize_tuples(dsoa, w.hand.F, dm[:n].contiguous(), prm, cf.opt_params(**kw), t_n,
+                                      f_all[:n].contiguous())
+        assert torch.equal(t_n, t_all[:n]), n
+        assert torch.equal(m_n, m_all[:n]) and torch.equal(a_n, a_all[:n]), n
+    assert cf.device_status() == 0
+    assert (t_all.cpu().numpy() != tup).any(), "the optimisation moved no contact"
