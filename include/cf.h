@@ -386,13 +386,13 @@ typedef struct cf_opt_params {
     float min_gain;     /* a candidate replaces the best so far only when its margin is < (1 - min_gain) x best */
     int32_t warm_start; /* 1: a candidate's LP_j starts from the current tuple's optimal LP_j basis, its moved
                            contact's columns replaced by their new values (a column-replacement pivot where they
-                           are basic), when that basis stays feasible (Sec. 5.4 "A Free Lunch"); 0: from c' = 0
-                           or the previous LP's basis.  Margins agree either way (each LP is solved to its
-                           optimum). */
+                           are basic), when that basis stays feasible (Sec. 5.4 "A Free Lunch"); 0: from
+                           c' = 0.  Margins agree either way (each LP is solved to its optimum). */
 } cf_opt_params;
 
-/* Improves every valid tuple of d_tuples [P][T][k] in place (prm->tuples_given
- * must be 1; d_fingers [P][T][k] gives each contact's finger).  For it = 0 ..
+/* Improves every valid tuple of d_tuples [P][T][k] in place (Sec. 5.4, Alg. 2;
+ * prm->tuples_given must be 1; d_fingers [P][T][k] gives each contact's finger;
+ * d_masks [P][n_fingers][ceil(N/32)] the domains the projections use).  For it = 0 ..
  * n_outer-1 and each contact i: with (x, y) the Duff et al. 2017 basis of
  * nu = -n_i, candidate c = 0 .. n_inner-1 mutates p_i by sigma (g1 x + g2 y), with
  * (g1, g2) the Box-Muller pair of Philox4x32-10 words (2 (c mod 2), 2 (c mod 2)
@@ -403,8 +403,12 @@ typedef struct cf_opt_params {
  * on ties).  Starting from the current point, the candidates in order replace
  * the best so far when their closure margin is below (1 - min_gain) x best
  * (margins <= zero_tol count as 0); contact i moves to the final best.  d_margin / d_accept receive the
- * final tuple's margin and margin <= eps.  Invalid tuples (an id < 0) are left
- * unchanged with margin +inf.  Errors: CF_EINVAL, CF_ENOMEM, CF_ECUDA. */
+ * final tuple's margin and margin <= eps.  Invalid tuples (an id outside [0, N) or a
+ * finger >= n_fingers) are left unchanged with margin +inf.  Each tuple's result
+ * depends only on the tuple (its pose index, tau, points and domains), not on how
+ * the launch schedules tuples over warps.  Needs scratch from the library's pool
+ * (word and chunk boxes of the points, and the warps' LP bases).  Errors: CF_EINVAL,
+ * CF_ENOMEM, CF_ECUDA; device status CF_DEV_LP_PIVOT_CAP, CF_DEV_OPT_STALL. */
 int cf_optimize_tuples(const cf_points *obj, int32_t n_fingers, const uint32_t *d_masks, int32_t n_poses,
                        const cf_score_params *prm, const cf_opt_params *opt, int32_t *d_tuples,
                        const uint8_t *d_fingers, float *d_margin, uint8_t *d_accept, cf_stream stream);
