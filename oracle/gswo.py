@@ -9,7 +9,10 @@ A the 6 x 3k matrix whose column block i is [nu_i x_i y_i ; (r_i x nu_i, r_i x x
 r_i x y_i) / rho] (r_i = p_i - c), the objective of Eq. GSWO with lambda = 1 /
 rho^2 is |A z|^2.  Subproblem j fixes alpha_j = 1 (its friction then lies in the
 disc |b_j| <= mu); every other contact lies in the cone |b_i| <= mu alpha_i.
-J = min_j J_j.
+J = min_j J_j.  Eq. FSWO (frictionless) is the case mu = 0: every b is 0 and
+each subproblem is the nonnegative least-squares problem min |a_j + A' alpha'|^2,
+alpha' >= 0, over the normal columns; the paper notes that GSWO's optimum is a
+lower bound of FSWO's.
 
 The paper solves the subproblems by projected gradient descent.  Reading taken
 (the paper gives no schedule): projected gradient with Nesterov momentum
@@ -50,9 +53,10 @@ def gswo_matrix(p, n, c, rho) -> np.ndarray:
 
 
 def project_cone(a: float, b: np.ndarray, mu: float):
-    """Nearest point of {(a, b): |b| <= mu a} to (a, b) (second-order cone)."""
+    """Nearest point of {(a, b): |b| <= mu a, a >= 0} to (a, b) (second-order cone; at mu = 0 the
+    ray b = 0, a >= 0 of a frictionless contact, Eq. FSWO)."""
     s = float(np.linalg.norm(b))
-    if s <= mu * a:
+    if a >= 0.0 and s <= mu * a:
         return a, b
     if mu * s <= -a:
         return 0.0, np.zeros_like(b)

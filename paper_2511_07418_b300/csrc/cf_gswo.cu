@@ -31,13 +31,15 @@ struct GswoArgs {
     uint8_t *accept;
 };
 
-// Projection of (a, b1, b2) onto |b| <= mu a, without branches: inside the cone
-// the point stays, inside the polar cone it goes to 0, otherwise to
-// a' = (a + mu s) / (1 + mu^2), b' = (mu a' / s) b.  inv1m = 1 / (1 + mu^2).
+// Projection of (a, b1, b2) onto |b| <= mu a, a >= 0, without branches: inside
+// the cone the point stays, inside the polar cone it goes to 0, otherwise to
+// a' = (a + mu s) / (1 + mu^2), b' = (mu a' / s) b.  inv1m = 1 / (1 + mu^2).  At
+// mu = 0 the cone is the ray b = 0, a >= 0 (a frictionless contact, Eq. FSWO),
+// so a point with b = 0 is inside only when a >= 0.
 __device__ __forceinline__ void project_soc(float &a, float &b1, float &b2, float mu, float inv1m) {
     const float s2 = b1 * b1 + b2 * b2;
     const float s = sqrtf(s2);
-    const bool inside = s <= mu * a, polar = mu * s <= -a;
+    const bool inside = a >= 0.f && s <= mu * a, polar = mu * s <= -a;
     const float a2 = (a + mu * s) * inv1m;
     const float f = mu * a2 * rsqrtf(fmaxf(s2, 1e-30f));
     const float fa = inside ? a : (polar ? 0.f : a2);

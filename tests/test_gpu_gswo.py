@@ -67,3 +67,32 @@ def test_gswo_edge_cases(cf):
     assert abs(v[0, 0] - ref) <= 1e-5 * ref
     with pytest.raises(cf.CfError):
         cf.score_gswo(soa, cf.score_params(2, 1, w.mu, w.K, w.eps, w.obj.centroid, w.obj.rho, 0, True), t, 8)
+
+
+def test_fswo_parity(cf):
+    """Eq. FSWO is Eq. GSWO with mu = 0 (no friction: every beta is 0).  Sampled tuples against
+    the oracle, plus tuples that repeat one point: three equal pushes cannot cancel (alpha >= 0),
+    so J = |nu|^2 + |r x nu|^2 / rho^2 = 1 on the sphere (no torque about its centre)."""
+    w = synth.workload("tiny_sphere", P=4, S=2048)
+    fd = oracle.Field(w.hand, w.q, w.inv_h, w.bins)
+    soa = w.obj.soa()
+    m, c = fd.query(soa, w.poses)
+    tup, _ = oracle.sample_tuples(m, c, w.obj.N, w.T, w.k, w.seed)
+    tup = tup.copy()
+    tup[0, 0] = [5, 5, 5]
+    tup[1, 2] = [77, 77, 77]
+    prm = cf.score_params(w.T, w.k, 0.0, w.K, w.eps, w.obj.centroid, w.obj.rho, w.seed, tuples_given=True)
+    gv, ga = cf.score_gswo(torch.from_numpy(soa).cuda(), prm, torch.from_numpy(tup).cuda(), 256, EPS_G)
+    torch.cuda.synchronize()
+    gv, ga = gv.cpu().numpy().astype(np.float64), ga.cpu().numpy()
+    ov = G.score_gswo(soa, tup, 0.0, w.obj.centroid, w.obj.rho, 256)
+    fin = np.isfinite(ov)
+    assert np.array_equal(np.isfinite(gv), fin)
+    err = np.abs(gv[fin] - ov[fin]) / np.maximum(ov[fin], EPS_G)
+    print(f"FSWO: {fin.sum()} tuples, max relative error {err.max():.3g}, accept {ga[fin].mean():.3f}")
+    assert err.max() <= REL
+    for i, t in ((0, 0), (1, 2)):
+        r = soa[0:3, tup[i, t, 0]].astype(np.float64) - w.obj.centroid
+        nu = -soa[3:6, tup[i, t, 0]].astype(np.float64)
+        exact = float(nu @ nu + np.sum(np.cross(r, nu) ** 2) / w.obj.rho ** 2)
+        assert abs(gv[i, t] - exact) <= 1e-4 * exact and abs(ov[i, t] - exact) <= 1e-9, (gv[i, t], ov[i, t], exact)
