@@ -443,15 +443,36 @@ __device__ __forceinline__ int lane_lp_price(const LaneLp &s, const Frames &fr, 
                              s.pi[4] * f.v[13] + s.pi[5] * f.v[14];
             const float ga = s.pi[0] * f.v[6] + s.pi[1] * f.v[7] + s.pi[2] * f.v[8] + s.pi[3] * f.v[15] +
                              s.pi[4] * f.v[16] + s.pi[5] * f.v[17];
-            const float bem = mu * be, gam = mu * ga;
             const int ci = i * K;
+            if constexpr (KT > 0 && KT % 2 == 0) {
+                // edges m and m + K/2 lie at angles theta_m and theta_m + pi, so the better of the
+                // pair is al + mu |cs_m be + sn_m ga|, its sign naming the edge: K/2 evaluations
+                constexpr int KH = KT / 2;
+                float tm = -1.f;
+                int mm = 0;
 #pragma unroll
-            for (int m = 0; m < KM; ++m) {
-                if (KT == 0 && m >= K) break;
-                const float d = __fmaf_rn(a.sn[m], gam, __fmaf_rn(a.cs[m], bem, al));
+                for (int m = 0; m < KH; ++m) {
+                    const float t = __fmaf_rn(a.sn[m], ga, __fmul_rn(a.cs[m], be));
+                    if (fabsf(t) > tm) {
+                        tm = fabsf(t);
+                        mm = t >= 0.f ? m : m + KH;
+                    }
+                }
+                const float d = __fmaf_rn(mu, tm, al);
                 if (d > best) {
                     best = d;
-                    e = ci + m;
+                    e = ci + mm;
+                }
+            } else {
+                const float bem = mu * be, gam = mu * ga;
+#pragma unroll
+                for (int m = 0; m < KM; ++m) {
+                    if (KT == 0 && m >= K) break;
+                    const float d = __fmaf_rn(a.sn[m], gam, __fmaf_rn(a.cs[m], bem, al));
+                    if (d > best) {
+                        best = d;
+                        e = ci + m;
+                    }
                 }
             }
         }
