@@ -59,6 +59,11 @@ def _args():
     ap.add_argument("--served-rates", default="10,100,1000")
     ap.add_argument("--served-slots", type=int, default=256, help="engine slots (requests on the GPU at once)")
     ap.add_argument("--served-chunk", type=int, default=256, help="poses per request per engine round")
+    ap.add_argument("--served-chunk-max", type=int, default=2048,
+                    help="the adaptive_chunks streams: after its first round a request takes up to this many "
+                         "poses per round (<= --served-chunk: no such streams)")
+    ap.add_argument("--served-chunk-pairs", type=int, default=1 << 26,
+                    help="adaptive chunks: at most this many point-pose pairs per request and round (0: no limit)")
     ap.add_argument("--realized-steps", type=int, default=20, help="steps of the IK + realization leg (0: skip)")
     ap.add_argument("--optimized-steps", type=int, default=5, help="steps of the Alg. 2 optimisation leg (0: skip)")
     ap.add_argument("--gswo-steps", type=int, default=10, help="steps of the Eq. GSWO scoring leg (0: skip)")
@@ -548,7 +553,9 @@ def run_ours(args):
         if args.served_seconds > 0:
             rates = [float(x) for x in args.served_rates.split(",") if x]
             line["served"] = run_served(cf, torch, dev, ws, fields, rates, args.served_seconds,
-                                        max_active=args.served_slots, pose_chunk=args.served_chunk)
+                                        max_active=args.served_slots, pose_chunk=args.served_chunk,
+                                        pose_chunk_max=args.served_chunk_max,
+                                        chunk_pairs_max=args.served_chunk_pairs)
     if world == 1 and args.extra_workload and args.extra_workload != w.name:
         we = synth.workload(args.extra_workload)
         ex = main_leg(cf, torch, dev, we, args.extra_steps, args.warmup, flush, barrier)
@@ -870,7 +877,8 @@ def run_batched(cf, torch, dev, n_objects, ws, fields, n_range=(2048, 131072), p
     return out
 
 
-def run_served(cf, torch, dev, ws, fields, rates, seconds, pool=24, max_active=64, pose_chunk=256):
+def run_served(cf, torch, dev, ws, fields, rates, seconds, pool=24, max_active=64, pose_chunk=256, pose_chunk_max=0,
+               chunk_pairs_max=0):
     """Poisson request streams against the engine (continuous batching) and
     against the same engine with one slot (one request at a time, plain
     per-request launches); p50 / p99 latency and valid grasps/s per rate."""
@@ -887,8 +895,9 @@ def run_served(cf, torch, dev, ws, fields, rates, seconds, pool=24, max_active=6
         poses = synth.palm_poses(8192, 4000 + o, ws[hi].hand.grasp_centre, obj.centroid)
         objs.append((hi, obj.soa(), poses, obj))
 
-    def stream(max_active, rate, seconds=seconds, budget=64 << 30):
-        eng = cf.Engine(fields, hbm_budget_bytes=budget, max_active=max_active, pose_chunk=pose_chunk, pose_cap=65536)
+    def stream(max_active, rate, seconds=seconds, budget=64 << 30, chunk_max=pose_chunk_max):
+        eng = cf.Engine(fields, hbm_budget_bytes=budget, max_active=max_active, pose_chunk=pose_chunk, pose_cap=65536,
+                        pose_chunk_max=chunk_max, chunk_pairs_max=chunk_pairs_max)
         r = np.random.default_rng(int(rate) * 7 + max_active)
         t = 0.0
         arrivals = []
@@ -934,14 +943,21 @@ def run_served(cf, torch, dev, ws, fields, rates, seconds, pool=24, max_active=6
     out = {"continuous_batching": [], "one_at_a_time": [],
            "workload": f"Poisson arrivals, {seconds:g} s per rate; objects drawn from {pool} generated objects "
                        "(superquadric / tool, 1,024-65,536 points) with a random hand; 100-5,000 grasps requested; "
-                       f"8,192 candidate poses per request (pose cap 65,536), chunk {pose_chunk} poses, {max_active} slots, "
-                       "HBM budget 64 GiB"}
+                       f"8,192 candidate poses per request (pose cap 65,536), chunk {pose_chunk} poses "
+                       f"(adaptive_chunks: up to {pose_chunk_max} poses and {chunk_pairs_max} point-pose pairs after "
+                       f"the first round), {max_active} slots, HBM budget 64 GiB"}
     for rate in rates:
-        out["continuous_batching"].append(stream(max_active, rate))
-        out["one_at_a_time"].append(stream(1, rate, seconds=min(seconds, 5.0)))
+        out["continuous_batching"].append(stream(max_active, rate, chunk_max=0))
+        out["one_at_a_time"].append(stream(1, rate, seconds=min(seconds, 5.0), chunk_max=0))
+    # adaptive chunks: fewer rounds for requests that need many poses (a lower p99 at light and
+    # moderate load), longer rounds for everyone they share them with (a higher p99 at 1,000 req/s)
+    if pose_chunk_max > pose_chunk:
+        out["adaptive_chunks"] = [stream(max_active, rate, seconds=min(seconds, 10.0)) for rate in rates]
     # admission by HBM budget that binds: a 128 MiB budget holds only a few dozen requests' device state
-    out["budget_gated"] = stream(max_active, max(rates), seconds=min(seconds, 10.0), budget=128 << 20)
-    out["engine"] = {"max_active": max_active, "pose_chunk": pose_chunk}
+    # (fixed chunks: each request holds one chunk's state)
+    out["budget_gated"] = stream(max_active, max(rates), seconds=min(seconds, 10.0), budget=128 << 20, chunk_max=0)
+    out["engine"] = {"max_active": max_active, "pose_chunk": pose_chunk, "pose_chunk_max": pose_chunk_max,
+                     "chunk_pairs_max": chunk_pairs_max}
     return out
 
 

@@ -561,6 +561,17 @@ typedef struct cf_engine_params {
     int32_t max_active;             /* requests processed concurrently (slots) */
     int32_t pose_chunk;             /* poses of each active request per round */
     int32_t pose_cap;               /* poses a request may use before it ends with a partial result */
+    int32_t pose_chunk_max;         /* <= pose_chunk: every round takes pose_chunk poses.  Larger: after its
+                                       first round a request takes the poses that its acceptance so far says
+                                       it still needs (with 25 % to spare; twice its last chunk while it has
+                                       none), between pose_chunk and pose_chunk_max; its device state (and
+                                       budget share) is sized for min(pose_chunk_max, its pose limit).  The
+                                       chunks depend only on the request's own results, so a result is still
+                                       the same alone and in any mix. */
+    int64_t chunk_pairs_max;        /* with adaptive chunks, a chunk above pose_chunk also keeps chunk x n
+                                       (the query's point-pose pairs) <= chunk_pairs_max, so one large
+                                       object's round stays short for the requests it shares it with
+                                       (0: no limit) */
 } cf_engine_params;
 
 typedef struct cf_request {

@@ -46,6 +46,7 @@ struct EngReq {
     float *h_in = nullptr;  // page-locked: soa [6][n] then poses [n_poses][12]
     size_t h_in_bytes = 0;
     int limit = 0;  // poses this request may use
+    int cap = 0;    // poses its device state holds (the largest chunk it may take)
     // device state
     void *d_block = nullptr;
     size_t bytes = 0;
@@ -262,7 +263,7 @@ int admit_one(cf_engine *e, EngReq *r) {
     int rc = pool_alloc(&r->d_block, r->bytes, e->st, "alloc request");
     if (rc) return rc;
     char *p = (char *)r->d_block;
-    const size_t W = (size_t)(q.n + 31) / 32, T = q.prm.n_tuples, k = q.prm.k, c = (size_t)e->prm.pose_chunk;
+    const size_t W = (size_t)(q.n + 31) / 32, T = q.prm.n_tuples, k = q.prm.k, c = (size_t)r->cap;
     r->d_soa = (float *)p; p += align256(sizeof(float) * 6 * q.n);
     r->d_poses = (float *)p; p += align256(sizeof(float) * 12 * (size_t)q.n_poses);
     r->d_masks = (uint32_t *)p; p += align256(sizeof(uint32_t) * c * F * W);
@@ -279,6 +280,25 @@ int admit_one(cf_engine *e, EngReq *r) {
     return CF_OK;
 }
 
+// The poses a request takes this round: pose_chunk, or, with adaptive chunks after its first
+// round, the poses its acceptance so far says it still needs (25 % to spare; twice its last
+// chunk while it has accepted nothing), at most chunk_pairs_max / n of them, kept between
+// pose_chunk and its capacity.  Depends only on the request's own progress.
+int next_chunk(const cf_engine *e, const EngReq *r) {
+    const int left = r->limit - r->pose_next;
+    long long c = e->prm.pose_chunk;
+    if (r->pose_next > 0 && r->cap > e->prm.pose_chunk) {
+        const long long got = (long long)r->res_margin.size(), need = (long long)r->req.n_grasps - got;
+        if (got > 0)
+            c = (long long)ceil(1.25 * (double)need * (double)r->pose_next / (double)got);
+        else
+            c = 2LL * r->chunk;
+        if (e->prm.chunk_pairs_max > 0) c = std::min<long long>(c, e->prm.chunk_pairs_max / std::max(1, r->req.n));
+        c = std::max<long long>(c, e->prm.pose_chunk);
+    }
+    return (int)std::max<long long>(1, std::min<long long>({c, (long long)r->cap, (long long)left}));
+}
+
 // One round over the active requests.  Returns CF_OK or an error code.
 int run_round(cf_engine *e, std::vector<EngReq *> &act) {
     const int n = (int)act.size();
@@ -292,7 +312,7 @@ int run_round(cf_engine *e, std::vector<EngReq *> &act) {
     for (int i = 0; i < n; ++i) {
         EngReq *r = act[i];
         const cf_request &q = r->req;
-        r->chunk = std::min(e->prm.pose_chunk, r->limit - r->pose_next);
+        r->chunk = next_chunk(e, r);
         objs[i] = cf_points{r->d_soa, r->d_soa + q.n, r->d_soa + 2 * q.n, r->d_soa + 3 * q.n, r->d_soa + 4 * q.n,
                             r->d_soa + 5 * q.n, q.n};
         int rc = fill_score_args(&objs[i], r->fd->F, r->d_masks, r->d_counts, r->chunk, &q.prm, r->d_tuples,
@@ -589,7 +609,8 @@ extern "C" int cf_engine_submit(cf_engine *e, const cf_request *q, uint64_t *id)
     r->req.h_soa = nullptr;
     r->req.h_poses = nullptr;
     r->limit = std::min(q->n_poses, e->prm.pose_cap);
-    r->bytes = state_bytes(*q, r->fd->F, e->prm.pose_chunk);
+    r->cap = std::max(1, std::min(r->limit, std::max(e->prm.pose_chunk, e->prm.pose_chunk_max)));
+    r->bytes = state_bytes(*q, r->fd->F, r->cap);
     {
         std::lock_guard<std::mutex> lk(e->mu);
         r->id = e->next_id++;

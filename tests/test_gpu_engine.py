@@ -123,6 +123,48 @@ def test_first_chunk_equals_plain_calls(setup):
     assert np.array_equal(r["margin"][sel], mar.cpu().numpy()[acc])
 
 
+def test_adaptive_chunks(setup):
+    """Adaptive chunks (after the first round a request takes the poses its acceptance says it
+    still needs): results the same alone and in the mix; on the poses both forms processed,
+    the same accepted tuples as fixed chunks; never more rounds per request, fewer overall."""
+    cf, ws, fields, reqs = setup
+    fixed = cf.Engine(fields, max_active=16, pose_chunk=64)
+    for q in reqs:
+        fixed.submit(q["field"], q["soa"], q["poses"], q["prm"], q["n_grasps"], q["tag"])
+    ref = _collect(fixed, len(reqs))
+    fixed.close()
+    eng = cf.Engine(fields, max_active=16, pose_chunk=64, pose_chunk_max=1024)
+    alone = {}
+    for q in reqs:
+        eng.submit(q["field"], q["soa"], q["poses"], q["prm"], q["n_grasps"], q["tag"])
+        alone.update(_collect(eng, 1))
+    for q in reqs:
+        eng.submit(q["field"], q["soa"], q["poses"], q["prm"], q["n_grasps"], q["tag"])
+    mixed = _collect(eng, len(reqs))
+    eng.close()
+    for q in reqs:
+        a, f = mixed[q["tag"]], ref[q["tag"]]
+        _same(alone[q["tag"]], a)
+        assert a["n_accepted"] >= q["n_grasps"] or a["partial"]
+        assert a["n_rounds"] <= f["n_rounds"]
+        lim = min(a["n_poses_used"], f["n_poses_used"])
+        sa, sf = a["pose"] < lim, f["pose"] < lim
+        assert np.array_equal(a["pose"][sa], f["pose"][sf]) and np.array_equal(a["tuples"][sa], f["tuples"][sf])
+        assert np.array_equal(a["margin"][sa], f["margin"][sf])
+    assert sum(mixed[q["tag"]]["n_rounds"] for q in reqs) < sum(ref[q["tag"]]["n_rounds"] for q in reqs)
+    # a pair cap that never lets a chunk pass pose_chunk (every object has n >= 1,024): fixed chunks exactly
+    assert min(q["soa"].shape[1] for q in reqs) >= 1024
+    capped = cf.Engine(fields, max_active=16, pose_chunk=64, pose_chunk_max=1024, chunk_pairs_max=64 * 1024)
+    for q in reqs:
+        capped.submit(q["field"], q["soa"], q["poses"], q["prm"], q["n_grasps"], q["tag"])
+    got = _collect(capped, len(reqs))
+    capped.close()
+    for q in reqs:
+        _same(got[q["tag"]], ref[q["tag"]])
+        assert got[q["tag"]]["n_rounds"] == ref[q["tag"]]["n_rounds"]
+    assert cf.device_status() == 0
+
+
 def test_drain_is_a_bounded_wait(setup):
     """The engine's waits are on the host and bounded: a drain whose limit runs
     out while requests remain returns CF_ETIMEOUT (the engine keeps working), and
