@@ -38,9 +38,10 @@ L2_FLUSH_BYTES = 256 << 20
 # the current kernels per workload (dram__bytes_read.sum + dram__bytes_write.sum);
 # a workload or kernel without a capture of its current code reports None.
 # hand20_tool: captures at 4,096 of its 32,768 poses, scaled by 8 (the traffic grows with the poses).
-NCU_TRAFFIC = {"hand16_superquadric": {"k_query_domains": 2_243_328 + 11_180_800, "k_score_lanes": 6_723_072,
-                                       "k_fk_bin": 41_115_392 + 737_536, "k_sample_tuples": 67_269_376 + 928_512},
-               "hand20_tool": {"k_query_domains": 8 * (29_680_384 + 116_929_280), "k_score_lanes": 8 * 7_902_720}}
+NCU_TRAFFIC = {"hand16_superquadric": {"k_query_domains": 2_243_328 + 11_180_800, "k_score_lanes": 6_737_408 + 14_336,
+                                       "k_fk_bin": 41_115_392 + 737_536, "k_sample_tuples": 67_277_824 + 822_016},
+               "hand20_tool": {"k_query_domains": 8 * (29_575_168 + 116_316_416), "k_score_lanes": 8 * 7_904_768,
+                               "k_sample_tuples": 8 * (167_910_656 + 2_677_760)}}
 
 
 def _args():
