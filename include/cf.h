@@ -129,7 +129,8 @@ typedef struct cf_field_info {
     int32_t box_dims[3];               /* cells per axis (0 when the field is empty) */
     int32_t bits_per_finger;           /* 8, 16 or 32 */
     int32_t fingers_per_word;          /* 32 / bits_per_finger */
-    int32_t record_words;              /* ceil(n_slots / fingers_per_word) */
+    int32_t record_words;              /* ceil(n_slots / fingers_per_word) rounded up to 1, 2, 4, 8 or 16
+                                          (a record is whole aligned 16-byte loads; extra words are 0) */
     int32_t finger_lo[CF_MAX_FINGERS][3];   /* tight cell bounds of finger f's samples */
     int32_t finger_dims[CF_MAX_FINGERS][3]; /* (0 if the finger has no sample) */
     int64_t table_words;               /* total uint32 words of the bit table */

@@ -460,7 +460,7 @@ extern "C" int cf_build(const cf_hand_desc *hand, const cf_field_params *prm, co
     }
     g.bits = slot_bits_for(g.B);
     g.fpw = 32 / g.bits;
-    g.rw = (g.F + g.fpw - 1) / g.fpw;  // slots per record
+    g.rw = record_stride((g.F + g.fpw - 1) / g.fpw);  // words per record (padded to aligned loads)
     int64_t words = 0;
     if (lo[0] <= hi[0]) {
         for (int c = 0; c < 3; ++c) { g.lo[c] = lo[c]; g.dims[c] = hi[c] - lo[c] + 1; }
@@ -617,7 +617,7 @@ extern "C" int cf_field_destroy(cf_field *fd) {
 }
 
 namespace {
-const char kMagic[8] = {'C', 'F', 'F', 'I', 'E', 'L', 'D', '4'};
+const char kMagic[8] = {'C', 'F', 'F', 'I', 'E', 'L', 'D', '5'};
 }
 
 extern "C" int cf_field_save(const cf_field *fd, const char *path) {

@@ -86,6 +86,12 @@ struct FieldGeom {
 };
 
 inline int slot_bits_for(int B) { return B <= 8 ? 8 : (B <= 16 ? 16 : 32); }
+// Words per cell record in the table: the words the slots need, ceil(slots / slots per word),
+// rounded up to 1, 2, 4, 8 or 16 so a record is one or more aligned 16-byte loads (the extra
+// words stay zero).
+__host__ __device__ constexpr int record_stride(int words) {
+    return words <= 2 ? words : (words <= 4 ? 4 : (words <= 8 ? 8 : 16));
+}
 
 // Host: fill the candidate table for the given directions; returns the largest
 // per-cell candidate count.

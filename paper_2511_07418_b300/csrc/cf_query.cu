@@ -58,12 +58,15 @@ __device__ __forceinline__ void load_record(const uint32_t *__restrict__ r, uint
         const uint2 v = __ldg(reinterpret_cast<const uint2 *>(r));
         rec[0] = v.x;
         rec[1 % RW] = v.y;
-    } else if (RW == 4) {
-        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(r));
-        rec[0] = v.x;
-        rec[1 % RW] = v.y;
-        rec[2 % RW] = v.z;
-        rec[3 % RW] = v.w;
+    } else if (RW % 4 == 0) {
+#pragma unroll
+        for (int i = 0; i < RW / 4; ++i) {
+            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(r) + i);
+            rec[(4 * i) % RW] = v.x;
+            rec[(4 * i + 1) % RW] = v.y;
+            rec[(4 * i + 2) % RW] = v.z;
+            rec[(4 * i + 3) % RW] = v.w;
+        }
     } else {
 #pragma unroll
         for (int i = 0; i < RW; ++i) rec[i] = __ldg(r + i);
@@ -112,7 +115,7 @@ __device__ __forceinline__ void query_poses(const FieldGeom &g, const QueryDesc 
     const bool dilated = g.dilate_deg > 0.f;  // block-uniform
 
     constexpr int FPW = 32 / BITS;
-    constexpr int RW = (F + FPW - 1) / FPW;
+    constexpr int RW = record_stride((F + FPW - 1) / FPW);  // words per record (the table's stride)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int N = obj.n;
     const int B = g.B;
