@@ -63,6 +63,8 @@ def _args():
     ap.add_argument("--served-chunk-max", type=int, default=2048,
                     help="the adaptive_chunks streams: after its first round a request takes up to this many "
                          "poses per round (<= --served-chunk: no such streams)")
+    ap.add_argument("--served-reserve-gb", type=float, default=4.0,
+                    help="device memory each engine reserves in the library's pool at creation (GiB)")
     ap.add_argument("--served-chunk-pairs", type=int, default=1 << 26,
                     help="adaptive chunks: at most this many point-pose pairs per request and round (0: no limit)")
     ap.add_argument("--realized-steps", type=int, default=20, help="steps of the IK + realization leg (0: skip)")
@@ -556,7 +558,8 @@ def run_ours(args):
             line["served"] = run_served(cf, torch, dev, ws, fields, rates, args.served_seconds,
                                         max_active=args.served_slots, pose_chunk=args.served_chunk,
                                         pose_chunk_max=args.served_chunk_max,
-                                        chunk_pairs_max=args.served_chunk_pairs)
+                                        chunk_pairs_max=args.served_chunk_pairs,
+                                        reserve_bytes=int(args.served_reserve_gb * 2**30))
     if world == 1 and args.extra_workload and args.extra_workload != w.name:
         we = synth.workload(args.extra_workload)
         ex = main_leg(cf, torch, dev, we, args.extra_steps, args.warmup, flush, barrier)
@@ -879,7 +882,7 @@ def run_batched(cf, torch, dev, n_objects, ws, fields, n_range=(2048, 131072), p
 
 
 def run_served(cf, torch, dev, ws, fields, rates, seconds, pool=24, max_active=64, pose_chunk=256, pose_chunk_max=0,
-               chunk_pairs_max=0):
+               chunk_pairs_max=0, reserve_bytes=0):
     """Poisson request streams against the engine (continuous batching) and
     against the same engine with one slot (one request at a time, plain
     per-request launches); p50 / p99 latency and valid grasps/s per rate."""
@@ -898,7 +901,7 @@ def run_served(cf, torch, dev, ws, fields, rates, seconds, pool=24, max_active=6
 
     def stream(max_active, rate, seconds=seconds, budget=64 << 30, chunk_max=pose_chunk_max):
         eng = cf.Engine(fields, hbm_budget_bytes=budget, max_active=max_active, pose_chunk=pose_chunk, pose_cap=65536,
-                        pose_chunk_max=chunk_max, chunk_pairs_max=chunk_pairs_max)
+                        pose_chunk_max=chunk_max, chunk_pairs_max=chunk_pairs_max, reserve_bytes=min(budget, reserve_bytes))
         r = np.random.default_rng(int(rate) * 7 + max_active)
         t = 0.0
         arrivals = []
@@ -946,7 +949,8 @@ def run_served(cf, torch, dev, ws, fields, rates, seconds, pool=24, max_active=6
                        "(superquadric / tool, 1,024-65,536 points) with a random hand; 100-5,000 grasps requested; "
                        f"8,192 candidate poses per request (pose cap 65,536), chunk {pose_chunk} poses "
                        f"(adaptive_chunks: up to {pose_chunk_max} poses and {chunk_pairs_max} point-pose pairs after "
-                       f"the first round), {max_active} slots, HBM budget 64 GiB"}
+                       f"the first round), {max_active} slots, HBM budget 64 GiB, {reserve_bytes / 2**30:g} GiB of the "
+                       "library's pool reserved when each engine is created"}
     for rate in rates:
         out["continuous_batching"].append(stream(max_active, rate, chunk_max=0))
         out["one_at_a_time"].append(stream(1, rate, seconds=min(seconds, 5.0), chunk_max=0))
@@ -958,7 +962,7 @@ def run_served(cf, torch, dev, ws, fields, rates, seconds, pool=24, max_active=6
     # (fixed chunks: each request holds one chunk's state)
     out["budget_gated"] = stream(max_active, max(rates), seconds=min(seconds, 10.0), budget=128 << 20, chunk_max=0)
     out["engine"] = {"max_active": max_active, "pose_chunk": pose_chunk, "pose_chunk_max": pose_chunk_max,
-                     "chunk_pairs_max": chunk_pairs_max}
+                     "chunk_pairs_max": chunk_pairs_max, "reserve_bytes": reserve_bytes}
     return out
 
 

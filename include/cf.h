@@ -573,6 +573,9 @@ typedef struct cf_engine_params {
                                        (the query's point-pose pairs) <= chunk_pairs_max, so one large
                                        object's round stays short for the requests it shares it with
                                        (0: no limit) */
+    int64_t reserve_bytes;          /* device memory the engine grows the library's pool by at creation
+                                       (allocated and freed; the pool keeps freed memory), so the first
+                                       requests do not wait while the pool grows; 0: none */
 } cf_engine_params;
 
 typedef struct cf_request {

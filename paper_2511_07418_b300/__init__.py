@@ -123,7 +123,7 @@ class BatchItem(Structure):
 class EngineParams(Structure):
     _fields_ = [("fields", POINTER(c_void_p)), ("n_fields", c_int32), ("hbm_budget_bytes", c_int64),
                 ("max_active", c_int32), ("pose_chunk", c_int32), ("pose_cap", c_int32),
-                ("pose_chunk_max", c_int32), ("chunk_pairs_max", c_int64)]
+                ("pose_chunk_max", c_int32), ("chunk_pairs_max", c_int64), ("reserve_bytes", c_int64)]
 
 
 class Request(Structure):
@@ -586,13 +586,14 @@ class Engine:
     Results come back as dicts with the accepted tuples copied to numpy."""
 
     def __init__(self, fields, hbm_budget_bytes=64 << 30, max_active=64, pose_chunk=256, pose_cap=65536,
-                 pose_chunk_max=0, chunk_pairs_max=0):
-        """pose_chunk_max > pose_chunk: adaptive chunks (cf_engine_params.pose_chunk_max, chunk_pairs_max)."""
+                 pose_chunk_max=0, chunk_pairs_max=0, reserve_bytes=0):
+        """pose_chunk_max > pose_chunk: adaptive chunks (cf_engine_params.pose_chunk_max, chunk_pairs_max);
+        reserve_bytes: device memory the library's pool grows by at creation."""
         self.fields = list(fields)
         arr = (c_void_p * len(self.fields))(*[f.handle.value for f in self.fields])
         self._arr = arr
         p = EngineParams(arr, len(self.fields), int(hbm_budget_bytes), int(max_active), int(pose_chunk),
-                         int(pose_cap), int(pose_chunk_max), int(chunk_pairs_max))
+                         int(pose_cap), int(pose_chunk_max), int(chunk_pairs_max), int(reserve_bytes))
         h = c_void_p()
         _check(_cf_engine_create(byref(p), byref(h)))
         self._h = h

@@ -562,6 +562,7 @@ extern "C" int cf_engine_create(const cf_engine_params *prm, cf_engine **out) {
     if (prm->n_fields < 1 || !prm->fields) return fail(CF_EINVAL, "no fields");
     if (prm->max_active < 1 || prm->pose_chunk < 1 || prm->pose_cap < 1 || prm->hbm_budget_bytes <= 0)
         return fail(CF_EINVAL, "max_active, pose_chunk, pose_cap and the budget must be positive");
+    if (prm->reserve_bytes < 0) return fail(CF_EINVAL, "reserve_bytes must be >= 0");
     cf_engine *e = new cf_engine();
     e->prm = *prm;
     for (int i = 0; i < prm->n_fields; ++i) {
@@ -581,6 +582,20 @@ extern "C" int cf_engine_create(const cf_engine_params *prm, cf_engine **out) {
     e->tune = current_tuning();
     cudaError_t err = cudaStreamCreateWithFlags(&e->st, cudaStreamNonBlocking);
     if (err != cudaSuccess) { delete e; return cuda_fail(err, "stream"); }
+    if (prm->reserve_bytes > 0) {  // grow the pool now (it keeps what is freed), not while admitting requests
+        void *p = nullptr;
+        int rc = pool_alloc(&p, (size_t)prm->reserve_bytes, e->st, "reserve engine memory");
+        if (rc == CF_OK) {
+            err = cudaFreeAsync(p, e->st);
+            if (err == cudaSuccess) err = cudaStreamSynchronize(e->st);
+            if (err != cudaSuccess) rc = cuda_fail(err, "reserve engine memory");
+        }
+        if (rc != CF_OK) {
+            cudaStreamDestroy(e->st);
+            delete e;
+            return rc;
+        }
+    }
     e->t0 = std::chrono::steady_clock::now();
     e->worker = std::thread(worker_main, e);
     *out = e;

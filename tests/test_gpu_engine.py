@@ -165,6 +165,18 @@ def test_adaptive_chunks(setup):
     assert cf.device_status() == 0
 
 
+def test_reserve_grows_the_pool(setup):
+    """reserve_bytes grows the library's pool at creation; freed memory stays reserved."""
+    cf, ws, fields, reqs = setup
+    r = 96 << 20
+    eng = cf.Engine(fields, max_active=2, pose_chunk=64, reserve_bytes=r)
+    reserved = cf.pool_usage()["reserved"]
+    eng.close()
+    assert reserved >= r
+    with pytest.raises(cf.CfError):
+        cf.Engine(fields, max_active=2, pose_chunk=64, reserve_bytes=-1)
+
+
 def test_drain_is_a_bounded_wait(setup):
     """The engine's waits are on the host and bounded: a drain whose limit runs
     out while requests remain returns CF_ETIMEOUT (the engine keeps working), and
