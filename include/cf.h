@@ -68,8 +68,6 @@ enum {
 #define CF_DEV_LP_UNBOUNDED 0x2u   /* reserved (the scaled LP reads an unbounded ratio test as margin 0) */
 #define CF_DEV_REP_FULL 0x4u       /* the representative table had no free slot (cannot happen at load <= 1/2) */
 #define CF_DEV_REP_MISS 0x8u       /* an IK contact's code has no representative (tuple not from this field) */
-#define CF_DEV_OPT_STALL 0x10u     /* an Alg. 2 warp had no LP to run and no step to advance (cannot happen);
-                                      it stopped, leaving its tuples in flight unwritten */
 #define CF_DEV_BIN_RANGE 0x80000000u /* a build sample fell outside the table box (cannot happen) */
 
 typedef void *cf_stream; /* cudaStream_t */
@@ -408,8 +406,9 @@ typedef struct cf_opt_params {
  * finger >= n_fingers) are left unchanged with margin +inf.  Each tuple's result
  * depends only on the tuple (its pose index, tau, points and domains), not on how
  * the launch schedules tuples over warps.  Needs scratch from the library's pool
- * (word and chunk boxes of the points, and the warps' LP bases).  Errors: CF_EINVAL,
- * CF_ENOMEM, CF_ECUDA; device status CF_DEV_LP_PIVOT_CAP, CF_DEV_OPT_STALL. */
+ * (word and chunk boxes of the points, and per tuple its candidates, their LP values and,
+ * with warm_start, its k optimal LP bases: ~740 bytes per tuple at n_inner 8, k 3).  Errors: CF_EINVAL,
+ * CF_ENOMEM, CF_ECUDA; device status CF_DEV_LP_PIVOT_CAP. */
 int cf_optimize_tuples(const cf_points *obj, int32_t n_fingers, const uint32_t *d_masks, int32_t n_poses,
                        const cf_score_params *prm, const cf_opt_params *opt, int32_t *d_tuples,
                        const uint8_t *d_fingers, float *d_margin, uint8_t *d_accept, cf_stream stream);

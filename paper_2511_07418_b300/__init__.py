@@ -44,7 +44,6 @@ CF_DEV_LP_PIVOT_CAP = 0x1
 CF_DEV_LP_UNBOUNDED = 0x2
 CF_DEV_REP_FULL = 0x4
 CF_DEV_REP_MISS = 0x8
-CF_DEV_OPT_STALL = 0x10
 
 
 class CfError(RuntimeError):

@@ -866,21 +866,25 @@ extern "C" int cf_optimize_tuples(const cf_points *obj, int32_t n_fingers, const
     a.F = n_fingers;
     a.masks = d_masks;
     cudaStream_t st = (cudaStream_t)stream;
-    // scratch: the work counter, then the point boxes of the projections' pruning: one per mask
-    // word, then one per chunk of 32 words
+    // scratch: the work counter, then the point boxes of the projections' pruning (one per mask
+    // word, then one per chunk of 32 words), then the per-tuple state of the phases
     void *scratch = nullptr;
     const size_t box_off = 256,
-                 bytes = box_off + sizeof(float) * 6 * ((size_t)std::max(a.W, 1) + (size_t)(a.W + 31) / 32);
+                 box_bytes = sizeof(float) * 6 * ((size_t)std::max(a.W, 1) + (size_t)(a.W + 31) / 32),
+                 state_off = box_off + (box_bytes + 255) / 256 * 256,
+                 bytes = state_off + optimize_state_bytes((long long)n_poses * prm->n_tuples, opt->n_inner, prm->k,
+                                                           opt->warm_start);
     if ((rc = pool_alloc(&scratch, bytes, st, "alloc optimisation scratch"))) return rc;
     unsigned int *work = (unsigned int *)scratch;
     cudaError_t e = cudaMemsetAsync(work, 0, sizeof(unsigned int), st);
     if (e == cudaSuccess) {
         a.work = work;
         a.word_box = (float *)((char *)scratch + box_off);
-        e = launch_optimize(a, opt->n_outer, opt->n_inner, opt->sigma, opt->zero_tol, opt->min_gain, opt->warm_start, st);
+        e = launch_optimize(a, opt->n_outer, opt->n_inner, opt->sigma, opt->zero_tol, opt->min_gain, opt->warm_start,
+                            (char *)scratch + state_off, st);
     }
     cudaError_t e2 = cudaFreeAsync(scratch, st);
-    if (e != cudaSuccess) return cuda_fail(e, "launch k_word_boxes / k_chunk_boxes / k_optimize_pool");
+    if (e != cudaSuccess) return cuda_fail(e, "launch the Alg. 2 phases");
     if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync(optimisation scratch)");
     return CF_OK;
 }

@@ -361,10 +361,13 @@ cudaError_t launch_sample_batch(const ScoreArgs *d_descs, const long long *d_pos
 cudaError_t launch_score_batch(const ScoreArgs &launch, const ScoreArgs *d_descs, const long long *d_tuple0, int n_desc,
                                long long total_tuples, cudaStream_t st);
 size_t score_smem_bytes(int F, int W, int T, int k, bool sampling);
-// Alg. 2 contact optimisation of the tuples in place (a.tuples / a.fingers given;
-// a.masks, a.work zeroed, margin / accept out); n_inner in {4, 8, 16}
+// Alg. 2 contact optimisation of the tuples in place (a.tuples / a.fingers given; a.masks;
+// margin / accept out; a.word_box: scratch for (W + ceil(W / 32)) point boxes); n_inner in
+// {4, 8, 16}.  state: device scratch of optimize_state_bytes(P * T, n_inner, k, warm_start)
+// bytes for the per-tuple state between the phases (k_opt_* kernels).
+size_t optimize_state_bytes(long long n, int n_inner, int k, int warm);
 cudaError_t launch_optimize(const ScoreArgs &a, int n_outer, int n_inner, float sigma, float zero_tol,
-                            float min_gain, int warm_start, cudaStream_t st);
+                            float min_gain, int warm_start, void *state, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // host helpers shared by the ABI translation units

@@ -285,8 +285,6 @@ __global__ void k_chunk_boxes(float *__restrict__ box, int W) {
 // ---------------------------------------------------------------------------
 constexpr int kOptThreads = 128;
 constexpr int kOptWarps = kOptThreads / 32;
-constexpr int kOptSlots = 2;   // tuples in flight per warp
-constexpr int kOptRefill = 8;  // idle lanes before an Alg. 2 warp records results and hands out jobs
 
 struct OptArgs {
     int n_outer, n_inner;
@@ -929,48 +927,9 @@ __device__ __forceinline__ int project_candidates(const ScoreArgs &a, const floa
 // ---------------------------------------------------------------------------
 // Alg. 2 on the lane simplex
 // ---------------------------------------------------------------------------
-// A lane's LP sees contact d's frame in the current tuple, except contact i, which the
-// trial moves to its candidate's frame.
-struct MovedFrames {
-    const float *cur;   // the current tuple's frames, kContactFloats apart
-    const float *cand;  // the moved contact's new frame
-    int i;              // the moved contact (-1: none)
-    __device__ __forceinline__ const float *operator()(int d) const {
-        return d == i ? cand : cur + kContactFloats * d;
-    }
-};
-
-// An optimal basis of one LP_j, kept between solves (50 words).
-struct LpBasis {
-    float B[kRows][kRows];
-    float xb[kRows];
-    int beta[kRows];
-    unsigned basic_x, ystat;
-};
-
-__device__ __forceinline__ void basis_store(LpBasis &d, const LaneLp &s) {
-#pragma unroll
-    for (int r = 0; r < kRows; ++r) {
-#pragma unroll
-        for (int c = 0; c < kRows; ++c) d.B[r][c] = s.B[r][c];
-        d.xb[r] = s.xb[r];
-        d.beta[r] = s.beta[r];
-    }
-    d.basic_x = s.basic_x;
-    d.ystat = s.ystat;
-}
-
-__device__ __forceinline__ void basis_load(LaneLp &s, const LpBasis &d) {
-#pragma unroll
-    for (int r = 0; r < kRows; ++r) {
-#pragma unroll
-        for (int c = 0; c < kRows; ++c) s.B[r][c] = d.B[r][c];
-        s.xb[r] = d.xb[r];
-        s.beta[r] = d.beta[r];
-    }
-    s.basic_x = d.basic_x;
-    s.ystat = d.ystat;
-}
+// An LP_j's optimal basis as kept between solves: B^-1 (36 words), the basic values (6), the
+// basic ids (6) and the status words basic_x, ystat.
+constexpr int kBasisWords = 50;
 
 // Warm start with repair (Sec. 5.4, "A Free Lunch"): s is an optimal basis of the
 // current tuple's LP_j; the trial moves contact i to the frame fi.  Each basic
@@ -1071,334 +1030,151 @@ __device__ __forceinline__ float margin_from(const float *v, int k) {
     return bs > 0.f ? __fdiv_rn(1.f, bs) : INFINITY;
 }
 
-// A tuple in flight on an Alg. 2 warp and the LP jobs of its current step.
-struct OptSlot {
-    unsigned u;                          // the tuple
-    int pose, tau;
-    int id[CF_MAX_K], fg[CF_MAX_K];      // its contacts and their fingers
-    float J, Jc;                         // its margin; the margin with values <= zero_tol read as 0
-    int it, i;                           // the step: outer iteration, moved contact
-    int phase;                           // kSlotFree / kSlotRun / kSlotProject / kSlotComplete
-    int init;                            // the step solves the tuple's own LPs (else its candidates')
-    int n_jobs, n_assigned, n_done;      // LP jobs of the step: job g * k + j = LP_j of candidate g
-    int n_todo;                          // candidates of the step
-};
-constexpr int kSlotFree = 0, kSlotRun = 1, kSlotProject = 2, kSlotComplete = 3;
+// ---------------------------------------------------------------------------
+// Alg. 2 in phases: every tuple of the launch advances one step at a time
+// ---------------------------------------------------------------------------
+// Sec. 5.4, Alg. 2, with every tuple of the launch in lockstep.  First each
+// tuple's own k LPs (from c' = 0; their optimal bases are kept) give its margin.
+// Then each step (outer iteration it, contact i) is a projection kernel (a warp
+// per tuple: n_in Gaussian mutations of p_i in its tangent plane, each projected
+// onto finger f_i's domain), an LP-job kernel (a lane per LP_j of a candidate,
+// warm-started from the tuple's optimal LP_j basis repaired for the moved
+// contact -- "A Free Lunch" -- or from c' = 0; jobs handed out across the whole
+// grid) and a selection kernel (a thread per tuple: the candidates, in order,
+// replace the best so far when their margin is lower by more than the relative
+// min_gain; margins <= zero_tol count as 0 and end the tuple).  With the warm
+// start a fourth kernel replays the winners' LPs from the same starts, which
+// gives back their optimal bases without storing every candidate's.  Each
+// tuple's result depends only on the tuple.
 
-template <int NI>
-struct __align__(16) OptSlotSmem {
-    float cur[CF_MAX_K][kContactFloats];  // the tuple's contact frames
-    float cand[NI][kContactFloats];       // the step's candidates' frames (by rank)
-    LpBasis base[CF_MAX_K];               // the tuple's optimal LP_j bases: the warm starts
-    LpBasis job[NI * CF_MAX_K];           // each job's final basis (the winner's become the tuple's)
-    float sres[NI * CF_MAX_K];            // each job's s_j
-    int cand_pt[NI];                      // each candidate's point
-    OptSlot st;
+// Per-tuple state between the phases (global memory).
+struct OptPhaseState {
+    float *J;        // [n] the tuple's margin (+inf: invalid tuple)
+    uint8_t *live;   // [n] 1 while the tuple is optimised (valid, margin above zero_tol)
+    float *base;     // word w of LP_j's optimal basis of tuple u at base[w * n * k + u * k + j]
+    int *cand;       // [n][NI] the step's candidate points, by rank
+    int *n_todo;     // [n] the step's candidates
+    float *sres;     // [n][NI * k] s_j of job g * k + j (the tuple's own LPs: j)
+    int *win;        // [n] the step's winning rank, -1 when none
 };
+constexpr int kJobInit = 0;  // LP_j of the tuple itself, from c' = 0; its basis is kept
+constexpr int kJobCand = 1;  // LP_j of candidate g, warm-started (counted in the device counters)
+constexpr int kJobWin = 2;   // LP_j of the step's winner, replayed to keep its basis (not counted)
 
-template <int NI, int M>
-struct OptWarpSmem {
-    OptSlotSmem<NI> slot[M];
-    float xyz[NI][3];  // the mutated points being projected
-};
+__device__ __forceinline__ void basis_store_g(float *base, size_t stride, size_t at, const LaneLp &s) {
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+#pragma unroll
+        for (int c = 0; c < kRows; ++c) base[(size_t)(r * kRows + c) * stride + at] = s.B[r][c];
+        base[(size_t)(36 + r) * stride + at] = s.xb[r];
+        base[(size_t)(42 + r) * stride + at] = __int_as_float(s.beta[r]);
+    }
+    base[(size_t)48 * stride + at] = __uint_as_float(s.basic_x);
+    base[(size_t)49 * stride + at] = __uint_as_float(s.ystat);
+}
 
-// Alg. 2 with a job pool per warp (persistent warps, work counter).  A warp keeps M
-// tuples in flight.  Each tuple advances by steps: first its own k closure LPs;
-// then per outer iteration and contact i, NI Gaussian mutations of p_i in its
-// tangent plane (Box-Muller on Philox4x32-10 words) projected onto finger f_i's
-// domain (project_candidates, the whole warp), after which the step's jobs are
-// the candidates' LPs, LP_j of candidate g.  Idle lanes take the next job of any
-// tuple in flight and solve it with the lane simplex: a tuple's own LPs from
-// c' = 0, a candidate's LP_j from the tuple's optimal LP_j basis repaired for
-// the moved contact (Sec. 5.4, "A Free Lunch"; c' = 0 when the repair fails or
-// warm_start is off).  When a step's last job ends, its candidates replace the
-// best so far in order when their margin is lower by more than the relative
-// min_gain (margins <= zero_tol count as 0), so the margin never increases, and
-// the winner's bases become the tuple's.  Lanes thus stay busy while other
-// tuples wait for their slowest LP, and every job's LP runs as it would alone.
-template <int NI, int KT, int M>
-__global__ void __launch_bounds__(kOptThreads) k_optimize_pool(const ScoreArgs a, const OptArgs o, unsigned total) {
-    extern __shared__ __align__(16) unsigned char s_opt[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    OptWarpSmem<NI, M> &ws = reinterpret_cast<OptWarpSmem<NI, M> *>(s_opt)[warp];
-    const int k = a.k, K = KT > 0 ? KT : a.K, kK = k * K, F = a.F, W = a.W;
+__device__ __forceinline__ void basis_load_g(LaneLp &s, const float *base, size_t stride, size_t at) {
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+#pragma unroll
+        for (int c = 0; c < kRows; ++c) s.B[r][c] = base[(size_t)(r * kRows + c) * stride + at];
+        s.xb[r] = base[(size_t)(36 + r) * stride + at];
+        s.beta[r] = __float_as_int(base[(size_t)(42 + r) * stride + at]);
+    }
+    s.basic_x = __float_as_uint(base[(size_t)48 * stride + at]);
+    s.ystat = __float_as_uint(base[(size_t)49 * stride + at]);
+}
+
+// LP jobs of one phase: job q is (tuple u, candidate g, LP j) with u = q / JPT, JPT = NI k
+// for candidates (k otherwise).  Lanes take jobs together, when `refill` of them wait or
+// none is busy, from the block's contiguous share; a job whose tuple or candidate does not
+// exist ends at once.  The contact frames live in the lane's stretch of shared memory.
+template <int KT, int MODE>
+__global__ void __launch_bounds__(kLaneThreads) k_opt_lp_jobs(const ScoreArgs a, const OptPhaseState ps, int NI,
+                                                              int i_moved, int warm, unsigned n_jobs) {
+    __shared__ __align__(16) float s_c[kLaneThreads * kLaneStride];
+    __shared__ unsigned s_next;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int k = a.k, K = KT > 0 ? KT : a.K, kK = k * K;
+    const int JPT = MODE == kJobCand ? NI * k : k, SPT = NI * k;  // jobs and result slots per tuple
+    const size_t nk = (size_t)a.P * a.T * k;                     // the bases' word stride
+    const int refill = min(max(a.refill, 1), 32);
     const float mu = a.mu;
     const LaneObj ob = lane_obj(a);
-    unsigned long long n_piv = 0, n_lp = 0, n_tup = 0, n_warm = 0;
-    unsigned flags = 0;
-    const uint2 key = make_uint2(a.seed_lo, a.seed_hi);
-    const int blocks_per_draw = (NI + 1) / 2;
-    if (lane == 0)
-        for (int m = 0; m < M; ++m) ws.slot[m].st.phase = kSlotFree;
-    __syncwarp();
-
+    float *cf = s_c + tid * kLaneStride;
+    const unsigned per = (n_jobs + gridDim.x - 1) / gridDim.x;
+    const unsigned q_lo = min(n_jobs, blockIdx.x * per), q_hi = min(n_jobs, q_lo + per);
+    if (tid == 0) s_next = q_lo;
+    __syncthreads();
+    constexpr int kIdle = 0, kInLp = 1, kDone = 2;
+    int state = kIdle;
     LaneLp s;
     lane_lp_cold(s, kK);
-    bool act = false;   // the lane is solving a job
-    bool pend = false;  // the lane holds a finished job's result, not yet recorded
-    bool unb = false;   // that job's LP was unbounded
-    int jm = 0, jq = 0; // its slot and job
-    int jj = 0;         // its LP's objective (contact j)
-    MovedFrames fr{&ws.slot[0].cur[0][0], &ws.slot[0].cur[0][0], -1};
-    bool exhausted = false;
-
+    const OwnFrames fr{cf};
+    unsigned u = 0;
+    int j = 0, g = 0;
+    unsigned long long n_piv = 0, n_lp = 0, n_warm = 0;
+    unsigned flags = 0;
     for (;;) {
-        bool moved = false;  // warp-uniform: some slot advanced, a job started or a trip ran
-        // Bookkeeping runs only when kOptRefill lanes are idle or none is busy, so the
-        // lanes' result stores and job set-ups run together rather than a few lanes at a time.
-        const unsigned idle0 = __ballot_sync(kFull, !act);
-        if (__popc(idle0) >= kOptRefill || idle0 == kFull) {
-        // ---- record the finished jobs: s_j, final basis, and the step's count
-        if (pend) {
-            OptSlotSmem<NI> &sl = ws.slot[jm];
-            sl.sres[jq] = unb ? INFINITY : lane_lp_value(s, jj * K, jj * K + K);
-            basis_store(sl.job[jq], s);
-            ++n_lp;
-            n_piv += (unsigned)s.it;
-        }
-        __syncwarp();
-        for (int m = 0; m < M; ++m) {
-            const int cnt = __popc(__ballot_sync(kFull, pend && jm == m));
-            if (cnt && lane == 0) {
-                OptSlot &st = ws.slot[m].st;
-                st.n_done += cnt;
-                if (st.n_done == st.n_jobs) st.phase = kSlotComplete;
-            }
-            if (cnt) moved = true;
-        }
-        pend = false;
-        __syncwarp();
-        // ---- A. tuples: fetch, project, complete (warp-uniform per slot)
-        for (int m = 0; m < M; ++m) {
-            OptSlotSmem<NI> &sl = ws.slot[m];
-            if (sl.st.phase == kSlotFree && !exhausted) {
-                unsigned u = 0;
-                if (lane == 0) u = atomicAdd(a.work, 1u);
-                u = __shfl_sync(kFull, u, 0);
-                moved = true;
-                if (u >= total) {
-                    exhausted = true;
-                    continue;
-                }
-                int id[CF_MAX_K] = {0, 0, 0, 0}, fg[CF_MAX_K] = {0, 0, 0, 0};
-                bool valid = true;
-                for (int d = 0; d < k; ++d) {
-                    id[d] = __ldg(a.tuples + (size_t)u * k + d);
-                    fg[d] = (int)__ldg(a.fingers + (size_t)u * k + d);
-                    valid = valid && id[d] >= 0 && id[d] < a.N && fg[d] < F;
-                }
-                if (!valid) {  // scored as unusable; the slot stays free
-                    if (lane == 0) {
-                        a.margin[u] = INFINITY;
-                        a.accept[u] = 0;
-                    }
-                    continue;
-                }
-                if (lane < k) contact_frame(ob, lane == 0 ? id[0] : lane == 1 ? id[1] : lane == 2 ? id[2] : id[3],
-                                            &sl.cur[lane][0]);
-                if (lane == 0) {
-                    sl.st.u = u;
-                    sl.st.pose = (int)(u / (unsigned)a.T);
-                    sl.st.tau = (int)(u % (unsigned)a.T);
-                    for (int d = 0; d < CF_MAX_K; ++d) {
-                        sl.st.id[d] = id[d];
-                        sl.st.fg[d] = fg[d];
-                    }
-                    sl.st.it = 0;
-                    sl.st.i = 0;
-                    sl.st.init = 1;
-                    sl.st.n_jobs = k;
-                    sl.st.n_assigned = 0;
-                    sl.st.n_done = 0;
-                    sl.st.phase = kSlotRun;
-                }
-                __syncwarp();
-                continue;
-            }
-            if (sl.st.phase == kSlotComplete) {
-                moved = true;
-                const int i = sl.st.i;
-                float J = sl.st.J, Jc = sl.st.Jc;
-                int win = -1;  // the winning candidate's rank
-                if (sl.st.init) {
-                    J = margin_from(sl.sres, k);
-                    Jc = J <= o.zero_tol ? 0.f : J;
+        const unsigned idle = __ballot_sync(kFull, state == kIdle);
+        const unsigned busy = __ballot_sync(kFull, state == kInLp);
+        if (idle && (__popc(idle) >= refill || busy == 0)) {
+            const int leader = __ffs(idle) - 1;
+            unsigned base_q = 0;
+            if (lane == leader) base_q = atomicAdd(&s_next, (unsigned)__popc(idle));
+            base_q = __shfl_sync(kFull, base_q, leader);
+            if (state == kIdle) {
+                const unsigned q = base_q + (unsigned)__popc(idle & ((1u << lane) - 1u));
+                if (q >= q_hi) {
+                    state = kDone;
                 } else {
-                    // the candidates' margins in parallel, then in order against the best so far
-                    const int n_todo = sl.st.n_todo;
-                    const float Jt_mine = lane < n_todo ? margin_from(sl.sres + lane * k, k) : INFINITY;
-                    float best = Jc;
-                    for (int g = 0; g < n_todo; ++g) {
-                        const float Jt = __shfl_sync(kFull, Jt_mine, g);
-                        const float Jtc = Jt <= o.zero_tol ? 0.f : Jt;
-                        if (Jtc < (1.f - o.min_gain) * best) {
-                            best = Jtc;
-                            J = Jt;
-                            win = g;
+                    u = q / (unsigned)JPT;
+                    const int r = (int)(q - u * (unsigned)JPT);
+                    g = MODE == kJobCand ? r / k : 0;
+                    j = r - g * k;
+                    bool run = ps.live[u] != 0;
+                    if (MODE == kJobCand) run = run && g < ps.n_todo[u];
+                    if (MODE == kJobWin) run = run && ps.win[u] >= 0;
+                    if (run) {
+                        for (int d = 0; d < k; ++d) {
+                            int x = __ldg(a.tuples + (size_t)u * k + d);
+                            if (MODE == kJobCand && d == i_moved) x = ps.cand[(size_t)u * NI + g];
+                            contact_frame(ob, x, cf + kContactFloats * d);
                         }
-                    }
-                    if (win >= 0) Jc = best;
-                }
-                // the new current tuple's bases (and contact i's frame)
-                const int src = sl.st.init ? 0 : win * k;
-                if (sl.st.init || win >= 0) {
-                    for (int e = lane; e < k * (int)(sizeof(LpBasis) / 4); e += 32)
-                        reinterpret_cast<uint32_t *>(sl.base)[e] = reinterpret_cast<const uint32_t *>(sl.job + src)[e];
-                }
-                if (win >= 0 && lane < kContactFloats) sl.cur[i][lane] = sl.cand[win][lane];
-                __syncwarp();
-                if (lane == 0) {
-                    if (win >= 0) sl.st.id[i] = sl.cand_pt[win];
-                    sl.st.J = J;
-                    sl.st.Jc = Jc;
-                    int it = sl.st.it, ni = sl.st.i;
-                    if (!sl.st.init && ++ni == k) {
-                        ni = 0;
-                        ++it;
-                    }
-                    sl.st.it = it;
-                    sl.st.i = ni;
-                    sl.st.init = 0;
-                    if (Jc > 0.f && it < o.n_outer) {
-                        sl.st.phase = kSlotProject;
-                    } else {  // done: write the tuple out
-                        const unsigned u = sl.st.u;
-                        for (int d = 0; d < k; ++d) a.tuples[(size_t)u * k + d] = sl.st.id[d];
-                        a.margin[u] = J;
-                        a.accept[u] = (uint8_t)(J <= a.eps);
-                        sl.st.phase = kSlotFree;
+                        bool ws = false;
+                        if (MODE != kJobInit && warm) {
+                            basis_load_g(s, ps.base, nk, (size_t)u * k + j);
+                            ws = lane_lp_repair(s, cf + kContactFloats * i_moved, i_moved, K, kK, mu, a);
+                        }
+                        if (!ws) lane_lp_cold(s, kK);
+                        if (MODE == kJobCand) n_warm += ws;
+                        lane_lp_begin(s, j * K, j * K + K);
+                        state = kInLp;
                     }
                 }
-                __syncwarp();
-                if (sl.st.phase == kSlotFree) ++n_tup;
-            }
-            if (sl.st.phase == kSlotProject) {
-                moved = true;
-                const int it = sl.st.it, i = sl.st.i, pose = sl.st.pose, tau = sl.st.tau;
-                const int x0 = sl.st.id[i], fi = sl.st.fg[i];
-                // tangent basis of nu = -n at the current point (Duff et al. 2017) and the mutated
-                // points in explicitly rounded FP32 operations (no contraction left to the compiler)
-                const float px = __ldg(a.px + x0), py = __ldg(a.py + x0), pz = __ldg(a.pz + x0);
-                const float vx = -__ldg(a.nx + x0), vy = -__ldg(a.ny + x0), vz = -__ldg(a.nz + x0);
-                const float sgn = copysignf(1.f, vz);
-                const float aa = __fdiv_rn(-1.f, __fadd_rn(sgn, vz));
-                const float bb = __fmul_rn(__fmul_rn(vx, vy), aa);
-                const float xx = __fadd_rn(1.f, __fmul_rn(__fmul_rn(__fmul_rn(sgn, vx), vx), aa));
-                const float xy = __fmul_rn(sgn, bb), xz = -__fmul_rn(sgn, vx);
-                const float yx = bb, yy = __fadd_rn(sgn, __fmul_rn(__fmul_rn(vy, vy), aa)), yz = -vy;
-                if (lane < NI) {  // candidate `lane`: one Box-Muller pair, FP64 then rounded to FP32
-                    const int c = lane;
-                    const uint32_t pid = (uint32_t)pose + a.pose_base;
-                    const uint4 w4 = philox4x32_10(
-                        make_uint4(pid, (uint32_t)tau, (uint32_t)((it * k + i) * blocks_per_draw + c / 2), 0xA162u),
-                        key);
-                    const uint32_t w0 = (c & 1) ? w4.z : w4.x, w1 = (c & 1) ? w4.w : w4.y;
-                    const double u1 = (double)((w0 >> 8) + 1u) * 5.9604644775390625e-8;  // (0, 1]
-                    const double u2 = (double)(w1 >> 8) * 5.9604644775390625e-8;         // [0, 1)
-                    const double r = sqrt(-2.0 * log(u1));
-                    double sd, cd;
-                    sincospi(2.0 * u2, &sd, &cd);
-                    const float g1 = (float)(r * cd), g2 = (float)(r * sd);
-                    const float sg = o.sigma;
-                    ws.xyz[c][0] = __fadd_rn(px, __fmul_rn(sg, __fadd_rn(__fmul_rn(g1, xx), __fmul_rn(g2, yx))));
-                    ws.xyz[c][1] = __fadd_rn(py, __fmul_rn(sg, __fadd_rn(__fmul_rn(g1, xy), __fmul_rn(g2, yy))));
-                    ws.xyz[c][2] = __fadd_rn(pz, __fmul_rn(sg, __fadd_rn(__fmul_rn(g1, xz), __fmul_rn(g2, yz))));
-                }
-                __syncwarp();
-                const int cand_mine = project_candidates<NI>(a, &ws.xyz[0][0], a.masks + ((size_t)pose * F + fi) * W,
-                                                             x0, px, py, pz, lane);
-                // candidates equal to the current point or to an earlier candidate cannot win
-                const unsigned same = __match_any_sync(kFull, lane < NI ? cand_mine : -2 - lane);
-                const bool skip = lane >= NI || cand_mine < 0 || cand_mine == x0 || (same & ((1u << lane) - 1u)) != 0u;
-                const unsigned todo = __ballot_sync(kFull, !skip);
-                if (!skip) {
-                    const int g = __popc(todo & ((1u << lane) - 1u));  // the candidate's rank
-                    contact_frame(ob, cand_mine, &sl.cand[g][0]);
-                    sl.cand_pt[g] = cand_mine;
-                }
-                __syncwarp();
-                if (lane == 0) {
-                    const int n_todo = __popc(todo);
-                    sl.st.n_todo = n_todo;
-                    sl.st.n_jobs = n_todo * k;
-                    sl.st.n_assigned = 0;
-                    sl.st.n_done = 0;
-                    sl.st.phase = n_todo > 0 ? kSlotRun : kSlotComplete;
-                }
-                __syncwarp();
             }
         }
-        // ---- B. idle lanes take the next jobs, tuple by tuple
-        unsigned idle = __ballot_sync(kFull, !act);
-        bool fresh = false;
-        for (int m = 0; m < M && idle; ++m) {
-            OptSlotSmem<NI> &sl = ws.slot[m];
-            if (sl.st.phase != kSlotRun) continue;
-            const int n_assigned = sl.st.n_assigned;
-            const int take = min(sl.st.n_jobs - n_assigned, __popc(idle));
-            if (take <= 0) continue;
-            const int rank = __popc(idle & ((1u << lane) - 1u));
-            const bool mine = ((idle >> lane) & 1u) && rank < take;
-            if (mine) {
-                jm = m;
-                jq = n_assigned + rank;
-                fresh = true;
-            }
-            idle &= ~__ballot_sync(kFull, mine);
-            __syncwarp();
-            if (lane == 0) sl.st.n_assigned = n_assigned + take;
-            __syncwarp();
-            moved = true;
+        if (__all_sync(kFull, state == kDone)) break;
+        if (state != kInLp) continue;
+        float de = 0.f;
+        const int e = lane_lp_price<KT>(s, fr, k, K, j, mu, a, de);
+        bool end = e < 0, unb = false;
+        if (!end && s.it == kMaxPivots) {
+            flags |= CF_DEV_LP_PIVOT_CAP;
+            end = true;
         }
-        if (fresh) {  // set up the job's LP
-            OptSlotSmem<NI> &sl = ws.slot[jm];
-            bool warm = false;
-            if (sl.st.init) {
-                jj = jq;
-                fr = MovedFrames{&sl.cur[0][0], &sl.cur[0][0], -1};
-            } else {
-                const int g = jq / k, i = sl.st.i;
-                jj = jq - g * k;
-                fr = MovedFrames{&sl.cur[0][0], &sl.cand[g][0], i};
-                if (o.warm_start) {
-                    basis_load(s, sl.base[jj]);
-                    warm = lane_lp_repair(s, &sl.cand[g][0], i, K, kK, mu, a);
-                }
-            }
-            if (!warm) lane_lp_cold(s, kK);
-            n_warm += warm;
-            lane_lp_begin(s, jj * K, jj * K + K);
-            act = true;
+        if (!end && !lane_lp_pivot<KT>(s, fr, e, de, K, kK, mu, a)) {
+            unb = true;
+            end = true;
         }
-        }  // bookkeeping
-        // ---- C. one pricing + pivot trip of every lane with a job
-        if (__any_sync(kFull, act)) {
-            moved = true;
-            if (act) {
-                float de = 0.f;
-                const int e = lane_lp_price<KT>(s, fr, k, K, jj, mu, a, de);
-                bool end = e < 0;
-                unb = false;
-                if (!end && s.it == kMaxPivots) {
-                    flags |= CF_DEV_LP_PIVOT_CAP;
-                    end = true;
-                }
-                if (!end && !lane_lp_pivot<KT>(s, fr, e, de, K, kK, mu, a)) {
-                    unb = true;
-                    end = true;
-                }
-                if (end) {
-                    act = false;
-                    pend = true;
-                }
+        if (end) {
+            if (MODE != kJobWin) {
+                ps.sres[(size_t)u * SPT + g * k + j] = unb ? INFINITY : lane_lp_value(s, j * K, j * K + K);
+                ++n_lp;
+                n_piv += (unsigned)s.it;
             }
-        }
-        bool busy = __any_sync(kFull, pend);  // a result or a tuple still in flight
-        for (int m = 0; m < M; ++m) busy = busy || ws.slot[m].st.phase != kSlotFree;
-        if (!busy && exhausted) break;
-        if (!moved) {  // nothing to run and nothing to advance: cannot happen; stop rather than spin
-            flags |= CF_DEV_OPT_STALL;
-            break;
+            if (MODE != kJobCand && ps.base) basis_store_g(ps.base, nk, (size_t)u * k + j, s);
+            state = kIdle;
         }
     }
 #pragma unroll
@@ -1409,12 +1185,131 @@ __global__ void __launch_bounds__(kOptThreads) k_optimize_pool(const ScoreArgs a
     }
     flags = __reduce_or_sync(kFull, flags);
     if (lane == 0) {
-        atomicAdd(a.counters + 0, n_piv);
-        atomicAdd(a.counters + 1, n_lp);
-        atomicAdd(a.counters + 2, n_tup);
-        atomicAdd(a.counters + 3, n_warm);
+        if (n_piv) atomicAdd(a.counters + 0, n_piv);
+        if (n_lp) atomicAdd(a.counters + 1, n_lp);
+        if (n_warm) atomicAdd(a.counters + 3, n_warm);
         if (flags) atomicOr(a.status, flags);
     }
+}
+
+// A thread per tuple: validity (points in range, fingers below F), the starting margin
+// +inf, and the count of valid tuples.
+__global__ void k_opt_begin(const ScoreArgs a, const OptPhaseState ps, unsigned n) {
+    const unsigned u = blockIdx.x * blockDim.x + threadIdx.x;
+    bool valid = false;
+    if (u < n) {
+        valid = true;
+        for (int d = 0; d < a.k; ++d) {
+            const int x = __ldg(a.tuples + (size_t)u * a.k + d);
+            const int f = (int)__ldg(a.fingers + (size_t)u * a.k + d);
+            valid = valid && x >= 0 && x < a.N && f < a.F;
+        }
+        ps.live[u] = valid ? 1 : 0;
+        ps.J[u] = INFINITY;
+        ps.win[u] = -1;
+    }
+    const unsigned c = __reduce_add_sync(kFull, valid ? 1u : 0u);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(a.counters + 2, (unsigned long long)c);
+}
+
+// A warp per live tuple: the NI mutations of contact i at outer iteration it (Box-Muller on
+// Philox4x32-10 words at counter (pose, tau, (it k + i) ceil(n_in / 2) + c / 2, 0xA162), key seed),
+// their projections onto finger f_i's
+// domain, and the distinct candidates other than the current point, by rank.
+template <int NI>
+__global__ void __launch_bounds__(kOptThreads) k_opt_project(const ScoreArgs a, const OptArgs o, const OptPhaseState ps,
+                                                             int it, int i, unsigned n) {
+    __shared__ float s_xyz[kOptWarps][NI][3];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int k = a.k, F = a.F, W = a.W;
+    const uint2 key = make_uint2(a.seed_lo, a.seed_hi);
+    const int blocks_per_draw = (NI + 1) / 2;
+    for (unsigned u = blockIdx.x * kOptWarps + warp; u < n; u += gridDim.x * kOptWarps) {
+        if (!ps.live[u]) {
+            if (lane == 0) ps.n_todo[u] = 0;
+            continue;
+        }
+        const int pose = (int)(u / (unsigned)a.T), tau = (int)(u % (unsigned)a.T);
+        const int x0 = __ldg(a.tuples + (size_t)u * k + i), fi = (int)__ldg(a.fingers + (size_t)u * k + i);
+        // tangent basis of nu = -n at the current point (Duff et al. 2017) and the mutated points in
+        // explicitly rounded FP32 operations
+        const float px = __ldg(a.px + x0), py = __ldg(a.py + x0), pz = __ldg(a.pz + x0);
+        const float vx = -__ldg(a.nx + x0), vy = -__ldg(a.ny + x0), vz = -__ldg(a.nz + x0);
+        const float sgn = copysignf(1.f, vz);
+        const float aa = __fdiv_rn(-1.f, __fadd_rn(sgn, vz));
+        const float bb = __fmul_rn(__fmul_rn(vx, vy), aa);
+        const float xx = __fadd_rn(1.f, __fmul_rn(__fmul_rn(__fmul_rn(sgn, vx), vx), aa));
+        const float xy = __fmul_rn(sgn, bb), xz = -__fmul_rn(sgn, vx);
+        const float yx = bb, yy = __fadd_rn(sgn, __fmul_rn(__fmul_rn(vy, vy), aa)), yz = -vy;
+        if (lane < NI) {  // candidate `lane`: one Box-Muller pair, FP64 then rounded to FP32
+            const uint32_t pid = (uint32_t)pose + a.pose_base;
+            const uint4 w4 = philox4x32_10(
+                make_uint4(pid, (uint32_t)tau, (uint32_t)((it * k + i) * blocks_per_draw + lane / 2), 0xA162u), key);
+            const uint32_t w0 = (lane & 1) ? w4.z : w4.x, w1 = (lane & 1) ? w4.w : w4.y;
+            const double u1 = (double)((w0 >> 8) + 1u) * 5.9604644775390625e-8;  // (0, 1]
+            const double u2 = (double)(w1 >> 8) * 5.9604644775390625e-8;         // [0, 1)
+            const double r = sqrt(-2.0 * log(u1));
+            double sd, cd;
+            sincospi(2.0 * u2, &sd, &cd);
+            const float g1 = (float)(r * cd), g2 = (float)(r * sd);
+            const float sg = o.sigma;
+            s_xyz[warp][lane][0] = __fadd_rn(px, __fmul_rn(sg, __fadd_rn(__fmul_rn(g1, xx), __fmul_rn(g2, yx))));
+            s_xyz[warp][lane][1] = __fadd_rn(py, __fmul_rn(sg, __fadd_rn(__fmul_rn(g1, xy), __fmul_rn(g2, yy))));
+            s_xyz[warp][lane][2] = __fadd_rn(pz, __fmul_rn(sg, __fadd_rn(__fmul_rn(g1, xz), __fmul_rn(g2, yz))));
+        }
+        __syncwarp();
+        const int cand_mine = project_candidates<NI>(a, &s_xyz[warp][0][0], a.masks + ((size_t)pose * F + fi) * W, x0,
+                                                     px, py, pz, lane);
+        // candidates equal to the current point or to an earlier candidate cannot win
+        const unsigned same = __match_any_sync(kFull, lane < NI ? cand_mine : -2 - lane);
+        const bool skip = lane >= NI || cand_mine < 0 || cand_mine == x0 || (same & ((1u << lane) - 1u)) != 0u;
+        const unsigned todo = __ballot_sync(kFull, !skip);
+        if (!skip) ps.cand[(size_t)u * NI + __popc(todo & ((1u << lane) - 1u))] = cand_mine;
+        if (lane == 0) ps.n_todo[u] = __popc(todo);
+        __syncwarp();
+    }
+}
+
+// A thread per tuple.  init: the margin of the tuple's own LPs.  Otherwise the step's
+// candidates, in order, replace the best so far when their margin is lower by more than
+// the relative min_gain (margins <= zero_tol count as 0); the winner's point becomes
+// contact i.  A tuple whose margin reaches zero_tol stops.
+__global__ void k_opt_select(const ScoreArgs a, const OptArgs o, const OptPhaseState ps, int NI, int i, int init,
+                             unsigned n) {
+    const unsigned u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n || !ps.live[u]) return;
+    const int k = a.k;
+    const float *sr = ps.sres + (size_t)u * NI * k;
+    float J = ps.J[u];
+    if (init) {
+        J = margin_from(sr, k);
+    } else {
+        const int n_todo = ps.n_todo[u];
+        float best = J <= o.zero_tol ? 0.f : J;
+        int win = -1;
+        for (int g = 0; g < n_todo; ++g) {
+            const float Jt = margin_from(sr + g * k, k);
+            const float Jtc = Jt <= o.zero_tol ? 0.f : Jt;
+            if (Jtc < (1.f - o.min_gain) * best) {
+                best = Jtc;
+                J = Jt;
+                win = g;
+            }
+        }
+        if (win >= 0) a.tuples[(size_t)u * k + i] = ps.cand[(size_t)u * NI + win];
+        ps.win[u] = win;
+    }
+    ps.J[u] = J;
+    if (!((J <= o.zero_tol ? 0.f : J) > 0.f)) ps.live[u] = 0;
+}
+
+// A thread per tuple: the final margin and accept flag.
+__global__ void k_opt_finish(const ScoreArgs a, const OptPhaseState ps, unsigned n) {
+    const unsigned u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    const float J = ps.J[u];
+    a.margin[u] = J;
+    a.accept[u] = (uint8_t)(J <= a.eps);
 }
 
 }  // namespace
@@ -1469,43 +1364,103 @@ cudaError_t launch_score(const ScoreArgs &a, cudaStream_t st) {
     return launch_score_lanes<false>(a, nullptr, nullptr, 0, (long long)a.P * a.T, st);
 }
 
+namespace {
+size_t align256z(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// The phase state's arrays inside one scratch block (see optimize_state_bytes).
+OptPhaseState phase_state(void *scratch, size_t n, int NI, int k, bool warm) {
+    char *p = (char *)scratch;
+    OptPhaseState ps;
+    ps.J = (float *)p; p += align256z(sizeof(float) * n);
+    ps.live = (uint8_t *)p; p += align256z(n);
+    ps.win = (int *)p; p += align256z(sizeof(int) * n);
+    ps.n_todo = (int *)p; p += align256z(sizeof(int) * n);
+    ps.cand = (int *)p; p += align256z(sizeof(int) * n * NI);
+    ps.sres = (float *)p; p += align256z(sizeof(float) * n * NI * k);
+    ps.base = warm ? (float *)p : nullptr;
+    return ps;
+}
+
+template <int KT, int MODE>
+cudaError_t launch_lp_jobs(const ScoreArgs &a, const OptPhaseState &ps, int NI, int i, int warm, unsigned long long n_jobs,
+                           cudaStream_t st) {
+    if (n_jobs == 0) return cudaSuccess;
+    int sms = 0, per_sm = 0;
+    cudaError_t e = launch_shape((const void *)k_opt_lp_jobs<KT, MODE>, kLaneThreads, 0, &per_sm, &sms);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    if (a.bpsm > 0) per_sm = std::min(per_sm, a.bpsm);
+    const int grid = (int)std::min<long long>((long long)sms * per_sm, (long long)((n_jobs + kLaneThreads - 1) / kLaneThreads));
+    k_opt_lp_jobs<KT, MODE><<<grid, kLaneThreads, 0, st>>>(a, ps, NI, i, warm, (unsigned)n_jobs);
+    return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t lp_jobs(const ScoreArgs &a, const OptPhaseState &ps, int NI, int i, int warm, unsigned long long n_jobs,
+                    cudaStream_t st) {
+    return a.K == 8 ? launch_lp_jobs<8, MODE>(a, ps, NI, i, warm, n_jobs, st)
+                    : launch_lp_jobs<0, MODE>(a, ps, NI, i, warm, n_jobs, st);
+}
+
+template <int NI>
+cudaError_t launch_project(const ScoreArgs &a, const OptArgs &o, const OptPhaseState &ps, int it, int i, unsigned n,
+                           cudaStream_t st) {
+    int sms = 0, per_sm = 0;
+    cudaError_t e = launch_shape((const void *)k_opt_project<NI>, kOptThreads, 0, &per_sm, &sms);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int grid = (int)std::min<long long>((long long)sms * per_sm, ((long long)n + kOptWarps - 1) / kOptWarps);
+    k_opt_project<NI><<<grid, kOptThreads, 0, st>>>(a, o, ps, it, i, n);
+    return cudaGetLastError();
+}
+}  // namespace
+
+size_t optimize_state_bytes(long long n, int n_inner, int k, int warm) {
+    const size_t N = (size_t)std::max<long long>(n, 1);
+    return align256z(sizeof(float) * N) + align256z(N) + 2 * align256z(sizeof(int) * N) +
+           align256z(sizeof(int) * N * n_inner) + align256z(sizeof(float) * N * n_inner * k) +
+           (warm ? sizeof(float) * (size_t)kBasisWords * N * k : 0);
+}
+
 cudaError_t launch_optimize(const ScoreArgs &a, int n_outer, int n_inner, float sigma, float zero_tol,
-                            float min_gain, int warm_start, cudaStream_t st) {
+                            float min_gain, int warm_start, void *state, cudaStream_t st) {
     if (a.P <= 0) return cudaSuccess;
-    const OptArgs o{n_outer, n_inner, sigma, zero_tol, min_gain, warm_start};
     const long long total = (long long)a.P * a.T;
-    if (!a.word_box) return cudaErrorInvalidValue;
+    if (!a.word_box || !state) return cudaErrorInvalidValue;
+    if (total * n_inner * a.k >= (1LL << 32)) return cudaErrorInvalidValue;
+    if (n_inner != 4 && n_inner != 8 && n_inner != 16) return cudaErrorInvalidValue;
+    const OptArgs o{n_outer, n_inner, sigma, zero_tol, min_gain, warm_start};
+    const unsigned n = (unsigned)total;
+    const int NI = n_inner, k = a.k;
+    const OptPhaseState ps = phase_state(state, n, NI, k, warm_start != 0);
+    cudaError_t err;
     k_word_boxes<<<(unsigned)((a.W * 32 + 255) / 256), 256, 0, st>>>(a.px, a.py, a.pz, a.N, a.W, a.word_box);
-    cudaError_t err = cudaGetLastError();
-    if (err != cudaSuccess) return err;
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
     k_chunk_boxes<<<(unsigned)(((a.W + 31) / 32 * 32 + 255) / 256), 256, 0, st>>>(a.word_box, a.W);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    // persistent warps, kOptSlots tuples in flight each: as many blocks as fit at once (they take
-    // tuples from the work counter)
-    auto go = [&](auto kern, size_t smem) -> cudaError_t {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        int sms = 0, per_sm = 0;
-        if ((e = launch_shape((const void *)kern, kOptThreads, smem, &per_sm, &sms)) != cudaSuccess) return e;
-        if (per_sm < 1) return cudaErrorInvalidConfiguration;
-        const long long warps = (total + kOptSlots - 1) / kOptSlots;
-        const int grid = (int)std::min<long long>((long long)sms * per_sm, (warps + kOptWarps - 1) / kOptWarps);
-        kern<<<grid, kOptThreads, smem, st>>>(a, o, (unsigned)total);
-        return cudaGetLastError();
-    };
-    const bool k8 = a.K == 8;
-#define CF_OPT(NI)                                                                                     \
-    case NI: {                                                                                         \
-        const size_t smem = sizeof(OptWarpSmem<NI, kOptSlots>) * kOptWarps;                           \
-        return k8 ? go(k_optimize_pool<NI, 8, kOptSlots>, smem) : go(k_optimize_pool<NI, 0, kOptSlots>, smem); \
+    const unsigned tb = (n + 255) / 256;
+    k_opt_begin<<<tb, 256, 0, st>>>(a, ps, n);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    // the tuples' own LPs, from c' = 0; their optimal bases seed the candidates
+    if ((err = lp_jobs<kJobInit>(a, ps, NI, 0, warm_start, (unsigned long long)n * k, st)) != cudaSuccess) return err;
+    k_opt_select<<<tb, 256, 0, st>>>(a, o, ps, NI, 0, 1, n);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    for (int it = 0; it < n_outer; ++it) {
+        for (int i = 0; i < k; ++i) {
+            err = NI == 4 ? launch_project<4>(a, o, ps, it, i, n, st)
+                          : (NI == 8 ? launch_project<8>(a, o, ps, it, i, n, st) : launch_project<16>(a, o, ps, it, i, n, st));
+            if (err != cudaSuccess) return err;
+            if ((err = lp_jobs<kJobCand>(a, ps, NI, i, warm_start, (unsigned long long)n * NI * k, st)) != cudaSuccess)
+                return err;
+            k_opt_select<<<tb, 256, 0, st>>>(a, o, ps, NI, i, 0, n);
+            if ((err = cudaGetLastError()) != cudaSuccess) return err;
+            // the winners' LPs again from the same starts: their optimal bases become the tuples'
+            if (warm_start && (err = lp_jobs<kJobWin>(a, ps, NI, i, 1, (unsigned long long)n * k, st)) != cudaSuccess)
+                return err;
+        }
     }
-    switch (n_inner) {
-        CF_OPT(4)
-        CF_OPT(8)
-        CF_OPT(16)
-        default: return cudaErrorInvalidValue;
-    }
-#undef CF_OPT
+    k_opt_finish<<<tb, 256, 0, st>>>(a, ps, n);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_sample_batch(const ScoreArgs *d_descs, const long long *d_pose0, int n_desc, long long total_poses,
