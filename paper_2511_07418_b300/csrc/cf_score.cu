@@ -847,26 +847,29 @@ __device__ __forceinline__ int project_candidates(const ScoreArgs &a, const floa
     const int n_ch = (W + 31) / 32;
     const float *chunk_box = a.word_box + 6 * (size_t)W;
     for (int c0 = 0; c0 < n_ch; c0 += 32) {
-        bool hit = c0 + lane < n_ch;
-        if (hit && R2 < INFINITY) {
+        // the candidates whose ball reaches this lane's chunk (a word's box lies inside its chunk's)
+        unsigned ccm = c0 + lane < n_ch ? kAll : 0u;
+        if (ccm && R2 < INFINITY) {
             const float *bx = chunk_box + 6 * (size_t)(c0 + lane);
             const float lx = __ldg(bx), ly = __ldg(bx + 1), lz = __ldg(bx + 2);
             const float hx = __ldg(bx + 3), hy = __ldg(bx + 4), hz = __ldg(bx + 5);
-            hit = false;
+            ccm = 0u;
 #pragma unroll
             for (int c = 0; c < NI; ++c) {
                 const float *qc = kCandRegs ? cq[kCandRegs ? c : 0] : cand + 3 * c;
                 const float fx = fmaxf(fmaxf(lx - qc[0], qc[0] - hx), 0.f);
                 const float fy = fmaxf(fmaxf(ly - qc[1], qc[1] - hy), 0.f);
                 const float fz = fmaxf(fmaxf(lz - qc[2], qc[2] - hz), 0.f);
-                hit = hit || fx * fx + fy * fy + fz * fz <= r2c[c];
+                if (fx * fx + fy * fy + fz * fz <= r2c[c]) ccm |= 1u << c;
             }
         }
-        for (unsigned chm = __ballot_sync(kFull, hit); chm; chm &= chm - 1) {
-            const int w0 = 32 * (c0 + __ffs(chm) - 1);
+        for (unsigned chm = __ballot_sync(kFull, ccm != 0u); chm; chm &= chm - 1) {
+            const int cb = __ffs(chm) - 1;
+            const unsigned chunk_cm = __shfl_sync(kFull, ccm, cb);  // uniform across the warp
+            const int w0 = 32 * (c0 + cb);
             const int w = w0 + lane;
             uint32_t bits = w < W ? __ldg(row + w) : 0u;
-            unsigned cmask = kAll;  // the candidates this word can serve
+            unsigned cmask = chunk_cm;  // the candidates this word can serve
             if (bits && R2 < INFINITY) {
                 const float *bx = a.word_box + 6 * (size_t)w;
                 const float lx = __ldg(bx), ly = __ldg(bx + 1), lz = __ldg(bx + 2);
@@ -880,6 +883,7 @@ __device__ __forceinline__ int project_candidates(const ScoreArgs &a, const floa
                     cmask = 0u;
 #pragma unroll
                     for (int c = 0; c < NI; ++c) {
+                        if (!((chunk_cm >> c) & 1u)) continue;  // its ball misses the whole chunk
                         const float *qc = kCandRegs ? cq[kCandRegs ? c : 0] : cand + 3 * c;
                         const float r2 = r2c[c];
                         const float fx = fmaxf(fmaxf(lx - qc[0], qc[0] - hx), 0.f);
