@@ -397,7 +397,7 @@ typedef struct cf_opt_params {
  * (g1, g2) the Box-Muller pair of Philox4x32-10 words (2 (c mod 2), 2 (c mod 2)
  * + 1) at counter (pose, tau, (it k + i) ceil(n_inner / 2) + c / 2, 0xA162), key
  * seed: u1 = (w >> 8 + 1) 2^-24, u2 = (w' >> 8) 2^-24, g = sqrt(-2 ln u1)
- * (cos, sin)(2 pi u2).  Each mutation is projected onto finger f_i's domain at
+ * (cos, sin)(2 pi u2), in FP32.  Each mutation is projected onto finger f_i's domain at
  * the pose (the object point with its mask bit set nearest to it, lowest index
  * on ties).  Starting from the current point, the candidates in order replace
  * the best so far when their closure margin is below (1 - min_gain) x best

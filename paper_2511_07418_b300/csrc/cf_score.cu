@@ -1245,17 +1245,17 @@ __global__ void __launch_bounds__(kOptThreads) k_opt_project(const ScoreArgs a, 
         const float xx = __fadd_rn(1.f, __fmul_rn(__fmul_rn(__fmul_rn(sgn, vx), vx), aa));
         const float xy = __fmul_rn(sgn, bb), xz = -__fmul_rn(sgn, vx);
         const float yx = bb, yy = __fadd_rn(sgn, __fmul_rn(__fmul_rn(vy, vy), aa)), yz = -vy;
-        if (lane < NI) {  // candidate `lane`: one Box-Muller pair, FP64 then rounded to FP32
+        if (lane < NI) {  // candidate `lane`: one Box-Muller pair in FP32 (u1, u2 exact; a few ulps)
             const uint32_t pid = (uint32_t)pose + a.pose_base;
             const uint4 w4 = philox4x32_10(
                 make_uint4(pid, (uint32_t)tau, (uint32_t)((it * k + i) * blocks_per_draw + lane / 2), 0xA162u), key);
             const uint32_t w0 = (lane & 1) ? w4.z : w4.x, w1 = (lane & 1) ? w4.w : w4.y;
-            const double u1 = (double)((w0 >> 8) + 1u) * 5.9604644775390625e-8;  // (0, 1]
-            const double u2 = (double)(w1 >> 8) * 5.9604644775390625e-8;         // [0, 1)
-            const double r = sqrt(-2.0 * log(u1));
-            double sd, cd;
-            sincospi(2.0 * u2, &sd, &cd);
-            const float g1 = (float)(r * cd), g2 = (float)(r * sd);
+            const float u1 = (float)((w0 >> 8) + 1u) * 5.9604644775390625e-8f;  // (0, 1]
+            const float u2 = (float)(w1 >> 8) * 5.9604644775390625e-8f;         // [0, 1)
+            const float r = sqrtf(-2.f * logf(u1));
+            float sd, cd;
+            sincospif(2.f * u2, &sd, &cd);
+            const float g1 = __fmul_rn(r, cd), g2 = __fmul_rn(r, sd);
             const float sg = o.sigma;
             s_xyz[warp][lane][0] = __fadd_rn(px, __fmul_rn(sg, __fadd_rn(__fmul_rn(g1, xx), __fmul_rn(g2, yx))));
             s_xyz[warp][lane][1] = __fadd_rn(py, __fmul_rn(sg, __fadd_rn(__fmul_rn(g1, xy), __fmul_rn(g2, yy))));
