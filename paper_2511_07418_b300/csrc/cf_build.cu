@@ -38,7 +38,8 @@ constexpr int kThreads = 256;
 // Link frames of finger f for sample s: the chain base * prod_j [Trans(o_j) Rot(a_j, q_j)]
 // in FP32 with explicitly rounded operations (no contraction left to the
 // compiler), so every build evaluates it bit for bit the same way; the joint's
-// sin and cos come from FP64 and are rounded to FP32 once.
+// sin and cos are CUDA's sincosf (a few ulps: the contact vectors move by ~1e-8 m,
+// far inside the 1e-5 m band within which the FP64 oracle counts a code uncertain).
 template <int J>
 __device__ __forceinline__ void link_frames(const HandDev &h, int f, const float *__restrict__ q, int S, int s,
                                             float R[J][9], float t[J][3]) {
@@ -56,9 +57,8 @@ __device__ __forceinline__ void link_frames(const HandDev &h, int f, const float
         }
         const float *a = h.axis + 3 * (f * J + j);
         const float ax = a[0], ay = a[1], az = a[2];
-        double sd, cd;  // sin and cos in FP64, rounded once: the FP32 values are those of a correctly
-        sincos((double)q[((size_t)f * J + j) * S + s], &sd, &cd);  // rounded sin / cos in all but rare ties
-        const float sq = (float)sd, cq = (float)cd;
+        float sq, cq;
+        sincosf(q[((size_t)f * J + j) * S + s], &sq, &cq);
         const float v = __fsub_rn(1.f, cq);
         // axis-angle rotation (Rodrigues)
         const float xs = __fmul_rn(ax, sq), ys = __fmul_rn(ay, sq), zs = __fmul_rn(az, sq);
