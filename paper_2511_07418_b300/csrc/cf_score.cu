@@ -1219,9 +1219,11 @@ __global__ void k_opt_begin(const ScoreArgs a, const OptPhaseState ps, unsigned 
 // A warp per live tuple: the NI mutations of contact i at outer iteration it (Box-Muller on
 // Philox4x32-10 words at counter (pose, tau, (it k + i) ceil(n_in / 2) + c / 2, 0xA162), key seed),
 // their projections onto finger f_i's
-// domain, and the distinct candidates other than the current point, by rank.
+// domain, and the distinct candidates other than the current point, by rank.  Bounded to 7
+// blocks per SM (72 registers): latency-bound scans gain more from warps than they lose to
+// a few spilled words.
 template <int NI>
-__global__ void __launch_bounds__(kOptThreads) k_opt_project(const ScoreArgs a, const OptArgs o, const OptPhaseState ps,
+__global__ void __launch_bounds__(kOptThreads, 7) k_opt_project(const ScoreArgs a, const OptArgs o, const OptPhaseState ps,
                                                              int it, int i, unsigned n) {
     __shared__ float s_xyz[kOptWarps][NI][3];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
