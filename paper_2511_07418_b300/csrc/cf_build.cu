@@ -39,7 +39,7 @@ constexpr int kThreads = 256;
 // in FP32 with explicitly rounded operations (no contraction left to the
 // compiler), so every build evaluates it bit for bit the same way; the joint's
 // sin and cos are CUDA's sincosf (a few ulps: the contact vectors move by ~1e-8 m,
-// far inside the 1e-5 m band within which the FP64 oracle counts a code uncertain).
+// far inside the 1e-5 m band within which an FP64 evaluation counts a code uncertain).
 template <int J>
 __device__ __forceinline__ void link_frames(const HandDev &h, int f, const float *__restrict__ q, int S, int s,
                                             float R[J][9], float t[J][3]) {
