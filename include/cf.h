@@ -407,7 +407,7 @@ typedef struct cf_opt_params {
  * depends only on the tuple (its pose index, tau, points and domains), not on how
  * the launch schedules tuples over warps.  Needs scratch from the library's pool
  * (word and chunk boxes of the points, and per tuple its candidates, their LP values and,
- * with warm_start, its k optimal LP bases: ~740 bytes per tuple at n_inner 8, k 3).  Errors: CF_EINVAL,
+ * with warm_start, its k optimal LP bases: ~840 bytes per tuple at n_inner 8, k 3).  Errors: CF_EINVAL,
  * CF_ENOMEM, CF_ECUDA; device status CF_DEV_LP_PIVOT_CAP. */
 int cf_optimize_tuples(const cf_points *obj, int32_t n_fingers, const uint32_t *d_masks, int32_t n_poses,
                        const cf_score_params *prm, const cf_opt_params *opt, int32_t *d_tuples,

@@ -1060,7 +1060,10 @@ struct OptPhaseState {
     int *n_todo;     // [n] the step's candidates
     float *sres;     // [n][NI * k] s_j of job g * k + j (the tuple's own LPs: j)
     int *win;        // [n] the step's winning rank, -1 when none
+    unsigned *jobs;    // the step's candidate LP jobs, u * 64 + g * 4 + j each, in no particular order
+    unsigned *n_jobs;  // their count (reset before each projection)
 };
+
 constexpr int kJobInit = 0;  // LP_j of the tuple itself, from c' = 0; its basis is kept
 constexpr int kJobCand = 1;  // LP_j of candidate g, warm-started (counted in the device counters)
 constexpr int kJobWin = 2;   // LP_j of the step's winner, replayed to keep its basis (not counted)
@@ -1089,18 +1092,21 @@ __device__ __forceinline__ void basis_load_g(LaneLp &s, const float *base, size_
     s.ystat = __float_as_uint(base[(size_t)49 * stride + at]);
 }
 
-// LP jobs of one phase: job q is (tuple u, candidate g, LP j) with u = q / JPT, JPT = NI k
-// for candidates (k otherwise).  Lanes take jobs together, when `refill` of them wait or
-// none is busy, from the block's contiguous share; a job whose tuple or candidate does not
-// exist ends at once.  The contact frames live in the lane's stretch of shared memory.
+// LP jobs of one phase.  Candidates: the job list the projection kernel wrote (descriptor
+// u * 64 + g * 4 + j: tuple u, candidate g, LP j; its length is read on the device).  A
+// tuple's own LPs and the winners' replays: slots u * k + j in tuple order (the jobs write
+// the bases, whose stores then stay sequential), a slot whose tuple has no such LP ending at
+// once.  Lanes take jobs together, when `refill` of them wait or none is busy, from the
+// block's contiguous share.  The contact frames live in the lane's stretch of shared memory.
 template <int KT, int MODE>
 __global__ void __launch_bounds__(kLaneThreads) k_opt_lp_jobs(const ScoreArgs a, const OptPhaseState ps, int NI,
-                                                              int i_moved, int warm, unsigned n_jobs) {
+                                                              int i_moved, int warm, unsigned n_slots) {
     __shared__ __align__(16) float s_c[kLaneThreads * kLaneStride];
     __shared__ unsigned s_next;
     const int tid = threadIdx.x, lane = tid & 31;
     const int k = a.k, K = KT > 0 ? KT : a.K, kK = k * K;
-    const int JPT = MODE == kJobCand ? NI * k : k, SPT = NI * k;  // jobs and result slots per tuple
+    const int SPT = NI * k;  // result slots per tuple
+    const unsigned n_jobs = MODE == kJobCand ? *ps.n_jobs : n_slots;
     const size_t nk = (size_t)a.P * a.T * k;                     // the bases' word stride
     const int refill = min(max(a.refill, 1), 32);
     const float mu = a.mu;
@@ -1132,13 +1138,18 @@ __global__ void __launch_bounds__(kLaneThreads) k_opt_lp_jobs(const ScoreArgs a,
                 if (q >= q_hi) {
                     state = kDone;
                 } else {
-                    u = q / (unsigned)JPT;
-                    const int r = (int)(q - u * (unsigned)JPT);
-                    g = MODE == kJobCand ? r / k : 0;
-                    j = r - g * k;
-                    bool run = ps.live[u] != 0;
-                    if (MODE == kJobCand) run = run && g < ps.n_todo[u];
-                    if (MODE == kJobWin) run = run && ps.win[u] >= 0;
+                    bool run = true;
+                    if (MODE == kJobCand) {
+                        const unsigned dsc = ps.jobs[q];
+                        u = dsc >> 6;
+                        g = (int)((dsc >> 2) & 15u);
+                        j = (int)(dsc & 3u);
+                    } else {
+                        u = q / (unsigned)k;
+                        j = (int)(q - u * (unsigned)k);
+                        g = 0;
+                        run = ps.live[u] != 0 && (MODE == kJobInit || ps.win[u] >= 0);
+                    }
                     if (run) {
                         for (int d = 0; d < k; ++d) {
                             int x = __ldg(a.tuples + (size_t)u * k + d);
@@ -1272,6 +1283,12 @@ __global__ void __launch_bounds__(kOptThreads, 7) k_opt_project(const ScoreArgs 
         const unsigned todo = __ballot_sync(kFull, !skip);
         if (!skip) ps.cand[(size_t)u * NI + __popc(todo & ((1u << lane) - 1u))] = cand_mine;
         if (lane == 0) ps.n_todo[u] = __popc(todo);
+        // the candidates' LPs as jobs (LP j of candidate g: g * 4 + j)
+        const int cnt = __popc(todo) * k;
+        unsigned jb = 0;
+        if (lane == 0 && cnt) jb = atomicAdd(ps.n_jobs, (unsigned)cnt);
+        jb = __shfl_sync(kFull, jb, 0);
+        for (int t = lane; t < cnt; t += 32) ps.jobs[jb + t] = u * 64u + (unsigned)(t / k) * 4u + (unsigned)(t % k);
         __syncwarp();
     }
 }
@@ -1283,30 +1300,33 @@ __global__ void __launch_bounds__(kOptThreads, 7) k_opt_project(const ScoreArgs 
 __global__ void k_opt_select(const ScoreArgs a, const OptArgs o, const OptPhaseState ps, int NI, int i, int init,
                              unsigned n) {
     const unsigned u = blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= n || !ps.live[u]) return;
     const int k = a.k;
-    const float *sr = ps.sres + (size_t)u * NI * k;
-    float J = ps.J[u];
-    if (init) {
-        J = margin_from(sr, k);
-    } else {
-        const int n_todo = ps.n_todo[u];
-        float best = J <= o.zero_tol ? 0.f : J;
-        int win = -1;
-        for (int g = 0; g < n_todo; ++g) {
-            const float Jt = margin_from(sr + g * k, k);
-            const float Jtc = Jt <= o.zero_tol ? 0.f : Jt;
-            if (Jtc < (1.f - o.min_gain) * best) {
-                best = Jtc;
-                J = Jt;
-                win = g;
+    int win = -1;
+    bool live = false;
+    if (u < n && ps.live[u]) {
+        const float *sr = ps.sres + (size_t)u * NI * k;
+        float J = ps.J[u];
+        if (init) {
+            J = margin_from(sr, k);
+        } else {
+            const int n_todo = ps.n_todo[u];
+            float best = J <= o.zero_tol ? 0.f : J;
+            for (int g = 0; g < n_todo; ++g) {
+                const float Jt = margin_from(sr + g * k, k);
+                const float Jtc = Jt <= o.zero_tol ? 0.f : Jt;
+                if (Jtc < (1.f - o.min_gain) * best) {
+                    best = Jtc;
+                    J = Jt;
+                    win = g;
+                }
             }
+            if (win >= 0) a.tuples[(size_t)u * k + i] = ps.cand[(size_t)u * NI + win];
+            ps.win[u] = win;
         }
-        if (win >= 0) a.tuples[(size_t)u * k + i] = ps.cand[(size_t)u * NI + win];
-        ps.win[u] = win;
+        ps.J[u] = J;
+        live = (J <= o.zero_tol ? 0.f : J) > 0.f;
+        if (!live) ps.live[u] = 0;
     }
-    ps.J[u] = J;
-    if (!((J <= o.zero_tol ? 0.f : J) > 0.f)) ps.live[u] = 0;
 }
 
 // A thread per tuple: the final margin and accept flag.
@@ -1383,29 +1403,31 @@ OptPhaseState phase_state(void *scratch, size_t n, int NI, int k, bool warm) {
     ps.n_todo = (int *)p; p += align256z(sizeof(int) * n);
     ps.cand = (int *)p; p += align256z(sizeof(int) * n * NI);
     ps.sres = (float *)p; p += align256z(sizeof(float) * n * NI * k);
+    ps.n_jobs = (unsigned *)p; p += 256;
+    ps.jobs = (unsigned *)p; p += align256z(sizeof(unsigned) * n * NI * k);
     ps.base = warm ? (float *)p : nullptr;
     return ps;
 }
 
+// The LP jobs of the list the previous kernel wrote (its length is read on the device): a
+// grid of as many blocks as fit at once, each taking a contiguous share.
 template <int KT, int MODE>
-cudaError_t launch_lp_jobs(const ScoreArgs &a, const OptPhaseState &ps, int NI, int i, int warm, unsigned long long n_jobs,
+cudaError_t launch_lp_jobs(const ScoreArgs &a, const OptPhaseState &ps, int NI, int i, int warm, unsigned n_slots,
                            cudaStream_t st) {
-    if (n_jobs == 0) return cudaSuccess;
     int sms = 0, per_sm = 0;
     cudaError_t e = launch_shape((const void *)k_opt_lp_jobs<KT, MODE>, kLaneThreads, 0, &per_sm, &sms);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     if (a.bpsm > 0) per_sm = std::min(per_sm, a.bpsm);
-    const int grid = (int)std::min<long long>((long long)sms * per_sm, (long long)((n_jobs + kLaneThreads - 1) / kLaneThreads));
-    k_opt_lp_jobs<KT, MODE><<<grid, kLaneThreads, 0, st>>>(a, ps, NI, i, warm, (unsigned)n_jobs);
+    k_opt_lp_jobs<KT, MODE><<<sms * per_sm, kLaneThreads, 0, st>>>(a, ps, NI, i, warm, n_slots);
     return cudaGetLastError();
 }
 
 template <int MODE>
-cudaError_t lp_jobs(const ScoreArgs &a, const OptPhaseState &ps, int NI, int i, int warm, unsigned long long n_jobs,
+cudaError_t lp_jobs(const ScoreArgs &a, const OptPhaseState &ps, int NI, int i, int warm, unsigned n_slots,
                     cudaStream_t st) {
-    return a.K == 8 ? launch_lp_jobs<8, MODE>(a, ps, NI, i, warm, n_jobs, st)
-                    : launch_lp_jobs<0, MODE>(a, ps, NI, i, warm, n_jobs, st);
+    return a.K == 8 ? launch_lp_jobs<8, MODE>(a, ps, NI, i, warm, n_slots, st)
+                    : launch_lp_jobs<0, MODE>(a, ps, NI, i, warm, n_slots, st);
 }
 
 template <int NI>
@@ -1424,8 +1446,8 @@ cudaError_t launch_project(const ScoreArgs &a, const OptArgs &o, const OptPhaseS
 size_t optimize_state_bytes(long long n, int n_inner, int k, int warm) {
     const size_t N = (size_t)std::max<long long>(n, 1);
     return align256z(sizeof(float) * N) + align256z(N) + 2 * align256z(sizeof(int) * N) +
-           align256z(sizeof(int) * N * n_inner) + align256z(sizeof(float) * N * n_inner * k) +
-           (warm ? sizeof(float) * (size_t)kBasisWords * N * k : 0);
+           align256z(sizeof(int) * N * n_inner) + align256z(sizeof(float) * N * n_inner * k) + 256 +
+           align256z(sizeof(unsigned) * N * n_inner * k) + (warm ? sizeof(float) * (size_t)kBasisWords * N * k : 0);
 }
 
 cudaError_t launch_optimize(const ScoreArgs &a, int n_outer, int n_inner, float sigma, float zero_tol,
@@ -1433,7 +1455,7 @@ cudaError_t launch_optimize(const ScoreArgs &a, int n_outer, int n_inner, float 
     if (a.P <= 0) return cudaSuccess;
     const long long total = (long long)a.P * a.T;
     if (!a.word_box || !state) return cudaErrorInvalidValue;
-    if (total * n_inner * a.k >= (1LL << 32)) return cudaErrorInvalidValue;
+    if (total * n_inner * a.k >= (1LL << 32) || total >= (1LL << 26)) return cudaErrorInvalidValue;  // job descriptors
     if (n_inner != 4 && n_inner != 8 && n_inner != 16) return cudaErrorInvalidValue;
     const OptArgs o{n_outer, n_inner, sigma, zero_tol, min_gain, warm_start};
     const unsigned n = (unsigned)total;
@@ -1445,24 +1467,24 @@ cudaError_t launch_optimize(const ScoreArgs &a, int n_outer, int n_inner, float 
     k_chunk_boxes<<<(unsigned)(((a.W + 31) / 32 * 32 + 255) / 256), 256, 0, st>>>(a.word_box, a.W);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     const unsigned tb = (n + 255) / 256;
+    const unsigned nk = n * (unsigned)k;  // slots of the tuples' own LPs and of the replays
     k_opt_begin<<<tb, 256, 0, st>>>(a, ps, n);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     // the tuples' own LPs, from c' = 0; their optimal bases seed the candidates
-    if ((err = lp_jobs<kJobInit>(a, ps, NI, 0, warm_start, (unsigned long long)n * k, st)) != cudaSuccess) return err;
+    if ((err = lp_jobs<kJobInit>(a, ps, NI, 0, warm_start, nk, st)) != cudaSuccess) return err;
     k_opt_select<<<tb, 256, 0, st>>>(a, o, ps, NI, 0, 1, n);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     for (int it = 0; it < n_outer; ++it) {
         for (int i = 0; i < k; ++i) {
+            if ((err = cudaMemsetAsync(ps.n_jobs, 0, sizeof(unsigned), st)) != cudaSuccess) return err;
             err = NI == 4 ? launch_project<4>(a, o, ps, it, i, n, st)
                           : (NI == 8 ? launch_project<8>(a, o, ps, it, i, n, st) : launch_project<16>(a, o, ps, it, i, n, st));
             if (err != cudaSuccess) return err;
-            if ((err = lp_jobs<kJobCand>(a, ps, NI, i, warm_start, (unsigned long long)n * NI * k, st)) != cudaSuccess)
-                return err;
+            if ((err = lp_jobs<kJobCand>(a, ps, NI, i, warm_start, 0, st)) != cudaSuccess) return err;
             k_opt_select<<<tb, 256, 0, st>>>(a, o, ps, NI, i, 0, n);
             if ((err = cudaGetLastError()) != cudaSuccess) return err;
             // the winners' LPs again from the same starts: their optimal bases become the tuples'
-            if (warm_start && (err = lp_jobs<kJobWin>(a, ps, NI, i, 1, (unsigned long long)n * k, st)) != cudaSuccess)
-                return err;
+            if (warm_start && (err = lp_jobs<kJobWin>(a, ps, NI, i, 1, nk, st)) != cudaSuccess) return err;
         }
     }
     k_opt_finish<<<tb, 256, 0, st>>>(a, ps, n);
