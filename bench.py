@@ -479,31 +479,43 @@ def run_ours(args):
     ht = torch.empty((w.P, w.T, w.k), dtype=torch.int32, pin_memory=True).numpy()
     hm = torch.empty((w.P, w.T), dtype=torch.float32, pin_memory=True).numpy()
     ha = torch.empty((w.P, w.T), dtype=torch.uint8, pin_memory=True).numpy()
+    # the accepted grasps (24-byte records, room for every tuple) are what a caller keeps
+    hg = torch.empty(w.P * w.T * cf.GRASP_DTYPE.itemsize, dtype=torch.uint8, pin_memory=True).numpy()
+    hg = hg.view(cf.GRASP_DTYPE)
     plan = cf.Plan(F, w.obj.N, w.P, prm)
     q_d = torch.empty_like(q)
 
-    def e2e_step():
+    def e2e_step(all_outputs: bool):
         q_d.copy_(q_h, non_blocking=True)
         field = cf.build(w.hand, w.inv_h, w.bins, q_d)
-        return plan.run_host(field, soa_h, poses_h, ht, hm, ha)
+        if all_outputs:
+            return plan.run_host(field, soa_h, poses_h, ht, hm, ha)
+        return plan.run_host_accepted(field, soa_h, poses_h, hg)
 
-    # the host-driven path needs more warm-up than the device loop: its step time falls for ~40 calls
-    # (2.5 -> 2.1 ms on the B300 hosts) before it settles
-    for _ in range(max(40, args.warmup)):
-        e2e_step()
-    e2e_s, e2e_acc = 0.0, 0
+    def e2e_leg(all_outputs: bool):
+        # the host-driven path needs more warm-up than the device loop: its step time falls for ~40 calls
+        # (2.5 -> 2.1 ms on the B300 hosts) before it settles
+        for _ in range(max(40, args.warmup)):
+            e2e_step(all_outputs)
+        t_s, n_acc = 0.0, 0
+        for i in range(n_e2e):
+            flush.fill_(float(i))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            n_acc += e2e_step(all_outputs)
+            t_s += time.perf_counter() - t0
+        return t_s, n_acc
+
     n_e2e = max(1, min(args.e2e_steps, args.steps))
-    for i in range(n_e2e):
-        flush.fill_(float(i))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        e2e_acc += e2e_step()
-        e2e_s += time.perf_counter() - t0
+    e2e_s, e2e_acc = e2e_leg(False)
+    all_s, all_acc = e2e_leg(True)
     h2d = w.q.nbytes + 6 * 4 * w.obj.N + 12 * 4 * w.P
-    d2h = w.P * w.T * (4 * w.k + 4 + 1)
+    d2h_all = w.P * w.T * (4 * w.k + 4 + 1)
 
     # ---- reduce over ranks ------------------------------------------------
-    (total_ms, e2e_s), (accepted, e2e_acc) = reduce_over_ranks([total_ms, e2e_s], [accepted, e2e_acc], dev)
+    (total_ms, e2e_s, all_s), (accepted, e2e_acc, all_acc) = reduce_over_ranks([total_ms, e2e_s, all_s],
+                                                                                [accepted, e2e_acc, all_acc], dev)
+    d2h = 8 + cf.GRASP_DTYPE.itemsize * e2e_acc / (world * n_e2e)  # the count, then the records (mean)
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -528,7 +540,10 @@ def run_ours(args):
             "lp": {"pivots_per_tuple": counters["lp_pivots"] / max(1, counters["tuples_scored"]),
                    "lps_per_tuple": counters["lps"] / max(1, counters["tuples_scored"])},
             "e2e": {"value": e2e_acc / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "steps": n_e2e, "ms_per_step": 1e3 * e2e_s / n_e2e},
+                    "steps": n_e2e, "ms_per_step": 1e3 * e2e_s / n_e2e, "call": "cf_plan_run_host_accepted",
+                    "gpu_launches_per_step": 8,  # field build 2, query, sample, score, gather 3
+                    "all_outputs": {"value": all_acc / all_s, "d2h_bytes_per_step": d2h_all,
+                                    "ms_per_step": 1e3 * all_s / n_e2e, "call": "cf_plan_run_host"}},
             "clocks": clocks, "tuning": tuning or {"shapes": cf.get_tuning(), "autotuned": False}}
     if world == 1 and args.realized_steps > 0:
         line["realized"] = run_realized(cf, torch, dev, w, args.realized_steps, soa, poses, masks, counts, tuples,
@@ -726,7 +741,16 @@ def run_optimized(cf, torch, dev, w, steps, soa, poses, masks, counts, tuples, f
             "lp_per_tuple": counters["lps"] / max(1, counters["tuples_scored"]),
             "pivots_per_lp": counters["lp_pivots"] / max(1, counters["lps"]),
             "warm_starts_per_tuple": counters["warm_starts"] / max(1, counters["tuples_scored"]),
-            "gpu_launches_per_step": 4, "device_status": cf.device_status()}
+            "gpu_launches_per_step": 2 + opt_launches(w.k, OPT["n_outer"], warm_start),
+            "device_status": cf.device_status()}
+
+
+def opt_launches(k: int, n_outer: int, warm_start: bool) -> int:
+    """Kernels of one cf_optimize_tuples call: word and chunk boxes, begin, the
+    tuples' own LPs and their selection, then per step (n_outer x k) the
+    projection, the candidates' LPs, the selection and (warm start) the
+    winners' replay, and the finish."""
+    return 5 + n_outer * k * (4 if warm_start else 3) + 1
 
 
 # ---------------------------------------------------------------------------

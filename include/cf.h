@@ -664,6 +664,25 @@ int cf_plan_run_host(cf_plan *plan, const cf_field *field, const float *h_soa, i
                      const cf_score_params *prm, int32_t *h_tuples, float *h_margin, uint8_t *h_accept,
                      int64_t *h_n_accepted, cf_stream stream);
 
+/* One accepted grasp as cf_plan_run_host_accepted returns it. */
+typedef struct cf_grasp {
+    int32_t pose;              /* pose index within the request */
+    float margin;              /* its closure margin (<= eps) */
+    int32_t point[CF_MAX_K];   /* its k object point ids (-1 beyond k) */
+} cf_grasp;
+
+/* As cf_plan_run_host, but only the accepted tuples come back: they are gathered on the device,
+ * in (pose, tuple) order, into records (24 bytes each instead of 4k + 5 bytes per sampled tuple),
+ * and h_grasps[0 .. min(count, cap)) receives them; *h_n_accepted is the full count (larger
+ * than cap when h_grasps was too small).  The records are the tuples whose margin passes the
+ * closure test (the output set of Alg. 1).  h_grasps is the caller's (page-locked, or the copy
+ * is staged by the driver); cap = 0 with h_grasps NULL returns the count alone.  Synchronises
+ * `stream`.  Errors: CF_EINVAL (as cf_plan_run_host; cap < 0; h_grasps NULL with cap > 0),
+ * CF_ECUDA. */
+int cf_plan_run_host_accepted(cf_plan *plan, const cf_field *field, const float *h_soa, int32_t n,
+                              const float *h_poses, int32_t n_poses, const cf_score_params *prm, cf_grasp *h_grasps,
+                              int64_t cap, int64_t *h_n_accepted, cf_stream stream);
+
 int cf_plan_destroy(cf_plan *plan);
 
 /* ---- diagnostics (no paper counterpart) --------------------------------- */

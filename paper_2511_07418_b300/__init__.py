@@ -180,6 +180,9 @@ _cf_plan_create = _sig("cf_plan_create", [c_int32, c_int32, c_int32, POINTER(Sco
 _cf_plan_run_host = _sig("cf_plan_run_host", [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_int32,
                                               POINTER(ScoreParams), c_void_p, c_void_p, c_void_p, POINTER(c_int64),
                                               c_void_p])
+_cf_plan_run_host_accepted = _sig("cf_plan_run_host_accepted", [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_int32,
+                                                                POINTER(ScoreParams), c_void_p, c_int64,
+                                                                POINTER(c_int64), c_void_p])
 _cf_plan_destroy = _sig("cf_plan_destroy", [c_void_p])
 _cf_field_rep_slots = _sig("cf_field_rep_slots", [c_void_p, POINTER(c_int64)])
 _cf_field_copy_rep = _sig("cf_field_copy_rep", [c_void_p, POINTER(c_uint64), POINTER(c_uint32), c_int64])
@@ -215,7 +218,7 @@ _cf_append = _sig("cf_append_contact", [c_void_p, c_int32, c_int32, c_int32, c_v
 
 EXPORTED = ["cf_build", "cf_field_get_info", "cf_field_copy_table", "cf_field_destroy", "cf_field_save",
             "cf_field_load", "cf_query_domains", "cf_score_tuples", "cf_plan_create", "cf_plan_run_host",
-            "cf_plan_destroy", "cf_last_error", "cf_device_status", "cf_device_counters", "cf_pool_usage", "cf_sdf_box", "cf_merge_domains", "cf_place_static", "cf_append_contact", "cf_score_tuples_noalloc",
+            "cf_plan_run_host_accepted", "cf_plan_destroy", "cf_last_error", "cf_device_status", "cf_device_counters", "cf_pool_usage", "cf_sdf_box", "cf_merge_domains", "cf_place_static", "cf_append_contact", "cf_score_tuples_noalloc",
             "cf_sample_tuples", "cf_batch_create", "cf_batch_run", "cf_batch_launches", "cf_batch_destroy",
             "cf_engine_create", "cf_engine_submit", "cf_engine_poll", "cf_engine_result_free", "cf_engine_get_stats",
             "cf_engine_drain", "cf_engine_destroy", "cf_field_rep_slots", "cf_field_copy_rep", "cf_ik_dls",
@@ -646,6 +649,10 @@ class Engine:
             pass
 
 
+# cf_grasp: one accepted grasp (pose index, margin, the k point ids padded with -1 to CF_MAX_K)
+GRASP_DTYPE = np.dtype([("pose", "<i4"), ("margin", "<f4"), ("point", "<i4", (4,))])
+
+
 class Plan:
     """cf_plan: one object request driven from host buffers (H2D, query,
     sample + score, D2H inside the call)."""
@@ -670,6 +677,20 @@ class Plan:
 
         _check(_cf_plan_run_host(self._h, field.handle, ptr(h_soa), n, ptr(h_poses), P, byref(self.prm), ptr(h_tuples),
                                  ptr(h_margin), ptr(h_accept), byref(nacc), _stream(stream)))
+        return int(nacc.value)
+
+    def run_host_accepted(self, field: Field, h_soa: np.ndarray, h_poses: np.ndarray, h_grasps: np.ndarray,
+                          stream=None) -> int:
+        """cf_plan_run_host_accepted: the accepted tuples only, gathered on the device into
+        h_grasps (a GRASP_DTYPE array, ideally pinned), in (pose, tuple) order.  Returns the
+        number accepted (larger than len(h_grasps) when the array was too small)."""
+        if h_grasps.dtype != GRASP_DTYPE or not h_grasps.flags["C_CONTIGUOUS"]:
+            raise ValueError("h_grasps must be a contiguous GRASP_DTYPE array")
+        nacc = c_int64(0)
+        _check(_cf_plan_run_host_accepted(self._h, field.handle, c_void_p(h_soa.ctypes.data), int(h_soa.shape[1]),
+                                          c_void_p(h_poses.ctypes.data), int(h_poses.shape[0]), byref(self.prm),
+                                          c_void_p(h_grasps.ctypes.data) if len(h_grasps) else None, len(h_grasps),
+                                          byref(nacc), _stream(stream)))
         return int(nacc.value)
 
     def close(self):

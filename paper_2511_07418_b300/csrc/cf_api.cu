@@ -1383,6 +1383,88 @@ extern "C" int cf_autotune(const cf_batch_item *items, int32_t n_items, int32_t 
 // A plan runs a request's query, sampling and scoring as one launch each; its
 // inputs go up, and its results come back, on a second stream: the tuples while
 // the scoring kernel runs, the margins and flags after it.
+// Ordered gather of the accepted tuples into cf_grasp records, in chunks of kGatherChunk
+// tuples: count per chunk, an exclusive scan of the counts (one block), then each chunk
+// writes its records from its offset, in tuple order.
+constexpr int kGatherChunk = 4096;
+constexpr int kGatherThreads = 256;
+
+__global__ void __launch_bounds__(kGatherThreads) k_count_accepted(const uint8_t *__restrict__ accept, size_t n,
+                                                                   unsigned *__restrict__ cnt) {
+    const size_t c0 = (size_t)blockIdx.x * kGatherChunk, c1 = c0 + kGatherChunk < n ? c0 + kGatherChunk : n;
+    unsigned c = 0;
+    for (size_t u = c0 + threadIdx.x; u < c1; u += kGatherThreads) c += accept[u] != 0;
+    c = __reduce_add_sync(0xffffffffu, c);
+    __shared__ unsigned s_w[kGatherThreads / 32];
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned t = 0;
+        for (int w = 0; w < kGatherThreads / 32; ++w) t += s_w[w];
+        cnt[blockIdx.x] = t;
+    }
+}
+
+// In place: cnt[b] <- the sum of cnt[0 .. b) (one block, tiles of its threads in turn).
+__global__ void __launch_bounds__(1024) k_scan_counts(unsigned *cnt, int nb) {
+    __shared__ unsigned s_w[32];
+    __shared__ unsigned s_carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < nb; b0 += 1024) {
+        const int b = b0 + threadIdx.x;
+        const unsigned v = b < nb ? cnt[b] : 0u;
+        unsigned incl = v;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned x = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += x;
+        }
+        if (lane == 31) s_w[warp] = incl;
+        __syncthreads();
+        unsigned before = s_carry;
+        for (int w = 0; w < warp; ++w) before += s_w[w];
+        if (b < nb) cnt[b] = before + incl - v;
+        __syncthreads();  // every thread has read s_carry and s_w
+        if (threadIdx.x == 1023) s_carry = before + incl;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kGatherThreads) k_write_accepted(const uint8_t *__restrict__ accept,
+                                                                   const int32_t *__restrict__ tuples,
+                                                                   const float *__restrict__ margin, size_t n, int T,
+                                                                   int k, const unsigned *__restrict__ off,
+                                                                   cf_grasp *__restrict__ out) {
+    __shared__ unsigned s_w[kGatherThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const size_t c0 = (size_t)blockIdx.x * kGatherChunk, c1 = c0 + kGatherChunk < n ? c0 + kGatherChunk : n;
+    unsigned run = off[blockIdx.x];
+    for (size_t t0 = c0; t0 < c1; t0 += kGatherThreads) {
+        const size_t u = t0 + threadIdx.x;
+        const bool acc = u < c1 && accept[u] != 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, acc);
+        __syncthreads();  // the previous tile's counts have been read
+        if (lane == 0) s_w[warp] = __popc(bal);
+        __syncthreads();
+        unsigned before = 0, tile = 0;
+        for (int w = 0; w < kGatherThreads / 32; ++w) {
+            before += w < warp ? s_w[w] : 0u;
+            tile += s_w[w];
+        }
+        if (acc) {
+            cf_grasp g;
+            g.pose = (int32_t)(u / (size_t)T);
+            g.margin = margin[u];
+#pragma unroll
+            for (int q = 0; q < CF_MAX_K; ++q) g.point[q] = q < k ? tuples[u * k + q] : -1;
+            out[run + before + __popc(bal & ((1u << lane) - 1u))] = g;
+        }
+        run += tile;
+    }
+}
+
 constexpr int kPlanEvents = 2;  // tuples sampled; tuples scored
 
 struct cf_plan {
@@ -1393,6 +1475,8 @@ struct cf_plan {
     int32_t *d_tuples = nullptr;
     uint8_t *d_fingers = nullptr, *d_accept = nullptr;
     unsigned long long *d_n_acc = nullptr;  // accepted tuples of the request
+    cf_grasp *d_grasps = nullptr;           // the gathered accepted tuples
+    unsigned *d_chunk = nullptr;            // accepted tuples per gather chunk, then their offsets
     unsigned long long *h_n_acc = nullptr;  // page-locked copy
     cudaStream_t copy_st = nullptr;
     cudaEvent_t ev[kPlanEvents] = {};
@@ -1413,8 +1497,9 @@ extern "C" int cf_plan_create(int32_t n_fingers, int32_t n_max, int32_t p_max, c
     const size_t b_soa = al(sizeof(float) * 6 * n_max), b_pose = al(sizeof(float) * 12 * P),
                  b_mask = al(sizeof(uint32_t) * P * pl->F * W), b_cnt = al(sizeof(uint32_t) * P * pl->F),
                  b_tup = al(sizeof(int32_t) * PT * pl->k), b_fin = al(PT * pl->k), b_mar = al(sizeof(float) * PT),
-                 b_acc = al(PT), b_nacc = 256;
-    const size_t total = b_soa + b_pose + b_mask + b_cnt + b_tup + b_fin + b_mar + b_acc + b_nacc;
+                 b_acc = al(PT), b_nacc = 256, b_grasp = al(sizeof(cf_grasp) * PT),
+                 b_chunk = al(sizeof(unsigned) * ((PT + kGatherChunk - 1) / kGatherChunk + 1));
+    const size_t total = b_soa + b_pose + b_mask + b_cnt + b_tup + b_fin + b_mar + b_acc + b_nacc + b_grasp + b_chunk;
     cudaError_t e = cudaMalloc(&pl->d_block, total);
     if (e != cudaSuccess) { delete pl; return cuda_fail(e, "cudaMalloc(plan)"); }
     auto undo = [&](cudaError_t err, const char *what) {
@@ -1439,14 +1524,18 @@ extern "C" int cf_plan_create(int32_t n_fingers, int32_t n_max, int32_t p_max, c
     pl->d_fingers = (uint8_t *)p; p += b_fin;
     pl->d_margin = (float *)p; p += b_mar;
     pl->d_accept = (uint8_t *)p; p += b_acc;
-    pl->d_n_acc = (unsigned long long *)p;
+    pl->d_n_acc = (unsigned long long *)p; p += b_nacc;
+    pl->d_grasps = (cf_grasp *)p; p += b_grasp;
+    pl->d_chunk = (unsigned *)p;
     *out = pl;
     return CF_OK;
 }
 
-extern "C" int cf_plan_run_host(cf_plan *pl, const cf_field *fd, const float *h_soa, int32_t n, const float *h_poses,
-                                int32_t n_poses, const cf_score_params *prm, int32_t *h_tuples, float *h_margin,
-                                uint8_t *h_accept, int64_t *h_n_accepted, cf_stream stream) {
+namespace {
+// The request's inputs up, domains, sampling and scoring queued on `st`; the sampled tuples
+// go back to h_tuples (when given) on the copy stream while the scoring kernel runs.
+int plan_enqueue(cf_plan *pl, const cf_field *fd, const float *h_soa, int32_t n, const float *h_poses, int32_t n_poses,
+                 const cf_score_params *prm, int32_t *h_tuples, cf_stream stream) {
     if (!pl || !fd || !prm || (n > 0 && !h_soa) || (n_poses > 0 && !h_poses)) return fail(CF_EINVAL, "NULL argument");
     if (fd->F > pl->F) return fail(CF_EINVAL, "field has %d fingers, plan holds %d", fd->F, pl->F);
     if (fd->geom.patches) return fail(CF_EINVAL, "a plan samples from finger domains: not a patch field");
@@ -1479,7 +1568,6 @@ extern "C" int cf_plan_run_host(cf_plan *pl, const cf_field *fd, const float *h_
     a.n_accept = pl->d_n_acc;
     const size_t pt = (size_t)n_poses * T;
     if (n_poses > 0) CF_TRY(launch_sample(a, st), "launch k_sample_tuples");
-    // the tuples (most of the result bytes) go back while the scoring kernel runs; margins and flags follow
     CF_TRY(cudaEventRecord(pl->ev[0], st), "event record");
     CF_TRY(cudaStreamWaitEvent(pl->copy_st, pl->ev[0], 0), "stream wait");
     if (pt > 0 && h_tuples)
@@ -1489,6 +1577,18 @@ extern "C" int cf_plan_run_host(cf_plan *pl, const cf_field *fd, const float *h_
         a.tuples_given = 1;  // sampled above
         CF_TRY(launch_score(a, st), "launch k_score_lanes");
     }
+    return CF_OK;
+}
+}  // namespace
+
+extern "C" int cf_plan_run_host(cf_plan *pl, const cf_field *fd, const float *h_soa, int32_t n, const float *h_poses,
+                                int32_t n_poses, const cf_score_params *prm, int32_t *h_tuples, float *h_margin,
+                                uint8_t *h_accept, int64_t *h_n_accepted, cf_stream stream) {
+    // the tuples (most of the result bytes) go back while the scoring kernel runs; margins and flags follow
+    int rc = plan_enqueue(pl, fd, h_soa, n, h_poses, n_poses, prm, h_tuples, stream);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t pt = (size_t)n_poses * pl->T;
     CF_TRY(cudaEventRecord(pl->ev[1], st), "event record");
     CF_TRY(cudaStreamWaitEvent(pl->copy_st, pl->ev[1], 0), "stream wait");
     if (pt > 0 && h_margin)
@@ -1501,6 +1601,38 @@ extern "C" int cf_plan_run_host(cf_plan *pl, const cf_field *fd, const float *h_
     CF_TRY(cudaStreamSynchronize(pl->copy_st), "plan copies");
     CF_TRY(cudaStreamSynchronize(st), "plan run");
     if (h_n_accepted) *h_n_accepted = (int64_t)*pl->h_n_acc;
+    return CF_OK;
+}
+
+extern "C" int cf_plan_run_host_accepted(cf_plan *pl, const cf_field *fd, const float *h_soa, int32_t n,
+                                         const float *h_poses, int32_t n_poses, const cf_score_params *prm,
+                                         cf_grasp *h_grasps, int64_t cap, int64_t *h_n_accepted, cf_stream stream) {
+    if (cap < 0 || (cap > 0 && !h_grasps)) return fail(CF_EINVAL, "bad grasp buffer");
+    int rc = plan_enqueue(pl, fd, h_soa, n, h_poses, n_poses, prm, nullptr, stream);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t pt = (size_t)n_poses * pl->T;
+    const unsigned nb = (unsigned)((pt + kGatherChunk - 1) / kGatherChunk);
+    if (nb > 0) {  // the accepted tuples gathered in order, on the device
+        k_count_accepted<<<nb, kGatherThreads, 0, st>>>(pl->d_accept, pt, pl->d_chunk);
+        CF_TRY(cudaGetLastError(), "launch k_count_accepted");
+        k_scan_counts<<<1, 1024, 0, st>>>(pl->d_chunk, (int)nb);
+        CF_TRY(cudaGetLastError(), "launch k_scan_counts");
+        k_write_accepted<<<nb, kGatherThreads, 0, st>>>(pl->d_accept, pl->d_tuples, pl->d_margin, pt, pl->T, pl->k,
+                                                        pl->d_chunk, pl->d_grasps);
+        CF_TRY(cudaGetLastError(), "launch k_write_accepted");
+    }
+    CF_TRY(cudaMemcpyAsync(pl->h_n_acc, pl->d_n_acc, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st),
+           "D2H accept count");
+    CF_TRY(cudaStreamSynchronize(st), "plan run");
+    const int64_t count = (int64_t)*pl->h_n_acc, m = count < cap ? count : cap;
+    if (m > 0) {
+        CF_TRY(cudaMemcpyAsync(h_grasps, pl->d_grasps, sizeof(cf_grasp) * (size_t)m, cudaMemcpyDeviceToHost, st),
+               "D2H grasps");
+        CF_TRY(cudaStreamSynchronize(st), "plan copies");
+    }
+    CF_TRY(cudaStreamSynchronize(pl->copy_st), "plan copies");
+    if (h_n_accepted) *h_n_accepted = count;
     return CF_OK;
 }
 

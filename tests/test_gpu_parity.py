@@ -204,6 +204,17 @@ def test_plan_host_path_equals_device_path(cf):
     assert np.array_equal(ha, r["accept"].cpu().numpy())
     assert nacc == int(r["accept"].sum()) > 0
     assert plan.run_host(r["field"], soa_h, poses_h) == nacc  # outputs optional, count still returned
+    # the accepted tuples only, gathered on the device in (pose, tuple) order
+    g = torch.empty(nacc * 24, dtype=torch.uint8, pin_memory=True).numpy().view(cf.GRASP_DTYPE)
+    assert plan.run_host_accepted(r["field"], soa_h, poses_h, g) == nacc
+    pose_idx, tup_idx = np.nonzero(ha)
+    assert np.array_equal(g["pose"], pose_idx)
+    assert np.array_equal(g["margin"], hm[pose_idx, tup_idx])
+    assert np.array_equal(g["point"][:, :w.k], ht[pose_idx, tup_idx])
+    assert (g["point"][:, w.k:] == -1).all()
+    short = np.zeros(3, cf.GRASP_DTYPE)  # too small: the first 3, and the full count
+    assert plan.run_host_accepted(r["field"], soa_h, poses_h, short) == nacc
+    assert np.array_equal(short, g[:3])
 
 
 def test_far_and_non_finite_points_hit_nothing(cf):
