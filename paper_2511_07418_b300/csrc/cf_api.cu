@@ -1405,31 +1405,9 @@ __global__ void __launch_bounds__(kGatherThreads) k_count_accepted(const uint8_t
     }
 }
 
-// In place: cnt[b] <- the sum of cnt[0 .. b) (one block, tiles of its threads in turn).
+// In place: cnt[b] <- the sum of cnt[0 .. b) (one block).
 __global__ void __launch_bounds__(1024) k_scan_counts(unsigned *cnt, int nb) {
-    __shared__ unsigned s_w[32];
-    __shared__ unsigned s_carry;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_carry = 0;
-    __syncthreads();
-    for (int b0 = 0; b0 < nb; b0 += 1024) {
-        const int b = b0 + threadIdx.x;
-        const unsigned v = b < nb ? cnt[b] : 0u;
-        unsigned incl = v;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const unsigned x = __shfl_up_sync(0xffffffffu, incl, off);
-            if (lane >= off) incl += x;
-        }
-        if (lane == 31) s_w[warp] = incl;
-        __syncthreads();
-        unsigned before = s_carry;
-        for (int w = 0; w < warp; ++w) before += s_w[w];
-        if (b < nb) cnt[b] = before + incl - v;
-        __syncthreads();  // every thread has read s_carry and s_w
-        if (threadIdx.x == 1023) s_carry = before + incl;
-        __syncthreads();
-    }
+    block_exclusive_scan_1024(cnt, nb, nullptr);
 }
 
 __global__ void __launch_bounds__(kGatherThreads) k_write_accepted(const uint8_t *__restrict__ accept,

@@ -97,6 +97,36 @@ __host__ __device__ constexpr int record_stride(int words) {
 // per-cell candidate count.
 int build_bin_candidates(const float *dirs, int B, uint32_t *table);
 
+// In place, by one block of 1024 threads: v[b] <- v[0] + ... + v[b - 1] for b < nb (tiles of
+// 1024 entries in turn, the running sum carried across them); *total (when given) <- the sum of
+// all nb entries.  Every thread of the block must call it.
+__device__ __forceinline__ void block_exclusive_scan_1024(unsigned *v, int nb, unsigned *total) {
+    __shared__ unsigned s_w[32];
+    __shared__ unsigned s_carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < nb; b0 += 1024) {
+        const int b = b0 + threadIdx.x;
+        const unsigned x = b < nb ? v[b] : 0u;
+        unsigned incl = x;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += y;
+        }
+        if (lane == 31) s_w[warp] = incl;
+        __syncthreads();
+        unsigned before = s_carry;
+        for (int w = 0; w < warp; ++w) before += s_w[w];
+        if (b < nb) v[b] = before + incl - x;
+        __syncthreads();  // every thread has read s_carry and s_w
+        if (threadIdx.x == 1023) s_carry = before + incl;
+        __syncthreads();
+    }
+    if (total && threadIdx.x == 0) *total = s_carry;
+}
+
 // bin of m from the cube-map candidate list (exactly the full-scan argmax)
 __device__ __forceinline__ int bin_by_candidates(float mx, float my, float mz, const uint32_t *s_cand,
                                                  const float4 *s_dir) {

@@ -1060,10 +1060,16 @@ struct OptPhaseState {
     int *n_todo;     // [n] the step's candidates
     float *sres;     // [n][NI * k] s_j of job g * k + j (the tuple's own LPs: j)
     int *win;        // [n] the step's winning rank, -1 when none
-    unsigned *jobs;    // the step's candidate LP jobs, u * 64 + g * 4 + j each, in no particular order
-    unsigned *n_jobs;  // their count (reset before each projection)
+    unsigned *jobs;    // the step's candidate LP jobs, u * 64 + g * 4 + j each, by tuple, then g, then j
+    unsigned *n_jobs;  // their count
+    unsigned *chunk;   // [n / kJobChunk + 1] jobs per chunk of kJobChunk tuples, then the chunks' offsets
 };
 
+// Idle lanes before a group refill in the LP jobs.  Alg. 2's LPs are short (3.7 pivots with the
+// warm start, 7.1 cold, against 13 in the scorer) and a warm start loads and repairs a basis, so
+// starts are taken in larger groups than the scorer's: at hand20, 12 gave 355 ms (8: 364, 16: 355,
+// 24: 376) with the warm start and 358 ms cold (8: 358, 16: 365).
+constexpr int kOptRefill = 12;
 constexpr int kJobInit = 0;  // LP_j of the tuple itself, from c' = 0; its basis is kept
 constexpr int kJobCand = 1;  // LP_j of candidate g, warm-started (counted in the device counters)
 constexpr int kJobWin = 2;   // LP_j of the step's winner, replayed to keep its basis (not counted)
@@ -1108,7 +1114,7 @@ __global__ void __launch_bounds__(kLaneThreads) k_opt_lp_jobs(const ScoreArgs a,
     const int SPT = NI * k;  // result slots per tuple
     const unsigned n_jobs = MODE == kJobCand ? *ps.n_jobs : n_slots;
     const size_t nk = (size_t)a.P * a.T * k;                     // the bases' word stride
-    const int refill = min(max(a.refill, 1), 32);
+    constexpr int refill = kOptRefill;
     const float mu = a.mu;
     const LaneObj ob = lane_obj(a);
     float *cf = s_c + tid * kLaneStride;
@@ -1283,13 +1289,61 @@ __global__ void __launch_bounds__(kOptThreads, 7) k_opt_project(const ScoreArgs 
         const unsigned todo = __ballot_sync(kFull, !skip);
         if (!skip) ps.cand[(size_t)u * NI + __popc(todo & ((1u << lane) - 1u))] = cand_mine;
         if (lane == 0) ps.n_todo[u] = __popc(todo);
-        // the candidates' LPs as jobs (LP j of candidate g: g * 4 + j)
-        const int cnt = __popc(todo) * k;
-        unsigned jb = 0;
-        if (lane == 0 && cnt) jb = atomicAdd(ps.n_jobs, (unsigned)cnt);
-        jb = __shfl_sync(kFull, jb, 0);
-        for (int t = lane; t < cnt; t += 32) ps.jobs[jb + t] = u * 64u + (unsigned)(t / k) * 4u + (unsigned)(t % k);
         __syncwarp();
+    }
+}
+
+// The step's candidate LP jobs as one list in tuple order, so that the lanes of a block read
+// neighbouring tuples' bases (word-major rows: neighbouring tuples share sectors): the jobs per
+// chunk of kJobChunk tuples, an exclusive scan of those counts (one block; it also writes the
+// total), then every chunk writes its tuples' jobs from its offset.
+constexpr int kJobChunk = 4096;
+constexpr int kJobThreads = 256;
+
+__global__ void __launch_bounds__(kJobThreads) k_job_counts(const OptPhaseState ps, unsigned n, int k) {
+    __shared__ unsigned s_w[kJobThreads / 32];
+    const unsigned c0 = blockIdx.x * kJobChunk, c1 = min(n, c0 + kJobChunk);
+    unsigned c = 0;
+    for (unsigned u = c0 + threadIdx.x; u < c1; u += kJobThreads) c += (unsigned)ps.n_todo[u];
+    c = __reduce_add_sync(kFull, c);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned t = 0;
+        for (int w = 0; w < kJobThreads / 32; ++w) t += s_w[w];
+        ps.chunk[blockIdx.x] = t * (unsigned)k;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_job_scan(const OptPhaseState ps, int nb) {
+    block_exclusive_scan_1024(ps.chunk, nb, ps.n_jobs);
+}
+
+__global__ void __launch_bounds__(kJobThreads) k_job_write(const OptPhaseState ps, unsigned n, int k) {
+    __shared__ unsigned s_w[kJobThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned c0 = blockIdx.x * kJobChunk, c1 = min(n, c0 + kJobChunk);
+    unsigned run = ps.chunk[blockIdx.x];
+    for (unsigned t0 = c0; t0 < c1; t0 += kJobThreads) {
+        const unsigned u = t0 + threadIdx.x;
+        const unsigned cnt = u < c1 ? (unsigned)ps.n_todo[u] * (unsigned)k : 0u;
+        unsigned incl = cnt;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned y = __shfl_up_sync(kFull, incl, off);
+            if (lane >= off) incl += y;
+        }
+        __syncthreads();  // the previous tile's sums have been read
+        if (lane == 31) s_w[warp] = incl;
+        __syncthreads();
+        unsigned before = 0, tile = 0;
+        for (int w = 0; w < kJobThreads / 32; ++w) {
+            before += w < warp ? s_w[w] : 0u;
+            tile += s_w[w];
+        }
+        const unsigned at = run + before + incl - cnt;
+        for (unsigned t = 0; t < cnt; ++t) ps.jobs[at + t] = u * 64u + (t / (unsigned)k) * 4u + t % (unsigned)k;
+        run += tile;
     }
 }
 
@@ -1404,6 +1458,7 @@ OptPhaseState phase_state(void *scratch, size_t n, int NI, int k, bool warm) {
     ps.cand = (int *)p; p += align256z(sizeof(int) * n * NI);
     ps.sres = (float *)p; p += align256z(sizeof(float) * n * NI * k);
     ps.n_jobs = (unsigned *)p; p += 256;
+    ps.chunk = (unsigned *)p; p += align256z(sizeof(unsigned) * (n / kJobChunk + 1));
     ps.jobs = (unsigned *)p; p += align256z(sizeof(unsigned) * n * NI * k);
     ps.base = warm ? (float *)p : nullptr;
     return ps;
@@ -1447,7 +1502,7 @@ size_t optimize_state_bytes(long long n, int n_inner, int k, int warm) {
     const size_t N = (size_t)std::max<long long>(n, 1);
     return align256z(sizeof(float) * N) + align256z(N) + 2 * align256z(sizeof(int) * N) +
            align256z(sizeof(int) * N * n_inner) + align256z(sizeof(float) * N * n_inner * k) + 256 +
-           align256z(sizeof(unsigned) * N * n_inner * k) + (warm ? sizeof(float) * (size_t)kBasisWords * N * k : 0);
+           align256z(sizeof(unsigned) * (N / kJobChunk + 1)) + align256z(sizeof(unsigned) * N * n_inner * k) + (warm ? sizeof(float) * (size_t)kBasisWords * N * k : 0);
 }
 
 cudaError_t launch_optimize(const ScoreArgs &a, int n_outer, int n_inner, float sigma, float zero_tol,
@@ -1468,6 +1523,7 @@ cudaError_t launch_optimize(const ScoreArgs &a, int n_outer, int n_inner, float 
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     const unsigned tb = (n + 255) / 256;
     const unsigned nk = n * (unsigned)k;  // slots of the tuples' own LPs and of the replays
+    const unsigned nb = (n + kJobChunk - 1) / kJobChunk;  // chunks of the candidate job list
     k_opt_begin<<<tb, 256, 0, st>>>(a, ps, n);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     // the tuples' own LPs, from c' = 0; their optimal bases seed the candidates
@@ -1476,10 +1532,15 @@ cudaError_t launch_optimize(const ScoreArgs &a, int n_outer, int n_inner, float 
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     for (int it = 0; it < n_outer; ++it) {
         for (int i = 0; i < k; ++i) {
-            if ((err = cudaMemsetAsync(ps.n_jobs, 0, sizeof(unsigned), st)) != cudaSuccess) return err;
             err = NI == 4 ? launch_project<4>(a, o, ps, it, i, n, st)
                           : (NI == 8 ? launch_project<8>(a, o, ps, it, i, n, st) : launch_project<16>(a, o, ps, it, i, n, st));
             if (err != cudaSuccess) return err;
+            k_job_counts<<<nb, kJobThreads, 0, st>>>(ps, n, k);
+            if ((err = cudaGetLastError()) != cudaSuccess) return err;
+            k_job_scan<<<1, 1024, 0, st>>>(ps, (int)nb);
+            if ((err = cudaGetLastError()) != cudaSuccess) return err;
+            k_job_write<<<nb, kJobThreads, 0, st>>>(ps, n, k);
+            if ((err = cudaGetLastError()) != cudaSuccess) return err;
             if ((err = lp_jobs<kJobCand>(a, ps, NI, i, warm_start, 0, st)) != cudaSuccess) return err;
             k_opt_select<<<tb, 256, 0, st>>>(a, o, ps, NI, i, 0, n);
             if ((err = cudaGetLastError()) != cudaSuccess) return err;
