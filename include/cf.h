@@ -26,7 +26,8 @@
  *  - Work is queued on the caller's CUDA stream (cf_stream = cudaStream_t, NULL
  *    = legacy default stream).  cf_build waits once on that stream (for the
  *    table's extents) and returns with its last kernel queued;
- *    cf_plan_run_host synchronises the stream; the other calls do not.
+ *    cf_plan_run_host and cf_plan_run_host_accepted synchronise the stream;
+ *    the other calls do not.
  *  - Device memory the library owns comes from a per-device stream-ordered
  *    pool that keeps freed blocks for reuse.
  *  - Shapes are checked on the host (CF_EINVAL); a kernel that meets a
