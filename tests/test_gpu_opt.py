@@ -147,10 +147,12 @@ def test_optimize_invalid_tuples(cf):
 
 
 def test_optimize_schedule_independent(cf):
-    """Each tuple's result depends only on the tuple: one launch over 4,096 tuples (warps recycle
-    their tuple slots many times) equals, bit for bit, launches over its first 8 poses and its
-    first pose alone (the draws' counters use the pose index, so leading subsets keep theirs)."""
-    w, soa, m, tup, fing = _inputs("hand16_superquadric", 64, 4096)
+    """Each tuple's result depends only on the tuple: one launch over 10,240 tuples (warps recycle
+    their tuple slots many times; the candidate job list spans two full 4,096-tuple chunks and a
+    ragged one) equals, bit for bit, launches over its first 72 poses (a chunk and a ragged
+    one), its first 8 and its first pose alone (the draws' counters use the pose index, so
+    leading subsets keep theirs)."""
+    w, soa, m, tup, fing = _inputs("hand16_superquadric", 160, 4096)
     kw = dict(n_outer=2, n_inner=8, sigma=0.005, zero_tol=1e-6, min_gain=1e-2, warm_start=True)
     prm = cf.score_params(w.T, w.k, w.mu, w.K, w.eps, w.obj.centroid, w.obj.rho, w.seed, tuples_given=True)
     dsoa = torch.from_numpy(soa).cuda()
@@ -158,7 +160,7 @@ def test_optimize_schedule_independent(cf):
     f_all = torch.from_numpy(fing).cuda()
     t_all = torch.from_numpy(tup.copy()).cuda()
     m_all, a_all = cf.optimize_tuples(dsoa, w.hand.F, dm, prm, cf.opt_params(**kw), t_all, f_all)
-    for n in (8, 1):
+    for n in (72, 8, 1):
         t_n = torch.from_numpy(tup[:n].copy()).cuda()
         m_n, a_n = cf.optimize_tuples(dsoa, w.hand.F, dm[:n].contiguous(), prm, cf.opt_params(**kw), t_n,
                                       f_all[:n].contiguous())

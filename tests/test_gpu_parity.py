@@ -215,6 +215,15 @@ def test_plan_host_path_equals_device_path(cf):
     short = np.zeros(3, cf.GRASP_DTYPE)  # too small: the first 3, and the full count
     assert plan.run_host_accepted(r["field"], soa_h, poses_h, short) == nacc
     assert np.array_equal(short, g[:3])
+    # a ragged request (15 gather chunks of 4,096 tuples and 2,560 more) and an empty one
+    n2 = 4000
+    n_rag = plan.run_host(r["field"], soa_h, poses_h[:n2], ht[:n2], hm[:n2], ha[:n2])
+    g2 = np.zeros(n_rag + 1, cf.GRASP_DTYPE)
+    assert plan.run_host_accepted(r["field"], soa_h, poses_h[:n2], g2) == n_rag
+    pose_idx, tup_idx = np.nonzero(ha[:n2])
+    assert np.array_equal(g2["pose"][:n_rag], pose_idx)
+    assert np.array_equal(g2["point"][:n_rag, :w.k], ht[pose_idx, tup_idx])
+    assert plan.run_host_accepted(r["field"], soa_h, poses_h[:0], g2) == 0
 
 
 def test_far_and_non_finite_points_hit_nothing(cf):
