@@ -236,11 +236,14 @@ def test_ik_edge_cases(cf):
     assert cf.device_status() == 0
 
 
-@pytest.mark.parametrize("name", ["tiny_sphere", "hand16_superquadric"])
-def test_sdf_parity(cf, name):
-    w = synth.workload(name, P=1, N=2048, S=256)
+@pytest.mark.parametrize("name,N,h", [("tiny_sphere", 2048, 0.004), ("hand16_superquadric", 2048, 0.004),
+                                      ("hand20_tool", 8192, 0.008), ("hand20_tool", 1000, 0.006)])
+def test_sdf_parity(cf, name, N, h):
+    """Against the FP64 brute force: 2,048 points (two of the kernel's 1,024-point shared-memory
+    tiles), 8,192 (eight) over a tool-sized grid, and 1,000 (a ragged single tile)."""
+    w = synth.workload(name, P=1, N=N, S=256)
     soa = w.obj.soa()
-    lo, h, dims = cf.sdf_box(soa, 0.004, 0.02)
+    lo, h, dims = cf.sdf_box(soa, h, 0.02)
     sdf = cf.Sdf(torch.from_numpy(soa).cuda(), lo, h, dims)
     g = sdf.grid()
     o, amb = K.sdf_grid(soa, lo, h, dims)
