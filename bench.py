@@ -978,8 +978,9 @@ def run_served(cf, torch, dev, ws, fields, rates, seconds, pool=24, max_active=6
     for rate in rates:
         out["continuous_batching"].append(stream(max_active, rate, chunk_max=0))
         out["one_at_a_time"].append(stream(1, rate, seconds=min(seconds, 5.0), chunk_max=0))
-    # adaptive chunks: fewer rounds for requests that need many poses (a lower p99 at light and
-    # moderate load), longer rounds for everyone they share them with (a higher p99 at 1,000 req/s)
+    # adaptive chunks: fewer rounds for requests that need many poses, at the price of longer rounds
+    # for the requests they share them with; with the pool reserved at engine creation the fewer
+    # rounds win at every rate measured (10 s per rate here, beside the fixed-chunk streams)
     if pose_chunk_max > pose_chunk:
         out["adaptive_chunks"] = [stream(max_active, rate, seconds=min(seconds, 10.0)) for rate in rates]
     # admission by HBM budget that binds: a 128 MiB budget holds only a few dozen requests' device state
