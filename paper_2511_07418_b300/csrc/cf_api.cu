@@ -1382,7 +1382,9 @@ extern "C" int cf_autotune(const cf_batch_item *items, int32_t n_items, int32_t 
 // ---------------------------------------------------------------------------
 // A plan runs a request's query, sampling and scoring as one launch each; its
 // inputs go up, and its results come back, on a second stream: the tuples while
-// the scoring kernel runs, the margins and flags after it.
+// the scoring kernel runs, the margins and flags after it.  Or only the accepted
+// tuples come back (cf_plan_run_host_accepted), gathered first on the device.
+
 // Ordered gather of the accepted tuples into cf_grasp records, in chunks of kGatherChunk
 // tuples: count per chunk, an exclusive scan of the counts (one block), then each chunk
 // writes its records from its offset, in tuple order.
