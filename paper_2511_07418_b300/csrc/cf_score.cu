@@ -802,11 +802,11 @@ __global__ void __launch_bounds__(kLaneThreads) k_score_lanes(const ScoreArgs a,
 // domain point nearest to it (mask bit set in row `row`), lowest index on ties; lane c
 // returns candidate c's (-1 when the domain is empty).  Exact pruning: the current
 // point x0 (p) lies in the domain, so candidate q_c's nearest domain point lies within
-// r_c = |q_c - p| of q_c, hence within R = 2 max_c r_c of p.  Lanes test mask words
-// lane, lane + 32, ...: a word whose point box is farther than R from p is skipped, and
-// of the rest each candidate c whose r_c-ball misses the box is left out of the word
-// (radii with slack for rounding; no pruning when x0's bit is not set, e.g. for given
-// tuples outside the domain).  The warp then takes each surviving word together, lane b
+// r_c = |q_c - p| of q_c.  Chunks of 32 mask words, then the words of the chunks that
+// remain (lane, lane + 32, ...), keep only the candidates whose r_c-ball reaches their
+// point box, and a word left with none is skipped (radii with slack for rounding; no
+// pruning when x0's bit is not set, e.g. for given tuples outside the domain).  A test of
+// the word box against p alone was dropped: the balls already exclude every word it did.  The warp then takes each surviving word together, lane b
 // on the word's point b, for the candidates the word can serve: point loads are
 // coalesced and the candidate test is uniform across the warp.
 template <int NI>
@@ -840,6 +840,9 @@ __device__ __forceinline__ int project_candidates(const ScoreArgs &a, const floa
     for (int c = 0; c < NI; ++c) r2c[c] = __shfl_sync(kFull, rs * rs, c);
     rc = __uint_as_float(__reduce_max_sync(kFull, __float_as_uint(rc)));  // rc >= 0: bits order
     const bool in_dom = (__ldg(row + (x0 >> 5)) >> (x0 & 31)) & 1u;
+    // R bounds every candidate's nearest domain point from p (|q_c - p| + r_c <= 2 max r_c); finite
+    // only when p lies in the domain, R2 gates the pruning below (kept in this form: the same test on a
+    // bool costs the kernel a spill in its word loop)
     const float R = 2.f * rc * 1.0001f + 1e-6f;
     const float R2 = in_dom ? R * R : INFINITY;
     constexpr unsigned kAll = NI >= 32 ? 0xffffffffu : (1u << NI) - 1u;
@@ -874,12 +877,7 @@ __device__ __forceinline__ int project_candidates(const ScoreArgs &a, const floa
                 const float *bx = a.word_box + 6 * (size_t)w;
                 const float lx = __ldg(bx), ly = __ldg(bx + 1), lz = __ldg(bx + 2);
                 const float hx = __ldg(bx + 3), hy = __ldg(bx + 4), hz = __ldg(bx + 5);
-                const float ex = fmaxf(fmaxf(lx - px, px - hx), 0.f);
-                const float ey = fmaxf(fmaxf(ly - py, py - hy), 0.f);
-                const float ez = fmaxf(fmaxf(lz - pz, pz - hz), 0.f);
-                if (ex * ex + ey * ey + ez * ez > R2) {
-                    bits = 0u;  // every point of the word is farther
-                } else {
+                {
                     cmask = 0u;
 #pragma unroll
                     for (int c = 0; c < NI; ++c) {
