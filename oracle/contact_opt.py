@@ -164,20 +164,26 @@ def optimize_tuple(soa, masks_pose, ids, fingers, pose, tau, mu, K, c, rho, eps,
 
 
 def _opt_chunk(args):
-    soa, masks, tuples, fingers, us, T, mu, K, c, rho, eps, seed, n_outer, n_inner, sigma, zero_tol, min_gain = args
+    (soa, masks, tuples, fingers, pose_ids, us, T, mu, K, c, rho, eps, seed, n_outer, n_inner, sigma, zero_tol,
+     min_gain) = args
     out = []
     for u in us:
-        pose, tau = divmod(int(u), T)
-        out.append(optimize_tuple(soa, masks[pose], tuples[u], fingers[u], pose, tau, mu, K, c, rho, eps, seed,
-                                  n_outer, n_inner, sigma, zero_tol, min_gain))
+        row, tau = divmod(int(u), T)
+        out.append(optimize_tuple(soa, masks[row], tuples[u], fingers[u], int(pose_ids[row]), tau, mu, K, c, rho, eps,
+                                  seed, n_outer, n_inner, sigma, zero_tol, min_gain))
     return out
 
 
 def optimize_tuples(soa, masks, tuples, fingers, T, mu, K, c, rho, eps, seed, n_outer=2, n_inner=8, sigma=0.005,
-                    zero_tol=1e-6, min_gain=1e-2, workers: bool = True):
+                    zero_tol=1e-6, min_gain=1e-2, workers: bool = True, pose_ids=None):
     """All tuples [P,T,k] through Alg. 2: returns (tuples [P,T,k] int32,
-    margin [P,T], accept [P,T] uint8, ambiguous [P,T] bool)."""
+    margin [P,T], accept [P,T] uint8, ambiguous [P,T] bool).  pose_ids [P]: the
+    index of each row's pose in its request, which keys the row's draws (default
+    0 .. P-1), so that rows sampled from a larger request keep their draws."""
     P = masks.shape[0]
+    pose_ids = np.arange(P) if pose_ids is None else np.asarray(pose_ids, np.int64)
+    if pose_ids.shape != (P,):
+        raise ValueError("pose_ids must hold one index per mask row")
     k = tuples.shape[-1]
     flat = np.asarray(tuples, np.int64).reshape(-1, k)
     ff = np.asarray(fingers, np.int64).reshape(-1, k)
@@ -186,7 +192,7 @@ def optimize_tuples(soa, masks, tuples, fingers, T, mu, K, c, rho, eps, seed, n_
     soa = np.ascontiguousarray(soa, np.float32)
     masks = np.ascontiguousarray(masks, np.uint32)
     c = np.asarray(c, np.float64)
-    base = (soa, masks, flat, ff)
+    base = (soa, masks, flat, ff, pose_ids)
     rest = (T, float(mu), int(K), c, float(rho), float(eps), int(seed), int(n_outer), int(n_inner), float(sigma),
             float(zero_tol), float(min_gain))
     if workers and n > 8:

@@ -96,3 +96,38 @@ def test_fswo_parity(cf):
         nu = -soa[3:6, tup[i, t, 0]].astype(np.float64)
         exact = float(nu @ nu + np.sum(np.cross(r, nu) ** 2) / w.obj.rho ** 2)
         assert abs(gv[i, t] - exact) <= 1e-4 * exact and abs(ov[i, t] - exact) <= 1e-9, (gv[i, t], ov[i, t], exact)
+
+
+def test_gswo_full_size_sampled(cf):
+    """The benchmark's Eq. GSWO configuration at full size (hand20_tool: the whole field, 32,768 poses x
+    128 sampled tuples, 256 iterations): 1,000 tuples drawn over the whole launch against the oracle."""
+    w = synth.workload("hand20_tool")
+    dev = torch.device("cuda:0")
+    F, W = w.hand.F, (w.obj.N + 31) // 32
+    field = cf.build(w.hand, w.inv_h, w.bins, torch.from_numpy(w.q).to(dev))
+    soa_h = np.ascontiguousarray(w.obj.soa())
+    soa = torch.from_numpy(soa_h).to(dev)
+    masks = torch.empty((w.P, F, W), dtype=torch.int32, device=dev)
+    counts = torch.empty((w.P, F), dtype=torch.int32, device=dev)
+    tuples = torch.empty((w.P, w.T, w.k), dtype=torch.int32, device=dev)
+    fingers = torch.empty((w.P, w.T, w.k), dtype=torch.uint8, device=dev)
+    cf.query_domains(field, soa, torch.from_numpy(w.poses).to(dev), masks, counts)
+    prm = cf.score_params(w.T, w.k, w.mu, w.K, w.eps, w.obj.centroid, w.obj.rho, w.seed)
+    cf.sample_tuples(soa, F, masks, counts, prm, tuples, fingers)
+    prm_g = cf.score_params(w.T, w.k, w.mu, w.K, w.eps, w.obj.centroid, w.obj.rho, w.seed, tuples_given=True)
+    gv, ga = cf.score_gswo(soa, prm_g, tuples, 256, EPS_G)
+    torch.cuda.synchronize()
+    assert cf.device_status() == 0
+    idx = np.random.default_rng(5).choice(w.P * w.T, 1000, replace=False)
+    tup = tuples.reshape(-1, w.k)[torch.from_numpy(idx).to(dev)].cpu().numpy()
+    gv = gv.reshape(-1)[torch.from_numpy(idx).to(dev)].cpu().numpy().astype(np.float64)
+    ga = ga.reshape(-1)[torch.from_numpy(idx).to(dev)].cpu().numpy()
+    ov = G.score_gswo(soa_h, tup, w.mu, w.obj.centroid, w.obj.rho, 256)
+    fin = np.isfinite(ov)
+    assert np.array_equal(np.isfinite(gv), fin)
+    err = np.abs(gv[fin] - ov[fin]) / np.maximum(ov[fin], EPS_G)
+    print(f"hand20_tool full size: {fin.sum()} sampled tuples, max relative error {err.max():.3g}, "
+          f"accept {ga[fin].mean():.3f}")
+    assert err.max() <= REL
+    firm = fin & (np.abs(ov - EPS_G) > REL * np.maximum(ov, EPS_G))
+    assert np.array_equal(ga[firm], (ov[firm] <= EPS_G).astype(np.uint8))

@@ -168,3 +168,48 @@ def test_optimize_schedule_independent(cf):
         assert torch.equal(m_n, m_all[:n]) and torch.equal(a_n, a_all[:n]), n
     assert cf.device_status() == 0
     assert (t_all.cpu().numpy() != tup).any(), "the optimisation moved no contact"
+
+
+def test_optimize_full_size_sampled(cf):
+    """The benchmark's Alg. 2 configuration at full size (hand20_tool: the whole field, 32,768 poses x
+    128 tuples, warm start): the oracle re-runs six poses spread over the request from the same
+    starting tuples and the GPU's masks for those poses, their indices in the request keying the draws.
+    Decisions are checked by the same rule as the small cases."""
+    w = synth.workload("hand20_tool")
+    dev = torch.device("cuda:0")
+    F, W = w.hand.F, (w.obj.N + 31) // 32
+    field = cf.build(w.hand, w.inv_h, w.bins, torch.from_numpy(w.q).to(dev))
+    soa_h = np.ascontiguousarray(w.obj.soa())
+    soa = torch.from_numpy(soa_h).to(dev)
+    masks = torch.empty((w.P, F, W), dtype=torch.int32, device=dev)
+    counts = torch.empty((w.P, F), dtype=torch.int32, device=dev)
+    tuples = torch.empty((w.P, w.T, w.k), dtype=torch.int32, device=dev)
+    fingers = torch.empty((w.P, w.T, w.k), dtype=torch.uint8, device=dev)
+    cf.query_domains(field, soa, torch.from_numpy(w.poses).to(dev), masks, counts)
+    prm = cf.score_params(w.T, w.k, w.mu, w.K, w.eps, w.obj.centroid, w.obj.rho, w.seed)
+    cf.sample_tuples(soa, F, masks, counts, prm, tuples, fingers)
+    rows = np.array([0, 4097, 12345, 20000, 29999, w.P - 1])
+    ri = torch.from_numpy(rows).to(dev)
+    t0, f0 = tuples[ri].cpu().numpy(), fingers[ri].cpu().numpy()
+    m0 = masks[ri].cpu().numpy().view(np.uint32)
+    kw = dict(n_outer=2, n_inner=8, sigma=0.005, zero_tol=1e-6, min_gain=1e-2)
+    prm_opt = cf.score_params(w.T, w.k, w.mu, w.K, w.eps, w.obj.centroid, w.obj.rho, w.seed, tuples_given=True)
+    margin, accept = cf.optimize_tuples(soa, F, masks, prm_opt, cf.opt_params(**kw, warm_start=True), tuples,
+                                        fingers)
+    torch.cuda.synchronize()
+    assert cf.device_status() == 0
+    gt, gm, ga = tuples[ri].cpu().numpy(), margin[ri].cpu().numpy(), accept[ri].cpu().numpy()
+    ot, om, oa, amb = CO.optimize_tuples(soa_h, m0, t0, f0, w.T, w.mu, w.K, w.obj.centroid, w.obj.rho, w.eps, w.seed,
+                                         pose_ids=rows, **kw)
+    clear = ~amb
+    info = f"hand20_tool full size, poses {rows.tolist()}: ambiguous {amb.mean():.4f}, changed {(ot != t0).any(-1).mean():.3f}"
+    print(info)
+    assert amb.mean() < 0.10, info
+    assert (ot != t0).any(), "the optimisation moved no contact"
+    assert np.array_equal(gt[clear], ot[clear]), info
+    assert np.array_equal(np.isfinite(gm), np.isfinite(om)), info
+    fin = clear & np.isfinite(om)
+    err = np.abs(gm[fin] - np.maximum(om[fin], 0))
+    assert np.all(err <= 1e-4 * np.maximum(om[fin], w.eps)), (info, err.max())
+    firm = fin & (np.abs(om - w.eps) > 1e-4 * np.maximum(om, w.eps))
+    assert np.array_equal(ga[firm], oa[firm]), info

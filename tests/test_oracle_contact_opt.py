@@ -115,3 +115,19 @@ def test_degenerate_settings_leave_tuples(hand16_small):
     assert np.allclose(mm0[fin], m0[fin], rtol=1e-12, atol=0)
     ts, _, _, _ = CO.optimize_tuples(*args, sigma=0.0)  # every mutation projects back onto p_i (or a copy)
     assert np.array_equal(ts, tup)
+
+
+def test_pose_ids_key_the_draws(hand16_small):
+    """Rows taken out of a request keep their results when their pose indices come with them (the
+    draws are keyed by the pose's index in its request), and differ when they do not."""
+    w, soa, m, tup, fing, m0, a0 = hand16_small
+    args = (w.T, w.mu, w.K, w.obj.centroid, w.obj.rho, w.eps, w.seed)
+    ot, om, _, _ = CO.optimize_tuples(soa, m, tup, fing, *args)
+    rows = np.array([1, 0])
+    st, sm, _, _ = CO.optimize_tuples(soa, m[rows], tup[rows], fing[rows], *args, pose_ids=rows)
+    assert np.array_equal(st, ot[rows])
+    assert np.array_equal(sm, om[rows])
+    dt, _, _, _ = CO.optimize_tuples(soa, m[rows], tup[rows], fing[rows], *args)  # keyed as poses 0 and 1 instead
+    assert not np.array_equal(dt, ot[rows])
+    with pytest.raises(ValueError):
+        CO.optimize_tuples(soa, m[rows], tup[rows], fing[rows], *args, pose_ids=[0])
