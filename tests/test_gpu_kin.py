@@ -139,8 +139,14 @@ def test_ik_parity(cf, name, P, S):
     field = cf.build(w.hand, w.inv_h, w.bins, torch.from_numpy(w.q).cuda(), want_rep=True)
     soa, tup, fing, valid = _oracle_tuples(w)
     g, o, pr = _ik_both(cf, w, field, soa, tup, fing, valid)
-    n, k, F = valid.size, w.k, w.hand.F
     assert cf.device_status() == 0
+    _check_ik(w, g, o, pr, tup, fing, valid, name, np.arange(valid.size))
+
+
+def _check_ik(w, g, o, pr, tup, fing, valid, name, slots):
+    """GPU IK outputs g against the oracle's o (pr: the oracle under a perturbation, for the slots a
+    rounding could tip) on the same slots; slots are the slots' indices in the GPU launch."""
+    n, k, F = valid.size, w.k, w.hand.F
     sens = _sensitive(w, o, pr, tup, fing, valid).any(axis=1)
     att = valid.astype(bool)
     fc = fing.reshape(n, k).astype(np.int64)
@@ -160,7 +166,7 @@ def test_ik_parity(cf, name, P, S):
         return bool(g["ok"][u] != o["ok"][u]) or not np.array_equal(g["used"][u], o["used"][u])
 
     clear0 = att & ~sens
-    mm = np.array([mismatch(u) for u in range(n)]) & clear0
+    mm = np.array([bool(clear0[u]) and mismatch(u) for u in range(n)], bool)
     assert not np.any(mm & ~start_amb), f"{int(np.sum(mm & ~start_amb))} slots differ with a start clear of the band"
     clear = clear0 & ~mm
     rows = np.nonzero(clear)[0]
@@ -181,7 +187,7 @@ def test_ik_parity(cf, name, P, S):
     # structure: bit-exact on every clear slot
     assert np.array_equal(g["used"][clear], o["used"][clear]), info
     assert not g["ok"][~att].any(), info
-    e = np.arange(n * k).reshape(n, k)
+    e = np.asarray(slots, np.int64)[:, None] * k + np.arange(k)  # contacts are numbered by the launch's slots
     assert np.array_equal(g["rtuples"], np.where(g["ok"][:, None].astype(bool), e, -1)), info
     # values of clear contacts
     assert d["q"] <= TOL_Q and d["pos"] <= TOL_POS and d["cos"] <= TOL_COS, info
@@ -197,6 +203,53 @@ def test_ik_parity(cf, name, P, S):
     assert np.all(np.isinf(g["resid"][~att, :, 0])) and np.all(g["resid"][~att, :, 1] == -2)
     if name != "tiny_sphere":
         assert o["ok"][att].sum() > 0 and g["ok"][att].sum() > 0
+
+
+def test_ik_full_size_sampled(cf):
+    """The benchmark's IK configuration at full size (hand20_tool: the whole field with its
+    representatives, 32,768 poses x 128 tuples, IK on every accepted tuple): the oracle solves the
+    slots of the eight poses with the most accepted tuples, from the full field's representatives,
+    and the slots are checked by the rule of the small cases."""
+    from types import SimpleNamespace
+    w = synth.workload("hand20_tool")
+    dev = torch.device("cuda:0")
+    F, W, T, k = w.hand.F, (w.obj.N + 31) // 32, w.T, w.k
+    field = cf.build(w.hand, w.inv_h, w.bins, torch.from_numpy(w.q).to(dev), want_rep=True)
+    soa_h = np.ascontiguousarray(w.obj.soa())
+    soa, poses = torch.from_numpy(soa_h).to(dev), torch.from_numpy(w.poses).to(dev)
+    masks = torch.empty((w.P, F, W), dtype=torch.int32, device=dev)
+    counts = torch.empty((w.P, F), dtype=torch.int32, device=dev)
+    tuples = torch.empty((w.P, T, k), dtype=torch.int32, device=dev)
+    fingers = torch.empty((w.P, T, k), dtype=torch.uint8, device=dev)
+    margin = torch.empty((w.P, T), dtype=torch.float32, device=dev)
+    accept = torch.empty((w.P, T), dtype=torch.uint8, device=dev)
+    cf.query_domains(field, soa, poses, masks, counts)
+    cf.sample_tuples(soa, F, masks, counts, cf.score_params(T, k, w.mu, w.K, w.eps, w.obj.centroid, w.obj.rho, w.seed),
+                     tuples, fingers)
+    cf.score_tuples(soa, F, None, None,
+                    cf.score_params(T, k, w.mu, w.K, w.eps, w.obj.centroid, w.obj.rho, w.seed, tuples_given=True),
+                    tuples, margin=margin, accept=accept)
+    g_all = cf.ik_dls(field, soa, poses, T, k, tuples, fingers, accept, cf.ik_params())
+    torch.cuda.synchronize()
+    assert cf.device_status() == 0
+    acc = accept.cpu().numpy()
+    rows = np.sort(np.argsort(-acc.sum(axis=1, dtype=np.int64), kind="stable")[:8])
+    slots = (rows[:, None] * T + np.arange(T)).reshape(-1)
+    ek = (slots[:, None] * k + np.arange(k)).reshape(-1)
+    ga = {key: v.cpu().numpy() for key, v in g_all.items()}
+    g = dict(q=ga["q"][slots], used=ga["used"][slots], contacts=ga["contacts"][:, ek], rtuples=ga["rtuples"][slots],
+             resid=ga["resid"][slots], ok=ga["ok"][slots])
+    ri = torch.from_numpy(rows).to(dev)
+    tup, fing = tuples[ri].cpu().numpy(), fingers[ri].cpu().numpy()
+    valid = acc[rows].reshape(-1).astype(np.uint8)
+    both = {f: oracle.rep_codes(w.hand, w.q, w.inv_h, w.bins, f, with_sure=True, tau=1e-6) for f in range(F)}
+    okw = dict(rep={f: v[0] for f, v in both.items()}, rep_sure={f: v[1] for f, v in both.items()}, beta=0.01,
+               lam=1e-4, n_phase1=16, n_rounds=4, n_phase2=4, tol_pos=2e-3, tol_deg=20.0)
+    ws = SimpleNamespace(hand=w.hand, q=w.q, inv_h=w.inv_h, bins=w.bins, poses=w.poses[rows], T=T, k=k)
+    o = K.ik_dls(w.hand, w.q, w.inv_h, w.bins, soa_h, ws.poses, T, k, tup, fing, valid, **okw)
+    pr = K.ik_dls(w.hand, w.q, w.inv_h, w.bins, soa_h, ws.poses, T, k, tup, fing, valid, perturb=SENS_PERTURB, **okw)
+    assert valid.sum() >= 40, f"only {int(valid.sum())} accepted slots on the sampled poses"
+    _check_ik(ws, g, o, pr, tup, fing, valid, "hand20_tool full size", slots)
 
 
 def test_ik_edge_cases(cf):
