@@ -403,13 +403,18 @@ def random_joint(lo, hi, word):
 
 
 def realize(hand, sdf, sdf_amb, sdf_lo, sdf_h, poses, T: int, q, used, gate_a, gate_b, pen_margin=2e-3,
-            axis_step=1.25e-3, seed=0, band=1e-5):
+            axis_step=1.25e-3, seed=0, band=1e-5, slot_ids=None):
     """Post-processing of tuple slots (Sec. 5.6).  Returns (q [n,F,J] float32
     with free joints filled, flags [n] uint8 (1 gated out, 2 penetration,
-    4 self-collision), ambiguous [n] bool)."""
+    4 self-collision), ambiguous [n] bool).  Slot u takes pose u // T; its
+    draws are keyed by slot_ids[u], its index in its launch (default u), so
+    that slots taken out of a larger launch keep their draws."""
     q = np.array(q, np.float32, copy=True)
     used = np.asarray(used)
     n = q.shape[0]
+    slot_ids = np.arange(n) if slot_ids is None else np.asarray(slot_ids, np.int64)
+    if slot_ids.shape != (n,):
+        raise ValueError("slot_ids must hold one index per slot")
     F, J = hand.F, hand.J
     ga = np.ones(n, bool) if gate_a is None else np.asarray(gate_a).astype(bool)
     gb = np.ones(n, bool) if gate_b is None else np.asarray(gate_b).astype(bool)
@@ -423,7 +428,7 @@ def realize(hand, sdf, sdf_amb, sdf_lo, sdf_h, poses, T: int, q, used, gate_a, g
             words = None
             for j in range(J):
                 if j % 4 == 0:
-                    words = philox4x32_10([u, f, j // 4, 0x7EA1], key)
+                    words = philox4x32_10([int(slot_ids[u]), f, j // 4, 0x7EA1], key)
                 if not used[u, f, j]:
                     q[u, f, j] = random_joint(hand.lo[f, j], hand.hi[f, j], words[j % 4])
         R, t, _ = chain(hand, np.arange(F), q[u].astype(np.float64))

@@ -205,15 +205,16 @@ def _check_ik(w, g, o, pr, tup, fing, valid, name, slots):
         assert o["ok"][att].sum() > 0 and g["ok"][att].sum() > 0
 
 
-def test_ik_full_size_sampled(cf):
-    """The benchmark's IK configuration at full size (hand20_tool: the whole field with its
-    representatives, 32,768 poses x 128 tuples, IK on every accepted tuple): the oracle solves the
-    slots of the eight poses with the most accepted tuples, from the full field's representatives,
-    and the slots are checked by the rule of the small cases."""
-    from types import SimpleNamespace
+@pytest.fixture(scope="module")
+def full_h20(cf):
+    """The benchmark's realized step once at full size (hand20_tool: the whole field with its
+    representatives, 32,768 poses x 128 tuples): query, sampling, scoring, IK on every accepted tuple,
+    re-scoring of the IK contacts, the object SDF on the benchmark's 4 mm grid and the realization
+    filter.  Host copies of the slots of the eight poses with the most accepted tuples."""
     w = synth.workload("hand20_tool")
     dev = torch.device("cuda:0")
     F, W, T, k = w.hand.F, (w.obj.N + 31) // 32, w.T, w.k
+    n = w.P * T
     field = cf.build(w.hand, w.inv_h, w.bins, torch.from_numpy(w.q).to(dev), want_rep=True)
     soa_h = np.ascontiguousarray(w.obj.soa())
     soa, poses = torch.from_numpy(soa_h).to(dev), torch.from_numpy(w.poses).to(dev)
@@ -229,27 +230,68 @@ def test_ik_full_size_sampled(cf):
     cf.score_tuples(soa, F, None, None,
                     cf.score_params(T, k, w.mu, w.K, w.eps, w.obj.centroid, w.obj.rho, w.seed, tuples_given=True),
                     tuples, margin=margin, accept=accept)
-    g_all = cf.ik_dls(field, soa, poses, T, k, tuples, fingers, accept, cf.ik_params())
+    ik = cf.ik_dls(field, soa, poses, T, k, tuples, fingers, accept, cf.ik_params())
+    prm_re = cf.score_params(1, k, w.mu, w.K, w.eps, w.obj.centroid, w.obj.rho, w.seed, tuples_given=True)
+    _, _, _, acc2 = cf.score_tuples(ik["contacts"], F, None, None, prm_re, tuples=ik["rtuples"].view(n, 1, k))
+    lo, h, dims = cf.sdf_box(soa_h, 0.004, 0.02)
+    sdf = cf.Sdf(soa, lo, h, dims)
+    q_ik = ik["q"].clone()
+    pen, step, seed = 2e-3, 0.5 / float(w.inv_h), w.seed
+    flags = cf.realize(field, sdf, poses, T, ik["q"], ik["used"], ik["ok"], acc2.view(n),
+                       cf.realize_params(pen, step, seed))
     torch.cuda.synchronize()
     assert cf.device_status() == 0
     acc = accept.cpu().numpy()
     rows = np.sort(np.argsort(-acc.sum(axis=1, dtype=np.int64), kind="stable")[:8])
     slots = (rows[:, None] * T + np.arange(T)).reshape(-1)
     ek = (slots[:, None] * k + np.arange(k)).reshape(-1)
-    ga = {key: v.cpu().numpy() for key, v in g_all.items()}
-    g = dict(q=ga["q"][slots], used=ga["used"][slots], contacts=ga["contacts"][:, ek], rtuples=ga["rtuples"][slots],
-             resid=ga["resid"][slots], ok=ga["ok"][slots])
+    ga = {key: v.cpu().numpy() for key, v in ik.items()}
+    g_ik = dict(q=q_ik.cpu().numpy()[slots], used=ga["used"][slots], contacts=ga["contacts"][:, ek],
+                rtuples=ga["rtuples"][slots], resid=ga["resid"][slots], ok=ga["ok"][slots])
     ri = torch.from_numpy(rows).to(dev)
-    tup, fing = tuples[ri].cpu().numpy(), fingers[ri].cpu().numpy()
-    valid = acc[rows].reshape(-1).astype(np.uint8)
+    return dict(w=w, soa=soa_h, rows=rows, slots=slots, g_ik=g_ik, tup=tuples[ri].cpu().numpy(),
+                fing=fingers[ri].cpu().numpy(), valid=acc[rows].reshape(-1).astype(np.uint8),
+                q_real=ga["q"][slots], acc2=acc2.cpu().numpy().reshape(-1)[slots],
+                flags=flags.cpu().numpy()[slots], grid=sdf.grid(), sdf_lo=lo, sdf_h=h, pen=pen, step=step, seed=seed)
+
+
+def test_ik_full_size_sampled(full_h20):
+    """IK in the benchmark's configuration at full size: the oracle solves the sampled slots from the
+    full field's representatives, checked by the rule of the small cases."""
+    from types import SimpleNamespace
+    d = full_h20
+    w, rows, valid = d["w"], d["rows"], d["valid"]
+    F, T, k = w.hand.F, w.T, w.k
     both = {f: oracle.rep_codes(w.hand, w.q, w.inv_h, w.bins, f, with_sure=True, tau=1e-6) for f in range(F)}
     okw = dict(rep={f: v[0] for f, v in both.items()}, rep_sure={f: v[1] for f, v in both.items()}, beta=0.01,
                lam=1e-4, n_phase1=16, n_rounds=4, n_phase2=4, tol_pos=2e-3, tol_deg=20.0)
     ws = SimpleNamespace(hand=w.hand, q=w.q, inv_h=w.inv_h, bins=w.bins, poses=w.poses[rows], T=T, k=k)
-    o = K.ik_dls(w.hand, w.q, w.inv_h, w.bins, soa_h, ws.poses, T, k, tup, fing, valid, **okw)
-    pr = K.ik_dls(w.hand, w.q, w.inv_h, w.bins, soa_h, ws.poses, T, k, tup, fing, valid, perturb=SENS_PERTURB, **okw)
+    o = K.ik_dls(w.hand, w.q, w.inv_h, w.bins, d["soa"], ws.poses, T, k, d["tup"], d["fing"], valid, **okw)
+    pr = K.ik_dls(w.hand, w.q, w.inv_h, w.bins, d["soa"], ws.poses, T, k, d["tup"], d["fing"], valid,
+                  perturb=SENS_PERTURB, **okw)
     assert valid.sum() >= 40, f"only {int(valid.sum())} accepted slots on the sampled poses"
-    _check_ik(ws, g, o, pr, tup, fing, valid, "hand20_tool full size", slots)
+    _check_ik(ws, d["g_ik"], o, pr, d["tup"], d["fing"], valid, "hand20_tool full size", d["slots"])
+
+
+def test_realize_full_size_sampled(full_h20):
+    """The realization filter in the benchmark's configuration at full size, on the sampled slots and
+    given the GPU's IK joints, re-score flags and SDF grid (each checked on its own): free joints bit
+    for bit (drawn by the slots' indices in the launch), flags equal off the oracle's band."""
+    d = full_h20
+    w = d["w"]
+    gi = d["g_ik"]
+    oq, of, oamb = K.realize(w.hand, d["grid"], np.zeros(d["grid"].shape, bool), d["sdf_lo"], d["sdf_h"],
+                             w.poses[d["rows"]], w.T, gi["q"], gi["used"], gi["ok"], d["acc2"], pen_margin=d["pen"],
+                             axis_step=d["step"], seed=d["seed"], slot_ids=d["slots"])
+    gate = gi["ok"].astype(bool) & d["acc2"].astype(bool)
+    print(f"hand20_tool full size: {int(gate.sum())} slots realised, {int((of[gate] == 0).sum())} valid, "
+          f"{int(oamb[gate].sum())} in the band")
+    assert gate.sum() >= 20
+    assert np.array_equal(d["q_real"], oq)
+    assert np.all(d["flags"][~gate] == 1)
+    clear = gate & ~oamb
+    assert np.array_equal(d["flags"][clear], of[clear])
+    assert oamb[gate].mean() < 0.02
 
 
 def test_ik_edge_cases(cf):

@@ -416,3 +416,24 @@ def test_realize_fills_free_joints_only():
     lo = np.broadcast_to(hand.lo, q.shape)[free]
     hi = np.broadcast_to(hand.hi, q.shape)[free]
     assert np.all((qo[free] >= lo) & (qo[free] <= hi))
+
+
+def test_realize_slot_ids_key_the_draws():
+    """Slots taken out of a launch keep their free joints when their slot indices come with them."""
+    hand = synth.hand_anthropomorphic(4)
+    n, T = 6, 3
+    rng = np.random.default_rng(13)
+    q = rng.uniform(hand.lo, hand.hi, (n, hand.F, hand.J)).astype(np.float32)
+    used = (rng.random((n, hand.F, hand.J)) < 0.5).astype(np.uint8)
+    grid = np.full((4, 4, 4), 1.0)
+    amb = np.zeros_like(grid, bool)
+    poses = np.tile(np.array([1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 5.0], np.float32), (n // T, 1))
+    args = (hand, grid, amb, np.zeros(3, np.float32), 0.01)
+    qa, fa, _ = K.realize(*args, poses, T, q, used, None, None, seed=7)
+    sl = np.arange(T, 2 * T)  # the second pose's slots
+    qs, fs, _ = K.realize(*args, poses[1:], T, q[sl], used[sl], None, None, seed=7, slot_ids=sl)
+    assert np.array_equal(qs, qa[sl]) and np.array_equal(fs, fa[sl])
+    qd, _, _ = K.realize(*args, poses[1:], T, q[sl], used[sl], None, None, seed=7)  # keyed as slots 0 .. T-1
+    assert not np.array_equal(qd, qa[sl])
+    with pytest.raises(ValueError):
+        K.realize(*args, poses[1:], T, q[sl], used[sl], None, None, seed=7, slot_ids=sl[:1])
