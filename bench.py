@@ -748,9 +748,10 @@ def run_optimized(cf, torch, dev, w, steps, soa, poses, masks, counts, tuples, f
 def opt_launches(k: int, n_outer: int, warm_start: bool) -> int:
     """Kernels of one cf_optimize_tuples call: word and chunk boxes, begin, the
     tuples' own LPs and their selection, then per step (n_outer x k) the
-    projection, the candidates' LPs, the selection and (warm start) the
-    winners' replay, and the finish."""
-    return 5 + n_outer * k * (4 if warm_start else 3) + 1
+    projection, the candidate job list (count, scan, write), the candidates'
+    LPs, the selection and, with the warm start, the winners' job list and
+    replay, and the finish."""
+    return 5 + n_outer * k * (10 if warm_start else 6) + 1
 
 
 # ---------------------------------------------------------------------------

@@ -1110,7 +1110,7 @@ __global__ void __launch_bounds__(kLaneThreads) k_opt_lp_jobs(const ScoreArgs a,
     const int tid = threadIdx.x, lane = tid & 31;
     const int k = a.k, K = KT > 0 ? KT : a.K, kK = k * K;
     const int SPT = NI * k;  // result slots per tuple
-    const unsigned n_jobs = MODE == kJobCand ? *ps.n_jobs : n_slots;
+    const unsigned n_jobs = MODE != kJobInit ? *ps.n_jobs : n_slots;
     const size_t nk = (size_t)a.P * a.T * k;                     // the bases' word stride
     constexpr int refill = kOptRefill;
     const float mu = a.mu;
@@ -1143,7 +1143,7 @@ __global__ void __launch_bounds__(kLaneThreads) k_opt_lp_jobs(const ScoreArgs a,
                     state = kDone;
                 } else {
                     bool run = true;
-                    if (MODE == kJobCand) {
+                    if (MODE != kJobInit) {  // a listed job: every one runs
                         const unsigned dsc = ps.jobs[q];
                         u = dsc >> 6;
                         g = (int)((dsc >> 2) & 15u);
@@ -1152,7 +1152,7 @@ __global__ void __launch_bounds__(kLaneThreads) k_opt_lp_jobs(const ScoreArgs a,
                         u = q / (unsigned)k;
                         j = (int)(q - u * (unsigned)k);
                         g = 0;
-                        run = ps.live[u] != 0 && (MODE == kJobInit || ps.win[u] >= 0);
+                        run = ps.live[u] != 0;
                     }
                     if (run) {
                         for (int d = 0; d < k; ++d) {
@@ -1291,18 +1291,26 @@ __global__ void __launch_bounds__(kOptThreads, 7) k_opt_project(const ScoreArgs 
     }
 }
 
-// The step's candidate LP jobs as one list in tuple order, so that the lanes of a block read
-// neighbouring tuples' bases (word-major rows: neighbouring tuples share sectors): the jobs per
-// chunk of kJobChunk tuples, an exclusive scan of those counts (one block; it also writes the
-// total), then every chunk writes its tuples' jobs from its offset.
+// The step's candidate LP jobs, and then its winners' replays, as one list in tuple order, so that
+// the lanes of a block read neighbouring tuples' bases (word-major rows: neighbouring tuples share
+// sectors) and no lane takes a slot without work: the jobs per chunk of kJobChunk tuples, an
+// exclusive scan of those counts (one block; it also writes the total), then every chunk writes its
+// tuples' jobs from its offset.
 constexpr int kJobChunk = 4096;
 constexpr int kJobThreads = 256;
 
+// Jobs of tuple u over k: the step's candidates (kJobCand), or 1 when its winner's LPs replay (kJobWin).
+template <int MODE>
+__device__ __forceinline__ unsigned listed_per_tuple(const OptPhaseState &ps, unsigned u) {
+    return MODE == kJobCand ? (unsigned)ps.n_todo[u] : (ps.live[u] != 0 && ps.win[u] >= 0 ? 1u : 0u);
+}
+
+template <int MODE>
 __global__ void __launch_bounds__(kJobThreads) k_job_counts(const OptPhaseState ps, unsigned n, int k) {
     __shared__ unsigned s_w[kJobThreads / 32];
     const unsigned c0 = blockIdx.x * kJobChunk, c1 = min(n, c0 + kJobChunk);
     unsigned c = 0;
-    for (unsigned u = c0 + threadIdx.x; u < c1; u += kJobThreads) c += (unsigned)ps.n_todo[u];
+    for (unsigned u = c0 + threadIdx.x; u < c1; u += kJobThreads) c += listed_per_tuple<MODE>(ps, u);
     c = __reduce_add_sync(kFull, c);
     if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = c;
     __syncthreads();
@@ -1317,6 +1325,7 @@ __global__ void __launch_bounds__(1024) k_job_scan(const OptPhaseState ps, int n
     block_exclusive_scan_1024(ps.chunk, nb, ps.n_jobs);
 }
 
+template <int MODE>
 __global__ void __launch_bounds__(kJobThreads) k_job_write(const OptPhaseState ps, unsigned n, int k) {
     __shared__ unsigned s_w[kJobThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1324,7 +1333,7 @@ __global__ void __launch_bounds__(kJobThreads) k_job_write(const OptPhaseState p
     unsigned run = ps.chunk[blockIdx.x];
     for (unsigned t0 = c0; t0 < c1; t0 += kJobThreads) {
         const unsigned u = t0 + threadIdx.x;
-        const unsigned cnt = u < c1 ? (unsigned)ps.n_todo[u] * (unsigned)k : 0u;
+        const unsigned cnt = u < c1 ? listed_per_tuple<MODE>(ps, u) * (unsigned)k : 0u;
         unsigned incl = cnt;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
@@ -1533,17 +1542,25 @@ cudaError_t launch_optimize(const ScoreArgs &a, int n_outer, int n_inner, float 
             err = NI == 4 ? launch_project<4>(a, o, ps, it, i, n, st)
                           : (NI == 8 ? launch_project<8>(a, o, ps, it, i, n, st) : launch_project<16>(a, o, ps, it, i, n, st));
             if (err != cudaSuccess) return err;
-            k_job_counts<<<nb, kJobThreads, 0, st>>>(ps, n, k);
+            k_job_counts<kJobCand><<<nb, kJobThreads, 0, st>>>(ps, n, k);
             if ((err = cudaGetLastError()) != cudaSuccess) return err;
             k_job_scan<<<1, 1024, 0, st>>>(ps, (int)nb);
             if ((err = cudaGetLastError()) != cudaSuccess) return err;
-            k_job_write<<<nb, kJobThreads, 0, st>>>(ps, n, k);
+            k_job_write<kJobCand><<<nb, kJobThreads, 0, st>>>(ps, n, k);
             if ((err = cudaGetLastError()) != cudaSuccess) return err;
             if ((err = lp_jobs<kJobCand>(a, ps, NI, i, warm_start, 0, st)) != cudaSuccess) return err;
             k_opt_select<<<tb, 256, 0, st>>>(a, o, ps, NI, i, 0, n);
             if ((err = cudaGetLastError()) != cudaSuccess) return err;
             // the winners' LPs again from the same starts: their optimal bases become the tuples'
-            if (warm_start && (err = lp_jobs<kJobWin>(a, ps, NI, i, 1, nk, st)) != cudaSuccess) return err;
+            if (warm_start) {  // listed like the candidates': only the tuples with a winner replay
+                k_job_counts<kJobWin><<<nb, kJobThreads, 0, st>>>(ps, n, k);
+                if ((err = cudaGetLastError()) != cudaSuccess) return err;
+                k_job_scan<<<1, 1024, 0, st>>>(ps, (int)nb);
+                if ((err = cudaGetLastError()) != cudaSuccess) return err;
+                k_job_write<kJobWin><<<nb, kJobThreads, 0, st>>>(ps, n, k);
+                if ((err = cudaGetLastError()) != cudaSuccess) return err;
+                if ((err = lp_jobs<kJobWin>(a, ps, NI, i, 1, 0, st)) != cudaSuccess) return err;
+            }
         }
     }
     k_opt_finish<<<tb, 256, 0, st>>>(a, ps, n);
