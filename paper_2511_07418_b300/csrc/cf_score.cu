@@ -1325,9 +1325,12 @@ __global__ void __launch_bounds__(1024) k_job_scan(const OptPhaseState ps, int n
     block_exclusive_scan_1024(ps.chunk, nb, ps.n_jobs);
 }
 
+constexpr int kJobStage = 8192;  // jobs of one tile staged in shared memory for coalesced writes
+
 template <int MODE>
 __global__ void __launch_bounds__(kJobThreads) k_job_write(const OptPhaseState ps, unsigned n, int k) {
     __shared__ unsigned s_w[kJobThreads / 32];
+    __shared__ unsigned s_jobs[kJobStage];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned c0 = blockIdx.x * kJobChunk, c1 = min(n, c0 + kJobChunk);
     unsigned run = ps.chunk[blockIdx.x];
@@ -1348,8 +1351,15 @@ __global__ void __launch_bounds__(kJobThreads) k_job_write(const OptPhaseState p
             before += w < warp ? s_w[w] : 0u;
             tile += s_w[w];
         }
-        const unsigned at = run + before + incl - cnt;
-        for (unsigned t = 0; t < cnt; ++t) ps.jobs[at + t] = u * 64u + (t / (unsigned)k) * 4u + t % (unsigned)k;
+        const unsigned at = before + incl - cnt;  // within the tile
+        if (tile <= (unsigned)kJobStage) {  // block-uniform: staged, then written out coalesced
+            for (unsigned t = 0; t < cnt; ++t) s_jobs[at + t] = u * 64u + (t / (unsigned)k) * 4u + t % (unsigned)k;
+            __syncthreads();
+            for (unsigned q = threadIdx.x; q < tile; q += kJobThreads) ps.jobs[run + q] = s_jobs[q];
+        } else {
+            for (unsigned t = 0; t < cnt; ++t)
+                ps.jobs[run + at + t] = u * 64u + (t / (unsigned)k) * 4u + t % (unsigned)k;
+        }
         run += tile;
     }
 }
