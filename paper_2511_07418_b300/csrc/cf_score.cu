@@ -1096,10 +1096,10 @@ __device__ __forceinline__ void basis_load_g(LaneLp &s, const float *base, size_
     s.ystat = __float_as_uint(base[(size_t)49 * stride + at]);
 }
 
-// LP jobs of one phase.  Candidates: the job list the projection kernel wrote (descriptor
-// u * 64 + g * 4 + j: tuple u, candidate g, LP j; its length is read on the device).  A
-// tuple's own LPs and the winners' replays: slots u * k + j in tuple order (the jobs write
-// the bases, whose stores then stay sequential), a slot whose tuple has no such LP ending at
+// LP jobs of one phase.  Candidates and the winners' replays: the job list written after the
+// projection or the selection (descriptor u * 64 + g * 4 + j: tuple u, candidate g, LP j; its
+// length is read on the device).  A tuple's own LPs: slots u * k + j in tuple order (the jobs
+// write the bases, whose stores then stay sequential), a slot whose tuple is not live ending at
 // once.  Lanes take jobs together, when `refill` of them wait or none is busy, from the
 // block's contiguous share.  The contact frames live in the lane's stretch of shared memory.
 template <int KT, int MODE>
@@ -1539,8 +1539,8 @@ cudaError_t launch_optimize(const ScoreArgs &a, int n_outer, int n_inner, float 
     k_chunk_boxes<<<(unsigned)(((a.W + 31) / 32 * 32 + 255) / 256), 256, 0, st>>>(a.word_box, a.W);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     const unsigned tb = (n + 255) / 256;
-    const unsigned nk = n * (unsigned)k;  // slots of the tuples' own LPs and of the replays
-    const unsigned nb = (n + kJobChunk - 1) / kJobChunk;  // chunks of the candidate job list
+    const unsigned nk = n * (unsigned)k;  // slots of the tuples' own LPs
+    const unsigned nb = (n + kJobChunk - 1) / kJobChunk;  // chunks of the job lists
     k_opt_begin<<<tb, 256, 0, st>>>(a, ps, n);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     // the tuples' own LPs, from c' = 0; their optimal bases seed the candidates
