@@ -382,9 +382,9 @@ def roofline(w, per, counters, steps, peak_fp32, n_sm, sm_mhz, nominal_fp32, ora
     tuples = counters["tuples_scored"] / steps
     setup = w.k * w.K * 15
     s_flop_own = (counters["lp_pivots"] / steps * 7 * (w.k * w.K + 6) + tuples * setup) * 2
-    s_flop_survey = None
+    s_flop_tableau = None
     if oracle_pivots_per_tuple is not None:
-        s_flop_survey = tuples * (oracle_pivots_per_tuple * 13 * 39 + setup) * 2
+        s_flop_tableau = tuples * (oracle_pivots_per_tuple * 13 * 39 + setup) * 2
     b_flop = F * w.S * w.hand.M * (18 + 3 + 3 * w.B) * 2
     traffic = NCU_TRAFFIC.get(w.name, {})
     tf = lambda flop, ms: flop / (ms * 1e-3) / 1e12
@@ -396,13 +396,13 @@ def roofline(w, per, counters, steps, peak_fp32, n_sm, sm_mhz, nominal_fp32, ora
                             "traffic": traffic.get("k_query_domains")},
         "k_sample_tuples": {"ms": per[2], "traffic": traffic.get("k_sample_tuples")},
         "k_score_lanes": {"ms": per[3], "tflops": tf(s_flop_own, per[3]),
-                          "tflops_survey_count": tf(s_flop_survey, per[3]) if s_flop_survey else None,
+                          "tflops_tableau_count": tf(s_flop_tableau, per[3]) if s_flop_tableau else None,
                           "oracle_pivots_per_tuple": oracle_pivots_per_tuple,
                           "kernel_pivots_per_tuple": counters["lp_pivots"] / max(1, counters["tuples_scored"]),
                           "traffic": traffic.get("k_score_lanes")},
     }
     for v in kernels.values():
-        for key in ("tflops", "tflops_kernel_count", "tflops_survey_count"):
+        for key in ("tflops", "tflops_kernel_count", "tflops_tableau_count"):
             if v.get(key) is not None:
                 v["frac" + key[6:]] = v[key] / peak_fp32
     dom = max(["k_query_domains", "k_score_lanes"], key=lambda k: kernels[k]["ms"])

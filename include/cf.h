@@ -677,7 +677,7 @@ typedef struct cf_grasp {
  * and h_grasps[0 .. min(count, cap)) receives them; *h_n_accepted is the full count (larger
  * than cap when h_grasps was too small).  The records are the tuples whose margin passes the
  * closure test (the output set of Alg. 1).  h_grasps is the caller's (page-locked, or the copy
- * is staged by the driver); cap = 0 with h_grasps NULL returns the count alone.  Synchronises
+ * is staged by the CUDA driver); cap = 0 with h_grasps NULL returns the count alone.  Synchronises
  * `stream`.  Errors: CF_EINVAL (as cf_plan_run_host; cap < 0; h_grasps NULL with cap > 0),
  * CF_ECUDA. */
 int cf_plan_run_host_accepted(cf_plan *plan, const cf_field *field, const float *h_soa, int32_t n,
@@ -708,7 +708,7 @@ int cf_device_counters(uint64_t counters[4], int reset);
 /* Device memory of the library's stream-ordered pool on the current device,
  * from which every library-owned buffer (fields, batches, requests, temporary
  * work lists) is drawn: usage[0] bytes in use now, usage[1] bytes reserved
- * from the driver, usage[2] the largest use since the last reset.
+ * from the CUDA driver, usage[2] the largest use since the last reset.
  * reset_high != 0 restarts that high-water mark at the current use (after
  * reading it).  The first call on a device creates the pool.  Synchronous
  * with respect to nothing: allocations still queued on a stream count once

@@ -76,7 +76,7 @@ int device_state(DevState *out) {
 // ---------------------------------------------------------------------------
 // device memory: one stream-ordered pool per device, owned by the library
 // (allocations and frees are ordered on the caller's stream; the pool keeps
-// freed memory for reuse instead of returning it to the driver)
+// freed memory for reuse instead of returning it to the CUDA driver)
 // ---------------------------------------------------------------------------
 namespace cf {
 

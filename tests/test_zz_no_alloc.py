@@ -5,7 +5,7 @@ memory while scoring (a fixed memory budget on a shared GPU, a control loop
 that must not block or fail on an allocation).  It must give the same tuples,
 fingers, margins and accept flags as the allocating entry point, call after
 call, and it must not allocate: neither the library's own device pool nor
-torch's caching allocator nor the driver may see a new allocation during the
+torch's caching allocator nor the CUDA driver may see a new allocation during the
 calls.  The first call runs in this module, so the test also covers the
 per-device set-up.  The file name makes pytest collect it last.
 """
